@@ -1,0 +1,295 @@
+"""ORACLE — TEST INFRASTRUCTURE, NOT PART OF THE LIBRARY.
+
+ctypes loader for the plain double-precision CPU statement of the turbulent gas-kinetic scheme
+(``gks_oracle.cpp``).  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU baseline
+may import this package.  It imports nothing from ``paper_1302_2132_gb300`` and the library
+imports nothing from it.
+
+Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
+  moments / time coefficients / slope solves / face flux  -- pinned (quadrature, closed forms,
+      the compact form with corrected beta, Euler and Navier-Stokes limits)
+  whole scheme (MUSCL, update, CFL step, BCs)              -- pinned (Sod exact solution,
+      conservation, free-stream preservation)
+  turbulent relaxation-time field                           -- pinned for eta = 0 and k-eps/k-omega
+      equivalence; the turbulent configurations beyond their invariants are parity unpinned
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "gks_oracle.cpp")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD_DIR, "liboracle.so")
+
+FULL, POS, NEG = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_WALL, BC_DIRICHLET, BC_OUTFLOW = 0, 1, 2, 3, 4
+TURB_NONE, TURB_MUT, TURB_KEPS, TURB_KOMEGA = 0, 1, 2, 3
+LIM_MINMOD, LIM_VANLEER = 0, 1
+ABAR_TIMEINT, ABAR_T0 = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle with the host compiler (no -march=native, no FP contraction)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "gks_oracle.h"))):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", tmp, SRC]
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("dx", ctypes.POINTER(ctypes.c_double) * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("bc_prim", (ctypes.POINTER(ctypes.c_double) * 2) * 3),
+        ("gamma", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("T_wall", ctypes.c_double),
+        ("turb_model", ctypes.c_int),
+        ("C_mu", ctypes.c_double),
+        ("beta_star", ctypes.c_double),
+        ("C_a", ctypes.c_double),
+        ("limiter", ctypes.c_int),
+        ("multid", ctypes.c_int),
+        ("abar_mode", ctypes.c_int),
+    ]
+
+
+class Face(ctypes.Structure):
+    _fields_ = [
+        ("wl", ctypes.c_double * 5), ("wr", ctypes.c_double * 5),
+        ("cl", ctypes.c_double * 5), ("cr", ctypes.c_double * 5),
+        ("sl", ctypes.c_double * 5), ("sr", ctypes.c_double * 5),
+        ("tl", (ctypes.c_double * 5) * 2), ("tr", (ctypes.c_double * 5) * 2),
+        ("dxl", ctypes.c_double), ("dxr", ctypes.c_double), ("tau_t", ctypes.c_double),
+    ]
+
+
+class FaceDiag(ctypes.Structure):
+    _fields_ = [
+        ("w0", ctypes.c_double * 5), ("al", ctypes.c_double * 5), ("ar", ctypes.c_double * 5),
+        ("bl", (ctypes.c_double * 5) * 2), ("br", (ctypes.c_double * 5) * 2),
+        ("Al", ctypes.c_double * 5), ("Ar", ctypes.c_double * 5),
+        ("abl", ctypes.c_double * 5), ("abr", ctypes.c_double * 5),
+        ("bb", (ctypes.c_double * 5) * 2), ("Ab", ctypes.c_double * 5),
+        ("tau", ctypes.c_double), ("T", ctypes.c_double * 6),
+    ]
+
+
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(LIB)
+            L.orc_umoments.argtypes = [_D, _D, _I, _I, _PD]
+            L.orc_ximoments.argtypes = [_D, _D, _I, _PD]
+            L.orc_time_coeffs.argtypes = [_D, _D, _PD]
+            L.orc_slope.argtypes = [_I, _D, _PD, _PD, _PD]
+            L.orc_face_flux.argtypes = [_I, _D, _D, _D, _D, _I, _I, ctypes.POINTER(Face), _PD,
+                                        ctypes.POINTER(FaceDiag)]
+            L.orc_face_flux_compact.argtypes = [_I, _D, _D, _D, _D, _I, _I, _I, ctypes.POINTER(Face), _PD]
+            L.orc_euler_flux.argtypes = [_I, _D, _PD, _PD]
+            P = ctypes.POINTER(Problem)
+            L.orc_prim_to_cons.argtypes = [P, _PD, _PD, ctypes.c_long]
+            L.orc_cons_to_prim.argtypes = [P, _PD, _PD, ctypes.c_long]
+            L.orc_compute_dt.argtypes = [P, _PD, _D, _PD]
+            L.orc_tau_turb.argtypes = [P, _PD, _PD, _PD, _PD]
+            L.orc_rarefaction.argtypes = [P, _PD, _PD, _PD, _PD]
+            L.orc_step.argtypes = [P, _PD, _PD, _PD, _D, _PD, _I]
+            L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_PD)
+
+
+# ------------------------------------------------------------------------------------------------
+# Point functions
+# ------------------------------------------------------------------------------------------------
+def umoments(U, lam, region, nmax):
+    out = np.zeros(nmax + 1)
+    lib().orc_umoments(U, lam, region, nmax, _ptr(out))
+    return out
+
+
+def ximoments(K, lam, lmax):
+    out = np.zeros(lmax + 1)
+    lib().orc_ximoments(K, lam, lmax, _ptr(out))
+    return out
+
+
+def time_coeffs(dt, tau):
+    """T0..T5 and dt^2/2 - T2 of the time integral of Eq. resultingf."""
+    out = np.zeros(7)
+    lib().orc_time_coeffs(dt, tau, _ptr(out))
+    return out
+
+
+def slope(D, K, w, rhs):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    out = np.zeros(D + 2)
+    lib().orc_slope(D, K, _ptr(w), _ptr(rhs), _ptr(out))
+    return out
+
+
+def make_face(D, wl, wr, cl=None, cr=None, sl=None, sr=None, tl=None, tr=None, dxl=0.5, dxr=0.5, tau_t=0.0):
+    nv = D + 2
+    f = Face()
+    z = np.zeros(nv)
+    for name, val in (("wl", wl), ("wr", wr), ("cl", wl if cl is None else cl),
+                      ("cr", wr if cr is None else cr), ("sl", z if sl is None else sl),
+                      ("sr", z if sr is None else sr)):
+        arr = getattr(f, name)
+        for v in range(nv):
+            arr[v] = float(val[v])
+    for name, val in (("tl", tl), ("tr", tr)):
+        arr = getattr(f, name)
+        if val is not None:
+            for k in range(D - 1):
+                for v in range(nv):
+                    arr[k][v] = float(val[k][v])
+    f.dxl, f.dxr, f.tau_t = dxl, dxr, tau_t
+    return f
+
+
+def face_flux(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIMEINT, diag=False):
+    F = np.zeros(D + 2)
+    dg = FaceDiag()
+    lib().orc_face_flux(D, gamma, mu, C_a, dt, multid, abar_mode, ctypes.byref(face), _ptr(F),
+                        ctypes.byref(dg))
+    if diag:
+        return F, dg
+    return F
+
+
+def face_flux_compact(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIMEINT, printed_beta=False):
+    F = np.zeros(D + 2)
+    lib().orc_face_flux_compact(D, gamma, mu, C_a, dt, multid, abar_mode, int(printed_beta),
+                                ctypes.byref(face), _ptr(F))
+    return F
+
+
+def euler_flux(D, gamma, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    F = np.zeros(D + 2)
+    lib().orc_euler_flux(D, gamma, _ptr(w), _ptr(F))
+    return F
+
+
+# ------------------------------------------------------------------------------------------------
+# Grid problems
+# ------------------------------------------------------------------------------------------------
+class Case:
+    """A grid problem for the oracle.  Arrays are kept alive on the instance."""
+
+    def __init__(self, dim, n, dx, bc, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model=TURB_NONE,
+                 C_mu=0.09, beta_star=0.09, C_a=0.0, limiter=LIM_VANLEER, multid=1,
+                 abar_mode=ABAR_TIMEINT, bc_prim=None):
+        self.dim = dim
+        self.n = tuple(n)
+        self.P = Problem()
+        self.P.dim = dim
+        self._keep = []
+        for d in range(3):
+            self.P.n[d] = int(n[d]) if d < dim else 1
+        for d in range(dim):
+            w = np.ascontiguousarray(np.broadcast_to(np.asarray(dx[d], dtype=np.float64), (n[d],)))
+            self._keep.append(w)
+            self.P.dx[d] = _ptr(w)
+            for s in range(2):
+                self.P.bc[d][s] = int(bc[d][s])
+                if bc_prim is not None and bc_prim[d][s] is not None:
+                    a = np.ascontiguousarray(bc_prim[d][s], dtype=np.float64)
+                    self._keep.append(a)
+                    self.P.bc_prim[d][s] = _ptr(a)
+        self.P.gamma, self.P.mu, self.P.T_wall = gamma, mu, T_wall
+        self.P.turb_model, self.P.C_mu, self.P.beta_star, self.P.C_a = turb_model, C_mu, beta_star, C_a
+        self.P.limiter, self.P.multid, self.P.abar_mode = limiter, multid, abar_mode
+        self.ncell = int(np.prod(n[:dim]))
+        self.nv = dim + 2
+
+    def _state(self, W):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        assert W.size == self.nv * self.ncell
+        return W
+
+    def _field(self, f):
+        if f is None:
+            return None
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.ncell
+        return f
+
+    def prim_to_cons(self, prim):
+        prim = self._state(prim)
+        W = np.zeros_like(prim)
+        lib().orc_prim_to_cons(ctypes.byref(self.P), _ptr(prim), _ptr(W), self.ncell)
+        return W
+
+    def cons_to_prim(self, W):
+        W = self._state(W)
+        prim = np.zeros_like(W)
+        lib().orc_cons_to_prim(ctypes.byref(self.P), _ptr(W), _ptr(prim), self.ncell)
+        return prim
+
+    def compute_dt(self, W, cfl):
+        W = self._state(W)
+        dt = ctypes.c_double()
+        lib().orc_compute_dt(ctypes.byref(self.P), _ptr(W), cfl, ctypes.byref(dt))
+        return dt.value
+
+    def tau_turb(self, W, f1=None, f2=None):
+        W = self._state(W)
+        out = np.zeros(self.ncell)
+        lib().orc_tau_turb(ctypes.byref(self.P), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)), _ptr(out))
+        return out
+
+    def rarefaction(self, W, f1=None, f2=None):
+        W = self._state(W)
+        out = np.zeros(self.ncell)
+        lib().orc_rarefaction(ctypes.byref(self.P), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)),
+                              _ptr(out))
+        return out
+
+    def step(self, W, dt, f1=None, f2=None, nthreads=1):
+        """One step; returns (W_new, status, resid[3, nv] = L2, Linf, total)."""
+        W = self._state(W).copy()
+        resid = np.zeros(3 * self.nv)
+        st = lib().orc_step(ctypes.byref(self.P), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)), dt,
+                            _ptr(resid), nthreads)
+        return W, st, resid.reshape(3, self.nv)
+
+    def run(self, W, nsteps, cfl=0.5, dt_fixed=0.0, t_end=0.0, t0=0.0, f1=None, f2=None, nthreads=1):
+        """Steps until nsteps or t_end; returns (W, t, steps_done, status)."""
+        W = self._state(W).copy()
+        t = ctypes.c_double(t0)
+        done = ctypes.c_int(0)
+        st = lib().orc_run(ctypes.byref(self.P), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)),
+                           dt_fixed, cfl, nsteps, t_end, ctypes.byref(t), ctypes.byref(done), nthreads)
+        return W, t.value, done.value, st

@@ -1,0 +1,990 @@
+/*
+ * ORACLE — TEST INFRASTRUCTURE, NOT PART OF THE LIBRARY.
+ *
+ * A plain double-precision CPU statement of the gas-kinetic BGK-Navier-Stokes scheme with a
+ * turbulent relaxation time, written from Righi 2013 (Sections 2-4; the scheme is Xu's of 2001).
+ * Only the tests, __graft_entry__.smoke() and bench.py's cpu_baseline leg may load it.  It shares
+ * no code with the CUDA library: moments are taken of explicit polynomials in (u, v, w, xi^2)
+ * term by term, and every slope coefficient is found by an LU solve of the moment matrix
+ * <psi_m psi_n>, where the CUDA path uses hand-expanded closed forms.
+ *
+ * Readings of the paper that this file takes (the paper is silent, ambiguous or garbled there):
+ *   - Maxwellian normalisation: g = rho (lambda/pi)^((K+D)/2) exp(-lambda(|u-U|^2 + xi^2)),
+ *     K = 2/(gamma-1) - D internal degrees of freedom; the normalisation never enters the
+ *     rho-normalised moments (Eq. maxwellian prints a garbled exponent).
+ *   - Interface state (Eq. intermediatestate): the left Maxwellian contributes u > 0, the right
+ *     one u < 0.
+ *   - Equilibrium part (Eq. eqlgform): g0 (1 + abar x + bbar y + Abar t), with +Abar t as in
+ *     Eq. resultingf; abar_l from (w0 - W_j)/(x_{j+1/2} - x_j), abar_r from
+ *     (W_{j+1} - w0)/(x_{j+1} - x_{j+1/2}).
+ *   - Each side uses its own coefficients (index typos in Eqs. resultingf and fupwind).
+ *   - The flux is Xu's exact time integral (T0..T5 below) of Eq. resultingf; the compact form of
+ *     Eq. resultingf4 agrees with it only when beta = exp(-1/eps) (the printed eps*exp(-1/eps) does
+ *     not), which orc_face_flux_compact exhibits.
+ *   - tau = mu/p0 + tau_t + tau_a (Eqs. relaxation time, taua) is one sum used everywhere.
+ *   - Turbulent relaxation time (Eqs. tautchen, tautchenadjusted, tauttrivial): T = p/rho,
+ *     S = sqrt(2 S_ij S_ij) by central differences, nu_t = C_mu k^2/eps with eta = S k/eps, or
+ *     nu_t = k/omega with eta = S/(beta* omega); tau_t = rho nu_t / (p sqrt(1 + eta^2)); the face
+ *     value is the mean of the two cells.
+ *   - Rarefaction diagnostic (Eqs. tautautilde, tautilde): tauhat = rho/|D rho| with
+ *     D rho = -rho div U (continuity), so eps = (mu/p + tau_t) |div U| per cell.
+ *   - Reconstruction: MUSCL on conservative variables with minmod or van Leer, applied also to the
+ *     tangential slopes; a side whose reconstructed rho or p is not positive falls back to first
+ *     order at that face.
+ */
+#include "gks_oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const int MAXP = 10;  // highest power of u, v, w tabulated; (xi^2) up to 4
+
+// ---------------------------------------------------------------------------------------------
+// Polynomials in (u, v, w, xi^2): a list of monomials c * u^e0 v^e1 w^e2 (xi^2)^e3.
+// ---------------------------------------------------------------------------------------------
+struct Mono {
+  int e[4];
+  double c;
+};
+struct Poly {
+  std::vector<Mono> t;
+};
+
+Poly pconst(double c) {
+  Poly p;
+  p.t.push_back({{0, 0, 0, 0}, c});
+  return p;
+}
+// var 0,1,2 = velocity component in the normal frame (u, v, w); var 3 = xi^2
+Poly pvar(int var, double c = 1.0) {
+  Poly p;
+  Mono m = {{0, 0, 0, 0}, c};
+  m.e[var] = 1;
+  p.t.push_back(m);
+  return p;
+}
+void pmerge(Poly& p) {
+  std::vector<Mono> out;
+  for (const Mono& m : p.t) {
+    bool found = false;
+    for (Mono& o : out) {
+      if (o.e[0] == m.e[0] && o.e[1] == m.e[1] && o.e[2] == m.e[2] && o.e[3] == m.e[3]) {
+        o.c += m.c;
+        found = true;
+        break;
+      }
+    }
+    if (!found) out.push_back(m);
+  }
+  p.t.swap(out);
+}
+Poly operator+(const Poly& a, const Poly& b) {
+  Poly p = a;
+  p.t.insert(p.t.end(), b.t.begin(), b.t.end());
+  pmerge(p);
+  return p;
+}
+Poly operator*(double s, const Poly& a) {
+  Poly p = a;
+  for (Mono& m : p.t) m.c *= s;
+  return p;
+}
+Poly operator*(const Poly& a, const Poly& b) {
+  Poly p;
+  for (const Mono& x : a.t)
+    for (const Mono& y : b.t) {
+      Mono m;
+      for (int i = 0; i < 4; ++i) m.e[i] = x.e[i] + y.e[i];
+      m.c = x.c * y.c;
+      p.t.push_back(m);
+    }
+  pmerge(p);
+  return p;
+}
+
+// psi = (1, u_1..u_D, 1/2 (|u|^2 + xi^2)), Section 2 (moment map)
+Poly psi(int D, int m) {
+  if (m == 0) return pconst(1.0);
+  if (m <= D) return pvar(m - 1);
+  Poly e = pvar(3, 0.5);
+  for (int i = 0; i < D; ++i) e = e + 0.5 * (pvar(i) * pvar(i));
+  return e;
+}
+// a . psi, the polynomial expansion coefficient of Eq. initialf0
+Poly expansion(int D, const double* a) {
+  Poly p = a[0] * psi(D, 0);
+  for (int m = 1; m < D + 2; ++m) p = p + a[m] * psi(D, m);
+  return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Moments of a Maxwellian (Eq. maxwellian).  <u^n> over the full line or a half line, from the
+// textbook Gaussian integrals: <1>_{u>0} = erfc(-sqrt(lam) U)/2,
+// <u>_{u>0} = U <1>_{u>0} + exp(-lam U^2)/(2 sqrt(pi lam)), and integration by parts
+// <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lam) <u^n> (valid on u>0, u<0 and the full line).
+// Internal degrees of freedom: <(xi^2)^l> = prod_{i<l} (K + 2 i)/(2 lam).
+// ---------------------------------------------------------------------------------------------
+void umom(double U, double lam, int region, int nmax, double* out) {
+  const double pi = 3.14159265358979323846;
+  if (region == ORC_FULL) {
+    out[0] = 1.0;
+    out[1] = U;
+  } else {
+    double s = (region == ORC_POS) ? 1.0 : -1.0;
+    out[0] = 0.5 * std::erfc(-s * std::sqrt(lam) * U);
+    out[1] = U * out[0] + s * 0.5 * std::exp(-lam * U * U) / std::sqrt(pi * lam);
+  }
+  for (int n = 0; n + 2 <= nmax; ++n) out[n + 2] = U * out[n + 1] + (n + 1) / (2.0 * lam) * out[n];
+}
+void ximom(double K, double lam, int lmax, double* out) {
+  out[0] = 1.0;
+  for (int l = 1; l <= lmax; ++l) out[l] = out[l - 1] * (K + 2.0 * (l - 1)) / (2.0 * lam);
+}
+
+struct Maxw {
+  int D;
+  double K, rho, U[3], lam;
+  double mu[3][MAXP + 1];   // normal velocity: full, u>0, u<0
+  double mt[2][MAXP + 1];   // tangential velocities: full line
+  double mx[5];
+};
+
+Maxw make_maxw(int D, double K, const double* w) {
+  Maxw g;
+  g.D = D;
+  g.K = K;
+  g.rho = w[0];
+  double q = 0.0;
+  for (int i = 0; i < 3; ++i) g.U[i] = 0.0;
+  for (int i = 0; i < D; ++i) {
+    g.U[i] = w[1 + i] / w[0];
+    q += g.U[i] * g.U[i];
+  }
+  // rho E = 1/2 rho |U|^2 + (K + D) rho / (4 lambda)
+  g.lam = (K + D) * g.rho / (4.0 * (w[D + 1] - 0.5 * g.rho * q));
+  for (int r = 0; r < 3; ++r) umom(g.U[0], g.lam, r, MAXP, g.mu[r]);
+  for (int k = 0; k < 2; ++k) umom(g.U[1 + k], g.lam, ORC_FULL, MAXP, g.mt[k]);
+  ximom(K, g.lam, 4, g.mx);
+  return g;
+}
+
+double moment(const Maxw& g, int region, const Poly& p) {
+  double s = 0.0;
+  for (const Mono& m : p.t) {
+    if (m.e[0] > MAXP || m.e[1] > MAXP || m.e[2] > MAXP || m.e[3] > 4) return NAN;
+    if (g.D < 2 && m.e[1] > 0) return NAN;
+    if (g.D < 3 && m.e[2] > 0) return NAN;
+    double v = m.c * g.mu[region][m.e[0]] * g.mx[m.e[3]];
+    if (g.D >= 2) v *= g.mt[0][m.e[1]];
+    if (g.D >= 3) v *= g.mt[1][m.e[2]];
+    s += v;
+  }
+  return s;
+}
+
+// Dense LU with partial pivoting; solves M x = b in place (n <= 5).
+bool lu_solve(int n, double M[5][5], double* b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(M[c][k], M[piv][k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = M[r][c] / M[c][c];
+      for (int k = c; k < n; ++k) M[r][k] -= f * M[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < n; ++k) s -= M[r][k] * b[k];
+    b[r] = s / M[r][r];
+  }
+  return true;
+}
+
+// Coefficients a of a . psi with <(a . psi) psi_m>_g = rhs_m (moments normalised by rho).
+void slope(const Maxw& g, const double* rhs, double* a) {
+  int nv = g.D + 2;
+  double M[5][5];
+  for (int m = 0; m < nv; ++m)
+    for (int n = 0; n < nv; ++n) M[m][n] = moment(g, ORC_FULL, psi(g.D, m) * psi(g.D, n));
+  for (int m = 0; m < nv; ++m) a[m] = rhs[m];
+  if (!lu_solve(nv, M, a))
+    for (int m = 0; m < nv; ++m) a[m] = NAN;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Time integrals over [0, dt] of the kernels of Eq. resultingf (from Kogan's Eq. integralbgk):
+//   T0 = int (1 - e^{-t/tau})              T3 = int e^{-t/tau}
+//   T1 = int ((tau + t) e^{-t/tau} - tau)  T4 = -int (tau + t) e^{-t/tau}
+//   T2 = int (t - tau + tau e^{-t/tau})    T5 = -tau int e^{-t/tau}
+// and Dn = dt^2/2 - T2.  For x = dt/tau < 1 each integral is summed from the exponential series
+// term by term; otherwise the closed forms are used.
+// ---------------------------------------------------------------------------------------------
+void time_coeffs(double dt, double tau, double* T) {
+  double x = dt / tau;
+  if (tau > 0.0 && x < 1.0) {
+    double t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, dn = 0;
+    double xp = x, fact = 1.0;  // xp = x^(m+1), fact = (m+1)!
+    for (int m = 0; m < 40; ++m) {
+      double term = xp / fact;  // x^(m+1)/(m+1)!
+      double sg = (m % 2 == 0) ? 1.0 : -1.0;  // (-1)^m
+      t3 += sg * term;
+      if (m >= 1) t0 += -sg * term;  // (-1)^(m+1)
+      if (m >= 1) dn += -sg * term;
+      if (m >= 2) t1 += sg * (1.0 - m) * term;
+      if (m >= 2) t2 += sg * term;
+      t4 += -sg * (1.0 - m) * term;
+      xp *= x;
+      fact *= (m + 2);
+    }
+    T[0] = tau * t0;
+    T[1] = tau * tau * t1;
+    T[2] = tau * tau * t2;
+    T[3] = tau * t3;
+    T[4] = tau * tau * t4;
+    T[5] = -tau * T[3];
+    T[6] = tau * tau * dn;
+  } else {
+    double E = std::exp(-x), q = 1.0 - E;
+    T[0] = dt - tau * q;
+    T[1] = -tau * dt * (1.0 + E) + 2.0 * tau * tau * q;
+    T[2] = 0.5 * dt * dt - tau * dt + tau * tau * q;
+    T[3] = tau * q;
+    T[4] = tau * dt * E - 2.0 * tau * tau * q;
+    T[5] = -tau * tau * q;
+    T[6] = tau * dt - tau * tau * q;
+  }
+}
+
+double pressure(int D, double gamma, const double* w) {
+  double q = 0.0;
+  for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
+  return (gamma - 1.0) * (w[D + 1] - 0.5 * q / w[0]);
+}
+
+// Everything one face needs, Sections 2 and 4.
+struct FaceWork {
+  int D, nv;
+  Maxw gl, gr, g0;
+  double w0[5], al[5], ar[5], bl[2][5], br[2][5], Al[5], Ar[5], abl[5], abr[5], bb[2][5], Ab[5];
+  double tau, T[7];
+  Poly Ql, Qr, Q0l, Q0r, Qt0, PAl, PAr, PAb;
+};
+
+bool face_setup(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
+                const orc_face& f, FaceWork& W) {
+  const int nv = D + 2;
+  const double K = 2.0 / (gamma - 1.0) - D;
+  W.D = D;
+  W.nv = nv;
+  W.gl = make_maxw(D, K, f.wl);
+  W.gr = make_maxw(D, K, f.wr);
+  // Eq. intermediatestate: w0 = int_{u>0} psi g_l + int_{u<0} psi g_r
+  for (int m = 0; m < nv; ++m)
+    W.w0[m] = W.gl.rho * moment(W.gl, ORC_POS, psi(D, m)) + W.gr.rho * moment(W.gr, ORC_NEG, psi(D, m));
+  W.g0 = make_maxw(D, K, W.w0);
+  const double rl = W.gl.rho, rr = W.gr.rho, r0 = W.g0.rho;
+
+  // Eq. initialf0: spatial coefficients from the conservative gradients, <a psi> = (1/rho) dW/dn
+  double rhs[5];
+  for (int m = 0; m < nv; ++m) rhs[m] = f.sl[m] / rl;
+  slope(W.gl, rhs, W.al);
+  for (int m = 0; m < nv; ++m) rhs[m] = f.sr[m] / rr;
+  slope(W.gr, rhs, W.ar);
+  for (int k = 0; k < 2; ++k)
+    for (int m = 0; m < 5; ++m) W.bl[k][m] = W.br[k][m] = W.bb[k][m] = 0.0;
+  if (multid) {
+    for (int k = 0; k < D - 1; ++k) {
+      for (int m = 0; m < nv; ++m) rhs[m] = f.tl[k][m] / rl;
+      slope(W.gl, rhs, W.bl[k]);
+      for (int m = 0; m < nv; ++m) rhs[m] = f.tr[k][m] / rr;
+      slope(W.gr, rhs, W.br[k]);
+    }
+  }
+  // Polynomials a u + sum_k b_k v_k of the initial state (f0 = g (1 + a x + b y - tau(a u + b v + A)))
+  W.Ql = expansion(D, W.al) * pvar(0);
+  W.Qr = expansion(D, W.ar) * pvar(0);
+  for (int k = 0; k < D - 1; ++k) {
+    W.Ql = W.Ql + expansion(D, W.bl[k]) * pvar(1 + k);
+    W.Qr = W.Qr + expansion(D, W.br[k]) * pvar(1 + k);
+  }
+  // A from the compatibility condition at t = 0: <(a u + b v + A) psi> = 0
+  for (int m = 0; m < nv; ++m) rhs[m] = -moment(W.gl, ORC_FULL, W.Ql * psi(D, m));
+  slope(W.gl, rhs, W.Al);
+  for (int m = 0; m < nv; ++m) rhs[m] = -moment(W.gr, ORC_FULL, W.Qr * psi(D, m));
+  slope(W.gr, rhs, W.Ar);
+  W.PAl = expansion(D, W.Al);
+  W.PAr = expansion(D, W.Ar);
+
+  // Eq. eqlgform: equilibrium slopes from the linear interpolation through W_j, w0, W_{j+1}
+  for (int m = 0; m < nv; ++m) rhs[m] = (W.w0[m] - f.cl[m]) / (f.dxl * r0);
+  slope(W.g0, rhs, W.abl);
+  for (int m = 0; m < nv; ++m) rhs[m] = (f.cr[m] - W.w0[m]) / (f.dxr * r0);
+  slope(W.g0, rhs, W.abr);
+  if (multid) {
+    for (int k = 0; k < D - 1; ++k) {
+      for (int m = 0; m < nv; ++m) rhs[m] = 0.5 * (f.tl[k][m] + f.tr[k][m]) / r0;
+      slope(W.g0, rhs, W.bb[k]);
+    }
+  }
+  W.Q0l = expansion(D, W.abl) * pvar(0);
+  W.Q0r = expansion(D, W.abr) * pvar(0);
+  W.Qt0 = pconst(0.0);
+  for (int k = 0; k < D - 1; ++k) W.Qt0 = W.Qt0 + expansion(D, W.bb[k]) * pvar(1 + k);
+
+  // Eqs. relaxation time and taua: tau = mu/p + tau_t + C_a |p_r - p_l| / |p_r + p_l| dt
+  double p0 = r0 / (2.0 * W.g0.lam);
+  double pl = rl / (2.0 * W.gl.lam), pr = rr / (2.0 * W.gr.lam);
+  W.tau = mu / p0 + f.tau_t + C_a * std::fabs(pr - pl) / std::fabs(pr + pl) * dt;
+  time_coeffs(dt, W.tau, W.T);
+
+  // Abar from the compatibility condition integrated over [0, dt] at the face:
+  //   Dn <Abar psi>_0 = T1 <(abar u + bbar v) psi>_0 + T4 (rho_l <(a_l u + b_l v) psi>_{l,u>0}
+  //                     + rho_r <...>_{r,u<0}) / rho0 + T5 (rho_l <A_l psi>_{l,u>0} + rho_r <...>) / rho0
+  double X1[5], X4[5], X5[5];
+  for (int m = 0; m < nv; ++m) {
+    Poly p = psi(D, m);
+    X1[m] = moment(W.g0, ORC_POS, W.Q0l * p) + moment(W.g0, ORC_NEG, W.Q0r * p) + moment(W.g0, ORC_FULL, W.Qt0 * p);
+    X4[m] = (rl * moment(W.gl, ORC_POS, W.Ql * p) + rr * moment(W.gr, ORC_NEG, W.Qr * p)) / r0;
+    X5[m] = (rl * moment(W.gl, ORC_POS, W.PAl * p) + rr * moment(W.gr, ORC_NEG, W.PAr * p)) / r0;
+  }
+  for (int m = 0; m < nv; ++m) {
+    if (abar_mode == ORC_ABAR_T0 || W.tau == 0.0)
+      rhs[m] = -X1[m];  // t = 0 compatibility, also the tau -> 0 limit of the integrated one
+    else
+      rhs[m] = (W.T[1] * X1[m] + W.T[4] * X4[m] + W.T[5] * X5[m]) / W.T[6];
+  }
+  slope(W.g0, rhs, W.Ab);
+  W.PAb = expansion(D, W.Ab);
+  return true;
+}
+
+void fill_diag(const FaceWork& W, orc_face_diag* dg) {
+  if (!dg) return;
+  std::memset(dg, 0, sizeof(*dg));
+  for (int m = 0; m < W.nv; ++m) {
+    dg->w0[m] = W.w0[m];
+    dg->al[m] = W.al[m];
+    dg->ar[m] = W.ar[m];
+    dg->Al[m] = W.Al[m];
+    dg->Ar[m] = W.Ar[m];
+    dg->abl[m] = W.abl[m];
+    dg->abr[m] = W.abr[m];
+    dg->Ab[m] = W.Ab[m];
+    for (int k = 0; k < 2; ++k) {
+      dg->bl[k][m] = W.bl[k][m];
+      dg->br[k][m] = W.br[k][m];
+      dg->bb[k][m] = W.bb[k][m];
+    }
+  }
+  dg->tau = W.tau;
+  for (int i = 0; i < 6; ++i) dg->T[i] = W.T[i];
+}
+
+// Eq. fluxesf: F = int_0^dt int u psi f dXi dt, with f from Eq. resultingf.
+void face_flux(const FaceWork& W, double* F) {
+  const int D = W.D;
+  const Poly u = pvar(0);
+  const double r0 = W.g0.rho, rl = W.gl.rho, rr = W.gr.rho;
+  for (int m = 0; m < W.nv; ++m) {
+    Poly up = u * psi(D, m);
+    double eq = W.T[0] * moment(W.g0, ORC_FULL, up) +
+                W.T[1] * (moment(W.g0, ORC_POS, W.Q0l * up) + moment(W.g0, ORC_NEG, W.Q0r * up) +
+                          moment(W.g0, ORC_FULL, W.Qt0 * up)) +
+                W.T[2] * moment(W.g0, ORC_FULL, W.PAb * up);
+    double left = W.T[3] * moment(W.gl, ORC_POS, up) + W.T[4] * moment(W.gl, ORC_POS, W.Ql * up) +
+                  W.T[5] * moment(W.gl, ORC_POS, W.PAl * up);
+    double right = W.T[3] * moment(W.gr, ORC_NEG, up) + W.T[4] * moment(W.gr, ORC_NEG, W.Qr * up) +
+                   W.T[5] * moment(W.gr, ORC_NEG, W.PAr * up);
+    F[m] = r0 * eq + rl * left + rr * right;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Grid machinery: SoA state [nv][nz][ny][nx]; a padded copy with two ghost layers per active axis.
+// ---------------------------------------------------------------------------------------------
+struct Grid {
+  int D, nv, n[3], N[3], g[3];
+  long ncell, npad;
+  std::vector<double> w[3];  // widths with ghosts, index i + 2
+  long idx(int i, int j, int k) const {
+    return ((long)(k + g[2]) * N[1] + (j + g[1])) * N[0] + (i + g[0]);
+  }
+};
+
+Grid make_grid(const orc_problem* P) {
+  Grid G;
+  G.D = P->dim;
+  G.nv = P->dim + 2;
+  G.ncell = 1;
+  G.npad = 1;
+  for (int d = 0; d < 3; ++d) {
+    bool act = d < P->dim;
+    G.n[d] = act ? P->n[d] : 1;
+    G.g[d] = act ? 2 : 0;
+    G.N[d] = G.n[d] + 2 * G.g[d];
+    G.ncell *= G.n[d];
+    G.npad *= G.N[d];
+    G.w[d].assign(G.n[d] + 4, 1.0);
+    if (act) {
+      int n = G.n[d];
+      for (int i = 0; i < n; ++i) G.w[d][i + 2] = P->dx[d][i];
+      bool per = P->bc[d][0] == ORC_BC_PERIODIC;
+      for (int gi = 1; gi <= 2; ++gi) {
+        G.w[d][2 - gi] = per ? P->dx[d][n - gi] : P->dx[d][gi - 1];
+        G.w[d][n + 1 + gi] = per ? P->dx[d][gi - 1] : P->dx[d][n - gi];
+      }
+    }
+  }
+  return G;
+}
+double width(const Grid& G, int d, int i) { return G.w[d][i + 2]; }
+
+void cons_from_prim(int D, double gamma, const double* pr, double* w) {
+  double q = 0.0;
+  w[0] = pr[0];
+  for (int i = 0; i < D; ++i) {
+    w[1 + i] = pr[0] * pr[1 + i];
+    q += pr[1 + i] * pr[1 + i];
+  }
+  w[D + 1] = pr[D + 1] / (gamma - 1.0) + 0.5 * pr[0] * q;
+}
+void prim_from_cons(int D, double gamma, const double* w, double* pr) {
+  pr[0] = w[0];
+  for (int i = 0; i < D; ++i) pr[1 + i] = w[1 + i] / w[0];
+  pr[D + 1] = pressure(D, gamma, w);
+}
+
+// Ghost cells.  Axes are filled from the last to the first; when axis a is filled, lower axes
+// range over interior cells and higher axes over the padded range, so corners take the lower
+// axis' rule.  Wall: no-slip mirror with p_g = p_i and T_g = T_w^2 / T_i (T = p/rho), so that the
+// geometric mean of the two temperatures is the wall temperature.
+void fill_ghosts(const orc_problem* P, const Grid& G, std::vector<double>& Wp) {
+  const int D = G.D, nv = G.nv;
+  for (int a = D - 1; a >= 0; --a) {
+    int lo[3], hi[3];
+    for (int b = 0; b < 3; ++b) {
+      if (b < a) {
+        lo[b] = 0;
+        hi[b] = G.n[b];
+      } else {
+        lo[b] = -G.g[b];
+        hi[b] = G.n[b] + G.g[b];
+      }
+    }
+    const int n = G.n[a];
+    for (int side = 0; side < 2; ++side) {
+      int bc = P->bc[a][side];
+      for (int gi = 1; gi <= 2; ++gi) {
+        int gidx = side == 0 ? -gi : n - 1 + gi;
+        int c[3];
+        for (c[2] = lo[2]; c[2] < hi[2]; ++c[2])
+          for (c[1] = lo[1]; c[1] < hi[1]; ++c[1])
+            for (c[0] = lo[0]; c[0] < hi[0]; ++c[0]) {
+              if (c[a] != lo[a]) continue;  // iterate the transverse set once
+              int dst[3] = {c[0], c[1], c[2]};
+              dst[a] = gidx;
+              int src[3] = {c[0], c[1], c[2]};
+              double wv[5];
+              if (bc == ORC_BC_PERIODIC) {
+                src[a] = side == 0 ? n - gi : gi - 1;
+                for (int v = 0; v < nv; ++v) wv[v] = Wp[v * G.npad + G.idx(src[0], src[1], src[2])];
+              } else if (bc == ORC_BC_TRANSMISSIVE || bc == ORC_BC_OUTFLOW) {
+                src[a] = side == 0 ? 0 : n - 1;
+                for (int v = 0; v < nv; ++v) wv[v] = Wp[v * G.npad + G.idx(src[0], src[1], src[2])];
+              } else if (bc == ORC_BC_WALL) {
+                src[a] = side == 0 ? gi - 1 : n - gi;
+                double wi[5], pri[5], prg[5];
+                for (int v = 0; v < nv; ++v) wi[v] = Wp[v * G.npad + G.idx(src[0], src[1], src[2])];
+                prim_from_cons(D, P->gamma, wi, pri);
+                double Ti = pri[D + 1] / pri[0];
+                double Tg = P->T_wall * P->T_wall / Ti;
+                prg[D + 1] = pri[D + 1];
+                prg[0] = pri[D + 1] / Tg;
+                for (int i = 0; i < D; ++i) prg[1 + i] = -pri[1 + i];
+                cons_from_prim(D, P->gamma, prg, wv);
+              } else {  // Dirichlet: primitive state per boundary cell, transverse index clamped
+                long off = 0, stride = 1;
+                for (int b = 0; b < D; ++b) {
+                  if (b == a) continue;
+                  int cb = std::min(std::max(c[b], 0), G.n[b] - 1);
+                  off += cb * stride;
+                  stride *= G.n[b];
+                }
+                cons_from_prim(D, P->gamma, P->bc_prim[a][side] + off * nv, wv);
+              }
+              for (int v = 0; v < nv; ++v) Wp[v * G.npad + G.idx(dst[0], dst[1], dst[2])] = wv[v];
+            }
+      }
+    }
+  }
+}
+
+void pad_state(const Grid& G, const double* W, std::vector<double>& Wp) {
+  Wp.assign((size_t)G.nv * G.npad, 0.0);
+  for (int v = 0; v < G.nv; ++v)
+    for (int k = 0; k < G.n[2]; ++k)
+      for (int j = 0; j < G.n[1]; ++j)
+        for (int i = 0; i < G.n[0]; ++i)
+          Wp[v * G.npad + G.idx(i, j, k)] = W[v * G.ncell + ((long)k * G.n[1] + j) * G.n[0] + i];
+}
+
+// Turbulence fields with ghosts: periodic axes wrap, other axes repeat the nearest interior cell.
+std::vector<double> pad_scalar(const orc_problem* P, const Grid& G, const double* f) {
+  std::vector<double> out(G.npad, 0.0);
+  if (!f) return out;
+  for (int k = -G.g[2]; k < G.n[2] + G.g[2]; ++k)
+    for (int j = -G.g[1]; j < G.n[1] + G.g[1]; ++j)
+      for (int i = -G.g[0]; i < G.n[0] + G.g[0]; ++i) {
+        int c[3] = {i, j, k};
+        for (int d = 0; d < G.D; ++d) {
+          int n = G.n[d];
+          if (P->bc[d][0] == ORC_BC_PERIODIC)
+            c[d] = (c[d] + n) % n;
+          else
+            c[d] = std::min(std::max(c[d], 0), n - 1);
+        }
+        out[G.idx(i, j, k)] = f[((long)c[2] * G.n[1] + c[1]) * G.n[0] + c[0]];
+      }
+  return out;
+}
+
+void get_cell(const Grid& G, const std::vector<double>& Wp, int i, int j, int k, double* w) {
+  long id = G.idx(i, j, k);
+  for (int v = 0; v < G.nv; ++v) w[v] = Wp[v * G.npad + id];
+}
+
+// Velocity gradient by central differences; grad[a][b] = d U_b / d x_a
+void vel_grad(const Grid& G, const std::vector<double>& Wp, int i, int j, int k, double grad[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) grad[a][b] = 0.0;
+  int c[3] = {i, j, k};
+  for (int a = 0; a < G.D; ++a) {
+    int cm[3] = {i, j, k}, cp[3] = {i, j, k};
+    cm[a] -= 1;
+    cp[a] += 1;
+    double wm[5], wp[5];
+    get_cell(G, Wp, cm[0], cm[1], cm[2], wm);
+    get_cell(G, Wp, cp[0], cp[1], cp[2], wp);
+    double dist = 0.5 * width(G, a, c[a] - 1) + width(G, a, c[a]) + 0.5 * width(G, a, c[a] + 1);
+    for (int b = 0; b < G.D; ++b) grad[a][b] = (wp[1 + b] / wp[0] - wm[1 + b] / wm[0]) / dist;
+  }
+}
+
+double strain_rate(const Grid& G, const std::vector<double>& Wp, int i, int j, int k) {
+  double g[3][3];
+  vel_grad(G, Wp, i, j, k, g);
+  double s2 = 0.0;
+  for (int a = 0; a < G.D; ++a)
+    for (int b = 0; b < G.D; ++b) {
+      double sab = 0.5 * (g[a][b] + g[b][a]);
+      s2 += sab * sab;
+    }
+  return std::sqrt(2.0 * s2);
+}
+
+// Eqs. tauttrivial, tautchen and tautchenadjusted with T = p/rho (the turbulent part only).
+double tau_turb_cell(const orc_problem* P, const Grid& G, const std::vector<double>& Wp,
+                     const std::vector<double>& f1, const std::vector<double>& f2, int i, int j, int k) {
+  if (P->turb_model == ORC_TURB_NONE) return 0.0;
+  double w[5];
+  get_cell(G, Wp, i, j, k, w);
+  double rho = w[0], p = pressure(G.D, P->gamma, w);
+  long id = G.idx(i, j, k);
+  if (P->turb_model == ORC_TURB_MUT) return f1[id] / p;
+  double S = strain_rate(G, Wp, i, j, k);
+  double kk = f1[id], e2 = f2[id];
+  if (!(kk > 0.0) || !(e2 > 0.0)) return 0.0;
+  double nu_t, eta;
+  if (P->turb_model == ORC_TURB_KEPS) {
+    nu_t = P->C_mu * kk * kk / e2;
+    eta = S * kk / e2;
+  } else {
+    nu_t = kk / e2;
+    eta = S / (P->beta_star * e2);
+  }
+  return rho * nu_t / (p * std::sqrt(1.0 + eta * eta));
+}
+
+double limiter(int lim, double a, double b) {
+  if (lim == ORC_LIM_MINMOD) {
+    double sa = (a > 0) - (a < 0), sb = (b > 0) - (b < 0);
+    return 0.5 * (sa + sb) * std::min(std::fabs(a), std::fabs(b));
+  }
+  // van Leer: (a b + |a b|) / (a + b), zero when a b <= 0
+  return (a * b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+void perm_for(int D, int d, int* perm) {
+  if (D == 1) {
+    perm[0] = 0;
+  } else if (D == 2) {
+    perm[0] = d;
+    perm[1] = 1 - d;
+  } else {
+    perm[0] = d;
+    perm[1] = d == 0 ? 1 : 0;
+    perm[2] = d == 2 ? 1 : 2;
+  }
+}
+void rotate(int D, const int* perm, const double* w, double* r) {
+  r[0] = w[0];
+  for (int k = 0; k < D; ++k) r[1 + k] = w[1 + perm[k]];
+  r[D + 1] = w[D + 1];
+}
+
+struct StepCtx {
+  const orc_problem* P;
+  Grid G;
+  std::vector<double> Wp, f1p, f2p, taut;  // taut on the padded index
+};
+
+void prepare(const orc_problem* P, const double* W, const double* f1, const double* f2, StepCtx& C) {
+  C.P = P;
+  C.G = make_grid(P);
+  pad_state(C.G, W, C.Wp);
+  fill_ghosts(P, C.G, C.Wp);
+  C.f1p = pad_scalar(P, C.G, f1);
+  C.f2p = pad_scalar(P, C.G, f2);
+  C.taut.assign(C.G.npad, 0.0);
+  const Grid& G = C.G;
+  for (int k = -(G.g[2] / 2); k < G.n[2] + G.g[2] / 2; ++k)
+    for (int j = -(G.g[1] / 2); j < G.n[1] + G.g[1] / 2; ++j)
+      for (int i = -(G.g[0] / 2); i < G.n[0] + G.g[0] / 2; ++i)
+        C.taut[G.idx(i, j, k)] = tau_turb_cell(P, G, C.Wp, C.f1p, C.f2p, i, j, k);
+}
+
+// Face record for the face between cell c (index j along axis d) and its + neighbour.
+void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
+  const Grid& G = C.G;
+  const orc_problem* P = C.P;
+  const int D = G.D, nv = G.nv;
+  int perm[3];
+  perm_for(D, d, perm);
+  double S[4][5];  // cells j-1, j, j+1, j+2 along d (rotated)
+  double wd[4];
+  for (int s = 0; s < 4; ++s) {
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[d] += s - 1;
+    double w[5];
+    get_cell(G, C.Wp, cc[0], cc[1], cc[2], w);
+    rotate(D, perm, w, S[s]);
+    wd[s] = width(G, d, cc[d]);
+  }
+  std::memset(&f, 0, sizeof(f));
+  for (int v = 0; v < nv; ++v) {
+    double dm = (S[1][v] - S[0][v]) / (0.5 * (wd[0] + wd[1]));
+    double dc = (S[2][v] - S[1][v]) / (0.5 * (wd[1] + wd[2]));
+    double dp = (S[3][v] - S[2][v]) / (0.5 * (wd[2] + wd[3]));
+    f.sl[v] = limiter(P->limiter, dm, dc);
+    f.sr[v] = limiter(P->limiter, dc, dp);
+    f.wl[v] = S[1][v] + 0.5 * wd[1] * f.sl[v];
+    f.wr[v] = S[2][v] - 0.5 * wd[2] * f.sr[v];
+    f.cl[v] = S[1][v];
+    f.cr[v] = S[2][v];
+  }
+  // first order on a side whose reconstructed density or pressure is not positive
+  if (!(f.wl[0] > 0.0) || !(pressure(D, P->gamma, f.wl) > 0.0))
+    for (int v = 0; v < nv; ++v) {
+      f.wl[v] = S[1][v];
+      f.sl[v] = 0.0;
+    }
+  if (!(f.wr[0] > 0.0) || !(pressure(D, P->gamma, f.wr) > 0.0))
+    for (int v = 0; v < nv; ++v) {
+      f.wr[v] = S[2][v];
+      f.sr[v] = 0.0;
+    }
+  if (P->multid) {
+    for (int t = 0; t < D - 1; ++t) {
+      int ax = perm[1 + t];
+      for (int side = 0; side < 2; ++side) {
+        int cc[3] = {c[0], c[1], c[2]};
+        cc[d] += side;
+        double wm[5], w0[5], wp[5], rm[5], r0[5], rp[5];
+        int cm[3] = {cc[0], cc[1], cc[2]}, cp[3] = {cc[0], cc[1], cc[2]};
+        cm[ax] -= 1;
+        cp[ax] += 1;
+        get_cell(G, C.Wp, cm[0], cm[1], cm[2], wm);
+        get_cell(G, C.Wp, cc[0], cc[1], cc[2], w0);
+        get_cell(G, C.Wp, cp[0], cp[1], cp[2], wp);
+        rotate(D, perm, wm, rm);
+        rotate(D, perm, w0, r0);
+        rotate(D, perm, wp, rp);
+        double hm = 0.5 * (width(G, ax, cc[ax] - 1) + width(G, ax, cc[ax]));
+        double hp = 0.5 * (width(G, ax, cc[ax]) + width(G, ax, cc[ax] + 1));
+        for (int v = 0; v < nv; ++v) {
+          double s = limiter(P->limiter, (r0[v] - rm[v]) / hm, (rp[v] - r0[v]) / hp);
+          if (side == 0)
+            f.tl[t][v] = s;
+          else
+            f.tr[t][v] = s;
+        }
+      }
+    }
+  }
+  f.dxl = 0.5 * wd[1];
+  f.dxr = 0.5 * wd[2];
+  int cr[3] = {c[0], c[1], c[2]};
+  cr[d] += 1;
+  f.tau_t = 0.5 * (C.taut[G.idx(c[0], c[1], c[2])] + C.taut[G.idx(cr[0], cr[1], cr[2])]);
+}
+
+}  // namespace
+
+// =============================================================================================
+// C API
+// =============================================================================================
+extern "C" {
+
+int orc_umoments(double U, double lam, int region, int nmax, double* out) {
+  if (nmax < 1 || nmax > 40) return 1;
+  umom(U, lam, region, nmax, out);
+  return 0;
+}
+
+int orc_ximoments(double K, double lam, int lmax, double* out) {
+  ximom(K, lam, lmax, out);
+  return 0;
+}
+
+int orc_time_coeffs(double dt, double tau, double* T) {
+  time_coeffs(dt, tau, T);
+  return 0;
+}
+
+int orc_slope(int D, double K, const double* w, const double* rhs, double* a_out) {
+  Maxw g = make_maxw(D, K, w);
+  slope(g, rhs, a_out);
+  return 0;
+}
+
+int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
+                  const orc_face* f, double* F, orc_face_diag* diag) {
+  FaceWork W;
+  face_setup(D, gamma, mu, C_a, dt, multid, abar_mode, *f, W);
+  face_flux(W, F);
+  fill_diag(W, diag);
+  return 0;
+}
+
+// Compact form, Eq. resultingf4 (test only): F = dt int u psi fhat with
+//   fhat = f_c + 1/2 Abar dt g0 + alpha (f_u - f_c) + (alpha - beta) (f~_u - f~_c),
+// alpha = eps (1 - e^{-1/eps}), eps = tau/dt, beta = e^{-1/eps} (or the printed eps e^{-1/eps}).
+// Reading: f~_c = -tau (abar u + bbar v) g0 and f~_u = -tau (a u + b v) g_{l,r} carry only the
+// spatial-expansion terms, and the time factor of Eq. resultingf2 is (t/tau) e^{-t/tau}; with the
+// leading Maxwellians kept in f~ the form no longer equals the time integral of Eq. resultingf.
+int orc_face_flux_compact(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
+                          int printed_beta, const orc_face* f, double* F) {
+  FaceWork W;
+  face_setup(D, gamma, mu, C_a, dt, multid, abar_mode, *f, W);
+  const Poly u = pvar(0);
+  const double r0 = W.g0.rho, rl = W.gl.rho, rr = W.gr.rho, tau = W.tau;
+  double eps = tau / dt;
+  double ex = std::exp(-1.0 / eps);
+  double alpha = eps * (1.0 - ex);
+  double beta = printed_beta ? eps * ex : ex;
+  for (int m = 0; m < W.nv; ++m) {
+    Poly up = u * psi(D, m);
+    double Cg = r0 * moment(W.g0, ORC_FULL, up);
+    double Ca = r0 * (moment(W.g0, ORC_POS, W.Q0l * up) + moment(W.g0, ORC_NEG, W.Q0r * up) +
+                      moment(W.g0, ORC_FULL, W.Qt0 * up));
+    double CA = r0 * moment(W.g0, ORC_FULL, W.PAb * up);
+    double Ug = rl * moment(W.gl, ORC_POS, up) + rr * moment(W.gr, ORC_NEG, up);
+    double Ua = rl * moment(W.gl, ORC_POS, W.Ql * up) + rr * moment(W.gr, ORC_NEG, W.Qr * up);
+    double UA = rl * moment(W.gl, ORC_POS, W.PAl * up) + rr * moment(W.gr, ORC_NEG, W.PAr * up);
+    double fc = Cg - tau * (Ca + CA), fu = Ug - tau * (Ua + UA);
+    double fct = -tau * Ca, fut = -tau * Ua;
+    F[m] = dt * (fc + 0.5 * dt * CA + alpha * (fu - fc) + (alpha - beta) * (fut - fct));
+  }
+  return 0;
+}
+
+int orc_euler_flux(int D, double gamma, const double* w, double* F) {
+  double p = pressure(D, gamma, w), un = w[1] / w[0];
+  F[0] = w[1];
+  for (int i = 0; i < D; ++i) F[1 + i] = w[1 + i] * un + (i == 0 ? p : 0.0);
+  F[D + 1] = un * (w[D + 1] + p);
+  return 0;
+}
+
+int orc_prim_to_cons(const orc_problem* P, const double* prim, double* W, long ncell) {
+  int D = P->dim, nv = D + 2;
+  for (long c = 0; c < ncell; ++c) {
+    double pr[5], w[5];
+    for (int v = 0; v < nv; ++v) pr[v] = prim[v * ncell + c];
+    cons_from_prim(D, P->gamma, pr, w);
+    for (int v = 0; v < nv; ++v) W[v * ncell + c] = w[v];
+  }
+  return 0;
+}
+
+int orc_cons_to_prim(const orc_problem* P, const double* W, double* prim, long ncell) {
+  int D = P->dim, nv = D + 2;
+  for (long c = 0; c < ncell; ++c) {
+    double pr[5], w[5];
+    for (int v = 0; v < nv; ++v) w[v] = W[v * ncell + c];
+    prim_from_cons(D, P->gamma, w, pr);
+    for (int v = 0; v < nv; ++v) prim[v * ncell + c] = pr[v];
+  }
+  return 0;
+}
+
+// CFL time step: dt = cfl / max_cells sum_d (|U_d| + c) / dx_d, c = sqrt(gamma p / rho)
+int orc_compute_dt(const orc_problem* P, const double* W, double cfl, double* dt) {
+  Grid G = make_grid(P);
+  double rmax = 0.0;
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i) {
+        long c = ((long)k * G.n[1] + j) * G.n[0] + i;
+        double w[5];
+        for (int v = 0; v < G.nv; ++v) w[v] = W[v * G.ncell + c];
+        double p = pressure(G.D, P->gamma, w);
+        double cs = std::sqrt(P->gamma * p / w[0]);
+        int ci[3] = {i, j, k};
+        double r = 0.0;
+        for (int d = 0; d < G.D; ++d) r += (std::fabs(w[1 + d] / w[0]) + cs) / width(G, d, ci[d]);
+        rmax = std::max(rmax, r);
+      }
+  *dt = cfl / rmax;
+  return 0;
+}
+
+int orc_tau_turb(const orc_problem* P, const double* W, const double* f1, const double* f2, double* tau_t) {
+  StepCtx C;
+  prepare(P, W, f1, f2, C);
+  const Grid& G = C.G;
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i) tau_t[((long)k * G.n[1] + j) * G.n[0] + i] = C.taut[G.idx(i, j, k)];
+  return 0;
+}
+
+int orc_rarefaction(const orc_problem* P, const double* W, const double* f1, const double* f2, double* eps) {
+  StepCtx C;
+  prepare(P, W, f1, f2, C);
+  const Grid& G = C.G;
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i) {
+        double g[3][3], w[5];
+        vel_grad(G, C.Wp, i, j, k, g);
+        get_cell(G, C.Wp, i, j, k, w);
+        double div = 0.0;
+        for (int a = 0; a < G.D; ++a) div += g[a][a];
+        double tau = P->mu / pressure(G.D, P->gamma, w) + C.taut[G.idx(i, j, k)];
+        eps[((long)k * G.n[1] + j) * G.n[0] + i] = tau * std::fabs(div);
+      }
+  return 0;
+}
+
+// One unsplit single-stage step W <- W - sum_d (F_{d,j+1/2} - F_{d,j-1/2}) / dx_d with the
+// time-integrated fluxes of Eq. fluxesf.  Returns 4 if a cell ends with rho <= 0 or p <= 0.
+int orc_step(const orc_problem* P, double* W, const double* f1, const double* f2, double dt,
+             double* resid, int nthreads) {
+  StepCtx C;
+  prepare(P, W, f1, f2, C);
+  const Grid& G = C.G;
+  const int D = G.D, nv = G.nv;
+  std::vector<double> Wnew(W, W + (size_t)nv * G.ncell);
+  for (int d = 0; d < D; ++d) {
+    int nf[3] = {G.n[0], G.n[1], G.n[2]};
+    nf[d] += 1;  // faces j+1/2 for j = -1 .. n-1
+    long nfaces = (long)nf[0] * nf[1] * nf[2];
+    std::vector<double> Fd((size_t)nfaces * nv);
+    int perm[3];
+    perm_for(D, d, perm);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (long fi = 0; fi < nfaces; ++fi) {
+      int c[3];
+      c[0] = (int)(fi % nf[0]);
+      c[1] = (int)((fi / nf[0]) % nf[1]);
+      c[2] = (int)(fi / ((long)nf[0] * nf[1]));
+      c[d] -= 1;  // left cell of the face
+      orc_face f;
+      build_face(C, d, c, f);
+      double Fr[5];
+      FaceWork Wk;
+      face_setup(D, P->gamma, P->mu, P->C_a, dt, P->multid, P->abar_mode, f, Wk);
+      face_flux(Wk, Fr);
+      double* Fo = &Fd[fi * nv];
+      Fo[0] = Fr[0];
+      for (int k = 0; k < D; ++k) Fo[1 + perm[k]] = Fr[1 + k];
+      Fo[D + 1] = Fr[D + 1];
+    }
+    for (int k = 0; k < G.n[2]; ++k)
+      for (int j = 0; j < G.n[1]; ++j)
+        for (int i = 0; i < G.n[0]; ++i) {
+          int c[3] = {i, j, k};
+          int cp[3] = {i, j, k};
+          cp[d] += 1;
+          long fm = ((long)c[2] * nf[1] + c[1]) * nf[0] + c[0];
+          long fp = ((long)cp[2] * nf[1] + cp[1]) * nf[0] + cp[0];
+          double h = width(G, d, c[d]);
+          long cell = ((long)k * G.n[1] + j) * G.n[0] + i;
+          for (int v = 0; v < nv; ++v) Wnew[v * G.ncell + cell] -= (Fd[fp * nv + v] - Fd[fm * nv + v]) / h;
+        }
+  }
+  int status = 0;
+  for (int v = 0; v < nv && resid; ++v) resid[v] = resid[nv + v] = resid[2 * nv + v] = 0.0;
+  for (long c = 0; c < G.ncell; ++c) {
+    double w[5];
+    for (int v = 0; v < nv; ++v) w[v] = Wnew[v * G.ncell + c];
+    if (!(w[0] > 0.0) || !(pressure(D, P->gamma, w) > 0.0)) status = 4;
+    if (resid) {
+      int i = (int)(c % G.n[0]), j = (int)((c / G.n[0]) % G.n[1]), k = (int)(c / ((long)G.n[0] * G.n[1]));
+      int ci[3] = {i, j, k};
+      double vol = 1.0;
+      for (int d = 0; d < D; ++d) vol *= width(G, d, ci[d]);
+      for (int v = 0; v < nv; ++v) {
+        double r = (w[v] - W[v * G.ncell + c]) / dt;
+        resid[v] += r * r;
+        resid[nv + v] = std::max(resid[nv + v], std::fabs(r));
+        resid[2 * nv + v] += w[v] * vol;
+      }
+    }
+  }
+  if (resid)
+    for (int v = 0; v < nv; ++v) resid[v] = std::sqrt(resid[v] / G.ncell);
+  std::memcpy(W, Wnew.data(), sizeof(double) * nv * G.ncell);
+  return status;
+}
+
+// Steps with dt_fixed (> 0) or the CFL step, the last one clamped so that t_end (> 0) is met.
+int orc_run(const orc_problem* P, double* W, const double* f1, const double* f2, double dt_fixed,
+            double cfl, int nsteps, double t_end, double* t_inout, int* steps_done, int nthreads) {
+  double t = t_inout ? *t_inout : 0.0;
+  int done = 0, status = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    double dt = dt_fixed;
+    if (!(dt > 0.0)) orc_compute_dt(P, W, cfl, &dt);
+    if (t_end > 0.0) {
+      if (t >= t_end) break;
+      dt = std::min(dt, t_end - t);
+    }
+    status = orc_step(P, W, f1, f2, dt, nullptr, nthreads);
+    t += dt;
+    ++done;
+    if (status) break;
+  }
+  if (t_inout) *t_inout = t;
+  if (steps_done) *steps_done = done;
+  return status;
+}
+
+}  // extern "C"

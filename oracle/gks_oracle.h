@@ -1,0 +1,88 @@
+/*
+ * ORACLE — TEST INFRASTRUCTURE, NOT PART OF THE LIBRARY.
+ *
+ * Plain, slow, double-precision CPU statement of the gas-kinetic BGK-Navier-Stokes scheme with a
+ * turbulent relaxation time (Righi 2013, Sections 2-4, after Xu's 2001 scheme).  Only the tests,
+ * __graft_entry__.smoke() and bench.py's cpu_baseline leg may load it.  It shares no source, header,
+ * table or helper with the CUDA library (paper_1302_2132_gb300/csrc, include/gks.h).
+ *
+ * Conventions (all quantities double precision):
+ *   D      spatial dimension 1..3, nv = D + 2 conservative variables (rho, rho*u_1..u_D, rho*E)
+ *   K      internal degrees of freedom, K = 2/(gamma-1) - D (Section 2, Maxwellian)
+ *   lambda = rho / (2 p)
+ *   Moments <.> are normalised by rho.
+ */
+#ifndef GKS_ORACLE_H
+#define GKS_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_FULL = 0, ORC_POS = 1, ORC_NEG = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_TRANSMISSIVE = 1, ORC_BC_WALL = 2, ORC_BC_DIRICHLET = 3, ORC_BC_OUTFLOW = 4 };
+enum { ORC_TURB_NONE = 0, ORC_TURB_MUT = 1, ORC_TURB_KEPS = 2, ORC_TURB_KOMEGA = 3 };
+enum { ORC_LIM_MINMOD = 0, ORC_LIM_VANLEER = 1 };
+enum { ORC_ABAR_TIMEINT = 0, ORC_ABAR_T0 = 1 };
+
+typedef struct {
+  int dim;
+  int n[3];
+  const double* dx[3];          /* per-cell widths along each axis, n[d] entries */
+  int bc[3][2];                 /* ORC_BC_* per axis, [lo, hi] */
+  const double* bc_prim[3][2];  /* Dirichlet data: primitive (rho, u_1..u_D, p) per boundary cell */
+  double gamma, mu, T_wall;     /* T_wall in units of p/rho */
+  int turb_model;
+  double C_mu, beta_star, C_a;
+  int limiter, multid, abar_mode;
+} orc_problem;
+
+/* Per-face record, normal frame (velocity index 0 is the face normal):
+ *   wl, wr   reconstructed conservative states left/right of the face        (nv each)
+ *   cl, cr   cell averages of the two adjacent cells                          (nv each)
+ *   sl, sr   normal slopes dW/dn of the left and right cells                  (nv each)
+ *   tl, tr   tangential slopes, D-1 blocks of nv each                         (3*nv each slot)
+ *   dxl, dxr distance from the left/right cell centre to the face
+ *   tau_t    turbulent relaxation time at the face
+ */
+typedef struct {
+  double wl[5], wr[5], cl[5], cr[5], sl[5], sr[5];
+  double tl[2][5], tr[2][5];
+  double dxl, dxr, tau_t;
+} orc_face;
+
+typedef struct {
+  double w0[5];                 /* interface equilibrium state */
+  double al[5], ar[5];          /* normal slope coefficients */
+  double bl[2][5], br[2][5];    /* tangential slope coefficients */
+  double Al[5], Ar[5];          /* time coefficients of the initial state */
+  double abl[5], abr[5];        /* equilibrium normal slopes */
+  double bb[2][5];              /* equilibrium tangential slopes */
+  double Ab[5];                 /* equilibrium time coefficient */
+  double tau;                   /* total relaxation time */
+  double T[6];                  /* T0..T5 */
+} orc_face_diag;
+
+int orc_umoments(double U, double lam, int region, int nmax, double* out);
+int orc_ximoments(double K, double lam, int lmax, double* out);
+int orc_time_coeffs(double dt, double tau, double* T /* T0..T5, then dt^2/2 - T2 */);
+int orc_slope(int D, double K, const double* w, const double* rhs, double* a_out);
+int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
+                  const orc_face* f, double* F, orc_face_diag* diag);
+int orc_face_flux_compact(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
+                          int printed_beta, const orc_face* f, double* F);
+int orc_euler_flux(int D, double gamma, const double* w, double* F);
+
+int orc_prim_to_cons(const orc_problem* P, const double* prim, double* W, long ncell);
+int orc_cons_to_prim(const orc_problem* P, const double* W, double* prim, long ncell);
+int orc_compute_dt(const orc_problem* P, const double* W, double cfl, double* dt);
+int orc_tau_turb(const orc_problem* P, const double* W, const double* f1, const double* f2, double* tau_t);
+int orc_rarefaction(const orc_problem* P, const double* W, const double* f1, const double* f2, double* eps);
+int orc_step(const orc_problem* P, double* W, const double* f1, const double* f2, double dt,
+             double* resid /* 3*nv: L2, Linf, total */, int nthreads);
+int orc_run(const orc_problem* P, double* W, const double* f1, const double* f2, double dt_fixed,
+            double cfl, int nsteps, double t_end, double* t_inout, int* steps_done, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

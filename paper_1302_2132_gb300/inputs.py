@@ -1,0 +1,231 @@
+"""Seeded synthetic inputs (primitive variables and turbulence fields) for the tests and the bench.
+
+This module is shared by both sides of the parity tests, so it holds none of the scheme's
+arithmetic: it only draws the initial primitive states (rho, u_1..u_D, p), cell widths, boundary
+data and the prescribed turbulence fields.  Each side converts primitives to conservative
+variables on its own.
+
+Workloads (stand-ins for the paper's wind-tunnel cases, whose geometries and data are not public
+inputs of this library):
+  sod_1d            Sod shock tube, 1D
+  turbulence        decaying compressible turbulence, periodic box, 2D or 3D: random-phase
+                    solenoidal velocity with E(k) ~ k^4 exp(-2 (k/k0)^2) scaled to a turbulent Mach
+                    number, rho = 1, p = 1/gamma; log-normal k and epsilon fields from 8 Fourier modes
+  riemann_quadrant  2D four-state Riemann problem with seeded states
+  shock_boundary_layer  Mach 2.85 flat-plate boundary layer under an oblique shock on a
+                    wall-clustered grid, with log-law k-omega profiles
+"""
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def sod_1d(n, length=1.0, x0=0.5):
+    """Sod: (rho, u, p) = (1, 0, 1) left of x0, (0.125, 0, 0.1) right; uniform cells."""
+    x = (np.arange(n) + 0.5) * (length / n)
+    prim = np.zeros((3, n))
+    left = x < x0
+    prim[0] = np.where(left, 1.0, 0.125)
+    prim[2] = np.where(left, 1.0, 0.1)
+    return dict(dim=1, n=(n,), dx=[np.full(n, length / n)], bc=[[1, 1]], prim=prim)
+
+
+def _solenoidal_velocity(rng, n, dim, k0):
+    """Random-phase velocity with energy spectrum E(k) ~ k^4 exp(-2 (k/k0)^2), divergence-free."""
+    shape = (n,) * dim
+    kk = np.meshgrid(*([np.fft.fftfreq(n, d=1.0 / n)] * dim), indexing="ij")  # integer wavenumbers
+    kmag = np.sqrt(sum(k * k for k in kk))
+    kmag_safe = np.where(kmag == 0, 1.0, kmag)
+    E = kmag ** 4 * np.exp(-2.0 * (kmag / k0) ** 2)
+    shell = 2.0 * math.pi * kmag_safe if dim == 2 else 4.0 * math.pi * kmag_safe ** 2
+    amp = np.sqrt(E / shell)
+    amp[kmag == 0] = 0.0
+    uh = []
+    for _ in range(dim):
+        phase = rng.uniform(0.0, 2.0 * math.pi, shape)
+        uh.append(amp * np.exp(1j * phase) * rng.normal(size=shape))
+    # project out the component along k
+    dot = sum(u * k for u, k in zip(uh, kk)) / kmag_safe ** 2
+    uh = [u - dot * k for u, k in zip(uh, kk)]
+    vel = [np.real(np.fft.ifftn(u)) for u in uh]
+    return vel
+
+
+def _lognormal_field(rng, n, dim, ref, sigma=0.5, modes=8, kmax=4):
+    """ref * exp(sigma * sum_m A_m cos(kappa_m . x + phi_m) / sqrt(modes)) on [0, 2 pi)^dim."""
+    x = [np.arange(n) * (2.0 * math.pi / n)] * dim
+    X = np.meshgrid(*x, indexing="ij")
+    s = np.zeros((n,) * dim)
+    for _ in range(modes):
+        kap = rng.integers(-kmax, kmax + 1, size=dim)
+        while not np.any(kap):
+            kap = rng.integers(-kmax, kmax + 1, size=dim)
+        A = rng.normal()
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        s += A * np.cos(sum(k * xx for k, xx in zip(kap, X)) + phi)
+    return ref * np.exp(sigma * s / math.sqrt(modes))
+
+
+def turbulence(n, dim, seed, k0=None, mach_t=None, C_mu=0.09, nu_ref=2e-5, gamma=GAMMA):
+    """Decaying compressible turbulence on [0, 2 pi)^dim, periodic; returns primitives in
+    [var][z][y][x] order (x fastest) and float32-representable k, epsilon fields."""
+    if k0 is None:
+        k0 = 8.0 if dim == 2 else 4.0
+    if mach_t is None:
+        mach_t = 0.3 if dim == 2 else 0.5
+    rng = np.random.default_rng(seed)
+    vel = _solenoidal_velocity(rng, n, dim, k0)
+    urms = math.sqrt(np.mean(sum(v * v for v in vel)))
+    c = 1.0  # rho = 1, p = 1/gamma
+    vel = [v * (mach_t * c / urms) for v in vel]
+    urms = mach_t * c
+    prim = np.zeros((dim + 2,) + (n,) * dim)
+    prim[0] = 1.0
+    # arrays are indexed [x][y][z] above; store x fastest: transpose to [z][y][x]
+    for i, v in enumerate(vel):
+        prim[1 + i] = v.T
+    prim[dim + 1] = 1.0 / gamma
+    frng = np.random.default_rng(seed + 1)
+    k_ref = 1.5 * urms * urms
+    eps_ref = C_mu * k_ref * k_ref / nu_ref
+    kf = _lognormal_field(frng, n, dim, k_ref).T
+    ef = _lognormal_field(frng, n, dim, eps_ref).T
+    h = 2.0 * math.pi / n
+    return dict(dim=dim, n=(n,) * dim, dx=[np.full(n, h)] * dim, bc=[[0, 0]] * dim, prim=prim,
+                f1=kf.astype(np.float32).astype(np.float64), f2=ef.astype(np.float32).astype(np.float64))
+
+
+def riemann_quadrant(n, seed):
+    """2D four-quadrant Riemann problem on [0,1]^2, transmissive boundaries, seeded states with
+    rho, p in [0.1, 1.5] and u, v in [-0.8, 0.8]."""
+    rng = np.random.default_rng(seed)
+    st = [(rng.uniform(0.1, 1.5), rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), rng.uniform(0.1, 1.5))
+          for _ in range(4)]
+    x = (np.arange(n) + 0.5) / n
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    q = (X >= 0.5).astype(int) + 2 * (Y >= 0.5).astype(int)
+    prim = np.zeros((4, n, n))
+    for k in range(4):
+        for v in range(4):
+            prim[v][q == k] = st[k][v]
+    return dict(dim=2, n=(n, n), dx=[np.full(n, 1.0 / n)] * 2, bc=[[1, 1], [1, 1]], prim=prim)
+
+
+def sod_2d(n, seed=0):
+    """Planar Sod along x on [0,1] x [0, 1], periodic in y."""
+    s = sod_1d(n)
+    prim = np.zeros((4, n, n))
+    prim[0] = s["prim"][0][None, :]
+    prim[1] = s["prim"][1][None, :]
+    prim[3] = s["prim"][2][None, :]
+    return dict(dim=2, n=(n, n), dx=[np.full(n, 1.0 / n)] * 2, bc=[[1, 1], [0, 0]], prim=prim)
+
+
+def random_smooth_2d(n, seed, amp=0.1):
+    """A smooth positive periodic 2D state (for conservation tests)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) * (2 * math.pi / n)
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    prim = np.zeros((4, n, n))
+    f = lambda: sum(rng.normal() * np.cos(kx * X + ky * Y + rng.uniform(0, 6.28))
+                    for kx, ky in ((1, 0), (0, 1), (1, 1), (2, -1)))
+    prim[0] = 1.0 + amp * f()
+    prim[1] = 0.3 * f()
+    prim[2] = 0.3 * f()
+    prim[3] = 1.0 + amp * f()
+    return dict(dim=2, n=(n, n), dx=[np.full(n, 2 * math.pi / n)] * 2, bc=[[0, 0], [0, 0]], prim=prim)
+
+
+# ------------------------------------------------------------------------------------------------
+# Mach 2.85 shock / boundary-layer interaction
+# ------------------------------------------------------------------------------------------------
+def _oblique_shock(M1, theta, gamma=GAMMA):
+    """Weak-branch wave angle and the post-shock (rho2/rho1, p2/p1, M2) for deflection theta
+    (theta-beta-M relation and normal-shock relations, any gas-dynamics text)."""
+    def tb(beta):
+        return 2.0 / math.tan(beta) * (M1 ** 2 * math.sin(beta) ** 2 - 1) / (
+            M1 ** 2 * (gamma + math.cos(2 * beta)) + 2) - math.tan(theta)
+    mu = math.asin(1.0 / M1)
+    # the weak solution lies between the Mach angle and the angle of maximum deflection
+    best = None
+    for k in range(1, 4000):
+        b = mu + (math.pi / 2 - mu) * k / 4000
+        if tb(b) > 0:
+            best = b
+            break
+    lo, hi = best - (math.pi / 2 - mu) / 4000, best
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if tb(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    beta = 0.5 * (lo + hi)
+    Mn1 = M1 * math.sin(beta)
+    r = (gamma + 1) * Mn1 ** 2 / ((gamma - 1) * Mn1 ** 2 + 2)
+    pr = 1 + 2 * gamma / (gamma + 1) * (Mn1 ** 2 - 1)
+    Mn2 = math.sqrt((1 + 0.5 * (gamma - 1) * Mn1 ** 2) / (gamma * Mn1 ** 2 - 0.5 * (gamma - 1)))
+    M2 = Mn2 / math.sin(beta - theta)
+    return beta, r, pr, M2
+
+
+def shock_boundary_layer(nx, ny, M=2.85, delta=0.1, theta_deg=24.0, Re_delta=1.6e6, ratio=1.08,
+                         dy1=2e-5, xlen=2.0, ylen=1.0, x_shock=0.4, gamma=GAMMA):
+    """Flat plate at the bottom (isothermal no-slip wall), Dirichlet inflow with a 1/7-power
+    profile below delta, supersonic outflow, and a top boundary carrying the post-shock state of a
+    theta deflection over x >= x_shock (free stream before).  Rows grow geometrically with the given
+    ratio up to a cap chosen so that the heights sum to ylen.  Free stream rho = 1, p = 1/gamma
+    (c = 1), u = M.  Returns primitives and k, omega fields of log-law profiles."""
+    # wall-clustered row heights, growth capped
+    def heights(cap):
+        h = dy1 * ratio ** np.arange(ny)
+        return np.minimum(h, cap)
+    lo, hi = dy1, ylen
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if heights(mid).sum() > ylen:
+            hi = mid
+        else:
+            lo = mid
+    dy = heights(0.5 * (lo + hi))
+    dy *= ylen / dy.sum()
+    dx = np.full(nx, xlen / nx)
+    yc = np.cumsum(dy) - 0.5 * dy
+    xc = (np.arange(nx) + 0.5) * (xlen / nx)
+    T_inf = 1.0 / gamma  # p/rho
+    T_wall = T_inf * (1.0 + 0.89 * 0.5 * (gamma - 1.0) * M * M)
+    U = M
+    mu = U * delta / Re_delta
+    prof = np.where(yc < delta, (np.maximum(yc, 0.0) / delta) ** (1.0 / 7.0), 1.0)
+    # temperature linear in the velocity ratio across the layer, pressure constant
+    Tprof = T_wall + (T_inf - T_wall) * prof
+    prim = np.zeros((4, ny, nx))
+    prim[0] = (1.0 / gamma / Tprof)[:, None]
+    prim[1] = (U * prof)[:, None]
+    prim[3] = 1.0 / gamma
+    inflow = np.stack([prim[0][:, 0], prim[1][:, 0], prim[2][:, 0], prim[3][:, 0]], axis=1)
+    beta, r2, p2, M2 = _oblique_shock(M, math.radians(theta_deg), gamma)
+    c2 = math.sqrt(gamma * (p2 / gamma) / r2)
+    th = math.radians(theta_deg)
+    post = (r2, M2 * c2 * math.cos(th), -M2 * c2 * math.sin(th), p2 / gamma)
+    free = (1.0, U, 0.0, 1.0 / gamma)
+    top = np.array([post if x >= x_shock else free for x in xc])
+    # log-law k-omega, beta* = 0.09, kappa = 0.41, c_f = 0.0016
+    bstar, kap = 0.09, 0.41
+    utau = U * math.sqrt(0.0016 / 2.0)
+    nu_w = mu * gamma * T_wall  # mu / rho_wall, rho_wall = p / T_wall
+    yplus = yc * utau / nu_w
+    om_sub = 6.0 * nu_w / (0.075 * yc ** 2)
+    om_log = utau / (math.sqrt(bstar) * kap * yc)
+    omega = np.maximum(om_sub, om_log)
+    kprof = utau ** 2 / math.sqrt(bstar) * np.minimum(1.0, (yplus / 10.0) ** 2)
+    kprof = np.where(yc < delta, kprof, 1e-6 * U * U)
+    omega = np.where(yc < delta, omega, U / delta)
+    f1 = np.repeat(kprof[:, None], nx, axis=1)
+    f2 = np.repeat(omega[:, None], nx, axis=1)
+    bc = [[3, 4], [2, 3]]
+    bc_prim = [[inflow, None], [None, top]]
+    return dict(dim=2, n=(nx, ny), dx=[dx, dy], bc=bc, bc_prim=bc_prim, prim=prim, T_wall=T_wall, mu=mu,
+                f1=f1.astype(np.float32).astype(np.float64), f2=f2.astype(np.float32).astype(np.float64))
