@@ -1,0 +1,337 @@
+"""Throughput of the GB300 gas-kinetic scheme on the 2D decaying-turbulence workload.
+
+Workload (one bench step): 1024 x 1024 cells on [0, 2 pi)^2, periodic; random-phase solenoidal
+velocity with E(k) ~ k^4 exp(-2 (k/8)^2) at turbulent Mach 0.3, rho = 1, p = 1/gamma; k-epsilon
+turbulent relaxation time from seeded log-normal k, epsilon fields; multi-dimensional expansion,
+van Leer MUSCL; FP32 flux arithmetic with the state accumulated in a float pair (48-bit) form;
+200 CFL time steps (CFL 0.5) from the initial state.  Inputs are synthetic (seed 1302).
+
+Metric: interface-flux evaluations per second (2 faces per cell per time step in 2D); cell updates
+per second are reported beside it.  `value` is timed with CUDA events on the library's stream with
+the inputs resident in HBM; `e2e` through the same C ABI from pinned host buffers, host<->device
+copies included.  The L2 cache is flushed (a 256 MiB write) between bench steps; within one bench
+step the 200 time steps work on a state that fits in L2, as the algorithm allows.
+
+`--impl reference` times the CPU oracle (the plain FP64 statement of the method) on the host cores on
+a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "turb2d_1024_keps_multid_fp32"
+N = 1024
+NSTEPS = 200
+CFL = 0.5
+MU = 1e-5
+SEED = 1302
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32_acc64", "fp64"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_inputs():
+    from paper_1302_2132_gb300 import inputs
+    return inputs.turbulence(N, 2, seed=SEED)
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_1302_2132_gb300 import build, gks
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    gks.load()
+    spec = workload_inputs()
+    faces_per_step = 2 * N * N
+    cells = N * N
+    solver = gks.Solver(2, (N, N), spec["bc"], dx=spec["dx"], gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09,
+                        C_a=0.0, limiter="vanleer", expand="multid", precision=args.precision)
+    prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
+    f1 = torch.tensor(spec["f1"].ravel(), device=dev)
+    f2 = torch.tensor(spec["f2"].ravel(), device=dev)
+    solver.set_turbulence(f1, f2)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = solver.stream
+
+    def one_step():
+        solver.set_state(prim_dev, layout="soa_prim")
+        solver.step(nsteps=NSTEPS, cfl=CFL)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    # ---- timed region: K bench steps, each bracketed by events on the library stream ----------
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        stream.wait_stream(torch.cuda.current_stream())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step()
+        e1.record(stream)
+        evs.append((e0, e1))
+        torch.cuda.current_stream().wait_stream(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    # ---- dominant kernel: the fused step kernel, timed launch by launch (events on its stream) ----
+    solver.enable_timing(True)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        one_step()
+    kms, klaunch = solver.kernel_time()
+    solver.enable_timing(False)
+    clock_info = clocks.stop() if clocks else None
+    # sanity of the result: finite state, conservation monitor
+    _, _, total = solver.residual()
+    t_end, _ = solver.time()
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = tt.item()
+    # ---- end to end through the C ABI from pinned host memory ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        prim_host = torch.tensor(spec["prim"].ravel()).pin_memory()
+        f1_host = torch.tensor(spec["f1"].ravel()).pin_memory()
+        f2_host = torch.tensor(spec["f2"].ravel()).pin_memory()
+        out_host = torch.empty(4 * cells, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            solver.set_state(prim_host, layout="soa_prim")
+            solver.set_turbulence(f1_host, f2_host)
+            solver.step(nsteps=NSTEPS, cfl=CFL)
+            solver.get_state(out=out_host)
+        t1 = time.perf_counter()
+        assert torch.isfinite(out_host).all()
+        e2e_s = (t1 - t0)
+        e2e = {"value": faces_per_step * NSTEPS * args.steps * world / e2e_s, "unit": "face_flux_evals/s",
+               "h2d_bytes_per_step": int(prim_host.numel() * 8 + f1_host.numel() * 8 + f2_host.numel() * 8),
+               "d2h_bytes_per_step": int(out_host.numel() * 8)}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    secs = ms / 1e3
+    value = faces_per_step * NSTEPS * args.steps * world / secs
+    # roofline of the fused step kernel (FP32 ALU bound): algorithmic operations per launch
+    counts = flop_counts(multid=True)
+    per_face = sum(counts[:3])
+    per_cell = CELL_OPS
+    ops_per_launch = faces_per_step * per_face + cells * per_cell
+    avg_launch_s = kms / 1e3 / max(klaunch, 1)
+    achieved = ops_per_launch / avg_launch_s / 1e12
+    peak = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 lanes x FMA x max SM clock
+    line = {
+        "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
+        "value": value,
+        "unit": "face_flux_evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N, N], "time_steps_per_bench_step": NSTEPS, "cfl": CFL,
+                   "turbulence": "k-epsilon, seeded log-normal k and epsilon", "expand": "multid",
+                   "precision": args.precision, "state_accumulation": {"fp32": "float pair (hi+lo)",
+                                                                      "fp32_acc64": "IEEE double",
+                                                                      "fp64": "IEEE double"}[args.precision],
+                   "l2": "flushed between bench steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "single"},
+        "cell_updates_per_s": cells * NSTEPS * args.steps * world / secs,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "step_kernel<2, PREC_F32, multid>", "avg_launch_us": avg_launch_s * 1e6,
+                     "ops_per_face": per_face, "ops_per_cell": per_cell,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz (derived)"},
+        "gpu_launches": args.steps * (NSTEPS + 3),
+        "clocks": clock_info,
+        "e2e": e2e,
+        "final_time": t_end,
+        "total_mass": float(total[0]),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(budget_s=15.0)
+    print(json.dumps(line))
+    sys.stdout.flush()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# per-cell operations of the fused step besides the faces: turbulent relaxation time (velocity
+# gradient, strain rate, k-epsilon formula: about 60), update (nv x (2 x 3)), CFL rate (about 12)
+CELL_OPS = 60 + 4 * 6 + 12
+
+
+def flop_counts(multid=True):
+    import ctypes
+    from paper_1302_2132_gb300 import gks
+    L = gks.load()
+    c = (ctypes.c_longlong * 6)()
+    L.gks_face_op_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_face_op_count(2, int(multid), 1, c)
+    return list(c)
+
+
+def oracle_sample(n_crop, nthreads):
+    """One FP64 oracle time step on an n_crop^2 crop of the workload: (faces evaluated, seconds)."""
+    import oracle
+    spec = workload_inputs()
+    prim = spec["prim"][:, :n_crop, :n_crop]
+    h = 2 * math.pi / N
+    c = oracle.Case(2, (n_crop, n_crop), [np.full(n_crop, h)] * 2, [[0, 0], [0, 0]], gamma=1.4, mu=MU,
+                    turb_model=oracle.TURB_KEPS, C_mu=0.09, C_a=0.0, limiter=oracle.LIM_VANLEER, multid=1)
+    W = c.prim_to_cons(np.ascontiguousarray(prim).ravel())
+    f1 = np.ascontiguousarray(spec["f1"][:n_crop, :n_crop]).ravel()
+    f2 = np.ascontiguousarray(spec["f2"][:n_crop, :n_crop]).ravel()
+    dt = c.compute_dt(W, CFL)
+    t0 = time.perf_counter()
+    c.step(W, dt, f1=f1, f2=f2, nthreads=nthreads)
+    return 2 * n_crop * n_crop, time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s=15.0):
+    cores = os.cpu_count() or 1
+    n_crop = 128
+    faces, secs = oracle_sample(n_crop, cores)
+    # grow the crop to spend about budget_s of wall time
+    scale = max(1.0, math.sqrt(budget_s / max(secs, 1e-3)))
+    n_crop = int(min(N, 16 * round(n_crop * scale / 16)))
+    faces, secs = oracle_sample(n_crop, cores)
+    return {"value": faces / secs, "unit": "face_flux_evals/s", "cores": cores, "kind": "oracle",
+            "sample": "one FP64 time step of a %dx%d crop of the 1024^2 workload (OpenMP over faces, %d threads)"
+                      % (n_crop, n_crop, cores)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n_crop = 160
+    for _ in range(args.warmup):
+        oracle_sample(64, cores)
+    total_f, total_s = 0, 0.0
+    for _ in range(args.steps):
+        f, s = oracle_sample(n_crop, cores)
+        total_f += f
+        total_s += s
+    value = total_f / total_s
+    line = {"impl": "reference",
+            "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
+            "value": value, "unit": "face_flux_evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N, N], "sample_crop": [n_crop, n_crop]},
+            "cpu_baseline": {"value": value, "unit": "face_flux_evals/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: one FP64 time step of a %dx%d crop of the 1024^2 workload"
+                                       % (n_crop, n_crop)},
+            "e2e": {"value": value, "unit": "face_flux_evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

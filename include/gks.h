@@ -1,0 +1,171 @@
+/*
+ * gks.h -- C ABI of the GB300 gas-kinetic flux library (libgks.so).
+ *
+ * The library advances the compressible Navier-Stokes equations with the gas-kinetic BGK-NS
+ * interface flux (Righi 2013 Section 2; Xu's scheme) whose relaxation time carries a turbulent
+ * part built from prescribed turbulence fields (Section 3, Eqs. tauttrivial, tautchen; Section 4,
+ * Eqs. relaxation time, taua, tautchenadjusted).  One call of gks_step performs, per time step:
+ * boundary cells, the CFL time step, the turbulent relaxation-time field, MUSCL reconstruction,
+ * the interface equilibrium state from half-space Maxwellian moments, the slope coefficients
+ * a, A, b, the time-integration coefficients, flux assembly (Eq. fluxesf) and the conservative
+ * update, all in CUDA kernels on the handle's device.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a gks_status; nothing throws across the ABI.  gks_last_error() gives a
+ *     message for the last failing call on a handle.
+ *   - Caller buffers are never retained: state and fields are copied in and out.
+ *   - Device pointers must be on the handle's device.  Host buffers may be pageable or pinned
+ *     (pinned buffers make the copies asynchronous up to the synchronising calls).
+ *   - Work is ordered on the handle's CUDA stream.  gks_compute_dt, gks_residual, gks_get_time,
+ *     gks_status_word and the host-memory variants of the copy calls synchronise that stream.
+ *   - State layout: conservative variables W = (rho, rho u_1..rho u_D, rho E), nv = D + 2.
+ *     SOA means [v][z][y][x] (x fastest), AOS means [z][y][x][v].  Primitive layout is
+ *     (rho, u_1..u_D, p) in SOA order.
+ *   - GKS_ENONPHYS (a cell reached rho <= 0 or p <= 0) is sticky until the next gks_set_state;
+ *     it is reported by the synchronising calls.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gks_handle gks_handle;
+
+typedef enum {
+  GKS_OK = 0,
+  GKS_EINVAL = 1,       /* invalid argument */
+  GKS_ENOMEM = 2,       /* device or host allocation failed */
+  GKS_ECUDA = 3,        /* a CUDA runtime call failed */
+  GKS_ENONPHYS = 4,     /* non-physical state (rho <= 0 or p <= 0) produced */
+  GKS_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  GKS_EUNSUPPORTED = 6  /* option not built */
+} gks_status;
+
+/* boundary conditions per axis side (Section 4: walls are treated as in conventional CFD) */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1, GKS_BC_WALL = 2, GKS_BC_DIRICHLET = 3, GKS_BC_OUTFLOW = 4 };
+/* turbulent relaxation time: none, tau_t = mu_t/p (Eq. tauttrivial), k-epsilon (Eq. tautchen),
+ * k-omega (Eq. tautchenadjusted) */
+enum { GKS_TURB_NONE = 0, GKS_TURB_MUT = 1, GKS_TURB_KEPS = 2, GKS_TURB_KOMEGA = 3 };
+enum { GKS_LIM_MINMOD = 0, GKS_LIM_VANLEER = 1 };
+/* expansion of the distribution along the face normal only, or along every axis (Section 4) */
+enum { GKS_EXPAND_DIRECTIONAL = 0, GKS_EXPAND_MULTID = 1 };
+/* arithmetic: FP64 throughout; FP32 flux with the state accumulated as an unevaluated pair of
+ * floats (about 48 significant bits); FP32 flux with an IEEE double state */
+enum { GKS_FP64 = 0, GKS_FP32 = 1, GKS_FP32_ACC64 = 2 };
+/* equilibrium time slope Abar: time-integrated compatibility (default) or the t = 0 one */
+enum { GKS_ABAR_TIMEINT = 0, GKS_ABAR_T0 = 1 };
+enum { GKS_LAYOUT_SOA_CONS = 0, GKS_LAYOUT_AOS_CONS = 1, GKS_LAYOUT_SOA_PRIM = 2 };
+enum { GKS_MEM_HOST = 0, GKS_MEM_DEVICE = 1 };
+enum { GKS_F64 = 0, GKS_F32 = 1 };
+
+typedef struct {
+  int dim;                       /* 1, 2 or 3 */
+  int n[3];                      /* cells per axis (>= 2 on active axes) */
+  double lo[3], hi[3];           /* extent; used when dx[d] is NULL (uniform cells) */
+  const double* dx[3];           /* host array of n[d] cell widths, or NULL */
+  int bc[3][2];                  /* GKS_BC_* for [axis][lo, hi]; periodic must be set on both sides */
+  const double* bc_data[3][2];   /* host, GKS_BC_DIRICHLET only: primitive (rho, u.., p) per boundary
+                                    cell, cells ordered by the other axes in increasing order, [cell][nv] */
+} gks_grid;
+
+typedef struct {
+  double gamma;    /* ratio of specific heats; K = 2/(gamma-1) - dim internal degrees of freedom >= 0 */
+  double mu;       /* molecular viscosity, tau_mol = mu / p (Section 2, Chapman-Enskog) */
+  double prandtl;  /* only 1 (the BGK value) is built */
+  double T_wall;   /* wall temperature in units of p/rho, GKS_BC_WALL */
+} gks_gas;
+
+typedef struct {
+  int model;        /* GKS_TURB_* */
+  double C_mu;      /* k-epsilon constant (Eq. tautchen), usually 0.09 */
+  double beta_star; /* k-omega: eta = S / (beta* omega) */
+  double C_a;       /* artificial dissipation coefficient in [0, 1] (Eq. taua) */
+} gks_turb;
+
+typedef struct {
+  int limiter;    /* GKS_LIM_* */
+  int expand;     /* GKS_EXPAND_* */
+  int precision;  /* GKS_FP64 | GKS_FP32 | GKS_FP32_ACC64 */
+  int abar_mode;  /* GKS_ABAR_* */
+} gks_numerics;
+
+/* Create a solver on the current CUDA device.  cuda_stream is a cudaStream_t or NULL (the library
+ * then creates its own non-blocking stream).  All device buffers are allocated here and owned by
+ * the handle.  Errors: GKS_EINVAL for bad sizes, codes or Dirichlet data, GKS_ENOMEM, GKS_ECUDA. */
+gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb,
+                      const gks_numerics* num, void* cuda_stream, gks_handle** out);
+
+/* Copy a state in (any layout, float or double, host or device) and reset time to 0, the step
+ * counter and the sticky status.  The CFL rate of the new state is computed on the device. */
+gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace, int dtype);
+
+/* Copy out the current state in the requested layout and type. */
+gks_status gks_get_state(gks_handle* h, void* W_out, int layout, int memspace, int dtype);
+
+/* Copy in the turbulence fields, one value per cell in [z][y][x] order: f1 = k (or mu_t),
+ * f2 = epsilon or omega (NULL for GKS_TURB_MUT). */
+gks_status gks_set_turbulence(gks_handle* h, const void* f1, const void* f2, int memspace, int dtype);
+
+/* CFL time step of the current state: dt = cfl / max_cells sum_d (|U_d| + c) / dx_d. Synchronises. */
+gks_status gks_compute_dt(gks_handle* h, double cfl, double* dt_out);
+
+/* Advance nsteps steps.  dt > 0: fixed step; dt <= 0: the CFL step of the current state each step.
+ * t_end > 0: the step that would pass t_end is clamped to reach it and later steps do nothing.
+ * Asynchronous; the last step also accumulates the residual norms read by gks_residual. */
+gks_status gks_step(gks_handle* h, double dt, double cfl, int nsteps, double t_end);
+
+/* Time and number of steps taken since the last gks_set_state (or gks_set_time).  Synchronises. */
+gks_status gks_get_time(gks_handle* h, double* t, long long* steps);
+
+/* Set the solution time (restart from a checkpoint: gks_set_state then gks_set_time). */
+gks_status gks_set_time(gks_handle* h, double t);
+
+/* Norms of (W^{n+1} - W^n)/dt of the last step of the last gks_step call, per variable (nv each):
+ * L2 = sqrt(mean of squares), L-infinity, and total = sum of W times cell volume.  Synchronises. */
+gks_status gks_residual(gks_handle* h, double* l2, double* linf, double* total);
+
+/* Sticky status bits (bit 0: non-physical state) and the last time step used.  Synchronises. */
+gks_status gks_status_word(gks_handle* h, unsigned int* bits, double* last_dt);
+
+/* Rarefaction diagnostic per cell (Eqs. tautautilde, tautilde): eps = (mu/p + tau_t) |div U|,
+ * tauhat = rho / |D rho| with D rho = -rho div U. */
+gks_status gks_get_rarefaction(gks_handle* h, void* eps_out, int memspace, int dtype);
+
+/* Turbulent relaxation time per cell (Eqs. tauttrivial, tautchen, tautchenadjusted, T = p/rho). */
+gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtype);
+
+/* Device time of the step kernels launched by gks_step while timing is enabled (CUDA events on
+ * the handle's stream around each launch; graphs are not used while timing). */
+gks_status gks_enable_timing(gks_handle* h, int enable);
+gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
+
+gks_status gks_destroy(gks_handle* h);
+const char* gks_last_error(const gks_handle* h);
+
+/* Stateless evaluation of nfaces interface fluxes (Eq. fluxesf) on the device, for testing and
+ * for callers with their own reconstruction.  faces: device array of nfaces records of
+ * gks_face_record_len(dim) doubles, in the frame of the face (velocity 0 = normal):
+ *   wl[nv] wr[nv] cl[nv] cr[nv] sl[nv] sr[nv] tl[dim-1][nv] tr[dim-1][nv] dxl dxr tau_t
+ * (reconstructed states, adjacent cell averages, normal slopes, tangential slopes, centre-to-face
+ * distances, turbulent relaxation time).  F_out: device, nfaces * nv time-integrated fluxes;
+ * tau_out: device, nfaces total relaxation times, or NULL.  precision GKS_FP64 or GKS_FP32.
+ * Asynchronous on cuda_stream. */
+int gks_face_record_len(int dim);
+gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, double gamma, double mu,
+                         double C_a, double dt, const double* faces, long nfaces, double* F_out,
+                         double* tau_out, void* cuda_stream);
+
+/* Operation count of one interface flux as the device code is written (no GPU needed): counts[0..5]
+ * = additions/subtractions, multiplications, divisions, square roots, exponentials, erfc.
+ * with_recon adds the MUSCL reconstruction of the face (van Leer).  Operations on literal 0 or 1
+ * are not counted.  Used to state the algorithmic FLOPs behind the roofline figures. */
+int gks_face_op_count(int dim, int expand, int with_recon, long long* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_H */

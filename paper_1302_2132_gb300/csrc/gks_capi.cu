@@ -1,0 +1,827 @@
+// C ABI of the gas-kinetic library (include/gks.h): handle, device buffers, state conversion,
+// time stepping with captured CUDA graphs, diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gks.h"
+#include "gks_dispatch.h"
+#include "gks_step.cuh"
+
+using namespace gks;
+
+struct gks_handle {
+  int dev = 0;
+  int D = 1, nv = 3;
+  int n[3] = {1, 1, 1};
+  long ncell = 0;
+  int prec = PREC_F64;
+  bool multid = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* W[2] = {nullptr, nullptr};
+  float* Wlo[2] = {nullptr, nullptr};
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  double* widths[3] = {nullptr, nullptr, nullptr};
+  double* dir[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  Ctrl* ctrl = nullptr;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  long long step = 0;
+  bool has_state = false, has_turb = false;
+  int nblocks = 0;
+  StepArgs base;
+  std::map<int, cudaGraphExec_t> graphs;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  double ms_total = 0.0;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+const int kGraphChunk = 48;  // steps per captured graph; a multiple of 6 keeps buffer and slot phases fixed
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+gks_status fail(gks_handle* h, gks_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+gks_status cuda_fail(gks_handle* h, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(h, GKS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GKS_CK(h, call)                                          \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);     \
+  } while (0)
+
+size_t stored_bytes(int prec) { return prec == PREC_F32 ? sizeof(float) : sizeof(double); }
+size_t arith_bytes(int prec) { return prec == PREC_F64 ? sizeof(double) : sizeof(float); }
+
+// ------------------------------------------------------------------------------------------------
+// Kernels for state conversion, CFL rate and diagnostics
+// ------------------------------------------------------------------------------------------------
+template <class Tin>
+__global__ void state_in_kernel(const Tin* src, int layout, int D, long ncell, double gamma, int prec,
+                                void* W, float* Wlo) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int nv = D + 2;
+  double w[5];
+  for (int v = 0; v < nv; ++v) w[v] = (double)(layout == GKS_LAYOUT_AOS_CONS ? src[c * nv + v] : src[v * ncell + c]);
+  if (layout == GKS_LAYOUT_SOA_PRIM) {
+    const double rho = w[0], p = w[D + 1];
+    double q = 0.0;
+    for (int i = 0; i < D; ++i) {
+      q += w[1 + i] * w[1 + i];
+      w[1 + i] = rho * w[1 + i];
+    }
+    w[D + 1] = p / (gamma - 1.0) + 0.5 * rho * q;
+  }
+  for (int v = 0; v < nv; ++v) {
+    if (prec == PREC_F32) {
+      const float hi = (float)w[v];
+      ((float*)W)[v * ncell + c] = hi;
+      Wlo[v * ncell + c] = (float)(w[v] - (double)hi);
+    } else {
+      ((double*)W)[v * ncell + c] = w[v];
+    }
+  }
+}
+
+template <class Tout>
+__global__ void state_out_kernel(Tout* dst, int layout, int D, long ncell, double gamma, int prec, const void* W,
+                                 const float* Wlo) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int nv = D + 2;
+  double w[5];
+  for (int v = 0; v < nv; ++v)
+    w[v] = prec == PREC_F32 ? (double)((const float*)W)[v * ncell + c] + (double)Wlo[v * ncell + c]
+                            : ((const double*)W)[v * ncell + c];
+  if (layout == GKS_LAYOUT_SOA_PRIM) {
+    double q = 0.0;
+    for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
+    const double p = (gamma - 1.0) * (w[D + 1] - 0.5 * q / w[0]);
+    for (int i = 0; i < D; ++i) w[1 + i] = w[1 + i] / w[0];
+    w[D + 1] = p;
+  }
+  for (int v = 0; v < nv; ++v) {
+    if (layout == GKS_LAYOUT_AOS_CONS)
+      dst[c * nv + v] = (Tout)w[v];
+    else
+      dst[v * ncell + c] = (Tout)w[v];
+  }
+}
+
+template <class Tin, class Tout>
+__global__ void field_kernel(const Tin* src, Tout* dst, long n) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) dst[c] = (Tout)src[c];
+}
+
+template <class T>
+__global__ void copy_kernel(const T* src, T* dst, long n) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) dst[c] = src[c];
+}
+
+// CFL rate of the stored state into ctrl->rate[slot] (a step computes it for its successor).
+template <int D, int PREC>
+__global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ StepArgs A) {
+  using R = typename PrecT<PREC>::R;
+  __shared__ double red[kThreads / 32];
+  const DevGrid& g = A.g;
+  R rmax = R(0);
+  for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += (long)gridDim.x * blockDim.x) {
+    R w[D + 2];
+    load_stored<D, PREC>(A, c, w);
+    int pos[3];
+    pos[0] = (int)(c % g.n[0]);
+    pos[1] = (int)((c / g.n[0]) % g.n[1]);
+    pos[2] = (int)(c / ((long)g.n[0] * g.n[1]));
+    R h[D];
+    for (int d = 0; d < D; ++d) h[d] = (R)g.w[d][pos[d] + 2];
+    rmax = fmax(rmax, cell_rate<D, R>(w, (R)g.gamma, h));
+  }
+  const double m = block_max<double>((double)rmax, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(&A.ctrl->rate[A.slot], m);
+}
+
+// Per-cell turbulent relaxation time and rarefaction diagnostic, from the same cell formula the
+// step kernel uses (neighbourhood staged in registers with the boundary rules applied).
+template <int D, int PREC>
+__global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ StepArgs A, int what, void* out,
+                                                        int out_dtype) {
+  using R = typename PrecT<PREC>::R;
+  constexpr int nv = D + 2;
+  constexpr int S3 = D >= 3 ? 3 : 1, S2 = D >= 2 ? 3 : 1;
+  const DevGrid& g = A.g;
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
+  R Wn[nv * 3 * S2 * S3];
+  const int NN = 3 * S2 * S3;
+  for (int l = 0; l < NN; ++l) {
+    const int di = l % 3 - 1, dj = D >= 2 ? (l / 3) % 3 - 1 : 0, dk = D >= 3 ? l / 9 - 1 : 0;
+    const bool on_axis = (di != 0) + (dj != 0) + (dk != 0) <= 1;
+    R w[nv];
+    if (on_axis) {
+      load_cell<D, PREC>(A, i + di, j + dj, k + dk, w);
+    } else {
+      for (int v = 0; v < nv; ++v) w[v] = R(1);
+    }
+    for (int v = 0; v < nv; ++v) Wn[v * NN + l] = w[v];
+  }
+  R wx[3], wy[3], wz[3];
+  for (int q = 0; q < 3; ++q) {
+    wx[q] = (R)g.w[0][i + 1 + q];
+    wy[q] = D >= 2 ? (R)g.w[1][j + 1 + q] : R(1);
+    wz[q] = D >= 3 ? (R)g.w[2][k + 1 + q] : R(1);
+  }
+  const int strides[3] = {1, 3, 9};
+  const R* widths[3] = {wx, wy, wz};
+  const int pos[3] = {1, 1, 1};
+  const int idx = 1 + (D >= 2 ? 3 : 0) + (D >= 3 ? 9 : 0);
+  R f1 = R(0), f2 = R(0);
+  if (g.turb_model != TURB_NONE) {
+    f1 = ((const R*)A.f1)[c];
+    if (g.turb_model != TURB_MUT) f2 = ((const R*)A.f2)[c];
+  }
+  R val = tau_turb_cell<D, R>(g, Wn, NN, idx, strides, widths, pos, f1, f2);
+  if (what == 1) {  // rarefaction: (mu/p + tau_t) |div U|
+    R w[nv];
+    for (int v = 0; v < nv; ++v) w[v] = Wn[v * NN + idx];
+    const R p = pressure_of<R>(D, (R)g.gamma, w);
+    R div = R(0);
+    for (int a = 0; a < D; ++a) {
+      const R* wd = widths[a];
+      const R dist = R(0.5) * wd[0] + wd[1] + R(0.5) * wd[2];
+      const int im = idx - strides[a], ip = idx + strides[a];
+      div += (Wn[(1 + a) * NN + ip] / Wn[ip] - Wn[(1 + a) * NN + im] / Wn[im]) / dist;
+    }
+    val = ((R)g.mu / p + val) * g_abs(div);
+  }
+  if (out_dtype == GKS_F64)
+    ((double*)out)[c] = (double)val;
+  else
+    ((float*)out)[c] = (float)val;
+}
+
+__global__ void set_params_kernel(Ctrl* c, double dt_fixed, double cfl, double t_end) {
+  c->dt_fixed = dt_fixed;
+  c->cfl = cfl;
+  c->t_end = t_end;
+  for (int v = 0; v < 5; ++v) {
+    c->l2[v] = 0.0;
+    c->total[v] = 0.0;
+    c->linf[v] = 0ull;
+  }
+}
+
+__global__ void set_time_kernel(Ctrl* c, int slot, double t) { c->t[slot] = t; }
+
+inline unsigned grid_for(long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+void launch_step(gks_handle* h, const StepArgs& A) {
+  if (h->D == 1)
+    launch_step_d1(h->prec, false, A, h->nblocks, h->stream);
+  else if (h->D == 2)
+    launch_step_d2(h->prec, h->multid, A, h->nblocks, h->stream);
+  else
+    launch_step_d3(h->prec, h->multid, A, h->nblocks, h->stream);
+}
+
+// Arguments of the step that starts at absolute step index s.
+StepArgs step_args(const gks_handle* h, long long s, int resid) {
+  StepArgs A = h->base;
+  const int cur = (int)(s & 1);
+  A.Win = h->W[cur];
+  A.Wout = h->W[cur ^ 1];
+  A.Win_lo = h->Wlo[cur];
+  A.Wout_lo = h->Wlo[cur ^ 1];
+  A.slot = (int)(s % 3);
+  A.tslot = cur;
+  A.resid = resid;
+  return A;
+}
+
+template <int D>
+void launch_rate_d(gks_handle* h, const StepArgs& A, unsigned blocks) {
+  if (h->prec == PREC_F64)
+    rate_kernel<D, PREC_F64><<<blocks, kThreads, 0, h->stream>>>(A);
+  else if (h->prec == PREC_F32)
+    rate_kernel<D, PREC_F32><<<blocks, kThreads, 0, h->stream>>>(A);
+  else
+    rate_kernel<D, PREC_F32D><<<blocks, kThreads, 0, h->stream>>>(A);
+}
+
+gks_status launch_rate(gks_handle* h) {
+  StepArgs A = step_args(h, h->step, 0);
+  const unsigned blocks = std::min<unsigned>(grid_for(h->ncell, kThreads), 152u * 8u);
+  if (h->D == 1)
+    launch_rate_d<1>(h, A, blocks);
+  else if (h->D == 2)
+    launch_rate_d<2>(h, A, blocks);
+  else
+    launch_rate_d<3>(h, A, blocks);
+  GKS_CK(h, cudaGetLastError());
+  return GKS_OK;
+}
+
+template <int D>
+void launch_diag_d(gks_handle* h, const StepArgs& A, int what, void* out, int dtype) {
+  const unsigned blocks = grid_for(h->ncell, kThreads);
+  if (h->prec == PREC_F64)
+    diag_kernel<D, PREC_F64><<<blocks, kThreads, 0, h->stream>>>(A, what, out, dtype);
+  else if (h->prec == PREC_F32)
+    diag_kernel<D, PREC_F32><<<blocks, kThreads, 0, h->stream>>>(A, what, out, dtype);
+  else
+    diag_kernel<D, PREC_F32D><<<blocks, kThreads, 0, h->stream>>>(A, what, out, dtype);
+}
+
+gks_status ensure_staging(gks_handle* h, size_t bytes) {
+  if (h->staging_bytes >= bytes) return GKS_OK;
+  if (h->staging) cudaFree(h->staging);
+  h->staging = nullptr;
+  h->staging_bytes = 0;
+  if (cudaMalloc(&h->staging, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GKS_ENOMEM, "staging buffer allocation failed");
+  }
+  h->staging_bytes = bytes;
+  return GKS_OK;
+}
+
+bool valid_bc(int b) { return b >= GKS_BC_PERIODIC && b <= GKS_BC_OUTFLOW; }
+
+void free_all(gks_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+  for (int b = 0; b < 2; ++b) {
+    if (h->W[b]) cudaFree(h->W[b]);
+    if (h->Wlo[b]) cudaFree(h->Wlo[b]);
+  }
+  if (h->f1) cudaFree(h->f1);
+  if (h->f2) cudaFree(h->f2);
+  for (int d = 0; d < 3; ++d) {
+    if (h->widths[d]) cudaFree(h->widths[d]);
+    for (int s = 0; s < 2; ++s)
+      if (h->dir[d][s]) cudaFree(h->dir[d][s]);
+  }
+  if (h->ctrl) cudaFree(h->ctrl);
+  if (h->staging) cudaFree(h->staging);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+gks_status sticky_status(gks_handle* h) {
+  unsigned int st = 0;
+  GKS_CK(h, cudaMemcpyAsync(&st, &h->ctrl->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  if (st & 1u) return fail(h, GKS_ENONPHYS, "non-physical state (rho <= 0 or p <= 0) produced");
+  return GKS_OK;
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb, const gks_numerics* num,
+                      void* cuda_stream, gks_handle** out) {
+  if (!out) return GKS_EINVAL;
+  *out = nullptr;
+  if (!grid || !gas || !num) return GKS_EINVAL;
+  gks_handle* h = new (std::nothrow) gks_handle();
+  if (!h) return GKS_ENOMEM;
+  auto bad = [&](gks_status s, const char* m) {
+    h->err = m;
+    *out = h;  // return the handle so that the caller can read the message
+    return s;
+  };
+  const int D = grid->dim;
+  if (D < 1 || D > 3) return bad(GKS_EINVAL, "dim must be 1, 2 or 3");
+  h->D = D;
+  h->nv = D + 2;
+  h->ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    h->n[d] = d < D ? grid->n[d] : 1;
+    if (d < D && h->n[d] < 2) return bad(GKS_EINVAL, "at least two cells per active axis");
+    h->ncell *= h->n[d];
+  }
+  if (!(gas->gamma > 1.0)) return bad(GKS_EINVAL, "gamma must exceed 1");
+  const double bK = 2.0 / (gas->gamma - 1.0), K = bK - D;
+  if (K < 0.0) return bad(GKS_EINVAL, "gamma leaves a negative number of internal degrees of freedom");
+  if (!(gas->mu >= 0.0)) return bad(GKS_EINVAL, "mu must be >= 0");
+  if (gas->prandtl != 0.0 && gas->prandtl != 1.0) return bad(GKS_EUNSUPPORTED, "only Pr = 1 is built");
+  if (num->precision < GKS_FP64 || num->precision > GKS_FP32_ACC64) return bad(GKS_EINVAL, "precision");
+  if (num->limiter != GKS_LIM_MINMOD && num->limiter != GKS_LIM_VANLEER) return bad(GKS_EINVAL, "limiter");
+  if (num->expand != GKS_EXPAND_DIRECTIONAL && num->expand != GKS_EXPAND_MULTID) return bad(GKS_EINVAL, "expand");
+  if (num->abar_mode != GKS_ABAR_TIMEINT && num->abar_mode != GKS_ABAR_T0) return bad(GKS_EINVAL, "abar_mode");
+  const int model = turb ? turb->model : GKS_TURB_NONE;
+  if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA) return bad(GKS_EINVAL, "turbulence model");
+  for (int d = 0; d < D; ++d) {
+    for (int s = 0; s < 2; ++s) {
+      if (!valid_bc(grid->bc[d][s])) return bad(GKS_EINVAL, "boundary condition code");
+      if (grid->bc[d][s] == GKS_BC_DIRICHLET && !grid->bc_data[d][s]) return bad(GKS_EINVAL, "Dirichlet data missing");
+    }
+    if ((grid->bc[d][0] == GKS_BC_PERIODIC) != (grid->bc[d][1] == GKS_BC_PERIODIC))
+      return bad(GKS_EINVAL, "periodic boundaries must be set on both sides of an axis");
+    if (!grid->dx[d] && !(grid->hi[d] > grid->lo[d])) return bad(GKS_EINVAL, "extent hi > lo required");
+    if (grid->dx[d])
+      for (int i = 0; i < h->n[d]; ++i)
+        if (!(grid->dx[d][i] > 0.0)) return bad(GKS_EINVAL, "cell widths must be positive");
+  }
+  if (grid->bc[0][0] == GKS_BC_WALL || grid->bc[0][1] == GKS_BC_WALL || (D > 1 && (grid->bc[1][0] == GKS_BC_WALL ||
+      grid->bc[1][1] == GKS_BC_WALL)) || (D > 2 && (grid->bc[2][0] == GKS_BC_WALL || grid->bc[2][1] == GKS_BC_WALL)))
+    if (!(gas->T_wall > 0.0)) return bad(GKS_EINVAL, "T_wall must be positive with wall boundaries");
+  h->prec = num->precision;
+  h->multid = D > 1 && num->expand == GKS_EXPAND_MULTID;
+
+  if (cudaGetDevice(&h->dev) != cudaSuccess) {
+    cudaGetLastError();
+    return bad(GKS_ECUDA, "no CUDA device");
+  }
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return bad(GKS_ECUDA, "stream creation failed");
+    }
+    h->own_stream = true;
+  }
+  static bool prepared[4] = {false, false, false, false};
+  if (!prepared[D]) {
+    cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bad(GKS_ECUDA, "kernel attribute setup failed");
+    }
+    prepared[D] = true;
+  }
+
+  const size_t sb = stored_bytes(h->prec), nbytes = sb * h->nv * h->ncell;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  for (int b = 0; b < 2; ++b) {
+    if (!alloc(&h->W[b], nbytes)) return bad(GKS_ENOMEM, "state allocation failed");
+    if (h->prec == PREC_F32 && !alloc((void**)&h->Wlo[b], sizeof(float) * h->nv * h->ncell))
+      return bad(GKS_ENOMEM, "state allocation failed");
+  }
+  if (!alloc((void**)&h->ctrl, sizeof(Ctrl))) return bad(GKS_ENOMEM, "control block allocation failed");
+  cudaMemset(h->ctrl, 0, sizeof(Ctrl));
+  if (model != GKS_TURB_NONE) {
+    const size_t fb = arith_bytes(h->prec) * h->ncell;
+    if (!alloc(&h->f1, fb) || !alloc(&h->f2, fb)) return bad(GKS_ENOMEM, "field allocation failed");
+    cudaMemset(h->f1, 0, fb);
+    cudaMemset(h->f2, 0, fb);
+  }
+  // widths with two ghosts per side: periodic axes wrap, other axes mirror
+  for (int d = 0; d < 3; ++d) {
+    const int n = d < D ? h->n[d] : 1;
+    std::vector<double> w(n + 4, 1.0), in(n, 1.0);
+    if (d < D) {
+      for (int i = 0; i < n; ++i) in[i] = grid->dx[d] ? grid->dx[d][i] : (grid->hi[d] - grid->lo[d]) / n;
+      const bool per = grid->bc[d][0] == GKS_BC_PERIODIC;
+      for (int i = 0; i < n; ++i) w[i + 2] = in[i];
+      for (int gi = 1; gi <= 2; ++gi) {
+        w[2 - gi] = per ? in[n - gi] : in[gi - 1];
+        w[n + 1 + gi] = per ? in[gi - 1] : in[n - gi];
+      }
+    }
+    if (!alloc((void**)&h->widths[d], sizeof(double) * (n + 4))) return bad(GKS_ENOMEM, "width allocation failed");
+    cudaMemcpy(h->widths[d], w.data(), sizeof(double) * (n + 4), cudaMemcpyHostToDevice);
+  }
+  // Dirichlet states, converted to conservative variables
+  for (int d = 0; d < D; ++d)
+    for (int s = 0; s < 2; ++s) {
+      if (grid->bc[d][s] != GKS_BC_DIRICHLET) continue;
+      long cnt = 1;
+      for (int b = 0; b < D; ++b)
+        if (b != d) cnt *= h->n[b];
+      std::vector<double> cons(cnt * h->nv);
+      for (long c = 0; c < cnt; ++c) {
+        const double* pr = grid->bc_data[d][s] + c * h->nv;
+        if (!(pr[0] > 0.0) || !(pr[D + 1] > 0.0)) return bad(GKS_EINVAL, "Dirichlet state must have rho, p > 0");
+        double q = 0.0;
+        cons[c * h->nv] = pr[0];
+        for (int i = 0; i < D; ++i) {
+          cons[c * h->nv + 1 + i] = pr[0] * pr[1 + i];
+          q += pr[1 + i] * pr[1 + i];
+        }
+        cons[c * h->nv + D + 1] = pr[D + 1] / (gas->gamma - 1.0) + 0.5 * pr[0] * q;
+      }
+      if (!alloc((void**)&h->dir[d][s], sizeof(double) * cons.size())) return bad(GKS_ENOMEM, "allocation failed");
+      cudaMemcpy(h->dir[d][s], cons.data(), sizeof(double) * cons.size(), cudaMemcpyHostToDevice);
+    }
+  if (cudaGetLastError() != cudaSuccess) return bad(GKS_ECUDA, "device set-up failed");
+
+  DevGrid& g = h->base.g;
+  std::memset(&h->base, 0, sizeof(h->base));
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = h->n[d];
+    g.w[d] = h->widths[d];
+    for (int s = 0; s < 2; ++s) {
+      g.bc[d][s] = d < D ? grid->bc[d][s] : GKS_BC_PERIODIC;
+      g.dir[d][s] = h->dir[d][s];
+    }
+  }
+  g.ncell = h->ncell;
+  g.gamma = gas->gamma;
+  g.bK = bK;
+  g.K = K;
+  g.mu = gas->mu;
+  g.T_wall = gas->T_wall;
+  g.C_a = turb ? turb->C_a : 0.0;
+  g.C_mu = turb ? turb->C_mu : 0.09;
+  g.beta_star = turb ? turb->beta_star : 0.09;
+  g.turb_model = model;
+  g.limiter = num->limiter;
+  g.abar_t0 = num->abar_mode == GKS_ABAR_T0;
+  h->base.f1 = h->f1;
+  h->base.f2 = h->f2;
+  h->base.ctrl = h->ctrl;
+  long tiles = 1;
+  const int T[3] = {D == 1 ? Tile<1>::X : (D == 2 ? Tile<2>::X : Tile<3>::X),
+                    D == 1 ? 1 : (D == 2 ? Tile<2>::Y : Tile<3>::Y), D == 3 ? Tile<3>::Z : 1};
+  for (int d = 0; d < 3; ++d) tiles *= (h->n[d] + T[d] - 1) / T[d];
+  h->nblocks = (int)tiles;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return bad(GKS_ECUDA, "device set-up failed");
+  }
+  *out = h;
+  return GKS_OK;
+}
+
+gks_status gks_destroy(gks_handle* h) {
+  if (!h) return GKS_EINVAL;
+  {
+    DeviceGuard dg(h->dev);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+  }
+  delete h;
+  return GKS_OK;
+}
+
+const char* gks_last_error(const gks_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace, int dtype) {
+  if (!h || !W) return fail(h, GKS_EINVAL, "null argument");
+  if (layout < GKS_LAYOUT_SOA_CONS || layout > GKS_LAYOUT_SOA_PRIM || (dtype != GKS_F64 && dtype != GKS_F32) ||
+      (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
+    return fail(h, GKS_EINVAL, "layout, memspace or dtype");
+  DeviceGuard dg(h->dev);
+  const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * h->nv * h->ncell;
+  const void* src = W;
+  if (memspace == GKS_MEM_HOST) {
+    gks_status s = ensure_staging(h, bytes);
+    if (s) return s;
+    GKS_CK(h, cudaMemcpyAsync(h->staging, W, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = h->staging;
+  }
+  h->step = 0;
+  GKS_CK(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+  const unsigned blocks = grid_for(h->ncell, 256);
+  if (dtype == GKS_F64)
+    state_in_kernel<double><<<blocks, 256, 0, h->stream>>>((const double*)src, layout, h->D, h->ncell,
+                                                          h->base.g.gamma, h->prec, h->W[0], h->Wlo[0]);
+  else
+    state_in_kernel<float><<<blocks, 256, 0, h->stream>>>((const float*)src, layout, h->D, h->ncell,
+                                                         h->base.g.gamma, h->prec, h->W[0], h->Wlo[0]);
+  GKS_CK(h, cudaGetLastError());
+  h->has_state = true;
+  return launch_rate(h);
+}
+
+gks_status gks_get_state(gks_handle* h, void* W_out, int layout, int memspace, int dtype) {
+  if (!h || !W_out) return fail(h, GKS_EINVAL, "null argument");
+  if (!h->has_state) return fail(h, GKS_EINVAL, "no state set");
+  if (layout < GKS_LAYOUT_SOA_CONS || layout > GKS_LAYOUT_SOA_PRIM || (dtype != GKS_F64 && dtype != GKS_F32) ||
+      (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
+    return fail(h, GKS_EINVAL, "layout, memspace or dtype");
+  DeviceGuard dg(h->dev);
+  const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * h->nv * h->ncell;
+  void* dst = W_out;
+  if (memspace == GKS_MEM_HOST) {
+    gks_status s = ensure_staging(h, bytes);
+    if (s) return s;
+    dst = h->staging;
+  }
+  const int cur = (int)(h->step & 1);
+  const unsigned blocks = grid_for(h->ncell, 256);
+  if (dtype == GKS_F64)
+    state_out_kernel<double><<<blocks, 256, 0, h->stream>>>((double*)dst, layout, h->D, h->ncell, h->base.g.gamma,
+                                                           h->prec, h->W[cur], h->Wlo[cur]);
+  else
+    state_out_kernel<float><<<blocks, 256, 0, h->stream>>>((float*)dst, layout, h->D, h->ncell, h->base.g.gamma,
+                                                          h->prec, h->W[cur], h->Wlo[cur]);
+  GKS_CK(h, cudaGetLastError());
+  if (memspace == GKS_MEM_HOST) {
+    GKS_CK(h, cudaMemcpyAsync(W_out, h->staging, bytes, cudaMemcpyDeviceToHost, h->stream));
+    GKS_CK(h, cudaStreamSynchronize(h->stream));
+    return sticky_status(h);
+  }
+  return GKS_OK;
+}
+
+gks_status gks_set_turbulence(gks_handle* h, const void* f1, const void* f2, int memspace, int dtype) {
+  if (!h || !f1) return fail(h, GKS_EINVAL, "null argument");
+  if (h->base.g.turb_model == GKS_TURB_NONE) return fail(h, GKS_EINVAL, "handle created without a turbulence model");
+  if (h->base.g.turb_model != GKS_TURB_MUT && !f2) return fail(h, GKS_EINVAL, "second turbulence field missing");
+  if ((dtype != GKS_F64 && dtype != GKS_F32) || (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
+    return fail(h, GKS_EINVAL, "memspace or dtype");
+  DeviceGuard dg(h->dev);
+  const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * h->ncell;
+  const void* srcs[2] = {f1, f2};
+  void* dsts[2] = {h->f1, h->f2};
+  for (int q = 0; q < 2; ++q) {
+    if (!srcs[q]) continue;
+    const void* src = srcs[q];
+    if (memspace == GKS_MEM_HOST) {
+      gks_status s = ensure_staging(h, bytes);
+      if (s) return s;
+      GKS_CK(h, cudaMemcpyAsync(h->staging, src, bytes, cudaMemcpyHostToDevice, h->stream));
+      src = h->staging;
+    }
+    const unsigned blocks = grid_for(h->ncell, 256);
+    const bool f64 = h->prec == PREC_F64;
+    if (dtype == GKS_F64 && f64)
+      field_kernel<double, double><<<blocks, 256, 0, h->stream>>>((const double*)src, (double*)dsts[q], h->ncell);
+    else if (dtype == GKS_F64)
+      field_kernel<double, float><<<blocks, 256, 0, h->stream>>>((const double*)src, (float*)dsts[q], h->ncell);
+    else if (f64)
+      field_kernel<float, double><<<blocks, 256, 0, h->stream>>>((const float*)src, (double*)dsts[q], h->ncell);
+    else
+      field_kernel<float, float><<<blocks, 256, 0, h->stream>>>((const float*)src, (float*)dsts[q], h->ncell);
+    GKS_CK(h, cudaGetLastError());
+    if (memspace == GKS_MEM_HOST) GKS_CK(h, cudaStreamSynchronize(h->stream));  // staging is reused
+  }
+  h->has_turb = true;
+  return GKS_OK;
+}
+
+gks_status gks_compute_dt(gks_handle* h, double cfl, double* dt_out) {
+  if (!h || !dt_out || !(cfl > 0.0)) return fail(h, GKS_EINVAL, "bad argument");
+  if (!h->has_state) return fail(h, GKS_EINVAL, "no state set");
+  DeviceGuard dg(h->dev);
+  unsigned long long bits = 0;
+  GKS_CK(h, cudaMemcpyAsync(&bits, &h->ctrl->rate[h->step % 3], sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  double r;
+  std::memcpy(&r, &bits, sizeof(r));
+  *dt_out = cfl / r;
+  return sticky_status(h);
+}
+
+gks_status gks_step(gks_handle* h, double dt, double cfl, int nsteps, double t_end) {
+  if (!h || nsteps < 0) return fail(h, GKS_EINVAL, "bad argument");
+  if (!h->has_state) return fail(h, GKS_EINVAL, "no state set");
+  if (!(dt > 0.0) && !(cfl > 0.0)) return fail(h, GKS_EINVAL, "need dt > 0 or cfl > 0");
+  if (h->base.g.turb_model != GKS_TURB_NONE && !h->has_turb) return fail(h, GKS_EINVAL, "turbulence fields not set");
+  if (nsteps == 0) return GKS_OK;
+  DeviceGuard dg(h->dev);
+  set_params_kernel<<<1, 1, 0, h->stream>>>(h->ctrl, dt > 0.0 ? dt : 0.0, cfl, t_end);
+  GKS_CK(h, cudaGetLastError());
+  int remaining = nsteps;
+  while (remaining > 0) {
+    if (!h->timing && remaining - 1 >= kGraphChunk && h->step % 6 == 0) {
+      auto it = h->graphs.find(kGraphChunk);
+      if (it == h->graphs.end()) {
+        cudaGraph_t graph;
+        GKS_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < kGraphChunk; ++k) launch_step(h, step_args(h, k, 0));
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiation");
+        it = h->graphs.emplace(kGraphChunk, exec).first;
+      }
+      GKS_CK(h, cudaGraphLaunch(it->second, h->stream));
+      h->step += kGraphChunk;
+      remaining -= kGraphChunk;
+      continue;
+    }
+    const StepArgs A = step_args(h, h->step, remaining == 1);
+    if (h->timing) {
+      cudaEvent_t e0, e1;
+      GKS_CK(h, cudaEventCreate(&e0));
+      GKS_CK(h, cudaEventCreate(&e1));
+      h->ev.push_back(e0);
+      h->ev.push_back(e1);
+      GKS_CK(h, cudaEventRecord(e0, h->stream));
+      launch_step(h, A);
+      GKS_CK(h, cudaEventRecord(e1, h->stream));
+    } else {
+      launch_step(h, A);
+    }
+    GKS_CK(h, cudaGetLastError());
+    h->step += 1;
+    remaining -= 1;
+  }
+  return GKS_OK;
+}
+
+gks_status gks_get_time(gks_handle* h, double* t, long long* steps) {
+  if (!h) return GKS_EINVAL;
+  DeviceGuard dg(h->dev);
+  double tv = 0.0;
+  GKS_CK(h, cudaMemcpyAsync(&tv, &h->ctrl->t[h->step & 1], sizeof(tv), cudaMemcpyDeviceToHost, h->stream));
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  if (t) *t = tv;
+  if (steps) *steps = h->step;
+  return GKS_OK;
+}
+
+gks_status gks_set_time(gks_handle* h, double t) {
+  if (!h) return GKS_EINVAL;
+  DeviceGuard dg(h->dev);
+  set_time_kernel<<<1, 1, 0, h->stream>>>(h->ctrl, (int)(h->step & 1), t);
+  GKS_CK(h, cudaGetLastError());
+  return GKS_OK;
+}
+
+gks_status gks_residual(gks_handle* h, double* l2, double* linf, double* total) {
+  if (!h) return GKS_EINVAL;
+  DeviceGuard dg(h->dev);
+  Ctrl c;
+  GKS_CK(h, cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  for (int v = 0; v < h->nv; ++v) {
+    if (l2) l2[v] = std::sqrt(c.l2[v] / (double)h->ncell);
+    if (linf) std::memcpy(&linf[v], &c.linf[v], sizeof(double));
+    if (total) total[v] = c.total[v];
+  }
+  if (c.status & 1u) return fail(h, GKS_ENONPHYS, "non-physical state (rho <= 0 or p <= 0) produced");
+  return GKS_OK;
+}
+
+gks_status gks_status_word(gks_handle* h, unsigned int* bits, double* last_dt) {
+  if (!h) return GKS_EINVAL;
+  DeviceGuard dg(h->dev);
+  Ctrl c;
+  GKS_CK(h, cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  if (bits) *bits = c.status;
+  if (last_dt) *last_dt = c.last_dt;
+  return GKS_OK;
+}
+
+static gks_status get_diag(gks_handle* h, int what, void* out, int memspace, int dtype) {
+  if (!h || !out) return fail(h, GKS_EINVAL, "null argument");
+  if (!h->has_state) return fail(h, GKS_EINVAL, "no state set");
+  if (h->base.g.turb_model != GKS_TURB_NONE && !h->has_turb) return fail(h, GKS_EINVAL, "turbulence fields not set");
+  if ((dtype != GKS_F64 && dtype != GKS_F32) || (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
+    return fail(h, GKS_EINVAL, "memspace or dtype");
+  DeviceGuard dg(h->dev);
+  const size_t bytes = (dtype == GKS_F64 ? 8 : 4) * h->ncell;
+  void* dst = out;
+  if (memspace == GKS_MEM_HOST) {
+    gks_status s = ensure_staging(h, bytes);
+    if (s) return s;
+    dst = h->staging;
+  }
+  const StepArgs A = step_args(h, h->step, 0);
+  if (h->D == 1)
+    launch_diag_d<1>(h, A, what, dst, dtype);
+  else if (h->D == 2)
+    launch_diag_d<2>(h, A, what, dst, dtype);
+  else
+    launch_diag_d<3>(h, A, what, dst, dtype);
+  GKS_CK(h, cudaGetLastError());
+  if (memspace == GKS_MEM_HOST) {
+    GKS_CK(h, cudaMemcpyAsync(out, h->staging, bytes, cudaMemcpyDeviceToHost, h->stream));
+    GKS_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return GKS_OK;
+}
+
+gks_status gks_get_rarefaction(gks_handle* h, void* eps_out, int memspace, int dtype) {
+  return get_diag(h, 1, eps_out, memspace, dtype);
+}
+
+gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtype) {
+  return get_diag(h, 0, tau_out, memspace, dtype);
+}
+
+gks_status gks_enable_timing(gks_handle* h, int enable) {
+  if (!h) return GKS_EINVAL;
+  h->timing = enable != 0;
+  return GKS_OK;
+}
+
+gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches) {
+  if (!h) return GKS_EINVAL;
+  DeviceGuard dg(h->dev);
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i + 1 < h->ev.size(); i += 2) {
+    float ms = 0.0f;
+    GKS_CK(h, cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+    h->ms_total += ms;
+    h->launches += 1;
+  }
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+  if (ms_total) *ms_total = h->ms_total;
+  if (launches) *launches = h->launches;
+  h->ms_total = 0.0;
+  h->launches = 0;
+  return GKS_OK;
+}
+
+int gks_face_record_len(int dim) {
+  if (dim < 1 || dim > 3) return -1;
+  const int nv = dim + 2;
+  return 6 * nv + 2 * (dim - 1) * nv + 3;
+}
+
+gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, double gamma, double mu, double C_a,
+                         double dt, const double* faces, long nfaces, double* F_out, double* tau_out,
+                         void* cuda_stream) {
+  if (dim < 1 || dim > 3 || !faces || !F_out || nfaces < 0) return GKS_EINVAL;
+  if (precision != GKS_FP64 && precision != GKS_FP32) return GKS_EINVAL;
+  if (!(gamma > 1.0) || 2.0 / (gamma - 1.0) - dim < 0.0 || !(dt > 0.0)) return GKS_EINVAL;
+  if (nfaces == 0) return GKS_OK;
+  launch_face_flux(dim, precision == GKS_FP64 ? 0 : 1, dim > 1 && expand == GKS_EXPAND_MULTID,
+                   abar_mode == GKS_ABAR_T0, gamma, mu, C_a, dt, faces, nfaces, F_out, tau_out,
+                   (cudaStream_t)cuda_stream);
+  if (cudaGetLastError() != cudaSuccess) return GKS_ECUDA;
+  return GKS_OK;
+}
+
+}  // extern "C"

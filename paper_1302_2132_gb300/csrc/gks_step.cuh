@@ -1,0 +1,605 @@
+// Fused time step of the gas-kinetic finite-volume scheme on a structured grid.
+//
+// One launch advances the whole grid by one step.  Each CTA owns a tile of cells; it stages the
+// tile with two halo layers in shared memory (boundary cells are resolved while loading: periodic,
+// transmissive/outflow, isothermal no-slip wall, Dirichlet), computes the turbulent relaxation
+// time of the tile and its first halo ring (Eqs. tautchen, tautchenadjusted, tauttrivial), the
+// MUSCL-reconstructed face states and the time-integrated flux of every face of the tile
+// (Eq. fluxesf), then updates its cells W <- W - sum_d dF_d / dx_d and folds the CFL rate of the
+// new state into the control block for the next step.  Faces on a tile border are evaluated by
+// both neighbouring tiles (same inputs, same result), so no flux leaves the CTA.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gks_flux.cuh"
+
+namespace gks {
+
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_WALL = 2, BC_DIRICHLET = 3, BC_OUTFLOW = 4 };
+enum { TURB_NONE = 0, TURB_MUT = 1, TURB_KEPS = 2, TURB_KOMEGA = 3 };
+// arithmetic / storage of a run
+enum { PREC_F64 = 0,    // double flux, double state
+       PREC_F32 = 1,    // float flux, state as a pair of floats (hi + lo)
+       PREC_F32D = 2 };  // float flux, double state
+
+constexpr int kThreads = 256;
+
+template <int D> struct Tile;
+template <> struct Tile<1> { static constexpr int X = 256, Y = 1, Z = 1; };
+template <> struct Tile<2> { static constexpr int X = 32, Y = 16, Z = 1; };
+template <> struct Tile<3> { static constexpr int X = 16, Y = 8, Z = 4; };
+
+template <int D> struct TileGeom {
+  static constexpr int X = Tile<D>::X, Y = Tile<D>::Y, Z = Tile<D>::Z;
+  static constexpr int HX = X + 4, HY = D >= 2 ? Y + 4 : 1, HZ = D >= 3 ? Z + 4 : 1;
+  static constexpr int NH = HX * HY * HZ;  // cells with halo
+  static constexpr int RX = X + 2, RY = D >= 2 ? Y + 2 : 1, RZ = D >= 3 ? Z + 2 : 1;
+  static constexpr int NR = RX * RY * RZ;  // cells with the first halo ring
+  static constexpr int NC = X * Y * Z;
+  static constexpr int NFX = (X + 1) * Y * Z;
+  static constexpr int NFY = D >= 2 ? X * (Y + 1) * Z : 0;
+  static constexpr int NFZ = D >= 3 ? X * Y * (Z + 1) : 0;
+  static constexpr int NF = NFX + NFY + NFZ;
+  static constexpr int nv = D + 2;
+  template <class R> static constexpr size_t smem_bytes() {
+    return sizeof(R) * ((size_t)nv * NH + NR + (size_t)nv * NF + HX + HY + HZ);
+  }
+};
+
+struct Ctrl {
+  unsigned long long rate[3];  // bits of a non-negative double: max_cells sum_d (|U_d| + c)/dx_d
+  double t[2];
+  double dt_fixed, cfl, t_end;
+  double last_dt;
+  unsigned int status;  // bit 0: non-physical state after an update
+  unsigned int pad;
+  double l2[5], total[5];
+  unsigned long long linf[5];
+};
+
+struct DevGrid {
+  int n[3];
+  long ncell;
+  int bc[3][2];
+  const double* w[3];       // cell widths with two ghosts per side, index i + 2
+  const double* dir[3][2];  // Dirichlet conservative states, [transverse cell][nv]
+  double gamma, bK, K, mu, C_a, T_wall, C_mu, beta_star;
+  int turb_model, limiter, abar_t0;
+};
+
+struct StepArgs {
+  DevGrid g;
+  const void* Win;
+  void* Wout;
+  const float* Win_lo;  // PREC_F32 only
+  float* Wout_lo;
+  const void* f1;  // turbulence fields in the arithmetic type, or null
+  const void* f2;
+  Ctrl* ctrl;
+  int slot;    // rate slot read by this step (step index mod 3)
+  int tslot;   // time slot read by this step (step index mod 2)
+  int resid;   // accumulate residual norms in this step
+};
+
+template <int PREC> struct PrecT;
+template <> struct PrecT<PREC_F64> { using R = double; using S = double; };
+template <> struct PrecT<PREC_F32> { using R = float; using S = float; };
+template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
+
+__device__ __forceinline__ long cell_index(const DevGrid& g, int i, int j, int k) {
+  return ((long)k * g.n[1] + j) * g.n[0] + i;
+}
+
+template <class R>
+__device__ __forceinline__ R pressure_of(int D, R gamma, const R* w) {
+  R q = R(0);
+  for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
+  return (gamma - R(1)) * (w[D + 1] - R(0.5) * q / w[0]);
+}
+
+// Isothermal no-slip wall image: velocity reversed, same pressure, T_g = T_w^2 / T_i (T = p/rho).
+template <int D, class R>
+__device__ __forceinline__ void wall_image(const DevGrid& g, R* w) {
+  const R gamma = (R)g.gamma, Tw = (R)g.T_wall;
+  R U[D], q = R(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) U[i] = w[1 + i] / w[0];
+  const R p = pressure_of<R>(D, gamma, w);
+  const R Ti = p / w[0];
+  const R Tg = Tw * Tw / Ti;
+  const R rho = p / Tg;
+  w[0] = rho;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    w[1 + i] = rho * -U[i];
+    q += U[i] * U[i];
+  }
+  w[D + 1] = p / (gamma - R(1)) + R(0.5) * rho * q;
+}
+
+template <int D, int PREC>
+__device__ __forceinline__ void load_stored(const StepArgs& A, long c, typename PrecT<PREC>::R* out) {
+  using S = typename PrecT<PREC>::S;
+  using R = typename PrecT<PREC>::R;
+  const S* W = (const S*)A.Win;
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) out[v] = (R)W[(long)v * A.g.ncell + c];
+}
+
+// State of cell (i, j, k), possibly outside the grid: ghost cells follow the boundary rules, the
+// transform of the last axis applied first.
+template <int D, int PREC>
+__device__ void load_cell(const StepArgs& A, int i, int j, int k, typename PrecT<PREC>::R* out) {
+  using R = typename PrecT<PREC>::R;
+  const DevGrid& g = A.g;
+  int c[3] = {i, j, k}, xf[3] = {0, 0, 0}, side[3] = {0, 0, 0};
+  bool inside = true;
+  // cells further out than the two ghost layers only feed faces of cells outside the grid
+#pragma unroll
+  for (int a = 0; a < D; ++a) c[a] = min(max(c[a], -2), g.n[a] + 1);
+  int src[3] = {c[0], c[1], c[2]};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int n = g.n[a];
+    if (c[a] < 0 || c[a] >= n) {
+      inside = false;
+      const int s = c[a] < 0 ? 0 : 1;
+      side[a] = s;
+      const int bc = g.bc[a][s];
+      if (bc == BC_PERIODIC) {
+        src[a] = s == 0 ? c[a] + n : c[a] - n;
+      } else if (bc == BC_WALL) {
+        src[a] = s == 0 ? -c[a] - 1 : 2 * n - 1 - c[a];
+        xf[a] = 1;
+      } else if (bc == BC_DIRICHLET) {
+        src[a] = s == 0 ? 0 : n - 1;
+        xf[a] = 2;
+      } else {
+        src[a] = s == 0 ? 0 : n - 1;
+      }
+    }
+  }
+  load_stored<D, PREC>(A, cell_index(g, src[0], src[1], src[2]), out);
+  if (inside) return;
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) {
+    if (xf[a] == 1) {
+      wall_image<D, R>(g, out);
+    } else if (xf[a] == 2) {
+      long off = 0, stride = 1;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        if (b == a) continue;
+        int cb = b < a ? src[b] : min(max(c[b], 0), g.n[b] - 1);
+        off += cb * stride;
+        stride *= g.n[b];
+      }
+      const double* d = g.dir[a][side[a]] + off * (D + 2);
+#pragma unroll
+      for (int v = 0; v < D + 2; ++v) out[v] = (R)d[v];
+    }
+  }
+}
+
+template <class R>
+__device__ __forceinline__ R load_field(const StepArgs& A, const void* f, int D, int i, int j, int k) {
+  const DevGrid& g = A.g;
+  int c[3] = {i, j, k};
+  for (int a = 0; a < D; ++a) {
+    const int n = g.n[a];
+    if (c[a] < 0 || c[a] >= n) {
+      if (g.bc[a][0] == BC_PERIODIC)
+        c[a] = (c[a] + n) % n;
+      else
+        c[a] = min(max(c[a], 0), n - 1);
+    }
+  }
+  return ((const R*)f)[cell_index(g, c[0], c[1], c[2])];
+}
+
+// Turbulent part of the relaxation time of one cell (Eqs. tauttrivial, tautchen, tautchenadjusted
+// with T = p/rho); S = sqrt(2 S_ij S_ij) from central differences of the velocity.
+template <int D, class R>
+__device__ __forceinline__ R tau_turb_cell(const DevGrid& g, const R* Ws, int stride_v, int idx,
+                                           const int* strides, const R* const* widths, const int* pos,
+                                           R f1, R f2) {
+  if (g.turb_model == TURB_NONE) return R(0);
+  R w[D + 2];
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) w[v] = Ws[v * stride_v + idx];
+  const R p = pressure_of<R>(D, (R)g.gamma, w);
+  if (g.turb_model == TURB_MUT) return f1 / p;
+  if (!(f1 > R(0)) || !(f2 > R(0))) return R(0);
+  R grad[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int im = idx - strides[a], ip = idx + strides[a];
+    const R* wd = widths[a];
+    const R dist = R(0.5) * wd[pos[a] - 1] + wd[pos[a]] + R(0.5) * wd[pos[a] + 1];
+    const R rm = Ws[im], rp = Ws[ip];
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      grad[a][b] = (Ws[(1 + b) * stride_v + ip] / rp - Ws[(1 + b) * stride_v + im] / rm) / dist;
+  }
+  R s2 = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const R sab = R(0.5) * (grad[a][b] + grad[b][a]);
+      s2 += sab * sab;
+    }
+  const R S = g_sqrt(R(2) * s2);
+  R nu, eta;
+  if (g.turb_model == TURB_KEPS) {
+    nu = (R)g.C_mu * f1 * f1 / f2;
+    eta = S * f1 / f2;
+  } else {
+    nu = f1 / f2;
+    eta = S / ((R)g.beta_star * f2);
+  }
+  return w[0] * nu / (p * g_sqrt(R(1) + eta * eta));
+}
+
+__device__ __forceinline__ double step_dt(const StepArgs& A) {
+  const Ctrl* c = A.ctrl;
+  double dt = c->dt_fixed;
+  if (!(dt > 0.0)) dt = c->cfl / __longlong_as_double((long long)c->rate[A.slot]);
+  if (c->t_end > 0.0) {
+    const double t = c->t[A.tslot];
+    dt = (t >= c->t_end) ? 0.0 : fmin(dt, c->t_end - t);
+  }
+  return dt;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <class R>
+__device__ __forceinline__ R block_max(R v, R* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (kThreads / 32) ? red[lane] : R(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (kThreads / 32) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// CFL rate of one cell: sum_d (|U_d| + c) / dx_d, c = sqrt(gamma p / rho).
+template <int D, class R>
+__device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
+  const R p = pressure_of<R>(D, gamma, w);
+  const R cs = g_sqrt(gamma * p / w[0]);
+  R r = R(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) r += (g_abs(w[1 + d] / w[0]) + cs) / h[d];
+  return r;
+}
+
+template <int D, int PREC, bool MULTID>
+__global__ void __launch_bounds__(kThreads, 1)
+    step_kernel(const __grid_constant__ StepArgs A) {
+  using R = typename PrecT<PREC>::R;
+  using S = typename PrecT<PREC>::S;
+  using G = TileGeom<D>;
+  constexpr int nv = D + 2;
+  constexpr int X = G::X, Y = G::Y, Z = G::Z, HX = G::HX, HY = G::HY, HZ = G::HZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* Ws = (R*)smem_raw;                    // [nv][HZ][HY][HX]
+  R* taus = Ws + (size_t)nv * G::NH;       // [RZ][RY][RX]
+  R* Fs = taus + G::NR;                    // [nv][NF]
+  R* wsx = Fs + (size_t)nv * G::NF;        // widths with halo
+  R* wsy = wsx + HX;
+  R* wsz = wsy + HY;
+  __shared__ double red[kThreads / 32];
+
+  const DevGrid& g = A.g;
+  const int tiles_x = (g.n[0] + X - 1) / X;
+  const int tiles_y = D >= 2 ? (g.n[1] + Y - 1) / Y : 1;
+  const int b = blockIdx.x;
+  const int ox = (b % tiles_x) * X;
+  const int oy = D >= 2 ? ((b / tiles_x) % tiles_y) * Y : 0;
+  const int oz = D >= 3 ? (b / (tiles_x * tiles_y)) * Z : 0;
+  const int tid = threadIdx.x;
+
+  const double dt_d = step_dt(A);
+  if (tid == 0 && b == 0) {
+    Ctrl* c = A.ctrl;
+    c->t[A.tslot ^ 1] = c->t[A.tslot] + dt_d;
+    c->rate[(A.slot + 2) % 3] = 0ull;
+    c->last_dt = dt_d;
+  }
+  if (dt_d == 0.0) {  // t_end reached: carry the state over
+    for (int l = tid; l < G::NC; l += kThreads) {
+      const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
+      const int gi = ox + li, gj = oy + lj, gk = oz + lk;
+      if (gi >= g.n[0] || (D >= 2 && gj >= g.n[1]) || (D >= 3 && gk >= g.n[2])) continue;
+      const long c = cell_index(g, gi, gj, gk);
+      for (int v = 0; v < nv; ++v) {
+        ((S*)A.Wout)[(long)v * g.ncell + c] = ((const S*)A.Win)[(long)v * g.ncell + c];
+        if (PREC == PREC_F32) A.Wout_lo[(long)v * g.ncell + c] = A.Win_lo[(long)v * g.ncell + c];
+      }
+    }
+    return;
+  }
+  const R dt = (R)dt_d;
+
+  // ---- stage the tile with two halo layers -------------------------------------------------
+  for (int l = tid; l < G::NH; l += kThreads) {
+    const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
+    R w[nv];
+    load_cell<D, PREC>(A, ox + hi - 2, D >= 2 ? oy + hj - 2 : 0, D >= 3 ? oz + hk - 2 : 0, w);
+#pragma unroll
+    for (int v = 0; v < nv; ++v) Ws[v * G::NH + l] = w[v];
+  }
+  for (int l = tid; l < HX + HY + HZ; l += kThreads) {
+    // padded width index (cell + 2), clamped to the two ghost layers
+    if (l < HX)
+      wsx[l] = (R)g.w[0][min(ox + l, g.n[0] + 3)];
+    else if (l < HX + HY)
+      wsy[l - HX] = D >= 2 ? (R)g.w[1][min(oy + (l - HX), g.n[1] + 3)] : R(1);
+    else
+      wsz[l - HX - HY] = D >= 3 ? (R)g.w[2][min(oz + (l - HX - HY), g.n[2] + 3)] : R(1);
+  }
+  __syncthreads();
+
+  // ---- turbulent relaxation time on the tile and its first halo ring --------------------------
+  {
+    const int strides[3] = {1, HX, HX * HY};
+    const R* widths[3] = {wsx, wsy, wsz};
+    for (int l = tid; l < G::NR; l += kThreads) {
+      const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
+      const int hi = ri + 1, hj = D >= 2 ? rj + 1 : 0, hk = D >= 3 ? rk + 1 : 0;
+      const int idx = (hk * HY + hj) * HX + hi;
+      R f1 = R(0), f2 = R(0);
+      const int gi = ox + ri - 1, gj = D >= 2 ? oy + rj - 1 : 0, gk = D >= 3 ? oz + rk - 1 : 0;
+      if (g.turb_model != TURB_NONE) {
+        f1 = load_field<R>(A, A.f1, D, gi, gj, gk);
+        if (g.turb_model != TURB_MUT) f2 = load_field<R>(A, A.f2, D, gi, gj, gk);
+      }
+      const int pos[3] = {hi, hj, hk};
+      taus[l] = tau_turb_cell<D, R>(g, Ws, G::NH, idx, strides, widths, pos, f1, f2);
+    }
+  }
+  __syncthreads();
+
+  // ---- fluxes of every face of the tile ----------------------------------------------------
+  {
+    Gas<R> gas;
+    gas.bK = (R)g.bK;
+    gas.K = (R)g.K;
+    gas.mu = (R)g.mu;
+    gas.C_a = (R)g.C_a;
+    const R gamma = (R)g.gamma;
+    for (int f = tid; f < G::NF; f += kThreads) {
+      int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
+      if (f < G::NFX) {
+        ax = 0;
+        ci = f % (X + 1);
+        cj = (f / (X + 1)) % Y;
+        ck = f / ((X + 1) * Y);
+      } else if (D >= 2 && f < G::NFX + G::NFY) {
+        const int q = f - G::NFX;
+        ax = 1;
+        ci = q % X;
+        cj = (q / X) % (Y + 1);
+        ck = q / (X * (Y + 1));
+      } else {
+        const int q = f - G::NFX - G::NFY;
+        ax = 2;
+        ci = q % X;
+        cj = (q / X) % Y;
+        ck = q / (X * Y);
+      }
+      const int st[3] = {1, HX, HX * HY};
+      const int sn = st[ax];
+      const int hc = ((ck + (D >= 3 ? 2 : 0)) * HY + (cj + (D >= 2 ? 2 : 0))) * HX + (ci + 2);
+      // velocity order in the face frame: normal first, then tangential axes
+      int perm[3];
+      perm[0] = ax;
+      if (D == 2) perm[1] = 1 - ax;
+      if (D == 3) {
+        perm[1] = ax == 0 ? 1 : 0;
+        perm[2] = ax == 2 ? 1 : 2;
+      }
+      const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
+      const int pn = ax == 0 ? ci + 2 : (ax == 1 ? cj + 2 : ck + 2);  // halo coordinate of cell c
+      const R h0 = wn[pn - 2], h1 = wn[pn - 1], h2 = wn[pn], h3 = wn[pn + 1];
+      R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv];
+#pragma unroll
+      for (int v = 0; v < nv; ++v) {
+        const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+        const R* p = Ws + sv * G::NH + hc;
+        const R s1 = p[-sn], s2 = p[0];
+        muscl<R>(g.limiter, p[-2 * sn], s1, s2, p[sn], h0, h1, h2, h3, wl[v], wr[v], sl[v], sr[v]);
+        cl[v] = s1;
+        cr[v] = s2;
+      }
+      if (!(wl[0] > R(0)) || !(pressure_of<R>(D, gamma, wl) > R(0))) {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) {
+          wl[v] = cl[v];
+          sl[v] = R(0);
+        }
+      }
+      if (!(wr[0] > R(0)) || !(pressure_of<R>(D, gamma, wr) > R(0))) {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) {
+          wr[v] = cr[v];
+          sr[v] = R(0);
+        }
+      }
+      R tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
+      if (MULTID) {
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) {
+          const int ta = perm[1 + s];
+          const int stt = st[ta];
+          const R* wt = ta == 0 ? wsx : (ta == 1 ? wsy : wsz);
+          const int hcell[3] = {ci + 2, cj + (D >= 2 ? 2 : 0), ck + (D >= 3 ? 2 : 0)};
+          const int pt = hcell[ta];
+          const R hm = R(0.5) * (wt[pt - 1] + wt[pt]);
+          const R hp = R(0.5) * (wt[pt] + wt[pt + 1]);
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+            const R* pc = Ws + sv * G::NH + hc;
+            const R* pl = pc - sn;
+            tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) / hm, (pl[stt] - pl[0]) / hp);
+            tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) / hm, (pc[stt] - pc[0]) / hp);
+          }
+        }
+      }
+      // relaxation-time ring index of the two cells
+      const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
+      const int rst[3] = {1, G::RX, G::RX * G::RY};
+      const R tau_t = R(0.5) * (taus[rc - rst[ax]] + taus[rc]);
+      R F[nv], tau;
+      face_flux<D, R, MULTID>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
+                              g.abar_t0, F, &tau);
+      Fs[0 * G::NF + f] = F[0];
+#pragma unroll
+      for (int k = 0; k < D; ++k) Fs[(1 + perm[k]) * G::NF + f] = F[1 + k];
+      Fs[(D + 1) * G::NF + f] = F[D + 1];
+    }
+  }
+  __syncthreads();
+
+  // ---- conservative update, CFL rate of the new state, residual norms --------------------------
+  R rmax = R(0);
+  double racc[3 * 5];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) racc[q] = 0.0;
+  unsigned int bad = 0;
+  for (int l = tid; l < G::NC; l += kThreads) {
+    const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
+    const int gi = ox + li, gj = oy + lj, gk = oz + lk;
+    if (gi >= g.n[0] || (D >= 2 && gj >= g.n[1]) || (D >= 3 && gk >= g.n[2])) continue;
+    const long c = cell_index(g, gi, gj, gk);
+    // faces below/above the cell along each axis
+    int fm[3], fp[3];
+    R h[3];
+    fm[0] = (lk * Y + lj) * (X + 1) + li;
+    fp[0] = fm[0] + 1;
+    h[0] = wsx[li + 2];
+    if (D >= 2) {
+      fm[1] = G::NFX + (lk * (Y + 1) + lj) * X + li;
+      fp[1] = fm[1] + X;
+      h[1] = wsy[lj + 2];
+    }
+    if (D >= 3) {
+      fm[2] = G::NFX + G::NFY + (lk * Y + lj) * X + li;
+      fp[2] = fm[2] + X * Y;
+      h[2] = wsz[lk + 2];
+    }
+    R wn[nv];
+    double vol = 1.0;
+    if (A.resid) {  // cell volume from the double-precision widths
+      const int gc[3] = {gi, gj, gk};
+      for (int d = 0; d < D; ++d) vol *= g.w[d][gc[d] + 2];
+    }
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+      const long gidx = (long)v * g.ncell + c;
+      if (PREC == PREC_F64) {
+        double w = ((const double*)A.Win)[gidx];
+        const double w_old = w;
+#pragma unroll
+        for (int d = 0; d < D; ++d) w -= ((double)Fs[v * G::NF + fp[d]] - (double)Fs[v * G::NF + fm[d]]) / (double)h[d];
+        ((double*)A.Wout)[gidx] = w;
+        wn[v] = (R)w;
+        if (A.resid) {
+          const double r = (w - w_old) / dt_d;
+          racc[v] += r * r;
+          racc[5 + v] = fmax(racc[5 + v], fabs(r));
+          racc[10 + v] += w * vol;
+        }
+      } else {
+        R inc = R(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) inc -= (Fs[v * G::NF + fp[d]] - Fs[v * G::NF + fm[d]]) / h[d];
+        double wd;
+        if (PREC == PREC_F32) {
+          // (hi, lo) += inc with an error-free sum, then renormalise
+          const float hi = ((const float*)A.Win)[gidx], lo = A.Win_lo[gidx];
+          const float s = hi + inc;
+          const float bb = s - hi;
+          const float err = (hi - (s - bb)) + (inc - bb);
+          const float lo2 = lo + err;
+          const float nhi = s + lo2;
+          const float nlo = lo2 - (nhi - s);
+          ((float*)A.Wout)[gidx] = nhi;
+          A.Wout_lo[gidx] = nlo;
+          wn[v] = nhi;
+          wd = (double)nhi + (double)nlo;
+        } else {
+          const double w = ((const double*)A.Win)[gidx] + (double)inc;
+          ((double*)A.Wout)[gidx] = w;
+          wn[v] = (R)w;
+          wd = w;
+        }
+        if (A.resid) {
+          const double r = (double)inc / dt_d;
+          racc[v] += r * r;
+          racc[5 + v] = fmax(racc[5 + v], fabs(r));
+          racc[10 + v] += wd * vol;
+        }
+      }
+    }
+    const R p = pressure_of<R>(D, (R)g.gamma, wn);
+    if (!(wn[0] > R(0)) || !(p > R(0))) bad = 1u;
+    rmax = fmax(rmax, cell_rate<D, R>(wn, (R)g.gamma, h));
+  }
+  const double bmax = block_max<double>((double)rmax, red);
+  if (tid == 0) atomic_max_nonneg(&A.ctrl->rate[(A.slot + 1) % 3], bmax);
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(&A.ctrl->status, 1u);
+  if (A.resid) {
+    for (int v = 0; v < nv; ++v) {
+      double s = block_sum(racc[v], red);
+      if (tid == 0) atomicAdd(&A.ctrl->l2[v], s);
+      s = block_sum(racc[10 + v], red);
+      if (tid == 0) atomicAdd(&A.ctrl->total[v], s);
+      const double m = block_max<double>(racc[5 + v], red);
+      if (tid == 0) atomic_max_nonneg(&A.ctrl->linf[v], m);
+    }
+  }
+}
+
+template <int D, int PREC, bool MULTID>
+void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
+  using R = typename PrecT<PREC>::R;
+  const size_t sm = TileGeom<D>::template smem_bytes<R>();
+  step_kernel<D, PREC, MULTID><<<nblocks, kThreads, sm, s>>>(A);
+}
+
+template <int D, int PREC, bool MULTID>
+cudaError_t prepare_step() {
+  using R = typename PrecT<PREC>::R;
+  const size_t sm = TileGeom<D>::template smem_bytes<R>();
+  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sm);
+}
+
+}  // namespace gks

@@ -1,0 +1,26 @@
+// Instantiations of the fused step kernel for dimension 1.
+#include "gks_dispatch.h"
+#include "gks_step.cuh"
+
+namespace gks {
+
+cudaError_t prepare_step_d1() {
+  cudaError_t e = cudaSuccess;
+  cudaError_t r;
+#define GKS_PREP(P, M) if ((r = prepare_step<1, P, M>()) != cudaSuccess) e = r;
+  GKS_PREP(PREC_F64, false)
+  GKS_PREP(PREC_F32, false)
+  GKS_PREP(PREC_F32D, false)
+
+#undef GKS_PREP
+  return e;
+}
+
+void launch_step_d1(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
+
+  if (prec == PREC_F64) launch_step<1, PREC_F64, false>(A, nblocks, s);
+  else if (prec == PREC_F32) launch_step<1, PREC_F32, false>(A, nblocks, s);
+  else launch_step<1, PREC_F32D, false>(A, nblocks, s);
+}
+
+}  // namespace gks

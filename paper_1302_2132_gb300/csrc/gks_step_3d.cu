@@ -1,0 +1,33 @@
+// Instantiations of the fused step kernel for dimension 3.
+#include "gks_dispatch.h"
+#include "gks_step.cuh"
+
+namespace gks {
+
+cudaError_t prepare_step_d3() {
+  cudaError_t e = cudaSuccess;
+  cudaError_t r;
+#define GKS_PREP(P, M) if ((r = prepare_step<3, P, M>()) != cudaSuccess) e = r;
+  GKS_PREP(PREC_F64, false)
+  GKS_PREP(PREC_F32, false)
+  GKS_PREP(PREC_F32D, false)
+  GKS_PREP(PREC_F64, true)
+  GKS_PREP(PREC_F32, true)
+  GKS_PREP(PREC_F32D, true)
+#undef GKS_PREP
+  return e;
+}
+
+void launch_step_d3(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
+  if (multid) {
+    if (prec == PREC_F64) launch_step<3, PREC_F64, true>(A, nblocks, s);
+    else if (prec == PREC_F32) launch_step<3, PREC_F32, true>(A, nblocks, s);
+    else launch_step<3, PREC_F32D, true>(A, nblocks, s);
+    return;
+  }
+  if (prec == PREC_F64) launch_step<3, PREC_F64, false>(A, nblocks, s);
+  else if (prec == PREC_F32) launch_step<3, PREC_F32, false>(A, nblocks, s);
+  else launch_step<3, PREC_F32D, false>(A, nblocks, s);
+}
+
+}  // namespace gks

@@ -1,0 +1,292 @@
+"""ctypes binding of libgks.so (C ABI in include/gks.h): argument marshalling only.
+
+Every step of the scheme runs in the library's CUDA kernels; this module converts Python/torch
+arguments into the C structures and pointers.  PyTorch provides device memory for the caller's
+tensors and the CUDA stream the library works on.  If the library cannot be loaded the import
+fails: there is no other implementation behind this module.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgks.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT, EUNSUPPORTED = range(7)
+BC = {"periodic": 0, "transmissive": 1, "wall": 2, "dirichlet": 3, "outflow": 4}
+TURB = {"none": 0, "mut": 1, "keps": 2, "komega": 3}
+LIMITER = {"minmod": 0, "vanleer": 1}
+EXPAND = {"directional": 0, "multid": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
+ABAR = {"timeint": 0, "t0": 1}
+LAYOUT = {"soa_cons": 0, "aos_cons": 1, "soa_prim": 2}
+MEM_HOST, MEM_DEVICE = 0, 1
+F64, F32 = 0, 1
+
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+_V = ctypes.c_void_p
+
+
+class GksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gks error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", _I), ("n", _I * 3), ("lo", _D * 3), ("hi", _D * 3), ("dx", _PD * 3),
+                ("bc", (_I * 2) * 3), ("bc_data", (_PD * 2) * 3)]
+
+
+class _Gas(ctypes.Structure):
+    _fields_ = [("gamma", _D), ("mu", _D), ("prandtl", _D), ("T_wall", _D)]
+
+
+class _Turb(ctypes.Structure):
+    _fields_ = [("model", _I), ("C_mu", _D), ("beta_star", _D), ("C_a", _D)]
+
+
+class _Num(ctypes.Structure):
+    _fields_ = [("limiter", _I), ("expand", _I), ("precision", _I), ("abar_mode", _I)]
+
+
+_lib = None
+
+
+def load():
+    """Load libgks.so (built in-tree by paper_1302_2132_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgks.so not built: run paper_1302_2132_gb300.build.build() first (%s)" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    H = _V
+    L.gks_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Gas), ctypes.POINTER(_Turb),
+                             ctypes.POINTER(_Num), _V, ctypes.POINTER(H)]
+    L.gks_set_state.argtypes = [H, _V, _I, _I, _I]
+    L.gks_get_state.argtypes = [H, _V, _I, _I, _I]
+    L.gks_set_turbulence.argtypes = [H, _V, _V, _I, _I]
+    L.gks_compute_dt.argtypes = [H, _D, _PD]
+    L.gks_step.argtypes = [H, _D, _D, _I, _D]
+    L.gks_get_time.argtypes = [H, _PD, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_set_time.argtypes = [H, _D]
+    L.gks_residual.argtypes = [H, _PD, _PD, _PD]
+    L.gks_status_word.argtypes = [H, ctypes.POINTER(ctypes.c_uint), _PD]
+    L.gks_get_rarefaction.argtypes = [H, _V, _I, _I]
+    L.gks_get_tau_turb.argtypes = [H, _V, _I, _I]
+    L.gks_enable_timing.argtypes = [H, _I]
+    L.gks_kernel_time.argtypes = [H, _PD, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_destroy.argtypes = [H]
+    L.gks_last_error.argtypes = [H]
+    L.gks_last_error.restype = ctypes.c_char_p
+    L.gks_face_record_len.argtypes = [_I]
+    L.gks_face_flux.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _V, ctypes.c_long, _V, _V, _V]
+    for name in ("gks_create", "gks_set_state", "gks_get_state", "gks_set_turbulence", "gks_compute_dt",
+                 "gks_step", "gks_get_time", "gks_set_time", "gks_residual", "gks_status_word",
+                 "gks_get_rarefaction", "gks_get_tau_turb", "gks_enable_timing", "gks_kernel_time",
+                 "gks_destroy", "gks_face_flux"):
+        getattr(L, name).restype = _I
+    _lib = L
+    return L
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One grid problem on one GPU (see gks_create in include/gks.h for the meaning of each field).
+
+    Arrays passed in may be numpy arrays (host memory) or torch tensors (host or CUDA)."""
+
+    def __init__(self, dim, n, bc, dx=None, lo=None, hi=None, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0,
+                 turb_model="none", C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", expand="multid",
+                 precision="fp64", abar_mode="timeint", stream=None):
+        import torch
+        L = load()
+        self.dim, self.nv = dim, dim + 2
+        self.n = tuple(int(v) for v in n[:dim])
+        self.ncell = int(np.prod(self.n))
+        self._keep = []
+        g = _Grid()
+        g.dim = dim
+        for d in range(3):
+            g.n[d] = self.n[d] if d < dim else 1
+            g.lo[d] = lo[d] if lo is not None and d < dim else 0.0
+            g.hi[d] = hi[d] if hi is not None and d < dim else 1.0
+        for d in range(dim):
+            if dx is not None and dx[d] is not None:
+                w = _f64(np.broadcast_to(np.asarray(dx[d], dtype=np.float64), (self.n[d],)))
+                self._keep.append(w)
+                g.dx[d] = w.ctypes.data_as(_PD)
+            for s in range(2):
+                code = bc[d][s]
+                g.bc[d][s] = BC[code] if isinstance(code, str) else int(code)
+                if bc_data is not None and bc_data[d][s] is not None:
+                    a = _f64(bc_data[d][s])
+                    self._keep.append(a)
+                    g.bc_data[d][s] = a.ctypes.data_as(_PD)
+        gas = _Gas(gamma, mu, 1.0, T_wall)
+        tm = TURB[turb_model] if isinstance(turb_model, str) else int(turb_model)
+        turb = _Turb(tm, C_mu, beta_star, C_a)
+        num = _Num(LIMITER[limiter] if isinstance(limiter, str) else int(limiter),
+                   EXPAND[expand] if isinstance(expand, str) else int(expand),
+                   PRECISION[precision] if isinstance(precision, str) else int(precision),
+                   ABAR[abar_mode] if isinstance(abar_mode, str) else int(abar_mode))
+        self.precision = num.precision
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = _V()
+        st = L.gks_create(ctypes.byref(g), ctypes.byref(gas), ctypes.byref(turb), ctypes.byref(num),
+                          _V(self.stream.cuda_stream), ctypes.byref(h))
+        self._h = h
+        if st != OK:
+            msg = L.gks_last_error(h).decode() if h.value else "gks_create failed"
+            if h.value:
+                L.gks_destroy(h)
+            self._h = None
+            raise GksError(st, msg)
+
+    # -- helpers -----------------------------------------------------------------------------------
+    def _check(self, st):
+        if st != OK:
+            raise GksError(st, load().gks_last_error(self._h).decode())
+
+    def _ptr(self, x, writable=False):
+        """(pointer, memspace, dtype) of a numpy array or torch tensor; keeps a reference."""
+        if _is_torch(x):
+            import torch
+            assert x.is_contiguous()
+            dt = {torch.float64: F64, torch.float32: F32}[x.dtype]
+            mem = MEM_DEVICE if x.is_cuda else MEM_HOST
+            if x.is_cuda:
+                self.stream.wait_stream(torch.cuda.current_stream(x.device))
+            return _V(x.data_ptr()), mem, dt
+        a = np.asarray(x)
+        if not writable:
+            a = np.ascontiguousarray(a)
+        dt = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[a.dtype]
+        self._keep_tmp = a
+        return _V(a.ctypes.data), MEM_HOST, dt
+
+    def _after_device_write(self, x):
+        if _is_torch(x) and x.is_cuda:
+            import torch
+            torch.cuda.current_stream(x.device).wait_stream(self.stream)
+
+    # -- API ---------------------------------------------------------------------------------------
+    def set_state(self, W, layout="soa_cons"):
+        p, mem, dt = self._ptr(W)
+        self._check(load().gks_set_state(self._h, p, LAYOUT[layout], mem, dt))
+        if mem == MEM_HOST:
+            self.stream.synchronize()  # the host buffer may be reused by the caller
+
+    def set_turbulence(self, f1, f2=None):
+        p1, mem, dt = self._ptr(f1)
+        keep = self._keep_tmp if not _is_torch(f1) else f1
+        p2 = None
+        if f2 is not None:
+            p2, mem2, dt2 = self._ptr(f2)
+            assert (mem2, dt2) == (mem, dt)
+        self._check(load().gks_set_turbulence(self._h, p1, p2, mem, dt))
+        del keep
+        self.stream.synchronize()
+
+    def get_state(self, layout="soa_cons", out=None, dtype=np.float64):
+        if out is None:
+            out = np.zeros(self.nv * self.ncell, dtype=dtype)
+        p, mem, dt = self._ptr(out, writable=True)
+        self._check(load().gks_get_state(self._h, p, LAYOUT[layout], mem, dt))
+        self._after_device_write(out)
+        return out
+
+    def compute_dt(self, cfl):
+        v = _D()
+        self._check(load().gks_compute_dt(self._h, cfl, ctypes.byref(v)))
+        return v.value
+
+    def step(self, nsteps=1, dt=0.0, cfl=0.5, t_end=0.0):
+        self._check(load().gks_step(self._h, dt, cfl, int(nsteps), t_end))
+
+    def time(self):
+        t, s = _D(), ctypes.c_longlong()
+        self._check(load().gks_get_time(self._h, ctypes.byref(t), ctypes.byref(s)))
+        return t.value, s.value
+
+    def set_time(self, t):
+        self._check(load().gks_set_time(self._h, t))
+
+    def residual(self):
+        l2, li, tot = (np.zeros(self.nv) for _ in range(3))
+        self._check(load().gks_residual(self._h, l2.ctypes.data_as(_PD), li.ctypes.data_as(_PD),
+                                        tot.ctypes.data_as(_PD)))
+        return l2, li, tot
+
+    def status_word(self):
+        b, d = ctypes.c_uint(), _D()
+        self._check(load().gks_status_word(self._h, ctypes.byref(b), ctypes.byref(d)))
+        return b.value, d.value
+
+    def rarefaction(self, out=None):
+        if out is None:
+            out = np.zeros(self.ncell)
+        p, mem, dt = self._ptr(out, writable=True)
+        self._check(load().gks_get_rarefaction(self._h, p, mem, dt))
+        self._after_device_write(out)
+        return out
+
+    def tau_turb(self, out=None):
+        if out is None:
+            out = np.zeros(self.ncell)
+        p, mem, dt = self._ptr(out, writable=True)
+        self._check(load().gks_get_tau_turb(self._h, p, mem, dt))
+        self._after_device_write(out)
+        return out
+
+    def enable_timing(self, on=True):
+        self._check(load().gks_enable_timing(self._h, int(on)))
+
+    def kernel_time(self):
+        ms, n = _D(), ctypes.c_longlong()
+        self._check(load().gks_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if self._h is not None:
+            load().gks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def face_record_len(dim):
+    return load().gks_face_record_len(dim)
+
+
+def face_flux(dim, faces, dt, gamma=1.4, mu=1e-5, C_a=0.0, precision="fp64", expand="multid",
+              abar_mode="timeint", stream=None):
+    """Evaluate interface fluxes for face records held in a CUDA float64 tensor
+    [nfaces, face_record_len(dim)]; returns (F [nfaces, dim+2], tau [nfaces]) as CUDA tensors."""
+    import torch
+    assert faces.is_cuda and faces.dtype == torch.float64 and faces.is_contiguous()
+    nf = faces.shape[0]
+    F = torch.empty((nf, dim + 2), dtype=torch.float64, device=faces.device)
+    tau = torch.empty((nf,), dtype=torch.float64, device=faces.device)
+    s = stream if stream is not None else torch.cuda.current_stream(faces.device)
+    st = load().gks_face_flux(dim, PRECISION[precision], EXPAND[expand], ABAR[abar_mode], gamma, mu, C_a, dt,
+                              _V(faces.data_ptr()), nf, _V(F.data_ptr()), _V(tau.data_ptr()),
+                              _V(s.cuda_stream))
+    if st != OK:
+        raise GksError(st, "gks_face_flux failed")
+    return F, tau

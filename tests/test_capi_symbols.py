@@ -1,0 +1,48 @@
+"""The C ABI library loads and exports every entry point declared in include/gks.h (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(gks_[a-z0-9_]+)\s*\(", text, re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("gks_create", "gks_set_state", "gks_compute_dt", "gks_step", "gks_get_state", "gks_residual",
+              "gks_set_turbulence", "gks_get_rarefaction", "gks_destroy", "gks_last_error", "gks_face_flux"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1302_2132_gb300 import build
+    lib = build.build()
+    L = ctypes.CDLL(lib)
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1302_2132_gb300 import gks
+    monkeypatch.setattr(gks, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gks, "_lib", None)
+    with pytest.raises(ImportError):
+        gks.load()
+
+
+def test_face_record_length():
+    from paper_1302_2132_gb300 import build, gks
+    build.build()
+    gks.load()
+    assert [gks.face_record_len(d) for d in (1, 2, 3)] == [21, 35, 53]
