@@ -68,15 +68,24 @@ GKS_FN Maxw<D, T> maxwellian(const T* w, T bK) {
   return g;
 }
 
-// Moment tables of one Maxwellian restricted to one region of the normal velocity.
-//   u[n] = <u^n> (n <= 6) over the region, v[t][n] = <v_t^n> (n <= 5) over the full line,
-//   x[l] = <(xi^2)^l> (l <= 2).
-template <int D, class T> struct Tab {
-  T u[7];
-  T v[Dims<D>::nt][6];
-  T x[3];
+// Moments of one Maxwellian, split into the normal velocity u and the transverse part.
+//
+// Every polynomial the flux needs is linear in the transverse basis {1, v_s, Et}, with
+// Et = (sum_s v_s^2 + xi^2)/2 (so psi_E = u^2/2 + Et), and has polynomial coefficients in u.  Under
+// the Maxwellian u, the v_s and xi are independent, so a moment factors into a moment of u over the
+// chosen half line and a transverse moment over the full space.  The transverse moments of products
+// of up to three basis functions are tabulated once per Maxwellian.
+template <int D> struct Basis {
+  static constexpr int NB = D + 1;  // 0: 1, 1..D-1: v_s, D: Et
 };
 
+template <int D, class T> struct Trans {
+  T m1[D + 1];                     // <beta>
+  T m2[D + 1][D + 1];              // <alpha beta>
+  T m3[Dims<D>::nt][D + 1][D + 1];  // <v_s alpha beta>
+};
+
+// Gaussian moments <x^n>, n = 0..N-1, of mean U and variance il: x^{n+2} = U x^{n+1} + (n+1) il x^n.
 template <int N, class T>
 GKS_FN void recur(T U, T il, T* m) {
 #pragma unroll
@@ -84,111 +93,152 @@ GKS_FN void recur(T U, T il, T* m) {
 }
 
 template <int D, class T>
-GKS_FN void tang_and_xi(const Maxw<D, T>& g, T K, Tab<D, T>& t) {
+GKS_FN void transverse(const Maxw<D, T>& g, T K, Trans<D, T>& t) {
+  const T X1 = K * g.il;                        // <xi^2>
+  const T X2 = K * (K + T(2)) * g.il * g.il;    // <xi^4>
+  T V[Dims<D>::nt][6];
 #pragma unroll
   for (int s = 0; s < D - 1; ++s) {
-    t.v[s][0] = T(1);
-    t.v[s][1] = g.U[1 + s];
-    recur<6>(g.U[1 + s], g.il, t.v[s]);
+    V[s][0] = T(1);
+    V[s][1] = g.U[1 + s];
+    recur<6>(g.U[1 + s], g.il, V[s]);
   }
-  t.x[0] = T(1);
-  t.x[1] = K * g.il;
-  t.x[2] = K * (K + T(2)) * g.il * g.il;
+  t.m1[0] = T(1);
+#pragma unroll
+  for (int b = 0; b <= D; ++b) t.m2[0][b] = T(0);
+  if (D == 1) {
+    // basis {1, Et}, Et = xi^2 / 2
+    t.m1[1] = T(0.5) * X1;
+    t.m2[0][0] = T(1);
+    t.m2[0][1] = t.m2[1][0] = t.m1[1];
+    t.m2[1][1] = T(0.25) * X2;
+  } else if (D == 2) {
+    // basis {1, v, Et}, Et = (v^2 + xi^2)/2
+    const T* v = V[0];
+    const T e1 = v[2] + X1;                          // <2 Et>
+    const T ve = v[3] + v[1] * X1;                   // <v 2 Et>
+    const T vve = v[4] + v[2] * X1;                  // <v^2 2 Et>
+    const T ee = v[4] + T(2) * v[2] * X1 + X2;       // <(2 Et)^2>
+    const T vee = v[5] + T(2) * v[3] * X1 + v[1] * X2;  // <v (2 Et)^2>
+    t.m1[1] = v[1];
+    t.m1[2] = T(0.5) * e1;
+    t.m2[0][0] = T(1);
+    t.m2[0][1] = t.m2[1][0] = v[1];
+    t.m2[0][2] = t.m2[2][0] = t.m1[2];
+    t.m2[1][1] = v[2];
+    t.m2[1][2] = t.m2[2][1] = T(0.5) * ve;
+    t.m2[2][2] = T(0.25) * ee;
+    // <v alpha beta>
+    t.m3[0][0][0] = v[1];
+    t.m3[0][0][1] = t.m3[0][1][0] = v[2];
+    t.m3[0][0][2] = t.m3[0][2][0] = t.m2[1][2];
+    t.m3[0][1][1] = v[3];
+    t.m3[0][1][2] = t.m3[0][2][1] = T(0.5) * vve;
+    t.m3[0][2][2] = T(0.25) * vee;
+  } else {
+    // basis {1, v, w, Et}, Et = (v^2 + w^2 + xi^2)/2
+    const T* v = V[0];
+    const T* w = V[Dims<D>::nt - 1];
+    const T rv1 = w[2] + X1, rv2 = w[4] + T(2) * w[2] * X1 + X2;  // moments of 2Et - v^2
+    const T rw1 = v[2] + X1, rw2 = v[4] + T(2) * v[2] * X1 + X2;  // moments of 2Et - w^2
+    const T e1 = v[2] + rv1;
+    const T ee = v[4] + T(2) * v[2] * rv1 + rv2;
+    t.m1[1] = v[1];
+    t.m1[2] = w[1];
+    t.m1[3] = T(0.5) * e1;
+    t.m2[0][0] = T(1);
+#pragma unroll
+    for (int b = 1; b <= 3; ++b) t.m2[0][b] = t.m2[b][0] = t.m1[b];
+    t.m2[1][1] = v[2];
+    t.m2[1][2] = t.m2[2][1] = v[1] * w[1];
+    t.m2[2][2] = w[2];
+    t.m2[1][3] = t.m2[3][1] = T(0.5) * (v[3] + v[1] * rv1);
+    t.m2[2][3] = t.m2[3][2] = T(0.5) * (w[3] + w[1] * rw1);
+    t.m2[3][3] = T(0.25) * ee;
+    const T vwe = T(0.5) * (v[3] * w[1] + v[1] * w[3] + v[1] * w[1] * X1);  // <v w Et>
+    // gamma = v
+    t.m3[0][0][0] = v[1];
+    t.m3[0][0][1] = t.m3[0][1][0] = v[2];
+    t.m3[0][0][2] = t.m3[0][2][0] = t.m2[1][2];
+    t.m3[0][0][3] = t.m3[0][3][0] = t.m2[1][3];
+    t.m3[0][1][1] = v[3];
+    t.m3[0][1][2] = t.m3[0][2][1] = v[2] * w[1];
+    t.m3[0][2][2] = v[1] * w[2];
+    t.m3[0][1][3] = t.m3[0][3][1] = T(0.5) * (v[4] + v[2] * rv1);
+    t.m3[0][2][3] = t.m3[0][3][2] = vwe;
+    t.m3[0][3][3] = T(0.25) * (v[5] + T(2) * v[3] * rv1 + v[1] * rv2);
+    // gamma = w
+    t.m3[1][0][0] = w[1];
+    t.m3[1][0][1] = t.m3[1][1][0] = t.m2[1][2];
+    t.m3[1][0][2] = t.m3[1][2][0] = w[2];
+    t.m3[1][0][3] = t.m3[1][3][0] = t.m2[2][3];
+    t.m3[1][1][1] = v[2] * w[1];
+    t.m3[1][1][2] = t.m3[1][2][1] = v[1] * w[2];
+    t.m3[1][2][2] = w[3];
+    t.m3[1][1][3] = t.m3[1][3][1] = vwe;
+    t.m3[1][2][3] = t.m3[1][3][2] = T(0.5) * (w[4] + w[2] * rw1);
+    t.m3[1][3][3] = T(0.25) * (w[5] + T(2) * w[3] * rw1 + w[1] * rw2);
+  }
 }
 
-// Full-line table.
+// <u^n>, n = 0..6, over the full line.
 template <int D, class T>
-GKS_FN void tab_full(const Maxw<D, T>& g, T K, Tab<D, T>& t) {
-  t.u[0] = T(1);
-  t.u[1] = g.U[0];
-  recur<7>(g.U[0], g.il, t.u);
-  tang_and_xi(g, K, t);
+GKS_FN void u_full(const Maxw<D, T>& g, T* u) {
+  u[0] = T(1);
+  u[1] = g.U[0];
+  recur<7>(g.U[0], g.il, u);
 }
 
-// Half-line tables u > 0 (P) and u < 0 (N) from one erfc and one exp:
-//   <1>_{u>0} = erfc(-sqrt(lam) U)/2, <u>_{u>0} = U <1>_{u>0} + exp(-lam U^2)/(2 sqrt(pi lam)).
+// <u^n> over u > 0 (sgn = +1) or u < 0 (sgn = -1), from the textbook half-line Gaussian integrals
+//   <1>_{u>0} = erfc(-sqrt(lam) U)/2,  <u>_{u>0} = U <1>_{u>0} + exp(-lam U^2)/(2 sqrt(pi lam)).
 template <int D, class T>
-GKS_FN void tab_half(const Maxw<D, T>& g, T K, Tab<D, T>* P, Tab<D, T>* N) {
+GKS_FN void u_half(const Maxw<D, T>& g, T sgn, T* u) {
   const T sl = g_sqrt(g.lam);
   const T z = sl * g.U[0];
-  const T h = T(0.5) * g_exp(-z * z) * T(kInvSqrtPi) / sl;
-  if (P) {
-    P->u[0] = T(0.5) * g_erfc(-z);
-    P->u[1] = g.U[0] * P->u[0] + h;
-    recur<7>(g.U[0], g.il, P->u);
-    tang_and_xi(g, K, *P);
-  }
-  if (N) {
-    N->u[0] = T(0.5) * g_erfc(z);
-    N->u[1] = g.U[0] * N->u[0] - h;
-    recur<7>(g.U[0], g.il, N->u);
-    tang_and_xi(g, K, *N);
-  }
+  u[0] = T(0.5) * g_erfc(-sgn * z);
+  u[1] = g.U[0] * u[0] + sgn * T(0.5) * g_exp(-z * z) * T(kInvSqrtPi) / sl;
+  recur<7>(g.U[0], g.il, u);
 }
 
-// <u^a v^b0 w^b1 (xi^2)^l>
+// <psi_m> over the region of table u.
 template <int D, class T>
-GKS_FN T mono(const Tab<D, T>& t, int a, int b0, int b1, int l) {
-  T r = t.u[a];
-  if (D >= 2) r = r * t.v[0][b0];
-  if (D >= 3) r = r * t.v[D >= 3 ? 1 : 0][b1];
-  return r * t.x[l];
+GKS_FN void psi_mean(const T* u, const Trans<D, T>& t, T* out) {
+  out[0] = u[0];
+  out[1] = u[1];
+#pragma unroll
+  for (int s = 0; s < D - 1; ++s) out[2 + s] = u[0] * t.m1[1 + s];
+  out[D + 1] = T(0.5) * u[2] + u[0] * t.m1[D];
 }
 
-// out[m] = <u^a v^b0 w^b1 (xi^2)^l psi_m>, psi = (1, u, v, w, (u^2 + v^2 + w^2 + xi^2)/2)
+// acc[m] += s * <u^k gamma (a . psi) psi_m>, gamma = 1 (tg = -1) or v_tg.
+// With a . psi = A(u) + sum_beta a_beta beta, A(u) = a0 + a1 u + aE u^2 / 2, and
+// psi_m = P_m(u) + (transverse part), the moment is a sum of (u moment) x (transverse moment).
 template <int D, class T>
-GKS_FN void psi_mom(const Tab<D, T>& t, int a, int b0, int b1, int l, T* out) {
-  out[0] = mono(t, a, b0, b1, l);
-  out[1] = mono(t, a + 1, b0, b1, l);
-  if (D >= 2) out[2] = mono(t, a, b0 + 1, b1, l);
-  if (D >= 3) out[3] = mono(t, a, b0, b1 + 1, l);
-  T e = mono(t, a + 2, b0, b1, l) + mono(t, a, b0, b1, l + 1);
-  if (D >= 2) e += mono(t, a, b0 + 2, b1, l);
-  if (D >= 3) e += mono(t, a, b0, b1 + 2, l);
-  out[D + 1] = T(0.5) * e;
-}
-
-// acc[m] += s * <u^a v_j^(j == tj) (a . psi) psi_m>, tj = -1 for no tangential factor.
-template <int D, class T>
-GKS_FN void amom(const Tab<D, T>& t, int a, int tj, const T* c, T s, T* acc) {
-  constexpr int nv = D + 2;
-  const int b0 = (tj == 0) ? 1 : 0, b1 = (tj == 1) ? 1 : 0;
-  T r[nv], q[nv];
-  psi_mom<D, T>(t, a, b0, b1, 0, r);  // c0 * 1
+GKS_FN void amom(const T* u, const Trans<D, T>& t, int k, int tg, const T* a, T s, T* acc) {
+  constexpr int NB = D + 1;
+  const T hE = T(0.5) * a[D + 1];
+  const T SA0 = a[0] * u[k] + a[1] * u[k + 1] + hE * u[k + 2];
+  const T SA1 = a[0] * u[k + 1] + a[1] * u[k + 2] + hE * u[k + 3];
+  const T SA2 = a[0] * u[k + 2] + a[1] * u[k + 3] + hE * u[k + 4];
+  // transverse factors: <gamma beta> and <gamma beta tau>
+  T g1[NB], c2[NB];
 #pragma unroll
-  for (int m = 0; m < nv; ++m) q[m] = c[0] * r[m];
-  psi_mom<D, T>(t, a + 1, b0, b1, 0, r);  // c1 * u
+  for (int b = 0; b < NB; ++b) g1[b] = tg < 0 ? t.m1[b] : t.m2[1 + tg][b];
+  T c1 = T(0);
 #pragma unroll
-  for (int m = 0; m < nv; ++m) q[m] += c[1] * r[m];
-  if (D >= 2) {
-    psi_mom<D, T>(t, a, b0 + 1, b1, 0, r);
+  for (int b = 1; b < NB; ++b) c1 += a[b == D ? D + 1 : 1 + b] * g1[b];
 #pragma unroll
-    for (int m = 0; m < nv; ++m) q[m] += c[2] * r[m];
+  for (int tau = 1; tau < NB; ++tau) {
+    T q = T(0);
+#pragma unroll
+    for (int b = 1; b < NB; ++b) q += a[b == D ? D + 1 : 1 + b] * (tg < 0 ? t.m2[b][tau] : t.m3[tg][b][tau]);
+    c2[tau] = q;
   }
-  if (D >= 3) {
-    psi_mom<D, T>(t, a, b0, b1 + 1, 0, r);
+  acc[0] += s * (SA0 * g1[0] + u[k] * c1);
+  acc[1] += s * (SA1 * g1[0] + u[k + 1] * c1);
 #pragma unroll
-    for (int m = 0; m < nv; ++m) q[m] += c[3] * r[m];
-  }
-  // cE * (u^2 + v^2 + w^2 + xi^2) / 2
-  T e[nv];
-  psi_mom<D, T>(t, a + 2, b0, b1, 0, e);
-  psi_mom<D, T>(t, a, b0, b1, 1, r);
-#pragma unroll
-  for (int m = 0; m < nv; ++m) e[m] += r[m];
-  if (D >= 2) {
-    psi_mom<D, T>(t, a, b0 + 2, b1, 0, r);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) e[m] += r[m];
-  }
-  if (D >= 3) {
-    psi_mom<D, T>(t, a, b0, b1 + 2, 0, r);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) e[m] += r[m];
-  }
-  const T hE = T(0.5) * c[D + 1];
-#pragma unroll
-  for (int m = 0; m < nv; ++m) acc[m] += s * (q[m] + hE * e[m]);
+  for (int v = 0; v < D - 1; ++v) acc[2 + v] += s * (SA0 * g1[1 + v] + u[k] * c2[1 + v]);
+  acc[D + 1] += s * (T(0.5) * (SA2 * g1[0] + u[k + 2] * c1) + SA0 * g1[D] + u[k] * c2[D]);
 }
 
 enum { LIM_MINMOD = 0, LIM_VANLEER = 1 };
@@ -325,102 +375,37 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
 //   tl, tr   tangential slopes (multi-dimensional expansion only); dxl, dxr centre-to-face distances;
 //   tau_t    turbulent relaxation time at the face; dt the time step.
 // Output: F, the flux integrated over [0, dt] (Eq. fluxesf); tau_out the total relaxation time.
+//
+// The work is ordered so that each velocity region (u > 0 of the left Maxwellian, u < 0 of the
+// right one, and the two halves and the full line of the equilibrium g0) is visited once, adding
+// both its part of the right-hand side of the Abar equation and its part of the flux; only the
+// Abar term of the flux waits for Abar.
 template <int D, class T, bool MULTID>
-GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const T* sl,
-                                          const T* sr, const T (*tl)[D + 2], const T (*tr)[D + 2], T dxl,
-                                          T dxr, T tau_t, T dt, const Gas<T>& gas, int abar_t0, T* F,
-                                          T* tau_out) {
+GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const T* sl, const T* sr,
+                      const T (*tl)[D + 2], const T (*tr)[D + 2], T dxl, T dxr, T tau_t, T dt, const Gas<T>& gas,
+                      int abar_t0, T* F, T* tau_out) {
   constexpr int nv = D + 2;
-  constexpr int NT = Dims<D>::nt;
   const T bK = gas.bK, K = gas.K;
   const Maxw<D, T> gl = maxwellian<D, T>(wl, bK);
   const Maxw<D, T> gr = maxwellian<D, T>(wr, bK);
 
   // Eq. intermediatestate: w0 = rho_l <psi>_{l,u>0} + rho_r <psi>_{r,u<0}
-  Tab<D, T> lP, rN;
-  tab_half<D, T>(gl, K, &lP, nullptr);
-  tab_half<D, T>(gr, K, nullptr, &rN);
   T w0[nv];
+  T lP[7], rN[7];
+  Trans<D, T> trl, trr;
+  u_half<D, T>(gl, T(1), lP);
+  u_half<D, T>(gr, T(-1), rN);
+  transverse<D, T>(gl, K, trl);
+  transverse<D, T>(gr, K, trr);
   {
     T a[nv], b[nv];
-    psi_mom<D, T>(lP, 0, 0, 0, 0, a);
-    psi_mom<D, T>(rN, 0, 0, 0, 0, b);
+    psi_mean<D, T>(lP, trl, a);
+    psi_mean<D, T>(rN, trr, b);
 #pragma unroll
     for (int m = 0; m < nv; ++m) w0[m] = gl.rho * a[m] + gr.rho * b[m];
   }
   const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK);
-  Tab<D, T> oP, oN, oF;
-  tab_half<D, T>(g0, K, &oP, &oN);
-  tab_full<D, T>(g0, K, oF);
 
-  // Eq. initialf0: spatial coefficients of the initial state from the conservative gradients
-  T al[nv], ar[nv], bl[NT][nv], br[NT][nv];
-  {
-    T r[nv];
-    const T il = T(1) / gl.rho, ir = T(1) / gr.rho;
-#pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = sl[m] * il;
-    slope<D, T>(gl, bK, r, al);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = sr[m] * ir;
-    slope<D, T>(gr, bK, r, ar);
-#pragma unroll
-    for (int s = 0; s < D - 1; ++s) {
-      if (MULTID) {
-#pragma unroll
-        for (int m = 0; m < nv; ++m) r[m] = tl[s][m] * il;
-        slope<D, T>(gl, bK, r, bl[s]);
-#pragma unroll
-        for (int m = 0; m < nv; ++m) r[m] = tr[s][m] * ir;
-        slope<D, T>(gr, bK, r, br[s]);
-      }
-    }
-  }
-  // A from the compatibility condition at t = 0: <(a u + b v + A) psi> = 0 (full moments)
-  T Al[nv], Ar[nv];
-  {
-    Tab<D, T> f;
-    T rhs[nv];
-    tab_full<D, T>(gl, K, f);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) rhs[m] = T(0);
-    amom<D, T>(f, 1, -1, al, T(-1), rhs);
-    if (MULTID) {
-#pragma unroll
-      for (int s = 0; s < D - 1; ++s) amom<D, T>(f, 0, s, bl[s], T(-1), rhs);
-    }
-    slope<D, T>(gl, bK, rhs, Al);
-    tab_full<D, T>(gr, K, f);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) rhs[m] = T(0);
-    amom<D, T>(f, 1, -1, ar, T(-1), rhs);
-    if (MULTID) {
-#pragma unroll
-      for (int s = 0; s < D - 1; ++s) amom<D, T>(f, 0, s, br[s], T(-1), rhs);
-    }
-    slope<D, T>(gr, bK, rhs, Ar);
-  }
-  // Eq. eqlgform: equilibrium slopes from W_j -> w0 -> W_{j+1}
-  T abl[nv], abr[nv], bb[NT][nv];
-  {
-    T r[nv];
-    const T i0 = T(1) / g0.rho;
-    const T fl = i0 / dxl, fr = i0 / dxr;
-#pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = (w0[m] - cl[m]) * fl;
-    slope<D, T>(g0, bK, r, abl);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = (cr[m] - w0[m]) * fr;
-    slope<D, T>(g0, bK, r, abr);
-    if (MULTID) {
-#pragma unroll
-      for (int s = 0; s < D - 1; ++s) {
-#pragma unroll
-        for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (tl[s][m] + tr[s][m]) * i0;
-        slope<D, T>(g0, bK, r, bb[s]);
-      }
-    }
-  }
   // Eqs. relaxation time and taua: tau = mu/p0 + tau_t + C_a |p_r - p_l| / (p_r + p_l) dt
   const T p0 = g0.rho * g0.il, pl = gl.rho * gl.il, pr = gr.rho * gr.il;
   const T tau = gas.mu / p0 + tau_t + gas.C_a * g_abs(pr - pl) / (pr + pl) * dt;
@@ -431,71 +416,108 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
     r1 = T(-1);
     r4 = r5 = T(0);
   }
-  // Abar from the compatibility condition integrated over [0, dt]:
-  //   <Abar psi>_0 = r1 X1 + r4 X4 + r5 X5
-  T Ab[nv];
-  {
-    T rhs[nv];
+  const T i0 = T(1) / g0.rho;
+
+  // Abar right-hand side (per unit rho0) and flux, accumulated region by region
+  T rhs[nv];
 #pragma unroll
-    for (int m = 0; m < nv; ++m) rhs[m] = T(0);
-    amom<D, T>(oP, 1, -1, abl, r1, rhs);
-    amom<D, T>(oN, 1, -1, abr, r1, rhs);
-    if (MULTID) {
-#pragma unroll
-      for (int s = 0; s < D - 1; ++s) amom<D, T>(oF, 0, s, bb[s], r1, rhs);
-    }
-    const T i0 = T(1) / g0.rho;
-    const T sl4 = r4 * gl.rho * i0, sr4 = r4 * gr.rho * i0;
-    const T sl5 = r5 * gl.rho * i0, sr5 = r5 * gr.rho * i0;
-    amom<D, T>(lP, 1, -1, al, sl4, rhs);
-    amom<D, T>(rN, 1, -1, ar, sr4, rhs);
-    if (MULTID) {
-#pragma unroll
-      for (int s = 0; s < D - 1; ++s) {
-        amom<D, T>(lP, 0, s, bl[s], sl4, rhs);
-        amom<D, T>(rN, 0, s, br[s], sr4, rhs);
-      }
-    }
-    amom<D, T>(lP, 0, -1, Al, sl5, rhs);
-    amom<D, T>(rN, 0, -1, Ar, sr5, rhs);
-    slope<D, T>(g0, bK, rhs, Ab);
+  for (int m = 0; m < nv; ++m) {
+    rhs[m] = T(0);
+    F[m] = T(0);
   }
-  // Eq. fluxesf with the time integral of Eq. resultingf:
-  //   F = rho0 [<u (T0 + T2 Abar) psi>_0 + T1 (<u^2 abar psi>_{0,split} + <u v bbar psi>_0)]
-  //     + rho_l [<u (T3 + T5 A_l) psi>_{l,u>0} + T4 (<u^2 a_l psi> + <u v b_l psi>)_{l,u>0}] + (r, u<0)
-  {
-    T acc0[nv], accl[nv], accr[nv], c[nv];
+
+  // one side of the initial state: Eq. initialf0, slopes a (normal), b (tangential) and A
+  auto side = [&](const Maxw<D, T>& g, const Trans<D, T>& ts, const T* half, const T* sn, const T (*st)[D + 2]) {
+    T a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
+    const T ir = T(1) / g.rho;
 #pragma unroll
-    for (int m = 0; m < nv; ++m) acc0[m] = accl[m] = accr[m] = T(0);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) c[m] = Tc[2] * Ab[m];
-    c[0] += Tc[0];
-    amom<D, T>(oF, 1, -1, c, T(1), acc0);
-    amom<D, T>(oP, 2, -1, abl, Tc[1], acc0);
-    amom<D, T>(oN, 2, -1, abr, Tc[1], acc0);
+    for (int m = 0; m < nv; ++m) r[m] = sn[m] * ir;
+    slope<D, T>(g, bK, r, a);
     if (MULTID) {
 #pragma unroll
-      for (int s = 0; s < D - 1; ++s) amom<D, T>(oF, 1, s, bb[s], Tc[1], acc0);
-    }
+      for (int q = 0; q < D - 1; ++q) {
 #pragma unroll
-    for (int m = 0; m < nv; ++m) c[m] = Tc[5] * Al[m];
-    c[0] += Tc[3];
-    amom<D, T>(lP, 1, -1, c, T(1), accl);
-    amom<D, T>(lP, 2, -1, al, Tc[4], accl);
-#pragma unroll
-    for (int m = 0; m < nv; ++m) c[m] = Tc[5] * Ar[m];
-    c[0] += Tc[3];
-    amom<D, T>(rN, 1, -1, c, T(1), accr);
-    amom<D, T>(rN, 2, -1, ar, Tc[4], accr);
-    if (MULTID) {
-#pragma unroll
-      for (int s = 0; s < D - 1; ++s) {
-        amom<D, T>(lP, 1, s, bl[s], Tc[4], accl);
-        amom<D, T>(rN, 1, s, br[s], Tc[4], accr);
+        for (int m = 0; m < nv; ++m) r[m] = st[q][m] * ir;
+        slope<D, T>(g, bK, r, b[q]);
       }
     }
+    // A from the compatibility condition at t = 0: <(a u + b v + A) psi> = 0 (full line)
+    {
+      T uf[7];
+      u_full<D, T>(g, uf);
 #pragma unroll
-    for (int m = 0; m < nv; ++m) F[m] = g0.rho * acc0[m] + gl.rho * accl[m] + gr.rho * accr[m];
+      for (int m = 0; m < nv; ++m) r[m] = T(0);
+      amom<D, T>(uf, ts, 1, -1, a, T(-1), r);
+      if (MULTID) {
+#pragma unroll
+        for (int q = 0; q < D - 1; ++q) amom<D, T>(uf, ts, 0, q, b[q], T(-1), r);
+      }
+      slope<D, T>(g, bK, r, A);
+    }
+    // Abar rhs: r4 rho/rho0 <(a u + b v) psi> + r5 rho/rho0 <A psi> over the half line
+    const T s4 = r4 * g.rho * i0, s5 = r5 * g.rho * i0;
+    amom<D, T>(half, ts, 1, -1, a, s4, rhs);
+    amom<D, T>(half, ts, 0, -1, A, s5, rhs);
+    // flux: rho [<u (T3 + T5 A) psi> + T4 (<u^2 a psi> + <u v b psi>)]
+    T c[nv];
+#pragma unroll
+    for (int m = 0; m < nv; ++m) c[m] = Tc[5] * A[m];
+    c[0] += Tc[3];
+    amom<D, T>(half, ts, 1, -1, c, g.rho, F);
+    const T s4f = Tc[4] * g.rho;
+    amom<D, T>(half, ts, 2, -1, a, s4f, F);
+    if (MULTID) {
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+        amom<D, T>(half, ts, 0, q, b[q], s4, rhs);
+        amom<D, T>(half, ts, 1, q, b[q], s4f, F);
+      }
+    }
+  };
+  side(gl, trl, lP, sl, tl);
+  side(gr, trr, rN, sr, tr);
+
+  // equilibrium g0: Eq. eqlgform slopes from W_j -> w0 -> W_{j+1} (and the mean tangential slope)
+  Trans<D, T> tr0;
+  transverse<D, T>(g0, K, tr0);
+  T oF[7], oP[7], oN[7];
+  u_full<D, T>(g0, oF);
+  u_half<D, T>(g0, T(1), oP);
+#pragma unroll
+  for (int n = 0; n < 7; ++n) oN[n] = oF[n] - oP[n];
+  {
+    T r[nv], ab[nv];
+    const T fl = i0 / dxl, fr = i0 / dxr;
+    const T s1f = Tc[1] * g0.rho;
+#pragma unroll
+    for (int m = 0; m < nv; ++m) r[m] = (w0[m] - cl[m]) * fl;
+    slope<D, T>(g0, bK, r, ab);
+    amom<D, T>(oP, tr0, 1, -1, ab, r1, rhs);
+    amom<D, T>(oP, tr0, 2, -1, ab, s1f, F);
+#pragma unroll
+    for (int m = 0; m < nv; ++m) r[m] = (cr[m] - w0[m]) * fr;
+    slope<D, T>(g0, bK, r, ab);
+    amom<D, T>(oN, tr0, 1, -1, ab, r1, rhs);
+    amom<D, T>(oN, tr0, 2, -1, ab, s1f, F);
+    if (MULTID) {
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+#pragma unroll
+        for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (tl[q][m] + tr[q][m]) * i0;
+        slope<D, T>(g0, bK, r, ab);
+        amom<D, T>(oF, tr0, 0, q, ab, r1, rhs);
+        amom<D, T>(oF, tr0, 1, q, ab, s1f, F);
+      }
+    }
+  }
+  // Abar from the compatibility condition integrated over [0, dt]; flux rho0 <u (T0 + T2 Abar) psi>
+  {
+    T Ab[nv];
+    slope<D, T>(g0, bK, rhs, Ab);
+#pragma unroll
+    for (int m = 0; m < nv; ++m) Ab[m] *= Tc[2];
+    Ab[0] += Tc[0];
+    amom<D, T>(oF, tr0, 1, -1, Ab, g0.rho, F);
   }
 }
 

@@ -26,7 +26,7 @@ constexpr int kThreads = 256;
 
 template <int D> struct Tile;
 template <> struct Tile<1> { static constexpr int X = 256, Y = 1, Z = 1; };
-template <> struct Tile<2> { static constexpr int X = 32, Y = 16, Z = 1; };
+template <> struct Tile<2> { static constexpr int X = 32, Y = 15, Z = 1; };  // 1007 faces per 256 threads
 template <> struct Tile<3> { static constexpr int X = 16, Y = 8, Z = 4; };
 
 template <int D> struct TileGeom {
@@ -299,7 +299,7 @@ __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
 }
 
 template <int D, int PREC, bool MULTID>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1)
     step_kernel(const __grid_constant__ StepArgs A) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
