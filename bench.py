@@ -261,13 +261,8 @@ CELL_OPS = 60 + 4 * 6 + 12
 
 
 def flop_counts(multid=True):
-    import ctypes
     from paper_1302_2132_gb300 import gks
-    L = gks.load()
-    c = (ctypes.c_longlong * 6)()
-    L.gks_face_op_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
-    L.gks_face_op_count(2, int(multid), 1, c)
-    return list(c)
+    return list(gks.face_op_count(2, multid, True))
 
 
 def oracle_sample(n_crop, nthreads):

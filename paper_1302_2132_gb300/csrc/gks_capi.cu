@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ 
   using R = typename PrecT<PREC>::R;
   __shared__ double red[kThreads / 32];
   const DevGrid& g = A.g;
+  const Consts<R> kc = make_consts<R>(g);
   R rmax = R(0);
   for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += (long)gridDim.x * blockDim.x) {
     R w[D + 2];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ 
     pos[2] = (int)(c / ((long)g.n[0] * g.n[1]));
     R h[D];
     for (int d = 0; d < D; ++d) h[d] = (R)g.w[d][pos[d] + 2];
-    rmax = fmax(rmax, cell_rate<D, R>(w, (R)g.gamma, h));
+    rmax = fmax(rmax, cell_rate<D, R>(w, kc.gamma, h));
   }
   const double m = block_max<double>((double)rmax, red);
   if (threadIdx.x == 0) atomic_max_nonneg(&A.ctrl->rate[A.slot], m);
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
   const DevGrid& g = A.g;
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
+  const Consts<R> kc = make_consts<R>(g);
   const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
   R Wn[nv * 3 * S2 * S3];
   const int NN = 3 * S2 * S3;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
     const bool on_axis = (di != 0) + (dj != 0) + (dk != 0) <= 1;
     R w[nv];
     if (on_axis) {
-      load_cell<D, PREC>(A, i + di, j + dj, k + dk, w);
+      load_cell<D, PREC>(A, kc, i + di, j + dj, k + dk, w);
     } else {
       for (int v = 0; v < nv; ++v) w[v] = R(1);
     }
@@ -212,11 +214,11 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
     f1 = ((const R*)A.f1)[c];
     if (g.turb_model != TURB_MUT) f2 = ((const R*)A.f2)[c];
   }
-  R val = tau_turb_cell<D, R>(g, Wn, NN, idx, strides, widths, pos, f1, f2);
+  R val = tau_turb_cell<D, R>(g.turb_model, kc, Wn, NN, idx, strides, widths, pos, f1, f2);
   if (what == 1) {  // rarefaction: (mu/p + tau_t) |div U|
     R w[nv];
     for (int v = 0; v < nv; ++v) w[v] = Wn[v * NN + idx];
-    const R p = pressure_of<R>(D, (R)g.gamma, w);
+    const R p = pressure_of<R>(D, kc.gamma, w);
     R div = R(0);
     for (int a = 0; a < D; ++a) {
       const R* wd = widths[a];
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
       const int im = idx - strides[a], ip = idx + strides[a];
       div += (Wn[(1 + a) * NN + ip] / Wn[ip] - Wn[(1 + a) * NN + im] / Wn[im]) / dist;
     }
-    val = ((R)g.mu / p + val) * g_abs(div);
+    val = (kc.mu / p + val) * g_abs(div);
   }
   if (out_dtype == GKS_F64)
     ((double*)out)[c] = (double)val;

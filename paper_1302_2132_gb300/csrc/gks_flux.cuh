@@ -426,18 +426,32 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
     F[m] = T(0);
   }
 
-  // one side of the initial state: Eq. initialf0, slopes a (normal), b (tangential) and A
-  auto side = [&](const Maxw<D, T>& g, const Trans<D, T>& ts, const T* half, const T* sn, const T (*st)[D + 2]) {
-    T a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
+  // The two sides of the initial state, one loop body (sd = 0: left Maxwellian on u > 0, sd = 1:
+  // right Maxwellian on u < 0): Eq. initialf0 slopes a (normal), b (tangential), A; their parts of
+  // the Abar right-hand side and of the flux.
+#pragma unroll 1
+  for (int sd = 0; sd < 2; ++sd) {
+    const Maxw<D, T> g = sd ? gr : gl;
+    Trans<D, T> ts;
+    {
+      const T* pa = &trl.m1[0];
+      const T* pb = &trr.m1[0];
+      T* pt = &ts.m1[0];
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(Trans<D, T>) / sizeof(T)); ++q) pt[q] = sd ? pb[q] : pa[q];
+    }
+    T half[7], a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) half[n] = sd ? rN[n] : lP[n];
     const T ir = T(1) / g.rho;
 #pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = sn[m] * ir;
+    for (int m = 0; m < nv; ++m) r[m] = (sd ? sr[m] : sl[m]) * ir;
     slope<D, T>(g, bK, r, a);
     if (MULTID) {
 #pragma unroll
       for (int q = 0; q < D - 1; ++q) {
 #pragma unroll
-        for (int m = 0; m < nv; ++m) r[m] = st[q][m] * ir;
+        for (int m = 0; m < nv; ++m) r[m] = (sd ? tr[q][m] : tl[q][m]) * ir;
         slope<D, T>(g, bK, r, b[q]);
       }
     }
@@ -473,33 +487,31 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
         amom<D, T>(half, ts, 1, q, b[q], s4f, F);
       }
     }
-  };
-  side(gl, trl, lP, sl, tl);
-  side(gr, trr, rN, sr, tr);
+  }
 
   // equilibrium g0: Eq. eqlgform slopes from W_j -> w0 -> W_{j+1} (and the mean tangential slope)
   Trans<D, T> tr0;
   transverse<D, T>(g0, K, tr0);
-  T oF[7], oP[7], oN[7];
+  T oF[7], oP[7];
   u_full<D, T>(g0, oF);
   u_half<D, T>(g0, T(1), oP);
-#pragma unroll
-  for (int n = 0; n < 7; ++n) oN[n] = oF[n] - oP[n];
   {
-    T r[nv], ab[nv];
     const T fl = i0 / dxl, fr = i0 / dxr;
     const T s1f = Tc[1] * g0.rho;
+#pragma unroll 1
+    for (int sd = 0; sd < 2; ++sd) {
+      // sd = 0: abar_l on u > 0; sd = 1: abar_r on u < 0 (table = full line minus u > 0)
+      T r[nv], ab[nv], half[7];
 #pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = (w0[m] - cl[m]) * fl;
-    slope<D, T>(g0, bK, r, ab);
-    amom<D, T>(oP, tr0, 1, -1, ab, r1, rhs);
-    amom<D, T>(oP, tr0, 2, -1, ab, s1f, F);
+      for (int m = 0; m < nv; ++m) r[m] = sd ? (cr[m] - w0[m]) * fr : (w0[m] - cl[m]) * fl;
 #pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = (cr[m] - w0[m]) * fr;
-    slope<D, T>(g0, bK, r, ab);
-    amom<D, T>(oN, tr0, 1, -1, ab, r1, rhs);
-    amom<D, T>(oN, tr0, 2, -1, ab, s1f, F);
+      for (int n = 0; n < 7; ++n) half[n] = sd ? oF[n] - oP[n] : oP[n];
+      slope<D, T>(g0, bK, r, ab);
+      amom<D, T>(half, tr0, 1, -1, ab, r1, rhs);
+      amom<D, T>(half, tr0, 2, -1, ab, s1f, F);
+    }
     if (MULTID) {
+      T r[nv], ab[nv];
 #pragma unroll
       for (int q = 0; q < D - 1; ++q) {
 #pragma unroll

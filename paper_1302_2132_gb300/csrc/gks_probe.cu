@@ -1,0 +1,74 @@
+// Throughput probe of the FP32 and FP64 FMA pipes (independent FMA chains, every SM busy); context
+// for the ALU roofline of the step kernel.  Reads and writes only its own small buffers.
+#include <cuda_runtime.h>
+
+#include "gks.h"
+
+namespace {
+
+constexpr int kIters = 4096;
+
+__global__ void fma32_kernel(float* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0f + 1e-9f * (float)(i + k);
+  const float m = 0.999999f, c = 1e-7f;
+#pragma unroll 16
+  for (int it = 0; it < kIters; ++it)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], m, c);
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[i] = s;
+}
+
+__global__ void fma64_kernel(double* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = 1.0 + 1e-12 * (double)(i + k);
+  const double m = 0.9999999, c = 1e-9;
+#pragma unroll 16
+  for (int it = 0; it < kIters / 8; ++it)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = fma(a[k], m, c);
+  out[i] = a[0] + a[1] + a[2] + a[3];
+}
+
+}  // namespace
+
+extern "C" gks_status gks_probe_alu(double* fp32_tflops, double* fp64_tflops) {
+  int dev;
+  cudaDeviceProp p;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return GKS_ECUDA;
+  const int threads = 256, blocks = p.multiProcessorCount * 8, n = threads * blocks;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)n * sizeof(double)) != cudaSuccess) return GKS_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms = 0.0f;
+  fma32_kernel<<<blocks, threads>>>((float*)buf, n);
+  cudaEventRecord(e0);
+  fma32_kernel<<<blocks, threads>>>((float*)buf, n);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (fp32_tflops) *fp32_tflops = 2.0 * 8.0 * kIters * (double)n / (ms * 1e-3) / 1e12;
+  fma64_kernel<<<blocks, threads>>>((double*)buf, n);
+  cudaEventRecord(e0);
+  fma64_kernel<<<blocks, threads>>>((double*)buf, n);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (fp64_tflops) *fp64_tflops = 2.0 * 4.0 * (kIters / 8) * (double)n / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaGetLastError();
+  cudaFree(buf);
+  return e == cudaSuccess ? GKS_OK : GKS_ECUDA;
+}

@@ -81,6 +81,25 @@ struct StepArgs {
   int resid;   // accumulate residual norms in this step
 };
 
+// Gas and model constants in the arithmetic type (converted once per CTA).
+template <class R> struct Consts {
+  R gamma, mu, C_mu, beta_star, T_wall, bK, K, C_a;
+};
+
+template <class R>
+__device__ __forceinline__ Consts<R> make_consts(const DevGrid& g) {
+  Consts<R> c;
+  c.gamma = (R)g.gamma;
+  c.mu = (R)g.mu;
+  c.C_mu = (R)g.C_mu;
+  c.beta_star = (R)g.beta_star;
+  c.T_wall = (R)g.T_wall;
+  c.bK = (R)g.bK;
+  c.K = (R)g.K;
+  c.C_a = (R)g.C_a;
+  return c;
+}
+
 template <int PREC> struct PrecT;
 template <> struct PrecT<PREC_F64> { using R = double; using S = double; };
 template <> struct PrecT<PREC_F32> { using R = float; using S = float; };
@@ -99,8 +118,8 @@ __device__ __forceinline__ R pressure_of(int D, R gamma, const R* w) {
 
 // Isothermal no-slip wall image: velocity reversed, same pressure, T_g = T_w^2 / T_i (T = p/rho).
 template <int D, class R>
-__device__ __forceinline__ void wall_image(const DevGrid& g, R* w) {
-  const R gamma = (R)g.gamma, Tw = (R)g.T_wall;
+__device__ __forceinline__ void wall_image(const Consts<R>& k, R* w) {
+  const R gamma = k.gamma, Tw = k.T_wall;
   R U[D], q = R(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) U[i] = w[1 + i] / w[0];
@@ -129,7 +148,8 @@ __device__ __forceinline__ void load_stored(const StepArgs& A, long c, typename 
 // State of cell (i, j, k), possibly outside the grid: ghost cells follow the boundary rules, the
 // transform of the last axis applied first.
 template <int D, int PREC>
-__device__ void load_cell(const StepArgs& A, int i, int j, int k, typename PrecT<PREC>::R* out) {
+__device__ void load_cell(const StepArgs& A, const Consts<typename PrecT<PREC>::R>& kc, int i, int j, int k,
+                          typename PrecT<PREC>::R* out) {
   using R = typename PrecT<PREC>::R;
   const DevGrid& g = A.g;
   int c[3] = {i, j, k}, xf[3] = {0, 0, 0}, side[3] = {0, 0, 0};
@@ -164,7 +184,7 @@ __device__ void load_cell(const StepArgs& A, int i, int j, int k, typename PrecT
 #pragma unroll
   for (int a = D - 1; a >= 0; --a) {
     if (xf[a] == 1) {
-      wall_image<D, R>(g, out);
+      wall_image<D, R>(kc, out);
     } else if (xf[a] == 2) {
       long off = 0, stride = 1;
 #pragma unroll
@@ -200,15 +220,15 @@ __device__ __forceinline__ R load_field(const StepArgs& A, const void* f, int D,
 // Turbulent part of the relaxation time of one cell (Eqs. tauttrivial, tautchen, tautchenadjusted
 // with T = p/rho); S = sqrt(2 S_ij S_ij) from central differences of the velocity.
 template <int D, class R>
-__device__ __forceinline__ R tau_turb_cell(const DevGrid& g, const R* Ws, int stride_v, int idx,
+__device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, const R* Ws, int stride_v, int idx,
                                            const int* strides, const R* const* widths, const int* pos,
                                            R f1, R f2) {
-  if (g.turb_model == TURB_NONE) return R(0);
+  if (turb_model == TURB_NONE) return R(0);
   R w[D + 2];
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) w[v] = Ws[v * stride_v + idx];
-  const R p = pressure_of<R>(D, (R)g.gamma, w);
-  if (g.turb_model == TURB_MUT) return f1 / p;
+  const R p = pressure_of<R>(D, kc.gamma, w);
+  if (turb_model == TURB_MUT) return f1 / p;
   if (!(f1 > R(0)) || !(f2 > R(0))) return R(0);
   R grad[D][D];
 #pragma unroll
@@ -231,12 +251,12 @@ __device__ __forceinline__ R tau_turb_cell(const DevGrid& g, const R* Ws, int st
     }
   const R S = g_sqrt(R(2) * s2);
   R nu, eta;
-  if (g.turb_model == TURB_KEPS) {
-    nu = (R)g.C_mu * f1 * f1 / f2;
+  if (turb_model == TURB_KEPS) {
+    nu = kc.C_mu * f1 * f1 / f2;
     eta = S * f1 / f2;
   } else {
     nu = f1 / f2;
-    eta = S / ((R)g.beta_star * f2);
+    eta = S / (kc.beta_star * f2);
   }
   return w[0] * nu / (p * g_sqrt(R(1) + eta * eta));
 }
@@ -324,13 +344,22 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
   const int oz = D >= 3 ? (b / (tiles_x * tiles_y)) * Z : 0;
   const int tid = threadIdx.x;
 
-  const double dt_d = step_dt(A);
-  if (tid == 0 && b == 0) {
-    Ctrl* c = A.ctrl;
-    c->t[A.tslot ^ 1] = c->t[A.tslot] + dt_d;
-    c->rate[(A.slot + 2) % 3] = 0ull;
-    c->last_dt = dt_d;
+  __shared__ double s_dt;
+  __shared__ Consts<R> s_k;
+  if (tid == 0) {
+    const double dtv = step_dt(A);
+    s_dt = dtv;
+    s_k = make_consts<R>(A.g);
+    if (b == 0) {
+      Ctrl* c = A.ctrl;
+      c->t[A.tslot ^ 1] = c->t[A.tslot] + dtv;
+      c->rate[(A.slot + 2) % 3] = 0ull;
+      c->last_dt = dtv;
+    }
   }
+  __syncthreads();
+  const double dt_d = s_dt;
+  const Consts<R> kc = s_k;
   if (dt_d == 0.0) {  // t_end reached: carry the state over
     for (int l = tid; l < G::NC; l += kThreads) {
       const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
@@ -350,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
   for (int l = tid; l < G::NH; l += kThreads) {
     const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
     R w[nv];
-    load_cell<D, PREC>(A, ox + hi - 2, D >= 2 ? oy + hj - 2 : 0, D >= 3 ? oz + hk - 2 : 0, w);
+    load_cell<D, PREC>(A, kc, ox + hi - 2, D >= 2 ? oy + hj - 2 : 0, D >= 3 ? oz + hk - 2 : 0, w);
 #pragma unroll
     for (int v = 0; v < nv; ++v) Ws[v * G::NH + l] = w[v];
   }
@@ -380,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
         if (g.turb_model != TURB_MUT) f2 = load_field<R>(A, A.f2, D, gi, gj, gk);
       }
       const int pos[3] = {hi, hj, hk};
-      taus[l] = tau_turb_cell<D, R>(g, Ws, G::NH, idx, strides, widths, pos, f1, f2);
+      taus[l] = tau_turb_cell<D, R>(g.turb_model, kc, Ws, G::NH, idx, strides, widths, pos, f1, f2);
     }
   }
   __syncthreads();
@@ -388,11 +417,11 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
   // ---- fluxes of every face of the tile ----------------------------------------------------
   {
     Gas<R> gas;
-    gas.bK = (R)g.bK;
-    gas.K = (R)g.K;
-    gas.mu = (R)g.mu;
-    gas.C_a = (R)g.C_a;
-    const R gamma = (R)g.gamma;
+    gas.bK = kc.bK;
+    gas.K = kc.K;
+    gas.mu = kc.mu;
+    gas.C_a = kc.C_a;
+    const R gamma = kc.gamma;
     for (int f = tid; f < G::NF; f += kThreads) {
       int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
       if (f < G::NFX) {
@@ -568,9 +597,9 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
         }
       }
     }
-    const R p = pressure_of<R>(D, (R)g.gamma, wn);
+    const R p = pressure_of<R>(D, kc.gamma, wn);
     if (!(wn[0] > R(0)) || !(p > R(0))) bad = 1u;
-    rmax = fmax(rmax, cell_rate<D, R>(wn, (R)g.gamma, h));
+    rmax = fmax(rmax, cell_rate<D, R>(wn, kc.gamma, h));
   }
   const double bmax = block_max<double>((double)rmax, red);
   if (tid == 0) atomic_max_nonneg(&A.ctrl->rate[(A.slot + 1) % 3], bmax);

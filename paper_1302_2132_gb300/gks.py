@@ -84,6 +84,10 @@ def load():
     L.gks_last_error.argtypes = [H]
     L.gks_last_error.restype = ctypes.c_char_p
     L.gks_face_record_len.argtypes = [_I]
+    L.gks_probe_alu.argtypes = [_PD, _PD]
+    L.gks_probe_alu.restype = _I
+    L.gks_face_op_count.argtypes = [_I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_face_op_count.restype = _I
     L.gks_face_flux.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _V, ctypes.c_long, _V, _V, _V]
     for name in ("gks_create", "gks_set_state", "gks_get_state", "gks_set_turbulence", "gks_compute_dt",
                  "gks_step", "gks_get_time", "gks_set_time", "gks_residual", "gks_status_word",
@@ -268,6 +272,22 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def probe_alu():
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    a, b = _D(), _D()
+    st = load().gks_probe_alu(ctypes.byref(a), ctypes.byref(b))
+    if st != OK:
+        raise GksError(st, "gks_probe_alu failed")
+    return a.value, b.value
+
+
+def face_op_count(dim, expand=True, with_recon=True):
+    """Static per-face operation count of the flux code: (add, mul, div, sqrt, exp, erfc)."""
+    c = (ctypes.c_longlong * 6)()
+    load().gks_face_op_count(dim, int(expand), int(with_recon), c)
+    return tuple(c)
 
 
 def face_record_len(dim):

@@ -325,6 +325,7 @@ def test_full_size_2d_turbulence_sampled_cells(prec):
     errs = np.array(errs)
     # FP32 flux: the per-step increment is accurate to about 1e-4 relative
     assert np.median(errs) < (1e-9 if prec == "fp64" else 1e-3), np.median(errs)
-    # conservation at full size: total of every variable is unchanged
+    # conservation at full size: total of every variable is unchanged, up to the rounding of the
+    # per-cell increments (double, or single precision for the FP32 flux)
     W0 = oracle_case(spec, **kw).prim_to_cons(spec["prim"].ravel()).reshape(4, -1).sum(axis=1) * h * h
-    assert np.all(np.abs(tot - W0) <= 1e-11 * (np.abs(W0) + 1.0))
+    assert np.all(np.abs(tot - W0) <= (1e-11 if prec == "fp64" else 1e-9) * (np.abs(W0) + 1.0))
