@@ -24,12 +24,44 @@ template <class T> GKS_FN T g_sqrt(T x);
 template <> GKS_FN float g_sqrt<float>(float x) { return sqrtf(x); }
 template <> GKS_FN double g_sqrt<double>(double x) { return sqrt(x); }
 template <class T> GKS_FN T g_exp(T x);
+#ifdef GKS_HOST_COUNT
 template <> GKS_FN float g_exp<float>(float x) { return expf(x); }
+#endif
 template <> GKS_FN double g_exp<double>(double x) { return exp(x); }
 template <class T> GKS_FN T g_erfc(T x);
+#ifdef GKS_HOST_COUNT
 template <> GKS_FN float g_erfc<float>(float x) { return erfcf(x); }
+#endif
 template <> GKS_FN double g_erfc<double>(double x) { return erfc(x); }
 template <class T> GKS_FN T g_abs(T x) { return x < T(0) ? -x : x; }
+
+// Quotient and reciprocal: IEEE in double precision (the FP64 path matches the oracle to 1e-12);
+// in single precision the hardware reciprocal (about 1 ulp), which avoids the multi-instruction
+// IEEE sequence and its slow-path branch.  The FP32 form's tolerances are far above this error.
+template <class T> GKS_FN T g_div(T a, T b) { return a / b; }
+template <class T> GKS_FN T g_rcp(T x) { return T(1) / x; }
+#ifndef GKS_HOST_COUNT
+template <> GKS_FN float g_div<float>(float a, float b) { return __fdividef(a, b); }
+template <> GKS_FN float g_rcp<float>(float x) { return __fdividef(1.0f, x); }
+template <> GKS_FN float g_exp<float>(float x) { return __expf(x); }
+
+// Single-precision erfc from the Chebyshev-fitted form of Press, Teukolsky, Vetterling and Flannery
+// (Numerical Recipes, 2nd ed., section 6.2): for z = |x|, t = 1/(1 + z/2),
+// erfc(z) = t exp(-z^2 + P(t)) with a degree-9 polynomial P, fractional error below 1.2e-7;
+// erfc(-z) = 2 - erfc(z).
+GKS_FN float erfc_cheb(float x) {
+  const float z = fabsf(x);
+  const float t = __fdividef(1.0f, 1.0f + 0.5f * z);
+  const float c[10] = {-1.26551223f, 1.00002368f, 0.37409196f, 0.09678418f, -0.18628806f,
+                       0.27886807f, -1.13520398f, 1.48851587f, -0.82215223f, 0.17087277f};
+  float p = c[9];
+#pragma unroll
+  for (int i = 8; i >= 0; --i) p = fmaf(p, t, c[i]);
+  const float r = t * __expf(p - z * z);
+  return x >= 0.0f ? r : 2.0f - r;
+}
+template <> GKS_FN float g_erfc<float>(float x) { return erfc_cheb(x); }
+#endif
 
 constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
 
@@ -60,11 +92,11 @@ GKS_FN Maxw<D, T> maxwellian(const T* w, T bK) {
   T q = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    g.U[i] = w[1 + i] / w[0];
+    g.U[i] = g_div(w[1 + i], w[0]);
     q += g.U[i] * g.U[i];
   }
-  g.lam = bK * w[0] / (T(4) * (w[D + 1] - T(0.5) * w[0] * q));
-  g.il = T(0.5) / g.lam;
+  g.lam = g_div(bK * w[0], T(4) * (w[D + 1] - T(0.5) * w[0] * q));
+  g.il = g_div(T(0.5), g.lam);
   return g;
 }
 
@@ -196,7 +228,7 @@ GKS_FN void u_half(const Maxw<D, T>& g, T sgn, T* u) {
   const T sl = g_sqrt(g.lam);
   const T z = sl * g.U[0];
   u[0] = T(0.5) * g_erfc(-sgn * z);
-  u[1] = g.U[0] * u[0] + sgn * T(0.5) * g_exp(-z * z) * T(kInvSqrtPi) / sl;
+  u[1] = g.U[0] * u[0] + g_div(sgn * T(0.5) * g_exp(-z * z) * T(kInvSqrtPi), sl);
   recur<7>(g.U[0], g.il, u);
 }
 
@@ -252,16 +284,16 @@ GKS_FN R limiter(int lim, R a, R b) {
     const R ma = g_abs(a), mb = g_abs(b);
     return R(0.5) * (sa + sb) * (ma < mb ? ma : mb);
   }
-  return (a * b > R(0)) ? R(2) * a * b / (a + b) : R(0);
+  return (a * b > R(0)) ? g_div(R(2) * a * b, a + b) : R(0);
 }
 
 // MUSCL on one variable at the face between cells 1 and 2 of the stencil s0..s3 with widths
 // h0..h3: limited slopes of cells 1 and 2 and the face values left and right.
 template <class R>
 GKS_FN void muscl(int lim, R s0, R s1, R s2, R s3, R h0, R h1, R h2, R h3, R& wl, R& wr, R& sl, R& sr) {
-  const R dm = (s1 - s0) / (R(0.5) * (h0 + h1));
-  const R dc = (s2 - s1) / (R(0.5) * (h1 + h2));
-  const R dp = (s3 - s2) / (R(0.5) * (h2 + h3));
+  const R dm = g_div(s1 - s0, R(0.5) * (h0 + h1));
+  const R dc = g_div(s2 - s1, R(0.5) * (h1 + h2));
+  const R dp = g_div(s3 - s2, R(0.5) * (h2 + h3));
   sl = limiter<R>(lim, dm, dc);
   sr = limiter<R>(lim, dc, dp);
   wl = s1 + R(0.5) * h1 * sl;
@@ -281,7 +313,7 @@ GKS_FN void slope(const Maxw<D, T>& g, T bK, const T* rhs, T* a) {
   }
   const T c = q + bK * g.il;  // |U|^2 + bK / (2 lambda)
   const T RE = T(2) * rhs[D + 1] - c * rhs[0];
-  const T aE = (T(4) * g.lam * g.lam / bK) * (RE - T(2) * UR);
+  const T aE = g_div(T(4) * g.lam * g.lam, bK) * (RE - T(2) * UR);
   T a0 = rhs[0] - T(0.5) * aE * c;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -332,7 +364,7 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
     r4 = r5 = T(0);
     return;
   }
-  const T x = dt / tau;
+  const T x = g_div(dt, tau);
   if (x < T(1)) {
     // series branch in double precision for either arithmetic type
     double p1, p2, p3, e;
@@ -361,9 +393,9 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
     Tc[3] = tq;
     Tc[4] = tau * dt * e - T(2) * tau * tq;
     Tc[5] = -tau * tq;
-    const T y = tau / dt;
+    const T y = g_div(tau, dt);
     const T yq = y * q;
-    const T inv = T(1) / (T(1) - yq);
+    const T inv = g_rcp(T(1) - yq);
     r1 = (T(2) * yq - (T(1) + e)) * inv;
     r4 = (e - T(2) * yq) * inv;
     r5 = -yq * inv;
@@ -408,7 +440,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
 
   // Eqs. relaxation time and taua: tau = mu/p0 + tau_t + C_a |p_r - p_l| / (p_r + p_l) dt
   const T p0 = g0.rho * g0.il, pl = gl.rho * gl.il, pr = gr.rho * gr.il;
-  const T tau = gas.mu / p0 + tau_t + gas.C_a * g_abs(pr - pl) / (pr + pl) * dt;
+  const T tau = g_div(gas.mu, p0) + tau_t + g_div(gas.C_a * g_abs(pr - pl), pr + pl) * dt;
   *tau_out = tau;
   T Tc[6], r1, r4, r5;
   time_coeffs<T>(dt, tau, Tc, r1, r4, r5);
@@ -416,7 +448,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
     r1 = T(-1);
     r4 = r5 = T(0);
   }
-  const T i0 = T(1) / g0.rho;
+  const T i0 = g_rcp(g0.rho);
 
   // Abar right-hand side (per unit rho0) and flux, accumulated region by region
   T rhs[nv];
@@ -443,7 +475,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
     T half[7], a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
 #pragma unroll
     for (int n = 0; n < 7; ++n) half[n] = sd ? rN[n] : lP[n];
-    const T ir = T(1) / g.rho;
+    const T ir = g_rcp(g.rho);
 #pragma unroll
     for (int m = 0; m < nv; ++m) r[m] = (sd ? sr[m] : sl[m]) * ir;
     slope<D, T>(g, bK, r, a);
@@ -496,7 +528,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
   u_full<D, T>(g0, oF);
   u_half<D, T>(g0, T(1), oP);
   {
-    const T fl = i0 / dxl, fr = i0 / dxr;
+    const T fl = g_div(i0, dxl), fr = g_div(i0, dxr);
     const T s1f = Tc[1] * g0.rho;
 #pragma unroll 1
     for (int sd = 0; sd < 2; ++sd) {

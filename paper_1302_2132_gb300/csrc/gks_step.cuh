@@ -113,7 +113,7 @@ template <class R>
 __device__ __forceinline__ R pressure_of(int D, R gamma, const R* w) {
   R q = R(0);
   for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
-  return (gamma - R(1)) * (w[D + 1] - R(0.5) * q / w[0]);
+  return (gamma - R(1)) * (w[D + 1] - R(0.5) * g_div(q, w[0]));
 }
 
 // Isothermal no-slip wall image: velocity reversed, same pressure, T_g = T_w^2 / T_i (T = p/rho).
@@ -122,18 +122,18 @@ __device__ __forceinline__ void wall_image(const Consts<R>& k, R* w) {
   const R gamma = k.gamma, Tw = k.T_wall;
   R U[D], q = R(0);
 #pragma unroll
-  for (int i = 0; i < D; ++i) U[i] = w[1 + i] / w[0];
+  for (int i = 0; i < D; ++i) U[i] = g_div(w[1 + i], w[0]);
   const R p = pressure_of<R>(D, gamma, w);
-  const R Ti = p / w[0];
-  const R Tg = Tw * Tw / Ti;
-  const R rho = p / Tg;
+  const R Ti = g_div(p, w[0]);
+  const R Tg = g_div(Tw * Tw, Ti);
+  const R rho = g_div(p, Tg);
   w[0] = rho;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     w[1 + i] = rho * -U[i];
     q += U[i] * U[i];
   }
-  w[D + 1] = p / (gamma - R(1)) + R(0.5) * rho * q;
+  w[D + 1] = g_div(p, gamma - R(1)) + R(0.5) * rho * q;
 }
 
 template <int D, int PREC>
@@ -228,7 +228,7 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) w[v] = Ws[v * stride_v + idx];
   const R p = pressure_of<R>(D, kc.gamma, w);
-  if (turb_model == TURB_MUT) return f1 / p;
+  if (turb_model == TURB_MUT) return g_div(f1, p);
   if (!(f1 > R(0)) || !(f2 > R(0))) return R(0);
   R grad[D][D];
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
     const R rm = Ws[im], rp = Ws[ip];
 #pragma unroll
     for (int b = 0; b < D; ++b)
-      grad[a][b] = (Ws[(1 + b) * stride_v + ip] / rp - Ws[(1 + b) * stride_v + im] / rm) / dist;
+      grad[a][b] = g_div(g_div(Ws[(1 + b) * stride_v + ip], rp) - g_div(Ws[(1 + b) * stride_v + im], rm), dist);
   }
   R s2 = R(0);
 #pragma unroll
@@ -252,13 +252,13 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
   const R S = g_sqrt(R(2) * s2);
   R nu, eta;
   if (turb_model == TURB_KEPS) {
-    nu = kc.C_mu * f1 * f1 / f2;
-    eta = S * f1 / f2;
+    nu = g_div(kc.C_mu * f1 * f1, f2);
+    eta = g_div(S * f1, f2);
   } else {
-    nu = f1 / f2;
-    eta = S / (kc.beta_star * f2);
+    nu = g_div(f1, f2);
+    eta = g_div(S, kc.beta_star * f2);
   }
-  return w[0] * nu / (p * g_sqrt(R(1) + eta * eta));
+  return g_div(w[0] * nu, p * g_sqrt(R(1) + eta * eta));
 }
 
 __device__ __forceinline__ double step_dt(const StepArgs& A) {
@@ -311,16 +311,16 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <int D, class R>
 __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
   const R p = pressure_of<R>(D, gamma, w);
-  const R cs = g_sqrt(gamma * p / w[0]);
+  const R cs = g_sqrt(g_div(gamma * p, w[0]));
   R r = R(0);
 #pragma unroll
-  for (int d = 0; d < D; ++d) r += (g_abs(w[1 + d] / w[0]) + cs) / h[d];
+  for (int d = 0; d < D; ++d) r += g_div(g_abs(g_div(w[1 + d], w[0])) + cs, h[d]);
   return r;
 }
 
+// One tile of one step: every thread of the CTA calls it with the same arguments.
 template <int D, int PREC, bool MULTID>
-__global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1)
-    step_kernel(const __grid_constant__ StepArgs A) {
+__device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
   using G = TileGeom<D>;
@@ -338,7 +338,6 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
   const DevGrid& g = A.g;
   const int tiles_x = (g.n[0] + X - 1) / X;
   const int tiles_y = D >= 2 ? (g.n[1] + Y - 1) / Y : 1;
-  const int b = blockIdx.x;
   const int ox = (b % tiles_x) * X;
   const int oy = D >= 2 ? ((b / tiles_x) % tiles_y) * Y : 0;
   const int oz = D >= 3 ? (b / (tiles_x * tiles_y)) * Z : 0;
@@ -496,8 +495,8 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
             const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
             const R* pc = Ws + sv * G::NH + hc;
             const R* pl = pc - sn;
-            tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) / hm, (pl[stt] - pl[0]) / hp);
-            tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) / hm, (pc[stt] - pc[0]) / hp);
+            tl[s][v] = limiter<R>(g.limiter, g_div(pl[0] - pl[-stt], hm), g_div(pl[stt] - pl[0], hp));
+            tr[s][v] = limiter<R>(g.limiter, g_div(pc[0] - pc[-stt], hm), g_div(pc[stt] - pc[0], hp));
           }
         }
       }
@@ -568,8 +567,8 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
       } else {
         R inc = R(0);
 #pragma unroll
-        for (int d = 0; d < D; ++d) inc -= (Fs[v * G::NF + fp[d]] - Fs[v * G::NF + fm[d]]) / h[d];
-        double wd;
+        for (int d = 0; d < D; ++d) inc -= g_div(Fs[v * G::NF + fp[d]] - Fs[v * G::NF + fm[d]], h[d]);
+        double wd = 0.0;
         if (PREC == PREC_F32) {
           // (hi, lo) += inc with an error-free sum, then renormalise
           const float hi = ((const float*)A.Win)[gidx], lo = A.Win_lo[gidx];
@@ -582,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
           ((float*)A.Wout)[gidx] = nhi;
           A.Wout_lo[gidx] = nlo;
           wn[v] = nhi;
-          wd = (double)nhi + (double)nlo;
+          if (A.resid) wd = (double)nhi + (double)nlo;
         } else {
           const double w = ((const double*)A.Win)[gidx] + (double)inc;
           ((double*)A.Wout)[gidx] = w;
@@ -614,6 +613,63 @@ __global__ void __launch_bounds__(kThreads, (PREC != PREC_F64 && D <= 2) ? 2 : 1
       if (tid == 0) atomic_max_nonneg(&A.ctrl->linf[v], m);
     }
   }
+}
+
+template <int D> constexpr int min_blocks(int prec) { return (prec != PREC_F64 && D <= 2) ? 2 : 1; }
+
+template <int D, int PREC, bool MULTID>
+__global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) step_kernel(const __grid_constant__ StepArgs A) {
+  step_tile<D, PREC, MULTID>(A, blockIdx.x);
+}
+
+// ---- batches of independent solves --------------------------------------------------------------
+// A batch advances many solves of one dimension and arithmetic by one step per launch.  The
+// arguments of a solve depend on the batch step k only through k mod 6 (buffer k mod 2, rate slot
+// k mod 3), so each solve carries six precomputed argument sets.  A solve takes part while
+// k < stop_at; afterwards its state rests in buffer stop_at mod 2.
+struct BatchSolve {
+  StepArgs args[6];
+  long long stop_at;
+  int tiles;
+  int pad;
+};
+
+struct BatchArgs {
+  const BatchSolve* solves;
+  const int2* items;        // (solve, tile) work items
+  const int* nitems;        // device: number of valid items
+  long long* counter;       // batch step index, two slots
+  int phase;                // k mod 6 of the launch (fixed by the position in a captured chunk)
+};
+
+// Persistent CTAs stride over the work items of one step.
+template <int D, int PREC, bool MULTID>
+__global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) batch_step_kernel(const __grid_constant__ BatchArgs B) {
+  const int tslot = B.phase & 1;
+  const long long k = B.counter[tslot];
+  if (blockIdx.x == 0 && threadIdx.x == 0) B.counter[tslot ^ 1] = k + 1;
+  const int n = *B.nitems;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = B.items[it];
+    const BatchSolve& S = B.solves[w.x];
+    if (k < S.stop_at) step_tile<D, PREC, MULTID>(S.args[B.phase], w.y);
+    __syncthreads();
+  }
+}
+
+template <int D, int PREC, bool MULTID>
+void launch_batch(const BatchArgs& B, int nblocks, cudaStream_t s) {
+  using R = typename PrecT<PREC>::R;
+  const size_t sm = TileGeom<D>::template smem_bytes<R>();
+  batch_step_kernel<D, PREC, MULTID><<<nblocks, kThreads, sm, s>>>(B);
+}
+
+template <int D, int PREC, bool MULTID>
+cudaError_t prepare_batch() {
+  using R = typename PrecT<PREC>::R;
+  const size_t sm = TileGeom<D>::template smem_bytes<R>();
+  return cudaFuncSetAttribute(batch_step_kernel<D, PREC, MULTID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sm);
 }
 
 template <int D, int PREC, bool MULTID>
