@@ -165,6 +165,29 @@ gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, doub
  * are not counted.  Used to state the algorithmic FLOPs behind the roofline figures. */
 int gks_face_op_count(int dim, int expand, int with_recon, long long* counts);
 
+/* CFL time step, as gks_compute_dt computes it, of a caller-held FP64 state on a uniform grid, for
+ * callers that cannot allocate device memory (for example while another allocator holds all of
+ * the device's free memory, or on a path where the implicit synchronisation of cudaMalloc is not
+ * acceptable).  The paper has no counterpart: this is an allocation-free variant of the library's
+ * CFL reduction.
+ *   dim, n[dim], h[dim]  grid dimension, cells and (uniform) cell width per axis
+ *   W        device, SoA conservative state [nv][cells] in double (caller-owned, read only)
+ *   dt_out   host: cfl / max_cells sum_d (|U_d| + c) / h_d
+ * No device memory is allocated: the scratch is a static device array inside the library (about
+ * 8 KB, held on every device that loads the library until the process exits), which limits W to
+ * GKS_NOALLOC_MAX_CELLS cells (larger states return GKS_EINVAL).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array and the last call's contents stay in it, so calls that
+ * overlap on the GPU (concurrent streams or threads) race and must be serialised by the caller.
+ * Synchronises cuda_stream (NULL: the legacy default stream). */
+#define GKS_NOALLOC_MAX_CELLS (16384L * 1024L)
+gks_status gks_cfl_dt_noalloc(int dim, const int* n, const double* h, double gamma, const double* W,
+                              double cfl, double* dt_out, void* cuda_stream);
+
+/* Measured FMA throughput of the current device for FP32 and FP64 (independent FMA chains on every
+ * SM, CUDA events), in TFLOP/s: context for the arithmetic roofline.  Synchronises the device. */
+gks_status gks_probe_alu(double* fp32_tflops, double* fp64_tflops);
+
 #ifdef __cplusplus
 }
 #endif
