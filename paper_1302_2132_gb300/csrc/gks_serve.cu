@@ -1,0 +1,593 @@
+// Serving many independent solves on one GPU with continuous batching.
+//
+// Requests (1D or 2D grids of any size up to a limit, any number of steps) are admitted in arrival
+// order while the device arena has room for their state (footprint admission).  Admitted solves
+// stay resident and advance together: each batch step is one persistent CTA launch per group
+// (1D, 2D directional, 2D multi-dimensional) over a work table of (solve, tile) items, and chunks of
+// steps are replayed as captured CUDA graphs.  Between chunks a host worker thread retires solves
+// whose steps are done (their final state is copied to the host and their memory freed) and admits
+// waiting requests, so requests that arrive while others run join the next chunk.  Every solve's
+// arithmetic is the single-solve step (same tile kernel, its own CFL time step), so its result does
+// not depend on what else is in the batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gks.h"
+#include "gks_aux.cuh"
+#include "gks_dispatch.h"
+#include "gks_step.cuh"
+
+using namespace gks;
+using namespace gks::aux;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t round_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+inline double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over offsets of a device arena.
+class Arena {
+ public:
+  void init(size_t cap) {
+    free_.clear();
+    free_[0] = cap;
+    used_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = round_up(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes, start = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[start] = rest;
+      used_ += bytes;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = round_up(bytes);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0;
+};
+
+enum { REQ_PENDING = 0, REQ_ACTIVE = 1, REQ_DONE = 2, REQ_FAILED = 3 };
+enum { GROUP_1D = 0, GROUP_2D = 1, GROUP_2D_MULTID = 2, NGROUPS = 3 };
+
+struct Req {
+  long long id = 0;
+  gks_request q;
+  std::vector<double> prim, result;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int status = REQ_PENDING;
+  int slot = -1, group = 0, tiles = 0;
+  size_t off = 0, bytes = 0;
+  long long stop_at = 0;
+  long ncell = 0;
+};
+
+}  // namespace
+
+struct gks_server {
+  int dev = 0, prec = PREC_F32, chunk = 24, max_slots = 0;
+  long max_cells = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* arena = nullptr;
+  size_t capacity = 0;
+  Arena alloc;
+  BatchSolve* d_solves = nullptr;
+  BatchSolve* h_solve_stage = nullptr;  // pinned
+  int2* d_items[NGROUPS] = {nullptr, nullptr, nullptr};
+  int* d_nitems = nullptr;
+  int2* h_items = nullptr;  // pinned, NGROUPS * max_items
+  int* h_nitems = nullptr;  // pinned
+  int max_items = 0;
+  long long* d_counter = nullptr;
+  double* d_stage = nullptr;  // device staging for one state
+  double* h_stage = nullptr;  // pinned host staging for one state
+  std::vector<int> free_slots;
+  long long step = 0;
+  std::deque<Req*> pending;
+  std::vector<Req*> active;
+  std::map<long long, Req*> reqs;
+  long long next_id = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread worker;
+  bool stop = false;
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  int persistent_blocks = 0;
+  // statistics
+  long long completed = 0;
+  double t_first_submit = 0, t_last_done = 0, busy_s = 0;
+  std::vector<double> latencies;
+  std::string err;
+};
+
+namespace {
+
+size_t state_bytes(int prec, int nv, long ncell) {
+  return prec == PREC_F32 ? 4 * sizeof(float) * nv * ncell : 2 * sizeof(double) * nv * ncell;
+}
+
+size_t footprint(int prec, const Req& r) {
+  const int nv = r.q.dim + 2;
+  size_t b = round_up(state_bytes(prec, nv, r.ncell));
+  for (int d = 0; d < r.q.dim; ++d) b += round_up(sizeof(double) * (r.q.n[d] + 4));
+  return b + round_up(sizeof(Ctrl));
+}
+
+int tiles_of(const gks_request& q) {
+  if (q.dim == 1) return (q.n[0] + Tile<1>::X - 1) / Tile<1>::X;
+  return ((q.n[0] + Tile<2>::X - 1) / Tile<2>::X) * ((q.n[1] + Tile<2>::Y - 1) / Tile<2>::Y);
+}
+
+void fail_req(gks_server* s, Req* r, const char* msg) {
+  r->status = REQ_FAILED;
+  s->err = msg;
+}
+
+// Lay out the solve in its arena block, copy its initial state in, and fill its descriptor.
+bool admit(gks_server* s, Req* r) {
+  const gks_request& q = r->q;
+  const int D = q.dim, nv = D + 2;
+  char* base = s->arena + r->off;
+  const size_t sb = state_bytes(s->prec, nv, r->ncell) / (s->prec == PREC_F32 ? 4 : 2);
+  void* W[2];
+  float* Wlo[2] = {nullptr, nullptr};
+  W[0] = base;
+  W[1] = base + sb;
+  if (s->prec == PREC_F32) {
+    Wlo[0] = (float*)(base + 2 * sb);
+    Wlo[1] = (float*)(base + 3 * sb);
+  }
+  char* p = base + round_up(state_bytes(s->prec, nv, r->ncell));
+  double* widths[3] = {nullptr, nullptr, nullptr};
+  for (int d = 0; d < D; ++d) {
+    const int n = q.n[d];
+    std::vector<double> w(n + 4);
+    const double h = (q.hi[d] - q.lo[d]) / n;
+    for (int i = 0; i < n + 4; ++i) w[i] = h;  // uniform cells: ghosts equal too
+    widths[d] = (double*)p;
+    if (cudaMemcpyAsync(widths[d], w.data(), sizeof(double) * (n + 4), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+      return false;
+    p += round_up(sizeof(double) * (n + 4));
+  }
+  Ctrl* ctrl = (Ctrl*)p;
+  // initial state: pinned staging -> device staging -> stored form in buffer (step mod 2)
+  const int cur = (int)(s->step & 1);
+  std::memcpy(s->h_stage, r->prim.data(), sizeof(double) * nv * r->ncell);
+  if (cudaMemcpyAsync(s->d_stage, s->h_stage, sizeof(double) * nv * r->ncell, cudaMemcpyHostToDevice, s->stream) !=
+      cudaSuccess)
+    return false;
+  const unsigned blocks = (unsigned)((r->ncell + 255) / 256);
+  state_in_kernel<double><<<blocks, 256, 0, s->stream>>>(s->d_stage, GKS_LAYOUT_SOA_PRIM, D, r->ncell, q.gamma,
+                                                          s->prec, W[cur], Wlo[cur]);
+  cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s->stream);
+  set_params_kernel<0><<<1, 1, 0, s->stream>>>(ctrl, 0.0, q.cfl, 0.0);
+  // descriptor: arguments for the six phases of the batch step index
+  BatchSolve& S = *s->h_solve_stage;
+  std::memset(&S, 0, sizeof(S));
+  StepArgs base_args;
+  std::memset(&base_args, 0, sizeof(base_args));
+  DevGrid& g = base_args.g;
+  g.ncell = r->ncell;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = d < D ? q.n[d] : 1;
+    g.w[d] = widths[d];
+    for (int sd = 0; sd < 2; ++sd) g.bc[d][sd] = d < D ? q.bc[d][sd] : GKS_BC_PERIODIC;
+  }
+  g.gamma = q.gamma;
+  g.bK = 2.0 / (q.gamma - 1.0);
+  g.K = g.bK - D;
+  g.mu = q.mu;
+  g.C_a = q.C_a;
+  g.T_wall = q.T_wall;
+  g.C_mu = 0.09;
+  g.beta_star = 0.09;
+  g.turb_model = TURB_NONE;
+  g.limiter = q.limiter;
+  g.abar_t0 = 0;
+  base_args.ctrl = ctrl;
+  for (int ph = 0; ph < 6; ++ph) {
+    StepArgs A = base_args;
+    const int c = ph & 1;
+    A.Win = W[c];
+    A.Wout = W[c ^ 1];
+    A.Win_lo = Wlo[c];
+    A.Wout_lo = Wlo[c ^ 1];
+    A.slot = ph % 3;
+    A.tslot = c;
+    A.resid = 0;
+    S.args[ph] = A;
+  }
+  S.stop_at = s->step + q.nsteps;
+  S.tiles = r->tiles;
+  // the CFL rate of the initial state for the first step
+  StepArgs A0 = S.args[s->step % 6];
+  const unsigned rb = std::min<unsigned>(blocks, 152u * 8u);
+  if (D == 1) {
+    if (s->prec == PREC_F64)
+      rate_kernel<1, PREC_F64><<<rb, kThreads, 0, s->stream>>>(A0);
+    else
+      rate_kernel<1, PREC_F32><<<rb, kThreads, 0, s->stream>>>(A0);
+  } else {
+    if (s->prec == PREC_F64)
+      rate_kernel<2, PREC_F64><<<rb, kThreads, 0, s->stream>>>(A0);
+    else
+      rate_kernel<2, PREC_F32><<<rb, kThreads, 0, s->stream>>>(A0);
+  }
+  if (cudaMemcpyAsync(s->d_solves + r->slot, &S, sizeof(BatchSolve), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    return false;
+  // the staging buffers are reused by the next admission
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return false;
+  r->stop_at = S.stop_at;
+  r->t_admit = now_s();
+  r->status = REQ_ACTIVE;
+  return cudaGetLastError() == cudaSuccess;
+}
+
+bool retire(gks_server* s, Req* r) {
+  const int D = r->q.dim, nv = D + 2;
+  char* base = s->arena + r->off;
+  const size_t sb = state_bytes(s->prec, nv, r->ncell) / (s->prec == PREC_F32 ? 4 : 2);
+  const int fin = (int)(r->stop_at & 1);
+  const void* W = base + fin * sb;
+  const float* Wlo = s->prec == PREC_F32 ? (const float*)(base + (2 + fin) * sb) : nullptr;
+  const unsigned blocks = (unsigned)((r->ncell + 255) / 256);
+  state_out_kernel<double><<<blocks, 256, 0, s->stream>>>(s->d_stage, GKS_LAYOUT_SOA_CONS, D, r->ncell, r->q.gamma,
+                                                           s->prec, W, Wlo);
+  if (cudaMemcpyAsync(s->h_stage, s->d_stage, sizeof(double) * nv * r->ncell, cudaMemcpyDeviceToHost, s->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return false;
+  r->result.assign(s->h_stage, s->h_stage + (size_t)nv * r->ncell);
+  return true;
+}
+
+void rebuild_items(gks_server* s) {
+  int counts[NGROUPS] = {0, 0, 0};
+  for (Req* r : s->active) {
+    int2* dst = s->h_items + (size_t)r->group * s->max_items;
+    for (int t = 0; t < r->tiles; ++t) dst[counts[r->group]++] = make_int2(r->slot, t);
+  }
+  for (int g = 0; g < NGROUPS; ++g) {
+    s->h_nitems[g] = counts[g];
+    if (counts[g])
+      cudaMemcpyAsync(s->d_items[g], s->h_items + (size_t)g * s->max_items, sizeof(int2) * counts[g],
+                      cudaMemcpyHostToDevice, s->stream);
+  }
+  cudaMemcpyAsync(s->d_nitems, s->h_nitems, sizeof(int) * NGROUPS, cudaMemcpyHostToDevice, s->stream);
+  cudaStreamSynchronize(s->stream);  // pinned item tables are rewritten by the next rebuild
+  s->dirty = false;
+}
+
+void launch_chunk_steps(gks_server* s, int nsteps, long long start) {
+  for (int k = 0; k < nsteps; ++k) {
+    BatchArgs B;
+    B.solves = s->d_solves;
+    B.counter = s->d_counter;
+    B.phase = (int)((start + k) % 6);
+    for (int g = 0; g < NGROUPS; ++g) {
+      B.items = s->d_items[g];
+      B.nitems = s->d_nitems + g;
+      if (g == GROUP_1D)
+        launch_batch_d1(s->prec, false, B, s->persistent_blocks, s->stream);
+      else
+        launch_batch_d2(s->prec, g == GROUP_2D_MULTID, B, s->persistent_blocks, s->stream);
+    }
+  }
+}
+
+bool run_chunk(gks_server* s) {
+  if (!s->graph) {
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    launch_chunk_steps(s, s->chunk, 0);
+    if (cudaStreamEndCapture(s->stream, &g) != cudaSuccess) return false;
+    const cudaError_t e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return false;
+  }
+  if (cudaGraphLaunch(s->graph, s->stream) != cudaSuccess) return false;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess;
+}
+
+void worker_main(gks_server* s) {
+  cudaSetDevice(s->dev);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // admission, in arrival order, while memory and descriptor slots allow
+    while (!s->pending.empty() && !s->free_slots.empty()) {
+      Req* r = s->pending.front();
+      const size_t need = footprint(s->prec, *r);
+      size_t off;
+      if (!s->alloc.alloc(need, &off)) break;
+      s->pending.pop_front();
+      r->off = off;
+      r->bytes = need;
+      r->slot = s->free_slots.back();
+      s->free_slots.pop_back();
+      lk.unlock();
+      const bool ok = admit(s, r);
+      lk.lock();
+      if (!ok) {
+        fail_req(s, r, "admission failed");
+        s->alloc.release(r->off, r->bytes);
+        s->free_slots.push_back(r->slot);
+        s->cv_done.notify_all();
+        continue;
+      }
+      s->active.push_back(r);
+      s->dirty = true;
+    }
+    if (s->active.empty()) {
+      if (s->stop) break;
+      s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    const bool dirty = s->dirty;
+    lk.unlock();
+    if (dirty) rebuild_items(s);
+    const double t0 = now_s();
+    const bool ok = run_chunk(s);
+    const double t1 = now_s();
+    lk.lock();
+    s->busy_s += t1 - t0;
+    s->step += s->chunk;
+    if (!ok) {
+      s->err = "batch step failed";
+      for (Req* r : s->active) r->status = REQ_FAILED;
+      s->active.clear();
+      s->cv_done.notify_all();
+      break;
+    }
+    // retire finished solves
+    std::vector<Req*> keep;
+    for (Req* r : s->active) {
+      if (r->stop_at > s->step) {
+        keep.push_back(r);
+        continue;
+      }
+      lk.unlock();
+      const bool got = retire(s, r);
+      lk.lock();
+      r->t_done = now_s();
+      r->status = got ? REQ_DONE : REQ_FAILED;
+      s->alloc.release(r->off, r->bytes);
+      s->free_slots.push_back(r->slot);
+      if (got) {
+        s->completed++;
+        s->latencies.push_back(r->t_done - r->t_submit);
+        s->t_last_done = r->t_done;
+      }
+      s->dirty = true;
+    }
+    s->active.swap(keep);
+    s->cv_done.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+gks_status gks_server_create(int precision, size_t arena_bytes, long max_cells, int chunk_steps, void* cuda_stream,
+                             gks_server** out) {
+  if (!out) return GKS_EINVAL;
+  *out = nullptr;
+  if (precision != GKS_FP64 && precision != GKS_FP32) return GKS_EINVAL;
+  if (arena_bytes < (1u << 20) || max_cells < 4 || chunk_steps < 6 || chunk_steps % 6) return GKS_EINVAL;
+  gks_server* s = new (std::nothrow) gks_server();
+  if (!s) return GKS_ENOMEM;
+  s->prec = precision == GKS_FP64 ? PREC_F64 : PREC_F32;
+  s->chunk = chunk_steps;
+  s->max_cells = max_cells;
+  s->capacity = arena_bytes;
+  cudaGetDevice(&s->dev);
+  auto bail = [&](gks_status st) {
+    gks_server_destroy(s);
+    return st;
+  };
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GKS_ECUDA);
+    s->own_stream = true;
+  }
+  if (prepare_batch_d1() != cudaSuccess || prepare_batch_d2() != cudaSuccess) return bail(GKS_ECUDA);
+  // descriptor slots: enough for arena / smallest footprint, bounded
+  s->max_slots = 4096;
+  s->max_items = (int)std::min<long>(1L << 22, (long)(arena_bytes / (Tile<1>::X * 4 * sizeof(float) * 3)) + 4096);
+  if (cudaMalloc(&s->arena, arena_bytes) != cudaSuccess ||
+      cudaMalloc(&s->d_solves, sizeof(BatchSolve) * s->max_slots) != cudaSuccess ||
+      cudaMalloc(&s->d_nitems, sizeof(int) * NGROUPS) != cudaSuccess ||
+      cudaMalloc(&s->d_counter, sizeof(long long) * 2) != cudaSuccess ||
+      cudaMalloc(&s->d_stage, sizeof(double) * 5 * max_cells) != cudaSuccess ||
+      cudaMallocHost(&s->h_stage, sizeof(double) * 5 * max_cells) != cudaSuccess ||
+      cudaMallocHost(&s->h_solve_stage, sizeof(BatchSolve)) != cudaSuccess ||
+      cudaMallocHost(&s->h_items, sizeof(int2) * NGROUPS * (size_t)s->max_items) != cudaSuccess ||
+      cudaMallocHost(&s->h_nitems, sizeof(int) * NGROUPS) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(GKS_ENOMEM);
+  }
+  for (int g = 0; g < NGROUPS; ++g)
+    if (cudaMalloc(&s->d_items[g], sizeof(int2) * s->max_items) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(GKS_ENOMEM);
+    }
+  cudaMemset(s->d_nitems, 0, sizeof(int) * NGROUPS);
+  cudaMemset(s->d_counter, 0, sizeof(long long) * 2);
+  s->alloc.init(arena_bytes);
+  for (int i = s->max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
+  s->persistent_blocks = sms * (s->prec == PREC_F32 ? 2 : 1);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return bail(GKS_ECUDA);
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return GKS_OK;
+}
+
+gks_status gks_server_submit(gks_server* s, const gks_request* q, const double* prim, long long* id_out) {
+  if (!s || !q || !prim) return GKS_EINVAL;
+  if (q->dim < 1 || q->dim > 2 || q->nsteps < 1 || !(q->cfl > 0.0) || !(q->gamma > 1.0) || !(q->mu >= 0.0))
+    return GKS_EINVAL;
+  if (2.0 / (q->gamma - 1.0) - q->dim < 0.0) return GKS_EINVAL;
+  long ncell = 1;
+  for (int d = 0; d < q->dim; ++d) {
+    if (q->n[d] < 2 || !(q->hi[d] > q->lo[d])) return GKS_EINVAL;
+    ncell *= q->n[d];
+    for (int sd = 0; sd < 2; ++sd) {
+      const int b = q->bc[d][sd];
+      if (b != GKS_BC_PERIODIC && b != GKS_BC_TRANSMISSIVE && b != GKS_BC_WALL && b != GKS_BC_OUTFLOW)
+        return GKS_EUNSUPPORTED;
+      if (b == GKS_BC_WALL && !(q->T_wall > 0.0)) return GKS_EINVAL;
+    }
+    if ((q->bc[d][0] == GKS_BC_PERIODIC) != (q->bc[d][1] == GKS_BC_PERIODIC)) return GKS_EINVAL;
+  }
+  if (ncell > s->max_cells) return GKS_EINVAL;
+  if (q->limiter != GKS_LIM_MINMOD && q->limiter != GKS_LIM_VANLEER) return GKS_EINVAL;
+  Req* r = new (std::nothrow) Req();
+  if (!r) return GKS_ENOMEM;
+  r->q = *q;
+  r->ncell = ncell;
+  r->tiles = tiles_of(*q);
+  r->group = q->dim == 1 ? GROUP_1D : (q->expand == GKS_EXPAND_MULTID ? GROUP_2D_MULTID : GROUP_2D);
+  r->prim.assign(prim, prim + (size_t)(q->dim + 2) * ncell);
+  if (footprint(s->prec, *r) > s->capacity) {
+    delete r;
+    return GKS_ENOMEM;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if ((long)r->tiles > s->max_items) {
+      delete r;
+      return GKS_EINVAL;
+    }
+    r->id = s->next_id++;
+    r->t_submit = now_s();
+    if (s->t_first_submit == 0) s->t_first_submit = r->t_submit;
+    s->reqs[r->id] = r;
+    s->pending.push_back(r);
+    if (id_out) *id_out = r->id;
+  }
+  s->cv_work.notify_one();
+  return GKS_OK;
+}
+
+gks_status gks_server_poll(gks_server* s, long long id, int* done, double* W_out, double* latency_s) {
+  if (!s) return GKS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return GKS_EINVAL;
+  Req* r = it->second;
+  if (r->status == REQ_FAILED) return GKS_ECUDA;
+  if (done) *done = r->status == REQ_DONE;
+  if (r->status == REQ_DONE) {
+    if (W_out) std::memcpy(W_out, r->result.data(), sizeof(double) * r->result.size());
+    if (latency_s) *latency_s = r->t_done - r->t_submit;
+  }
+  return GKS_OK;
+}
+
+gks_status gks_server_wait_all(gks_server* s, double timeout_s) {
+  if (!s) return GKS_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (!(s->pending.empty() && s->active.empty())) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) return GKS_ETIMEOUT;
+  }
+  for (auto& kv : s->reqs)
+    if (kv.second->status == REQ_FAILED) return GKS_ECUDA;
+  return GKS_OK;
+}
+
+gks_status gks_server_stats(gks_server* s, long long* completed, double* p50_s, double* p99_s, double* solves_per_s,
+                            double* busy_s) {
+  if (!s) return GKS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::vector<double> l = s->latencies;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    const double pos = q * (l.size() - 1);
+    const size_t i = (size_t)pos;
+    const double f = pos - i;
+    return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+  };
+  if (completed) *completed = s->completed;
+  if (p50_s) *p50_s = pct(0.5);
+  if (p99_s) *p99_s = pct(0.99);
+  const double span = s->t_last_done - s->t_first_submit;
+  if (solves_per_s) *solves_per_s = span > 0 ? s->completed / span : 0.0;
+  if (busy_s) *busy_s = s->busy_s;
+  return GKS_OK;
+}
+
+gks_status gks_server_destroy(gks_server* s) {
+  if (!s) return GKS_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->pending.clear();
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->arena) cudaFree(s->arena);
+  if (s->d_solves) cudaFree(s->d_solves);
+  for (int g = 0; g < NGROUPS; ++g)
+    if (s->d_items[g]) cudaFree(s->d_items[g]);
+  if (s->d_nitems) cudaFree(s->d_nitems);
+  if (s->d_counter) cudaFree(s->d_counter);
+  if (s->d_stage) cudaFree(s->d_stage);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->h_solve_stage) cudaFreeHost(s->h_solve_stage);
+  if (s->h_items) cudaFreeHost(s->h_items);
+  if (s->h_nitems) cudaFreeHost(s->h_nitems);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+  return GKS_OK;
+}
+
+}  // extern "C"

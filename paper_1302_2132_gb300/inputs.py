@@ -229,3 +229,59 @@ def shock_boundary_layer(nx, ny, M=2.85, delta=0.1, theta_deg=24.0, Re_delta=1.6
     bc_prim = [[inflow, None], [None, top]]
     return dict(dim=2, n=(nx, ny), dx=[dx, dy], bc=bc, bc_prim=bc_prim, prim=prim, T_wall=T_wall, mu=mu,
                 f1=f1.astype(np.float32).astype(np.float64), f2=f2.astype(np.float32).astype(np.float64))
+
+
+# ------------------------------------------------------------------------------------------------
+# Serving request stream
+# ------------------------------------------------------------------------------------------------
+def turbulence_1d(n, seed, k0=8.0, mach=0.3, gamma=GAMMA):
+    """Periodic 1D random-phase velocity with E(k) ~ k^4 exp(-2 (k/k0)^2), rho = 1, p = 1/gamma."""
+    rng = np.random.default_rng(seed)
+    k = np.fft.rfftfreq(n, d=1.0 / n)
+    amp = np.sqrt(k ** 4 * np.exp(-2.0 * (k / k0) ** 2))
+    uh = amp * np.exp(1j * rng.uniform(0, 2 * math.pi, k.size))
+    uh[0] = 0.0
+    u = np.fft.irfft(uh, n)
+    u *= mach / max(np.sqrt(np.mean(u * u)), 1e-300)
+    prim = np.zeros((3, n))
+    prim[0] = 1.0
+    prim[1] = u
+    prim[2] = 1.0 / gamma
+    return dict(dim=1, n=(n,), dx=[np.full(n, 2 * math.pi / n)], bc=[[0, 0]], prim=prim,
+                lo=[0.0], hi=[2 * math.pi])
+
+
+def serving_request(i, seed):
+    """Request i of the seeded serving stream: 50% 1D with n log-uniform in [256, 4096], 50% 2D with
+    n^2 log-uniform in [64^2, 512^2]; Sod, Riemann quadrant (2D only) or periodic turbulence; steps
+    uniform in [50, 500].  Returns a spec with the initial primitive state and run parameters."""
+    rng = np.random.default_rng([seed, i])
+    steps = int(rng.integers(50, 501))
+    if rng.random() < 0.5:
+        n = int(round(math.exp(rng.uniform(math.log(256), math.log(4096)))))
+        if rng.random() < 0.5:
+            s = sod_1d(n)
+            s.update(lo=[0.0], hi=[1.0], kind="sod1d")
+        else:
+            s = turbulence_1d(n, seed=int(rng.integers(1 << 30)))
+            s.update(kind="turb1d")
+    else:
+        n = int(round(math.exp(0.5 * rng.uniform(math.log(64 * 64), math.log(512 * 512)))))
+        kind = rng.integers(3)
+        if kind == 0:
+            s = sod_2d(n)
+            s.update(lo=[0.0, 0.0], hi=[1.0, 1.0], kind="sod2d")
+        elif kind == 1:
+            s = riemann_quadrant(n, seed=int(rng.integers(1 << 30)))
+            s.update(lo=[0.0, 0.0], hi=[1.0, 1.0], kind="quadrant")
+        else:
+            s = turbulence(n, 2, seed=int(rng.integers(1 << 30)), k0=min(8.0, n / 8.0))
+            s.update(lo=[0.0, 0.0], hi=[2 * math.pi, 2 * math.pi], kind="turb2d")
+    s["nsteps"] = steps
+    return s
+
+
+def poisson_arrivals(count, rate, seed):
+    """Arrival times (seconds) of a Poisson process with the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, count))

@@ -1,0 +1,96 @@
+"""Serving form: continuous batching of independent solves (gks_server_* through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle
+from cases import oracle_case, rel_err_per_var
+from paper_1302_2132_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1302_2132_gb300 import gks, serve  # noqa: E402
+
+KW = dict(gamma=1.4, mu=1e-4, C_a=0.5, cfl=0.5, limiter="vanleer")
+
+
+def small_requests():
+    out = []
+    for i in range(40):
+        s = inputs.serving_request(i, 4000)
+        if (s["dim"] == 1 and s["n"][0] <= 1024) or (s["dim"] == 2 and s["n"][0] <= 96):
+            s["nsteps"] = min(s["nsteps"], 120)
+            out.append(s)
+        if len(out) == 8:
+            break
+    return out
+
+
+def run_server(specs, precision="fp32", arena=1 << 30):
+    srv = serve.Server(precision=precision, arena_bytes=arena, max_cells=512 * 512, chunk_steps=24)
+    ids = [srv.submit(s, **KW) for s in specs]
+    srv.wait_all(300)
+    res = [srv.poll(i)[1] for i in ids]
+    st = srv.stats()
+    srv.close()
+    return res, st
+
+
+def test_result_is_the_same_alone_and_in_the_mix():
+    specs = small_requests()
+    kinds = {s["kind"] for s in specs}
+    assert len(specs) == 8 and len(kinds) >= 3
+    mix, st = run_server(specs)
+    assert st["completed"] == 8
+    for k in (0, 3, 7):
+        alone, _ = run_server([specs[k]])
+        assert np.array_equal(alone[0], mix[k]), specs[k]["kind"]
+
+
+def test_served_solve_agrees_with_the_single_solve_path():
+    """The batch kernel and the single-solve kernel inline the same step body into two different
+    kernels, so the compiler may contract a few multiply-adds differently: the results agree to
+    FP32 rounding, not bit for bit (within one kernel, alone vs mixed, they are bitwise equal)."""
+    specs = small_requests()[:4]
+    res, _ = run_server(specs)
+    for s, W in zip(specs, res):
+        sol = gks.Solver(s["dim"], s["n"], s["bc"], dx=s["dx"], gamma=KW["gamma"], mu=KW["mu"], C_a=KW["C_a"],
+                         limiter="vanleer", expand="multid", precision="fp32")
+        sol.set_state(s["prim"].ravel(), layout="soa_prim")
+        sol.step(nsteps=s["nsteps"], cfl=KW["cfl"])
+        err = rel_err_per_var(sol.get_state(), W, s["dim"] + 2)
+        assert np.all(err < 1e-5), (s["kind"], err)
+        sol.close()
+
+
+def test_fp64_server_matches_the_oracle():
+    spec = inputs.sod_1d(128)
+    spec.update(lo=[0.0], hi=[1.0], nsteps=40)
+    quad = inputs.riemann_quadrant(40, seed=9)
+    quad.update(lo=[0.0, 0.0], hi=[1.0, 1.0], nsteps=20)
+    res, _ = run_server([spec, quad], precision="fp64")
+    for s, W in zip([spec, quad], res):
+        c = oracle_case(s, C_a=KW["C_a"], mu=KW["mu"], multid=1, limiter=1)
+        Wo, t, n, stt = c.run(c.prim_to_cons(s["prim"].ravel()), s["nsteps"], cfl=KW["cfl"], nthreads=8)
+        assert n == s["nsteps"] and stt == 0
+        assert np.all(rel_err_per_var(W, Wo, s["dim"] + 2) < 1e-10)
+
+
+def test_admission_waits_for_memory():
+    specs = [inputs.sod_2d(96) for _ in range(6)]
+    for s in specs:
+        s.update(lo=[0.0, 0.0], hi=[1.0, 1.0], nsteps=30)
+    # one 96^2 float-pair solve needs about 0.6 MB: a 2 MB arena holds three at a time
+    res, st = run_server(specs, arena=2 << 20)
+    assert st["completed"] == 6
+    assert all(np.array_equal(r, res[0]) for r in res)
+    big = inputs.sod_2d(512)
+    big.update(lo=[0.0, 0.0], hi=[1.0, 1.0], nsteps=6)
+    srv = serve.Server(arena_bytes=2 << 20)
+    with pytest.raises(gks.GksError) as e:
+        srv.submit(big, **KW)
+    assert e.value.code == gks.ENOMEM
+    srv.close()
