@@ -43,9 +43,14 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32_acc64", "fp64"])
+    p.add_argument("--precision", default=None, choices=["fp32", "fp32_acc64", "fp64"])
+    p.add_argument("--workload", default="turb2d_1024",
+                   choices=["turb2d_1024", "sod1d_400", "shock_bl_1024x384", "turb3d_256"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serving", action="store_true", help="measure the serving form only")
+    p.add_argument("--no-serving", action="store_true", help="leave the serving summary out")
+    p.add_argument("--requests", type=int, default=4000)
     return p.parse_args()
 
 
@@ -105,9 +110,60 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, device=None):
+    """Largest value of x over the ranks of the default process group (the job's wall time is the
+    slowest rank's); each rank processes its own replica, so units add up across ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def workload_inputs():
     from paper_1302_2132_gb300 import inputs
     return inputs.turbulence(N, 2, seed=SEED)
+
+
+def make_workload(name, precision):
+    """Workload descriptions: the default is the 2D decaying turbulence the metric is quoted on; the
+    others are the remaining configurations, measured with the same timing rules."""
+    from paper_1302_2132_gb300 import inputs
+    if name == "turb2d_1024":
+        spec = workload_inputs()
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
+                                       expand="multid"), nsteps=NSTEPS, t_end=0.0, precision=precision or "fp32",
+                    desc="2D decaying turbulence 1024^2, k-epsilon tau_t, multi-D, 200 CFL steps")
+    if name == "sod1d_400":
+        spec = inputs.sod_1d(400)
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=1e-5, C_a=1.0, limiter="vanleer", expand="directional"),
+                    nsteps=0, t_end=0.2, precision=precision or "fp64",
+                    desc="Sod shock tube, 400 cells, van Leer, C_a = 1, CFL 0.5, to t = 0.2")
+    if name == "shock_bl_1024x384":
+        spec = inputs.shock_boundary_layer(1024, 384)
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega",
+                                       beta_star=0.09, C_a=0.5, limiter="vanleer", expand="multid"),
+                    nsteps=5000, t_end=0.0, precision=precision or "fp32",
+                    desc="Mach 2.85 boundary layer under a 24-degree shock, 1024x384 wall-clustered, k-omega tau_t, "
+                         "5000 CFL steps")
+    if name == "turb3d_256":
+        spec = inputs.turbulence(256, 3, seed=2132)
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
+                                       expand="multid"), nsteps=100, t_end=0.0, precision=precision or "fp32",
+                    desc="3D decaying turbulence 256^3, k-epsilon tau_t, multi-D, 100 CFL steps")
+    raise ValueError(name)
+
+
+def faces_of(n):
+    D = len(n)
+    tot = 0
+    for d in range(D):
+        f = n[d] + 1
+        for e in range(D):
+            if e != d:
+                f *= n[e]
+        tot += f
+    return tot
 
 
 def run_ours(args):
@@ -124,21 +180,33 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     gks.load()
-    spec = workload_inputs()
-    faces_per_step = 2 * N * N
-    cells = N * N
-    solver = gks.Solver(2, (N, N), spec["bc"], dx=spec["dx"], gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09,
-                        C_a=0.0, limiter="vanleer", expand="multid", precision=args.precision)
+    wl = make_workload(args.workload, args.precision)
+    spec = wl["spec"]
+    D = spec["dim"]
+    n = tuple(spec["n"])
+    faces_per_step = faces_of(n)
+    cells = int(np.prod(n))
+    solver = gks.Solver(D, n, spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"), precision=wl["precision"],
+                        **wl["kw"])
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
-    f1 = torch.tensor(spec["f1"].ravel(), device=dev)
-    f2 = torch.tensor(spec["f2"].ravel(), device=dev)
-    solver.set_turbulence(f1, f2)
+    turb = wl["kw"].get("turb_model", "none") != "none"
+    if turb:
+        f1 = torch.tensor(spec["f1"].ravel(), device=dev)
+        f2 = torch.tensor(spec["f2"].ravel(), device=dev)
+        solver.set_turbulence(f1, f2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = solver.stream
+    nsteps = wl["nsteps"]
+    if wl["t_end"] > 0.0:  # count the steps that reach t_end
+        solver.set_state(prim_dev, layout="soa_prim")
+        nsteps = 0
+        while solver.time()[0] < wl["t_end"]:
+            solver.step(nsteps=1, cfl=CFL, t_end=wl["t_end"])
+            nsteps += 1
 
     def one_step():
         solver.set_state(prim_dev, layout="soa_prim")
-        solver.step(nsteps=NSTEPS, cfl=CFL)
+        solver.step(nsteps=nsteps, cfl=CFL, t_end=wl["t_end"])
 
     for _ in range(args.warmup):
         one_step()
@@ -179,43 +247,45 @@ def run_ours(args):
     _, _, total = solver.residual()
     t_end, _ = solver.time()
     if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = tt.item()
+        ms = max_over_ranks(ms, dev)
     # ---- end to end through the C ABI from pinned host memory ----------------------------------
     e2e = None
     if not args.no_e2e:
         prim_host = torch.tensor(spec["prim"].ravel()).pin_memory()
-        f1_host = torch.tensor(spec["f1"].ravel()).pin_memory()
-        f2_host = torch.tensor(spec["f2"].ravel()).pin_memory()
-        out_host = torch.empty(4 * cells, dtype=torch.float64).pin_memory()
+        f1_host = torch.tensor(spec["f1"].ravel()).pin_memory() if turb else None
+        f2_host = torch.tensor(spec["f2"].ravel()).pin_memory() if turb else None
+        out_host = torch.empty((D + 2) * cells, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             solver.set_state(prim_host, layout="soa_prim")
-            solver.set_turbulence(f1_host, f2_host)
-            solver.step(nsteps=NSTEPS, cfl=CFL)
+            if turb:
+                solver.set_turbulence(f1_host, f2_host)
+            solver.step(nsteps=nsteps, cfl=CFL, t_end=wl["t_end"])
             solver.get_state(out=out_host)
         t1 = time.perf_counter()
         assert torch.isfinite(out_host).all()
         e2e_s = (t1 - t0)
-        e2e = {"value": faces_per_step * NSTEPS * args.steps * world / e2e_s, "unit": "face_flux_evals/s",
-               "h2d_bytes_per_step": int(prim_host.numel() * 8 + f1_host.numel() * 8 + f2_host.numel() * 8),
+        e2e = {"value": faces_per_step * nsteps * args.steps * world / e2e_s, "unit": "face_flux_evals/s",
+               "h2d_bytes_per_step": int(prim_host.numel() * 8 + (2 * cells * 8 if turb else 0)),
                "d2h_bytes_per_step": int(out_host.numel() * 8)}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     secs = ms / 1e3
-    value = faces_per_step * NSTEPS * args.steps * world / secs
-    # roofline of the fused step kernel (FP32 ALU bound): algorithmic operations per launch
-    counts = flop_counts(multid=True)
+    value = faces_per_step * nsteps * args.steps * world / secs
+    # roofline of the fused step kernel (ALU bound): algorithmic operations per launch
+    multid = wl["kw"].get("expand") == "multid" and D > 1
+    counts = gks.face_op_count(D, multid, True)
     per_face = sum(counts[:3])
     per_cell = CELL_OPS
     ops_per_launch = faces_per_step * per_face + cells * per_cell
     avg_launch_s = kms / 1e3 / max(klaunch, 1)
     achieved = ops_per_launch / avg_launch_s / 1e12
-    peak = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 lanes x FMA x max SM clock
+    fp64 = wl["precision"] == "fp64"
+    lanes = 2 if fp64 else 128  # FP64 runs at 1/64 of the FP32 rate on this part
+    peak = 152 * lanes * 2 * 2.070e9 / 1e12
     line = {
         "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
         "value": value,
@@ -227,28 +297,39 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision != "fp64" else "f64",
+        "dtype": "f64" if fp64 else "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N, N], "time_steps_per_bench_step": NSTEPS, "cfl": CFL,
-                   "turbulence": "k-epsilon, seeded log-normal k and epsilon", "expand": "multid",
-                   "precision": args.precision, "state_accumulation": {"fp32": "float pair (hi+lo)",
-                                                                      "fp32_acc64": "IEEE double",
-                                                                      "fp64": "IEEE double"}[args.precision],
+        "config": {"workload": WORKLOAD if args.workload == "turb2d_1024" else args.workload,
+                   "description": wl["desc"], "grid": list(n), "time_steps_per_bench_step": nsteps, "cfl": CFL,
+                   "expand": "multid" if multid else "directional",
+                   "precision": wl["precision"], "state_accumulation": {"fp32": "float pair (hi+lo)",
+                                                                        "fp32_acc64": "IEEE double",
+                                                                        "fp64": "IEEE double"}[wl["precision"]],
                    "l2": "flushed between bench steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "single"},
-        "cell_updates_per_s": cells * NSTEPS * args.steps * world / secs,
+        "cell_updates_per_s": cells * nsteps * args.steps * world / secs,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "step_kernel<2, PREC_F32, multid>", "avg_launch_us": avg_launch_s * 1e6,
+                     "kernel": "step_kernel<%d, %s, %s>" % (D, "PREC_F64" if fp64 else "PREC_F32",
+                                                             "multid" if multid else "directional"),
+                     "avg_launch_us": avg_launch_s * 1e6,
                      "ops_per_face": per_face, "ops_per_cell": per_cell,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz (derived)"},
-        "gpu_launches": args.steps * (NSTEPS + 3),
+                     "peak_basis": "152 SMs x %d %s lanes x 2 (FMA) x 2070 MHz (derived)" % (lanes, "FP64" if fp64
+                                                                                            else "FP32")},
+        "gpu_launches": args.steps * (nsteps + 3),
         "clocks": clock_info,
         "e2e": e2e,
         "final_time": t_end,
         "total_mass": float(total[0]),
     }
-    if not args.no_cpu_baseline:
+    tile = solver.tile_shape()
+    line["config"]["tile"] = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
+    if not args.no_cpu_baseline and args.workload == "turb2d_1024":
         line["cpu_baseline"] = cpu_baseline(budget_s=15.0)
+    if not args.no_serving and args.workload == "turb2d_1024":
+        try:
+            line["serving"] = serving_summary(args.requests)
+        except Exception as exc:  # the serving figures are reported beside the main metric
+            line["serving"] = {"error": repr(exc)}
     print(json.dumps(line))
     sys.stdout.flush()
     if world > 1:
@@ -324,9 +405,112 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _gen_request(args):
+    from paper_1302_2132_gb300 import inputs
+    return inputs.serving_request(*args)
+
+
+def serving_requests(count, seed=4000):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_request, [(i, seed) for i in range(count)], chunksize=16)
+
+
+SERVE_KW = dict(gamma=1.4, mu=1e-4, C_a=0.5, cfl=0.5, limiter="vanleer", expand="multid")
+
+
+def serve_stream(reqs, rate, seed, arena=16 << 30):
+    """Submit reqs at Poisson arrival times (rate per second; 0 = all at once) and wait for all."""
+    from paper_1302_2132_gb300 import inputs, serve
+    srv = serve.Server(precision="fp32", arena_bytes=arena, max_cells=512 * 512, chunk_steps=24)
+    arrivals = inputs.poisson_arrivals(len(reqs), rate, seed) if rate > 0 else np.zeros(len(reqs))
+    t0 = time.perf_counter()
+    for r, ta in zip(reqs, arrivals):
+        wait = t0 + ta - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        srv.submit(r, **SERVE_KW)
+    srv.wait_all(3600)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    st["wall_s"] = wall
+    st["offered_rate"] = rate
+    return st
+
+
+def fp64_loop(reqs):
+    """The plain FP64 per-solve loop on the same GPU: one solver per request, run to completion."""
+    import torch
+    from paper_1302_2132_gb300 import gks
+    t0 = time.perf_counter()
+    lat = []
+    for r in reqs:
+        ts = time.perf_counter()
+        s = gks.Solver(r["dim"], r["n"], r["bc"], dx=r["dx"], gamma=1.4, mu=SERVE_KW["mu"], C_a=SERVE_KW["C_a"],
+                       limiter="vanleer", expand="multid", precision="fp64")
+        s.set_state(r["prim"].ravel(), layout="soa_prim")
+        s.step(nsteps=r["nsteps"], cfl=SERVE_KW["cfl"])
+        s.get_state()
+        s.close()
+        lat.append(time.perf_counter() - ts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"solves_per_s": len(reqs) / wall, "requests": len(reqs), "p50_s": float(np.median(lat)),
+            "p99_s": float(np.percentile(lat, 99))}
+
+
+def serving_summary(count):
+    """Serving form on the seeded stream: capacity (burst of 400), a Poisson stream at 0.8x capacity,
+    a 2x overload of 1000 requests, and the plain FP64 per-solve loop on the first 40 requests."""
+    reqs = serving_requests(count)
+    burst = serve_stream(reqs[:400], 0.0, 1)
+    capacity = burst["completed"] / burst["wall_s"]
+    steady = serve_stream(reqs, 0.8 * capacity, 2)
+    over = serve_stream(reqs[:1000], 2.0 * capacity, 3)
+    base = fp64_loop(reqs[:40])
+    return {"metric": "serving solves/sec, p50/p99", "unit": "solves/s", "requests": len(reqs),
+            "solves_per_s": steady["solves_per_s"], "p50_s": steady["p50_s"], "p99_s": steady["p99_s"],
+            "offered_rate": steady["offered_rate"], "capacity_solves_per_s": capacity,
+            "overload_2x": {k: over[k] for k in ("solves_per_s", "p50_s", "p99_s", "completed")},
+            "fp64_per_solve_loop_solves_per_s": base["solves_per_s"],
+            "batched_fp32_over_fp64_loop": capacity / base["solves_per_s"],
+            "mix": "50% 1D (256-4096 cells), 50% 2D (64^2-512^2); Sod, Riemann quadrant, periodic turbulence; "
+                   "50-500 steps; seed 4000; Poisson arrivals"}
+
+
+def run_serving(args):
+    import torch
+    from paper_1302_2132_gb300 import build, gks
+    torch.cuda.init()
+    reqs = serving_requests(args.requests)  # spawned workers, before the first kernel
+    build.build()
+    gks.load()
+    cells = [int(np.prod(r["n"])) * r["nsteps"] for r in reqs]
+    burst = serve_stream(reqs[:400], 0.0, 1)
+    capacity = burst["completed"] / burst["wall_s"]
+    steady = serve_stream(reqs, 0.8 * capacity, 2)
+    over = serve_stream(reqs[:1000], 2.0 * capacity, 3)
+    sample = reqs[:40]
+    base = fp64_loop(sample)
+    line = {"metric": "serving solves/sec, p50/p99", "value": steady["solves_per_s"], "unit": "solves/s",
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_stream_4000", "requests": len(reqs), "seed": 4000,
+                       "mix": "50% 1D (256-4096 cells), 50% 2D (64^2-512^2); Sod, Riemann quadrant, periodic "
+                              "turbulence; 50-500 steps; FP32 flux, float-pair state",
+                       "cell_steps_total": int(sum(cells))},
+            "capacity_solves_per_s": capacity, "burst": burst, "steady_0p8": steady, "overload_2x": over,
+            "fp64_per_solve_loop": base,
+            "batched_vs_fp64_loop": capacity / base["solves_per_s"]}
+    print(json.dumps(line))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serving:
+        run_serving(a)
     else:
         run_ours(a)

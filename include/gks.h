@@ -143,6 +143,12 @@ gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtyp
 gks_status gks_enable_timing(gks_handle* h, int enable);
 gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
 
+/* Tile shape of the handle's step kernel.  2D FP32 handles choose among three shapes (32x15 and
+ * 64x7 cells per 256-thread CTA, 32x31 per 512-thread CTA) on their first gks_step: each is timed on
+ * the step about to be taken and the fastest kept (and reused by later handles of the same grid);
+ * the environment variable GKS_TILE_VARIANT=0|1|2 forces one.  The result does not depend on it. */
+gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz);
+
 gks_status gks_destroy(gks_handle* h);
 const char* gks_last_error(const gks_handle* h);
 
@@ -183,6 +189,46 @@ int gks_face_op_count(int dim, int expand, int with_recon, long long* counts);
 #define GKS_NOALLOC_MAX_CELLS (16384L * 1024L)
 gks_status gks_cfl_dt_noalloc(int dim, const int* n, const double* h, double gamma, const double* W,
                               double cfl, double* dt_out, void* cuda_stream);
+
+/* ---- Serving: continuous batching of independent solves on one GPU ----------------------------
+ * A server owns a device arena.  Submitted requests wait in arrival order until the arena has room
+ * for their state (footprint admission); admitted solves stay resident and advance together, one
+ * persistent batch launch per step per group (1D, 2D directional, 2D multi-dimensional), in chunks
+ * of chunk_steps steps replayed as captured CUDA graphs.  Between chunks a worker thread retires
+ * finished solves (final state copied to the host, memory freed) and admits waiting ones.  Each
+ * solve computes exactly what the single-solve path computes (same tile kernel, its own CFL time
+ * step), so its result does not depend on the rest of the batch.  Uniform grids without turbulence
+ * model; boundaries periodic, transmissive, outflow or wall. */
+typedef struct gks_server gks_server;
+
+typedef struct {
+  int dim;               /* 1 or 2 */
+  int n[3];              /* cells per axis */
+  double lo[3], hi[3];   /* extent (uniform cells) */
+  int bc[3][2];          /* GKS_BC_PERIODIC | TRANSMISSIVE | OUTFLOW | WALL */
+  double gamma, mu, C_a, T_wall;
+  double cfl;            /* CFL number of the time step */
+  int limiter, expand;   /* GKS_LIM_*, GKS_EXPAND_* */
+  int nsteps;            /* steps to run */
+} gks_request;
+
+/* precision GKS_FP32 (float-pair state) or GKS_FP64; arena_bytes of device memory for resident
+ * solves; max_cells per request; chunk_steps a multiple of 6.  Starts the worker thread. */
+gks_status gks_server_create(int precision, size_t arena_bytes, long max_cells, int chunk_steps, void* cuda_stream,
+                             gks_server** out);
+/* Queue a request with its initial primitive state (host, SoA (rho, u.., p), copied).  GKS_ENOMEM if
+ * the request can never fit in the arena. */
+gks_status gks_server_submit(gks_server* s, const gks_request* q, const double* prim, long long* id_out);
+/* done = 1 once finished; then W_out (host, SoA conservative, or NULL) receives the final state and
+ * latency_s the time from submission to completion. */
+gks_status gks_server_poll(gks_server* s, long long id, int* done, double* W_out, double* latency_s);
+/* Block until every submitted request has finished (GKS_ETIMEOUT after timeout_s seconds). */
+gks_status gks_server_wait_all(gks_server* s, double timeout_s);
+/* Completed requests, latency percentiles (seconds), completions per second since the first
+ * submission, and seconds the GPU spent in batch steps. */
+gks_status gks_server_stats(gks_server* s, long long* completed, double* p50_s, double* p99_s, double* solves_per_s,
+                            double* busy_s);
+gks_status gks_server_destroy(gks_server* s);
 
 /* Measured FMA throughput of the current device for FP32 and FP64 (independent FMA chains on every
  * SM, CUDA events), in TFLOP/s: context for the arithmetic roofline.  Synchronises the device. */

@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -14,8 +16,10 @@
 #include "gks.h"
 #include "gks_dispatch.h"
 #include "gks_step.cuh"
+#include "gks_aux.cuh"
 
 using namespace gks;
+using namespace gks::aux;
 
 struct gks_handle {
   int dev = 0;
@@ -38,6 +42,8 @@ struct gks_handle {
   long long step = 0;
   bool has_state = false, has_turb = false;
   int nblocks = 0;
+  int tile_variant = 0;   // 2D FP32: tile shape chosen by the autotuner
+  bool tuned = false;
   StepArgs base;
   std::map<int, cudaGraphExec_t> graphs;
   bool timing = false;
@@ -85,94 +91,6 @@ size_t arith_bytes(int prec) { return prec == PREC_F64 ? sizeof(double) : sizeof
 // ------------------------------------------------------------------------------------------------
 // Kernels for state conversion, CFL rate and diagnostics
 // ------------------------------------------------------------------------------------------------
-template <class Tin>
-__global__ void state_in_kernel(const Tin* src, int layout, int D, long ncell, double gamma, int prec,
-                                void* W, float* Wlo) {
-  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int nv = D + 2;
-  double w[5];
-  for (int v = 0; v < nv; ++v) w[v] = (double)(layout == GKS_LAYOUT_AOS_CONS ? src[c * nv + v] : src[v * ncell + c]);
-  if (layout == GKS_LAYOUT_SOA_PRIM) {
-    const double rho = w[0], p = w[D + 1];
-    double q = 0.0;
-    for (int i = 0; i < D; ++i) {
-      q += w[1 + i] * w[1 + i];
-      w[1 + i] = rho * w[1 + i];
-    }
-    w[D + 1] = p / (gamma - 1.0) + 0.5 * rho * q;
-  }
-  for (int v = 0; v < nv; ++v) {
-    if (prec == PREC_F32) {
-      const float hi = (float)w[v];
-      ((float*)W)[v * ncell + c] = hi;
-      Wlo[v * ncell + c] = (float)(w[v] - (double)hi);
-    } else {
-      ((double*)W)[v * ncell + c] = w[v];
-    }
-  }
-}
-
-template <class Tout>
-__global__ void state_out_kernel(Tout* dst, int layout, int D, long ncell, double gamma, int prec, const void* W,
-                                 const float* Wlo) {
-  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int nv = D + 2;
-  double w[5];
-  for (int v = 0; v < nv; ++v)
-    w[v] = prec == PREC_F32 ? (double)((const float*)W)[v * ncell + c] + (double)Wlo[v * ncell + c]
-                            : ((const double*)W)[v * ncell + c];
-  if (layout == GKS_LAYOUT_SOA_PRIM) {
-    double q = 0.0;
-    for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
-    const double p = (gamma - 1.0) * (w[D + 1] - 0.5 * q / w[0]);
-    for (int i = 0; i < D; ++i) w[1 + i] = w[1 + i] / w[0];
-    w[D + 1] = p;
-  }
-  for (int v = 0; v < nv; ++v) {
-    if (layout == GKS_LAYOUT_AOS_CONS)
-      dst[c * nv + v] = (Tout)w[v];
-    else
-      dst[v * ncell + c] = (Tout)w[v];
-  }
-}
-
-template <class Tin, class Tout>
-__global__ void field_kernel(const Tin* src, Tout* dst, long n) {
-  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < n) dst[c] = (Tout)src[c];
-}
-
-template <class T>
-__global__ void copy_kernel(const T* src, T* dst, long n) {
-  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < n) dst[c] = src[c];
-}
-
-// CFL rate of the stored state into ctrl->rate[slot] (a step computes it for its successor).
-template <int D, int PREC>
-__global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ StepArgs A) {
-  using R = typename PrecT<PREC>::R;
-  __shared__ double red[kThreads / 32];
-  const DevGrid& g = A.g;
-  const Consts<R> kc = make_consts<R>(g);
-  R rmax = R(0);
-  for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += (long)gridDim.x * blockDim.x) {
-    R w[D + 2];
-    load_stored<D, PREC>(A, c, w);
-    int pos[3];
-    pos[0] = (int)(c % g.n[0]);
-    pos[1] = (int)((c / g.n[0]) % g.n[1]);
-    pos[2] = (int)(c / ((long)g.n[0] * g.n[1]));
-    R h[D];
-    for (int d = 0; d < D; ++d) h[d] = (R)g.w[d][pos[d] + 2];
-    rmax = fmax(rmax, cell_rate<D, R>(w, kc.gamma, h));
-  }
-  const double m = block_max<double>((double)rmax, red);
-  if (threadIdx.x == 0) atomic_max_nonneg(&A.ctrl->rate[A.slot], m);
-}
-
 // Per-cell turbulent relaxation time and rarefaction diagnostic, from the same cell formula the
 // step kernel uses (neighbourhood staged in registers with the boundary rules applied).
 template <int D, int PREC>
@@ -234,29 +152,30 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
     ((float*)out)[c] = (float)val;
 }
 
-__global__ void set_params_kernel(Ctrl* c, double dt_fixed, double cfl, double t_end) {
-  c->dt_fixed = dt_fixed;
-  c->cfl = cfl;
-  c->t_end = t_end;
-  for (int v = 0; v < 5; ++v) {
-    c->l2[v] = 0.0;
-    c->total[v] = 0.0;
-    c->linf[v] = 0ull;
-  }
-}
-
 __global__ void set_time_kernel(Ctrl* c, int slot, double t) { c->t[slot] = t; }
 
 inline unsigned grid_for(long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-void launch_step(gks_handle* h, const StepArgs& A) {
+int tiles_for(const gks_handle* h, int variant) {
+  int t[3];
+  tile_shape(h->D, variant, &t[0], &t[1], &t[2]);
+  long n = 1;
+  for (int d = 0; d < 3; ++d) n *= (h->n[d] + t[d] - 1) / t[d];
+  return (int)n;
+}
+
+void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
   if (h->D == 1)
     launch_step_d1(h->prec, false, A, h->nblocks, h->stream);
+  else if (h->D == 2 && variant > 0)
+    launch_step_d2_variant(variant, h->multid, A, tiles_for(h, variant), h->stream);
   else if (h->D == 2)
-    launch_step_d2(h->prec, h->multid, A, h->nblocks, h->stream);
+    launch_step_d2(h->prec, h->multid, A, tiles_for(h, 0), h->stream);
   else
     launch_step_d3(h->prec, h->multid, A, h->nblocks, h->stream);
 }
+
+void launch_step(gks_handle* h, const StepArgs& A) { launch_step_variant(h, A, h->tile_variant); }
 
 // Arguments of the step that starts at absolute step index s.
 StepArgs step_args(const gks_handle* h, long long s, int resid) {
@@ -350,6 +269,65 @@ gks_status sticky_status(gks_handle* h) {
   return GKS_OK;
 }
 
+// Tile-shape autotuner (2D FP32): each variant runs the step that is about to be taken three times
+// from the current state (the results are identical, and the step is then taken for real), timed
+// with CUDA events; the fastest is kept for the handle and for later handles of the same shape.
+struct TuneKey {
+  int n0, n1, multid;
+  bool operator<(const TuneKey& o) const {
+    return n0 != o.n0 ? n0 < o.n0 : (n1 != o.n1 ? n1 < o.n1 : multid < o.multid);
+  }
+};
+std::map<TuneKey, int> g_tuned;
+std::mutex g_tuned_mutex;
+
+gks_status autotune(gks_handle* h) {
+  h->tuned = true;
+  if (h->D != 2 || h->prec != PREC_F32) return GKS_OK;
+  const char* force = std::getenv("GKS_TILE_VARIANT");
+  if (force) {
+    const int v = std::atoi(force);
+    if (v >= 0 && v < kTileVariants2D) h->tile_variant = v;
+    return GKS_OK;
+  }
+  const TuneKey key{h->n[0], h->n[1], (int)h->multid};
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      h->tile_variant = it->second;
+      return GKS_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  GKS_CK(h, cudaEventCreate(&e0));
+  GKS_CK(h, cudaEventCreate(&e1));
+  const StepArgs A = step_args(h, h->step, 0);
+  float best = 1e30f;
+  int best_v = 0;
+  for (int v = 0; v < kTileVariants2D; ++v) {
+    launch_step_variant(h, A, v);  // warm-up
+    GKS_CK(h, cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < 3; ++r) launch_step_variant(h, A, v);
+    GKS_CK(h, cudaEventRecord(e1, h->stream));
+    GKS_CK(h, cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    GKS_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the trials max-wrote the next step's CFL-rate slot: clear it so that the real step alone sets it
+  GKS_CK(h, cudaMemsetAsync(&h->ctrl->rate[(h->step + 1) % 3], 0, sizeof(unsigned long long), h->stream));
+  h->tile_variant = best_v;
+  std::lock_guard<std::mutex> lk(g_tuned_mutex);
+  g_tuned[key] = best_v;
+  return GKS_OK;
+}
+
 }  // namespace
 
 // ================================================================================================
@@ -422,6 +400,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   static bool prepared[4] = {false, false, false, false};
   if (!prepared[D]) {
     cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
+    if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bad(GKS_ECUDA, "kernel attribute setup failed");
@@ -656,8 +635,12 @@ gks_status gks_step(gks_handle* h, double dt, double cfl, int nsteps, double t_e
   if (h->base.g.turb_model != GKS_TURB_NONE && !h->has_turb) return fail(h, GKS_EINVAL, "turbulence fields not set");
   if (nsteps == 0) return GKS_OK;
   DeviceGuard dg(h->dev);
-  set_params_kernel<<<1, 1, 0, h->stream>>>(h->ctrl, dt > 0.0 ? dt : 0.0, cfl, t_end);
+  set_params_kernel<0><<<1, 1, 0, h->stream>>>(h->ctrl, dt > 0.0 ? dt : 0.0, cfl, t_end);
   GKS_CK(h, cudaGetLastError());
+  if (!h->tuned) {
+    const gks_status st = autotune(h);
+    if (st != GKS_OK) return st;
+  }
   int remaining = nsteps;
   while (remaining > 0) {
     if (!h->timing && remaining - 1 >= kGraphChunk && h->step % 6 == 0) {
@@ -803,6 +786,17 @@ gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches)
   if (launches) *launches = h->launches;
   h->ms_total = 0.0;
   h->launches = 0;
+  return GKS_OK;
+}
+
+gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz) {
+  if (!h) return GKS_EINVAL;
+  int t[3];
+  tile_shape(h->D, h->tile_variant, &t[0], &t[1], &t[2]);
+  if (variant) *variant = h->tile_variant;
+  if (tx) *tx = t[0];
+  if (ty) *ty = t[1];
+  if (tz) *tz = t[2];
   return GKS_OK;
 }
 

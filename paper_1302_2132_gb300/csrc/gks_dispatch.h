@@ -5,6 +5,7 @@
 namespace gks {
 
 struct StepArgs;
+struct BatchArgs;
 
 cudaError_t prepare_step_d1();
 cudaError_t prepare_step_d2();
@@ -12,6 +13,18 @@ cudaError_t prepare_step_d3();
 void launch_step_d1(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void launch_step_d2(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void launch_step_d3(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
+
+// 2D FP32 tile variants 1 and 2 (variant 0 is launch_step_d2) and the tile shape of a variant
+cudaError_t prepare_step_d2_variants();
+void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
+void tile_shape(int D, int variant, int* x, int* y, int* z);
+constexpr int kTileVariants2D = 3;
+
+// batches of independent solves (FP64 or FP32 float-pair arithmetic)
+cudaError_t prepare_batch_d1();
+cudaError_t prepare_batch_d2();
+void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
+void launch_batch_d2(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
 
 void launch_face_flux(int D, int prec, bool multid, int abar_t0, double gamma, double mu, double C_a,
                       double dt, const double* faces, long nfaces, double* F, double* tau, cudaStream_t s);

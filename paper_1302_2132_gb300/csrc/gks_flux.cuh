@@ -73,6 +73,7 @@ template <int D> struct Dims {
 // Macroscopic description of one Maxwellian.
 template <int D, class T> struct Maxw {
   T rho, U[D], lam, il;  // il = 1/(2 lambda)
+  T c, f4;               // |U|^2 + bK il and 4 lambda^2 / bK (used by every slope solve)
 };
 
 // Gas constants used by every face.
@@ -97,6 +98,8 @@ GKS_FN Maxw<D, T> maxwellian(const T* w, T bK) {
   }
   g.lam = g_div(bK * w[0], T(4) * (w[D + 1] - T(0.5) * w[0] * q));
   g.il = g_div(T(0.5), g.lam);
+  g.c = q + bK * g.il;
+  g.f4 = g_div(T(4) * g.lam * g.lam, bK);
   return g;
 }
 
@@ -213,6 +216,19 @@ GKS_FN void transverse(const Maxw<D, T>& g, T K, Trans<D, T>& t) {
   }
 }
 
+// <beta> for the transverse basis {1, v_s, Et} (the first row of the transverse table).
+template <int D, class T>
+GKS_FN void trans_mean(const Maxw<D, T>& g, T K, T* m1) {
+  T e = K * g.il;  // <xi^2>
+#pragma unroll
+  for (int s = 0; s < D - 1; ++s) {
+    m1[1 + s] = g.U[1 + s];
+    e += g.U[1 + s] * g.U[1 + s] + g.il;  // <v_s^2>
+  }
+  m1[0] = T(1);
+  m1[D] = T(0.5) * e;
+}
+
 // <u^n>, n = 0..6, over the full line.
 template <int D, class T>
 GKS_FN void u_full(const Maxw<D, T>& g, T* u) {
@@ -232,14 +248,14 @@ GKS_FN void u_half(const Maxw<D, T>& g, T sgn, T* u) {
   recur<7>(g.U[0], g.il, u);
 }
 
-// <psi_m> over the region of table u.
+// <psi_m> over the region of table u, m1 the transverse means.
 template <int D, class T>
-GKS_FN void psi_mean(const T* u, const Trans<D, T>& t, T* out) {
+GKS_FN void psi_mean(const T* u, const T* m1, T* out) {
   out[0] = u[0];
   out[1] = u[1];
 #pragma unroll
-  for (int s = 0; s < D - 1; ++s) out[2 + s] = u[0] * t.m1[1 + s];
-  out[D + 1] = T(0.5) * u[2] + u[0] * t.m1[D];
+  for (int s = 0; s < D - 1; ++s) out[2 + s] = u[0] * m1[1 + s];
+  out[D + 1] = T(0.5) * u[2] + u[0] * m1[D];
 }
 
 // acc[m] += s * <u^k gamma (a . psi) psi_m>, gamma = 1 (tg = -1) or v_tg.
@@ -300,24 +316,59 @@ GKS_FN void muscl(int lim, R s0, R s1, R s2, R s3, R h0, R h1, R h2, R h3, R& wl
   wr = s2 - R(0.5) * h2 * sr;
 }
 
+// The pair <u^k gamma (a . psi) psi_m> and <u^(k+1) gamma (a . psi) psi_m>, which share the u-moments
+// of A(u) and the transverse sums: acc_lo += s_lo * first, acc_hi += s_hi * second (k <= 1).
+template <int D, class T>
+GKS_FN void amom2(const T* u, const Trans<D, T>& t, int k, int tg, const T* a, T s_lo, T* acc_lo, T s_hi,
+                  T* acc_hi) {
+  constexpr int NB = D + 1;
+  const T hE = T(0.5) * a[D + 1];
+  T SA[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) SA[j] = a[0] * u[k + j] + a[1] * u[k + j + 1] + hE * u[k + j + 2];
+  T g1[NB], c2[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) g1[b] = tg < 0 ? t.m1[b] : t.m2[1 + tg][b];
+  T c1 = T(0);
+#pragma unroll
+  for (int b = 1; b < NB; ++b) c1 += a[b == D ? D + 1 : 1 + b] * g1[b];
+#pragma unroll
+  for (int tau = 1; tau < NB; ++tau) {
+    T q = T(0);
+#pragma unroll
+    for (int b = 1; b < NB; ++b) q += a[b == D ? D + 1 : 1 + b] * (tg < 0 ? t.m2[b][tau] : t.m3[tg][b][tau]);
+    c2[tau] = q;
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const T s = h ? s_hi : s_lo;
+    T* acc = h ? acc_hi : acc_lo;
+    const int kk = k + h;
+    acc[0] += s * (SA[h] * g1[0] + u[kk] * c1);
+    acc[1] += s * (SA[h + 1] * g1[0] + u[kk + 1] * c1);
+#pragma unroll
+    for (int v = 0; v < D - 1; ++v) acc[2 + v] += s * (SA[h] * g1[1 + v] + u[kk] * c2[1 + v]);
+    acc[D + 1] += s * (T(0.5) * (SA[h + 2] * g1[0] + u[kk + 2] * c1) + SA[h] * g1[D] + u[kk] * c2[D]);
+  }
+}
+
 // Coefficients a of a . psi with <(a . psi) psi> = rhs (already divided by rho): closed-form inverse
 // of the Maxwellian moment matrix.
 template <int D, class T>
 GKS_FN void slope(const Maxw<D, T>& g, T bK, const T* rhs, T* a) {
-  T R[D], q = T(0), UR = T(0);
+  T R[D], UR = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     R[i] = rhs[1 + i] - g.U[i] * rhs[0];
-    q += g.U[i] * g.U[i];
     UR += g.U[i] * R[i];
   }
-  const T c = q + bK * g.il;  // |U|^2 + bK / (2 lambda)
-  const T RE = T(2) * rhs[D + 1] - c * rhs[0];
-  const T aE = g_div(T(4) * g.lam * g.lam, bK) * (RE - T(2) * UR);
-  T a0 = rhs[0] - T(0.5) * aE * c;
+  const T RE = T(2) * rhs[D + 1] - g.c * rhs[0];
+  const T aE = g.f4 * (RE - T(2) * UR);
+  const T l2 = T(2) * g.lam;
+  T a0 = rhs[0] - T(0.5) * aE * g.c;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    a[1 + i] = T(2) * g.lam * R[i] - g.U[i] * aE;
+    a[1 + i] = l2 * R[i] - g.U[i] * aE;
     a0 -= g.U[i] * a[1 + i];
   }
   a[0] = a0;
@@ -424,15 +475,14 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
   // Eq. intermediatestate: w0 = rho_l <psi>_{l,u>0} + rho_r <psi>_{r,u<0}
   T w0[nv];
   T lP[7], rN[7];
-  Trans<D, T> trl, trr;
   u_half<D, T>(gl, T(1), lP);
   u_half<D, T>(gr, T(-1), rN);
-  transverse<D, T>(gl, K, trl);
-  transverse<D, T>(gr, K, trr);
   {
-    T a[nv], b[nv];
-    psi_mean<D, T>(lP, trl, a);
-    psi_mean<D, T>(rN, trr, b);
+    T a[nv], b[nv], ml[D + 1], mr[D + 1];
+    trans_mean<D, T>(gl, K, ml);
+    trans_mean<D, T>(gr, K, mr);
+    psi_mean<D, T>(lP, ml, a);
+    psi_mean<D, T>(rN, mr, b);
 #pragma unroll
     for (int m = 0; m < nv; ++m) w0[m] = gl.rho * a[m] + gr.rho * b[m];
   }
@@ -465,13 +515,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
   for (int sd = 0; sd < 2; ++sd) {
     const Maxw<D, T> g = sd ? gr : gl;
     Trans<D, T> ts;
-    {
-      const T* pa = &trl.m1[0];
-      const T* pb = &trr.m1[0];
-      T* pt = &ts.m1[0];
-#pragma unroll
-      for (int q = 0; q < (int)(sizeof(Trans<D, T>) / sizeof(T)); ++q) pt[q] = sd ? pb[q] : pa[q];
-    }
+    transverse<D, T>(g, K, ts);
     T half[7], a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
 #pragma unroll
     for (int n = 0; n < 7; ++n) half[n] = sd ? rN[n] : lP[n];
@@ -500,24 +544,22 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
       }
       slope<D, T>(g, bK, r, A);
     }
-    // Abar rhs: r4 rho/rho0 <(a u + b v) psi> + r5 rho/rho0 <A psi> over the half line
-    const T s4 = r4 * g.rho * i0, s5 = r5 * g.rho * i0;
-    amom<D, T>(half, ts, 1, -1, a, s4, rhs);
-    amom<D, T>(half, ts, 0, -1, A, s5, rhs);
-    // flux: rho [<u (T3 + T5 A) psi> + T4 (<u^2 a psi> + <u v b psi>)]
-    T c[nv];
+    // Abar rhs: r4 rho/rho0 <(a u + b v) psi> + r5 rho/rho0 <A psi> over the half line, and the
+    // flux rho [T3 <u psi> + T5 <u A psi> + T4 (<u^2 a psi> + <u v b psi>)]: each polynomial once,
+    // at u^k for the rhs and u^(k+1) for the flux
+    const T s4 = r4 * g.rho * i0, s5 = r5 * g.rho * i0, s4f = Tc[4] * g.rho;
+    amom2<D, T>(half, ts, 1, -1, a, s4, rhs, s4f, F);
+    amom2<D, T>(half, ts, 0, -1, A, s5, rhs, Tc[5] * g.rho, F);
+    {
+      T m[nv];
+      psi_mean<D, T>(half + 1, ts.m1, m);  // <u psi> over the half line
+      const T s3 = Tc[3] * g.rho;
 #pragma unroll
-    for (int m = 0; m < nv; ++m) c[m] = Tc[5] * A[m];
-    c[0] += Tc[3];
-    amom<D, T>(half, ts, 1, -1, c, g.rho, F);
-    const T s4f = Tc[4] * g.rho;
-    amom<D, T>(half, ts, 2, -1, a, s4f, F);
+      for (int q = 0; q < nv; ++q) F[q] += s3 * m[q];
+    }
     if (MULTID) {
 #pragma unroll
-      for (int q = 0; q < D - 1; ++q) {
-        amom<D, T>(half, ts, 0, q, b[q], s4, rhs);
-        amom<D, T>(half, ts, 1, q, b[q], s4f, F);
-      }
+      for (int q = 0; q < D - 1; ++q) amom2<D, T>(half, ts, 0, q, b[q], s4, rhs, s4f, F);
     }
   }
 
@@ -539,8 +581,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
 #pragma unroll
       for (int n = 0; n < 7; ++n) half[n] = sd ? oF[n] - oP[n] : oP[n];
       slope<D, T>(g0, bK, r, ab);
-      amom<D, T>(half, tr0, 1, -1, ab, r1, rhs);
-      amom<D, T>(half, tr0, 2, -1, ab, s1f, F);
+      amom2<D, T>(half, tr0, 1, -1, ab, r1, rhs, s1f, F);
     }
     if (MULTID) {
       T r[nv], ab[nv];
@@ -549,8 +590,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
 #pragma unroll
         for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (tl[q][m] + tr[q][m]) * i0;
         slope<D, T>(g0, bK, r, ab);
-        amom<D, T>(oF, tr0, 0, q, ab, r1, rhs);
-        amom<D, T>(oF, tr0, 1, q, ab, s1f, F);
+        amom2<D, T>(oF, tr0, 0, q, ab, r1, rhs, s1f, F);
       }
     }
   }

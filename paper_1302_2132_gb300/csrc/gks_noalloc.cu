@@ -47,7 +47,7 @@ gks_status scratch_address(int dev, double** out) {
 template <int D>
 __global__ void __launch_bounds__(kThreadsNA) rate_partials(const double* W, long ncell, double gamma, double h0,
                                                             double h1, double h2, double* scratch) {
-  __shared__ double red[kThreadsNA / 32];
+  __shared__ double red[gks::kMaxWarps];
   const double h[3] = {h0, h1, h2};
   const long begin = (long)blockIdx.x * kCellsPerBlock;
   const long end = begin + kCellsPerBlock < ncell ? begin + kCellsPerBlock : ncell;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kThreadsNA) rate_partials(const double* W, lon
 
 // One block folds the partials written by this call (blocks [0, nblocks)) and stores cfl / max.
 __global__ void __launch_bounds__(kThreadsNA) finish_dt(double* scratch, int nblocks, double cfl) {
-  __shared__ double red[kThreadsNA / 32];
+  __shared__ double red[gks::kMaxWarps];
   double m = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += kThreadsNA) m = fmax(m, scratch[b]);
   m = gks::block_max<double>(m, red);

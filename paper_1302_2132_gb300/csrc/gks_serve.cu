@@ -533,8 +533,15 @@ gks_status gks_server_wait_all(gks_server* s, double timeout_s) {
   if (!s) return GKS_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);
   const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
-  while (!(s->pending.empty() && s->active.empty())) {
-    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) return GKS_ETIMEOUT;
+  // every submitted request finished (a request being admitted is in neither queue for a moment,
+  // so the statuses are what is checked)
+  auto all_finished = [&]() {
+    for (auto& kv : s->reqs)
+      if (kv.second->status == REQ_PENDING || kv.second->status == REQ_ACTIVE) return false;
+    return true;
+  };
+  while (!all_finished()) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !all_finished()) return GKS_ETIMEOUT;
   }
   for (auto& kv : s->reqs)
     if (kv.second->status == REQ_FAILED) return GKS_ECUDA;

@@ -22,15 +22,21 @@ enum { PREC_F64 = 0,    // double flux, double state
        PREC_F32 = 1,    // float flux, state as a pair of floats (hi + lo)
        PREC_F32D = 2 };  // float flux, double state
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;   // threads of the auxiliary kernels and of tile variant 0
+constexpr int kMaxWarps = 16;   // largest CTA of any tile variant: 512 threads
 
-template <int D> struct Tile;
-template <> struct Tile<1> { static constexpr int X = 256, Y = 1, Z = 1; };
-template <> struct Tile<2> { static constexpr int X = 32, Y = 15, Z = 1; };  // 1007 faces per 256 threads
-template <> struct Tile<3> { static constexpr int X = 16, Y = 8, Z = 4; };
+// Tile of cells owned by one CTA (variant 0 is the default; 2D has two more, chosen by the
+// autotuner).  Each 2D shape makes the face count of a tile fill whole rounds of its threads:
+// 32x15: 1007 faces / 256 threads, 64x7: 967 / 256, 32x31: 2047 / 512.
+template <int D, int V = 0> struct Tile;
+template <> struct Tile<1, 0> { static constexpr int X = 256, Y = 1, Z = 1, T = 256; };
+template <> struct Tile<2, 0> { static constexpr int X = 32, Y = 15, Z = 1, T = 256; };
+template <> struct Tile<2, 1> { static constexpr int X = 64, Y = 7, Z = 1, T = 256; };
+template <> struct Tile<2, 2> { static constexpr int X = 32, Y = 31, Z = 1, T = 512; };
+template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 256; };
 
-template <int D> struct TileGeom {
-  static constexpr int X = Tile<D>::X, Y = Tile<D>::Y, Z = Tile<D>::Z;
+template <int D, int V = 0> struct TileGeom {
+  static constexpr int X = Tile<D, V>::X, Y = Tile<D, V>::Y, Z = Tile<D, V>::Z, T = Tile<D, V>::T;
   static constexpr int HX = X + 4, HY = D >= 2 ? Y + 4 : 1, HZ = D >= 3 ? Z + 4 : 1;
   static constexpr int NH = HX * HY * HZ;  // cells with halo
   static constexpr int RX = X + 2, RY = D >= 2 ? Y + 2 : 1, RZ = D >= 3 ? Z + 2 : 1;
@@ -285,7 +291,7 @@ __device__ __forceinline__ R block_max(R v, R* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < (kThreads / 32) ? red[lane] : R(0);
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : R(0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   }
@@ -300,7 +306,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < (kThreads / 32) ? red[lane] : 0.0;
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   }
@@ -319,11 +325,12 @@ __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
 }
 
 // One tile of one step: every thread of the CTA calls it with the same arguments.
-template <int D, int PREC, bool MULTID>
+template <int D, int PREC, bool MULTID, int V = 0>
 __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
-  using G = TileGeom<D>;
+  using G = TileGeom<D, V>;
+  constexpr int kThreads = G::T;
   constexpr int nv = D + 2;
   constexpr int X = G::X, Y = G::Y, Z = G::Z, HX = G::HX, HY = G::HY, HZ = G::HZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -333,7 +340,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   R* wsx = Fs + (size_t)nv * G::NF;        // widths with halo
   R* wsy = wsx + HX;
   R* wsz = wsy + HY;
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kMaxWarps];
 
   const DevGrid& g = A.g;
   const int tiles_x = (g.n[0] + X - 1) / X;
@@ -615,11 +622,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   }
 }
 
-template <int D> constexpr int min_blocks(int prec) { return (prec != PREC_F64 && D <= 2) ? 2 : 1; }
+template <int D, int V = 0> constexpr int min_blocks(int prec) {
+  return (prec != PREC_F64 && D <= 2) ? 512 / Tile<D, V>::T : 1;
+}
 
-template <int D, int PREC, bool MULTID>
-__global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) step_kernel(const __grid_constant__ StepArgs A) {
-  step_tile<D, PREC, MULTID>(A, blockIdx.x);
+template <int D, int PREC, bool MULTID, int V = 0>
+__global__ void __launch_bounds__(Tile<D, V>::T, min_blocks<D, V>(PREC))
+    step_kernel(const __grid_constant__ StepArgs A) {
+  step_tile<D, PREC, MULTID, V>(A, blockIdx.x);
 }
 
 // ---- batches of independent solves --------------------------------------------------------------
@@ -672,18 +682,18 @@ cudaError_t prepare_batch() {
                               (int)sm);
 }
 
-template <int D, int PREC, bool MULTID>
+template <int D, int PREC, bool MULTID, int V = 0>
 void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>();
-  step_kernel<D, PREC, MULTID><<<nblocks, kThreads, sm, s>>>(A);
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>();
+  step_kernel<D, PREC, MULTID, V><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
 }
 
-template <int D, int PREC, bool MULTID>
+template <int D, int PREC, bool MULTID, int V = 0>
 cudaError_t prepare_step() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>();
-  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>();
+  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }
 

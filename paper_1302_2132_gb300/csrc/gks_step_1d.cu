@@ -23,4 +23,17 @@ void launch_step_d1(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
   else launch_step<1, PREC_F32D, false>(A, nblocks, s);
 }
 
+
+cudaError_t prepare_batch_d1() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = prepare_batch<1, PREC_F64, false>()) != cudaSuccess) e = r;
+  if ((r = prepare_batch<1, PREC_F32, false>()) != cudaSuccess) e = r;
+  return e;
+}
+
+void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s) {
+  if (prec == PREC_F64) launch_batch<1, PREC_F64, false>(B, nblocks, s);
+  else launch_batch<1, PREC_F32, false>(B, nblocks, s);
+}
+
 }  // namespace gks

@@ -30,4 +30,24 @@ void launch_step_d2(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
   else launch_step<2, PREC_F32D, false>(A, nblocks, s);
 }
 
+
+cudaError_t prepare_batch_d2() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = prepare_batch<2, PREC_F64, false>()) != cudaSuccess) e = r;
+  if ((r = prepare_batch<2, PREC_F32, false>()) != cudaSuccess) e = r;
+  if ((r = prepare_batch<2, PREC_F64, true>()) != cudaSuccess) e = r;
+  if ((r = prepare_batch<2, PREC_F32, true>()) != cudaSuccess) e = r;
+  return e;
+}
+
+void launch_batch_d2(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s) {
+  if (multid) {
+    if (prec == PREC_F64) launch_batch<2, PREC_F64, true>(B, nblocks, s);
+    else launch_batch<2, PREC_F32, true>(B, nblocks, s);
+    return;
+  }
+  if (prec == PREC_F64) launch_batch<2, PREC_F64, false>(B, nblocks, s);
+  else launch_batch<2, PREC_F32, false>(B, nblocks, s);
+}
+
 }  // namespace gks

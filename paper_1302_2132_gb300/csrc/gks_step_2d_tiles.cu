@@ -1,0 +1,35 @@
+// Alternative 2D tile shapes of the FP32 step kernel, chosen at run time by the autotuner.
+#include "gks_dispatch.h"
+#include "gks_step.cuh"
+
+namespace gks {
+
+cudaError_t prepare_step_d2_variants() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = prepare_step<2, PREC_F32, false, 1>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<2, PREC_F32, true, 1>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<2, PREC_F32, false, 2>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<2, PREC_F32, true, 2>()) != cudaSuccess) e = r;
+  return e;
+}
+
+void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
+  if (variant == 1) {
+    if (multid) launch_step<2, PREC_F32, true, 1>(A, nblocks, s);
+    else launch_step<2, PREC_F32, false, 1>(A, nblocks, s);
+  } else {
+    if (multid) launch_step<2, PREC_F32, true, 2>(A, nblocks, s);
+    else launch_step<2, PREC_F32, false, 2>(A, nblocks, s);
+  }
+}
+
+void tile_shape(int D, int variant, int* x, int* y, int* z) {
+  if (D == 1) { *x = Tile<1, 0>::X; *y = 1; *z = 1; return; }
+  if (D == 3) { *x = Tile<3, 0>::X; *y = Tile<3, 0>::Y; *z = Tile<3, 0>::Z; return; }
+  if (variant == 1) { *x = Tile<2, 1>::X; *y = Tile<2, 1>::Y; }
+  else if (variant == 2) { *x = Tile<2, 2>::X; *y = Tile<2, 2>::Y; }
+  else { *x = Tile<2, 0>::X; *y = Tile<2, 0>::Y; }
+  *z = 1;
+}
+
+}  // namespace gks

@@ -84,6 +84,8 @@ def load():
     L.gks_last_error.argtypes = [H]
     L.gks_last_error.restype = ctypes.c_char_p
     L.gks_face_record_len.argtypes = [_I]
+    L.gks_tile_shape.argtypes = [H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    L.gks_tile_shape.restype = _I
     L.gks_probe_alu.argtypes = [_PD, _PD]
     L.gks_probe_alu.restype = _I
     L.gks_face_op_count.argtypes = [_I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]
@@ -261,6 +263,12 @@ class Solver:
         ms, n = _D(), ctypes.c_longlong()
         self._check(load().gks_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def tile_shape(self):
+        """(variant, tx, ty, tz) of the step kernel's tile (2D FP32: chosen by the autotuner)."""
+        v, x, y, z = _I(), _I(), _I(), _I()
+        self._check(load().gks_tile_shape(self._h, ctypes.byref(v), ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)))
+        return v.value, x.value, y.value, z.value
 
     def close(self):
         if self._h is not None:

@@ -329,3 +329,31 @@ def test_full_size_2d_turbulence_sampled_cells(prec):
     # per-cell increments (double, or single precision for the FP32 flux)
     W0 = oracle_case(spec, **kw).prim_to_cons(spec["prim"].ravel()).reshape(4, -1).sum(axis=1) * h * h
     assert np.all(np.abs(tot - W0) <= (1e-11 if prec == "fp64" else 1e-9) * (np.abs(W0) + 1.0))
+
+
+def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
+    """The three 2D FP32 tile shapes evaluate the same faces: their results agree to FP32 rounding
+    (different compiled kernels), and the autotuner keeps one of them."""
+    spec = inputs.turbulence(100, 2, seed=8)
+    kw = dict(turb_model=2, multid=1, mu=1e-5, precision="fp32")
+    out = []
+    for v in ("0", "1", "2"):
+        monkeypatch.setenv("GKS_TILE_VARIANT", v)
+        s = gpu_solver(spec, **kw)
+        s.set_state(spec["prim"].ravel(), layout="soa_prim")
+        s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+        s.step(nsteps=30, cfl=0.5)
+        assert s.tile_shape()[0] == int(v)
+        out.append(s.get_state())
+        s.close()
+    for W in out[1:]:
+        assert np.all(rel_err_per_var(W, out[0], 4) < 1e-6)
+    monkeypatch.delenv("GKS_TILE_VARIANT")
+    s = gpu_solver(spec, **kw)
+    s.set_state(spec["prim"].ravel(), layout="soa_prim")
+    s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+    s.step(nsteps=30, cfl=0.5)
+    v = s.tile_shape()
+    assert v[0] in (0, 1, 2) and v[1] * v[2] in (480, 448, 992)
+    assert np.all(rel_err_per_var(s.get_state(), out[0], 4) < 1e-6)
+    s.close()
