@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--serving", action="store_true", help="measure the serving form only")
     p.add_argument("--no-serving", action="store_true", help="leave the serving summary out")
     p.add_argument("--requests", type=int, default=4000)
+    p.add_argument("--accuracy", action="store_true", help="report FP32-form errors against the oracle")
     return p.parse_args()
 
 
@@ -279,7 +280,7 @@ def run_ours(args):
     multid = wl["kw"].get("expand") == "multid" and D > 1
     counts = gks.face_op_count(D, multid, True)
     per_face = sum(counts[:3])
-    per_cell = CELL_OPS
+    per_cell = CELL_OPS + sum(gks.cell_op_count(D)[:3])
     ops_per_launch = faces_per_step * per_face + cells * per_cell
     avg_launch_s = kms / 1e3 / max(klaunch, 1)
     achieved = ops_per_launch / avg_launch_s / 1e12
@@ -336,8 +337,9 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# per-cell operations of the fused step besides the faces: turbulent relaxation time (velocity
-# gradient, strain rate, k-epsilon formula: about 60), update (nv x (2 x 3)), CFL rate (about 12)
+# per-cell operations of the fused step besides the faces and the reconstruction slopes (counted by
+# gks_cell_op_count): turbulent relaxation time (velocity gradient, strain rate, k-epsilon formula:
+# about 60), update (nv x (2 x 3)), CFL rate (about 12) -- a hand count
 CELL_OPS = 60 + 4 * 6 + 12
 
 
@@ -480,6 +482,56 @@ def serving_summary(count):
                    "50-500 steps; seed 4000; Poisson arrivals"}
 
 
+def run_accuracy(args):
+    """L1(rho) of the FP32 forms against the FP64 oracle after a run, on small instances of each
+    configuration (the oracle runs them in seconds on the host cores)."""
+    import torch
+    import oracle
+    from paper_1302_2132_gb300 import build, gks, inputs
+    torch.cuda.init()
+    build.build()
+    oracle.build()
+    gks.load()
+    cores = os.cpu_count() or 1
+    cases = []
+    s = inputs.sod_1d(400)
+    cases.append(("sod1d_400_to_t0.2", s, dict(mu=1e-5, C_a=1.0, limiter="vanleer", expand="directional"),
+                  dict(mu=1e-5, C_a=1.0, limiter=oracle.LIM_VANLEER, multid=0), 0, 0.2))
+    s = inputs.turbulence(64, 2, seed=1302)
+    cases.append(("turb2d_64_200steps", s, dict(mu=MU, turb_model="keps", expand="multid"),
+                  dict(mu=MU, turb_model=oracle.TURB_KEPS, multid=1), 200, 0.0))
+    s = inputs.shock_boundary_layer(96, 48)
+    cases.append(("shock_bl_96x48_300steps", s, dict(mu=s["mu"], T_wall=s["T_wall"], turb_model="komega", C_a=0.5,
+                                                   expand="multid"),
+                  dict(mu=s["mu"], T_wall=s["T_wall"], turb_model=oracle.TURB_KOMEGA, C_a=0.5, multid=1), 300, 0.0))
+    s = inputs.turbulence(24, 3, seed=2132)
+    cases.append(("turb3d_24_30steps", s, dict(mu=MU, turb_model="keps", expand="multid"),
+                  dict(mu=MU, turb_model=oracle.TURB_KEPS, multid=1), 30, 0.0))
+    out = {}
+    for name, spec, gkw, okw, nsteps, t_end in cases:
+        c = oracle.Case(spec["dim"], spec["n"], spec["dx"], spec["bc"], gamma=1.4, bc_prim=spec.get("bc_prim"), **okw)
+        W0 = c.prim_to_cons(spec["prim"].ravel())
+        f1 = spec.get("f1")
+        f2 = spec.get("f2")
+        f1 = None if f1 is None else f1.ravel()
+        f2 = None if f2 is None else f2.ravel()
+        Wo, to, no, st = c.run(W0, nsteps if nsteps else 100000, cfl=CFL, t_end=t_end, f1=f1, f2=f2, nthreads=cores)
+        rho_o = Wo.reshape(spec["dim"] + 2, -1)[0]
+        res = {"oracle_steps": no}
+        for prec in ("fp32", "fp32_acc64", "fp64"):
+            sol = gks.Solver(spec["dim"], spec["n"], spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"),
+                             gamma=1.4, precision=prec, **gkw)
+            sol.set_state(spec["prim"].ravel(), layout="soa_prim")
+            if f1 is not None:
+                sol.set_turbulence(f1, f2)
+            sol.step(nsteps=nsteps if nsteps else no, cfl=CFL, t_end=t_end)
+            rho = sol.get_state().reshape(spec["dim"] + 2, -1)[0]
+            res[prec + "_L1_rho_rel"] = float(np.sum(np.abs(rho - rho_o)) / np.sum(np.abs(rho_o)))
+            sol.close()
+        out[name] = res
+    print(json.dumps({"metric": "L1(rho) relative error against the FP64 oracle after the run", "cases": out}))
+
+
 def run_serving(args):
     import torch
     from paper_1302_2132_gb300 import build, gks
@@ -512,5 +564,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.serving:
         run_serving(a)
+    elif a.accuracy:
+        run_accuracy(a)
     else:
         run_ours(a)

@@ -144,9 +144,10 @@ gks_status gks_enable_timing(gks_handle* h, int enable);
 gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
 
 /* Tile shape of the handle's step kernel.  2D FP32 handles choose among three shapes (32x15 and
- * 64x7 cells per 256-thread CTA, 32x31 per 512-thread CTA) on their first gks_step: each is timed on
- * the step about to be taken and the fastest kept (and reused by later handles of the same grid);
- * the environment variable GKS_TILE_VARIANT=0|1|2 forces one.  The result does not depend on it. */
+ * 64x7 cells per 256-thread CTA, 32x31 per 512-thread CTA), 1D handles among 256, 31 and 63 cells
+ * per CTA, on their first gks_step: each is timed on the step about to be taken and the fastest kept
+ * (and reused by later handles of the same grid); the environment variable GKS_TILE_VARIANT=0|1|2
+ * forces one.  The result does not depend on it beyond rounding. */
 gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz);
 
 gks_status gks_destroy(gks_handle* h);
@@ -167,9 +168,12 @@ gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, doub
 
 /* Operation count of one interface flux as the device code is written (no GPU needed): counts[0..5]
  * = additions/subtractions, multiplications, divisions, square roots, exponentials, erfc.
- * with_recon adds the MUSCL reconstruction of the face (van Leer).  Operations on literal 0 or 1
- * are not counted.  Used to state the algorithmic FLOPs behind the roofline figures. */
+ * with_recon adds the face values of the MUSCL reconstruction from the cell slopes.  Operations on
+ * literal 0 or 1 are not counted.  Used to state the algorithmic FLOPs behind the roofline figures. */
 int gks_face_op_count(int dim, int expand, int with_recon, long long* counts);
+/* The same count for the per-cell part of the reconstruction: the limited (van Leer) slope of every
+ * variable along every axis, computed once per cell and step. */
+int gks_cell_op_count(int dim, long long* counts);
 
 /* CFL time step, as gks_compute_dt computes it, of a caller-held FP64 state on a uniform grid, for
  * callers that cannot allocate device memory (for example while another allocator holds all of

@@ -165,8 +165,10 @@ int tiles_for(const gks_handle* h, int variant) {
 }
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
-  if (h->D == 1)
-    launch_step_d1(h->prec, false, A, h->nblocks, h->stream);
+  if (h->D == 1 && variant > 0)
+    launch_step_d1_variant(variant, h->prec, A, tiles_for(h, variant), h->stream);
+  else if (h->D == 1)
+    launch_step_d1(h->prec, false, A, tiles_for(h, 0), h->stream);
   else if (h->D == 2 && variant > 0)
     launch_step_d2_variant(variant, h->multid, A, tiles_for(h, variant), h->stream);
   else if (h->D == 2)
@@ -281,16 +283,23 @@ struct TuneKey {
 std::map<TuneKey, int> g_tuned;
 std::mutex g_tuned_mutex;
 
+int n_variants(const gks_handle* h) {
+  if (h->D == 1) return kTileVariants1D;
+  if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
+  return 1;
+}
+
 gks_status autotune(gks_handle* h) {
   h->tuned = true;
-  if (h->D != 2 || h->prec != PREC_F32) return GKS_OK;
+  const int nvar = n_variants(h);
+  if (nvar == 1) return GKS_OK;
   const char* force = std::getenv("GKS_TILE_VARIANT");
   if (force) {
     const int v = std::atoi(force);
-    if (v >= 0 && v < kTileVariants2D) h->tile_variant = v;
+    if (v >= 0 && v < nvar) h->tile_variant = v;
     return GKS_OK;
   }
-  const TuneKey key{h->n[0], h->n[1], (int)h->multid};
+  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, (int)h->multid};
   {
     std::lock_guard<std::mutex> lk(g_tuned_mutex);
     auto it = g_tuned.find(key);
@@ -305,7 +314,7 @@ gks_status autotune(gks_handle* h) {
   const StepArgs A = step_args(h, h->step, 0);
   float best = 1e30f;
   int best_v = 0;
-  for (int v = 0; v < kTileVariants2D; ++v) {
+  for (int v = 0; v < nvar; ++v) {
     launch_step_variant(h, A, v);  // warm-up
     GKS_CK(h, cudaEventRecord(e0, h->stream));
     for (int r = 0; r < 3; ++r) launch_step_variant(h, A, v);
@@ -401,6 +410,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   if (!prepared[D]) {
     cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
     if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
+    if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bad(GKS_ECUDA, "kernel attribute setup failed");

@@ -91,24 +91,23 @@ static void count_face(int with_recon, Ops* out) {
   for (int c = 0; c < 4; ++c)
     for (int v = 0; v < nv; ++v) s[c][v] = Cnt::run(v == 0 ? 1.0 + 0.1 * c : (v == nv - 1 ? 2.5 + 0.2 * c : 0.1 * (c + v)));
   const Cnt h = Cnt::run(0.01);
+  // the step kernel reads the limited cell slopes from shared memory (computed once per cell, see
+  // count_cell) and forms the face values w = W +- (h/2) s
   for (int v = 0; v < nv; ++v) {
+    sl[v] = Cnt::run(0.3);
+    sr[v] = Cnt::run(0.2);
     if (with_recon) {
-      muscl<Cnt>(LIM_VANLEER, s[0][v], s[1][v], s[2][v], s[3][v], h, h, h, h, wl[v], wr[v], sl[v], sr[v]);
+      wl[v] = s[1][v] + Cnt(0.5) * h * sl[v];
+      wr[v] = s[2][v] - Cnt(0.5) * h * sr[v];
     } else {
       wl[v] = s[1][v];
       wr[v] = s[2][v];
-      sl[v] = Cnt::run(0.3);
-      sr[v] = Cnt::run(0.2);
     }
     cl[v] = s[1][v];
     cr[v] = s[2][v];
     for (int t = 0; t < Dims<D>::nt; ++t) {
-      tl[t][v] = M ? (with_recon ? limiter<Cnt>(LIM_VANLEER, (s[1][v] - s[0][v]) / h, (s[2][v] - s[1][v]) / h)
-                                 : Cnt::run(0.1))
-                   : Cnt(0.0);
-      tr[t][v] = M ? (with_recon ? limiter<Cnt>(LIM_VANLEER, (s[2][v] - s[1][v]) / h, (s[3][v] - s[2][v]) / h)
-                                 : Cnt::run(0.1))
-                   : Cnt(0.0);
+      tl[t][v] = M ? Cnt::run(0.1) : Cnt(0.0);
+      tr[t][v] = M ? Cnt::run(0.1) : Cnt(0.0);
     }
   }
   Gas<Cnt> gas;
@@ -122,7 +121,43 @@ static void count_face(int with_recon, Ops* out) {
   *out = g_ops;
 }
 
+// Per cell of the step: the van Leer-limited slope of every variable along every axis (two
+// differences over the centre distances, the limiter), done once per cell and axis.
+template <int D>
+static void count_cell(Ops* out) {
+  constexpr int nv = D + 2;
+  g_ops = Ops{0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < D; ++a) {
+    const Cnt wm = Cnt::run(0.01), w0 = Cnt::run(0.011), wp = Cnt::run(0.012);
+    const Cnt hm = Cnt(0.5) * (wm + w0), hp = Cnt(0.5) * (w0 + wp);
+    for (int v = 0; v < nv; ++v) {
+      const Cnt cm = Cnt::run(1.0), c0 = Cnt::run(1.1), cp = Cnt::run(1.3);
+      (void)limiter<Cnt>(LIM_VANLEER, (c0 - cm) / hm, (cp - c0) / hp);
+    }
+  }
+  *out = g_ops;
+}
+
 }  // namespace gks
+
+extern "C" int gks_cell_op_count(int dim, long long* counts) {
+  gks::Ops o{0, 0, 0, 0, 0, 0};
+  if (dim == 1)
+    gks::count_cell<1>(&o);
+  else if (dim == 2)
+    gks::count_cell<2>(&o);
+  else if (dim == 3)
+    gks::count_cell<3>(&o);
+  else
+    return 1;
+  counts[0] = o.add;
+  counts[1] = o.mul;
+  counts[2] = o.div;
+  counts[3] = o.sqrt;
+  counts[4] = o.exp;
+  counts[5] = o.erfc;
+  return 0;
+}
 
 extern "C" int gks_face_op_count(int dim, int expand, int with_recon, long long* counts) {
   gks::Ops o{0, 0, 0, 0, 0, 0};

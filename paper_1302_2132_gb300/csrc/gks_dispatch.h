@@ -19,6 +19,10 @@ cudaError_t prepare_step_d2_variants();
 void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void tile_shape(int D, int variant, int* x, int* y, int* z);
 constexpr int kTileVariants2D = 3;
+// 1D tile variants 1 and 2 (narrow tiles for small grids)
+cudaError_t prepare_step_d1_variants();
+void launch_step_d1_variant(int variant, int prec, const StepArgs& A, int nblocks, cudaStream_t s);
+constexpr int kTileVariants1D = 3;
 
 // batches of independent solves (FP64 or FP32 float-pair arithmetic)
 cudaError_t prepare_batch_d1();

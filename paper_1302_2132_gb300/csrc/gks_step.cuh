@@ -30,6 +30,9 @@ constexpr int kMaxWarps = 16;   // largest CTA of any tile variant: 512 threads
 // 32x15: 1007 faces / 256 threads, 64x7: 967 / 256, 32x31: 2047 / 512.
 template <int D, int V = 0> struct Tile;
 template <> struct Tile<1, 0> { static constexpr int X = 256, Y = 1, Z = 1, T = 256; };
+// narrow 1D tiles spread small grids over more SMs: 31 cells (32 faces) per warp, 63 per two warps
+template <> struct Tile<1, 1> { static constexpr int X = 31, Y = 1, Z = 1, T = 32; };
+template <> struct Tile<1, 2> { static constexpr int X = 63, Y = 1, Z = 1, T = 64; };
 template <> struct Tile<2, 0> { static constexpr int X = 32, Y = 15, Z = 1, T = 256; };
 template <> struct Tile<2, 1> { static constexpr int X = 64, Y = 7, Z = 1, T = 256; };
 template <> struct Tile<2, 2> { static constexpr int X = 32, Y = 31, Z = 1, T = 512; };
@@ -47,8 +50,9 @@ template <int D, int V = 0> struct TileGeom {
   static constexpr int NFZ = D >= 3 ? X * Y * (Z + 1) : 0;
   static constexpr int NF = NFX + NFY + NFZ;
   static constexpr int nv = D + 2;
-  template <class R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * ((size_t)nv * NH + NR + (size_t)nv * NF + HX + HY + HZ);
+  // pre: limited slopes of the first halo ring stored per cell and axis (D * nv * NR more values)
+  template <class R> static constexpr size_t smem_bytes(bool pre = true) {
+    return sizeof(R) * ((size_t)nv * NH + NR + (size_t)nv * NF + HX + HY + HZ + (pre ? (size_t)D * nv * NR : 0));
   }
 };
 
@@ -107,6 +111,9 @@ __device__ __forceinline__ Consts<R> make_consts(const DevGrid& g) {
 }
 
 template <int PREC> struct PrecT;
+
+// Cell slopes are precomputed in shared memory except where that would not fit (3D, FP64).
+template <int D, int PREC> __host__ __device__ constexpr bool pre_slopes() { return !(D == 3 && PREC == 0); }
 template <> struct PrecT<PREC_F64> { using R = double; using S = double; };
 template <> struct PrecT<PREC_F32> { using R = float; using S = float; };
 template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
@@ -335,11 +342,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   constexpr int X = G::X, Y = G::Y, Z = G::Z, HX = G::HX, HY = G::HY, HZ = G::HZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* Ws = (R*)smem_raw;                    // [nv][HZ][HY][HX]
+  constexpr bool PRE = pre_slopes<D, PREC>();
   R* taus = Ws + (size_t)nv * G::NH;       // [RZ][RY][RX]
   R* Fs = taus + G::NR;                    // [nv][NF]
   R* wsx = Fs + (size_t)nv * G::NF;        // widths with halo
   R* wsy = wsx + HX;
   R* wsz = wsy + HY;
+  R* Ss = wsz + HZ;  // PRE: [D][nv][NR] limited slopes of the ring cells along each axis
   __shared__ double red[kMaxWarps];
 
   const DevGrid& g = A.g;
@@ -416,6 +425,22 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       }
       const int pos[3] = {hi, hj, hk};
       taus[l] = tau_turb_cell<D, R>(g.turb_model, kc, Ws, G::NH, idx, strides, widths, pos, f1, f2);
+      if (PRE) {
+        // MUSCL slope of this cell along each axis (normal slope of the faces along that axis and
+        // tangential slope of the faces along the others)
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const R* wa = widths[a];
+          const R hm = R(0.5) * (wa[pos[a] - 1] + wa[pos[a]]);
+          const R hp = R(0.5) * (wa[pos[a]] + wa[pos[a] + 1]);
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            const R* pc = Ws + v * G::NH + idx;
+            Ss[(a * nv + v) * G::NR + l] =
+                limiter<R>(g.limiter, g_div(pc[0] - pc[-strides[a]], hm), g_div(pc[strides[a]] - pc[0], hp));
+          }
+        }
+      }
     }
   }
   __syncthreads();
@@ -462,13 +487,24 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
       const int pn = ax == 0 ? ci + 2 : (ax == 1 ? cj + 2 : ck + 2);  // halo coordinate of cell c
       const R h0 = wn[pn - 2], h1 = wn[pn - 1], h2 = wn[pn], h3 = wn[pn + 1];
+      // ring indices of the two cells
+      const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
+      const int rst[3] = {1, G::RX, G::RX * G::RY};
+      const int rl = rc - rst[ax];
       R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv];
 #pragma unroll
       for (int v = 0; v < nv; ++v) {
         const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
         const R* p = Ws + sv * G::NH + hc;
         const R s1 = p[-sn], s2 = p[0];
-        muscl<R>(g.limiter, p[-2 * sn], s1, s2, p[sn], h0, h1, h2, h3, wl[v], wr[v], sl[v], sr[v]);
+        if (PRE) {
+          sl[v] = Ss[(ax * nv + sv) * G::NR + rl];
+          sr[v] = Ss[(ax * nv + sv) * G::NR + rc];
+          wl[v] = s1 + R(0.5) * h1 * sl[v];
+          wr[v] = s2 - R(0.5) * h2 * sr[v];
+        } else {
+          muscl<R>(g.limiter, p[-2 * sn], s1, s2, p[sn], h0, h1, h2, h3, wl[v], wr[v], sl[v], sr[v]);
+        }
         cl[v] = s1;
         cr[v] = s2;
       }
@@ -487,7 +523,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         }
       }
       R tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
-      if (MULTID) {
+      if (MULTID && PRE) {
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) {
+          const int ta = perm[1 + s];
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+            tl[s][v] = Ss[(ta * nv + sv) * G::NR + rl];
+            tr[s][v] = Ss[(ta * nv + sv) * G::NR + rc];
+          }
+        }
+      } else if (MULTID) {
 #pragma unroll
         for (int s = 0; s < D - 1; ++s) {
           const int ta = perm[1 + s];
@@ -507,10 +554,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           }
         }
       }
-      // relaxation-time ring index of the two cells
-      const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
-      const int rst[3] = {1, G::RX, G::RX * G::RY};
-      const R tau_t = R(0.5) * (taus[rc - rst[ax]] + taus[rc]);
+      const R tau_t = R(0.5) * (taus[rl] + taus[rc]);
       R F[nv], tau;
       face_flux<D, R, MULTID>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
                               g.abar_t0, F, &tau);
@@ -670,14 +714,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) batch_step_kern
 template <int D, int PREC, bool MULTID>
 void launch_batch(const BatchArgs& B, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>();
+  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>());
   batch_step_kernel<D, PREC, MULTID><<<nblocks, kThreads, sm, s>>>(B);
 }
 
 template <int D, int PREC, bool MULTID>
 cudaError_t prepare_batch() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>();
+  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>());
   return cudaFuncSetAttribute(batch_step_kernel<D, PREC, MULTID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }
@@ -685,14 +729,14 @@ cudaError_t prepare_batch() {
 template <int D, int PREC, bool MULTID, int V = 0>
 void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>();
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>());
   step_kernel<D, PREC, MULTID, V><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
 }
 
 template <int D, int PREC, bool MULTID, int V = 0>
 cudaError_t prepare_step() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>();
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>());
   return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }

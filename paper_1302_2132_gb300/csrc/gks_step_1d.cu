@@ -36,4 +36,28 @@ void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cud
   else launch_batch<1, PREC_F32, false>(B, nblocks, s);
 }
 
+
+cudaError_t prepare_step_d1_variants() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = prepare_step<1, PREC_F64, false, 1>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<1, PREC_F32, false, 1>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<1, PREC_F32D, false, 1>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<1, PREC_F64, false, 2>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<1, PREC_F32, false, 2>()) != cudaSuccess) e = r;
+  if ((r = prepare_step<1, PREC_F32D, false, 2>()) != cudaSuccess) e = r;
+  return e;
+}
+
+void launch_step_d1_variant(int variant, int prec, const StepArgs& A, int nblocks, cudaStream_t s) {
+  if (variant == 1) {
+    if (prec == PREC_F64) launch_step<1, PREC_F64, false, 1>(A, nblocks, s);
+    else if (prec == PREC_F32) launch_step<1, PREC_F32, false, 1>(A, nblocks, s);
+    else launch_step<1, PREC_F32D, false, 1>(A, nblocks, s);
+  } else {
+    if (prec == PREC_F64) launch_step<1, PREC_F64, false, 2>(A, nblocks, s);
+    else if (prec == PREC_F32) launch_step<1, PREC_F32, false, 2>(A, nblocks, s);
+    else launch_step<1, PREC_F32D, false, 2>(A, nblocks, s);
+  }
+}
+
 }  // namespace gks

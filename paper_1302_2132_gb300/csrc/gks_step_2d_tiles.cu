@@ -24,7 +24,12 @@ void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nbl
 }
 
 void tile_shape(int D, int variant, int* x, int* y, int* z) {
-  if (D == 1) { *x = Tile<1, 0>::X; *y = 1; *z = 1; return; }
+  if (D == 1) {
+    *x = variant == 1 ? Tile<1, 1>::X : (variant == 2 ? Tile<1, 2>::X : Tile<1, 0>::X);
+    *y = 1;
+    *z = 1;
+    return;
+  }
   if (D == 3) { *x = Tile<3, 0>::X; *y = Tile<3, 0>::Y; *z = Tile<3, 0>::Z; return; }
   if (variant == 1) { *x = Tile<2, 1>::X; *y = Tile<2, 1>::Y; }
   else if (variant == 2) { *x = Tile<2, 2>::X; *y = Tile<2, 2>::Y; }

@@ -90,6 +90,8 @@ def load():
     L.gks_probe_alu.restype = _I
     L.gks_face_op_count.argtypes = [_I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_face_op_count.restype = _I
+    L.gks_cell_op_count.argtypes = [_I, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_cell_op_count.restype = _I
     L.gks_face_flux.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _V, ctypes.c_long, _V, _V, _V]
     for name in ("gks_create", "gks_set_state", "gks_get_state", "gks_set_turbulence", "gks_compute_dt",
                  "gks_step", "gks_get_time", "gks_set_time", "gks_residual", "gks_status_word",
@@ -295,6 +297,13 @@ def face_op_count(dim, expand=True, with_recon=True):
     """Static per-face operation count of the flux code: (add, mul, div, sqrt, exp, erfc)."""
     c = (ctypes.c_longlong * 6)()
     load().gks_face_op_count(dim, int(expand), int(with_recon), c)
+    return tuple(c)
+
+
+def cell_op_count(dim):
+    """Static per-cell operation count of the reconstruction slopes: (add, mul, div, sqrt, exp, erfc)."""
+    c = (ctypes.c_longlong * 6)()
+    load().gks_cell_op_count(dim, c)
     return tuple(c)
 
 

@@ -357,3 +357,14 @@ def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
     assert v[0] in (0, 1, 2) and v[1] * v[2] in (480, 448, 992)
     assert np.all(rel_err_per_var(s.get_state(), out[0], 4) < 1e-6)
     s.close()
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2"])
+def test_1d_tile_variants_match_oracle(monkeypatch, variant):
+    """Each 1D tile shape (256, 31 and 63 cells per CTA) gives the FP64 Sod step of the oracle."""
+    monkeypatch.setenv("GKS_TILE_VARIANT", variant)
+    spec = inputs.sod_1d(400)
+    s, c, Wg, Wo, res = step_both(spec, nsteps=3, C_a=1.0, limiter=1, mu=1e-5)
+    assert s.tile_shape()[:2] == (int(variant), {"0": 256, "1": 31, "2": 63}[variant])
+    assert np.all(rel_err_per_var(Wg, Wo, 3) < 1e-12)
+    s.close()
