@@ -237,6 +237,10 @@ gks_status gks_server_destroy(gks_server* s);
 /* Measured FMA throughput of the current device for FP32 and FP64 (independent FMA chains on every
  * SM, CUDA events), in TFLOP/s: context for the arithmetic roofline.  Synchronises the device. */
 gks_status gks_probe_alu(double* fp32_tflops, double* fp64_tflops);
+/* The FP32 chains of gks_probe_alu with the paired single-precision FMA (two FMAs per thread
+ * instruction, sm_100 and later), in TFLOP/s: whether pairing raises the FP32 rate or only halves the
+ * issue slots it takes.  Same conditions and errors as gks_probe_alu. */
+gks_status gks_probe_alu_packed(double* fp32x2_tflops);
 
 #ifdef __cplusplus
 }

@@ -125,6 +125,13 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
   }
   const int strides[3] = {1, 3, 9};
   const R* widths[3] = {wx, wy, wz};
+  // inverse distance between the centres of the two neighbours along each axis (position 1)
+  R igx[3], igy[3], igz[3];
+  igx[1] = g_rcp(R(0.5) * wx[0] + wx[1] + R(0.5) * wx[2]);
+  igy[1] = g_rcp(R(0.5) * wy[0] + wy[1] + R(0.5) * wy[2]);
+  igz[1] = g_rcp(R(0.5) * wz[0] + wz[1] + R(0.5) * wz[2]);
+  igx[0] = igx[2] = igy[0] = igy[2] = igz[0] = igz[2] = R(1);
+  const R* igrad[3] = {igx, igy, igz};
   const int pos[3] = {1, 1, 1};
   const int idx = 1 + (D >= 2 ? 3 : 0) + (D >= 3 ? 9 : 0);
   R f1 = R(0), f2 = R(0);
@@ -132,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
     f1 = ((const R*)A.f1)[c];
     if (g.turb_model != TURB_MUT) f2 = ((const R*)A.f2)[c];
   }
-  R val = tau_turb_cell<D, R>(g.turb_model, kc, Wn, NN, idx, strides, widths, pos, f1, f2);
+  R val = tau_turb_cell<D, R>(g.turb_model, kc, Wn, NN, idx, strides, igrad, pos, f1, f2);
   if (what == 1) {  // rarefaction: (mu/p + tau_t) |div U|
     R w[nv];
     for (int v = 0; v < nv; ++v) w[v] = Wn[v * NN + idx];
@@ -501,6 +508,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   g.turb_model = model;
   g.limiter = num->limiter;
   g.abar_t0 = num->abar_mode == GKS_ABAR_T0;
+  set_consts(g);
   h->base.f1 = h->f1;
   h->base.f2 = h->f2;
   h->base.ctrl = h->ctrl;

@@ -39,7 +39,51 @@ __global__ void fma64_kernel(double* out, int n) {
   out[i] = a[0] + a[1] + a[2] + a[3];
 }
 
+// The same chains with the paired single-precision FMA (two lanes' worth of FMA per thread
+// instruction, sm_100 and later): shows whether pairing raises the FP32 rate or only saves issue slots.
+__global__ void fma32x2_kernel(float* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float2 a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = make_float2(1.0f + 1e-9f * (float)(i + 2 * k), 1.0f + 1e-9f * (float)(i + 2 * k + 1));
+  const float2 m = make_float2(0.999999f, 0.999999f), c = make_float2(1e-7f, 1e-7f);
+#pragma unroll 16
+  for (int it = 0; it < kIters; ++it)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = __ffma2_rn(a[k], m, c);
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s += a[k].x + a[k].y;
+  out[i] = s;
+}
+
 }  // namespace
+
+extern "C" gks_status gks_probe_alu_packed(double* fp32x2_tflops) {
+  int dev;
+  cudaDeviceProp p;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return GKS_ECUDA;
+  const int threads = 256, blocks = p.multiProcessorCount * 8, n = threads * blocks;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)n * sizeof(float)) != cudaSuccess) return GKS_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms = 0.0f;
+  fma32x2_kernel<<<blocks, threads>>>((float*)buf, n);
+  cudaEventRecord(e0);
+  fma32x2_kernel<<<blocks, threads>>>((float*)buf, n);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (fp32x2_tflops) *fp32x2_tflops = 2.0 * 8.0 * kIters * (double)n / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaGetLastError();
+  cudaFree(buf);
+  return e == cudaSuccess ? GKS_OK : GKS_ECUDA;
+}
 
 extern "C" gks_status gks_probe_alu(double* fp32_tflops, double* fp64_tflops) {
   int dev;

@@ -223,6 +223,7 @@ bool admit(gks_server* s, Req* r) {
   g.turb_model = TURB_NONE;
   g.limiter = q.limiter;
   g.abar_t0 = 0;
+  set_consts(g);
   base_args.ctrl = ctrl;
   for (int ph = 0; ph < 6; ++ph) {
     StepArgs A = base_args;

@@ -50,9 +50,13 @@ template <int D, int V = 0> struct TileGeom {
   static constexpr int NFZ = D >= 3 ? X * Y * (Z + 1) : 0;
   static constexpr int NF = NFX + NFY + NFZ;
   static constexpr int nv = D + 2;
-  // pre: limited slopes of the first halo ring stored per cell and axis (D * nv * NR more values)
-  template <class R> static constexpr size_t smem_bytes(bool pre = true) {
-    return sizeof(R) * ((size_t)nv * NH + NR + (size_t)nv * NF + HX + HY + HZ + (pre ? (size_t)D * nv * NR : 0));
+  // pre: limited slopes of the first halo ring stored per cell and axis (D * nv * NR more values);
+  // then the two turbulence fields of the ring and, for the float-pair state, the low words of the
+  // tile's own cells (staged with the state so that the tile waits on global memory once)
+  template <class R> static constexpr size_t smem_bytes(bool pre, bool lo) {
+    return sizeof(R) * ((size_t)nv * NH + NR + (size_t)nv * NF + 3 * (HX + HY + HZ) + (pre ? (size_t)D * nv * NR : 0) +
+                        2 * (size_t)NR) +
+           (lo ? sizeof(float) * (size_t)nv * NC : 0);
   }
 };
 
@@ -67,6 +71,11 @@ struct Ctrl {
   unsigned long long linf[5];
 };
 
+// Gas and model constants in the arithmetic type.
+template <class R> struct Consts {
+  R gamma, mu, C_mu, beta_star, T_wall, bK, K, C_a;
+};
+
 struct DevGrid {
   int n[3];
   long ncell;
@@ -75,7 +84,37 @@ struct DevGrid {
   const double* dir[3][2];  // Dirichlet conservative states, [transverse cell][nv]
   double gamma, bK, K, mu, C_a, T_wall, C_mu, beta_star;
   int turb_model, limiter, abar_t0;
+  // the constants above in each arithmetic type, filled by set_consts on the host (kernels read
+  // them from the parameter bank instead of converting)
+  Consts<float> kf;
+  Consts<double> kd;
 };
+
+template <class R>
+inline void fill_consts(const DevGrid& g, Consts<R>& c) {
+  c.gamma = (R)g.gamma;
+  c.mu = (R)g.mu;
+  c.C_mu = (R)g.C_mu;
+  c.beta_star = (R)g.beta_star;
+  c.T_wall = (R)g.T_wall;
+  c.bK = (R)g.bK;
+  c.K = (R)g.K;
+  c.C_a = (R)g.C_a;
+}
+
+// Host: derive the per-type constants once the double-precision ones are set.
+inline void set_consts(DevGrid& g) {
+  fill_consts<float>(g, g.kf);
+  fill_consts<double>(g, g.kd);
+}
+
+template <class R>
+__device__ __forceinline__ Consts<R> make_consts(const DevGrid& g) {
+  if constexpr (sizeof(R) == sizeof(float))
+    return g.kf;
+  else
+    return g.kd;
+}
 
 struct StepArgs {
   DevGrid g;
@@ -91,24 +130,6 @@ struct StepArgs {
   int resid;   // accumulate residual norms in this step
 };
 
-// Gas and model constants in the arithmetic type (converted once per CTA).
-template <class R> struct Consts {
-  R gamma, mu, C_mu, beta_star, T_wall, bK, K, C_a;
-};
-
-template <class R>
-__device__ __forceinline__ Consts<R> make_consts(const DevGrid& g) {
-  Consts<R> c;
-  c.gamma = (R)g.gamma;
-  c.mu = (R)g.mu;
-  c.C_mu = (R)g.C_mu;
-  c.beta_star = (R)g.beta_star;
-  c.T_wall = (R)g.T_wall;
-  c.bK = (R)g.bK;
-  c.K = (R)g.K;
-  c.C_a = (R)g.C_a;
-  return c;
-}
 
 template <int PREC> struct PrecT;
 
@@ -120,6 +141,24 @@ template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
 
 __device__ __forceinline__ long cell_index(const DevGrid& g, int i, int j, int k) {
   return ((long)k * g.n[1] + j) * g.n[0] + i;
+}
+
+// Asynchronous global -> shared copy of one 4- or 8-byte element (cp.async, completed by
+// cp_async_wait_all); the thread's registers are not involved, so all of a tile's loads are in
+// flight together.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "element copies of 4 or 8 bytes");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ bool in_grid(const DevGrid& g, int D, int i, int j, int k) {
+  return i >= 0 && i < g.n[0] && (D < 2 || (j >= 0 && j < g.n[1])) && (D < 3 || (k >= 0 && k < g.n[2]));
 }
 
 template <class R>
@@ -232,9 +271,10 @@ __device__ __forceinline__ R load_field(const StepArgs& A, const void* f, int D,
 
 // Turbulent part of the relaxation time of one cell (Eqs. tauttrivial, tautchen, tautchenadjusted
 // with T = p/rho); S = sqrt(2 S_ij S_ij) from central differences of the velocity.
+// igrad[a][p] = 1 / (distance between the centres of halo cells p - 1 and p + 1 along axis a).
 template <int D, class R>
 __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, const R* Ws, int stride_v, int idx,
-                                           const int* strides, const R* const* widths, const int* pos,
+                                           const int* strides, const R* const* igrad, const int* pos,
                                            R f1, R f2) {
   if (turb_model == TURB_NONE) return R(0);
   R w[D + 2];
@@ -247,12 +287,11 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const int im = idx - strides[a], ip = idx + strides[a];
-    const R* wd = widths[a];
-    const R dist = R(0.5) * wd[pos[a] - 1] + wd[pos[a]] + R(0.5) * wd[pos[a] + 1];
-    const R rm = Ws[im], rp = Ws[ip];
+    const R id = igrad[a][pos[a]];
+    const R irm = g_rcp(Ws[im]), irp = g_rcp(Ws[ip]);
 #pragma unroll
     for (int b = 0; b < D; ++b)
-      grad[a][b] = g_div(g_div(Ws[(1 + b) * stride_v + ip], rp) - g_div(Ws[(1 + b) * stride_v + im], rm), dist);
+      grad[a][b] = (Ws[(1 + b) * stride_v + ip] * irp - Ws[(1 + b) * stride_v + im] * irm) * id;
   }
   R s2 = R(0);
 #pragma unroll
@@ -275,13 +314,12 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
 }
 
 __device__ __forceinline__ double step_dt(const StepArgs& A) {
+  // every control word is read up front: one round trip to memory
   const Ctrl* c = A.ctrl;
-  double dt = c->dt_fixed;
-  if (!(dt > 0.0)) dt = c->cfl / __longlong_as_double((long long)c->rate[A.slot]);
-  if (c->t_end > 0.0) {
-    const double t = c->t[A.tslot];
-    dt = (t >= c->t_end) ? 0.0 : fmin(dt, c->t_end - t);
-  }
+  const double dt_fixed = c->dt_fixed, cfl = c->cfl, t_end = c->t_end, t = c->t[A.tslot];
+  const unsigned long long rate = c->rate[A.slot];
+  double dt = dt_fixed > 0.0 ? dt_fixed : cfl / __longlong_as_double((long long)rate);
+  if (t_end > 0.0) dt = (t >= t_end) ? 0.0 : fmin(dt, t_end - t);
   return dt;
 }
 
@@ -303,6 +341,50 @@ __device__ __forceinline__ R block_max(R v, R* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   }
   return v;  // valid in thread 0
+}
+
+// Block maximum of a non-negative CFL rate, returned (in thread 0) as the bit pattern of the double
+// that atomicMax folds into the control block.  Single precision reduces in float; double precision
+// reduces the bit patterns as unsigned integers (non-negative doubles order like their bits), which
+// keeps the reduction off the FP64 pipe.  A NaN rate counts as zero, as fmax would treat it.
+template <class R>
+__device__ __forceinline__ unsigned long long block_max_rate(R v, double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    float* rf = (float*)red;
+    float m = v == v ? (float)v : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (lane == 0) rf[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+      m = lane < (int)(blockDim.x >> 5) ? rf[lane] : 0.0f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    return (unsigned long long)__double_as_longlong((double)m);
+  } else {
+    unsigned long long* ru = (unsigned long long*)red;
+    unsigned long long m = v == v ? (unsigned long long)__double_as_longlong((double)v) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+      m = t > m ? t : m;
+    }
+    __syncthreads();
+    if (lane == 0) ru[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+      m = lane < (int)(blockDim.x >> 5) ? ru[lane] : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+      }
+    }
+    return m;
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -348,7 +430,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   R* wsx = Fs + (size_t)nv * G::NF;        // widths with halo
   R* wsy = wsx + HX;
   R* wsz = wsy + HY;
-  R* Ss = wsz + HZ;  // PRE: [D][nv][NR] limited slopes of the ring cells along each axis
+  R* icx = wsz + HZ;  // 1 / centre distance between halo cells p - 1 and p, per axis
+  R* icy = icx + HX;
+  R* icz = icy + HY;
+  R* igx = icz + HZ;  // 1 / (distance between the centres of p - 1 and p + 1), per axis
+  R* igy = igx + HX;
+  R* igz = igy + HY;
+  R* Ss = igz + HZ;  // PRE: [D][nv][NR] limited slopes of the ring cells along each axis
+  R* Fl = Ss + (PRE ? (size_t)D * nv * G::NR : 0);  // [2][NR] turbulence fields of the ring cells
+  float* Lo = (float*)(Fl + 2 * G::NR);             // PREC_F32: [nv][NC] low words of the tile's cells
+  // the stored type is the arithmetic type (FP64, FP32 pair): in-grid cells are copied as they are
+  constexpr bool ASYNC = sizeof(S) == sizeof(R);
   __shared__ double red[kMaxWarps];
 
   const DevGrid& g = A.g;
@@ -358,13 +450,76 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   const int oy = D >= 2 ? ((b / tiles_x) % tiles_y) * Y : 0;
   const int oz = D >= 3 ? (b / (tiles_x * tiles_y)) * Z : 0;
   const int tid = threadIdx.x;
-
+  const Consts<R> kc = make_consts<R>(g);
   __shared__ double s_dt;
-  __shared__ Consts<R> s_k;
+
+  // ---- stage the tile with two halo layers, the ring's turbulence fields and the low words ------
+  // In-grid cells are copied asynchronously; ghost cells are resolved by the boundary rules.
+  for (int l = tid; l < G::NH; l += kThreads) {
+    const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
+    const int gi = ox + hi - 2, gj = D >= 2 ? oy + hj - 2 : 0, gk = D >= 3 ? oz + hk - 2 : 0;
+    if (ASYNC && in_grid(g, D, gi, gj, gk)) {
+      const S* src = (const S*)A.Win + cell_index(g, gi, gj, gk);
+#pragma unroll
+      for (int v = 0; v < nv; ++v) cp_async<sizeof(S)>(&Ws[v * G::NH + l], src + (long)v * g.ncell);
+    } else {
+      R w[nv];
+      load_cell<D, PREC>(A, kc, gi, gj, gk, w);
+#pragma unroll
+      for (int v = 0; v < nv; ++v) Ws[v * G::NH + l] = w[v];
+    }
+  }
+  if (g.turb_model != TURB_NONE) {
+    const bool two = g.turb_model != TURB_MUT;
+    for (int l = tid; l < G::NR; l += kThreads) {
+      const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
+      const int gi = ox + ri - 1, gj = D >= 2 ? oy + rj - 1 : 0, gk = D >= 3 ? oz + rk - 1 : 0;
+      if (in_grid(g, D, gi, gj, gk)) {
+        const long c = cell_index(g, gi, gj, gk);
+        cp_async<sizeof(R)>(&Fl[l], (const R*)A.f1 + c);
+        if (two) cp_async<sizeof(R)>(&Fl[G::NR + l], (const R*)A.f2 + c);
+      } else {
+        Fl[l] = load_field<R>(A, A.f1, D, gi, gj, gk);
+        if (two) Fl[G::NR + l] = load_field<R>(A, A.f2, D, gi, gj, gk);
+      }
+    }
+  }
+  if (PREC == PREC_F32) {
+    for (int l = tid; l < G::NC; l += kThreads) {
+      const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
+      const int gi = ox + li, gj = oy + lj, gk = oz + lk;
+      if (!in_grid(g, D, gi, gj, gk)) continue;
+      const float* src = A.Win_lo + cell_index(g, gi, gj, gk);
+#pragma unroll
+      for (int v = 0; v < nv; ++v) cp_async<4>(&Lo[v * G::NC + l], src + (long)v * g.ncell);
+    }
+  }
+  for (int l = tid; l < HX + HY + HZ; l += kThreads) {
+    // padded width index (cell + 2), clamped to the two ghost layers; the inverse distances make
+    // the slope and gradient quotients products
+    const int a = l < HX ? 0 : (l < HX + HY ? 1 : 2);
+    const int p = a == 0 ? l : (a == 1 ? l - HX : l - HX - HY);
+    R* wd = a == 0 ? wsx : (a == 1 ? wsy : wsz);
+    R* ic = a == 0 ? icx : (a == 1 ? icy : icz);
+    R* ig = a == 0 ? igx : (a == 1 ? igy : igz);
+    if (a < D) {
+      const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 3;
+      const R wm = (R)g.w[a][min(max(o + p - 1, 0), top)];
+      const R w0 = (R)g.w[a][min(o + p, top)];
+      const R wp = (R)g.w[a][min(o + p + 1, top)];
+      wd[p] = w0;
+      ic[p] = g_rcp(R(0.5) * (wm + w0));
+      ig[p] = g_rcp(R(0.5) * wm + w0 + R(0.5) * wp);
+    } else {
+      wd[p] = R(1);
+      ic[p] = R(1);
+      ig[p] = R(1);
+    }
+  }
+  // the time step of this step (thread 0), read while the tile's copies are in flight
   if (tid == 0) {
     const double dtv = step_dt(A);
     s_dt = dtv;
-    s_k = make_consts<R>(A.g);
     if (b == 0) {
       Ctrl* c = A.ctrl;
       c->t[A.tslot ^ 1] = c->t[A.tslot] + dtv;
@@ -372,9 +527,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       c->last_dt = dtv;
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   const double dt_d = s_dt;
-  const Consts<R> kc = s_k;
   if (dt_d == 0.0) {  // t_end reached: carry the state over
     for (int l = tid; l < G::NC; l += kThreads) {
       const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
@@ -390,54 +545,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   }
   const R dt = (R)dt_d;
 
-  // ---- stage the tile with two halo layers -------------------------------------------------
-  for (int l = tid; l < G::NH; l += kThreads) {
-    const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
-    R w[nv];
-    load_cell<D, PREC>(A, kc, ox + hi - 2, D >= 2 ? oy + hj - 2 : 0, D >= 3 ? oz + hk - 2 : 0, w);
-#pragma unroll
-    for (int v = 0; v < nv; ++v) Ws[v * G::NH + l] = w[v];
-  }
-  for (int l = tid; l < HX + HY + HZ; l += kThreads) {
-    // padded width index (cell + 2), clamped to the two ghost layers
-    if (l < HX)
-      wsx[l] = (R)g.w[0][min(ox + l, g.n[0] + 3)];
-    else if (l < HX + HY)
-      wsy[l - HX] = D >= 2 ? (R)g.w[1][min(oy + (l - HX), g.n[1] + 3)] : R(1);
-    else
-      wsz[l - HX - HY] = D >= 3 ? (R)g.w[2][min(oz + (l - HX - HY), g.n[2] + 3)] : R(1);
-  }
-  __syncthreads();
-
   // ---- turbulent relaxation time on the tile and its first halo ring --------------------------
   {
     const int strides[3] = {1, HX, HX * HY};
-    const R* widths[3] = {wsx, wsy, wsz};
+    const R* igrad[3] = {igx, igy, igz};
+    const R* icent[3] = {icx, icy, icz};
     for (int l = tid; l < G::NR; l += kThreads) {
       const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
       const int hi = ri + 1, hj = D >= 2 ? rj + 1 : 0, hk = D >= 3 ? rk + 1 : 0;
       const int idx = (hk * HY + hj) * HX + hi;
       R f1 = R(0), f2 = R(0);
-      const int gi = ox + ri - 1, gj = D >= 2 ? oy + rj - 1 : 0, gk = D >= 3 ? oz + rk - 1 : 0;
       if (g.turb_model != TURB_NONE) {
-        f1 = load_field<R>(A, A.f1, D, gi, gj, gk);
-        if (g.turb_model != TURB_MUT) f2 = load_field<R>(A, A.f2, D, gi, gj, gk);
+        f1 = Fl[l];
+        if (g.turb_model != TURB_MUT) f2 = Fl[G::NR + l];
       }
       const int pos[3] = {hi, hj, hk};
-      taus[l] = tau_turb_cell<D, R>(g.turb_model, kc, Ws, G::NH, idx, strides, widths, pos, f1, f2);
+      taus[l] = tau_turb_cell<D, R>(g.turb_model, kc, Ws, G::NH, idx, strides, igrad, pos, f1, f2);
       if (PRE) {
         // MUSCL slope of this cell along each axis (normal slope of the faces along that axis and
         // tangential slope of the faces along the others)
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          const R* wa = widths[a];
-          const R hm = R(0.5) * (wa[pos[a] - 1] + wa[pos[a]]);
-          const R hp = R(0.5) * (wa[pos[a]] + wa[pos[a] + 1]);
+          const R im = icent[a][pos[a]], ip = icent[a][pos[a] + 1];
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
             const R* pc = Ws + v * G::NH + idx;
             Ss[(a * nv + v) * G::NR + l] =
-                limiter<R>(g.limiter, g_div(pc[0] - pc[-strides[a]], hm), g_div(pc[strides[a]] - pc[0], hp));
+                limiter<R>(g.limiter, (pc[0] - pc[-strides[a]]) * im, (pc[strides[a]] - pc[0]) * ip);
           }
         }
       }
@@ -599,11 +733,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       const int gc[3] = {gi, gj, gk};
       for (int d = 0; d < D; ++d) vol *= g.w[d][gc[d] + 2];
     }
+    // the cell's old state: staged in shared memory (FP64, float pair), else read from the grid
+    const int hidx = ((lk + (D >= 3 ? 2 : 0)) * HY + (lj + (D >= 2 ? 2 : 0))) * HX + (li + 2);
 #pragma unroll
     for (int v = 0; v < nv; ++v) {
       const long gidx = (long)v * g.ncell + c;
       if (PREC == PREC_F64) {
-        double w = ((const double*)A.Win)[gidx];
+        double w = (double)Ws[v * G::NH + hidx];
         const double w_old = w;
 #pragma unroll
         for (int d = 0; d < D; ++d) w -= ((double)Fs[v * G::NF + fp[d]] - (double)Fs[v * G::NF + fm[d]]) / (double)h[d];
@@ -622,7 +758,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         double wd = 0.0;
         if (PREC == PREC_F32) {
           // (hi, lo) += inc with an error-free sum, then renormalise
-          const float hi = ((const float*)A.Win)[gidx], lo = A.Win_lo[gidx];
+          const float hi = (float)Ws[v * G::NH + hidx], lo = Lo[v * G::NC + l];
           const float s = hi + inc;
           const float bb = s - hi;
           const float err = (hi - (s - bb)) + (inc - bb);
@@ -651,8 +787,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     if (!(wn[0] > R(0)) || !(p > R(0))) bad = 1u;
     rmax = fmax(rmax, cell_rate<D, R>(wn, kc.gamma, h));
   }
-  const double bmax = block_max<double>((double)rmax, red);
-  if (tid == 0) atomic_max_nonneg(&A.ctrl->rate[(A.slot + 1) % 3], bmax);
+  const unsigned long long bmax = block_max_rate<R>(rmax, red);
+  if (tid == 0) atomicMax(&A.ctrl->rate[(A.slot + 1) % 3], bmax);
   if (__syncthreads_or(bad) && tid == 0) atomicOr(&A.ctrl->status, 1u);
   if (A.resid) {
     for (int v = 0; v < nv; ++v) {
@@ -714,14 +850,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) batch_step_kern
 template <int D, int PREC, bool MULTID>
 void launch_batch(const BatchArgs& B, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>());
+  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
   batch_step_kernel<D, PREC, MULTID><<<nblocks, kThreads, sm, s>>>(B);
 }
 
 template <int D, int PREC, bool MULTID>
 cudaError_t prepare_batch() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>());
+  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
   return cudaFuncSetAttribute(batch_step_kernel<D, PREC, MULTID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }
@@ -729,14 +865,14 @@ cudaError_t prepare_batch() {
 template <int D, int PREC, bool MULTID, int V = 0>
 void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>());
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
   step_kernel<D, PREC, MULTID, V><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
 }
 
 template <int D, int PREC, bool MULTID, int V = 0>
 cudaError_t prepare_step() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>());
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
   return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }

@@ -88,6 +88,8 @@ def load():
     L.gks_tile_shape.restype = _I
     L.gks_probe_alu.argtypes = [_PD, _PD]
     L.gks_probe_alu.restype = _I
+    L.gks_probe_alu_packed.argtypes = [_PD]
+    L.gks_probe_alu_packed.restype = _I
     L.gks_face_op_count.argtypes = [_I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_face_op_count.restype = _I
     L.gks_cell_op_count.argtypes = [_I, ctypes.POINTER(ctypes.c_longlong)]
@@ -291,6 +293,15 @@ def probe_alu():
     if st != OK:
         raise GksError(st, "gks_probe_alu failed")
     return a.value, b.value
+
+
+def probe_alu_packed():
+    """Measured throughput of the paired FP32 FMA (two FMAs per thread instruction), TFLOP/s."""
+    a = _D()
+    st = load().gks_probe_alu_packed(ctypes.byref(a))
+    if st != OK:
+        raise GksError(st, "gks_probe_alu_packed failed")
+    return a.value
 
 
 def face_op_count(dim, expand=True, with_recon=True):
