@@ -14,11 +14,14 @@ void launch_step_d1(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
 void launch_step_d2(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void launch_step_d3(int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 
-// 2D FP32 tile variants 1 and 2 (variant 0 is launch_step_d2) and the tile shape of a variant
+// 2D FP32 tile variants 1 to 4 (variant 0 is launch_step_d2) and the tile shape of a variant
 cudaError_t prepare_step_d2_variants();
 void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void tile_shape(int D, int variant, int* x, int* y, int* z);
-constexpr int kTileVariants2D = 3;
+constexpr int kTileVariants2D = 5;
+// variants 3 and 4 (their own translation unit)
+cudaError_t prepare_step_d2_variants2();
+void launch_step_d2_variant2(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 // 1D tile variants 1 and 2 (narrow tiles for small grids)
 cudaError_t prepare_step_d1_variants();
 void launch_step_d1_variant(int variant, int prec, const StepArgs& A, int nblocks, cudaStream_t s);

@@ -25,7 +25,7 @@ enum { PREC_F64 = 0,    // double flux, double state
 constexpr int kThreads = 256;   // threads of the auxiliary kernels and of tile variant 0
 constexpr int kMaxWarps = 16;   // largest CTA of any tile variant: 512 threads
 
-// Tile of cells owned by one CTA (variant 0 is the default; 2D has two more, chosen by the
+// Tile of cells owned by one CTA (variant 0 is the default; 2D has four more, chosen by the
 // autotuner).  Each 2D shape makes the face count of a tile fill whole rounds of its threads:
 // 32x15: 1007 faces / 256 threads, 64x7: 967 / 256, 32x31: 2047 / 512.
 template <int D, int V = 0> struct Tile;
@@ -36,6 +36,10 @@ template <> struct Tile<1, 2> { static constexpr int X = 63, Y = 1, Z = 1, T = 6
 template <> struct Tile<2, 0> { static constexpr int X = 32, Y = 15, Z = 1, T = 256; };
 template <> struct Tile<2, 1> { static constexpr int X = 64, Y = 7, Z = 1, T = 256; };
 template <> struct Tile<2, 2> { static constexpr int X = 32, Y = 31, Z = 1, T = 512; };
+// 32x27: 1787 faces in 7 rounds of 256 (99.7%), 1216 tiles on a 1024^2 grid = 4 full waves of two
+// CTAs per SM; 32x18: 1202 faces in 5 rounds (94%), 1824 tiles = 6 full waves
+template <> struct Tile<2, 3> { static constexpr int X = 32, Y = 27, Z = 1, T = 256; };
+template <> struct Tile<2, 4> { static constexpr int X = 32, Y = 18, Z = 1, T = 256; };
 template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 256; };
 
 template <int D, int V = 0> struct TileGeom {

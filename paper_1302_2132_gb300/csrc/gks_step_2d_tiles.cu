@@ -5,7 +5,7 @@
 namespace gks {
 
 cudaError_t prepare_step_d2_variants() {
-  cudaError_t e = cudaSuccess, r;
+  cudaError_t e = prepare_step_d2_variants2(), r;
   if ((r = prepare_step<2, PREC_F32, false, 1>()) != cudaSuccess) e = r;
   if ((r = prepare_step<2, PREC_F32, true, 1>()) != cudaSuccess) e = r;
   if ((r = prepare_step<2, PREC_F32, false, 2>()) != cudaSuccess) e = r;
@@ -14,7 +14,9 @@ cudaError_t prepare_step_d2_variants() {
 }
 
 void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
-  if (variant == 1) {
+  if (variant >= 3) {
+    launch_step_d2_variant2(variant, multid, A, nblocks, s);
+  } else if (variant == 1) {
     if (multid) launch_step<2, PREC_F32, true, 1>(A, nblocks, s);
     else launch_step<2, PREC_F32, false, 1>(A, nblocks, s);
   } else {
@@ -33,6 +35,8 @@ void tile_shape(int D, int variant, int* x, int* y, int* z) {
   if (D == 3) { *x = Tile<3, 0>::X; *y = Tile<3, 0>::Y; *z = Tile<3, 0>::Z; return; }
   if (variant == 1) { *x = Tile<2, 1>::X; *y = Tile<2, 1>::Y; }
   else if (variant == 2) { *x = Tile<2, 2>::X; *y = Tile<2, 2>::Y; }
+  else if (variant == 3) { *x = Tile<2, 3>::X; *y = Tile<2, 3>::Y; }
+  else if (variant == 4) { *x = Tile<2, 4>::X; *y = Tile<2, 4>::Y; }
   else { *x = Tile<2, 0>::X; *y = Tile<2, 0>::Y; }
   *z = 1;
 }
