@@ -143,12 +143,12 @@ gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtyp
 gks_status gks_enable_timing(gks_handle* h, int enable);
 gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
 
-/* Tile shape of the handle's step kernel.  2D FP32 handles choose among five shapes (variants
- * 0..4: 32x15, 64x7, 32x31, 32x27, 32x18 cells; 512 threads per CTA for 32x31, 256 otherwise), 1D
- * handles among 256, 31 and 63 cells per CTA, on their first gks_step: each is timed on the step
- * about to be taken and the fastest kept (and reused by later handles of the same grid); the
- * environment variable GKS_TILE_VARIANT forces one (0..4 in 2D, 0..2 in 1D).  The result does not
- * depend on it beyond rounding. */
+/* Tile shape of the handle's step kernel.  2D FP32 handles choose among six shapes (variants
+ * 0..5: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 cells; 512 threads per CTA for 32x31 and 64x27, 256
+ * otherwise), 1D handles among 256, 31 and 63 cells per CTA, on their first gks_step: each is timed
+ * on the step about to be taken and the fastest kept (and reused by later handles of the same grid);
+ * the environment variable GKS_TILE_VARIANT forces one (0..5 in 2D, 0..2 in 1D).  The result does
+ * not depend on it beyond rounding. */
 gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz);
 
 gks_status gks_destroy(gks_handle* h);

@@ -18,8 +18,8 @@ void launch_step_d3(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
 cudaError_t prepare_step_d2_variants();
 void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void tile_shape(int D, int variant, int* x, int* y, int* z);
-constexpr int kTileVariants2D = 5;
-// variants 3 and 4 (their own translation unit)
+constexpr int kTileVariants2D = 6;
+// variants 3 to 5 (their own translation unit)
 cudaError_t prepare_step_d2_variants2();
 void launch_step_d2_variant2(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 // 1D tile variants 1 and 2 (narrow tiles for small grids)

@@ -21,7 +21,17 @@
 namespace gks {
 
 template <class T> GKS_FN T g_sqrt(T x);
+#ifdef GKS_HOST_COUNT
 template <> GKS_FN float g_sqrt<float>(float x) { return sqrtf(x); }
+#else
+// single precision: the hardware approximate square root (relative error about 2^-23, no slow-path
+// branch); double precision stays IEEE
+template <> GKS_FN float g_sqrt<float>(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+#endif
 template <> GKS_FN double g_sqrt<double>(double x) { return sqrt(x); }
 template <class T> GKS_FN T g_exp(T x);
 #ifdef GKS_HOST_COUNT
@@ -404,17 +414,10 @@ GKS_FN void phi_series(double x, double& p1, double& p2, double& p3, double& e) 
   e = 1.0 - x * p1;
 }
 
+// tau = 0 needs no branch of its own: x = dt/tau is +infinity, e = 0, and the closed forms give the
+// limits T0 = dt, T1 = 0, T2 = dt^2/2, T3 = T4 = T5 = 0, r1 = -1, r4 = r5 = 0 exactly.
 template <class T>
 GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
-  if (!(tau > T(0))) {  // tau = 0: x -> infinity
-    Tc[0] = dt;
-    Tc[1] = T(0);
-    Tc[2] = T(0.5) * dt * dt;
-    Tc[3] = Tc[4] = Tc[5] = T(0);
-    r1 = T(-1);
-    r4 = r5 = T(0);
-    return;
-  }
   const T x = g_div(dt, tau);
   if (x < T(1)) {
     // series branch in double precision for either arithmetic type

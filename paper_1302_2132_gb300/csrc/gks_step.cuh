@@ -11,6 +11,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gks_flux.cuh"
 
 namespace gks {
@@ -40,6 +42,9 @@ template <> struct Tile<2, 2> { static constexpr int X = 32, Y = 31, Z = 1, T = 
 // CTAs per SM; 32x18: 1202 faces in 5 rounds (94%), 1824 tiles = 6 full waves
 template <> struct Tile<2, 3> { static constexpr int X = 32, Y = 27, Z = 1, T = 256; };
 template <> struct Tile<2, 4> { static constexpr int X = 32, Y = 18, Z = 1, T = 256; };
+// 64x27 on one 512-thread CTA per SM: 3547 faces in 7 rounds (99%), 608 tiles = 4 full waves; all
+// warps of an SM work in the same phase of one tile
+template <> struct Tile<2, 5> { static constexpr int X = 64, Y = 27, Z = 1, T = 512; };
 template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 256; };
 
 template <int D, int V = 0> struct TileGeom {
@@ -317,6 +322,43 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
   return g_div(w[0] * nu, p * g_sqrt(R(1) + eta * eta));
 }
 
+// The k-epsilon / k-omega branch of tau_turb_cell written without early returns, so that several
+// cells can be evaluated side by side: the same arithmetic, with the non-positive k or
+// epsilon|omega case selected to zero at the end.
+template <int D, class R>
+__device__ __forceinline__ R tau_turb_two_eq(bool keps, const Consts<R>& kc, const R* Ws, int stride_v, int idx,
+                                             const int* strides, const R* const* igrad, const int* pos, R f1,
+                                             R f2) {
+  R w[D + 2];
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) w[v] = Ws[v * stride_v + idx];
+  const R p = pressure_of<R>(D, kc.gamma, w);
+  R grad[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int im = idx - strides[a], ip = idx + strides[a];
+    const R id = igrad[a][pos[a]];
+    const R irm = g_rcp(Ws[im]), irp = g_rcp(Ws[ip]);
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      grad[a][b] = (Ws[(1 + b) * stride_v + ip] * irp - Ws[(1 + b) * stride_v + im] * irm) * id;
+  }
+  R s2 = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const R sab = R(0.5) * (grad[a][b] + grad[b][a]);
+      s2 += sab * sab;
+    }
+  const R S = g_sqrt(R(2) * s2);
+  // k-epsilon: nu = C_mu k^2/eps, eta = S k/eps; k-omega: nu = k/omega, eta = S/(beta* omega)
+  const R nu = keps ? g_div(kc.C_mu * f1 * f1, f2) : g_div(f1, f2);
+  const R eta = keps ? g_div(S * f1, f2) : g_div(S, kc.beta_star * f2);
+  const R t = g_div(w[0] * nu, p * g_sqrt(R(1) + eta * eta));
+  return (f1 > R(0) && f2 > R(0)) ? t : R(0);
+}
+
 __device__ __forceinline__ double step_dt(const StepArgs& A) {
   // every control word is read up front: one round trip to memory
   const Ctrl* c = A.ctrl;
@@ -415,6 +457,88 @@ __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
 #pragma unroll
   for (int d = 0; d < D; ++d) r += g_div(g_abs(g_div(w[1 + d], w[0])) + cs, h[d]);
   return r;
+}
+
+// Turbulent relaxation time (Eqs. tautchen, tautchenadjusted, tauttrivial) and, with PRE, the
+// limited MUSCL slope along each axis of every cell of the tile's first halo ring.  A function of its
+// own (not inlined) so that its register allocation is separate from the face loop's: each thread
+// evaluates its ring cells tid + q T side by side, results in registers and stored afterwards, so
+// that their shared-memory and MUFU latencies overlap.  A slot past the ring repeats the last cell
+// and is not stored.  The model and limiter branches are taken once, outside the cells.
+template <int D, int PREC, int V>
+__device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc, int turb_model, int lim,
+                                        const typename PrecT<PREC>::R* Ws, const typename PrecT<PREC>::R* Fl,
+                                        typename PrecT<PREC>::R* taus, typename PrecT<PREC>::R* Ss,
+                                        const typename PrecT<PREC>::R* icx, const typename PrecT<PREC>::R* icy,
+                                        const typename PrecT<PREC>::R* icz, const typename PrecT<PREC>::R* igx,
+                                        const typename PrecT<PREC>::R* igy, const typename PrecT<PREC>::R* igz) {
+  using R = typename PrecT<PREC>::R;
+  using G = TileGeom<D, V>;
+  constexpr int kThreads = G::T, nv = D + 2, HX = G::HX, HY = G::HY;
+  constexpr bool PRE = pre_slopes<D, PREC>();
+  const int tid = threadIdx.x;
+  const int strides[3] = {1, HX, HX * HY};
+  const R* igrad[3] = {igx, igy, igz};
+  const R* icent[3] = {icx, icy, icz};
+  constexpr int NIT = (G::NR + kThreads - 1) / kThreads;
+  constexpr int GRP = D == 3 ? 2 : (NIT < 4 ? NIT : 4);
+  constexpr int NS = PRE ? D * nv : 1;
+  const bool keps = turb_model == TURB_KEPS;
+  auto ring = [&](auto two_eq_tag, auto lim_tag) {
+    constexpr bool TWO_EQ = decltype(two_eq_tag)::value;
+    constexpr int LIM = decltype(lim_tag)::value;
+    (void)LIM;
+    for (int i0 = 0; i0 < NIT; i0 += GRP) {
+      R tv[GRP], sv[GRP][NS];
+      (void)sv;
+#pragma unroll
+      for (int q = 0; q < GRP; ++q) {
+        const int l = min(tid + (i0 + q) * kThreads, G::NR - 1);
+        const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
+        const int hi = ri + 1, hj = D >= 2 ? rj + 1 : 0, hk = D >= 3 ? rk + 1 : 0;
+        const int idx = (hk * HY + hj) * HX + hi;
+        const int pos[3] = {hi, hj, hk};
+        if constexpr (TWO_EQ)
+          tv[q] = tau_turb_two_eq<D, R>(keps, kc, Ws, G::NH, idx, strides, igrad, pos, Fl[l], Fl[G::NR + l]);
+        else
+          tv[q] = tau_turb_cell<D, R>(turb_model, kc, Ws, G::NH, idx, strides, igrad, pos,
+                                      turb_model == TURB_NONE ? R(0) : Fl[l], R(0));
+        if constexpr (PRE) {
+          // slope along each axis: normal slope of the faces along that axis, tangential slope of
+          // the faces along the others
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const R im = icent[a][pos[a]], ip = icent[a][pos[a] + 1];
+#pragma unroll
+            for (int v = 0; v < nv; ++v) {
+              const R* pc = Ws + v * G::NH + idx;
+              sv[q][a * nv + v] = limiter<R>(LIM, (pc[0] - pc[-strides[a]]) * im, (pc[strides[a]] - pc[0]) * ip);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < GRP; ++q) {
+        const int l = tid + (i0 + q) * kThreads;
+        if (i0 + q >= NIT || l >= G::NR) continue;
+        taus[l] = tv[q];
+        if constexpr (PRE) {
+#pragma unroll
+          for (int j = 0; j < NS; ++j) Ss[j * G::NR + l] = sv[q][j];
+        }
+      }
+    }
+  };
+  using T1 = std::integral_constant<bool, true>;
+  using T0 = std::integral_constant<bool, false>;
+  using LV = std::integral_constant<int, LIM_VANLEER>;
+  using LM = std::integral_constant<int, LIM_MINMOD>;
+  const bool two_eq = turb_model == TURB_KEPS || turb_model == TURB_KOMEGA;
+  if (lim == LIM_VANLEER) {
+    if (two_eq) ring(T1{}, LV{}); else ring(T0{}, LV{});
+  } else {
+    if (two_eq) ring(T1{}, LM{}); else ring(T0{}, LM{});
+  }
 }
 
 // One tile of one step: every thread of the CTA calls it with the same arguments.
@@ -549,38 +673,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   }
   const R dt = (R)dt_d;
 
-  // ---- turbulent relaxation time on the tile and its first halo ring --------------------------
-  {
-    const int strides[3] = {1, HX, HX * HY};
-    const R* igrad[3] = {igx, igy, igz};
-    const R* icent[3] = {icx, icy, icz};
-    for (int l = tid; l < G::NR; l += kThreads) {
-      const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
-      const int hi = ri + 1, hj = D >= 2 ? rj + 1 : 0, hk = D >= 3 ? rk + 1 : 0;
-      const int idx = (hk * HY + hj) * HX + hi;
-      R f1 = R(0), f2 = R(0);
-      if (g.turb_model != TURB_NONE) {
-        f1 = Fl[l];
-        if (g.turb_model != TURB_MUT) f2 = Fl[G::NR + l];
-      }
-      const int pos[3] = {hi, hj, hk};
-      taus[l] = tau_turb_cell<D, R>(g.turb_model, kc, Ws, G::NH, idx, strides, igrad, pos, f1, f2);
-      if (PRE) {
-        // MUSCL slope of this cell along each axis (normal slope of the faces along that axis and
-        // tangential slope of the faces along the others)
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          const R im = icent[a][pos[a]], ip = icent[a][pos[a] + 1];
-#pragma unroll
-          for (int v = 0; v < nv; ++v) {
-            const R* pc = Ws + v * G::NH + idx;
-            Ss[(a * nv + v) * G::NR + l] =
-                limiter<R>(g.limiter, (pc[0] - pc[-strides[a]]) * im, (pc[strides[a]] - pc[0]) * ip);
-          }
-        }
-      }
-    }
-  }
+  // ---- turbulent relaxation time and limited slopes on the tile and its first halo ring -------
+  ring_phase<D, PREC, V>(kc, g.turb_model, g.limiter, Ws, Fl, taus, Ss, icx, icy, icz, igx, igy, igz);
   __syncthreads();
 
   // ---- fluxes of every face of the tile ----------------------------------------------------

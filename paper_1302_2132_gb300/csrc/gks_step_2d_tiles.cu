@@ -37,6 +37,7 @@ void tile_shape(int D, int variant, int* x, int* y, int* z) {
   else if (variant == 2) { *x = Tile<2, 2>::X; *y = Tile<2, 2>::Y; }
   else if (variant == 3) { *x = Tile<2, 3>::X; *y = Tile<2, 3>::Y; }
   else if (variant == 4) { *x = Tile<2, 4>::X; *y = Tile<2, 4>::Y; }
+  else if (variant == 5) { *x = Tile<2, 5>::X; *y = Tile<2, 5>::Y; }
   else { *x = Tile<2, 0>::X; *y = Tile<2, 0>::Y; }
   *z = 1;
 }

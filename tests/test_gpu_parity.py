@@ -332,12 +332,12 @@ def test_full_size_2d_turbulence_sampled_cells(prec):
 
 
 def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
-    """The five 2D FP32 tile shapes evaluate the same faces: their results agree to FP32 rounding
+    """The six 2D FP32 tile shapes evaluate the same faces: their results agree to FP32 rounding
     (different compiled kernels), and the autotuner keeps one of them."""
     spec = inputs.turbulence(100, 2, seed=8)
     kw = dict(turb_model=2, multid=1, mu=1e-5, precision="fp32")
     out = []
-    for v in ("0", "1", "2", "3", "4"):
+    for v in ("0", "1", "2", "3", "4", "5"):
         monkeypatch.setenv("GKS_TILE_VARIANT", v)
         s = gpu_solver(spec, **kw)
         s.set_state(spec["prim"].ravel(), layout="soa_prim")
@@ -354,7 +354,7 @@ def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
     s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
     s.step(nsteps=30, cfl=0.5)
     v = s.tile_shape()
-    assert v[0] in (0, 1, 2, 3, 4) and v[1] * v[2] in (480, 448, 992, 864, 576)
+    assert v[0] in (0, 1, 2, 3, 4, 5) and v[1] * v[2] in (480, 448, 992, 864, 576, 1728)
     assert np.all(rel_err_per_var(s.get_state(), out[0], 4) < 1e-6)
     s.close()
 
