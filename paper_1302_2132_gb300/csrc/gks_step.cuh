@@ -142,8 +142,9 @@ struct StepArgs {
 
 template <int PREC> struct PrecT;
 
-// Cell slopes are precomputed in shared memory except where that would not fit (3D, FP64).
-template <int D, int PREC> __host__ __device__ constexpr bool pre_slopes() { return !(D == 3 && PREC == 0); }
+// Cell slopes are precomputed in shared memory in 1D and 2D; in 3D the 15 slopes per ring cell would
+// hold the tile to one CTA per SM, so the faces recompute them (two CTAs per SM in FP32).
+template <int D, int PREC> __host__ __device__ constexpr bool pre_slopes() { return D < 3; }
 template <> struct PrecT<PREC_F64> { using R = double; using S = double; };
 template <> struct PrecT<PREC_F32> { using R = float; using S = float; };
 template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
@@ -718,7 +719,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       }
       const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
       const int pn = ax == 0 ? ci + 2 : (ax == 1 ? cj + 2 : ck + 2);  // halo coordinate of cell c
-      const R h0 = wn[pn - 2], h1 = wn[pn - 1], h2 = wn[pn], h3 = wn[pn + 1];
+      const R h1 = wn[pn - 1], h2 = wn[pn];
+      const R* icn = ax == 0 ? icx : (ax == 1 ? icy : icz);
+      (void)icn;
       // ring indices of the two cells
       const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
       const int rst[3] = {1, G::RX, G::RX * G::RY};
@@ -735,7 +738,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           wl[v] = s1 + R(0.5) * h1 * sl[v];
           wr[v] = s2 - R(0.5) * h2 * sr[v];
         } else {
-          muscl<R>(g.limiter, p[-2 * sn], s1, s2, p[sn], h0, h1, h2, h3, wl[v], wr[v], sl[v], sr[v]);
+          // MUSCL with the tabulated inverse centre distances (cells pn-2 .. pn+1 along the normal)
+          const R dm = (s1 - p[-2 * sn]) * icn[pn - 1], dc = (s2 - s1) * icn[pn], dp = (p[sn] - s2) * icn[pn + 1];
+          sl[v] = limiter<R>(g.limiter, dm, dc);
+          sr[v] = limiter<R>(g.limiter, dc, dp);
+          wl[v] = s1 + R(0.5) * h1 * sl[v];
+          wr[v] = s2 - R(0.5) * h2 * sr[v];
         }
         cl[v] = s1;
         cr[v] = s2;
@@ -771,18 +779,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         for (int s = 0; s < D - 1; ++s) {
           const int ta = perm[1 + s];
           const int stt = st[ta];
-          const R* wt = ta == 0 ? wsx : (ta == 1 ? wsy : wsz);
+          const R* ict = ta == 0 ? icx : (ta == 1 ? icy : icz);
           const int hcell[3] = {ci + 2, cj + (D >= 2 ? 2 : 0), ck + (D >= 3 ? 2 : 0)};
           const int pt = hcell[ta];
-          const R hm = R(0.5) * (wt[pt - 1] + wt[pt]);
-          const R hp = R(0.5) * (wt[pt] + wt[pt + 1]);
+          const R im = ict[pt], ip = ict[pt + 1];
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
             const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
             const R* pc = Ws + sv * G::NH + hc;
             const R* pl = pc - sn;
-            tl[s][v] = limiter<R>(g.limiter, g_div(pl[0] - pl[-stt], hm), g_div(pl[stt] - pl[0], hp));
-            tr[s][v] = limiter<R>(g.limiter, g_div(pc[0] - pc[-stt], hm), g_div(pc[stt] - pc[0], hp));
+            tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) * im, (pl[stt] - pl[0]) * ip);
+            tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) * im, (pc[stt] - pc[0]) * ip);
           }
         }
       }
@@ -901,7 +908,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
 }
 
 template <int D, int V = 0> constexpr int min_blocks(int prec) {
-  return (prec != PREC_F64 && D <= 2) ? 512 / Tile<D, V>::T : 1;
+  return prec != PREC_F64 ? 512 / Tile<D, V>::T : 1;
 }
 
 template <int D, int PREC, bool MULTID, int V = 0>
