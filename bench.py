@@ -300,7 +300,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if fp64 else "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "turb2d_1024" else args.workload,
+        "config": {"workload": (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32"
+                                else "%s_%s" % (args.workload, wl["precision"])),
                    "description": wl["desc"], "grid": list(n), "time_steps_per_bench_step": nsteps, "cfl": CFL,
                    "expand": "multid" if multid else "directional",
                    "precision": wl["precision"], "state_accumulation": {"fp32": "float pair (hi+lo)",

@@ -686,121 +686,132 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     gas.mu = kc.mu;
     gas.C_a = kc.C_a;
     const R gamma = kc.gamma;
-    for (int f = tid; f < G::NF; f += kThreads) {
-      int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
-      if (f < G::NFX) {
-        ax = 0;
-        ci = f % (X + 1);
-        cj = (f / (X + 1)) % Y;
-        ck = f / ((X + 1) * Y);
-      } else if (D >= 2 && f < G::NFX + G::NFY) {
-        const int q = f - G::NFX;
-        ax = 1;
-        ci = q % X;
-        cj = (q / X) % (Y + 1);
-        ck = q / (X * (Y + 1));
-      } else {
-        const int q = f - G::NFX - G::NFY;
-        ax = 2;
-        ci = q % X;
-        cj = (q / X) % Y;
-        ck = q / (X * Y);
-      }
-      const int st[3] = {1, HX, HX * HY};
-      const int sn = st[ax];
-      const int hc = ((ck + (D >= 3 ? 2 : 0)) * HY + (cj + (D >= 2 ? 2 : 0))) * HX + (ci + 2);
-      // velocity order in the face frame: normal first, then tangential axes
-      int perm[3];
-      perm[0] = ax;
-      if (D == 2) perm[1] = 1 - ax;
-      if (D == 3) {
-        perm[1] = ax == 0 ? 1 : 0;
-        perm[2] = ax == 2 ? 1 : 2;
-      }
-      const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
-      const int pn = ax == 0 ? ci + 2 : (ax == 1 ? cj + 2 : ck + 2);  // halo coordinate of cell c
-      const R h1 = wn[pn - 1], h2 = wn[pn];
-      const R* icn = ax == 0 ? icx : (ax == 1 ? icy : icz);
-      (void)icn;
-      // ring indices of the two cells
-      const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
-      const int rst[3] = {1, G::RX, G::RX * G::RY};
-      const int rl = rc - rst[ax];
-      R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv];
-#pragma unroll
-      for (int v = 0; v < nv; ++v) {
-        const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
-        const R* p = Ws + sv * G::NH + hc;
-        const R s1 = p[-sn], s2 = p[0];
-        if (PRE) {
-          sl[v] = Ss[(ax * nv + sv) * G::NR + rl];
-          sr[v] = Ss[(ax * nv + sv) * G::NR + rc];
-          wl[v] = s1 + R(0.5) * h1 * sl[v];
-          wr[v] = s2 - R(0.5) * h2 * sr[v];
+    // Rounds of kThreads faces; after each round the warps of every 128-thread group meet at a
+    // named barrier, so that the warps sharing an SM sub-partition run the ~1000-instruction face
+    // body close together and share its instruction fetches.  Every thread runs every round.
+    constexpr int kRounds = (G::NF + kThreads - 1) / kThreads;
+    for (int it = 0; it < kRounds; ++it) {
+      const int f = tid + it * kThreads;
+      if (f < G::NF) {
+        int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
+        if (f < G::NFX) {
+          ax = 0;
+          ci = f % (X + 1);
+          cj = (f / (X + 1)) % Y;
+          ck = f / ((X + 1) * Y);
+        } else if (D >= 2 && f < G::NFX + G::NFY) {
+          const int q = f - G::NFX;
+          ax = 1;
+          ci = q % X;
+          cj = (q / X) % (Y + 1);
+          ck = q / (X * (Y + 1));
         } else {
-          // MUSCL with the tabulated inverse centre distances (cells pn-2 .. pn+1 along the normal)
-          const R dm = (s1 - p[-2 * sn]) * icn[pn - 1], dc = (s2 - s1) * icn[pn], dp = (p[sn] - s2) * icn[pn + 1];
-          sl[v] = limiter<R>(g.limiter, dm, dc);
-          sr[v] = limiter<R>(g.limiter, dc, dp);
-          wl[v] = s1 + R(0.5) * h1 * sl[v];
-          wr[v] = s2 - R(0.5) * h2 * sr[v];
+          const int q = f - G::NFX - G::NFY;
+          ax = 2;
+          ci = q % X;
+          cj = (q / X) % Y;
+          ck = q / (X * Y);
         }
-        cl[v] = s1;
-        cr[v] = s2;
-      }
-      if (!(wl[0] > R(0)) || !(pressure_of<R>(D, gamma, wl) > R(0))) {
+        const int st[3] = {1, HX, HX * HY};
+        const int sn = st[ax];
+        const int hc = ((ck + (D >= 3 ? 2 : 0)) * HY + (cj + (D >= 2 ? 2 : 0))) * HX + (ci + 2);
+        // velocity order in the face frame: normal first, then tangential axes
+        int perm[3];
+        perm[0] = ax;
+        if (D == 2) perm[1] = 1 - ax;
+        if (D == 3) {
+          perm[1] = ax == 0 ? 1 : 0;
+          perm[2] = ax == 2 ? 1 : 2;
+        }
+        const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
+        const int pn = ax == 0 ? ci + 2 : (ax == 1 ? cj + 2 : ck + 2);  // halo coordinate of cell c
+        const R h1 = wn[pn - 1], h2 = wn[pn];
+        const R* icn = ax == 0 ? icx : (ax == 1 ? icy : icz);
+        (void)icn;
+        // ring indices of the two cells
+        const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
+        const int rst[3] = {1, G::RX, G::RX * G::RY};
+        const int rl = rc - rst[ax];
+        R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv];
 #pragma unroll
         for (int v = 0; v < nv; ++v) {
-          wl[v] = cl[v];
-          sl[v] = R(0);
+          const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+          const R* p = Ws + sv * G::NH + hc;
+          const R s1 = p[-sn], s2 = p[0];
+          if (PRE) {
+            sl[v] = Ss[(ax * nv + sv) * G::NR + rl];
+            sr[v] = Ss[(ax * nv + sv) * G::NR + rc];
+            wl[v] = s1 + R(0.5) * h1 * sl[v];
+            wr[v] = s2 - R(0.5) * h2 * sr[v];
+          } else {
+            // MUSCL with the tabulated inverse centre distances (cells pn-2 .. pn+1 along the normal)
+            const R dm = (s1 - p[-2 * sn]) * icn[pn - 1], dc = (s2 - s1) * icn[pn], dp = (p[sn] - s2) * icn[pn + 1];
+            sl[v] = limiter<R>(g.limiter, dm, dc);
+            sr[v] = limiter<R>(g.limiter, dc, dp);
+            wl[v] = s1 + R(0.5) * h1 * sl[v];
+            wr[v] = s2 - R(0.5) * h2 * sr[v];
+          }
+          cl[v] = s1;
+          cr[v] = s2;
         }
-      }
-      if (!(wr[0] > R(0)) || !(pressure_of<R>(D, gamma, wr) > R(0))) {
-#pragma unroll
-        for (int v = 0; v < nv; ++v) {
-          wr[v] = cr[v];
-          sr[v] = R(0);
-        }
-      }
-      R tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
-      if (MULTID && PRE) {
-#pragma unroll
-        for (int s = 0; s < D - 1; ++s) {
-          const int ta = perm[1 + s];
+        if (!(wl[0] > R(0)) || !(pressure_of<R>(D, gamma, wl) > R(0))) {
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
-            const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
-            tl[s][v] = Ss[(ta * nv + sv) * G::NR + rl];
-            tr[s][v] = Ss[(ta * nv + sv) * G::NR + rc];
+            wl[v] = cl[v];
+            sl[v] = R(0);
           }
         }
-      } else if (MULTID) {
-#pragma unroll
-        for (int s = 0; s < D - 1; ++s) {
-          const int ta = perm[1 + s];
-          const int stt = st[ta];
-          const R* ict = ta == 0 ? icx : (ta == 1 ? icy : icz);
-          const int hcell[3] = {ci + 2, cj + (D >= 2 ? 2 : 0), ck + (D >= 3 ? 2 : 0)};
-          const int pt = hcell[ta];
-          const R im = ict[pt], ip = ict[pt + 1];
+        if (!(wr[0] > R(0)) || !(pressure_of<R>(D, gamma, wr) > R(0))) {
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
-            const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
-            const R* pc = Ws + sv * G::NH + hc;
-            const R* pl = pc - sn;
-            tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) * im, (pl[stt] - pl[0]) * ip);
-            tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) * im, (pc[stt] - pc[0]) * ip);
+            wr[v] = cr[v];
+            sr[v] = R(0);
           }
         }
-      }
-      const R tau_t = R(0.5) * (taus[rl] + taus[rc]);
-      R F[nv], tau;
-      face_flux<D, R, MULTID>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
-                              g.abar_t0, F, &tau);
-      Fs[0 * G::NF + f] = F[0];
+        R tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
+        if (MULTID && PRE) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) Fs[(1 + perm[k]) * G::NF + f] = F[1 + k];
-      Fs[(D + 1) * G::NF + f] = F[D + 1];
+          for (int s = 0; s < D - 1; ++s) {
+            const int ta = perm[1 + s];
+#pragma unroll
+            for (int v = 0; v < nv; ++v) {
+              const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+              tl[s][v] = Ss[(ta * nv + sv) * G::NR + rl];
+              tr[s][v] = Ss[(ta * nv + sv) * G::NR + rc];
+            }
+          }
+        } else if (MULTID) {
+#pragma unroll
+          for (int s = 0; s < D - 1; ++s) {
+            const int ta = perm[1 + s];
+            const int stt = st[ta];
+            const R* ict = ta == 0 ? icx : (ta == 1 ? icy : icz);
+            const int hcell[3] = {ci + 2, cj + (D >= 2 ? 2 : 0), ck + (D >= 3 ? 2 : 0)};
+            const int pt = hcell[ta];
+            const R im = ict[pt], ip = ict[pt + 1];
+#pragma unroll
+            for (int v = 0; v < nv; ++v) {
+              const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+              const R* pc = Ws + sv * G::NH + hc;
+              const R* pl = pc - sn;
+              tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) * im, (pl[stt] - pl[0]) * ip);
+              tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) * im, (pc[stt] - pc[0]) * ip);
+            }
+          }
+        }
+        const R tau_t = R(0.5) * (taus[rl] + taus[rc]);
+        R F[nv], tau;
+        face_flux<D, R, MULTID>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
+                                g.abar_t0, F, &tau);
+        Fs[0 * G::NF + f] = F[0];
+#pragma unroll
+        for (int k = 0; k < D; ++k) Fs[(1 + perm[k]) * G::NF + f] = F[1 + k];
+        Fs[(D + 1) * G::NF + f] = F[D + 1];
+      }
+      if constexpr (kThreads % 128 == 0)
+        asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");
+      else
+        __syncwarp();
     }
   }
   __syncthreads();
