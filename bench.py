@@ -155,6 +155,12 @@ def make_workload(name, precision):
     raise ValueError(name)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the step kernel, taken from
+# one ncu capture of the same kernel build, keyed by workload and tile variant; a combination that
+# was not captured (or whose kernel changed since) reports null.
+TRAFFIC_PER_LAUNCH = {("turb2d_1024_keps_multid_fp32", 3): 44.478720e6}
+
+
 def faces_of(n):
     D = len(n)
     tot = 0
@@ -287,6 +293,10 @@ def run_ours(args):
     fp64 = wl["precision"] == "fp64"
     lanes = 2 if fp64 else 128  # FP64 runs at 1/64 of the FP32 rate on this part
     peak = 152 * lanes * 2 * 2.070e9 / 1e12
+    workload_name = (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32"
+                     else "%s_%s" % (args.workload, wl["precision"]))
+    tile = solver.tile_shape()
+    tile_info = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
     line = {
         "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
         "value": value,
@@ -300,8 +310,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if fp64 else "f32",
         "data": "synthetic",
-        "config": {"workload": (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32"
-                                else "%s_%s" % (args.workload, wl["precision"])),
+        "config": {"workload": workload_name,
                    "description": wl["desc"], "grid": list(n), "time_steps_per_bench_step": nsteps, "cfl": CFL,
                    "expand": "multid" if multid else "directional",
                    "precision": wl["precision"], "state_accumulation": {"fp32": "float pair (hi+lo)",
@@ -310,8 +319,10 @@ def run_ours(args):
                    "l2": "flushed between bench steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "single"},
         "cell_updates_per_s": cells * nsteps * args.steps * world / secs,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "step_kernel<%d, %s, %s>" % (D, "PREC_F64" if fp64 else "PREC_F32",
+                     "frac": achieved / peak,
+                     "traffic": TRAFFIC_PER_LAUNCH.get((workload_name, tile_info.get("variant"))),
+                     "kernel": "step_kernel<%d, %s, %s>" % (D, {"fp64": "PREC_F64", "fp32": "PREC_F32",
+                                                                "fp32_acc64": "PREC_F32D"}[wl["precision"]],
                                                              "multid" if multid else "directional"),
                      "avg_launch_us": avg_launch_s * 1e6,
                      "ops_per_face": per_face, "ops_per_cell": per_cell,
@@ -323,8 +334,7 @@ def run_ours(args):
         "final_time": t_end,
         "total_mass": float(total[0]),
     }
-    tile = solver.tile_shape()
-    line["config"]["tile"] = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
+    line["config"]["tile"] = tile_info
     if not args.no_cpu_baseline and args.workload == "turb2d_1024":
         line["cpu_baseline"] = cpu_baseline(budget_s=15.0)
     if not args.no_serving and args.workload == "turb2d_1024":
