@@ -178,6 +178,20 @@ __device__ __forceinline__ R pressure_of(int D, R gamma, const R* w) {
   return (gamma - R(1)) * (w[D + 1] - R(0.5) * g_div(q, w[0]));
 }
 
+// rho > 0 and p > 0 for a conservative state.  Single precision tests 2 rho (rho E) > |rho U|^2 (the
+// same condition once rho > 0, without a quotient); double precision evaluates p as the oracle does.
+template <int D, class R>
+__device__ __forceinline__ bool physical(R gamma, const R* w) {
+  if constexpr (sizeof(R) == sizeof(float)) {
+    R q = R(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
+    return w[0] > R(0) && R(2) * w[0] * w[D + 1] > q;
+  } else {
+    return w[0] > R(0) && pressure_of<R>(D, gamma, w) > R(0);
+  }
+}
+
 // Isothermal no-slip wall image: velocity reversed, same pressure, T_g = T_w^2 / T_i (T = p/rho).
 template <int D, class R>
 __device__ __forceinline__ void wall_image(const Consts<R>& k, R* w) {
@@ -754,14 +768,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           cl[v] = s1;
           cr[v] = s2;
         }
-        if (!(wl[0] > R(0)) || !(pressure_of<R>(D, gamma, wl) > R(0))) {
+        if (!physical<D, R>(gamma, wl)) {
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
             wl[v] = cl[v];
             sl[v] = R(0);
           }
         }
-        if (!(wr[0] > R(0)) || !(pressure_of<R>(D, gamma, wr) > R(0))) {
+        if (!physical<D, R>(gamma, wr)) {
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
             wr[v] = cr[v];
@@ -843,6 +857,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       fp[2] = fm[2] + X * Y;
       h[2] = wsz[lk + 2];
     }
+    R ih[3];
+#pragma unroll
+    for (int d = 0; d < D; ++d) ih[d] = g_rcp(h[d]);
     R wn[nv];
     double vol = 1.0;
     if (A.resid) {  // cell volume from the double-precision widths
@@ -870,7 +887,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       } else {
         R inc = R(0);
 #pragma unroll
-        for (int d = 0; d < D; ++d) inc -= g_div(Fs[v * G::NF + fp[d]] - Fs[v * G::NF + fm[d]], h[d]);
+        for (int d = 0; d < D; ++d) inc -= (Fs[v * G::NF + fp[d]] - Fs[v * G::NF + fm[d]]) * ih[d];
         double wd = 0.0;
         if (PREC == PREC_F32) {
           // (hi, lo) += inc with an error-free sum, then renormalise
