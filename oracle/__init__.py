@@ -12,6 +12,9 @@ Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
       conservation, free-stream preservation)
   turbulent relaxation-time field                           -- pinned for eta = 0 and k-eps/k-omega
       equivalence; the turbulent configurations beyond their invariants are parity unpinned
+  k-omega transport (Wilcox 2006 reading)                   -- pinned (homogeneous decay against the
+      closed-form ODE solution, uniform-shear production and its limiter, exact discrete diffusion of
+      a Fourier mode, advection by a uniform stream, conservation on periodic grids)
 """
 import ctypes
 import os
@@ -90,6 +93,15 @@ class FaceDiag(ctypes.Structure):
     ]
 
 
+class KOmega(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("beta0", ctypes.c_double), ("beta_star", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("sigma_star", ctypes.c_double), ("sigma_do", ctypes.c_double),
+        ("C_lim", ctypes.c_double), ("omega_floor", ctypes.c_double),
+        ("sources", ctypes.c_int), ("diffusion", ctypes.c_int),
+    ]
+
+
 _D = ctypes.c_double
 _PD = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.c_int
@@ -117,6 +129,8 @@ def lib():
             L.orc_rarefaction.argtypes = [P, _PD, _PD, _PD, _PD]
             L.orc_step.argtypes = [P, _PD, _PD, _PD, _D, _PD, _I]
             L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
+            L.orc_komega_defaults.argtypes = [ctypes.POINTER(KOmega)]
+            L.orc_step_komega.argtypes = [P, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _I]
             _lib = L
     return _lib
 
@@ -293,3 +307,23 @@ class Case:
         st = lib().orc_run(ctypes.byref(self.P), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)),
                            dt_fixed, cfl, nsteps, t_end, ctypes.byref(t), ctypes.byref(done), nthreads)
         return W, t.value, done.value, st
+
+    def step_komega(self, W, RK, RW, dt, coeffs=None, nthreads=1):
+        """One flow step plus the k-omega transport step (Wilcox 2006 reading) of RK = rho k and
+        RW = rho omega; returns (W, RK, RW, status).  coeffs: a KOmega (default Wilcox's values)."""
+        W = self._state(W).copy()
+        RK = self._field(RK).copy()
+        RW = self._field(RW).copy()
+        c = coeffs if coeffs is not None else komega_defaults()
+        st = lib().orc_step_komega(ctypes.byref(self.P), ctypes.byref(c), _ptr(W), _ptr(RK), _ptr(RW), dt,
+                                   nthreads)
+        return W, RK, RW, st
+
+
+def komega_defaults(**over):
+    """Wilcox's 2006 k-omega closure coefficients (and the test switches), optionally overridden."""
+    c = KOmega()
+    lib().orc_komega_defaults(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c

@@ -742,6 +742,9 @@ void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
   f.tau_t = 0.5 * (C.taut[G.idx(c[0], c[1], c[2])] + C.taut[G.idx(cr[0], cr[1], cr[2])]);
 }
 
+int flow_step(const orc_problem* P, double* W, const double* f1, const double* f2, double dt, double* resid,
+              int nthreads, std::vector<double>* mflux);
+
 }  // namespace
 
 // =============================================================================================
@@ -895,6 +898,16 @@ int orc_rarefaction(const orc_problem* P, const double* W, const double* f1, con
 // time-integrated fluxes of Eq. fluxesf.  Returns 4 if a cell ends with rho <= 0 or p <= 0.
 int orc_step(const orc_problem* P, double* W, const double* f1, const double* f2, double dt,
              double* resid, int nthreads) {
+  return flow_step(P, W, f1, f2, dt, resid, nthreads, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+// The flow step of orc_step; mflux (if given) receives, per axis d, the time-integrated mass flux of
+// every face along d (faces j-1/2, j = 0 .. n_d, x fastest).
+int flow_step(const orc_problem* P, double* W, const double* f1, const double* f2, double dt, double* resid,
+              int nthreads, std::vector<double>* mflux) {
   StepCtx C;
   prepare(P, W, f1, f2, C);
   const Grid& G = C.G;
@@ -926,6 +939,10 @@ int orc_step(const orc_problem* P, double* W, const double* f1, const double* f2
       Fo[0] = Fr[0];
       for (int k = 0; k < D; ++k) Fo[1 + perm[k]] = Fr[1 + k];
       Fo[D + 1] = Fr[D + 1];
+    }
+    if (mflux) {
+      mflux[d].resize(nfaces);
+      for (long fi = 0; fi < nfaces; ++fi) mflux[d][fi] = Fd[fi * nv];
     }
     for (int k = 0; k < G.n[2]; ++k)
       for (int j = 0; j < G.n[1]; ++j)
@@ -962,6 +979,206 @@ int orc_step(const orc_problem* P, double* W, const double* f1, const double* f2
   if (resid)
     for (int v = 0; v < nv; ++v) resid[v] = std::sqrt(resid[v] / G.ncell);
   std::memcpy(W, Wnew.data(), sizeof(double) * nv * G.ncell);
+  return status;
+}
+
+// ---------------------------------------------------------------------------------------------
+// k-omega transport (Wilcox 2006), explicit in time with the flow step's dt:
+//   d(rho k)/dt + div(rho U k)     = P - beta* rho k omega + div((mu + sigma* rho k / omega) grad k)
+//   d(rho w)/dt + div(rho U w)     = alpha (omega/k) P - beta rho omega^2 + sigma_d (rho/omega) grad k . grad omega
+//                                    + div((mu + sigma rho k / omega) grad omega)
+//   P = rho tau_ij dU_i/dx_j = mu_T (2 S:S - 2/3 (div U)^2) - 2/3 rho k div U,
+//   mu_T = rho k / omega~, omega~ = max(omega, C_lim sqrt(2 Sbar:Sbar / beta*)), Sbar = S - (div U)/3 I,
+//   beta = beta0 f_beta, f_beta = (1 + 85 chi)/(1 + 100 chi), chi = |Omega_ij Omega_jk Shat_ki| / (beta* omega)^3,
+//   Shat = S - (div U)/2 I, sigma_d = sigma_do where grad k . grad omega > 0, else 0.
+// Discretisation (the reading of this build): convective flux F_rho * phi_face with F_rho the
+// face's time-integrated GKS mass flux and phi_face the upwind cell's value plus half its limited
+// slope times (width - F_rho / rho), the face value at the half time (MUSCL-Hancock, second order
+// for smooth advection); diffusive flux dt (mu + sigma rho k / omega |face) (phi_R - phi_L) /
+// (centre distance), the coefficient the mean of the two cells; gradients in the sources by
+// central differences; destruction point-implicit:
+//   (rho k)^{n+1} = [(rho k)^n - sum_d dG_d / dx_d + dt P] / (1 + dt beta* omega^n),
+//   (rho w)^{n+1} = [(rho w)^n - sum_d dG_d / dx_d + dt (alpha rho (omega/omega~) X
+//                    - 2/3 alpha rho omega div U + CD)] / (1 + dt beta omega^n),  X = 2 S:S - 2/3 (div U)^2,
+// then rho k >= 0 and omega >= omega_floor.  Ghost values of k and omega: periodic axes wrap, other
+// axes repeat the nearest interior cell (zero gradient).
+// ---------------------------------------------------------------------------------------------
+double central_grad(const Grid& G, const std::vector<double>& fp, int a, const int* c) {
+  int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+  cm[a] -= 1;
+  cp[a] += 1;
+  double dist = 0.5 * width(G, a, c[a] - 1) + width(G, a, c[a]) + 0.5 * width(G, a, c[a] + 1);
+  return (fp[G.idx(cp[0], cp[1], cp[2])] - fp[G.idx(cm[0], cm[1], cm[2])]) / dist;
+}
+
+void komega_update(const orc_problem* P, const orc_komega* K, const Grid& G, const std::vector<double>& Wp,
+                   const std::vector<double>& kp, const std::vector<double>& wp, const std::vector<double>* mflux,
+                   double dt, const double* RK, const double* RW, const double* Wnew, double* RKn, double* RWn) {
+  const int D = G.D;
+  // face fluxes G^k, G^omega per axis, faces j - 1/2 for j = 0 .. n_d
+  std::vector<double> Gk[3], Gw[3];
+  for (int d = 0; d < D; ++d) {
+    int nf[3] = {G.n[0], G.n[1], G.n[2]};
+    nf[d] += 1;
+    long nfaces = (long)nf[0] * nf[1] * nf[2];
+    Gk[d].assign(nfaces, 0.0);
+    Gw[d].assign(nfaces, 0.0);
+    for (long fi = 0; fi < nfaces; ++fi) {
+      int cr[3];
+      cr[0] = (int)(fi % nf[0]);
+      cr[1] = (int)((fi / nf[0]) % nf[1]);
+      cr[2] = (int)(fi / ((long)nf[0] * nf[1]));
+      int cl[3] = {cr[0], cr[1], cr[2]};
+      cl[d] -= 1;
+      const double hl = width(G, d, cl[d]), hr = width(G, d, cr[d]);
+      const double fr = mflux[d][fi];
+      for (int q = 0; q < 2; ++q) {
+        const std::vector<double>& f = q == 0 ? kp : wp;
+        // limited slopes of the two cells along d
+        double s[2], v[4];
+        for (int t = 0; t < 4; ++t) {
+          int cc[3] = {cl[0], cl[1], cl[2]};
+          cc[d] += t - 1;
+          v[t] = f[G.idx(cc[0], cc[1], cc[2])];
+        }
+        for (int side = 0; side < 2; ++side) {
+          int c0 = cl[d] + side;
+          double hm = 0.5 * (width(G, d, c0 - 1) + width(G, d, c0));
+          double hp = 0.5 * (width(G, d, c0) + width(G, d, c0 + 1));
+          s[side] = limiter(P->limiter, (v[1 + side] - v[side]) / hm, (v[2 + side] - v[1 + side]) / hp);
+        }
+        // upwind face value at the half time: the fluid crossing the face in dt comes from the
+        // last F_rho / rho of the upwind cell (MUSCL-Hancock form)
+        double rl0 = Wp[G.idx(cl[0], cl[1], cl[2])], rr0 = Wp[G.idx(cr[0], cr[1], cr[2])];
+        double phiL = v[1] + 0.5 * s[0] * (hl - fr / rl0);
+        double phiR = v[2] - 0.5 * s[1] * (hr + fr / rr0);
+        double g = fr * (fr >= 0.0 ? phiL : phiR);
+        if (K->diffusion) {
+          double sig = q == 0 ? K->sigma_star : K->sigma;
+          double rl = Wp[G.idx(cl[0], cl[1], cl[2])], rr = Wp[G.idx(cr[0], cr[1], cr[2])];
+          double mdl = rl * kp[G.idx(cl[0], cl[1], cl[2])] / wp[G.idx(cl[0], cl[1], cl[2])];
+          double mdr = rr * kp[G.idx(cr[0], cr[1], cr[2])] / wp[G.idx(cr[0], cr[1], cr[2])];
+          double coef = P->mu + sig * 0.5 * (mdl + mdr);
+          g -= dt * coef * (v[2] - v[1]) / (0.5 * hl + 0.5 * hr);
+        }
+        (q == 0 ? Gk : Gw)[d][fi] = g;
+      }
+    }
+  }
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i) {
+        const int c[3] = {i, j, k};
+        const long cell = ((long)k * G.n[1] + j) * G.n[0] + i;
+        const long id = G.idx(i, j, k);
+        double rho = Wp[id];
+        double kk = kp[id], om = wp[id];
+        double ak = RK[cell], aw = RW[cell];
+        for (int d = 0; d < D; ++d) {
+          int nf[3] = {G.n[0], G.n[1], G.n[2]};
+          nf[d] += 1;
+          int cp[3] = {i, j, k};
+          cp[d] += 1;
+          long fm = ((long)c[2] * nf[1] + c[1]) * nf[0] + c[0];
+          long fp = ((long)cp[2] * nf[1] + cp[1]) * nf[0] + cp[0];
+          double h = width(G, d, c[d]);
+          ak -= (Gk[d][fp] - Gk[d][fm]) / h;
+          aw -= (Gw[d][fp] - Gw[d][fm]) / h;
+        }
+        double rate_k = 0.0, rate_w = 0.0;
+        if (K->sources) {
+          double g[3][3];  // g[a][b] = dU_b/dx_a
+          vel_grad(G, Wp, i, j, k, g);
+          double div = 0.0;
+          for (int a = 0; a < D; ++a) div += g[a][a];
+          double SS = 0.0, SbSb = 0.0;
+          double Sm[3][3], Om[3][3];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              Sm[a][b] = 0.5 * (g[a][b] + g[b][a]);
+              Om[a][b] = 0.5 * (g[b][a] - g[a][b]);  // Omega_ab = (dU_a/dx_b - dU_b/dx_a)/2
+            }
+          for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) {
+              SS += Sm[a][b] * Sm[a][b];
+              double sb = Sm[a][b] - (a == b ? div / 3.0 : 0.0);
+              SbSb += sb * sb;
+            }
+          double X = 2.0 * SS - 2.0 / 3.0 * div * div;
+          double wt = std::max(om, K->C_lim * std::sqrt(2.0 * SbSb / K->beta_star));
+          double muT = rho * kk / wt;
+          double Pk = muT * X - 2.0 / 3.0 * rho * kk * div;
+          // vortex-stretching function (zero in 1D and 2D)
+          double chi = 0.0;
+          if (D == 3) {
+            double t = 0.0;
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b)
+                for (int e = 0; e < 3; ++e) {
+                  double sh = Sm[e][a] - (e == a ? 0.5 * div : 0.0);
+                  t += Om[a][b] * Om[b][e] * sh;
+                }
+            double bo = K->beta_star * om;
+            chi = std::fabs(t / (bo * bo * bo));
+          }
+          double fbeta = (1.0 + 85.0 * chi) / (1.0 + 100.0 * chi);
+          double beta = K->beta0 * fbeta;
+          double dkdw = 0.0;
+          for (int a = 0; a < D; ++a) dkdw += central_grad(G, kp, a, c) * central_grad(G, wp, a, c);
+          double sd = dkdw > 0.0 ? K->sigma_do : 0.0;
+          double CD = sd * rho / om * dkdw;
+          ak += dt * Pk;
+          aw += dt * (K->alpha * rho * (om / wt) * X - 2.0 / 3.0 * K->alpha * rho * om * div + CD);
+          rate_k = K->beta_star * om;
+          rate_w = beta * om;
+        }
+        ak /= 1.0 + dt * rate_k;
+        aw /= 1.0 + dt * rate_w;
+        double rho_new = Wnew[cell];
+        RKn[cell] = std::max(ak, 0.0);
+        RWn[cell] = std::max(aw, rho_new * K->omega_floor);
+      }
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_komega_defaults(orc_komega* c) {
+  c->alpha = 13.0 / 25.0;
+  c->beta0 = 0.0708;
+  c->beta_star = 0.09;
+  c->sigma = 0.5;
+  c->sigma_star = 0.6;
+  c->sigma_do = 0.125;
+  c->C_lim = 7.0 / 8.0;
+  c->omega_floor = 1e-12;
+  c->sources = 1;
+  c->diffusion = 1;
+  return 0;
+}
+
+int orc_step_komega(const orc_problem* P, const orc_komega* c, double* W, double* RK, double* RW, double dt,
+                    int nthreads) {
+  if (P->turb_model != ORC_TURB_KOMEGA) return 1;
+  Grid G = make_grid(P);
+  const long n = G.ncell;
+  std::vector<double> kk(n), om(n), Wold(W, W + (size_t)G.nv * n);
+  for (long i = 0; i < n; ++i) {
+    kk[i] = RK[i] / W[i];
+    om[i] = RW[i] / W[i];
+  }
+  std::vector<double> mflux[3];
+  int status = flow_step(P, W, kk.data(), om.data(), dt, nullptr, nthreads, mflux);
+  // the transport step sees the state at the start of the step (with the flow's ghost cells)
+  std::vector<double> Wp;
+  pad_state(G, Wold.data(), Wp);
+  fill_ghosts(P, G, Wp);
+  std::vector<double> kp = pad_scalar(P, G, kk.data()), wp = pad_scalar(P, G, om.data());
+  std::vector<double> RKn(n), RWn(n);
+  komega_update(P, c, G, Wp, kp, wp, mflux, dt, RK, RW, W, RKn.data(), RWn.data());
+  std::memcpy(RK, RKn.data(), sizeof(double) * n);
+  std::memcpy(RW, RWn.data(), sizeof(double) * n);
   return status;
 }
 

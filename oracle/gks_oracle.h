@@ -82,6 +82,23 @@ int orc_step(const orc_problem* P, double* W, const double* f1, const double* f2
 int orc_run(const orc_problem* P, double* W, const double* f1, const double* f2, double dt_fixed,
             double cfl, int nsteps, double t_end, double* t_inout, int* steps_done, int nthreads);
 
+/* k-omega transport solved together with the flow equations (Section 4 evolves k and omega this
+ * way with Wilcox's 2006 k-omega model, which it cites without printing the equations).  Closure
+ * coefficients; orc_komega_defaults fills Wilcox's 2006 values.  sources = 0 and diffusion = 0
+ * switch those parts off (tests only). */
+typedef struct {
+  double alpha, beta0, beta_star, sigma, sigma_star, sigma_do, C_lim;
+  double omega_floor;   /* smallest omega kept after an update */
+  int sources, diffusion;
+} orc_komega;
+int orc_komega_defaults(orc_komega* c);
+/* One flow step (as orc_step, with the turbulent relaxation time of the k-omega model from
+ * k = RK/rho and omega = RW/rho) followed by the transport step of RK = rho k and RW = rho omega
+ * with the same dt and the face mass fluxes of that flow step.  P->turb_model must be
+ * ORC_TURB_KOMEGA.  Returns 4 if a cell ends with rho <= 0 or p <= 0. */
+int orc_step_komega(const orc_problem* P, const orc_komega* c, double* W, double* RK, double* RW, double dt,
+                    int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
