@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None, choices=["fp32", "fp32_acc64", "fp64"])
     p.add_argument("--workload", default="turb2d_1024",
-                   choices=["turb2d_1024", "sod1d_400", "shock_bl_1024x384", "turb3d_256"])
+                   choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--serving", action="store_true", help="measure the serving form only")
@@ -135,6 +135,16 @@ def make_workload(name, precision):
         return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
                                        expand="multid"), nsteps=NSTEPS, t_end=0.0, precision=precision or "fp32",
                     desc="2D decaying turbulence 1024^2, k-epsilon tau_t, multi-D, 200 CFL steps")
+    if name == "turb2d_1024_transport":
+        spec = dict(workload_inputs())
+        # k-omega transport from the same initial fields: omega = eps / (C_mu k), so that nu_t = k/omega
+        # equals the k-epsilon C_mu k^2/eps of the default workload at t = 0
+        spec["f2"] = spec["f2"] / (0.09 * spec["f1"])
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="komega_transport", beta_star=0.09, C_a=0.0,
+                                       limiter="vanleer", expand="multid"), nsteps=NSTEPS, t_end=0.0,
+                    precision=precision or "fp32", transport=True,
+                    desc="2D decaying turbulence 1024^2 with k and omega transported (Wilcox 2006 k-omega), "
+                         "multi-D, 200 CFL steps")
     if name == "sod1d_400":
         spec = inputs.sod_1d(400)
         return dict(spec=spec, kw=dict(gamma=1.4, mu=1e-5, C_a=1.0, limiter="vanleer", expand="directional"),
@@ -198,15 +208,19 @@ def run_ours(args):
                         **wl["kw"])
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
     turb = wl["kw"].get("turb_model", "none") != "none"
+    transport = wl.get("transport", False)
     if turb:
         f1 = torch.tensor(spec["f1"].ravel(), device=dev)
         f2 = torch.tensor(spec["f2"].ravel(), device=dev)
-        solver.set_turbulence(f1, f2)
+        if not transport:  # transported fields are set after each set_state
+            solver.set_turbulence(f1, f2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = solver.stream
     nsteps = wl["nsteps"]
     if wl["t_end"] > 0.0:  # count the steps that reach t_end
         solver.set_state(prim_dev, layout="soa_prim")
+        if transport:
+            solver.set_turbulence(f1, f2)
         nsteps = 0
         while solver.time()[0] < wl["t_end"]:
             solver.step(nsteps=1, cfl=CFL, t_end=wl["t_end"])
@@ -214,6 +228,8 @@ def run_ours(args):
 
     def one_step():
         solver.set_state(prim_dev, layout="soa_prim")
+        if transport:
+            solver.set_turbulence(f1, f2)
         solver.step(nsteps=nsteps, cfl=CFL, t_end=wl["t_end"])
 
     for _ in range(args.warmup):
@@ -287,7 +303,7 @@ def run_ours(args):
     multid = wl["kw"].get("expand") == "multid" and D > 1
     counts = gks.face_op_count(D, multid, True)
     per_face = sum(counts[:3])
-    per_cell = CELL_OPS + sum(gks.cell_op_count(D)[:3])
+    per_cell = CELL_OPS + sum(gks.cell_op_count(D)[:3]) + (KOMEGA_CELL_OPS[D] if transport else 0)
     ops_per_launch = faces_per_step * per_face + cells * per_cell
     avg_launch_s = kms / 1e3 / max(klaunch, 1)
     achieved = ops_per_launch / avg_launch_s / 1e12
@@ -322,14 +338,18 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": TRAFFIC_PER_LAUNCH.get((workload_name, tile_info.get("variant"))),
-                     "kernel": "step_kernel<%d, %s, %s>" % (D, {"fp64": "PREC_F64", "fp32": "PREC_F32",
-                                                                "fp32_acc64": "PREC_F32D"}[wl["precision"]],
-                                                             "multid" if multid else "directional"),
+                     "kernel": "step_kernel<%d, %s, %s>%s" % (D, {"fp64": "PREC_F64", "fp32": "PREC_F32",
+                                                                  "fp32_acc64": "PREC_F32D"}[wl["precision"]],
+                                                               "multid" if multid else "directional",
+                                                               " + komega_kernel (timed together)" if transport
+                                                               else ""),
                      "avg_launch_us": avg_launch_s * 1e6,
                      "ops_per_face": per_face, "ops_per_cell": per_cell,
                      "peak_basis": "152 SMs x %d %s lanes x 2 (FMA) x 2070 MHz (derived)" % (lanes, "FP64" if fp64
                                                                                             else "FP32")},
-        "gpu_launches": args.steps * (nsteps + 3),
+        # per bench step: state_in + rate kernels, the step kernels (plus the transport kernels and
+        # the two field conversions of set_turbulence with k-omega transport)
+        "gpu_launches": args.steps * ((2 * nsteps + 2 + 4) if transport else (nsteps + 3)),
         "clocks": clock_info,
         "e2e": e2e,
         "final_time": t_end,
@@ -348,6 +368,11 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
 
+
+# per-cell operations of the k-omega transport step (hand count of the kernel: per axis about 190 --
+# k and omega of five cells, two limited-slope triples, two half-time face values with diffusion,
+# gradients; sources about 100)
+KOMEGA_CELL_OPS = {1: 290, 2: 480, 3: 670}
 
 # per-cell operations of the fused step besides the faces and the reconstruction slopes (counted by
 # gks_cell_op_count): turbulent relaxation time (velocity gradient, strain rate, k-epsilon formula:

@@ -48,8 +48,9 @@ typedef enum {
 /* boundary conditions per axis side (Section 4: walls are treated as in conventional CFD) */
 enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1, GKS_BC_WALL = 2, GKS_BC_DIRICHLET = 3, GKS_BC_OUTFLOW = 4 };
 /* turbulent relaxation time: none, tau_t = mu_t/p (Eq. tauttrivial), k-epsilon (Eq. tautchen),
- * k-omega (Eq. tautchenadjusted) */
-enum { GKS_TURB_NONE = 0, GKS_TURB_MUT = 1, GKS_TURB_KEPS = 2, GKS_TURB_KOMEGA = 3 };
+ * k-omega (Eq. tautchenadjusted) from prescribed fields, or k-omega with k and omega transported
+ * alongside the flow (Section 4; Wilcox's 2006 k-omega equations, see gks_komega) */
+enum { GKS_TURB_NONE = 0, GKS_TURB_MUT = 1, GKS_TURB_KEPS = 2, GKS_TURB_KOMEGA = 3, GKS_TURB_KOMEGA_TRANSPORT = 4 };
 enum { GKS_LIM_MINMOD = 0, GKS_LIM_VANLEER = 1 };
 /* expansion of the distribution along the face normal only, or along every axis (Section 4) */
 enum { GKS_EXPAND_DIRECTIONAL = 0, GKS_EXPAND_MULTID = 1 };
@@ -107,8 +108,41 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
 gks_status gks_get_state(gks_handle* h, void* W_out, int layout, int memspace, int dtype);
 
 /* Copy in the turbulence fields, one value per cell in [z][y][x] order: f1 = k (or mu_t),
- * f2 = epsilon or omega (NULL for GKS_TURB_MUT). */
+ * f2 = epsilon or omega (NULL for GKS_TURB_MUT).  With GKS_TURB_KOMEGA_TRANSPORT these are the
+ * initial k and omega, stored as rho k and rho omega with the density of the current state: call
+ * it after gks_set_state (which clears transported fields); GKS_EINVAL otherwise. */
 gks_status gks_set_turbulence(gks_handle* h, const void* f1, const void* f2, int memspace, int dtype);
+
+/* k-omega transport (GKS_TURB_KOMEGA_TRANSPORT).  Each gks_step step advances the flow and then
+ * rho k, rho omega with the same dt:
+ *   d(rho k)/dt + div(rho U k) = P - beta* rho k omega + div((mu + sigma* rho k/omega) grad k)
+ *   d(rho w)/dt + div(rho U w) = alpha (omega/k) P - beta rho omega^2
+ *                                + sigma_d (rho/omega) grad k . grad omega + div((mu + sigma rho k/omega) grad omega)
+ *   P = mu_T (2 S:S - 2/3 (div U)^2) - 2/3 rho k div U, mu_T = rho k / max(omega, C_lim sqrt(2 Sbar:Sbar/beta*)),
+ *   beta = beta0 (1 + 85 chi)/(1 + 100 chi) (chi the vortex-stretching invariant, zero in 1D and 2D),
+ *   sigma_d = sigma_do where grad k . grad omega > 0, else 0;
+ * convection by the flow step's face mass fluxes with half-time MUSCL face values of the upwind
+ * cell, normal diffusion with the mean coefficient of the two cells, destruction point-implicit,
+ * then k >= 0 and omega >= omega_floor.  The turbulent relaxation time of the flow step uses
+ * k and omega of the step's start (Eq. tautchenadjusted).  beta* is gks_turb.beta_star.  Ghost
+ * values of k and omega: periodic axes wrap, other boundaries take the nearest interior cell. */
+typedef struct {
+  double alpha, beta0, sigma, sigma_star, sigma_do, C_lim;
+  double omega_floor;  /* smallest omega kept after an update */
+  int sources;         /* 0: convection and diffusion only (tests) */
+  int diffusion;       /* 0: no diffusion (tests) */
+} gks_komega;
+
+/* Wilcox's 2006 values: alpha 13/25, beta0 0.0708, sigma 1/2, sigma* 3/5, sigma_do 1/8, C_lim 7/8;
+ * omega_floor 1e-12, sources and diffusion on.  Errors: GKS_EINVAL for a null pointer. */
+gks_status gks_komega_defaults(gks_komega* c);
+
+/* Replace the closure coefficients of a GKS_TURB_KOMEGA_TRANSPORT handle (the defaults are set at
+ * gks_create).  Takes effect from the next gks_step.  Errors: GKS_EINVAL (null, other model). */
+gks_status gks_set_komega(gks_handle* h, const gks_komega* c);
+
+/* Copy out the transported k and omega (GKS_TURB_KOMEGA_TRANSPORT), one value per cell. */
+gks_status gks_get_turbulence(gks_handle* h, void* k_out, void* omega_out, int memspace, int dtype);
 
 /* CFL time step of the current state: dt = cfl / max_cells sum_d (|U_d| + c) / dx_d. Synchronises. */
 gks_status gks_compute_dt(gks_handle* h, double cfl, double* dt_out);

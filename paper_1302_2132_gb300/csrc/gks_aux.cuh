@@ -68,6 +68,19 @@ __global__ void field_kernel(const Tin* src, Tout* dst, long n) {
   if (c < n) dst[c] = (Tout)src[c];
 }
 
+// f *= rho (scale = 1) or out = f / rho (scale = 0) with rho the density of a stored state; the
+// conversions between k, omega and the transported rho k, rho omega
+template <class R, class S>
+__global__ void density_scale_kernel(R* f, const S* W, long n) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) f[c] = f[c] * (R)W[c];
+}
+template <class R, class S, class O>
+__global__ void density_unscale_kernel(const R* f, const S* W, O* out, long n) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) out[c] = (O)(f[c] / (R)W[c]);
+}
+
 template <class T>
 __global__ void copy_kernel(const T* src, T* dst, long n) {
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ 
   R rmax = R(0);
   for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += (long)gridDim.x * blockDim.x) {
     R w[D + 2];
-    load_stored<D, PREC>(A, c, w);
+    load_stored<D, PREC>(A.g, A.Win, c, w);
     int pos[3];
     pos[0] = (int)(c % g.n[0]);
     pos[1] = (int)((c / g.n[0]) % g.n[1]);

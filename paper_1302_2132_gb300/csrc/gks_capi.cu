@@ -34,6 +34,11 @@ struct gks_handle {
   float* Wlo[2] = {nullptr, nullptr};
   void* f1 = nullptr;
   void* f2 = nullptr;
+  bool transport = false;            // GKS_TURB_KOMEGA_TRANSPORT: k and omega evolve with the flow
+  void* RK[2] = {nullptr, nullptr};  // rho k, rho omega (arithmetic type), buffered like the state
+  void* RW[2] = {nullptr, nullptr};
+  void* mflux[3] = {nullptr, nullptr, nullptr};  // face mass fluxes of the last flow step
+  gks_komega kw{};
   double* widths[3] = {nullptr, nullptr, nullptr};
   double* dir[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   Ctrl* ctrl = nullptr;
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
     const bool on_axis = (di != 0) + (dj != 0) + (dk != 0) <= 1;
     R w[nv];
     if (on_axis) {
-      load_cell<D, PREC>(A, kc, i + di, j + dj, k + dk, w);
+      load_cell<D, PREC>(A.g, A.Win, kc, i + di, j + dj, k + dk, w);
     } else {
       for (int v = 0; v < nv; ++v) w[v] = R(1);
     }
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
     f1 = ((const R*)A.f1)[c];
     if (g.turb_model != TURB_MUT) f2 = ((const R*)A.f2)[c];
   }
-  R val = tau_turb_cell<D, R>(g.turb_model, kc, Wn, NN, idx, strides, igrad, pos, f1, f2);
+  R val = tau_turb_cell<D, R>(g.turb_model, g.turb_cons != 0, kc, Wn, NN, idx, strides, igrad, pos, f1, f2);
   if (what == 1) {  // rarefaction: (mu/p + tau_t) |div U|
     R w[nv];
     for (int v = 0; v < nv; ++v) w[v] = Wn[v * NN + idx];
@@ -184,7 +189,35 @@ void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
     launch_step_d3(h->prec, h->multid, A, h->nblocks, h->stream);
 }
 
-void launch_step(gks_handle* h, const StepArgs& A) { launch_step_variant(h, A, h->tile_variant); }
+// One full step: the flow step and, with k-omega transport, the transport step of rho k and
+// rho omega (into the other buffer pair) with the same dt and the flow step's mass fluxes.
+void launch_step(gks_handle* h, const StepArgs& A) {
+  launch_step_variant(h, A, h->tile_variant);
+  if (!h->transport) return;
+  const int cur = A.Win == h->W[0] ? 0 : 1;
+  KOmegaArgs K;
+  std::memset(&K, 0, sizeof(K));
+  K.g = A.g;
+  K.Win = A.Win;
+  K.Wnew = A.Wout;
+  K.RKin = h->RK[cur];
+  K.RWin = h->RW[cur];
+  K.RKout = h->RK[cur ^ 1];
+  K.RWout = h->RW[cur ^ 1];
+  for (int d = 0; d < 3; ++d) K.mflux[d] = h->mflux[d];
+  K.ctrl = h->ctrl;
+  K.alpha = h->kw.alpha;
+  K.beta0 = h->kw.beta0;
+  K.beta_star = A.g.beta_star;
+  K.sigma = h->kw.sigma;
+  K.sigma_star = h->kw.sigma_star;
+  K.sigma_do = h->kw.sigma_do;
+  K.C_lim = h->kw.C_lim;
+  K.omega_floor = h->kw.omega_floor;
+  K.sources = h->kw.sources;
+  K.diffusion = h->kw.diffusion;
+  launch_komega(h->D, h->prec, K, h->stream);
+}
 
 // Arguments of the step that starts at absolute step index s.
 StepArgs step_args(const gks_handle* h, long long s, int resid) {
@@ -197,6 +230,11 @@ StepArgs step_args(const gks_handle* h, long long s, int resid) {
   A.slot = (int)(s % 3);
   A.tslot = cur;
   A.resid = resid;
+  if (h->transport) {
+    A.f1 = h->RK[cur];
+    A.f2 = h->RW[cur];
+    for (int d = 0; d < 3; ++d) A.mflux[d] = h->mflux[d];
+  }
   return A;
 }
 
@@ -260,6 +298,12 @@ void free_all(gks_handle* h) {
   }
   if (h->f1) cudaFree(h->f1);
   if (h->f2) cudaFree(h->f2);
+  for (int b = 0; b < 2; ++b) {
+    if (h->RK[b]) cudaFree(h->RK[b]);
+    if (h->RW[b]) cudaFree(h->RW[b]);
+  }
+  for (int d = 0; d < 3; ++d)
+    if (h->mflux[d]) cudaFree(h->mflux[d]);
   for (int d = 0; d < 3; ++d) {
     if (h->widths[d]) cudaFree(h->widths[d]);
     for (int s = 0; s < 2; ++s)
@@ -381,7 +425,8 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   if (num->expand != GKS_EXPAND_DIRECTIONAL && num->expand != GKS_EXPAND_MULTID) return bad(GKS_EINVAL, "expand");
   if (num->abar_mode != GKS_ABAR_TIMEINT && num->abar_mode != GKS_ABAR_T0) return bad(GKS_EINVAL, "abar_mode");
   const int model = turb ? turb->model : GKS_TURB_NONE;
-  if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA) return bad(GKS_EINVAL, "turbulence model");
+  if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA_TRANSPORT) return bad(GKS_EINVAL, "turbulence model");
+  h->transport = model == GKS_TURB_KOMEGA_TRANSPORT;
   for (int d = 0; d < D; ++d) {
     for (int s = 0; s < 2; ++s) {
       if (!valid_bc(grid->bc[d][s])) return bad(GKS_EINVAL, "boundary condition code");
@@ -440,7 +485,20 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   }
   if (!alloc((void**)&h->ctrl, sizeof(Ctrl))) return bad(GKS_ENOMEM, "control block allocation failed");
   cudaMemset(h->ctrl, 0, sizeof(Ctrl));
-  if (model != GKS_TURB_NONE) {
+  if (h->transport) {
+    const size_t fb = arith_bytes(h->prec) * h->ncell;
+    for (int b = 0; b < 2; ++b) {
+      if (!alloc(&h->RK[b], fb) || !alloc(&h->RW[b], fb)) return bad(GKS_ENOMEM, "field allocation failed");
+      cudaMemset(h->RK[b], 0, fb);
+      cudaMemset(h->RW[b], 0, fb);
+    }
+    for (int d = 0; d < D; ++d) {
+      long nf = 1;
+      for (int b = 0; b < D; ++b) nf *= h->n[b] + (b == d ? 1 : 0);
+      if (!alloc(&h->mflux[d], arith_bytes(h->prec) * nf)) return bad(GKS_ENOMEM, "mass-flux allocation failed");
+    }
+    gks_komega_defaults(&h->kw);
+  } else if (model != GKS_TURB_NONE) {
     const size_t fb = arith_bytes(h->prec) * h->ncell;
     if (!alloc(&h->f1, fb) || !alloc(&h->f2, fb)) return bad(GKS_ENOMEM, "field allocation failed");
     cudaMemset(h->f1, 0, fb);
@@ -505,7 +563,8 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   g.C_a = turb ? turb->C_a : 0.0;
   g.C_mu = turb ? turb->C_mu : 0.09;
   g.beta_star = turb ? turb->beta_star : 0.09;
-  g.turb_model = model;
+  g.turb_model = h->transport ? (int)GKS_TURB_KOMEGA : model;
+  g.turb_cons = h->transport ? 1 : 0;
   g.limiter = num->limiter;
   g.abar_t0 = num->abar_mode == GKS_ABAR_T0;
   set_consts(g);
@@ -563,6 +622,7 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
                                                          h->base.g.gamma, h->prec, h->W[0], h->Wlo[0]);
   GKS_CK(h, cudaGetLastError());
   h->has_state = true;
+  if (h->transport) h->has_turb = false;  // rho k, rho omega belong to the previous state
   return launch_rate(h);
 }
 
@@ -603,10 +663,12 @@ gks_status gks_set_turbulence(gks_handle* h, const void* f1, const void* f2, int
   if (h->base.g.turb_model != GKS_TURB_MUT && !f2) return fail(h, GKS_EINVAL, "second turbulence field missing");
   if ((dtype != GKS_F64 && dtype != GKS_F32) || (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
     return fail(h, GKS_EINVAL, "memspace or dtype");
+  if (h->transport && !h->has_state) return fail(h, GKS_EINVAL, "k-omega transport: set the state first");
   DeviceGuard dg(h->dev);
   const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * h->ncell;
   const void* srcs[2] = {f1, f2};
-  void* dsts[2] = {h->f1, h->f2};
+  const int cur = (int)(h->step & 1);
+  void* dsts[2] = {h->transport ? h->RK[cur] : h->f1, h->transport ? h->RW[cur] : h->f2};
   for (int q = 0; q < 2; ++q) {
     if (!srcs[q]) continue;
     const void* src = srcs[q];
@@ -627,9 +689,96 @@ gks_status gks_set_turbulence(gks_handle* h, const void* f1, const void* f2, int
     else
       field_kernel<float, float><<<blocks, 256, 0, h->stream>>>((const float*)src, (float*)dsts[q], h->ncell);
     GKS_CK(h, cudaGetLastError());
+    if (h->transport) {  // k, omega -> rho k, rho omega with the density of the current state
+      if (f64)
+        density_scale_kernel<double, double><<<blocks, 256, 0, h->stream>>>((double*)dsts[q], (const double*)h->W[cur],
+                                                                            h->ncell);
+      else if (h->prec == PREC_F32)
+        density_scale_kernel<float, float><<<blocks, 256, 0, h->stream>>>((float*)dsts[q], (const float*)h->W[cur],
+                                                                          h->ncell);
+      else
+        density_scale_kernel<float, double><<<blocks, 256, 0, h->stream>>>((float*)dsts[q], (const double*)h->W[cur],
+                                                                           h->ncell);
+      GKS_CK(h, cudaGetLastError());
+    }
     if (memspace == GKS_MEM_HOST) GKS_CK(h, cudaStreamSynchronize(h->stream));  // staging is reused
   }
   h->has_turb = true;
+  return GKS_OK;
+}
+
+gks_status gks_komega_defaults(gks_komega* c) {
+  if (!c) return GKS_EINVAL;
+  c->alpha = 13.0 / 25.0;
+  c->beta0 = 0.0708;
+  c->sigma = 0.5;
+  c->sigma_star = 0.6;
+  c->sigma_do = 0.125;
+  c->C_lim = 7.0 / 8.0;
+  c->omega_floor = 1e-12;
+  c->sources = 1;
+  c->diffusion = 1;
+  return GKS_OK;
+}
+
+gks_status gks_set_komega(gks_handle* h, const gks_komega* c) {
+  if (!h || !c) return fail(h, GKS_EINVAL, "null argument");
+  if (!h->transport) return fail(h, GKS_EINVAL, "handle not created with GKS_TURB_KOMEGA_TRANSPORT");
+  if (!(c->omega_floor > 0.0)) return fail(h, GKS_EINVAL, "omega_floor must be positive");
+  h->kw = *c;
+  // captured graphs hold the old coefficients in their kernel parameters
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  return GKS_OK;
+}
+
+gks_status gks_get_turbulence(gks_handle* h, void* k_out, void* omega_out, int memspace, int dtype) {
+  if (!h || !k_out || !omega_out) return fail(h, GKS_EINVAL, "null argument");
+  if (!h->transport) return fail(h, GKS_EINVAL, "handle not created with GKS_TURB_KOMEGA_TRANSPORT");
+  if (!h->has_turb) return fail(h, GKS_EINVAL, "turbulence fields not set");
+  if ((dtype != GKS_F64 && dtype != GKS_F32) || (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
+    return fail(h, GKS_EINVAL, "memspace or dtype");
+  DeviceGuard dg(h->dev);
+  const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * h->ncell;
+  const int cur = (int)(h->step & 1);
+  const unsigned blocks = grid_for(h->ncell, 256);
+  void* outs[2] = {k_out, omega_out};
+  const void* srcs[2] = {h->RK[cur], h->RW[cur]};
+  for (int q = 0; q < 2; ++q) {
+    void* dst = outs[q];
+    if (memspace == GKS_MEM_HOST) {
+      gks_status s = ensure_staging(h, bytes);
+      if (s) return s;
+      dst = h->staging;
+    }
+    if (h->prec == PREC_F64) {
+      if (dtype == GKS_F64)
+        density_unscale_kernel<double, double, double><<<blocks, 256, 0, h->stream>>>(
+            (const double*)srcs[q], (const double*)h->W[cur], (double*)dst, h->ncell);
+      else
+        density_unscale_kernel<double, double, float><<<blocks, 256, 0, h->stream>>>(
+            (const double*)srcs[q], (const double*)h->W[cur], (float*)dst, h->ncell);
+    } else if (h->prec == PREC_F32) {
+      if (dtype == GKS_F64)
+        density_unscale_kernel<float, float, double><<<blocks, 256, 0, h->stream>>>(
+            (const float*)srcs[q], (const float*)h->W[cur], (double*)dst, h->ncell);
+      else
+        density_unscale_kernel<float, float, float><<<blocks, 256, 0, h->stream>>>(
+            (const float*)srcs[q], (const float*)h->W[cur], (float*)dst, h->ncell);
+    } else {
+      if (dtype == GKS_F64)
+        density_unscale_kernel<float, double, double><<<blocks, 256, 0, h->stream>>>(
+            (const float*)srcs[q], (const double*)h->W[cur], (double*)dst, h->ncell);
+      else
+        density_unscale_kernel<float, double, float><<<blocks, 256, 0, h->stream>>>(
+            (const float*)srcs[q], (const double*)h->W[cur], (float*)dst, h->ncell);
+    }
+    GKS_CK(h, cudaGetLastError());
+    if (memspace == GKS_MEM_HOST) {
+      GKS_CK(h, cudaMemcpyAsync(outs[q], h->staging, bytes, cudaMemcpyDeviceToHost, h->stream));
+      GKS_CK(h, cudaStreamSynchronize(h->stream));
+    }
+  }
   return GKS_OK;
 }
 

@@ -6,6 +6,7 @@ namespace gks {
 
 struct StepArgs;
 struct BatchArgs;
+struct KOmegaArgs;
 
 cudaError_t prepare_step_d1();
 cudaError_t prepare_step_d2();
@@ -32,6 +33,9 @@ cudaError_t prepare_batch_d1();
 cudaError_t prepare_batch_d2();
 void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
 void launch_batch_d2(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
+
+// k-omega transport step after a flow step (gks_komega.cu)
+void launch_komega(int D, int prec, const KOmegaArgs& K, cudaStream_t s);
 
 void launch_face_flux(int D, int prec, bool multid, int abar_t0, double gamma, double mu, double C_a,
                       double dt, const double* faces, long nfaces, double* F, double* tau, cudaStream_t s);

@@ -93,6 +93,7 @@ struct DevGrid {
   const double* dir[3][2];  // Dirichlet conservative states, [transverse cell][nv]
   double gamma, bK, K, mu, C_a, T_wall, C_mu, beta_star;
   int turb_model, limiter, abar_t0;
+  int turb_cons;  // the turbulence fields hold rho k and rho omega (k-omega transport), not k and omega
   // the constants above in each arithmetic type, filled by set_consts on the host (kernels read
   // them from the parameter bank instead of converting)
   Consts<float> kf;
@@ -134,9 +135,27 @@ struct StepArgs {
   const void* f1;  // turbulence fields in the arithmetic type, or null
   const void* f2;
   Ctrl* ctrl;
+  void* mflux[3];  // if set: time-integrated mass flux of every face along each axis, faces j - 1/2
+                   // for j = 0 .. n_d (x fastest), in the arithmetic type (k-omega transport input)
   int slot;    // rate slot read by this step (step index mod 3)
   int tslot;   // time slot read by this step (step index mod 2)
   int resid;   // accumulate residual norms in this step
+};
+
+// Arguments of the k-omega transport step that follows a flow step (closure coefficients in
+// double; the kernel converts them to its arithmetic type).
+struct KOmegaArgs {
+  DevGrid g;
+  const void* Win;   // flow state at the start of the step (stored type)
+  const void* Wnew;  // flow state after the step: its density scales the omega floor
+  const void* RKin;  // rho k, rho omega at the start of the step (arithmetic type)
+  const void* RWin;
+  void* RKout;
+  void* RWout;
+  const void* mflux[3];  // the flow step's time-integrated face mass fluxes (StepArgs::mflux)
+  const Ctrl* ctrl;      // last_dt: the step's dt
+  double alpha, beta0, beta_star, sigma, sigma_star, sigma_do, C_lim, omega_floor;
+  int sources, diffusion;
 };
 
 
@@ -213,21 +232,20 @@ __device__ __forceinline__ void wall_image(const Consts<R>& k, R* w) {
 }
 
 template <int D, int PREC>
-__device__ __forceinline__ void load_stored(const StepArgs& A, long c, typename PrecT<PREC>::R* out) {
+__device__ __forceinline__ void load_stored(const DevGrid& g, const void* Win, long c, typename PrecT<PREC>::R* out) {
   using S = typename PrecT<PREC>::S;
   using R = typename PrecT<PREC>::R;
-  const S* W = (const S*)A.Win;
+  const S* W = (const S*)Win;
 #pragma unroll
-  for (int v = 0; v < D + 2; ++v) out[v] = (R)W[(long)v * A.g.ncell + c];
+  for (int v = 0; v < D + 2; ++v) out[v] = (R)W[(long)v * g.ncell + c];
 }
 
 // State of cell (i, j, k), possibly outside the grid: ghost cells follow the boundary rules, the
 // transform of the last axis applied first.
 template <int D, int PREC>
-__device__ void load_cell(const StepArgs& A, const Consts<typename PrecT<PREC>::R>& kc, int i, int j, int k,
-                          typename PrecT<PREC>::R* out) {
+__device__ void load_cell(const DevGrid& g, const void* Win, const Consts<typename PrecT<PREC>::R>& kc, int i, int j,
+                          int k, typename PrecT<PREC>::R* out) {
   using R = typename PrecT<PREC>::R;
-  const DevGrid& g = A.g;
   int c[3] = {i, j, k}, xf[3] = {0, 0, 0}, side[3] = {0, 0, 0};
   bool inside = true;
   // cells further out than the two ghost layers only feed faces of cells outside the grid
@@ -255,7 +273,7 @@ __device__ void load_cell(const StepArgs& A, const Consts<typename PrecT<PREC>::
       }
     }
   }
-  load_stored<D, PREC>(A, cell_index(g, src[0], src[1], src[2]), out);
+  load_stored<D, PREC>(g, Win, cell_index(g, src[0], src[1], src[2]), out);
   if (inside) return;
 #pragma unroll
   for (int a = D - 1; a >= 0; --a) {
@@ -277,9 +295,9 @@ __device__ void load_cell(const StepArgs& A, const Consts<typename PrecT<PREC>::
   }
 }
 
-template <class R>
-__device__ __forceinline__ R load_field(const StepArgs& A, const void* f, int D, int i, int j, int k) {
-  const DevGrid& g = A.g;
+// Cell whose turbulence field value a (possibly ghost) cell takes: periodic axes wrap, other axes
+// the nearest interior cell.
+__device__ __forceinline__ long field_cell(const DevGrid& g, int D, int i, int j, int k) {
   int c[3] = {i, j, k};
   for (int a = 0; a < D; ++a) {
     const int n = g.n[a];
@@ -290,20 +308,29 @@ __device__ __forceinline__ R load_field(const StepArgs& A, const void* f, int D,
         c[a] = min(max(c[a], 0), n - 1);
     }
   }
-  return ((const R*)f)[cell_index(g, c[0], c[1], c[2])];
+  return cell_index(g, c[0], c[1], c[2]);
+}
+
+template <class R>
+__device__ __forceinline__ R load_field(const StepArgs& A, const void* f, int D, int i, int j, int k) {
+  return ((const R*)f)[field_cell(A.g, D, i, j, k)];
 }
 
 // Turbulent part of the relaxation time of one cell (Eqs. tauttrivial, tautchen, tautchenadjusted
 // with T = p/rho); S = sqrt(2 S_ij S_ij) from central differences of the velocity.
 // igrad[a][p] = 1 / (distance between the centres of halo cells p - 1 and p + 1 along axis a).
 template <int D, class R>
-__device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, const R* Ws, int stride_v, int idx,
-                                           const int* strides, const R* const* igrad, const int* pos,
+__device__ __forceinline__ R tau_turb_cell(int turb_model, bool cons, const Consts<R>& kc, const R* Ws, int stride_v,
+                                           int idx, const int* strides, const R* const* igrad, const int* pos,
                                            R f1, R f2) {
   if (turb_model == TURB_NONE) return R(0);
   R w[D + 2];
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) w[v] = Ws[v * stride_v + idx];
+  if (cons) {  // rho k, rho omega -> k, omega
+    f1 = g_div(f1, w[0]);
+    f2 = g_div(f2, w[0]);
+  }
   const R p = pressure_of<R>(D, kc.gamma, w);
   if (turb_model == TURB_MUT) return g_div(f1, p);
   if (!(f1 > R(0)) || !(f2 > R(0))) return R(0);
@@ -341,12 +368,16 @@ __device__ __forceinline__ R tau_turb_cell(int turb_model, const Consts<R>& kc, 
 // cells can be evaluated side by side: the same arithmetic, with the non-positive k or
 // epsilon|omega case selected to zero at the end.
 template <int D, class R>
-__device__ __forceinline__ R tau_turb_two_eq(bool keps, const Consts<R>& kc, const R* Ws, int stride_v, int idx,
-                                             const int* strides, const R* const* igrad, const int* pos, R f1,
-                                             R f2) {
+__device__ __forceinline__ R tau_turb_two_eq(bool keps, bool cons, const Consts<R>& kc, const R* Ws, int stride_v,
+                                             int idx, const int* strides, const R* const* igrad, const int* pos,
+                                             R f1, R f2) {
   R w[D + 2];
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) w[v] = Ws[v * stride_v + idx];
+  if (cons) {  // rho k, rho omega -> k, omega
+    f1 = g_div(f1, w[0]);
+    f2 = g_div(f2, w[0]);
+  }
   const R p = pressure_of<R>(D, kc.gamma, w);
   R grad[D][D];
 #pragma unroll
@@ -481,7 +512,7 @@ __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
 // that their shared-memory and MUFU latencies overlap.  A slot past the ring repeats the last cell
 // and is not stored.  The model and limiter branches are taken once, outside the cells.
 template <int D, int PREC, int V>
-__device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc, int turb_model, int lim,
+__device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc, int turb_model, bool cons, int lim,
                                         const typename PrecT<PREC>::R* Ws, const typename PrecT<PREC>::R* Fl,
                                         typename PrecT<PREC>::R* taus, typename PrecT<PREC>::R* Ss,
                                         const typename PrecT<PREC>::R* icx, const typename PrecT<PREC>::R* icy,
@@ -514,9 +545,10 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
         const int idx = (hk * HY + hj) * HX + hi;
         const int pos[3] = {hi, hj, hk};
         if constexpr (TWO_EQ)
-          tv[q] = tau_turb_two_eq<D, R>(keps, kc, Ws, G::NH, idx, strides, igrad, pos, Fl[l], Fl[G::NR + l]);
+          tv[q] = tau_turb_two_eq<D, R>(keps, cons, kc, Ws, G::NH, idx, strides, igrad, pos, Fl[l],
+                                        Fl[G::NR + l]);
         else
-          tv[q] = tau_turb_cell<D, R>(turb_model, kc, Ws, G::NH, idx, strides, igrad, pos,
+          tv[q] = tau_turb_cell<D, R>(turb_model, cons, kc, Ws, G::NH, idx, strides, igrad, pos,
                                       turb_model == TURB_NONE ? R(0) : Fl[l], R(0));
         if constexpr (PRE) {
           // slope along each axis: normal slope of the faces along that axis, tangential slope of
@@ -607,7 +639,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       for (int v = 0; v < nv; ++v) cp_async<sizeof(S)>(&Ws[v * G::NH + l], src + (long)v * g.ncell);
     } else {
       R w[nv];
-      load_cell<D, PREC>(A, kc, gi, gj, gk, w);
+      load_cell<D, PREC>(g, A.Win, kc, gi, gj, gk, w);
 #pragma unroll
       for (int v = 0; v < nv; ++v) Ws[v * G::NH + l] = w[v];
     }
@@ -622,8 +654,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         cp_async<sizeof(R)>(&Fl[l], (const R*)A.f1 + c);
         if (two) cp_async<sizeof(R)>(&Fl[G::NR + l], (const R*)A.f2 + c);
       } else {
-        Fl[l] = load_field<R>(A, A.f1, D, gi, gj, gk);
-        if (two) Fl[G::NR + l] = load_field<R>(A, A.f2, D, gi, gj, gk);
+        R v1 = load_field<R>(A, A.f1, D, gi, gj, gk), v2 = two ? load_field<R>(A, A.f2, D, gi, gj, gk) : R(0);
+        if (g.turb_cons) {
+          // a ghost cell takes k and omega of its source cell; the ring phase divides rho k, rho omega
+          // by this cell's own (boundary-rule) density, so carry the ratio of the two densities
+          R wg[nv];
+          load_cell<D, PREC>(g, A.Win, kc, gi, gj, gk, wg);
+          const R sc = g_div(wg[0], (R)((const S*)A.Win)[field_cell(g, D, gi, gj, gk)]);
+          v1 *= sc;
+          v2 *= sc;
+        }
+        Fl[l] = v1;
+        if (two) Fl[G::NR + l] = v2;
       }
     }
   }
@@ -689,7 +731,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   const R dt = (R)dt_d;
 
   // ---- turbulent relaxation time and limited slopes on the tile and its first halo ring -------
-  ring_phase<D, PREC, V>(kc, g.turb_model, g.limiter, Ws, Fl, taus, Ss, icx, icy, icz, igx, igy, igz);
+  ring_phase<D, PREC, V>(kc, g.turb_model, g.turb_cons != 0, g.limiter, Ws, Fl, taus, Ss, icx, icy, icz, igx, igy,
+                         igz);
   __syncthreads();
 
   // ---- fluxes of every face of the tile ----------------------------------------------------
@@ -821,6 +864,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
 #pragma unroll
         for (int k = 0; k < D; ++k) Fs[(1 + perm[k]) * G::NF + f] = F[1 + k];
         Fs[(D + 1) * G::NF + f] = F[D + 1];
+        if (A.mflux[0]) {
+          // global face (cell c = tile origin + (ci, cj, ck), face c - 1/2 along ax)
+          const int gc[3] = {ox + ci, oy + cj, oz + ck};
+          int nf[3] = {g.n[0], g.n[1], g.n[2]};
+          nf[ax] += 1;
+          if (gc[0] < nf[0] && gc[1] < nf[1] && gc[2] < nf[2])
+            ((R*)A.mflux[ax])[((long)gc[2] * nf[1] + gc[1]) * nf[0] + gc[0]] = F[0];
+        }
       }
       if constexpr (kThreads % 128 == 0)
         asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libgks.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT, EUNSUPPORTED = range(7)
 BC = {"periodic": 0, "transmissive": 1, "wall": 2, "dirichlet": 3, "outflow": 4}
-TURB = {"none": 0, "mut": 1, "keps": 2, "komega": 3}
+TURB = {"none": 0, "mut": 1, "keps": 2, "komega": 3, "komega_transport": 4}
 LIMITER = {"minmod": 0, "vanleer": 1}
 EXPAND = {"directional": 0, "multid": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
@@ -78,6 +78,9 @@ def load():
     L.gks_status_word.argtypes = [H, ctypes.POINTER(ctypes.c_uint), _PD]
     L.gks_get_rarefaction.argtypes = [H, _V, _I, _I]
     L.gks_get_tau_turb.argtypes = [H, _V, _I, _I]
+    L.gks_komega_defaults.argtypes = [ctypes.POINTER(KOmega)]
+    L.gks_set_komega.argtypes = [H, ctypes.POINTER(KOmega)]
+    L.gks_get_turbulence.argtypes = [H, _V, _V, _I, _I]
     L.gks_enable_timing.argtypes = [H, _I]
     L.gks_kernel_time.argtypes = [H, _PD, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_destroy.argtypes = [H]
@@ -98,7 +101,7 @@ def load():
     for name in ("gks_create", "gks_set_state", "gks_get_state", "gks_set_turbulence", "gks_compute_dt",
                  "gks_step", "gks_get_time", "gks_set_time", "gks_residual", "gks_status_word",
                  "gks_get_rarefaction", "gks_get_tau_turb", "gks_enable_timing", "gks_kernel_time",
-                 "gks_destroy", "gks_face_flux"):
+                 "gks_destroy", "gks_face_flux", "gks_komega_defaults", "gks_set_komega", "gks_get_turbulence"):
         getattr(L, name).restype = _I
     _lib = L
     return L
@@ -110,6 +113,21 @@ def _f64(a):
 
 def _is_torch(x):
     return type(x).__module__.startswith("torch")
+
+
+class KOmega(ctypes.Structure):
+    """gks_komega: closure coefficients of the k-omega transport (Wilcox 2006 defaults)."""
+    _fields_ = [("alpha", ctypes.c_double), ("beta0", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("sigma_star", ctypes.c_double), ("sigma_do", ctypes.c_double), ("C_lim", ctypes.c_double),
+                ("omega_floor", ctypes.c_double), ("sources", ctypes.c_int), ("diffusion", ctypes.c_int)]
+
+
+def komega_defaults(**over):
+    c = KOmega()
+    load().gks_komega_defaults(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
 
 
 class Solver:
@@ -251,6 +269,24 @@ class Solver:
         self._check(load().gks_get_rarefaction(self._h, p, mem, dt))
         self._after_device_write(out)
         return out
+
+    def set_komega(self, **coeffs):
+        """Closure coefficients of the k-omega transport (keywords of gks_komega)."""
+        self._check(load().gks_set_komega(self._h, ctypes.byref(komega_defaults(**coeffs))))
+
+    def get_turbulence(self, k_out=None, omega_out=None):
+        """Transported k and omega (k-omega transport handles)."""
+        if k_out is None:
+            k_out = np.zeros(self.ncell)
+        if omega_out is None:
+            omega_out = np.zeros(self.ncell)
+        pk, mem, dt = self._ptr(k_out, writable=True)
+        pw, mem2, dt2 = self._ptr(omega_out, writable=True)
+        assert (mem, dt) == (mem2, dt2)
+        self._check(load().gks_get_turbulence(self._h, pk, pw, mem, dt))
+        self._after_device_write(k_out)
+        self._after_device_write(omega_out)
+        return k_out, omega_out
 
     def tau_turb(self, out=None):
         if out is None:
