@@ -216,6 +216,14 @@ void launch_step(gks_handle* h, const StepArgs& A) {
   K.omega_floor = h->kw.omega_floor;
   K.sources = h->kw.sources;
   K.diffusion = h->kw.diffusion;
+  K.falpha = (float)K.alpha;
+  K.fbeta0 = (float)K.beta0;
+  K.fbeta_star = (float)K.beta_star;
+  K.fsigma = (float)K.sigma;
+  K.fsigma_star = (float)K.sigma_star;
+  K.fsigma_do = (float)K.sigma_do;
+  K.fC_lim = (float)K.C_lim;
+  K.fomega_floor = (float)K.omega_floor;
   launch_komega(h->D, h->prec, K, h->stream);
 }
 

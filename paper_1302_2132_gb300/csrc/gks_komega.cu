@@ -15,7 +15,8 @@
 // omega >= omega_floor.  Ghost values of k and omega: periodic axes wrap, other axes repeat the
 // nearest interior cell; ghost flow states follow the flow's boundary rules.
 //
-// One thread per cell; the inputs (state, k, omega, mass fluxes) of a 1024^2 grid stay in L2.
+// Tiles of cells per block with a shared-memory halo (ghost cells resolved once per tile), one
+// thread per cell; the inputs (state, k, omega, mass fluxes) of a 1024^2 grid stay in L2.
 #include "gks_dispatch.h"
 #include "gks_step.cuh"
 
@@ -23,35 +24,75 @@ namespace gks {
 
 namespace {
 
+// Tile of cells per 256-thread block; k, omega, density and velocity of the tile and two halo
+// layers are staged in shared memory once (ghost cells resolved there), then one thread per cell.
+template <int D> struct KTile;
+template <> struct KTile<1> { static constexpr int X = 256, Y = 1, Z = 1; };
+template <> struct KTile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <> struct KTile<3> { static constexpr int X = 8, Y = 8, Z = 4; };
+
 template <int D, int PREC>
 __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOmegaArgs K) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
+  using T = KTile<D>;
   constexpr int nv = D + 2;
+  constexpr int HX = T::X + 4, HY = D >= 2 ? T::Y + 4 : 1, HZ = D >= 3 ? T::Z + 4 : 1, NH = HX * HY * HZ;
+  __shared__ R sk[NH], sw[NH], sr[NH], su[D][NH];
+  __shared__ R swid[HX + HY + HZ];  // widths of the halo cells along each axis (arithmetic type)
+  __shared__ R s_dt;
   const DevGrid& g = K.g;
-  const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= g.ncell) return;
-  const int c[3] = {(int)(cell % g.n[0]), (int)((cell / g.n[0]) % g.n[1]), (int)(cell / ((long)g.n[0] * g.n[1]))};
+  const int tiles_x = (g.n[0] + T::X - 1) / T::X;
+  const int tiles_y = D >= 2 ? (g.n[1] + T::Y - 1) / T::Y : 1;
+  const int b = blockIdx.x;
+  const int ox = (b % tiles_x) * T::X;
+  const int oy = D >= 2 ? ((b / tiles_x) % tiles_y) * T::Y : 0;
+  const int oz = D >= 3 ? (b / (tiles_x * tiles_y)) * T::Z : 0;
+  const int tid = threadIdx.x;
   const Consts<R> kc = make_consts<R>(g);
-  const R dt = (R)K.ctrl->last_dt;
-  const R mu = kc.mu;
   const R* RK = (const R*)K.RKin;
   const R* RW = (const R*)K.RWin;
   const S* W = (const S*)K.Win;
 
-  // cell index of the cell shifted by s along axis a: periodic wrap, otherwise the nearest cell
-  auto mapped = [&](int a, int s) -> long {
-    int cc[3] = {c[0], c[1], c[2]};
-    const int n = g.n[a];
-    cc[a] += s;
-    if (cc[a] < 0 || cc[a] >= n) cc[a] = g.bc[a][0] == BC_PERIODIC ? (cc[a] + 2 * n) % n : min(max(cc[a], 0), n - 1);
-    return cell_index(g, cc[0], cc[1], cc[2]);
-  };
+  // ---- stage: flow state with the boundary rules, k and omega of the source cell ------------
+  for (int l = tid; l < NH; l += 256) {
+    const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
+    const int gi = ox + hi - 2, gj = D >= 2 ? oy + hj - 2 : 0, gk = D >= 3 ? oz + hk - 2 : 0;
+    R w[nv];
+    load_cell<D, PREC>(g, K.Win, kc, gi, gj, gk, w);
+    sr[l] = w[0];
+#pragma unroll
+    for (int a = 0; a < D; ++a) su[a][l] = g_div(w[1 + a], w[0]);
+    const long m = field_cell(g, D, gi, gj, gk);
+    const R rm = (R)W[m];
+    sk[l] = g_div(RK[m], rm);
+    sw[l] = g_div(RW[m], rm);
+  }
+  // widths (converted once per block: double-to-float conversions run on the FP64 pipe) and dt
+  for (int l = tid; l < HX + HY + HZ; l += 256) {
+    const int a = l < HX ? 0 : (l < HX + HY ? 1 : 2);
+    const int p = a == 0 ? l : (a == 1 ? l - HX : l - HX - HY);
+    const int o = a == 0 ? ox : (a == 1 ? oy : oz);
+    swid[l] = a < D ? (R)g.w[a][min(o + p, g.n[a] + 3)] : R(1);
+  }
+  if (tid == 0) s_dt = (R)K.ctrl->last_dt;
+  __syncthreads();
 
-  R wc[nv];
-  load_stored<D, PREC>(g, K.Win, cell, wc);
-  const R rho = wc[0];
-  const R kk = g_div(RK[cell], rho), om = g_div(RW[cell], rho);
+  const int li = tid % T::X, lj = (tid / T::X) % T::Y, lk = tid / (T::X * T::Y);
+  const int c[3] = {ox + li, oy + lj, oz + lk};
+  if (c[0] >= g.n[0] || (D >= 2 && c[1] >= g.n[1]) || (D >= 3 && c[2] >= g.n[2])) return;
+  const long cell = cell_index(g, c[0], c[1], c[2]);
+  const int h0 = ((lk + (D >= 3 ? 2 : 0)) * HY + (lj + (D >= 2 ? 2 : 0))) * HX + (li + 2);
+  const int hs[3] = {1, HX, HX * HY};
+  const R dt = s_dt;
+  const R mu = kc.mu;
+  constexpr bool F = sizeof(R) == sizeof(float);
+  const R c_alpha = F ? (R)K.falpha : (R)K.alpha, c_beta0 = F ? (R)K.fbeta0 : (R)K.beta0;
+  const R c_bstar = F ? (R)K.fbeta_star : (R)K.beta_star, c_sigma = F ? (R)K.fsigma : (R)K.sigma;
+  const R c_sstar = F ? (R)K.fsigma_star : (R)K.sigma_star, c_sdo = F ? (R)K.fsigma_do : (R)K.sigma_do;
+  const R c_clim = F ? (R)K.fC_lim : (R)K.C_lim, c_wfloor = F ? (R)K.fomega_floor : (R)K.omega_floor;
+  const R rho = sr[h0];
+  const R kk = sk[h0], om = sw[h0];
   R ak = RK[cell], aw = RW[cell];
   R grad[3][3];  // grad[a][b] = dU_b / dx_a
   R gk[3], gw[3];
@@ -59,33 +100,25 @@ __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOm
   for (int a = 0; a < 3; ++a) {
     gk[a] = gw[a] = R(0);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) grad[a][b] = R(0);
+    for (int bb = 0; bb < 3; ++bb) grad[a][bb] = R(0);
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const double* wd = g.w[a];
-    // k, omega at the cells -2 .. +2 along a; flow states (boundary rules) at -1 and +1
+    const R* wd = swid + (a == 0 ? 0 : (a == 1 ? HX : HX + HY));  // halo position p = cell + 2 - tile origin
+    const int st = hs[a];
+    const int pa = (a == 0 ? li : (a == 1 ? lj : lk)) + 2;
+    // k, omega and widths at the cells -2 .. +2 along a
     R phi[2][5], wid[5];
 #pragma unroll
     for (int t = -2; t <= 2; ++t) {
-      const long m = mapped(a, t);
-      const R r = (R)W[m];
-      phi[0][t + 2] = g_div(RK[m], r);
-      phi[1][t + 2] = g_div(RW[m], r);
-      wid[t + 2] = (R)wd[c[a] + t + 2];
+      phi[0][t + 2] = sk[h0 + t * st];
+      phi[1][t + 2] = sw[h0 + t * st];
+      wid[t + 2] = wd[pa + t];
     }
-    R wm[nv], wp[nv];
-    {
-      int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
-      cm[a] -= 1;
-      cp[a] += 1;
-      load_cell<D, PREC>(g, K.Win, kc, cm[0], cm[1], cm[2], wm);
-      load_cell<D, PREC>(g, K.Win, kc, cp[0], cp[1], cp[2], wp);
-    }
-    const R rfl[3] = {wm[0], rho, wp[0]};  // flow densities of the cells -1, 0, +1
+    const R rfl[3] = {sr[h0 - st], rho, sr[h0 + st]};  // flow densities of the cells -1, 0, +1
     const R dist = R(0.5) * wid[1] + wid[2] + R(0.5) * wid[3];
 #pragma unroll
-    for (int b = 0; b < D; ++b) grad[a][b] = g_div(g_div(wp[1 + b], wp[0]) - g_div(wm[1 + b], wm[0]), dist);
+    for (int bb = 0; bb < D; ++bb) grad[a][bb] = g_div(su[bb][h0 + st] - su[bb][h0 - st], dist);
     gk[a] = g_div(phi[0][3] - phi[0][1], dist);
     gw[a] = g_div(phi[1][3] - phi[1][1], dist);
     // mass fluxes of the faces c - 1/2 and c + 1/2
@@ -110,10 +143,10 @@ __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOm
         const R hp = R(0.5) * (wid[t] + wid[t + 1]);
         sl[t - 1] = limiter<R>(g.limiter, g_div(v[t] - v[t - 1], hm), g_div(v[t + 1] - v[t], hp));
       }
-      const R sig = q == 0 ? (R)K.sigma_star : (R)K.sigma;
+      const R sig = q == 0 ? c_sstar : c_sigma;
       R G[2];
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {  // face between cells e - 1 and e (relative positions)
+      for (int e = 0; e < 2; ++e) {  // face between the cells e - 1 and e (relative positions)
         const int tl = e, tr = e + 1;  // indices into sl / rfl / md (cells -1, 0, +1)
         const R fr = Fm[e];
         const R hl = wid[tl + 1], hr = wid[tr + 1];
@@ -156,8 +189,8 @@ __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOm
         SbSb += sb * sb;
       }
     const R X = R(2) * SS - g_div(R(2), R(3)) * div * div;
-    const R bstar = (R)K.beta_star;
-    const R lim = (R)K.C_lim * g_sqrt(g_div(R(2) * SbSb, bstar));
+    const R bstar = c_bstar;
+    const R lim = c_clim * g_sqrt(g_div(R(2) * SbSb, bstar));
     const R wt = om > lim ? om : lim;
     const R muT = g_div(rho * kk, wt);
     const R Pk = muT * X - g_div(R(2), R(3)) * rho * kk * div;
@@ -174,13 +207,13 @@ __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOm
       chi = g_abs(g_div(t, bo * bo * bo));
     }
     const R fbeta = g_div(R(1) + R(85) * chi, R(1) + R(100) * chi);
-    const R beta = (R)K.beta0 * fbeta;
+    const R beta = c_beta0 * fbeta;
     R dkdw = R(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) dkdw += gk[a] * gw[a];
-    const R sd = dkdw > R(0) ? (R)K.sigma_do : R(0);
+    const R sd = dkdw > R(0) ? c_sdo : R(0);
     const R CD = g_div(sd * rho, om) * dkdw;
-    const R alpha = (R)K.alpha;
+    const R alpha = c_alpha;
     ak += dt * Pk;
     aw += dt * (alpha * rho * g_div(om, wt) * X - g_div(R(2), R(3)) * alpha * rho * om * div + CD);
     rate_k = bstar * om;
@@ -189,14 +222,17 @@ __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOm
   ak = g_div(ak, R(1) + dt * rate_k);
   aw = g_div(aw, R(1) + dt * rate_w);
   const R rho_new = (R)((const S*)K.Wnew)[cell];
-  const R wfloor = rho_new * (R)K.omega_floor;
+  const R wfloor = rho_new * c_wfloor;
   ((R*)K.RKout)[cell] = ak > R(0) ? ak : R(0);
   ((R*)K.RWout)[cell] = aw > wfloor ? aw : wfloor;
 }
 
 template <int D, int PREC>
 void launch_d(const KOmegaArgs& K, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((K.g.ncell + 255) / 256);
+  using T = KTile<D>;
+  unsigned blocks = 1;
+  const int tt[3] = {T::X, T::Y, T::Z};
+  for (int a = 0; a < 3; ++a) blocks *= (unsigned)((K.g.n[a] + tt[a] - 1) / tt[a]);
   komega_kernel<D, PREC><<<blocks, 256, 0, s>>>(K);
 }
 

@@ -155,6 +155,7 @@ struct KOmegaArgs {
   const void* mflux[3];  // the flow step's time-integrated face mass fluxes (StepArgs::mflux)
   const Ctrl* ctrl;      // last_dt: the step's dt
   double alpha, beta0, beta_star, sigma, sigma_star, sigma_do, C_lim, omega_floor;
+  float falpha, fbeta0, fbeta_star, fsigma, fsigma_star, fsigma_do, fC_lim, fomega_floor;  // same, float
   int sources, diffusion;
 };
 
