@@ -471,6 +471,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
     if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
+    if (e == cudaSuccess) e = prepare_komega();
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bad(GKS_ECUDA, "kernel attribute setup failed");

@@ -35,6 +35,7 @@ void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cud
 void launch_batch_d2(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
 
 // k-omega transport step after a flow step (gks_komega.cu)
+cudaError_t prepare_komega();
 void launch_komega(int D, int prec, const KOmegaArgs& K, cudaStream_t s);
 
 void launch_face_flux(int D, int prec, bool multid, int abar_t0, double gamma, double mu, double C_a,
