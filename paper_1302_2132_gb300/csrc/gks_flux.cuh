@@ -392,51 +392,55 @@ GKS_FN void slope(const Maxw<D, T>& g, T bK, const T* rhs, T* a) {
 // With x = dt/tau and phi_k(x) = sum_m (-x)^m/(m+k)!: T0 = dt x phi2, T1 = -dt^2 x (phi2 - 2 phi3),
 // T2 = dt^2 x phi3, T3 = dt phi1, T4 = tau dt (e - 2 phi1), T5 = -tau dt phi1, Dn = dt^2 phi2.
 // For x < 1 phi3 is summed from its series and phi2, phi1, e by the backward recurrence
-// phi_{k-1} = 1/(k-1)! - x phi_k (no cancellation); otherwise the closed forms in e = exp(-x) are used.
+// phi_{k-1} = 1/(k-1)! - x phi_k (no cancellation), in the arithmetic type; otherwise the closed
+// forms in e = exp(-x) are used.
 struct TimeCoef {
   double T[6];
   double r1, r4, r5;
 };
 
-GKS_FN void phi_series(double x, double& p1, double& p2, double& p3, double& e) {
-  // 1/(m+3)! for m = 0..17
+// phi3 = sum_m (-x)^m / (m+3)! by Horner, then phi2, phi1 and e = exp(-x) by the backward recurrence
+// phi_{k-1} = 1/(k-1)! - x phi_k.  For 0 <= x < 1 every step is free of cancellation; 18 terms
+// reach double precision, 12 leave a truncation below 1e-9 (enough in single precision).
+template <class T>
+GKS_FN void phi_series(T x, T& p1, T& p2, T& p3, T& e) {
+  constexpr int N = sizeof(T) == sizeof(float) ? 12 : 18;
   const double c[18] = {1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
                         1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
                         1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0,
                         1.0 / 355687428096000.0, 1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0,
                         1.0 / 2432902008176640000.0};
-  double s = c[17];
+  T s = T(c[N - 1]);
 #pragma unroll
-  for (int m = 16; m >= 0; --m) s = c[m] - x * s;
+  for (int m = N - 2; m >= 0; --m) s = T(c[m]) - x * s;
   p3 = s;
-  p2 = 0.5 - x * p3;
-  p1 = 1.0 - x * p2;
-  e = 1.0 - x * p1;
+  p2 = T(0.5) - x * p3;
+  p1 = T(1) - x * p2;
+  e = T(1) - x * p1;
 }
 
-// tau = 0 needs no branch of its own: x = dt/tau is +infinity, e = 0, and the closed forms give the
-// limits T0 = dt, T1 = 0, T2 = dt^2/2, T3 = T4 = T5 = 0, r1 = -1, r4 = r5 = 0 exactly.
 template <class T>
 GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
   const T x = g_div(dt, tau);
   if (x < T(1)) {
-    // series branch in double precision for either arithmetic type
-    double p1, p2, p3, e;
-    const double xd = (double)x, dtd = (double)dt, taud = (double)tau;
+    // series branch (phi_k summed, no cancellation) in the arithmetic type
+    T p1, p2, p3, e;
+    const T xd = x, dtd = dt, taud = tau;
     phi_series(xd, p1, p2, p3, e);
-    const double Dn = dtd * dtd * p2;
-    const double T1 = -dtd * dtd * xd * (p2 - 2.0 * p3);
-    const double T4 = taud * dtd * (e - 2.0 * p1);
-    const double T5 = -taud * dtd * p1;
-    Tc[0] = (T)(dtd * xd * p2);
-    Tc[1] = (T)T1;
-    Tc[2] = (T)(dtd * dtd * xd * p3);
-    Tc[3] = (T)(dtd * p1);
-    Tc[4] = (T)T4;
-    Tc[5] = (T)T5;
-    r1 = (T)(T1 / Dn);
-    r4 = (T)(T4 / Dn);
-    r5 = (T)(T5 / Dn);
+    const T Dn = dtd * dtd * p2;
+    const T T1 = -dtd * dtd * xd * (p2 - T(2) * p3);
+    const T T4 = taud * dtd * (e - T(2) * p1);
+    const T T5 = -taud * dtd * p1;
+    Tc[0] = dtd * xd * p2;
+    Tc[1] = T1;
+    Tc[2] = dtd * dtd * xd * p3;
+    Tc[3] = dtd * p1;
+    Tc[4] = T4;
+    Tc[5] = T5;
+    const T iDn = g_rcp(Dn);
+    r1 = T1 * iDn;
+    r4 = T4 * iDn;
+    r5 = T5 * iDn;
   } else {
     const T e = g_exp(-x);
     const T q = T(1) - e;
