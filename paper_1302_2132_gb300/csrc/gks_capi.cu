@@ -183,6 +183,8 @@ void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
     launch_step_d1(h->prec, false, A, tiles_for(h, 0), h->stream);
   else if (h->D == 2 && variant > 0)
     launch_step_d2_variant(variant, h->multid, A, tiles_for(h, variant), h->stream);
+  else if (h->D == 3 && variant > 0)
+    launch_step_d3_variant(variant, h->multid, A, tiles_for(h, variant), h->stream);
   else if (h->D == 2)
     launch_step_d2(h->prec, h->multid, A, tiles_for(h, 0), h->stream);
   else
@@ -345,6 +347,7 @@ std::mutex g_tuned_mutex;
 int n_variants(const gks_handle* h) {
   if (h->D == 1) return kTileVariants1D;
   if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
+  if (h->D == 3 && h->prec == PREC_F32) return kTileVariants3D;
   return 1;
 }
 
@@ -471,6 +474,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
     if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
+    if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess) e = prepare_komega();
     if (e != cudaSuccess) {
       cudaGetLastError();

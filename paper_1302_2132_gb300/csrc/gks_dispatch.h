@@ -23,6 +23,10 @@ constexpr int kTileVariants2D = 6;
 // variants 3 to 5 (their own translation unit)
 cudaError_t prepare_step_d2_variants2();
 void launch_step_d2_variant2(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
+// 3D FP32 tile variants 1 and 2 (256-cell tiles with the slope table)
+cudaError_t prepare_step_d3_variants();
+void launch_step_d3_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
+constexpr int kTileVariants3D = 3;
 // 1D tile variants 1 and 2 (narrow tiles for small grids)
 cudaError_t prepare_step_d1_variants();
 void launch_step_d1_variant(int variant, int prec, const StepArgs& A, int nblocks, cudaStream_t s);

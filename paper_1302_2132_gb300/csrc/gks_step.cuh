@@ -46,6 +46,9 @@ template <> struct Tile<2, 4> { static constexpr int X = 32, Y = 18, Z = 1, T = 
 // warps of an SM work in the same phase of one tile
 template <> struct Tile<2, 5> { static constexpr int X = 64, Y = 27, Z = 1, T = 512; };
 template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 256; };
+// 256-cell 3D tiles with the per-cell slope table (two CTAs per SM): 944 and 896 faces
+template <> struct Tile<3, 1> { static constexpr int X = 16, Y = 8, Z = 2, T = 256; };
+template <> struct Tile<3, 2> { static constexpr int X = 8, Y = 8, Z = 4, T = 256; };
 
 template <int D, int V = 0> struct TileGeom {
   static constexpr int X = Tile<D, V>::X, Y = Tile<D, V>::Y, Z = Tile<D, V>::Z, T = Tile<D, V>::T;
@@ -162,9 +165,10 @@ struct KOmegaArgs {
 
 template <int PREC> struct PrecT;
 
-// Cell slopes are precomputed in shared memory in 1D and 2D; in 3D the 15 slopes per ring cell would
-// hold the tile to one CTA per SM, so the faces recompute them (two CTAs per SM in FP32).
-template <int D, int PREC> __host__ __device__ constexpr bool pre_slopes() { return D < 3; }
+// Cell slopes are precomputed in shared memory in 1D, 2D and for the small 3D tiles (variants 1, 2:
+// 256 cells); the 15 slopes per ring cell of the 512-cell 3D tile would hold it to one CTA per SM,
+// so its faces recompute them (two CTAs per SM in FP32).
+template <int D, int PREC, int V = 0> __host__ __device__ constexpr bool pre_slopes() { return D < 3 || V > 0; }
 template <> struct PrecT<PREC_F64> { using R = double; using S = double; };
 template <> struct PrecT<PREC_F32> { using R = float; using S = float; };
 template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
@@ -522,7 +526,7 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
   using R = typename PrecT<PREC>::R;
   using G = TileGeom<D, V>;
   constexpr int kThreads = G::T, nv = D + 2, HX = G::HX, HY = G::HY;
-  constexpr bool PRE = pre_slopes<D, PREC>();
+  constexpr bool PRE = pre_slopes<D, PREC, V>();
   const int tid = threadIdx.x;
   const int strides[3] = {1, HX, HX * HY};
   const R* igrad[3] = {igx, igy, igz};
@@ -600,7 +604,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   constexpr int X = G::X, Y = G::Y, Z = G::Z, HX = G::HX, HY = G::HY, HZ = G::HZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* Ws = (R*)smem_raw;                    // [nv][HZ][HY][HX]
-  constexpr bool PRE = pre_slopes<D, PREC>();
+  constexpr bool PRE = pre_slopes<D, PREC, V>();
   R* taus = Ws + (size_t)nv * G::NH;       // [RZ][RY][RX]
   R* Fs = taus + G::NR;                    // [nv][NF]
   R* wsx = Fs + (size_t)nv * G::NF;        // widths with halo
@@ -1050,14 +1054,14 @@ cudaError_t prepare_batch() {
 template <int D, int PREC, bool MULTID, int V = 0>
 void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
   step_kernel<D, PREC, MULTID, V><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
 }
 
 template <int D, int PREC, bool MULTID, int V = 0>
 cudaError_t prepare_step() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
+  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
   return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }

@@ -32,7 +32,12 @@ void tile_shape(int D, int variant, int* x, int* y, int* z) {
     *z = 1;
     return;
   }
-  if (D == 3) { *x = Tile<3, 0>::X; *y = Tile<3, 0>::Y; *z = Tile<3, 0>::Z; return; }
+  if (D == 3) {
+    if (variant == 1) { *x = Tile<3, 1>::X; *y = Tile<3, 1>::Y; *z = Tile<3, 1>::Z; }
+    else if (variant == 2) { *x = Tile<3, 2>::X; *y = Tile<3, 2>::Y; *z = Tile<3, 2>::Z; }
+    else { *x = Tile<3, 0>::X; *y = Tile<3, 0>::Y; *z = Tile<3, 0>::Z; }
+    return;
+  }
   if (variant == 1) { *x = Tile<2, 1>::X; *y = Tile<2, 1>::Y; }
   else if (variant == 2) { *x = Tile<2, 2>::X; *y = Tile<2, 2>::Y; }
   else if (variant == 3) { *x = Tile<2, 3>::X; *y = Tile<2, 3>::Y; }

@@ -368,3 +368,22 @@ def test_1d_tile_variants_match_oracle(monkeypatch, variant):
     assert s.tile_shape()[:2] == (int(variant), {"0": 256, "1": 31, "2": 63}[variant])
     assert np.all(rel_err_per_var(Wg, Wo, 3) < 1e-12)
     s.close()
+
+
+def test_3d_tile_variants_agree(monkeypatch):
+    """The three 3D FP32 tile shapes (16x8x4 without the slope table, 16x8x2 and 8x8x4 with it)
+    evaluate the same faces: their results agree to FP32 rounding."""
+    spec = inputs.turbulence(20, 3, seed=17)
+    kw = dict(turb_model=2, multid=1, mu=1e-5, precision="fp32")
+    out = []
+    for v in ("0", "1", "2"):
+        monkeypatch.setenv("GKS_TILE_VARIANT", v)
+        s = gpu_solver(spec, **kw)
+        s.set_state(spec["prim"].ravel(), layout="soa_prim")
+        s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+        s.step(nsteps=10, cfl=0.5)
+        assert s.tile_shape()[0] == int(v)
+        out.append(s.get_state())
+        s.close()
+    for W in out[1:]:
+        assert np.all(rel_err_per_var(W, out[0], 5) < 1e-6)
