@@ -33,6 +33,7 @@ BC_PERIODIC, BC_TRANSMISSIVE, BC_WALL, BC_DIRICHLET, BC_OUTFLOW = 0, 1, 2, 3, 4
 TURB_NONE, TURB_MUT, TURB_KEPS, TURB_KOMEGA = 0, 1, 2, 3
 LIM_MINMOD, LIM_VANLEER = 0, 1
 ABAR_TIMEINT, ABAR_T0 = 0, 1
+RECON_MUSCL2, RECON_MUSCL3, RECON_WENO5 = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -69,6 +70,7 @@ class Problem(ctypes.Structure):
         ("limiter", ctypes.c_int),
         ("multid", ctypes.c_int),
         ("abar_mode", ctypes.c_int),
+        ("recon", ctypes.c_int),
     ]
 
 
@@ -121,6 +123,7 @@ def lib():
                                         ctypes.POINTER(FaceDiag)]
             L.orc_face_flux_compact.argtypes = [_I, _D, _D, _D, _D, _I, _I, _I, ctypes.POINTER(Face), _PD]
             L.orc_euler_flux.argtypes = [_I, _D, _PD, _PD]
+            L.orc_reconstruct.argtypes = [_I, _I, _PD, _PD, _I, _PD, _PD]
             P = ctypes.POINTER(Problem)
             L.orc_prim_to_cons.argtypes = [P, _PD, _PD, ctypes.c_long]
             L.orc_cons_to_prim.argtypes = [P, _PD, _PD, ctypes.c_long]
@@ -209,6 +212,17 @@ def face_flux_compact(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIME
     return F
 
 
+def reconstruct(recon, v, h=None, limiter=LIM_VANLEER):
+    """Face values of a 1D row of cell averages: (wl, wr) with wl[i] the value of cell i at its right
+    face and wr[i] at its left face (NaN where the stencil is incomplete)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    h = np.ascontiguousarray(np.ones_like(v) if h is None else h, dtype=np.float64)
+    wl = np.full_like(v, np.nan)
+    wr = np.full_like(v, np.nan)
+    lib().orc_reconstruct(recon, limiter, _ptr(v), _ptr(h), v.size, _ptr(wl), _ptr(wr))
+    return wl, wr
+
+
 def euler_flux(D, gamma, w):
     w = np.ascontiguousarray(w, dtype=np.float64)
     F = np.zeros(D + 2)
@@ -224,7 +238,7 @@ class Case:
 
     def __init__(self, dim, n, dx, bc, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model=TURB_NONE,
                  C_mu=0.09, beta_star=0.09, C_a=0.0, limiter=LIM_VANLEER, multid=1,
-                 abar_mode=ABAR_TIMEINT, bc_prim=None):
+                 abar_mode=ABAR_TIMEINT, bc_prim=None, recon=RECON_MUSCL2):
         self.dim = dim
         self.n = tuple(n)
         self.P = Problem()
@@ -245,6 +259,7 @@ class Case:
         self.P.gamma, self.P.mu, self.P.T_wall = gamma, mu, T_wall
         self.P.turb_model, self.P.C_mu, self.P.beta_star, self.P.C_a = turb_model, C_mu, beta_star, C_a
         self.P.limiter, self.P.multid, self.P.abar_mode = limiter, multid, abar_mode
+        self.P.recon = recon
         self.ncell = int(np.prod(n[:dim]))
         self.nv = dim + 2
 

@@ -416,6 +416,8 @@ void face_flux(const FaceWork& W, double* F) {
 // ---------------------------------------------------------------------------------------------
 // Grid machinery: SoA state [nv][nz][ny][nx]; a padded copy with two ghost layers per active axis.
 // ---------------------------------------------------------------------------------------------
+const int NGH = 3;  // ghost layers per side (the WENO-5 stencil reaches three cells)
+
 struct Grid {
   int D, nv, n[3], N[3], g[3];
   long ncell, npad;
@@ -434,24 +436,24 @@ Grid make_grid(const orc_problem* P) {
   for (int d = 0; d < 3; ++d) {
     bool act = d < P->dim;
     G.n[d] = act ? P->n[d] : 1;
-    G.g[d] = act ? 2 : 0;
+    G.g[d] = act ? NGH : 0;
     G.N[d] = G.n[d] + 2 * G.g[d];
     G.ncell *= G.n[d];
     G.npad *= G.N[d];
-    G.w[d].assign(G.n[d] + 4, 1.0);
+    G.w[d].assign(G.n[d] + 2 * NGH, 1.0);
     if (act) {
       int n = G.n[d];
-      for (int i = 0; i < n; ++i) G.w[d][i + 2] = P->dx[d][i];
+      for (int i = 0; i < n; ++i) G.w[d][i + NGH] = P->dx[d][i];
       bool per = P->bc[d][0] == ORC_BC_PERIODIC;
-      for (int gi = 1; gi <= 2; ++gi) {
-        G.w[d][2 - gi] = per ? P->dx[d][n - gi] : P->dx[d][gi - 1];
-        G.w[d][n + 1 + gi] = per ? P->dx[d][gi - 1] : P->dx[d][n - gi];
+      for (int gi = 1; gi <= NGH; ++gi) {
+        G.w[d][NGH - gi] = per ? P->dx[d][n - gi] : P->dx[d][std::min(gi - 1, n - 1)];
+        G.w[d][n + NGH - 1 + gi] = per ? P->dx[d][gi - 1] : P->dx[d][std::max(n - gi, 0)];
       }
     }
   }
   return G;
 }
-double width(const Grid& G, int d, int i) { return G.w[d][i + 2]; }
+double width(const Grid& G, int d, int i) { return G.w[d][i + NGH]; }
 
 void cons_from_prim(int D, double gamma, const double* pr, double* w) {
   double q = 0.0;
@@ -488,7 +490,7 @@ void fill_ghosts(const orc_problem* P, const Grid& G, std::vector<double>& Wp) {
     const int n = G.n[a];
     for (int side = 0; side < 2; ++side) {
       int bc = P->bc[a][side];
-      for (int gi = 1; gi <= 2; ++gi) {
+      for (int gi = 1; gi <= NGH; ++gi) {
         int gidx = side == 0 ? -gi : n - 1 + gi;
         int c[3];
         for (c[2] = lo[2]; c[2] < hi[2]; ++c[2])
@@ -628,6 +630,47 @@ double limiter(int lim, double a, double b) {
   return (a * b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
 }
 
+// Face values at the face between cells 0 and 1 of a stencil v[0..5] = cells -2 .. 3 (widths wd):
+// wl is cell 0's value at that face, wr cell 1's.
+//   MUSCL2: limited slopes over the centre distances, w = W +- h/2 s (the scheme's default).
+//   MUSCL3: the kappa = 1/3 scheme in index space, each one-sided difference limited by minmod
+//           against 4 times the other (the compression (3 - kappa)/(1 - kappa) of kappa = 1/3):
+//           w_{j+1/2} = W_j + (1/6) minmod(D-, 4 D+) + (1/3) minmod(D+, 4 D-), mirrored for w_{j-1/2}.
+//   WENO5:  Jiang and Shu's fifth-order weighted reconstruction in index space (linear weights
+//           1/10, 6/10, 3/10; smoothness indicators with 13/12 and 1/4; epsilon 1e-6).
+double weno5(double a, double b, double c, double d, double e) {  // value at the face right of c
+  double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+  double b0 = 13.0 / 12.0 * (a - 2.0 * b + c) * (a - 2.0 * b + c) + 0.25 * (a - 4.0 * b + 3.0 * c) * (a - 4.0 * b + 3.0 * c);
+  double b1 = 13.0 / 12.0 * (b - 2.0 * c + d) * (b - 2.0 * c + d) + 0.25 * (b - d) * (b - d);
+  double b2 = 13.0 / 12.0 * (c - 2.0 * d + e) * (c - 2.0 * d + e) + 0.25 * (3.0 * c - 4.0 * d + e) * (3.0 * c - 4.0 * d + e);
+  const double eps = 1e-6;
+  double a0 = 0.1 / ((eps + b0) * (eps + b0));
+  double a1 = 0.6 / ((eps + b1) * (eps + b1));
+  double a2 = 0.3 / ((eps + b2) * (eps + b2));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+void recon_face(int recon, int lim, const double* v, const double* wd, double& wl, double& wr) {
+  if (recon == ORC_RECON_WENO5) {
+    wl = weno5(v[0], v[1], v[2], v[3], v[4]);
+    wr = weno5(v[5], v[4], v[3], v[2], v[1]);
+  } else if (recon == ORC_RECON_MUSCL3) {
+    double dm = v[2] - v[1], dp = v[3] - v[2];  // cell 0
+    wl = v[2] + limiter(ORC_LIM_MINMOD, dm, 4.0 * dp) / 6.0 + limiter(ORC_LIM_MINMOD, dp, 4.0 * dm) / 3.0;
+    dm = v[3] - v[2];  // cell 1
+    dp = v[4] - v[3];
+    wr = v[3] - limiter(ORC_LIM_MINMOD, dp, 4.0 * dm) / 6.0 - limiter(ORC_LIM_MINMOD, dm, 4.0 * dp) / 3.0;
+  } else {
+    double dm = (v[2] - v[1]) / (0.5 * (wd[1] + wd[2]));
+    double dc = (v[3] - v[2]) / (0.5 * (wd[2] + wd[3]));
+    double dp = (v[4] - v[3]) / (0.5 * (wd[3] + wd[4]));
+    wl = v[2] + 0.5 * wd[2] * limiter(lim, dm, dc);
+    wr = v[3] - 0.5 * wd[3] * limiter(lim, dc, dp);
+  }
+}
+
 void perm_for(int D, int d, int* perm) {
   if (D == 1) {
     perm[0] = 0;
@@ -674,11 +717,11 @@ void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
   const int D = G.D, nv = G.nv;
   int perm[3];
   perm_for(D, d, perm);
-  double S[4][5];  // cells j-1, j, j+1, j+2 along d (rotated)
-  double wd[4];
-  for (int s = 0; s < 4; ++s) {
+  double S[6][5];  // cells j-2 .. j+3 along d (rotated)
+  double wd[6];
+  for (int s = 0; s < 6; ++s) {
     int cc[3] = {c[0], c[1], c[2]};
-    cc[d] += s - 1;
+    cc[d] += s - 2;
     double w[5];
     get_cell(G, C.Wp, cc[0], cc[1], cc[2], w);
     rotate(D, perm, w, S[s]);
@@ -686,25 +729,33 @@ void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
   }
   std::memset(&f, 0, sizeof(f));
   for (int v = 0; v < nv; ++v) {
-    double dm = (S[1][v] - S[0][v]) / (0.5 * (wd[0] + wd[1]));
-    double dc = (S[2][v] - S[1][v]) / (0.5 * (wd[1] + wd[2]));
-    double dp = (S[3][v] - S[2][v]) / (0.5 * (wd[2] + wd[3]));
-    f.sl[v] = limiter(P->limiter, dm, dc);
-    f.sr[v] = limiter(P->limiter, dc, dp);
-    f.wl[v] = S[1][v] + 0.5 * wd[1] * f.sl[v];
-    f.wr[v] = S[2][v] - 0.5 * wd[2] * f.sr[v];
-    f.cl[v] = S[1][v];
-    f.cr[v] = S[2][v];
+    double st[6];
+    for (int s = 0; s < 6; ++s) st[s] = S[s][v];
+    recon_face(P->recon, P->limiter, st, wd, f.wl[v], f.wr[v]);
+    // normal slopes of the two cells: the one-sided difference to the face value (for MUSCL2 this
+    // is the limited slope itself)
+    if (P->recon == ORC_RECON_MUSCL2) {
+      double dm = (S[2][v] - S[1][v]) / (0.5 * (wd[1] + wd[2]));
+      double dc = (S[3][v] - S[2][v]) / (0.5 * (wd[2] + wd[3]));
+      double dp = (S[4][v] - S[3][v]) / (0.5 * (wd[3] + wd[4]));
+      f.sl[v] = limiter(P->limiter, dm, dc);
+      f.sr[v] = limiter(P->limiter, dc, dp);
+    } else {
+      f.sl[v] = (f.wl[v] - S[2][v]) / (0.5 * wd[2]);
+      f.sr[v] = (S[3][v] - f.wr[v]) / (0.5 * wd[3]);
+    }
+    f.cl[v] = S[2][v];
+    f.cr[v] = S[3][v];
   }
   // first order on a side whose reconstructed density or pressure is not positive
   if (!(f.wl[0] > 0.0) || !(pressure(D, P->gamma, f.wl) > 0.0))
     for (int v = 0; v < nv; ++v) {
-      f.wl[v] = S[1][v];
+      f.wl[v] = S[2][v];
       f.sl[v] = 0.0;
     }
   if (!(f.wr[0] > 0.0) || !(pressure(D, P->gamma, f.wr) > 0.0))
     for (int v = 0; v < nv; ++v) {
-      f.wr[v] = S[2][v];
+      f.wr[v] = S[3][v];
       f.sr[v] = 0.0;
     }
   if (P->multid) {
@@ -735,8 +786,8 @@ void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
       }
     }
   }
-  f.dxl = 0.5 * wd[1];
-  f.dxr = 0.5 * wd[2];
+  f.dxl = 0.5 * wd[2];
+  f.dxr = 0.5 * wd[3];
   int cr[3] = {c[0], c[1], c[2]};
   cr[d] += 1;
   f.tau_t = 0.5 * (C.taut[G.idx(c[0], c[1], c[2])] + C.taut[G.idx(cr[0], cr[1], cr[2])]);
@@ -1143,6 +1194,21 @@ void komega_update(const orc_problem* P, const orc_komega* K, const Grid& G, con
 }  // namespace
 
 extern "C" {
+
+int orc_reconstruct(int recon, int limiter, const double* v, const double* h, int n, double* wl, double* wr) {
+  if (n < 6) return 1;
+  for (int j = 2; j + 3 < n; ++j) {  // face between cells j and j + 1
+    double st[6], wd[6], a, b;
+    for (int s = 0; s < 6; ++s) {
+      st[s] = v[j - 2 + s];
+      wd[s] = h[j - 2 + s];
+    }
+    recon_face(recon, limiter, st, wd, a, b);
+    wl[j] = a;
+    wr[j + 1] = b;
+  }
+  return 0;
+}
 
 int orc_komega_defaults(orc_komega* c) {
   c->alpha = 13.0 / 25.0;

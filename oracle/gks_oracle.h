@@ -23,6 +23,8 @@ enum { ORC_BC_PERIODIC = 0, ORC_BC_TRANSMISSIVE = 1, ORC_BC_WALL = 2, ORC_BC_DIR
 enum { ORC_TURB_NONE = 0, ORC_TURB_MUT = 1, ORC_TURB_KEPS = 2, ORC_TURB_KOMEGA = 3 };
 enum { ORC_LIM_MINMOD = 0, ORC_LIM_VANLEER = 1 };
 enum { ORC_ABAR_TIMEINT = 0, ORC_ABAR_T0 = 1 };
+/* face reconstruction (Section 4 lists second- and third-order MUSCL and fifth-order WENO) */
+enum { ORC_RECON_MUSCL2 = 0, ORC_RECON_MUSCL3 = 1, ORC_RECON_WENO5 = 2 };
 
 typedef struct {
   int dim;
@@ -34,6 +36,7 @@ typedef struct {
   int turb_model;
   double C_mu, beta_star, C_a;
   int limiter, multid, abar_mode;
+  int recon;                    /* ORC_RECON_*; MUSCL2 uses `limiter` */
 } orc_problem;
 
 /* Per-face record, normal frame (velocity index 0 is the face normal):
@@ -71,6 +74,10 @@ int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int mul
 int orc_face_flux_compact(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
                           int printed_beta, const orc_face* f, double* F);
 int orc_euler_flux(int D, double gamma, const double* w, double* F);
+/* Face values of a 1D row of cell averages v[0..n) with widths h (the ends take the nearest
+ * cell): wl[i] = value at the right face of cell i (its own reconstruction), wr[i] = value at the
+ * left face of cell i, for the faces with a full stencil; other entries are left untouched. */
+int orc_reconstruct(int recon, int limiter, const double* v, const double* h, int n, double* wl, double* wr);
 
 int orc_prim_to_cons(const orc_problem* P, const double* prim, double* W, long ncell);
 int orc_cons_to_prim(const orc_problem* P, const double* W, double* prim, long ncell);
