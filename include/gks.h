@@ -59,6 +59,14 @@ enum { GKS_EXPAND_DIRECTIONAL = 0, GKS_EXPAND_MULTID = 1 };
 enum { GKS_FP64 = 0, GKS_FP32 = 1, GKS_FP32_ACC64 = 2 };
 /* equilibrium time slope Abar: time-integrated compatibility (default) or the t = 0 one */
 enum { GKS_ABAR_TIMEINT = 0, GKS_ABAR_T0 = 1 };
+/* face reconstruction (Section 4 lists second- and third-order MUSCL and fifth-order WENO):
+ * MUSCL2 = limited slopes over the centre distances (the default, `limiter` chooses minmod or van
+ * Leer); MUSCL3 = the kappa = 1/3 scheme with minmod compression 4; WENO5 = Jiang and Shu's
+ * fifth-order weighted reconstruction.  MUSCL3 and WENO5 work in index space on the conservative
+ * variables, take the GKS normal slopes as the one-sided differences to the face values, keep the
+ * MUSCL2 tangential slopes, and are built for GKS_FP64 and GKS_FP32 (in 3D for multi-dimensional
+ * expansion only). */
+enum { GKS_RECON_MUSCL2 = 0, GKS_RECON_MUSCL3 = 1, GKS_RECON_WENO5 = 2 };
 enum { GKS_LAYOUT_SOA_CONS = 0, GKS_LAYOUT_AOS_CONS = 1, GKS_LAYOUT_SOA_PRIM = 2 };
 enum { GKS_MEM_HOST = 0, GKS_MEM_DEVICE = 1 };
 enum { GKS_F64 = 0, GKS_F32 = 1 };
@@ -92,6 +100,7 @@ typedef struct {
   int expand;     /* GKS_EXPAND_* */
   int precision;  /* GKS_FP64 | GKS_FP32 | GKS_FP32_ACC64 */
   int abar_mode;  /* GKS_ABAR_* */
+  int reconstruction;  /* GKS_RECON_*; zero (the default) is MUSCL2 */
 } gks_numerics;
 
 /* Create a solver on the current CUDA device.  cuda_stream is a cudaStream_t or NULL (the library

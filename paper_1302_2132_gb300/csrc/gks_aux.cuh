@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ 
     pos[1] = (int)((c / g.n[0]) % g.n[1]);
     pos[2] = (int)(c / ((long)g.n[0] * g.n[1]));
     R h[D];
-    for (int d = 0; d < D; ++d) h[d] = (R)g.w[d][pos[d] + 2];
+    for (int d = 0; d < D; ++d) h[d] = (R)g.w[d][pos[d] + kWG];
     rmax = fmax(rmax, cell_rate<D, R>(w, kc.gamma, h));
   }
   const double m = block_max<double>((double)rmax, red);

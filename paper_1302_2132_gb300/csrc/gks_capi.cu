@@ -28,6 +28,7 @@ struct gks_handle {
   long ncell = 0;
   int prec = PREC_F64;
   bool multid = false;
+  int recon = 0;  // GKS_RECON_*
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   void* W[2] = {nullptr, nullptr};
@@ -124,9 +125,9 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(const __grid_constant__ 
   }
   R wx[3], wy[3], wz[3];
   for (int q = 0; q < 3; ++q) {
-    wx[q] = (R)g.w[0][i + 1 + q];
-    wy[q] = D >= 2 ? (R)g.w[1][j + 1 + q] : R(1);
-    wz[q] = D >= 3 ? (R)g.w[2][k + 1 + q] : R(1);
+    wx[q] = (R)g.w[0][i + kWG - 1 + q];
+    wy[q] = D >= 2 ? (R)g.w[1][j + kWG - 1 + q] : R(1);
+    wz[q] = D >= 3 ? (R)g.w[2][k + kWG - 1 + q] : R(1);
   }
   const int strides[3] = {1, 3, 9};
   const R* widths[3] = {wx, wy, wz};
@@ -177,6 +178,14 @@ int tiles_for(const gks_handle* h, int variant) {
 }
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
+  if (h->recon == GKS_RECON_MUSCL3) {
+    launch_step_muscl3(h->D, h->prec, h->multid, A, tiles_for(h, 0), h->stream);
+    return;
+  }
+  if (h->recon == GKS_RECON_WENO5) {
+    launch_step_weno5(h->D, h->prec, h->multid, A, tiles_for(h, 0), h->stream);
+    return;
+  }
   if (h->D == 1 && variant > 0)
     launch_step_d1_variant(variant, h->prec, A, tiles_for(h, variant), h->stream);
   else if (h->D == 1)
@@ -345,6 +354,7 @@ std::map<TuneKey, int> g_tuned;
 std::mutex g_tuned_mutex;
 
 int n_variants(const gks_handle* h) {
+  if (h->recon != GKS_RECON_MUSCL2) return 1;  // higher-order reconstructions: default tiles only
   if (h->D == 1) return kTileVariants1D;
   if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
   if (h->D == 3 && h->prec == PREC_F32) return kTileVariants3D;
@@ -455,6 +465,12 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     if (!(gas->T_wall > 0.0)) return bad(GKS_EINVAL, "T_wall must be positive with wall boundaries");
   h->prec = num->precision;
   h->multid = D > 1 && num->expand == GKS_EXPAND_MULTID;
+  h->recon = num->reconstruction;
+  if (h->recon < GKS_RECON_MUSCL2 || h->recon > GKS_RECON_WENO5) return bad(GKS_EINVAL, "reconstruction");
+  if (h->recon != GKS_RECON_MUSCL2 && (h->prec == PREC_F32D || (D == 3 && !h->multid)))
+    return bad(GKS_EUNSUPPORTED, "higher-order reconstruction needs GKS_FP64 or GKS_FP32 (and multi-D in 3D)");
+  for (int d = 0; d < D; ++d)
+    if (h->recon == GKS_RECON_WENO5 && h->n[d] < 3) return bad(GKS_EINVAL, "WENO5 needs at least 3 cells per axis");
 
   if (cudaGetDevice(&h->dev) != cudaSuccess) {
     cudaGetLastError();
@@ -476,6 +492,8 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess) e = prepare_komega();
+    if (e == cudaSuccess) e = prepare_step_muscl3();
+    if (e == cudaSuccess) e = prepare_step_weno5();
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bad(GKS_ECUDA, "kernel attribute setup failed");
@@ -517,21 +535,22 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     cudaMemset(h->f1, 0, fb);
     cudaMemset(h->f2, 0, fb);
   }
-  // widths with two ghosts per side: periodic axes wrap, other axes mirror
+  // widths with kWG ghosts per side: periodic axes wrap, other axes mirror
   for (int d = 0; d < 3; ++d) {
     const int n = d < D ? h->n[d] : 1;
-    std::vector<double> w(n + 4, 1.0), in(n, 1.0);
+    std::vector<double> w(n + 2 * kWG, 1.0), in(n, 1.0);
     if (d < D) {
       for (int i = 0; i < n; ++i) in[i] = grid->dx[d] ? grid->dx[d][i] : (grid->hi[d] - grid->lo[d]) / n;
       const bool per = grid->bc[d][0] == GKS_BC_PERIODIC;
-      for (int i = 0; i < n; ++i) w[i + 2] = in[i];
-      for (int gi = 1; gi <= 2; ++gi) {
-        w[2 - gi] = per ? in[n - gi] : in[gi - 1];
-        w[n + 1 + gi] = per ? in[gi - 1] : in[n - gi];
+      for (int i = 0; i < n; ++i) w[i + kWG] = in[i];
+      for (int gi = 1; gi <= kWG; ++gi) {
+        w[kWG - gi] = per ? in[(n - gi % n) % n] : in[std::min(gi - 1, n - 1)];
+        w[n + kWG - 1 + gi] = per ? in[(gi - 1) % n] : in[std::max(n - gi, 0)];
       }
     }
-    if (!alloc((void**)&h->widths[d], sizeof(double) * (n + 4))) return bad(GKS_ENOMEM, "width allocation failed");
-    cudaMemcpy(h->widths[d], w.data(), sizeof(double) * (n + 4), cudaMemcpyHostToDevice);
+    const size_t wb = sizeof(double) * (n + 2 * kWG);
+    if (!alloc((void**)&h->widths[d], wb)) return bad(GKS_ENOMEM, "width allocation failed");
+    cudaMemcpy(h->widths[d], w.data(), wb, cudaMemcpyHostToDevice);
   }
   // Dirichlet states, converted to conservative variables
   for (int d = 0; d < D; ++d)

@@ -106,14 +106,14 @@ __global__ void __launch_bounds__(256) komega_kernel(const __grid_constant__ KOm
     sw[l] = RW[m] * irm;
   }
   for (int l = tid; l < G::NW; l += 256) {
-    // halo position p of axis a is the cell origin + p - 2 (width index origin + p, two ghosts)
+    // halo position p of axis a is the cell origin + p - 2 (width index that cell + kWG)
     const int a = l < HX ? 0 : (l < HX + HY ? 1 : 2);
     const int p = l - woff[a];
     if (a < D) {
-      const int top = g.n[a] + 3;
-      const R wm = (R)g.w[a][min(max(org[a] + p - 1, 0), top)];
-      const R w0 = (R)g.w[a][min(org[a] + p, top)];
-      const R wp = (R)g.w[a][min(org[a] + p + 1, top)];
+      const int top = g.n[a] + 2 * kWG - 1, iw = org[a] + p - 2 + kWG;
+      const R wm = (R)g.w[a][min(max(iw - 1, 0), top)];
+      const R w0 = (R)g.w[a][min(max(iw, 0), top)];
+      const R wp = (R)g.w[a][min(max(iw + 1, 0), top)];
       swid[l] = w0;
       sic[l] = g_rcp(R(0.5) * (wm + w0));
       sig_[l] = g_rcp(R(0.5) * wm + w0 + R(0.5) * wp);

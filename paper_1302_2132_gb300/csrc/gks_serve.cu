@@ -148,7 +148,7 @@ size_t state_bytes(int prec, int nv, long ncell) {
 size_t footprint(int prec, const Req& r) {
   const int nv = r.q.dim + 2;
   size_t b = round_up(state_bytes(prec, nv, r.ncell));
-  for (int d = 0; d < r.q.dim; ++d) b += round_up(sizeof(double) * (r.q.n[d] + 4));
+  for (int d = 0; d < r.q.dim; ++d) b += round_up(sizeof(double) * (r.q.n[d] + 2 * kWG));
   return b + round_up(sizeof(Ctrl));
 }
 
@@ -180,13 +180,14 @@ bool admit(gks_server* s, Req* r) {
   double* widths[3] = {nullptr, nullptr, nullptr};
   for (int d = 0; d < D; ++d) {
     const int n = q.n[d];
-    std::vector<double> w(n + 4);
+    std::vector<double> w(n + 2 * kWG);
     const double h = (q.hi[d] - q.lo[d]) / n;
-    for (int i = 0; i < n + 4; ++i) w[i] = h;  // uniform cells: ghosts equal too
+    for (int i = 0; i < n + 2 * kWG; ++i) w[i] = h;  // uniform cells: ghosts equal too
     widths[d] = (double*)p;
-    if (cudaMemcpyAsync(widths[d], w.data(), sizeof(double) * (n + 4), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(widths[d], w.data(), sizeof(double) * (n + 2 * kWG), cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
       return false;
-    p += round_up(sizeof(double) * (n + 4));
+    p += round_up(sizeof(double) * (n + 2 * kWG));
   }
   Ctrl* ctrl = (Ctrl*)p;
   // initial state: pinned staging -> device staging -> stored form in buffer (step mod 2)

@@ -25,6 +25,11 @@ enum { PREC_F64 = 0,    // double flux, double state
        PREC_F32D = 2 };  // float flux, double state
 
 constexpr int kThreads = 256;   // threads of the auxiliary kernels and of tile variant 0
+constexpr int kWG = 3;          // ghost entries per side of the cell-width arrays (index cell + kWG)
+// face reconstruction: second-order MUSCL (limited slopes), third-order MUSCL (kappa = 1/3),
+// fifth-order WENO (three halo layers)
+enum { RECON_MUSCL2 = 0, RECON_MUSCL3 = 1, RECON_WENO5 = 2 };
+__host__ __device__ constexpr int halo_of(int recon) { return recon == RECON_WENO5 ? 3 : 2; }
 constexpr int kMaxWarps = 16;   // largest CTA of any tile variant: 512 threads
 
 // Tile of cells owned by one CTA (variant 0 is the default; 2D has four more, chosen by the
@@ -50,9 +55,10 @@ template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 2
 template <> struct Tile<3, 1> { static constexpr int X = 16, Y = 8, Z = 2, T = 256; };
 template <> struct Tile<3, 2> { static constexpr int X = 8, Y = 8, Z = 4, T = 256; };
 
-template <int D, int V = 0> struct TileGeom {
+template <int D, int V = 0, int H = 2> struct TileGeom {
   static constexpr int X = Tile<D, V>::X, Y = Tile<D, V>::Y, Z = Tile<D, V>::Z, T = Tile<D, V>::T;
-  static constexpr int HX = X + 4, HY = D >= 2 ? Y + 4 : 1, HZ = D >= 3 ? Z + 4 : 1;
+  static constexpr int HALO = H;  // halo layers staged around the tile
+  static constexpr int HX = X + 2 * H, HY = D >= 2 ? Y + 2 * H : 1, HZ = D >= 3 ? Z + 2 * H : 1;
   static constexpr int NH = HX * HY * HZ;  // cells with halo
   static constexpr int RX = X + 2, RY = D >= 2 ? Y + 2 : 1, RZ = D >= 3 ? Z + 2 : 1;
   static constexpr int NR = RX * RY * RZ;  // cells with the first halo ring
@@ -92,7 +98,7 @@ struct DevGrid {
   int n[3];
   long ncell;
   int bc[3][2];
-  const double* w[3];       // cell widths with two ghosts per side, index i + 2
+  const double* w[3];       // cell widths with kWG ghosts per side, index i + kWG
   const double* dir[3][2];  // Dirichlet conservative states, [transverse cell][nv]
   double gamma, bK, K, mu, C_a, T_wall, C_mu, beta_star;
   int turb_model, limiter, abar_t0;
@@ -202,6 +208,42 @@ __device__ __forceinline__ R pressure_of(int D, R gamma, const R* w) {
   return (gamma - R(1)) * (w[D + 1] - R(0.5) * g_div(q, w[0]));
 }
 
+// Higher-order face values in index space (Section 4 lists third-order MUSCL and fifth-order
+// WENO beside the second-order default).  muscl3_right(a, b, c) is cell b's value at its right face
+// from cells a, b, c; muscl3_left(a, b, c) cell b's value at its left face: the kappa = 1/3 scheme
+// with each one-sided difference limited by minmod against 4 times the other.
+template <class R>
+__device__ __forceinline__ R muscl3_right(R a, R b, R c) {
+  const R dm = b - a, dp = c - b;
+  return b + limiter<R>(LIM_MINMOD, dm, R(4) * dp) * R(1.0 / 6.0) + limiter<R>(LIM_MINMOD, dp, R(4) * dm) * R(1.0 / 3.0);
+}
+template <class R>
+__device__ __forceinline__ R muscl3_left(R a, R b, R c) {
+  const R dm = b - a, dp = c - b;
+  return b - limiter<R>(LIM_MINMOD, dp, R(4) * dm) * R(1.0 / 6.0) - limiter<R>(LIM_MINMOD, dm, R(4) * dp) * R(1.0 / 3.0);
+}
+// Jiang and Shu's WENO-5: the value at the face to the right of c from cells a, b, c, d, e
+// (candidate stencils' face values, smoothness indicators with 13/12 and 1/4, linear weights
+// 1/10, 6/10, 3/10, epsilon 1e-6).
+template <class R>
+__device__ __forceinline__ R weno5(R a, R b, R c, R d, R e) {
+  const R s6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0);
+  const R q0 = (R(2) * a - R(7) * b + R(11) * c) * s6;
+  const R q1 = (-b + R(5) * c + R(2) * d) * s6;
+  const R q2 = (R(2) * c + R(5) * d - e) * s6;
+  const R t0 = a - R(2) * b + c, u0 = a - R(4) * b + R(3) * c;
+  const R t1 = b - R(2) * c + d, u1 = b - d;
+  const R t2 = c - R(2) * d + e, u2 = R(3) * c - R(4) * d + e;
+  const R b0 = c13 * t0 * t0 + R(0.25) * u0 * u0;
+  const R b1 = c13 * t1 * t1 + R(0.25) * u1 * u1;
+  const R b2 = c13 * t2 * t2 + R(0.25) * u2 * u2;
+  const R eps = R(1e-6);
+  const R a0 = g_div(R(0.1), (eps + b0) * (eps + b0));
+  const R a1 = g_div(R(0.6), (eps + b1) * (eps + b1));
+  const R a2 = g_div(R(0.3), (eps + b2) * (eps + b2));
+  return g_div(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
 // rho > 0 and p > 0 for a conservative state.  Single precision tests 2 rho (rho E) > |rho U|^2 (the
 // same condition once rho > 0, without a quotient); double precision evaluates p as the oracle does.
 template <int D, class R>
@@ -253,9 +295,9 @@ __device__ void load_cell(const DevGrid& g, const void* Win, const Consts<typena
   using R = typename PrecT<PREC>::R;
   int c[3] = {i, j, k}, xf[3] = {0, 0, 0}, side[3] = {0, 0, 0};
   bool inside = true;
-  // cells further out than the two ghost layers only feed faces of cells outside the grid
+  // cells further out than the three ghost layers only feed faces of cells outside the grid
 #pragma unroll
-  for (int a = 0; a < D; ++a) c[a] = min(max(c[a], -2), g.n[a] + 1);
+  for (int a = 0; a < D; ++a) c[a] = min(max(c[a], -3), g.n[a] + 2);
   int src[3] = {c[0], c[1], c[2]};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -516,7 +558,7 @@ __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
 // evaluates its ring cells tid + q T side by side, results in registers and stored afterwards, so
 // that their shared-memory and MUFU latencies overlap.  A slot past the ring repeats the last cell
 // and is not stored.  The model and limiter branches are taken once, outside the cells.
-template <int D, int PREC, int V>
+template <int D, int PREC, int V, int H>
 __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc, int turb_model, bool cons, int lim,
                                         const typename PrecT<PREC>::R* Ws, const typename PrecT<PREC>::R* Fl,
                                         typename PrecT<PREC>::R* taus, typename PrecT<PREC>::R* Ss,
@@ -524,7 +566,7 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
                                         const typename PrecT<PREC>::R* icz, const typename PrecT<PREC>::R* igx,
                                         const typename PrecT<PREC>::R* igy, const typename PrecT<PREC>::R* igz) {
   using R = typename PrecT<PREC>::R;
-  using G = TileGeom<D, V>;
+  using G = TileGeom<D, V, H>;
   constexpr int kThreads = G::T, nv = D + 2, HX = G::HX, HY = G::HY;
   constexpr bool PRE = pre_slopes<D, PREC, V>();
   const int tid = threadIdx.x;
@@ -546,7 +588,7 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
       for (int q = 0; q < GRP; ++q) {
         const int l = min(tid + (i0 + q) * kThreads, G::NR - 1);
         const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
-        const int hi = ri + 1, hj = D >= 2 ? rj + 1 : 0, hk = D >= 3 ? rk + 1 : 0;
+        const int hi = ri + H - 1, hj = D >= 2 ? rj + H - 1 : 0, hk = D >= 3 ? rk + H - 1 : 0;
         const int idx = (hk * HY + hj) * HX + hi;
         const int pos[3] = {hi, hj, hk};
         if constexpr (TWO_EQ)
@@ -594,11 +636,12 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
 }
 
 // One tile of one step: every thread of the CTA calls it with the same arguments.
-template <int D, int PREC, bool MULTID, int V = 0>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
 __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
-  using G = TileGeom<D, V>;
+  constexpr int H = halo_of(RECON);
+  using G = TileGeom<D, V, H>;
   constexpr int kThreads = G::T;
   constexpr int nv = D + 2;
   constexpr int X = G::X, Y = G::Y, Z = G::Z, HX = G::HX, HY = G::HY, HZ = G::HZ;
@@ -637,7 +680,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   // In-grid cells are copied asynchronously; ghost cells are resolved by the boundary rules.
   for (int l = tid; l < G::NH; l += kThreads) {
     const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
-    const int gi = ox + hi - 2, gj = D >= 2 ? oy + hj - 2 : 0, gk = D >= 3 ? oz + hk - 2 : 0;
+    const int gi = ox + hi - H, gj = D >= 2 ? oy + hj - H : 0, gk = D >= 3 ? oz + hk - H : 0;
     if (ASYNC && in_grid(g, D, gi, gj, gk)) {
       const S* src = (const S*)A.Win + cell_index(g, gi, gj, gk);
 #pragma unroll
@@ -685,18 +728,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     }
   }
   for (int l = tid; l < HX + HY + HZ; l += kThreads) {
-    // padded width index (cell + 2), clamped to the two ghost layers; the inverse distances make
-    // the slope and gradient quotients products
+    // halo position p is the cell origin + p - H, width index cell + kWG (clamped to the ghosts);
+    // the inverse distances make the slope and gradient quotients products
     const int a = l < HX ? 0 : (l < HX + HY ? 1 : 2);
     const int p = a == 0 ? l : (a == 1 ? l - HX : l - HX - HY);
     R* wd = a == 0 ? wsx : (a == 1 ? wsy : wsz);
     R* ic = a == 0 ? icx : (a == 1 ? icy : icz);
     R* ig = a == 0 ? igx : (a == 1 ? igy : igz);
     if (a < D) {
-      const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 3;
-      const R wm = (R)g.w[a][min(max(o + p - 1, 0), top)];
-      const R w0 = (R)g.w[a][min(o + p, top)];
-      const R wp = (R)g.w[a][min(o + p + 1, top)];
+      const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 2 * kWG - 1;
+      const int iw = o + p - H + kWG;
+      const R wm = (R)g.w[a][min(max(iw - 1, 0), top)];
+      const R w0 = (R)g.w[a][min(max(iw, 0), top)];
+      const R wp = (R)g.w[a][min(max(iw + 1, 0), top)];
       wd[p] = w0;
       ic[p] = g_rcp(R(0.5) * (wm + w0));
       ig[p] = g_rcp(R(0.5) * wm + w0 + R(0.5) * wp);
@@ -736,7 +780,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   const R dt = (R)dt_d;
 
   // ---- turbulent relaxation time and limited slopes on the tile and its first halo ring -------
-  ring_phase<D, PREC, V>(kc, g.turb_model, g.turb_cons != 0, g.limiter, Ws, Fl, taus, Ss, icx, icy, icz, igx, igy,
+  ring_phase<D, PREC, V, H>(kc, g.turb_model, g.turb_cons != 0, g.limiter, Ws, Fl, taus, Ss, icx, icy, icz, igx, igy,
                          igz);
   __syncthreads();
 
@@ -776,7 +820,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         }
         const int st[3] = {1, HX, HX * HY};
         const int sn = st[ax];
-        const int hc = ((ck + (D >= 3 ? 2 : 0)) * HY + (cj + (D >= 2 ? 2 : 0))) * HX + (ci + 2);
+        const int hc = ((ck + (D >= 3 ? H : 0)) * HY + (cj + (D >= 2 ? H : 0))) * HX + (ci + H);
         // velocity order in the face frame: normal first, then tangential axes
         int perm[3];
         perm[0] = ax;
@@ -786,8 +830,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           perm[2] = ax == 2 ? 1 : 2;
         }
         const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
-        const int pn = ax == 0 ? ci + 2 : (ax == 1 ? cj + 2 : ck + 2);  // halo coordinate of cell c
+        const int pn = ax == 0 ? ci + H : (ax == 1 ? cj + H : ck + H);  // halo coordinate of cell c
         const R h1 = wn[pn - 1], h2 = wn[pn];
+        R i2h1 = R(0), i2h2 = R(0);  // 2 / width of the two cells (higher-order slopes)
+        if constexpr (RECON != RECON_MUSCL2) {
+          i2h1 = g_rcp(R(0.5) * h1);
+          i2h2 = g_rcp(R(0.5) * h2);
+        }
         const R* icn = ax == 0 ? icx : (ax == 1 ? icy : icz);
         (void)icn;
         // ring indices of the two cells
@@ -800,7 +849,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
           const R* p = Ws + sv * G::NH + hc;
           const R s1 = p[-sn], s2 = p[0];
-          if (PRE) {
+          if constexpr (RECON != RECON_MUSCL2) {
+            // higher-order face values from the normal stencil (cells pn-3 .. pn+2); the normal
+            // slopes are the one-sided differences to them
+            if constexpr (RECON == RECON_WENO5) {
+              wl[v] = weno5<R>(p[-3 * sn], p[-2 * sn], s1, s2, p[sn]);
+              wr[v] = weno5<R>(p[2 * sn], p[sn], s2, s1, p[-2 * sn]);
+            } else {
+              wl[v] = muscl3_right<R>(p[-2 * sn], s1, s2);
+              wr[v] = muscl3_left<R>(s1, s2, p[sn]);
+            }
+            sl[v] = (wl[v] - s1) * i2h1;
+            sr[v] = (s2 - wr[v]) * i2h2;
+          } else if (PRE) {
             sl[v] = Ss[(ax * nv + sv) * G::NR + rl];
             sr[v] = Ss[(ax * nv + sv) * G::NR + rc];
             wl[v] = s1 + R(0.5) * h1 * sl[v];
@@ -848,7 +909,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
             const int ta = perm[1 + s];
             const int stt = st[ta];
             const R* ict = ta == 0 ? icx : (ta == 1 ? icy : icz);
-            const int hcell[3] = {ci + 2, cj + (D >= 2 ? 2 : 0), ck + (D >= 3 ? 2 : 0)};
+            const int hcell[3] = {ci + H, cj + (D >= 2 ? H : 0), ck + (D >= 3 ? H : 0)};
             const int pt = hcell[ta];
             const R im = ict[pt], ip = ict[pt + 1];
 #pragma unroll
@@ -902,16 +963,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     R h[3];
     fm[0] = (lk * Y + lj) * (X + 1) + li;
     fp[0] = fm[0] + 1;
-    h[0] = wsx[li + 2];
+    h[0] = wsx[li + H];
     if (D >= 2) {
       fm[1] = G::NFX + (lk * (Y + 1) + lj) * X + li;
       fp[1] = fm[1] + X;
-      h[1] = wsy[lj + 2];
+      h[1] = wsy[lj + H];
     }
     if (D >= 3) {
       fm[2] = G::NFX + G::NFY + (lk * Y + lj) * X + li;
       fp[2] = fm[2] + X * Y;
-      h[2] = wsz[lk + 2];
+      h[2] = wsz[lk + H];
     }
     R ih[3];
 #pragma unroll
@@ -920,10 +981,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     double vol = 1.0;
     if (A.resid) {  // cell volume from the double-precision widths
       const int gc[3] = {gi, gj, gk};
-      for (int d = 0; d < D; ++d) vol *= g.w[d][gc[d] + 2];
+      for (int d = 0; d < D; ++d) vol *= g.w[d][gc[d] + kWG];
     }
     // the cell's old state: staged in shared memory (FP64, float pair), else read from the grid
-    const int hidx = ((lk + (D >= 3 ? 2 : 0)) * HY + (lj + (D >= 2 ? 2 : 0))) * HX + (li + 2);
+    const int hidx = ((lk + (D >= 3 ? H : 0)) * HY + (lj + (D >= 2 ? H : 0))) * HX + (li + H);
 #pragma unroll
     for (int v = 0; v < nv; ++v) {
       const long gidx = (long)v * g.ncell + c;
@@ -995,10 +1056,10 @@ template <int D, int V = 0> constexpr int min_blocks(int prec) {
   return prec != PREC_F64 ? 512 / Tile<D, V>::T : 1;
 }
 
-template <int D, int PREC, bool MULTID, int V = 0>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
 __global__ void __launch_bounds__(Tile<D, V>::T, min_blocks<D, V>(PREC))
     step_kernel(const __grid_constant__ StepArgs A) {
-  step_tile<D, PREC, MULTID, V>(A, blockIdx.x);
+  step_tile<D, PREC, MULTID, V, RECON>(A, blockIdx.x);
 }
 
 // ---- batches of independent solves --------------------------------------------------------------
@@ -1051,18 +1112,20 @@ cudaError_t prepare_batch() {
                               (int)sm);
 }
 
-template <int D, int PREC, bool MULTID, int V = 0>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
 void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
-  step_kernel<D, PREC, MULTID, V><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
+  const size_t sm =
+      TileGeom<D, V, halo_of(RECON)>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
+  step_kernel<D, PREC, MULTID, V, RECON><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
 }
 
-template <int D, int PREC, bool MULTID, int V = 0>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
 cudaError_t prepare_step() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
-  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t sm =
+      TileGeom<D, V, halo_of(RECON)>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
+  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V, RECON>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sm);
 }
 

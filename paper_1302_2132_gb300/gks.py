@@ -20,6 +20,7 @@ LIMITER = {"minmod": 0, "vanleer": 1}
 EXPAND = {"directional": 0, "multid": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
 ABAR = {"timeint": 0, "t0": 1}
+RECON = {"muscl2": 0, "muscl3": 1, "weno5": 2}
 LAYOUT = {"soa_cons": 0, "aos_cons": 1, "soa_prim": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
 F64, F32 = 0, 1
@@ -50,7 +51,7 @@ class _Turb(ctypes.Structure):
 
 
 class _Num(ctypes.Structure):
-    _fields_ = [("limiter", _I), ("expand", _I), ("precision", _I), ("abar_mode", _I)]
+    _fields_ = [("limiter", _I), ("expand", _I), ("precision", _I), ("abar_mode", _I), ("reconstruction", _I)]
 
 
 _lib = None
@@ -137,7 +138,7 @@ class Solver:
 
     def __init__(self, dim, n, bc, dx=None, lo=None, hi=None, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0,
                  turb_model="none", C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", expand="multid",
-                 precision="fp64", abar_mode="timeint", stream=None):
+                 precision="fp64", abar_mode="timeint", reconstruction="muscl2", stream=None):
         import torch
         L = load()
         self.dim, self.nv = dim, dim + 2
@@ -168,7 +169,8 @@ class Solver:
         num = _Num(LIMITER[limiter] if isinstance(limiter, str) else int(limiter),
                    EXPAND[expand] if isinstance(expand, str) else int(expand),
                    PRECISION[precision] if isinstance(precision, str) else int(precision),
-                   ABAR[abar_mode] if isinstance(abar_mode, str) else int(abar_mode))
+                   ABAR[abar_mode] if isinstance(abar_mode, str) else int(abar_mode),
+                   RECON[reconstruction] if isinstance(reconstruction, str) else int(reconstruction))
         self.precision = num.precision
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = _V()

@@ -7,21 +7,21 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
 
 
 def oracle_case(spec, turb_model=0, limiter=1, multid=1, abar_mode=0, gamma=1.4, mu=1e-5, C_a=0.0,
-                C_mu=0.09, beta_star=0.09, T_wall=None):
+                C_mu=0.09, beta_star=0.09, T_wall=None, recon=0):
     return oracle.Case(spec["dim"], spec["n"], spec["dx"], spec["bc"], gamma=gamma, mu=mu,
                        T_wall=spec.get("T_wall", 1.0) if T_wall is None else T_wall, turb_model=turb_model,
                        C_mu=C_mu, beta_star=beta_star, C_a=C_a, limiter=limiter, multid=multid,
-                       abar_mode=abar_mode, bc_prim=spec.get("bc_prim"))
+                       abar_mode=abar_mode, bc_prim=spec.get("bc_prim"), recon=recon)
 
 
 def gpu_solver(spec, turb_model=0, limiter=1, multid=1, abar_mode=0, gamma=1.4, mu=1e-5, C_a=0.0, C_mu=0.09,
-               beta_star=0.09, precision="fp64", T_wall=None):
+               beta_star=0.09, precision="fp64", T_wall=None, recon=0):
     from paper_1302_2132_gb300 import gks
     return gks.Solver(spec["dim"], spec["n"], spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"), gamma=gamma,
                       mu=mu, T_wall=spec.get("T_wall", 1.0) if T_wall is None else T_wall, turb_model=turb_model,
                       C_mu=C_mu, beta_star=beta_star, C_a=C_a, limiter=limiter,
                       expand="multid" if multid else "directional", precision=precision,
-                      abar_mode="t0" if abar_mode else "timeint")
+                      abar_mode="t0" if abar_mode else "timeint", reconstruction=int(recon))
 
 
 def rel_err_per_var(a, b, nv):
