@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--precision", default=None, choices=["fp32", "fp32_acc64", "fp64"])
     p.add_argument("--workload", default="turb2d_1024",
                    choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256"])
+    p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
+                   help="face reconstruction (the default is the second-order MUSCL the metric is quoted on)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--serving", action="store_true", help="measure the serving form only")
@@ -205,7 +207,7 @@ def run_ours(args):
     faces_per_step = faces_of(n)
     cells = int(np.prod(n))
     solver = gks.Solver(D, n, spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"), precision=wl["precision"],
-                        **wl["kw"])
+                        reconstruction=args.reconstruction, **wl["kw"])
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
     turb = wl["kw"].get("turb_model", "none") != "none"
     transport = wl.get("transport", False)
@@ -301,8 +303,8 @@ def run_ours(args):
     value = faces_per_step * nsteps * args.steps * world / secs
     # roofline of the fused step kernel (ALU bound): algorithmic operations per launch
     multid = wl["kw"].get("expand") == "multid" and D > 1
-    counts = gks.face_op_count(D, multid, True)
-    per_face = sum(counts[:3])
+    counts = gks.face_op_count(D, multid, args.reconstruction == "muscl2")
+    per_face = sum(counts[:3]) + sum(gks.recon_op_count(D, args.reconstruction)[:3])
     per_cell = CELL_OPS + sum(gks.cell_op_count(D)[:3]) + (KOMEGA_CELL_OPS[D] if transport else 0)
     ops_per_launch = faces_per_step * per_face + cells * per_cell
     avg_launch_s = kms / 1e3 / max(klaunch, 1)
@@ -312,6 +314,8 @@ def run_ours(args):
     peak = 152 * lanes * 2 * 2.070e9 / 1e12
     workload_name = (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32"
                      else "%s_%s" % (args.workload, wl["precision"]))
+    if args.reconstruction != "muscl2":
+        workload_name += "_" + args.reconstruction
     tile = solver.tile_shape()
     tile_info = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
     line = {
@@ -329,7 +333,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": workload_name,
                    "description": wl["desc"], "grid": list(n), "time_steps_per_bench_step": nsteps, "cfl": CFL,
-                   "expand": "multid" if multid else "directional",
+                   "expand": "multid" if multid else "directional", "reconstruction": args.reconstruction,
                    "precision": wl["precision"], "state_accumulation": {"fp32": "float pair (hi+lo)",
                                                                         "fp32_acc64": "IEEE double",
                                                                         "fp64": "IEEE double"}[wl["precision"]],

@@ -218,6 +218,10 @@ int gks_face_op_count(int dim, int expand, int with_recon, long long* counts);
 /* The same count for the per-cell part of the reconstruction: the limited (van Leer) slope of every
  * variable along every axis, computed once per cell and step. */
 int gks_cell_op_count(int dim, long long* counts);
+/* The same count for the face values of a higher-order reconstruction (recon = GKS_RECON_MUSCL3 or
+ * GKS_RECON_WENO5): both sides, every variable, and the two one-sided normal slopes of a face.
+ * Returns nonzero for other values. */
+int gks_recon_op_count(int dim, int recon, long long* counts);
 
 /* CFL time step, as gks_compute_dt computes it, of a caller-held FP64 state on a uniform grid, for
  * callers that cannot allocate device memory (for example while another allocator holds all of

@@ -179,11 +179,11 @@ int tiles_for(const gks_handle* h, int variant) {
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
   if (h->recon == GKS_RECON_MUSCL3) {
-    launch_step_muscl3(h->D, h->prec, h->multid, A, tiles_for(h, 0), h->stream);
+    launch_step_muscl3(h->D, h->prec, h->multid, variant, A, tiles_for(h, variant), h->stream);
     return;
   }
   if (h->recon == GKS_RECON_WENO5) {
-    launch_step_weno5(h->D, h->prec, h->multid, A, tiles_for(h, 0), h->stream);
+    launch_step_weno5(h->D, h->prec, h->multid, variant, A, tiles_for(h, variant), h->stream);
     return;
   }
   if (h->D == 1 && variant > 0)
@@ -353,8 +353,23 @@ struct TuneKey {
 std::map<TuneKey, int> g_tuned;
 std::mutex g_tuned_mutex;
 
+// Tile variants the autotuner tries for a handle (variant indices of tile_shape).
+std::vector<int> tile_candidates(const gks_handle* h) {
+  std::vector<int> c;
+  if (h->recon != GKS_RECON_MUSCL2) {
+    c.push_back(0);
+    if (h->D == 2 && h->prec == PREC_F32 && h->multid) c.push_back(3);  // 32 x 27 (four full waves at 1024^2)
+    return c;
+  }
+  const int n = h->D == 1 ? kTileVariants1D
+                          : (h->D == 2 && h->prec == PREC_F32 ? kTileVariants2D
+                                                               : (h->D == 3 && h->prec == PREC_F32 ? kTileVariants3D : 1));
+  for (int v = 0; v < n; ++v) c.push_back(v);
+  return c;
+}
+
 int n_variants(const gks_handle* h) {
-  if (h->recon != GKS_RECON_MUSCL2) return 1;  // higher-order reconstructions: default tiles only
+  if (h->recon != GKS_RECON_MUSCL2) return (int)tile_candidates(h).size();
   if (h->D == 1) return kTileVariants1D;
   if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
   if (h->D == 3 && h->prec == PREC_F32) return kTileVariants3D;
@@ -368,7 +383,8 @@ gks_status autotune(gks_handle* h) {
   const char* force = std::getenv("GKS_TILE_VARIANT");
   if (force) {
     const int v = std::atoi(force);
-    if (v >= 0 && v < nvar) h->tile_variant = v;
+    for (int c : tile_candidates(h))
+      if (c == v) h->tile_variant = v;
     return GKS_OK;
   }
   const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, (int)h->multid};
@@ -386,7 +402,7 @@ gks_status autotune(gks_handle* h) {
   const StepArgs A = step_args(h, h->step, 0);
   float best = 1e30f;
   int best_v = 0;
-  for (int v = 0; v < nvar; ++v) {
+  for (int v : tile_candidates(h)) {
     launch_step_variant(h, A, v);  // warm-up
     GKS_CK(h, cudaEventRecord(e0, h->stream));
     for (int r = 0; r < 3; ++r) launch_step_variant(h, A, v);

@@ -138,7 +138,51 @@ static void count_cell(Ops* out) {
   *out = g_ops;
 }
 
+// Per face of a higher-order reconstruction: the face values of both sides for every variable
+// (recon 1: third-order MUSCL, 2: fifth-order WENO) and the two one-sided normal slopes.
+template <int D>
+static void count_recon(int recon, Ops* out) {
+  constexpr int nv = D + 2;
+  g_ops = Ops{0, 0, 0, 0, 0, 0};
+  const Cnt i2h = Cnt::run(200.0);
+  for (int v = 0; v < nv; ++v) {
+    const Cnt a = Cnt::run(1.0), b = Cnt::run(1.1), c = Cnt::run(1.3), d = Cnt::run(1.4), e = Cnt::run(1.6),
+              f = Cnt::run(1.65);
+    Cnt wl, wr;
+    if (recon == 2) {
+      wl = weno5<Cnt>(a, b, c, d, e);
+      wr = weno5<Cnt>(f, e, d, c, b);
+    } else {
+      wl = muscl3_right<Cnt>(b, c, d);
+      wr = muscl3_left<Cnt>(c, d, e);
+    }
+    (void)((wl - c) * i2h);
+    (void)((d - wr) * i2h);
+  }
+  *out = g_ops;
+}
+
 }  // namespace gks
+
+extern "C" int gks_recon_op_count(int dim, int recon, long long* counts) {
+  gks::Ops o{0, 0, 0, 0, 0, 0};
+  if (recon != 1 && recon != 2) return 1;
+  if (dim == 1)
+    gks::count_recon<1>(recon, &o);
+  else if (dim == 2)
+    gks::count_recon<2>(recon, &o);
+  else if (dim == 3)
+    gks::count_recon<3>(recon, &o);
+  else
+    return 1;
+  counts[0] = o.add;
+  counts[1] = o.mul;
+  counts[2] = o.div;
+  counts[3] = o.sqrt;
+  counts[4] = o.exp;
+  counts[5] = o.erfc;
+  return 0;
+}
 
 extern "C" int gks_cell_op_count(int dim, long long* counts) {
   gks::Ops o{0, 0, 0, 0, 0, 0};

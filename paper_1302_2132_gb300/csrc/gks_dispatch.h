@@ -38,12 +38,12 @@ cudaError_t prepare_batch_d2();
 void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
 void launch_batch_d2(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s);
 
-// higher-order reconstructions (default tiles; FP64 and FP32; 3D multi-dimensional only): false if
-// the combination is not built
+// higher-order reconstructions (default tiles, and the 32 x 27 tile for 2D FP32 multi-D; FP64 and
+// FP32; 3D multi-dimensional only): false if the combination is not built
 cudaError_t prepare_step_muscl3();
 cudaError_t prepare_step_weno5();
-bool launch_step_muscl3(int D, int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
-bool launch_step_weno5(int D, int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
+bool launch_step_muscl3(int D, int prec, bool multid, int variant, const StepArgs& A, int nblocks, cudaStream_t s);
+bool launch_step_weno5(int D, int prec, bool multid, int variant, const StepArgs& A, int nblocks, cudaStream_t s);
 
 // k-omega transport step after a flow step (gks_komega.cu)
 cudaError_t prepare_komega();

@@ -313,6 +313,42 @@ GKS_FN R limiter(int lim, R a, R b) {
   return (a * b > R(0)) ? g_div(R(2) * a * b, a + b) : R(0);
 }
 
+// Higher-order face values in index space (Section 4 lists third-order MUSCL and fifth-order
+// WENO beside the second-order default).  muscl3_right(a, b, c) is cell b's value at its right face
+// from cells a, b, c; muscl3_left(a, b, c) cell b's value at its left face: the kappa = 1/3 scheme
+// with each one-sided difference limited by minmod against 4 times the other.
+template <class R>
+GKS_FN R muscl3_right(R a, R b, R c) {
+  const R dm = b - a, dp = c - b;
+  return b + limiter<R>(LIM_MINMOD, dm, R(4) * dp) * R(1.0 / 6.0) + limiter<R>(LIM_MINMOD, dp, R(4) * dm) * R(1.0 / 3.0);
+}
+template <class R>
+GKS_FN R muscl3_left(R a, R b, R c) {
+  const R dm = b - a, dp = c - b;
+  return b - limiter<R>(LIM_MINMOD, dp, R(4) * dm) * R(1.0 / 6.0) - limiter<R>(LIM_MINMOD, dm, R(4) * dp) * R(1.0 / 3.0);
+}
+// Jiang and Shu's WENO-5: the value at the face to the right of c from cells a, b, c, d, e
+// (candidate stencils' face values, smoothness indicators with 13/12 and 1/4, linear weights
+// 1/10, 6/10, 3/10, epsilon 1e-6).
+template <class R>
+GKS_FN R weno5(R a, R b, R c, R d, R e) {
+  const R s6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0);
+  const R q0 = (R(2) * a - R(7) * b + R(11) * c) * s6;
+  const R q1 = (-b + R(5) * c + R(2) * d) * s6;
+  const R q2 = (R(2) * c + R(5) * d - e) * s6;
+  const R t0 = a - R(2) * b + c, u0 = a - R(4) * b + R(3) * c;
+  const R t1 = b - R(2) * c + d, u1 = b - d;
+  const R t2 = c - R(2) * d + e, u2 = R(3) * c - R(4) * d + e;
+  const R b0 = c13 * t0 * t0 + R(0.25) * u0 * u0;
+  const R b1 = c13 * t1 * t1 + R(0.25) * u1 * u1;
+  const R b2 = c13 * t2 * t2 + R(0.25) * u2 * u2;
+  const R eps = R(1e-6);
+  const R a0 = g_div(R(0.1), (eps + b0) * (eps + b0));
+  const R a1 = g_div(R(0.6), (eps + b1) * (eps + b1));
+  const R a2 = g_div(R(0.3), (eps + b2) * (eps + b2));
+  return g_div(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
 // MUSCL on one variable at the face between cells 1 and 2 of the stencil s0..s3 with widths
 // h0..h3: limited slopes of cells 1 and 2 and the face values left and right.
 template <class R>

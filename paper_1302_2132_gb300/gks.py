@@ -98,6 +98,8 @@ def load():
     L.gks_face_op_count.restype = _I
     L.gks_cell_op_count.argtypes = [_I, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_cell_op_count.restype = _I
+    L.gks_recon_op_count.argtypes = [_I, _I, ctypes.POINTER(ctypes.c_longlong)]
+    L.gks_recon_op_count.restype = _I
     L.gks_face_flux.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _V, ctypes.c_long, _V, _V, _V]
     for name in ("gks_create", "gks_set_state", "gks_get_state", "gks_set_turbulence", "gks_compute_dt",
                  "gks_step", "gks_get_time", "gks_set_time", "gks_residual", "gks_status_word",
@@ -353,6 +355,16 @@ def cell_op_count(dim):
     """Static per-cell operation count of the reconstruction slopes: (add, mul, div, sqrt, exp, erfc)."""
     c = (ctypes.c_longlong * 6)()
     load().gks_cell_op_count(dim, c)
+    return tuple(c)
+
+
+def recon_op_count(dim, reconstruction):
+    """Static per-face operation count of a higher-order reconstruction's face values and slopes."""
+    c = (ctypes.c_longlong * 6)()
+    r = RECON[reconstruction] if isinstance(reconstruction, str) else int(reconstruction)
+    if r == 0:
+        return (0,) * 6
+    load().gks_recon_op_count(dim, r, c)
     return tuple(c)
 
 

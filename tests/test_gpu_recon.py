@@ -77,3 +77,20 @@ def test_unsupported_combinations_are_rejected():
     t3 = inputs.turbulence(8, 3, seed=1)
     with pytest.raises(gks.GksError):
         gpu_solver(t3, multid=0, recon=MUSCL3)
+
+
+@pytest.mark.parametrize("recon", [MUSCL3, WENO5])
+def test_higher_order_tile_shapes_agree(monkeypatch, recon):
+    """The 32x15 and 32x27 tiles of the higher-order step evaluate the same faces (FP32 rounding)."""
+    spec = inputs.turbulence(70, 2, seed=5)
+    out = []
+    for v in ("0", "3"):
+        monkeypatch.setenv("GKS_TILE_VARIANT", v)
+        s = gpu_solver(spec, precision="fp32", recon=recon, turb_model=2, mu=1e-5)
+        s.set_state(spec["prim"].ravel(), layout="soa_prim")
+        s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+        s.step(nsteps=20, cfl=0.5)
+        assert s.tile_shape()[0] == int(v)
+        out.append(s.get_state())
+        s.close()
+    assert np.all(rel_err_per_var(out[1], out[0], 4) < 1e-6)
