@@ -132,6 +132,8 @@ def lib():
             L.orc_rarefaction.argtypes = [P, _PD, _PD, _PD, _PD]
             L.orc_step.argtypes = [P, _PD, _PD, _PD, _D, _PD, _I]
             L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
+            L.orc_step_curv.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I]
+            L.orc_compute_dt_curv.argtypes = [P, _PD, _PD, _D, _PD]
             L.orc_komega_defaults.argtypes = [ctypes.POINTER(KOmega)]
             L.orc_step_komega.argtypes = [P, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _I]
             _lib = L
@@ -333,6 +335,30 @@ class Case:
         st = lib().orc_step_komega(ctypes.byref(self.P), ctypes.byref(c), _ptr(W), _ptr(RK), _ptr(RW), dt,
                                    nthreads)
         return W, RK, RW, st
+
+
+    def _nodes(self, nodes):
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        assert self.dim == 2 and nodes.size == 2 * (self.n[0] + 1) * (self.n[1] + 1)
+        return nodes
+
+    def step_curv(self, nodes, W, dt, f1=None, f2=None, nthreads=1):
+        """One directional step on the curvilinear grid of the node array nodes[n1 + 1, n0 + 1, 2]
+        (the problem's dx is not used); returns (W_new, status).  Status 2: a cell that is not a
+        convex counter-clockwise quadrilateral."""
+        nodes = self._nodes(nodes)
+        W = self._state(W).copy()
+        st = lib().orc_step_curv(ctypes.byref(self.P), _ptr(nodes), _ptr(W), _ptr(self._field(f1)),
+                                 _ptr(self._field(f2)), dt, nthreads)
+        return W, st
+
+    def compute_dt_curv(self, nodes, W, cfl):
+        nodes = self._nodes(nodes)
+        W = self._state(W)
+        dt = ctypes.c_double()
+        st = lib().orc_compute_dt_curv(ctypes.byref(self.P), _ptr(nodes), _ptr(W), cfl, ctypes.byref(dt))
+        assert st == 0
+        return dt.value
 
 
 def komega_defaults(**over):

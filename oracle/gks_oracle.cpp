@@ -31,6 +31,12 @@
  *   - Reconstruction: MUSCL on conservative variables with minmod or van Leer, applied also to the
  *     tangential slopes; a side whose reconstructed rho or p is not positive falls back to first
  *     order at that face.
+ *   - Body-fitted 2D grids (the paper's C-type and channel grids, Table 2) with the directional
+ *     expansion: each face works in its own (normal, tangent) frame; MUSCL runs along the grid
+ *     line with centroid distances (vertex-average centroids, ghosts mirrored through the boundary
+ *     face or translated by the period); the face flux is weighted by the face length and the
+ *     update divided by the cell area; tau_t takes Green-Gauss velocity gradients (face value the
+ *     mean of the two cells) and a ghost cell the value of its source cell.
  */
 #include "gks_oracle.h"
 
@@ -1191,9 +1197,322 @@ void komega_update(const orc_problem* P, const orc_komega* K, const Grid& G, con
       }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Curvilinear 2D geometry
+// ---------------------------------------------------------------------------------------------
+struct CurvGeom {
+  int n0, n1;
+  bool convex;  // every cell a convex, counter-clockwise quadrilateral
+  std::vector<double> area, cx, cy;        // cells, [j][i]
+  std::vector<double> inx, iny, iL, imx, imy;  // i-faces (i = 0..n0, j = 0..n1-1), [j][i]
+  std::vector<double> jnx, jny, jL, jmx, jmy;  // j-faces (i = 0..n0-1, j = 0..n1), [j][i]
+  // centroids with two ghost layers per side, padded [j + 2][i + 2]
+  std::vector<double> pcx, pcy;
+  double nx(const double* nodes, int i, int j) const { return nodes[((long)j * (n0 + 1) + i) * 2]; }
+  double ny(const double* nodes, int i, int j) const { return nodes[((long)j * (n0 + 1) + i) * 2 + 1]; }
+  long pidx(int i, int j) const { return (long)(j + 2) * (n0 + 4) + (i + 2); }
+};
+
+CurvGeom curv_geometry(const orc_problem* P, const double* nodes) {
+  CurvGeom g;
+  const int n0 = P->n[0], n1 = P->n[1];
+  g.n0 = n0;
+  g.n1 = n1;
+  g.area.resize((size_t)n0 * n1);
+  g.cx.resize((size_t)n0 * n1);
+  g.cy.resize((size_t)n0 * n1);
+  g.convex = true;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const double x00 = g.nx(nodes, i, j), y00 = g.ny(nodes, i, j);
+      const double x10 = g.nx(nodes, i + 1, j), y10 = g.ny(nodes, i + 1, j);
+      const double x11 = g.nx(nodes, i + 1, j + 1), y11 = g.ny(nodes, i + 1, j + 1);
+      const double x01 = g.nx(nodes, i, j + 1), y01 = g.ny(nodes, i, j + 1);
+      const long c = (long)j * n0 + i;
+      g.area[c] = 0.5 * ((x11 - x00) * (y01 - y10) - (x01 - x10) * (y11 - y00));  // > 0: right-handed
+      // every corner of the quadrilateral (counter-clockwise 00, 10, 11, 01) turns left
+      const double qx[4] = {x00, x10, x11, x01}, qy[4] = {y00, y10, y11, y01};
+      for (int q = 0; q < 4; ++q) {
+        const int a = (q + 3) % 4, b = (q + 1) % 4;
+        if (!((qx[q] - qx[a]) * (qy[b] - qy[q]) - (qy[q] - qy[a]) * (qx[b] - qx[q]) > 0.0)) g.convex = false;
+      }
+      g.cx[c] = 0.25 * (x00 + x10 + x11 + x01);
+      g.cy[c] = 0.25 * (y00 + y10 + y11 + y01);
+    }
+  g.inx.resize((size_t)(n0 + 1) * n1);
+  g.iny.resize(g.inx.size());
+  g.iL.resize(g.inx.size());
+  g.imx.resize(g.inx.size());
+  g.imy.resize(g.inx.size());
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i <= n0; ++i) {
+      const double ex = g.nx(nodes, i, j + 1) - g.nx(nodes, i, j), ey = g.ny(nodes, i, j + 1) - g.ny(nodes, i, j);
+      const double L = std::sqrt(ex * ex + ey * ey);
+      const long f = (long)j * (n0 + 1) + i;
+      g.iL[f] = L;
+      g.inx[f] = ey / L;
+      g.iny[f] = -ex / L;
+      g.imx[f] = 0.5 * (g.nx(nodes, i, j) + g.nx(nodes, i, j + 1));
+      g.imy[f] = 0.5 * (g.ny(nodes, i, j) + g.ny(nodes, i, j + 1));
+    }
+  g.jnx.resize((size_t)n0 * (n1 + 1));
+  g.jny.resize(g.jnx.size());
+  g.jL.resize(g.jnx.size());
+  g.jmx.resize(g.jnx.size());
+  g.jmy.resize(g.jnx.size());
+  for (int j = 0; j <= n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const double ex = g.nx(nodes, i + 1, j) - g.nx(nodes, i, j), ey = g.ny(nodes, i + 1, j) - g.ny(nodes, i, j);
+      const double L = std::sqrt(ex * ex + ey * ey);
+      const long f = (long)j * n0 + i;
+      g.jL[f] = L;
+      g.jnx[f] = -ey / L;
+      g.jny[f] = ex / L;
+      g.jmx[f] = 0.5 * (g.nx(nodes, i, j) + g.nx(nodes, i + 1, j));
+      g.jmy[f] = 0.5 * (g.ny(nodes, i, j) + g.ny(nodes, i + 1, j));
+    }
+  // centroids with ghosts: on a periodic axis a ghost is its source cell translated by the period
+  // (the difference of the two boundary face midpoints), on other axes the mirror image of the
+  // interior cell through the boundary face midpoint -- the positions the ghost widths of a
+  // rectilinear grid give.  The i ghosts first, then the j ghosts over the padded i range.
+  g.pcx.assign((size_t)(n0 + 4) * (n1 + 4), 0.0);
+  g.pcy.assign(g.pcx.size(), 0.0);
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      g.pcx[g.pidx(i, j)] = g.cx[(long)j * n0 + i];
+      g.pcy[g.pidx(i, j)] = g.cy[(long)j * n0 + i];
+    }
+  const bool per0 = P->bc[0][0] == ORC_BC_PERIODIC, per1 = P->bc[1][0] == ORC_BC_PERIODIC;
+  for (int j = 0; j < n1; ++j)
+    for (int k = 1; k <= 2; ++k) {
+      const long fl = (long)j * (n0 + 1), fr = (long)j * (n0 + 1) + n0;
+      double* X[2] = {g.pcx.data(), g.pcy.data()};
+      const double ml[2] = {g.imx[fl], g.imy[fl]}, mr[2] = {g.imx[fr], g.imy[fr]};
+      for (int q = 0; q < 2; ++q) {
+        if (per0) {
+          X[q][g.pidx(-k, j)] = X[q][g.pidx(n0 - k, j)] + (ml[q] - mr[q]);
+          X[q][g.pidx(n0 - 1 + k, j)] = X[q][g.pidx(k - 1, j)] + (mr[q] - ml[q]);
+        } else {
+          X[q][g.pidx(-k, j)] = 2.0 * ml[q] - X[q][g.pidx(k - 1, j)];
+          X[q][g.pidx(n0 - 1 + k, j)] = 2.0 * mr[q] - X[q][g.pidx(n0 - k, j)];
+        }
+      }
+    }
+  for (int i = -2; i < n0 + 2; ++i)
+    for (int k = 1; k <= 2; ++k) {
+      const int ii = std::min(std::max(i, 0), n0 - 1);
+      const long fb = ii, ft = (long)n1 * n0 + ii;
+      double* X[2] = {g.pcx.data(), g.pcy.data()};
+      const double mb[2] = {g.jmx[fb], g.jmy[fb]}, mt[2] = {g.jmx[ft], g.jmy[ft]};
+      for (int q = 0; q < 2; ++q) {
+        if (per1) {
+          X[q][g.pidx(i, -k)] = X[q][g.pidx(i, n1 - k)] + (mb[q] - mt[q]);
+          X[q][g.pidx(i, n1 - 1 + k)] = X[q][g.pidx(i, k - 1)] + (mt[q] - mb[q]);
+        } else {
+          X[q][g.pidx(i, -k)] = 2.0 * mb[q] - X[q][g.pidx(i, k - 1)];
+          X[q][g.pidx(i, n1 - 1 + k)] = 2.0 * mt[q] - X[q][g.pidx(i, n1 - k)];
+        }
+      }
+    }
+  return g;
+}
+
+bool curv_valid(const CurvGeom& g) {
+  if (!g.convex) return false;
+  for (double a : g.area)
+    if (!(a > 0.0)) return false;
+  for (double L : g.iL)
+    if (!(L > 0.0)) return false;
+  for (double L : g.jL)
+    if (!(L > 0.0)) return false;
+  return true;
+}
+
+double cdist(const CurvGeom& g, int i0, int j0, int i1, int j1) {
+  const double dx = g.pcx[g.pidx(i1, j1)] - g.pcx[g.pidx(i0, j0)], dy = g.pcy[g.pidx(i1, j1)] - g.pcy[g.pidx(i0, j0)];
+  return std::sqrt(dx * dx + dy * dy);
+}
+
 }  // namespace
 
 extern "C" {
+
+int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt) {
+  if (P->dim != 2) return 1;
+  const CurvGeom g = curv_geometry(P, nodes);
+  if (!curv_valid(g)) return 2;
+  const int n0 = g.n0, n1 = g.n1;
+  const long ncell = (long)n0 * n1;
+  double rmax = 0.0;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      double w[4];
+      for (int v = 0; v < 4; ++v) w[v] = W[v * ncell + c];
+      const double p = pressure(2, P->gamma, w), cs = std::sqrt(P->gamma * p / w[0]);
+      const double u = w[1] / w[0], v = w[2] / w[0];
+      const long fi[2] = {(long)j * (n0 + 1) + i, (long)j * (n0 + 1) + i + 1};
+      const long fj[2] = {(long)j * n0 + i, (long)(j + 1) * n0 + i};
+      double r = 0.0;
+      for (int s = 0; s < 2; ++s) {
+        r += (std::fabs(u * g.inx[fi[s]] + v * g.iny[fi[s]]) + cs) * g.iL[fi[s]];
+        r += (std::fabs(u * g.jnx[fj[s]] + v * g.jny[fj[s]]) + cs) * g.jL[fj[s]];
+      }
+      rmax = std::max(rmax, r / (2.0 * g.area[c]));
+    }
+  *dt = cfl / rmax;
+  return 0;
+}
+
+int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
+                  double dt, int nthreads) {
+  if (P->dim != 2 || P->recon != ORC_RECON_MUSCL2) return 1;
+  const CurvGeom g = curv_geometry(P, nodes);
+  if (!curv_valid(g)) return 2;
+  Grid G = make_grid(P);
+  const int n0 = g.n0, n1 = g.n1, nv = 4;
+  const long ncell = (long)n0 * n1;
+  std::vector<double> Wp;
+  pad_state(G, W, Wp);
+  fill_ghosts(P, G, Wp);
+  std::vector<double> f1p = pad_scalar(P, G, f1), f2p = pad_scalar(P, G, f2);
+  // turbulent relaxation time per cell from Green-Gauss velocity gradients; ghosts take the
+  // value of their source cell
+  std::vector<double> taut(ncell, 0.0);
+  if (P->turb_model != ORC_TURB_NONE) {
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n0; ++i) {
+        const long c = (long)j * n0 + i;
+        double w[5];
+        get_cell(G, Wp, i, j, 0, w);
+        const double rho = w[0], p = pressure(2, P->gamma, w);
+        const double kk = f1p[G.idx(i, j, 0)], e2 = f2p[G.idx(i, j, 0)];
+        if (P->turb_model == ORC_TURB_MUT) {
+          taut[c] = kk / p;
+          continue;
+        }
+        if (!(kk > 0.0) || !(e2 > 0.0)) continue;
+        double gr[2][2] = {{0, 0}, {0, 0}};  // gr[a][b] = dU_b/dx_a
+        const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+        const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
+        const long fidx[4] = {(long)j * (n0 + 1) + i, (long)j * (n0 + 1) + i + 1, (long)j * n0 + i,
+                              (long)(j + 1) * n0 + i};
+        for (int q = 0; q < 4; ++q) {
+          double wn[5];
+          get_cell(G, Wp, nb[q][0], nb[q][1], 0, wn);
+          const double nxq = q < 2 ? g.inx[fidx[q]] : g.jnx[fidx[q]], nyq = q < 2 ? g.iny[fidx[q]] : g.jny[fidx[q]];
+          const double L = q < 2 ? g.iL[fidx[q]] : g.jL[fidx[q]];
+          for (int b = 0; b < 2; ++b) {
+            const double uf = 0.5 * (w[1 + b] / w[0] + wn[1 + b] / wn[0]);
+            gr[0][b] += sgn[q] * uf * nxq * L;
+            gr[1][b] += sgn[q] * uf * nyq * L;
+          }
+        }
+        double s2 = 0.0;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) {
+            const double sab = 0.5 * (gr[a][b] + gr[b][a]) / g.area[c];
+            s2 += sab * sab;
+          }
+        const double S = std::sqrt(2.0 * s2);
+        double nu_t, eta;
+        if (P->turb_model == ORC_TURB_KEPS) {
+          nu_t = P->C_mu * kk * kk / e2;
+          eta = S * kk / e2;
+        } else {
+          nu_t = kk / e2;
+          eta = S / (P->beta_star * e2);
+        }
+        taut[c] = rho * nu_t / (p * std::sqrt(1.0 + eta * eta));
+      }
+  }
+  auto tau_of = [&](int i, int j) {  // ghost cells take their source cell's value
+    if (P->bc[0][0] == ORC_BC_PERIODIC) i = (i + n0) % n0; else i = std::min(std::max(i, 0), n0 - 1);
+    if (P->bc[1][0] == ORC_BC_PERIODIC) j = (j + n1) % n1; else j = std::min(std::max(j, 0), n1 - 1);
+    return taut[(long)j * n0 + i];
+  };
+  // fluxes times face length, per axis
+  std::vector<double> Fi((size_t)(n0 + 1) * n1 * nv), Fj((size_t)n0 * (n1 + 1) * nv);
+  for (int d = 0; d < 2; ++d) {
+    const int nf0 = d == 0 ? n0 + 1 : n0, nf1 = d == 0 ? n1 : n1 + 1;
+    const long nfaces = (long)nf0 * nf1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (long f = 0; f < nfaces; ++f) {
+      const int fi = (int)(f % nf0), fj = (int)(f / nf0);
+      const double nxf = d == 0 ? g.inx[f] : g.jnx[f], nyf = d == 0 ? g.iny[f] : g.jny[f];
+      const double L = d == 0 ? g.iL[f] : g.jL[f];
+      const double mx = d == 0 ? g.imx[f] : g.jmx[f], my = d == 0 ? g.imy[f] : g.jmy[f];
+      // stencil cells s = 0..3: index (face index) - 2 + s along d
+      int ci[4], cj[4];
+      double S4[4][4];
+      for (int s2 = 0; s2 < 4; ++s2) {
+        ci[s2] = d == 0 ? fi - 2 + s2 : fi;
+        cj[s2] = d == 0 ? fj : fj - 2 + s2;
+        double w[5];
+        get_cell(G, Wp, ci[s2], cj[s2], 0, w);
+        S4[s2][0] = w[0];
+        S4[s2][1] = w[1] * nxf + w[2] * nyf;   // rho u_n
+        S4[s2][2] = -w[1] * nyf + w[2] * nxf;  // rho u_t, t = (-n_y, n_x)
+        S4[s2][3] = w[3];
+      }
+      const double d01 = cdist(g, ci[0], cj[0], ci[1], cj[1]), d12 = cdist(g, ci[1], cj[1], ci[2], cj[2]);
+      const double d23 = cdist(g, ci[2], cj[2], ci[3], cj[3]);
+      const double dl = std::sqrt((mx - g.pcx[g.pidx(ci[1], cj[1])]) * (mx - g.pcx[g.pidx(ci[1], cj[1])]) +
+                                  (my - g.pcy[g.pidx(ci[1], cj[1])]) * (my - g.pcy[g.pidx(ci[1], cj[1])]));
+      const double dr = std::sqrt((mx - g.pcx[g.pidx(ci[2], cj[2])]) * (mx - g.pcx[g.pidx(ci[2], cj[2])]) +
+                                  (my - g.pcy[g.pidx(ci[2], cj[2])]) * (my - g.pcy[g.pidx(ci[2], cj[2])]));
+      orc_face fc;
+      std::memset(&fc, 0, sizeof(fc));
+      for (int v = 0; v < nv; ++v) {
+        const double sl = limiter(P->limiter, (S4[1][v] - S4[0][v]) / d01, (S4[2][v] - S4[1][v]) / d12);
+        const double sr = limiter(P->limiter, (S4[2][v] - S4[1][v]) / d12, (S4[3][v] - S4[2][v]) / d23);
+        fc.sl[v] = sl;
+        fc.sr[v] = sr;
+        fc.wl[v] = S4[1][v] + dl * sl;
+        fc.wr[v] = S4[2][v] - dr * sr;
+        fc.cl[v] = S4[1][v];
+        fc.cr[v] = S4[2][v];
+      }
+      if (!(fc.wl[0] > 0.0) || !(pressure(2, P->gamma, fc.wl) > 0.0))
+        for (int v = 0; v < nv; ++v) {
+          fc.wl[v] = S4[1][v];
+          fc.sl[v] = 0.0;
+        }
+      if (!(fc.wr[0] > 0.0) || !(pressure(2, P->gamma, fc.wr) > 0.0))
+        for (int v = 0; v < nv; ++v) {
+          fc.wr[v] = S4[2][v];
+          fc.sr[v] = 0.0;
+        }
+      fc.dxl = dl;
+      fc.dxr = dr;
+      fc.tau_t = 0.5 * (tau_of(ci[1], cj[1]) + tau_of(ci[2], cj[2]));
+      FaceWork Wk;
+      face_setup(2, P->gamma, P->mu, P->C_a, dt, 0, P->abar_mode, fc, Wk);
+      double Fr[4];
+      face_flux(Wk, Fr);
+      double* Fo = d == 0 ? &Fi[f * nv] : &Fj[f * nv];
+      Fo[0] = Fr[0] * L;
+      Fo[1] = (Fr[1] * nxf - Fr[2] * nyf) * L;
+      Fo[2] = (Fr[1] * nyf + Fr[2] * nxf) * L;
+      Fo[3] = Fr[3] * L;
+    }
+  }
+  int status = 0;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      const long fa = (long)j * (n0 + 1) + i, fb = fa + 1, fc2 = (long)j * n0 + i, fd = (long)(j + 1) * n0 + i;
+      double w[4];
+      for (int v = 0; v < nv; ++v) {
+        W[v * ncell + c] -= (Fi[fb * nv + v] - Fi[fa * nv + v] + Fj[fd * nv + v] - Fj[fc2 * nv + v]) / g.area[c];
+        w[v] = W[v * ncell + c];
+      }
+      if (!(w[0] > 0.0) || !(pressure(2, P->gamma, w) > 0.0)) status = 4;
+    }
+  return status;
+}
 
 int orc_reconstruct(int recon, int limiter, const double* v, const double* h, int n, double* wl, double* wr) {
   if (n < 6) return 1;

@@ -106,6 +106,23 @@ int orc_komega_defaults(orc_komega* c);
 int orc_step_komega(const orc_problem* P, const orc_komega* c, double* W, double* RK, double* RW, double dt,
                     int nthreads);
 
+/* Curvilinear (body-fitted) 2D grids with the directional expansion: the cells are the
+ * quadrilaterals of a structured node lattice nodes[(j (n0+1) + i) * 2 + {0, 1}] = (x, y),
+ * i = 0..n0, j = 0..n1 (P->dx is not used; P->dim must be 2, P->recon MUSCL2).  Per face: unit
+ * normal pointing to increasing index, length, midpoint; per cell: area (diagonal cross product)
+ * and the vertex-average centroid.  A face rotates its four-cell stencil along the grid line into
+ * its (normal, tangent) frame, reconstructs with limited slopes over the centroid distances,
+ * evaluates the face flux with the centroid-to-midpoint distances, rotates the momentum flux back
+ * and weights it by the face length; a cell's update divides by its area.  Ghost cells follow
+ * the boundary rules of the index lattice; ghost centroids are interior centroids reflected
+ * through the boundary face midpoints; the turbulent relaxation time uses Green-Gauss gradients
+ * (face velocity = mean of the two cells) and a ghost cell takes its source cell's value. */
+/* Status 2 (nothing updated): a cell that is not a convex counter-clockwise quadrilateral. */
+int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
+                  double dt, int nthreads);
+/* CFL step on a curvilinear grid: dt = cfl / max_cells sum_faces (|U.n| + c) L / (2 A). */
+int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,10 @@ inputs of this library):
   riemann_quadrant  2D four-state Riemann problem with seeded states
   shock_boundary_layer  Mach 2.85 flat-plate boundary layer under an oblique shock on a
                     wall-clustered grid, with log-law k-omega profiles
+  compression_corner  Mach 2.85 boundary layer over a ramp of alpha degrees on a body-fitted,
+                    wall-clustered channel grid (nodes given), log-law k-omega profiles
+  wavy_nodes        smoothly skewed periodic grids (with smooth_state_at, positive_fields_at) for the
+                    curvilinear invariance and parity tests
 """
 import math
 
@@ -229,6 +233,138 @@ def shock_boundary_layer(nx, ny, M=2.85, delta=0.1, theta_deg=24.0, Re_delta=1.6
     bc_prim = [[inflow, None], [None, top]]
     return dict(dim=2, n=(nx, ny), dx=[dx, dy], bc=bc, bc_prim=bc_prim, prim=prim, T_wall=T_wall, mu=mu,
                 f1=f1.astype(np.float32).astype(np.float64), f2=f2.astype(np.float32).astype(np.float64))
+
+
+# ------------------------------------------------------------------------------------------------
+# Curvilinear (body-fitted) 2D grids: node arrays nodes[n1 + 1, n0 + 1, 2] = (x, y), right-handed
+# ------------------------------------------------------------------------------------------------
+def uniform_nodes(n0, n1, lx=1.0, ly=1.0):
+    """The nodes of a uniform rectilinear grid on [0, lx] x [0, ly]."""
+    X, Y = np.meshgrid(np.linspace(0.0, lx, n0 + 1), np.linspace(0.0, ly, n1 + 1), indexing="xy")
+    return np.stack([X, Y], axis=-1)
+
+
+def rectilinear_nodes(dx, dy):
+    """The nodes of the tensor-product grid with column widths dx and row heights dy."""
+    xs = np.concatenate([[0.0], np.cumsum(dx)])
+    ys = np.concatenate([[0.0], np.cumsum(dy)])
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    return np.stack([X, Y], axis=-1)
+
+
+def wavy_nodes(n0, n1, lx=1.0, ly=1.0, amp=0.03, shear=0.05):
+    """A smoothly distorted grid on an lx x ly box that is periodic by translation:
+    x = X + shear ly sin(2 pi Y/ly) + amp lx sin(2 pi X/lx) sin(2 pi Y/ly),
+    y = Y + shear lx sin(2 pi X/lx) + amp ly sin(2 pi X/lx) sin(4 pi Y/ly);
+    node (n0, j) is node (0, j) moved by (lx, 0), node (i, n1) is node (i, 0) moved by (0, ly).
+    Cells are skewed by up to about 20 degrees and change area by up to about 40%."""
+    U = uniform_nodes(n0, n1, lx, ly)
+    X, Y = U[..., 0], U[..., 1]
+    sx, sy = np.sin(2 * math.pi * X / lx), np.sin(2 * math.pi * Y / ly)
+    x = X + shear * ly * sy + amp * lx * sx * sy
+    y = Y + shear * lx * sx + amp * ly * sx * np.sin(4 * math.pi * Y / ly)
+    return np.stack([x, y], axis=-1)
+
+
+def rotate_nodes(nodes, theta):
+    c, s = math.cos(theta), math.sin(theta)
+    x, y = nodes[..., 0], nodes[..., 1]
+    return np.stack([c * x - s * y, s * x + c * y], axis=-1)
+
+
+def rotate_prim(prim, theta):
+    """Primitive state (rho, u, v, p)[4, ...] with the velocity turned by theta."""
+    c, s = math.cos(theta), math.sin(theta)
+    out = np.array(prim, dtype=np.float64, copy=True)
+    out[1] = c * prim[1] - s * prim[2]
+    out[2] = s * prim[1] + c * prim[2]
+    return out
+
+
+def cell_points(nodes):
+    """One sample point per cell (the mean of its four nodes), [n1, n0, 2]: where the input
+    generators evaluate initial fields."""
+    return 0.25 * (nodes[:-1, :-1] + nodes[:-1, 1:] + nodes[1:, :-1] + nodes[1:, 1:])
+
+
+def smooth_state_at(points, seed, lx=1.0, ly=1.0, amp=0.1):
+    """A smooth positive state periodic on the lx x ly box, evaluated at points[..., 2]."""
+    rng = np.random.default_rng(seed)
+    X = points[..., 0] * (2 * math.pi / lx)
+    Y = points[..., 1] * (2 * math.pi / ly)
+    f = lambda: sum(rng.normal() * np.cos(kx * X + ky * Y + rng.uniform(0, 6.28))
+                    for kx, ky in ((1, 0), (0, 1), (1, 1), (2, -1)))
+    prim = np.zeros((4,) + X.shape)
+    prim[0] = 1.0 + amp * f()
+    prim[1] = 0.3 * f()
+    prim[2] = 0.3 * f()
+    prim[3] = 1.0 + amp * f()
+    return prim
+
+
+def positive_fields_at(points, seed, lx=1.0, ly=1.0, k_ref=0.01, om_ref=20.0):
+    """Smooth positive turbulence fields (k, second variable) periodic on the box."""
+    rng = np.random.default_rng(seed)
+    X = points[..., 0] * (2 * math.pi / lx)
+    Y = points[..., 1] * (2 * math.pi / ly)
+    g = lambda: sum(rng.normal() * np.cos(kx * X + ky * Y + rng.uniform(0, 6.28)) for kx, ky in ((1, 0), (0, 1), (1, -1)))
+    return k_ref * np.exp(0.3 * g()), om_ref * np.exp(0.3 * g())
+
+
+def _row_heights(ny, dy1, ratio, total):
+    def heights(cap):
+        return np.minimum(dy1 * ratio ** np.arange(ny), cap)
+    lo, hi = dy1, total
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if heights(mid).sum() > total:
+            hi = mid
+        else:
+            lo = mid
+    h = heights(0.5 * (lo + hi))
+    return h * (total / h.sum())
+
+
+def compression_corner(nx, ny, alpha_deg=24.0, M=2.85, delta=0.1, Re_delta=1.6e6, ratio=1.08, dy1=2e-5,
+                       xlen=2.0, ylen=1.0, gamma=GAMMA):
+    """Supersonic compression corner in a channel (the geometry type of the paper's Settles cases;
+    the exact experimental geometry is not an input here): the lower wall is flat for x < 0 and
+    turns up by alpha at x = 0; the grid lines x = const run from the wall to the flat top y = ylen,
+    rows clustered at the wall by the given growth ratio (first row dy1, as a fraction of the local
+    channel height).  Isothermal no-slip lower wall, Dirichlet inflow carrying a 1/7-power boundary
+    layer of thickness delta and log-law k, omega, supersonic outflow at the right and the top.
+    Free stream rho = 1, p = 1/gamma (c = 1), u = M.  Returns nodes, primitives at the cells, the
+    inflow state, k and omega."""
+    xs = np.linspace(-0.5 * xlen, 0.5 * xlen, nx + 1)
+    yw = np.where(xs > 0.0, xs * math.tan(math.radians(alpha_deg)), 0.0)
+    eta = np.concatenate([[0.0], np.cumsum(_row_heights(ny, dy1, ratio, 1.0))])
+    X = np.repeat(xs[None, :], ny + 1, axis=0)
+    Y = yw[None, :] + (ylen - yw[None, :]) * eta[:, None]
+    nodes = np.stack([X, Y], axis=-1)
+    pts = cell_points(nodes)
+    ywc = 0.5 * (yw[:-1] + yw[1:])
+    dist = np.maximum(pts[..., 1] - ywc[None, :], 1e-12)  # distance above the wall along the grid line
+    T_inf = 1.0 / gamma
+    T_wall = T_inf * (1.0 + 0.89 * 0.5 * (gamma - 1.0) * M * M)
+    mu = M * delta / Re_delta
+    prof = np.where(dist < delta, (dist / delta) ** (1.0 / 7.0), 1.0)
+    Tprof = T_wall + (T_inf - T_wall) * prof
+    prim = np.zeros((4, ny, nx))
+    prim[0] = 1.0 / gamma / Tprof
+    prim[1] = M * prof
+    prim[3] = 1.0 / gamma
+    inflow = np.stack([prim[v][:, 0] for v in range(4)], axis=1)
+    bstar, kap = 0.09, 0.41
+    utau = M * math.sqrt(0.0016 / 2.0)
+    nu_w = mu * gamma * T_wall
+    om = np.maximum(6.0 * nu_w / (0.075 * dist ** 2), utau / (math.sqrt(bstar) * kap * dist))
+    kk = utau ** 2 / math.sqrt(bstar) * np.minimum(1.0, (dist * utau / nu_w / 10.0) ** 2)
+    kk = np.where(dist < delta, kk, 1e-6 * M * M)
+    om = np.where(dist < delta, om, M / delta)
+    bc = [[3, 4], [2, 4]]
+    bc_prim = [[inflow, None], [None, None]]
+    return dict(dim=2, n=(nx, ny), nodes=nodes, bc=bc, bc_prim=bc_prim, prim=prim, T_wall=T_wall, mu=mu,
+                f1=kk.astype(np.float32).astype(np.float64), f2=om.astype(np.float32).astype(np.float64))
 
 
 # ------------------------------------------------------------------------------------------------
