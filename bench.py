@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None, choices=["fp32", "fp32_acc64", "fp64"])
     p.add_argument("--workload", default="turb2d_1024",
-                   choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256"])
+                   choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
+                            "corner2d_528x136", "corner2d_2112x544"])
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
                    help="face reconstruction (the default is the second-order MUSCL the metric is quoted on)")
     p.add_argument("--no-e2e", action="store_true")
@@ -159,6 +160,16 @@ def make_workload(name, precision):
                     nsteps=5000, t_end=0.0, precision=precision or "fp32",
                     desc="Mach 2.85 boundary layer under a 24-degree shock, 1024x384 wall-clustered, k-omega tau_t, "
                          "5000 CFL steps")
+    if name.startswith("corner2d_"):
+        nx, ny = (int(v) for v in name.split("_")[1].split("x"))
+        spec = inputs.compression_corner(nx, ny, alpha_deg=24.0)
+        spec["dx"] = [np.full(nx, 1.0 / nx), np.full(ny, 1.0 / ny)]  # unused: the grid is body-fitted
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega",
+                                       beta_star=0.09, C_a=0.5, limiter="vanleer", expand="directional"),
+                    nsteps=2000, t_end=0.0, precision=precision or "fp32", nodes=spec["nodes"],
+                    desc="Mach 2.85 boundary layer over a 24-degree compression corner on a body-fitted "
+                         "%dx%d wall-clustered channel grid, k-omega tau_t, directional expansion in each "
+                         "face's frame, 2000 CFL steps" % (nx, ny))
     if name == "turb3d_256":
         spec = inputs.turbulence(256, 3, seed=2132)
         return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
@@ -208,6 +219,9 @@ def run_ours(args):
     cells = int(np.prod(n))
     solver = gks.Solver(D, n, spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"), precision=wl["precision"],
                         reconstruction=args.reconstruction, **wl["kw"])
+    curv = wl.get("nodes") is not None
+    if curv:
+        solver.set_nodes(wl["nodes"])
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
     turb = wl["kw"].get("turb_model", "none") != "none"
     transport = wl.get("transport", False)
@@ -310,6 +324,7 @@ def run_ours(args):
     avg_launch_s = kms / 1e3 / max(klaunch, 1)
     achieved = ops_per_launch / avg_launch_s / 1e12
     fp64 = wl["precision"] == "fp64"
+    prec_name = {"fp64": "PREC_F64", "fp32": "PREC_F32", "fp32_acc64": "PREC_F32D"}[wl["precision"]]
     lanes = 2 if fp64 else 128  # FP64 runs at 1/64 of the FP32 rate on this part
     peak = 152 * lanes * 2 * 2.070e9 / 1e12
     workload_name = (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32"
@@ -317,7 +332,8 @@ def run_ours(args):
     if args.reconstruction != "muscl2":
         workload_name += "_" + args.reconstruction
     tile = solver.tile_shape()
-    tile_info = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
+    tile_info = ({"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"} if not curv
+                 else {"threads_per_block": 128, "form": "one thread per face / per cell"})
     line = {
         "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
         "value": value,
@@ -342,18 +358,19 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": TRAFFIC_PER_LAUNCH.get((workload_name, tile_info.get("variant"))),
-                     "kernel": "step_kernel<%d, %s, %s>%s" % (D, {"fp64": "PREC_F64", "fp32": "PREC_F32",
-                                                                  "fp32_acc64": "PREC_F32D"}[wl["precision"]],
-                                                               "multid" if multid else "directional",
-                                                               " + komega_kernel (timed together)" if transport
-                                                               else ""),
+                     "kernel": (("step_kernel<%d, %s, %s>%s" % (D, prec_name, "multid" if multid else "directional",
+                                                                 " + komega_kernel (timed together)" if transport
+                                                                 else "")) if not curv else
+                                "curv_tau_kernel + curv_face_kernel + curv_update_kernel<%s> (timed together)"
+                                % prec_name),
                      "avg_launch_us": avg_launch_s * 1e6,
                      "ops_per_face": per_face, "ops_per_cell": per_cell,
                      "peak_basis": "152 SMs x %d %s lanes x 2 (FMA) x 2070 MHz (derived)" % (lanes, "FP64" if fp64
                                                                                             else "FP32")},
         # per bench step: state_in + rate kernels, the step kernels (plus the transport kernels and
         # the two field conversions of set_turbulence with k-omega transport)
-        "gpu_launches": args.steps * ((2 * nsteps + 2 + 4) if transport else (nsteps + 3)),
+        "gpu_launches": args.steps * ((2 * nsteps + 2 + 4) if transport else
+                                      ((3 * nsteps + 3) if curv else (nsteps + 3))),
         "clocks": clock_info,
         "e2e": e2e,
         "final_time": t_end,

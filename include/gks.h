@@ -113,6 +113,24 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
  * counter and the sticky status.  The CFL rate of the new state is computed on the device. */
 gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace, int dtype);
 
+/* Body-fitted 2D grid (the C-type and channel grids of the paper's cases, Section 5, Table 2):
+ * nodes[(n1 + 1)][(n0 + 1)][2] = (x, y) of the structured node lattice (host or device, double;
+ * copied, not retained); cell (i, j) is the quadrilateral of nodes (i, j), (i+1, j), (i+1, j+1),
+ * (i, j+1), which must be convex and counter-clockwise.  The grid's widths and extents are then
+ * unused; boundary conditions keep their meaning on the index lattice (GKS_BC_WALL: no-slip image;
+ * a periodic axis repeats by translation).  Each face works in its own frame: unit normal n
+ * towards increasing index, states rotated to (rho, rho u_n, rho u_t, rho E), MUSCL slopes along
+ * the grid line over centroid distances (vertex-average centroids; ghost centroids mirrored
+ * through the boundary face midpoint, or translated by the period), the flux weighted by the face
+ * length and the update divided by the cell area; tau_t from Green-Gauss velocity gradients (a
+ * ghost cell takes its source cell's value); CFL rate sum_faces (|U.n| + c) L / (2 A).  Built for
+ * dim 2, GKS_EXPAND_DIRECTIONAL, GKS_RECON_MUSCL2, no k-omega transport (GKS_EUNSUPPORTED
+ * otherwise), every precision.  May be called before or after gks_set_state; a second call
+ * replaces the grid.  GKS_EINVAL for a folded or clockwise cell (the handle's grid is then the
+ * rectilinear one again).
+ * gks_get_tau_turb works on such grids, gks_get_rarefaction returns GKS_EUNSUPPORTED. */
+gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
+
 /* Copy out the current state in the requested layout and type. */
 gks_status gks_get_state(gks_handle* h, void* W_out, int layout, int memspace, int dtype);
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gks.h"
+#include "gks_curv.h"
 #include "gks_dispatch.h"
 #include "gks_step.cuh"
 #include "gks_aux.cuh"
@@ -40,6 +41,8 @@ struct gks_handle {
   void* RW[2] = {nullptr, nullptr};
   void* mflux[3] = {nullptr, nullptr, nullptr};  // face mass fluxes of the last flow step
   gks_komega kw{};
+  bool curv = false;  // body-fitted 2D grid set by gks_set_nodes
+  CurvGeom cg{};
   double* widths[3] = {nullptr, nullptr, nullptr};
   double* dir[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   Ctrl* ctrl = nullptr;
@@ -47,6 +50,7 @@ struct gks_handle {
   size_t staging_bytes = 0;
   long long step = 0;
   bool has_state = false, has_turb = false;
+  bool rate_stale = false;  // a step call with t_end ran: steps past t_end leave the next CFL rate unset
   int nblocks = 0;
   int tile_variant = 0;   // 2D FP32: tile shape chosen by the autotuner
   bool tuned = false;
@@ -203,6 +207,10 @@ void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
 // One full step: the flow step and, with k-omega transport, the transport step of rho k and
 // rho omega (into the other buffer pair) with the same dt and the flow step's mass fluxes.
 void launch_step(gks_handle* h, const StepArgs& A) {
+  if (h->curv) {
+    launch_curv_step(h->prec, A, h->cg, h->stream);
+    return;
+  }
   launch_step_variant(h, A, h->tile_variant);
   if (!h->transport) return;
   const int cur = A.Win == h->W[0] ? 0 : 1;
@@ -269,6 +277,11 @@ void launch_rate_d(gks_handle* h, const StepArgs& A, unsigned blocks) {
 
 gks_status launch_rate(gks_handle* h) {
   StepArgs A = step_args(h, h->step, 0);
+  if (h->curv) {
+    launch_curv_rate(h->prec, A, h->cg, h->stream);
+    GKS_CK(h, cudaGetLastError());
+    return GKS_OK;
+  }
   const unsigned blocks = std::min<unsigned>(grid_for(h->ncell, kThreads), 152u * 8u);
   if (h->D == 1)
     launch_rate_d<1>(h, A, blocks);
@@ -306,7 +319,21 @@ gks_status ensure_staging(gks_handle* h, size_t bytes) {
 
 bool valid_bc(int b) { return b >= GKS_BC_PERIODIC && b <= GKS_BC_OUTFLOW; }
 
+void free_curv(gks_handle* h) {
+  CurvGeom& G = h->cg;
+  for (int a = 0; a < 2; ++a) {
+    if (G.face[a]) cudaFree(G.face[a]);
+    if (G.flux[a]) cudaFree(G.flux[a]);
+  }
+  if (G.iarea) cudaFree(G.iarea);
+  if (G.area) cudaFree(G.area);
+  if (G.tau) cudaFree(G.tau);
+  G = CurvGeom{};
+  h->curv = false;
+}
+
 void free_all(gks_handle* h) {
+  free_curv(h);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -670,6 +697,7 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
                                                          h->base.g.gamma, h->prec, h->W[0], h->Wlo[0]);
   GKS_CK(h, cudaGetLastError());
   h->has_state = true;
+  h->rate_stale = false;
   if (h->transport) h->has_turb = false;  // rho k, rho omega belong to the previous state
   return launch_rate(h);
 }
@@ -830,10 +858,23 @@ gks_status gks_get_turbulence(gks_handle* h, void* k_out, void* omega_out, int m
   return GKS_OK;
 }
 
+// Steps taken at or past t_end carry the state over without computing the CFL rate of the next
+// step; before the next use of that rate it is computed from the stored state.
+gks_status refresh_rate(gks_handle* h) {
+  if (!h->rate_stale) return GKS_OK;
+  h->rate_stale = false;
+  GKS_CK(h, cudaMemsetAsync(&h->ctrl->rate[h->step % 3], 0, sizeof(unsigned long long), h->stream));
+  return launch_rate(h);
+}
+
 gks_status gks_compute_dt(gks_handle* h, double cfl, double* dt_out) {
   if (!h || !dt_out || !(cfl > 0.0)) return fail(h, GKS_EINVAL, "bad argument");
   if (!h->has_state) return fail(h, GKS_EINVAL, "no state set");
   DeviceGuard dg(h->dev);
+  {
+    const gks_status rs = refresh_rate(h);
+    if (rs != GKS_OK) return rs;
+  }
   unsigned long long bits = 0;
   GKS_CK(h, cudaMemcpyAsync(&bits, &h->ctrl->rate[h->step % 3], sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
   GKS_CK(h, cudaStreamSynchronize(h->stream));
@@ -850,8 +891,13 @@ gks_status gks_step(gks_handle* h, double dt, double cfl, int nsteps, double t_e
   if (h->base.g.turb_model != GKS_TURB_NONE && !h->has_turb) return fail(h, GKS_EINVAL, "turbulence fields not set");
   if (nsteps == 0) return GKS_OK;
   DeviceGuard dg(h->dev);
+  {
+    const gks_status rs = refresh_rate(h);
+    if (rs != GKS_OK) return rs;
+  }
   set_params_kernel<0><<<1, 1, 0, h->stream>>>(h->ctrl, dt > 0.0 ? dt : 0.0, cfl, t_end);
   GKS_CK(h, cudaGetLastError());
+  if (t_end > 0.0) h->rate_stale = true;
   if (!h->tuned) {
     const gks_status st = autotune(h);
     if (st != GKS_OK) return st;
@@ -957,7 +1003,23 @@ static gks_status get_diag(gks_handle* h, int what, void* out, int memspace, int
     dst = h->staging;
   }
   const StepArgs A = step_args(h, h->step, 0);
-  if (h->D == 1)
+  if (h->curv) {
+    if (what != 0) return fail(h, GKS_EUNSUPPORTED, "rarefaction diagnostic on a curvilinear grid");
+    if (h->base.g.turb_model == GKS_TURB_NONE) {
+      GKS_CK(h, cudaMemsetAsync(dst, 0, bytes, h->stream));
+    } else {
+      launch_curv_tau(h->prec, A, h->cg, h->cg.tau, h->stream);
+      const unsigned blocks = grid_for(h->ncell, 256);
+      if (h->prec == PREC_F64 && dtype == GKS_F64)
+        field_kernel<double, double><<<blocks, 256, 0, h->stream>>>((const double*)h->cg.tau, (double*)dst, h->ncell);
+      else if (h->prec == PREC_F64)
+        field_kernel<double, float><<<blocks, 256, 0, h->stream>>>((const double*)h->cg.tau, (float*)dst, h->ncell);
+      else if (dtype == GKS_F64)
+        field_kernel<float, double><<<blocks, 256, 0, h->stream>>>((const float*)h->cg.tau, (double*)dst, h->ncell);
+      else
+        field_kernel<float, float><<<blocks, 256, 0, h->stream>>>((const float*)h->cg.tau, (float*)dst, h->ncell);
+    }
+  } else if (h->D == 1)
     launch_diag_d<1>(h, A, what, dst, dtype);
   else if (h->D == 2)
     launch_diag_d<2>(h, A, what, dst, dtype);
@@ -977,6 +1039,77 @@ gks_status gks_get_rarefaction(gks_handle* h, void* eps_out, int memspace, int d
 
 gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtype) {
   return get_diag(h, 0, tau_out, memspace, dtype);
+}
+
+gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
+  if (!h || !nodes) return fail(h, GKS_EINVAL, "null argument");
+  if (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE) return fail(h, GKS_EINVAL, "memspace");
+  if (h->D != 2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids are built in 2D");
+  if (h->multid) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids take the directional expansion");
+  if (h->recon != GKS_RECON_MUSCL2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids take MUSCL2 reconstruction");
+  if (h->transport) return fail(h, GKS_EUNSUPPORTED, "k-omega transport on a curvilinear grid");
+  DeviceGuard dg(h->dev);
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  free_curv(h);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  const int n0 = h->n[0], n1 = h->n[1];
+  CurvGeom& G = h->cg;
+  G.nf[0] = (long)(n0 + 1) * n1;
+  G.nf[1] = (long)n0 * (n1 + 1);
+  const size_t rb = arith_bytes(h->prec);
+  bool ok = true;
+  auto alloc = [&](void** p, size_t b) {
+    if (ok && cudaMalloc(p, b) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      ok = false;
+    }
+  };
+  for (int a = 0; a < 2; ++a) {
+    alloc(&G.face[a], rb * 8 * G.nf[a]);
+    alloc(&G.flux[a], rb * 4 * G.nf[a]);
+  }
+  alloc(&G.iarea, rb * h->ncell);
+  alloc((void**)&G.area, sizeof(double) * h->ncell);
+  alloc(&G.tau, rb * h->ncell);
+  if (!ok) {
+    free_curv(h);
+    return fail(h, GKS_ENOMEM, "curvilinear grid allocation failed");
+  }
+  const size_t nb = sizeof(double) * 2 * (size_t)(n0 + 1) * (n1 + 1);
+  gks_status st = ensure_staging(h, nb + 16);
+  if (st) {
+    free_curv(h);
+    return st;
+  }
+  const double* src = nodes;
+  if (memspace == GKS_MEM_HOST) {
+    GKS_CK(h, cudaMemcpyAsync(h->staging, nodes, nb, cudaMemcpyHostToDevice, h->stream));
+    src = (const double*)h->staging;
+  }
+  int* bad_dev = (int*)((char*)h->staging + ((nb + 7) / 8) * 8);
+  GKS_CK(h, cudaMemsetAsync(bad_dev, 0, sizeof(int), h->stream));
+  const bool periodic[2] = {h->base.g.bc[0][0] == GKS_BC_PERIODIC, h->base.g.bc[1][0] == GKS_BC_PERIODIC};
+  cudaError_t e = curv_metrics(src, n0, n1, periodic, h->prec, G, bad_dev, h->stream);
+  if (e != cudaSuccess) {
+    free_curv(h);
+    return cuda_fail(h, e, "curvilinear metrics");
+  }
+  int bad_host = 0;
+  GKS_CK(h, cudaMemcpyAsync(&bad_host, bad_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  GKS_CK(h, cudaStreamSynchronize(h->stream));
+  if (bad_host) {
+    free_curv(h);
+    return fail(h, GKS_EINVAL, "a cell is not a convex counter-clockwise quadrilateral");
+  }
+  h->curv = true;
+  h->tuned = true;  // one kernel shape; no tile autotuning
+  if (h->has_state) {
+    GKS_CK(h, cudaMemsetAsync(&h->ctrl->rate[h->step % 3], 0, sizeof(unsigned long long), h->stream));
+    return launch_rate(h);
+  }
+  return GKS_OK;
 }
 
 gks_status gks_enable_timing(gks_handle* h, int enable) {

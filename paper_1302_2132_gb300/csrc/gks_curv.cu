@@ -1,0 +1,495 @@
+// Body-fitted 2D grids with the directional expansion (the paper's C-type and channel grids,
+// Section 5, Table 2).  The cells are the quadrilaterals of a structured node lattice; each face
+// evaluates the gas-kinetic flux of Section 4 in its own (normal, tangent) frame:
+//   - metrics (once per grid, double precision): per face the unit normal n pointing to increasing
+//     index, the length L, and the distances of the face's MUSCL stencil (centroid to centroid along
+//     the grid line, centroid to face midpoint); per cell the area.  Centroids are vertex averages;
+//     a ghost centroid is its source cell translated by the period on a periodic axis, else the
+//     mirror image of the interior cell through the boundary face midpoint;
+//   - per step: the turbulent relaxation time of every cell from Green-Gauss velocity gradients
+//     (face value the mean of the two cells); the face fluxes, one thread per face: the four cells
+//     of the stencil rotated into the face frame (rho, rho u_n, rho u_t, rho E), limited slopes over
+//     the centroid distances, the flux of face_flux with the centroid-to-midpoint distances, the
+//     momentum flux rotated back and weighted by L; then the update of each cell by its four face
+//     fluxes divided by its area, the CFL rate sum_faces (|U.n| + c) L / (2 A) of the new state for
+//     the next step, the physical-state check and the residual norms.
+// Ghost cells follow the boundary rules of the index lattice (load_cell); a ghost cell's
+// turbulent relaxation time is that of its source cell.
+#include <algorithm>
+
+#include "gks_curv.h"
+#include "gks_flux.cuh"
+#include "gks_step.cuh"
+
+namespace gks {
+
+namespace {
+
+constexpr int kCurvThreads = 128;
+
+__device__ __forceinline__ double node_x(const double* nodes, int n0, int i, int j) {
+  return nodes[((long)j * (n0 + 1) + i) * 2];
+}
+__device__ __forceinline__ double node_y(const double* nodes, int n0, int i, int j) {
+  return nodes[((long)j * (n0 + 1) + i) * 2 + 1];
+}
+
+// Vertex-average centroid of interior cell (i, j).
+__device__ void centroid_in(const double* nodes, int n0, int i, int j, double& x, double& y) {
+  x = 0.25 * (node_x(nodes, n0, i, j) + node_x(nodes, n0, i + 1, j) + node_x(nodes, n0, i + 1, j + 1) +
+              node_x(nodes, n0, i, j + 1));
+  y = 0.25 * (node_y(nodes, n0, i, j) + node_y(nodes, n0, i + 1, j) + node_y(nodes, n0, i + 1, j + 1) +
+              node_y(nodes, n0, i, j + 1));
+}
+
+// Midpoint of the face between nodes (i0, j0) and (i1, j1).
+__device__ void mid(const double* nodes, int n0, int i0, int j0, int i1, int j1, double& x, double& y) {
+  x = 0.5 * (node_x(nodes, n0, i0, j0) + node_x(nodes, n0, i1, j1));
+  y = 0.5 * (node_y(nodes, n0, i0, j0) + node_y(nodes, n0, i1, j1));
+}
+
+// Centroid of cell (i, j) of a stencil along axis a: at most two layers outside the grid along a,
+// the other index inside.
+__device__ void centroid(const double* nodes, int n0, int n1, int a, bool periodic, int i, int j, double& x,
+                         double& y) {
+  const int n = a == 0 ? n0 : n1;
+  const int c = a == 0 ? i : j;
+  if (c >= 0 && c < n) {
+    centroid_in(nodes, n0, i, j, x, y);
+    return;
+  }
+  double lx, ly, hx, hy;  // midpoints of the low and high boundary faces of this grid line
+  if (a == 0) {
+    mid(nodes, n0, 0, j, 0, j + 1, lx, ly);
+    mid(nodes, n0, n0, j, n0, j + 1, hx, hy);
+  } else {
+    mid(nodes, n0, i, 0, i + 1, 0, lx, ly);
+    mid(nodes, n0, i, n1, i + 1, n1, hx, hy);
+  }
+  const bool lo = c < 0;
+  const int k = lo ? -c : c - n + 1;  // ghost layer 1 or 2
+  double sx, sy;
+  if (periodic) {
+    const int s = lo ? n - k : k - 1;
+    if (a == 0)
+      centroid_in(nodes, n0, s, j, sx, sy);
+    else
+      centroid_in(nodes, n0, i, s, sx, sy);
+    x = sx + (lo ? lx - hx : hx - lx);
+    y = sy + (lo ? ly - hy : hy - ly);
+  } else {
+    const int s = lo ? k - 1 : n - k;
+    if (a == 0)
+      centroid_in(nodes, n0, s, j, sx, sy);
+    else
+      centroid_in(nodes, n0, i, s, sx, sy);
+    x = 2.0 * (lo ? lx : hx) - sx;
+    y = 2.0 * (lo ? ly : hy) - sy;
+  }
+}
+
+__device__ __forceinline__ double dist(double ax, double ay, double bx, double by) {
+  return sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+}
+
+// Per-cell metrics: area (double and the inverse in the arithmetic type) and the convexity check.
+template <class R>
+__global__ void metrics_cell_kernel(const double* nodes, int n0, int n1, double* area, R* iarea, int* bad) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (long)n0 * n1) return;
+  const int i = (int)(c % n0), j = (int)(c / n0);
+  const double qx[4] = {node_x(nodes, n0, i, j), node_x(nodes, n0, i + 1, j), node_x(nodes, n0, i + 1, j + 1),
+                        node_x(nodes, n0, i, j + 1)};
+  const double qy[4] = {node_y(nodes, n0, i, j), node_y(nodes, n0, i + 1, j), node_y(nodes, n0, i + 1, j + 1),
+                        node_y(nodes, n0, i, j + 1)};
+  const double A = 0.5 * ((qx[2] - qx[0]) * (qy[3] - qy[1]) - (qx[3] - qx[1]) * (qy[2] - qy[0]));
+  bool ok = A > 0.0;
+  for (int q = 0; q < 4; ++q) {
+    const int a = (q + 3) % 4, b = (q + 1) % 4;
+    if (!((qx[q] - qx[a]) * (qy[b] - qy[q]) - (qy[q] - qy[a]) * (qx[b] - qx[q]) > 0.0)) ok = false;
+  }
+  if (!ok) atomicOr(bad, 1);
+  area[c] = A;
+  iarea[c] = (R)(1.0 / A);
+}
+
+// Per-face metrics along axis a, in the order of CurvGeom::face.
+template <class R>
+__global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, bool periodic, R* out, long nf) {
+  const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int nfa = a == 0 ? n0 + 1 : n0;
+  const int fi = (int)(f % nfa), fj = (int)(f / nfa);
+  // face end points: i-face from node (fi, fj) to (fi, fj + 1), j-face from (fi, fj) to (fi + 1, fj)
+  const int ei = a == 0 ? fi : fi + 1, ej = a == 0 ? fj + 1 : fj;
+  const double ex = node_x(nodes, n0, ei, ej) - node_x(nodes, n0, fi, fj);
+  const double ey = node_y(nodes, n0, ei, ej) - node_y(nodes, n0, fi, fj);
+  const double L = sqrt(ex * ex + ey * ey);
+  const double nx = a == 0 ? ey / L : -ey / L, ny = a == 0 ? -ex / L : ex / L;
+  double mx, my;
+  mid(nodes, n0, fi, fj, ei, ej, mx, my);
+  double cx[4], cy[4];
+  for (int s = 0; s < 4; ++s) {
+    const int ci = a == 0 ? fi - 2 + s : fi, cj = a == 0 ? fj : fj - 2 + s;
+    centroid(nodes, n0, n1, a, periodic, ci, cj, cx[s], cy[s]);
+  }
+  const double g[8] = {nx,
+                       ny,
+                       L,
+                       1.0 / dist(cx[0], cy[0], cx[1], cy[1]),
+                       1.0 / dist(cx[1], cy[1], cx[2], cy[2]),
+                       1.0 / dist(cx[2], cy[2], cx[3], cy[3]),
+                       dist(mx, my, cx[1], cy[1]),
+                       dist(mx, my, cx[2], cy[2])};
+  for (int q = 0; q < 8; ++q) out[(long)q * nf + f] = (R)g[q];
+}
+
+template <class R>
+struct FaceView {
+  const R* p;
+  long nf;
+  __device__ __forceinline__ R operator()(int q, long f) const { return p[(long)q * nf + f]; }
+};
+
+// Turbulent relaxation time of every cell from Green-Gauss velocity gradients.
+template <int PREC>
+__global__ void __launch_bounds__(kCurvThreads) curv_tau_kernel(const __grid_constant__ StepArgs A,
+                                                                const __grid_constant__ CurvGeom G, void* tau_out) {
+  using R = typename PrecT<PREC>::R;
+  const DevGrid& g = A.g;
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const Consts<R> kc = make_consts<R>(g);
+  const int n0 = g.n[0];
+  const int i = (int)(c % n0), j = (int)(c / n0);
+  R w[4];
+  load_stored<2, PREC>(g, A.Win, c, w);
+  const R p = pressure_of<R>(2, kc.gamma, w);
+  const R f1 = ((const R*)A.f1)[c];
+  R t = R(0);
+  if (g.turb_model == TURB_MUT) {
+    t = g_div(f1, p);
+  } else {
+    const R f2 = ((const R*)A.f2)[c];
+    const FaceView<R> fi{(const R*)G.face[0], G.nf[0]}, fj{(const R*)G.face[1], G.nf[1]};
+    const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+    const long fid[4] = {fa, fa + 1, fc, fc + n0};
+    const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+    const R ir = g_rcp(w[0]);
+    const R U[2] = {w[1] * ir, w[2] * ir};
+    R gr[2][2] = {{R(0), R(0)}, {R(0), R(0)}};  // gr[a][b] = area * dU_b/dx_a
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      R wn[4];
+      load_cell<2, PREC>(g, A.Win, kc, nb[q][0], nb[q][1], 0, wn);
+      const FaceView<R>& fv = q < 2 ? fi : fj;
+      const R nx = fv(0, fid[q]), ny = fv(1, fid[q]), L = fv(2, fid[q]);
+      const R sgn = (q & 1) ? R(1) : R(-1);
+      const R irn = g_rcp(wn[0]);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const R uf = R(0.5) * (U[b] + wn[1 + b] * irn);
+        gr[0][b] += sgn * uf * nx * L;
+        gr[1][b] += sgn * uf * ny * L;
+      }
+    }
+    const R ia = ((const R*)G.iarea)[c];
+    R s2 = R(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const R sab = R(0.5) * (gr[a][b] + gr[b][a]) * ia;
+        s2 += sab * sab;
+      }
+    const R S = g_sqrt(R(2) * s2);
+    R nu, eta;
+    if (g.turb_model == TURB_KEPS) {
+      nu = g_div(kc.C_mu * f1 * f1, f2);
+      eta = g_div(S * f1, f2);
+    } else {
+      nu = g_div(f1, f2);
+      eta = g_div(S, kc.beta_star * f2);
+    }
+    t = (f1 > R(0) && f2 > R(0)) ? g_div(w[0] * nu, p * g_sqrt(R(1) + eta * eta)) : R(0);
+  }
+  ((R*)tau_out)[c] = t;
+}
+
+// Face fluxes times face length, one thread per face; i-faces then j-faces in one launch.
+template <int PREC>
+__global__ void __launch_bounds__(kCurvThreads, PREC == PREC_F64 ? 1 : 4)
+    curv_face_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CurvGeom G) {
+  using R = typename PrecT<PREC>::R;
+  const DevGrid& g = A.g;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    const double dtv = step_dt(A);
+    Ctrl* c = A.ctrl;
+    c->t[A.tslot ^ 1] = c->t[A.tslot] + dtv;
+    c->rate[(A.slot + 2) % 3] = 0ull;
+    c->last_dt = dtv;
+  }
+  const long nf0 = G.nf[0], nf1 = G.nf[1];
+  if (t >= nf0 + nf1) return;
+  const int a = t < nf0 ? 0 : 1;
+  const long f = a == 0 ? t : t - nf0;
+  const int n0 = g.n[0];
+  const int nfa = a == 0 ? n0 + 1 : n0;
+  const int fi = (int)(f % nfa), fj = (int)(f / nfa);
+  R* Fo = (R*)G.flux[a];
+  const long nf = a == 0 ? nf0 : nf1;
+  const double dt_d = step_dt(A);
+  if (dt_d == 0.0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Fo[(long)v * nf + f] = R(0);
+    return;
+  }
+  const R dt = (R)dt_d;
+  const Consts<R> kc = make_consts<R>(g);
+  const FaceView<R> fv{(const R*)G.face[a], nf};
+  const R nx = fv(0, f), ny = fv(1, f), L = fv(2, f);
+  const R i01 = fv(3, f), i12 = fv(4, f), i23 = fv(5, f), dl = fv(6, f), dr = fv(7, f);
+  R S4[4][4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int ci = a == 0 ? fi - 2 + s : fi, cj = a == 0 ? fj : fj - 2 + s;
+    R w[4];
+    load_cell<2, PREC>(g, A.Win, kc, ci, cj, 0, w);
+    S4[s][0] = w[0];
+    S4[s][1] = w[1] * nx + w[2] * ny;
+    S4[s][2] = -w[1] * ny + w[2] * nx;
+    S4[s][3] = w[3];
+  }
+  R wl[4], wr[4], cl[4], cr[4], sl[4], sr[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const R dm = (S4[1][v] - S4[0][v]) * i01, dc = (S4[2][v] - S4[1][v]) * i12, dp = (S4[3][v] - S4[2][v]) * i23;
+    sl[v] = limiter<R>(g.limiter, dm, dc);
+    sr[v] = limiter<R>(g.limiter, dc, dp);
+    wl[v] = S4[1][v] + dl * sl[v];
+    wr[v] = S4[2][v] - dr * sr[v];
+    cl[v] = S4[1][v];
+    cr[v] = S4[2][v];
+  }
+  if (!physical<2, R>(kc.gamma, wl))
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      wl[v] = cl[v];
+      sl[v] = R(0);
+    }
+  if (!physical<2, R>(kc.gamma, wr))
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      wr[v] = cr[v];
+      sr[v] = R(0);
+    }
+  R tau_t = R(0);
+  if (g.turb_model != TURB_NONE) {
+    const R* tc = (const R*)G.tau;
+    const int li = a == 0 ? fi - 1 : fi, lj = a == 0 ? fj : fj - 1;
+    const int ri = a == 0 ? fi : fi, rj = a == 0 ? fj : fj;
+    tau_t = R(0.5) * (tc[field_cell(g, 2, li, lj, 0)] + tc[field_cell(g, 2, ri, rj, 0)]);
+  }
+  Gas<R> gas;
+  gas.bK = kc.bK;
+  gas.K = kc.K;
+  gas.mu = kc.mu;
+  gas.C_a = kc.C_a;
+  const R tl[1][4] = {{R(0), R(0), R(0), R(0)}}, tr[1][4] = {{R(0), R(0), R(0), R(0)}};
+  R F[4], tau;
+  face_flux<2, R, false>(wl, wr, cl, cr, sl, sr, tl, tr, dl, dr, tau_t, dt, gas, g.abar_t0, F, &tau);
+  Fo[f] = F[0] * L;
+  Fo[nf + f] = (F[1] * nx - F[2] * ny) * L;
+  Fo[2 * nf + f] = (F[1] * ny + F[2] * nx) * L;
+  Fo[3 * nf + f] = F[3] * L;
+}
+
+// CFL rate of a cell on the curvilinear grid: sum over its faces of (|U.n| + c) L / (2 A).
+template <class R>
+__device__ __forceinline__ R curv_rate(const R* w, R gamma, const CurvGeom& G, int n0, int i, int j, long c) {
+  const FaceView<R> fi{(const R*)G.face[0], G.nf[0]}, fj{(const R*)G.face[1], G.nf[1]};
+  const R ir = g_rcp(w[0]);
+  const R u = w[1] * ir, v = w[2] * ir;
+  const R p = pressure_of<R>(2, gamma, w);
+  const R cs = g_sqrt(g_div(gamma * p, w[0]));
+  const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+  R r = R(0);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    r += (g_abs(u * fi(0, fa + s) + v * fi(1, fa + s)) + cs) * fi(2, fa + s);
+    r += (g_abs(u * fj(0, fc + s * n0) + v * fj(1, fc + s * n0)) + cs) * fj(2, fc + s * n0);
+  }
+  return R(0.5) * r * ((const R*)G.iarea)[c];
+}
+
+// Conservative update, next CFL rate, physical check and residual norms.
+template <int PREC>
+__global__ void __launch_bounds__(kCurvThreads) curv_update_kernel(const __grid_constant__ StepArgs A,
+                                                                   const __grid_constant__ CurvGeom G) {
+  using R = typename PrecT<PREC>::R;
+  using S = typename PrecT<PREC>::S;
+  __shared__ double red[kMaxWarps];
+  const DevGrid& g = A.g;
+  const int tid = threadIdx.x;
+  const long c = (long)blockIdx.x * blockDim.x + tid;
+  const double dt_d = A.ctrl->last_dt;
+  const int n0 = g.n[0];
+  const bool active = c < g.ncell;
+  if (dt_d == 0.0) {  // t_end reached: carry the state over
+    if (active)
+      for (int v = 0; v < 4; ++v) {
+        ((S*)A.Wout)[(long)v * g.ncell + c] = ((const S*)A.Win)[(long)v * g.ncell + c];
+        if (PREC == PREC_F32) A.Wout_lo[(long)v * g.ncell + c] = A.Win_lo[(long)v * g.ncell + c];
+      }
+    return;
+  }
+  const Consts<R> kc = make_consts<R>(g);
+  R rmax = R(0);
+  unsigned bad = 0u;
+  double racc[15];
+  for (int q = 0; q < 15; ++q) racc[q] = 0.0;
+  if (active) {
+    const int i = (int)(c % n0), j = (int)(c / n0);
+    const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+    const R* Fi = (const R*)G.flux[0];
+    const R* Fj = (const R*)G.flux[1];
+    const long nf0 = G.nf[0], nf1 = G.nf[1];
+    R wn[4];
+    for (int v = 0; v < 4; ++v) {
+      const R net = Fi[v * nf0 + fa + 1] - Fi[v * nf0 + fa] + Fj[v * nf1 + fc + n0] - Fj[v * nf1 + fc];
+      const long gidx = (long)v * g.ncell + c;
+      double wd;
+      if (PREC == PREC_F64) {
+        const double w_old = ((const double*)A.Win)[gidx];
+        const double w = w_old - (double)net / G.area[c];
+        ((double*)A.Wout)[gidx] = w;
+        wn[v] = (R)w;
+        wd = w;
+        if (A.resid) {
+          const double r = (w - w_old) / dt_d;
+          racc[v] += r * r;
+          racc[5 + v] = fmax(racc[5 + v], fabs(r));
+        }
+      } else {
+        const R inc = -net * ((const R*)G.iarea)[c];
+        if (PREC == PREC_F32) {
+          const float hi = ((const float*)A.Win)[gidx], lo = A.Win_lo[gidx];
+          const float s = hi + inc;
+          const float bb = s - hi;
+          const float err = (hi - (s - bb)) + (inc - bb);
+          const float lo2 = lo + err;
+          const float nhi = s + lo2;
+          const float nlo = lo2 - (nhi - s);
+          ((float*)A.Wout)[gidx] = nhi;
+          A.Wout_lo[gidx] = nlo;
+          wn[v] = nhi;
+          wd = (double)nhi + (double)nlo;
+        } else {
+          const double w = ((const double*)A.Win)[gidx] + (double)inc;
+          ((double*)A.Wout)[gidx] = w;
+          wn[v] = (R)w;
+          wd = w;
+        }
+        if (A.resid) {
+          const double r = (double)inc / dt_d;
+          racc[v] += r * r;
+          racc[5 + v] = fmax(racc[5 + v], fabs(r));
+        }
+      }
+      if (A.resid) racc[10 + v] += wd * G.area[c];
+    }
+    if (!physical<2, R>(kc.gamma, wn)) bad = 1u;
+    rmax = curv_rate<R>(wn, kc.gamma, G, n0, i, j, c);
+  }
+  const unsigned long long bmax = block_max_rate<R>(rmax, red);
+  if (tid == 0) atomicMax(&A.ctrl->rate[(A.slot + 1) % 3], bmax);
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(&A.ctrl->status, 1u);
+  if (A.resid) {
+    for (int v = 0; v < 4; ++v) {
+      double s = block_sum(racc[v], red);
+      if (tid == 0) atomicAdd(&A.ctrl->l2[v], s);
+      s = block_sum(racc[10 + v], red);
+      if (tid == 0) atomicAdd(&A.ctrl->total[v], s);
+      const double m = block_max<double>(racc[5 + v], red);
+      if (tid == 0) atomic_max_nonneg(&A.ctrl->linf[v], m);
+    }
+  }
+}
+
+// CFL rate of the stored state into ctrl->rate[slot].
+template <int PREC>
+__global__ void __launch_bounds__(kCurvThreads) curv_rate_kernel(const __grid_constant__ StepArgs A,
+                                                                 const __grid_constant__ CurvGeom G) {
+  using R = typename PrecT<PREC>::R;
+  __shared__ double red[kMaxWarps];
+  const DevGrid& g = A.g;
+  const Consts<R> kc = make_consts<R>(g);
+  R rmax = R(0);
+  for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += (long)gridDim.x * blockDim.x) {
+    R w[4];
+    load_stored<2, PREC>(g, A.Win, c, w);
+    rmax = fmax(rmax, curv_rate<R>(w, kc.gamma, G, g.n[0], (int)(c % g.n[0]), (int)(c / g.n[0]), c));
+  }
+  const double m = block_max<double>((double)rmax, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(&A.ctrl->rate[A.slot], m);
+}
+
+inline unsigned blocks_for(long n) { return (unsigned)((n + kCurvThreads - 1) / kCurvThreads); }
+
+template <int PREC>
+void step_prec(const StepArgs& A, const CurvGeom& G, cudaStream_t s) {
+  if (A.g.turb_model != TURB_NONE)
+    curv_tau_kernel<PREC><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, G.tau);
+  curv_face_kernel<PREC><<<blocks_for(G.nf[0] + G.nf[1]), kCurvThreads, 0, s>>>(A, G);
+  curv_update_kernel<PREC><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G);
+}
+
+}  // namespace
+
+cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int prec, CurvGeom& G,
+                         int* bad, cudaStream_t s) {
+  const long nc = (long)n0 * n1;
+  if (prec == PREC_F64) {
+    metrics_cell_kernel<double><<<blocks_for(nc), kCurvThreads, 0, s>>>(nodes, n0, n1, G.area, (double*)G.iarea, bad);
+    for (int a = 0; a < 2; ++a)
+      metrics_face_kernel<double><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a],
+                                                                               (double*)G.face[a], G.nf[a]);
+  } else {
+    metrics_cell_kernel<float><<<blocks_for(nc), kCurvThreads, 0, s>>>(nodes, n0, n1, G.area, (float*)G.iarea, bad);
+    for (int a = 0; a < 2; ++a)
+      metrics_face_kernel<float><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a],
+                                                                             (float*)G.face[a], G.nf[a]);
+  }
+  return cudaGetLastError();
+}
+
+void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s) {
+  if (prec == PREC_F64)
+    step_prec<PREC_F64>(A, G, s);
+  else if (prec == PREC_F32)
+    step_prec<PREC_F32>(A, G, s);
+  else
+    step_prec<PREC_F32D>(A, G, s);
+}
+
+void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s) {
+  const unsigned blocks = std::min<unsigned>(blocks_for(A.g.ncell), 152u * 16u);
+  if (prec == PREC_F64)
+    curv_rate_kernel<PREC_F64><<<blocks, kCurvThreads, 0, s>>>(A, G);
+  else if (prec == PREC_F32)
+    curv_rate_kernel<PREC_F32><<<blocks, kCurvThreads, 0, s>>>(A, G);
+  else
+    curv_rate_kernel<PREC_F32D><<<blocks, kCurvThreads, 0, s>>>(A, G);
+}
+
+void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s) {
+  if (prec == PREC_F64)
+    curv_tau_kernel<PREC_F64><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out);
+  else if (prec == PREC_F32)
+    curv_tau_kernel<PREC_F32><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out);
+  else
+    curv_tau_kernel<PREC_F32D><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out);
+}
+
+}  // namespace gks

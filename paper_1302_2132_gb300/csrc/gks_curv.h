@@ -1,0 +1,30 @@
+// Body-fitted 2D grids (gks_curv.cu): device metrics and the step kernels of the directional
+// expansion in each face's (normal, tangent) frame.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gks {
+
+struct StepArgs;
+
+// Device buffers of a curvilinear grid, owned by the handle.
+struct CurvGeom {
+  long nf[2];     // faces per axis: (n0 + 1) n1 i-faces (x fastest), n0 (n1 + 1) j-faces
+  void* face[2];  // per axis [8][nf], arithmetic type: n_x, n_y, L, 1/d01, 1/d12, 1/d23, d_l, d_r
+                  // (d01, d12, d23 the centroid distances of the four-cell stencil along the grid
+                  // line, d_l, d_r the distances from the two adjacent centroids to the face midpoint)
+  void* iarea;    // 1 / area per cell, arithmetic type
+  double* area;   // area per cell
+  void* tau;      // per-cell turbulent relaxation time of the current step, arithmetic type
+  void* flux[2];  // per axis [4][nf]: time-integrated face flux times face length, arithmetic type
+};
+
+// Metrics from nodes[(n1 + 1)][(n0 + 1)][2] (device, double); *bad (device) is or-ed with 1 if a
+// cell is not a convex counter-clockwise quadrilateral.
+cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int prec, CurvGeom& G,
+                         int* bad, cudaStream_t s);
+void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
+void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
+void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s);
+
+}  // namespace gks

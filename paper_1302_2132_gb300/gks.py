@@ -71,6 +71,7 @@ def load():
     L.gks_set_state.argtypes = [H, _V, _I, _I, _I]
     L.gks_get_state.argtypes = [H, _V, _I, _I, _I]
     L.gks_set_turbulence.argtypes = [H, _V, _V, _I, _I]
+    L.gks_set_nodes.argtypes = [H, _V, _I]
     L.gks_compute_dt.argtypes = [H, _D, _PD]
     L.gks_step.argtypes = [H, _D, _D, _I, _D]
     L.gks_get_time.argtypes = [H, _PD, ctypes.POINTER(ctypes.c_longlong)]
@@ -229,6 +230,20 @@ class Solver:
             assert (mem2, dt2) == (mem, dt)
         self._check(load().gks_set_turbulence(self._h, p1, p2, mem, dt))
         del keep
+        self.stream.synchronize()
+
+    def set_nodes(self, nodes):
+        """Make the grid body-fitted: nodes[(n1 + 1), (n0 + 1), 2] = (x, y), double, host array or
+        CUDA tensor (2D, directional expansion, MUSCL2)."""
+        if _is_torch(nodes):
+            assert nodes.dtype.is_floating_point and nodes.element_size() == 8
+        else:
+            nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        p, mem, dt = self._ptr(nodes)
+        assert dt == F64
+        n0, n1 = self.n[0], self.n[1]
+        assert int(np.prod(nodes.shape)) == 2 * (n0 + 1) * (n1 + 1)
+        self._check(load().gks_set_nodes(self._h, p, mem))
         self.stream.synchronize()
 
     def get_state(self, layout="soa_cons", out=None, dtype=np.float64):

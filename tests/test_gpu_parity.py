@@ -387,3 +387,24 @@ def test_3d_tile_variants_agree(monkeypatch):
         s.close()
     for W in out[1:]:
         assert np.all(rel_err_per_var(W, out[0], 5) < 1e-6)
+
+
+def test_steps_continue_after_t_end():
+    """A run stopped by t_end (the last steps carry the state over) continues with the CFL time step
+    of the stored state: the next step equals the oracle's step from that state."""
+    spec = inputs.turbulence(40, 2, seed=17)
+    s = gpu_solver(spec, turb_model=2, mu=1e-5)
+    c = oracle_case(spec, turb_model=2, mu=1e-5)
+    s.set_state(spec["prim"].ravel(), layout="soa_prim")
+    s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+    s.step(nsteps=50, cfl=0.5, t_end=0.01)
+    t, _ = s.time()
+    assert abs(t - 0.01) < 1e-15
+    W = s.get_state()
+    dt_o = c.compute_dt(W, 0.5)
+    assert abs(s.compute_dt(0.5) - dt_o) <= 1e-14 * dt_o
+    s.step(nsteps=1, cfl=0.5)
+    Wo, st, _ = c.step(W, dt_o, f1=spec["f1"].ravel(), f2=spec["f2"].ravel(), nthreads=8)
+    assert st == 0
+    assert np.all(rel_err_per_var(s.get_state(), Wo, 4) < 1e-12)
+    s.close()
