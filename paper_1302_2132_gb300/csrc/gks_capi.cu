@@ -182,6 +182,10 @@ int tiles_for(const gks_handle* h, int variant) {
 }
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
+  if (h->curv) {
+    launch_curv_step(h->prec, A, h->cg, variant, h->stream);
+    return;
+  }
   if (h->recon == GKS_RECON_MUSCL3) {
     launch_step_muscl3(h->D, h->prec, h->multid, variant, A, tiles_for(h, variant), h->stream);
     return;
@@ -207,10 +211,6 @@ void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
 // One full step: the flow step and, with k-omega transport, the transport step of rho k and
 // rho omega (into the other buffer pair) with the same dt and the flow step's mass fluxes.
 void launch_step(gks_handle* h, const StepArgs& A) {
-  if (h->curv) {
-    launch_curv_step(h->prec, A, h->cg, h->stream);
-    return;
-  }
   launch_step_variant(h, A, h->tile_variant);
   if (!h->transport) return;
   const int cur = A.Win == h->W[0] ? 0 : 1;
@@ -329,6 +329,10 @@ void free_curv(gks_handle* h) {
   if (G.area) cudaFree(G.area);
   if (G.tau) cudaFree(G.tau);
   G = CurvGeom{};
+  if (h->curv) {  // back to the rectilinear step: its tile shape is chosen again
+    h->tile_variant = 0;
+    h->tuned = false;
+  }
   h->curv = false;
 }
 
@@ -383,6 +387,10 @@ std::mutex g_tuned_mutex;
 // Tile variants the autotuner tries for a handle (variant indices of tile_shape).
 std::vector<int> tile_candidates(const gks_handle* h) {
   std::vector<int> c;
+  if (h->curv) {
+    for (int v = 0; v < kCurvVariants; ++v) c.push_back(v);
+    return c;
+  }
   if (h->recon != GKS_RECON_MUSCL2) {
     c.push_back(0);
     if (h->D == 2 && h->prec == PREC_F32 && h->multid) c.push_back(3);  // 32 x 27 (four full waves at 1024^2)
@@ -396,6 +404,7 @@ std::vector<int> tile_candidates(const gks_handle* h) {
 }
 
 int n_variants(const gks_handle* h) {
+  if (h->curv) return kCurvVariants;
   if (h->recon != GKS_RECON_MUSCL2) return (int)tile_candidates(h).size();
   if (h->D == 1) return kTileVariants1D;
   if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
@@ -414,7 +423,7 @@ gks_status autotune(gks_handle* h) {
       if (c == v) h->tile_variant = v;
     return GKS_OK;
   }
-  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, (int)h->multid};
+  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, h->curv ? 2 : (int)h->multid};
   {
     std::lock_guard<std::mutex> lk(g_tuned_mutex);
     auto it = g_tuned.find(key);
@@ -532,6 +541,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   if (!prepared[D]) {
     cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
     if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
+    if (e == cudaSuccess && D == 2) e = prepare_curv();
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess) e = prepare_komega();
@@ -1104,7 +1114,8 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
     return fail(h, GKS_EINVAL, "a cell is not a convex counter-clockwise quadrilateral");
   }
   h->curv = true;
-  h->tuned = true;  // one kernel shape; no tile autotuning
+  h->tile_variant = 0;
+  h->tuned = false;  // the tile shape of the curvilinear step is chosen at the first step
   if (h->has_state) {
     GKS_CK(h, cudaMemsetAsync(&h->ctrl->rate[h->step % 3], 0, sizeof(unsigned long long), h->stream));
     return launch_rate(h);
@@ -1140,7 +1151,12 @@ gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches)
 gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz) {
   if (!h) return GKS_EINVAL;
   int t[3];
-  tile_shape(h->D, h->tile_variant, &t[0], &t[1], &t[2]);
+  if (h->curv) {
+    curv_tile_shape(h->tile_variant, &t[0], &t[1]);
+    t[2] = 1;
+  } else {
+    tile_shape(h->D, h->tile_variant, &t[0], &t[1], &t[2]);
+  }
   if (variant) *variant = h->tile_variant;
   if (tx) *tx = t[0];
   if (ty) *ty = t[1];

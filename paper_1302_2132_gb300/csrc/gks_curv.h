@@ -23,7 +23,11 @@ struct CurvGeom {
 // cell is not a convex counter-clockwise quadrilateral.
 cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int prec, CurvGeom& G,
                          int* bad, cudaStream_t s);
-void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
+// The fused tile step (variant 0: 32 x 15 cells, 256 threads; variant 1: 16 x 7, 128 threads).
+cudaError_t prepare_curv();
+void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s);
+void curv_tile_shape(int variant, int* x, int* y);
+constexpr int kCurvVariants = 2;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
 void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s);
 
