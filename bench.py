@@ -332,8 +332,7 @@ def run_ours(args):
     if args.reconstruction != "muscl2":
         workload_name += "_" + args.reconstruction
     tile = solver.tile_shape()
-    tile_info = ({"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"} if not curv
-                 else {"threads_per_block": 128, "form": "one thread per face / per cell"})
+    tile_info = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
     line = {
         "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
         "value": value,
@@ -361,8 +360,7 @@ def run_ours(args):
                      "kernel": (("step_kernel<%d, %s, %s>%s" % (D, prec_name, "multid" if multid else "directional",
                                                                  " + komega_kernel (timed together)" if transport
                                                                  else "")) if not curv else
-                                "curv_tau_kernel + curv_face_kernel + curv_update_kernel<%s> (timed together)"
-                                % prec_name),
+                                "curv_step_kernel<%s, variant %d>" % (prec_name, tile[0])),
                      "avg_launch_us": avg_launch_s * 1e6,
                      "ops_per_face": per_face, "ops_per_cell": per_cell,
                      "peak_basis": "152 SMs x %d %s lanes x 2 (FMA) x 2070 MHz (derived)" % (lanes, "FP64" if fp64
