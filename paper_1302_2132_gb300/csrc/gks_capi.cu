@@ -372,9 +372,10 @@ gks_status sticky_status(gks_handle* h) {
   return GKS_OK;
 }
 
-// Tile-shape autotuner (2D FP32): each variant runs the step that is about to be taken three times
-// from the current state (the results are identical, and the step is then taken for real), timed
-// with CUDA events; the fastest is kept for the handle and for later handles of the same shape.
+// Tile-shape autotuner: each candidate shape runs the step that is about to be taken from the current
+// state (the results are identical, and the step is then taken for real) five times, round robin
+// over the shapes, each launch timed with CUDA events; the shape with the fastest launch is kept for
+// the handle and for later handles of the same grid.
 struct TuneKey {
   int n0, n1, multid;
   bool operator<(const TuneKey& o) const {
@@ -436,21 +437,28 @@ gks_status autotune(gks_handle* h) {
   GKS_CK(h, cudaEventCreate(&e0));
   GKS_CK(h, cudaEventCreate(&e1));
   const StepArgs A = step_args(h, h->step, 0);
-  float best = 1e30f;
-  int best_v = 0;
-  for (int v : tile_candidates(h)) {
-    launch_step_variant(h, A, v);  // warm-up
-    GKS_CK(h, cudaEventRecord(e0, h->stream));
-    for (int r = 0; r < 3; ++r) launch_step_variant(h, A, v);
-    GKS_CK(h, cudaEventRecord(e1, h->stream));
-    GKS_CK(h, cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    GKS_CK(h, cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      best_v = v;
+  const std::vector<int> cand = tile_candidates(h);
+  std::vector<float> fastest(cand.size(), 1e30f);
+  for (int v : cand) launch_step_variant(h, A, v);  // warm-up
+  // round robin, each launch timed alone, the fastest launch of each shape kept: a clock that is
+  // still ramping up penalises no shape in particular
+  for (int r = 0; r < 5; ++r)
+    for (size_t k = 0; k < cand.size(); ++k) {
+      GKS_CK(h, cudaEventRecord(e0, h->stream));
+      launch_step_variant(h, A, cand[k]);
+      GKS_CK(h, cudaEventRecord(e1, h->stream));
+      GKS_CK(h, cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      GKS_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+      fastest[k] = std::min(fastest[k], ms);
     }
-  }
+  int best_v = cand[0];
+  float best = fastest[0];
+  for (size_t k = 1; k < cand.size(); ++k)
+    if (fastest[k] < best) {
+      best = fastest[k];
+      best_v = cand[k];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the trials max-wrote the next step's CFL-rate slot: clear it so that the real step alone sets it
