@@ -134,6 +134,9 @@ def lib():
             L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
             L.orc_step_curv.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I]
             L.orc_compute_dt_curv.argtypes = [P, _PD, _PD, _D, _PD]
+            L.orc_steady_residual.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I, _PD, _PD, _I]
+            L.orc_lusgs.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD, _I, _I, _PD]
+            L.orc_steady_cycle.argtypes = [P, _PD, _PD, _PD, _PD, _D, _D, _I, _I, _I, _I, _PD]
             L.orc_komega_defaults.argtypes = [ctypes.POINTER(KOmega)]
             L.orc_step_komega.argtypes = [P, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _I]
             _lib = L
@@ -359,6 +362,44 @@ class Case:
         st = lib().orc_compute_dt_curv(ctypes.byref(self.P), _ptr(nodes), _ptr(W), cfl, ctypes.byref(dt))
         assert st == 0
         return dt.value
+
+
+    def steady_residual(self, nodes, W, cfl_flux=0.5, first_order=False, f1=None, f2=None, nthreads=1):
+        """Local explicit steps (CFL 1) and the steady residual (flux rates over the face windows
+        cfl_flux min(dt_l, dt_r), times face length, outward) on a curvilinear grid: (dt_cell, R)."""
+        nodes = self._nodes(nodes)
+        W = self._state(W)
+        dtc = np.zeros(self.ncell)
+        R = np.zeros(self.nv * self.ncell)
+        st = lib().orc_steady_residual(ctypes.byref(self.P), _ptr(nodes), _ptr(W), _ptr(self._field(f1)),
+                                       _ptr(self._field(f2)), cfl_flux, int(first_order), _ptr(dtc), _ptr(R),
+                                       nthreads)
+        assert st == 0, st
+        return dtc, R
+
+    def lusgs(self, nodes, W, dt_cell, R, tiles=(32, 32), f1=None, f2=None):
+        """The LU-SGS increment of residual R with local steps dt_cell, tile by tile."""
+        nodes = self._nodes(nodes)
+        W = self._state(W)
+        dtc = np.ascontiguousarray(dt_cell, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        dW = np.zeros(self.nv * self.ncell)
+        st = lib().orc_lusgs(ctypes.byref(self.P), _ptr(nodes), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)),
+                             _ptr(dtc), _ptr(R), int(tiles[0]), int(tiles[1]), _ptr(dW))
+        assert st == 0, st
+        return dW
+
+    def steady_cycle(self, nodes, W, cfl, cfl_flux=0.5, levels=4, tiles=(32, 32), f1=None, f2=None, nthreads=1):
+        """One FAS multigrid cycle with LU-SGS smoothing (pseudo-time steps cfl times the local explicit
+        steps); returns (W, residual before the cycle, status)."""
+        nodes = self._nodes(nodes)
+        W = self._state(W).copy()
+        res = ctypes.c_double()
+        st = lib().orc_steady_cycle(ctypes.byref(self.P), _ptr(nodes), _ptr(W), _ptr(self._field(f1)),
+                                    _ptr(self._field(f2)), cfl, cfl_flux, int(levels), int(tiles[0]), int(tiles[1]),
+                                    nthreads,
+                                    ctypes.byref(res))
+        return W, res.value, st
 
 
 def komega_defaults(**over):

@@ -37,6 +37,8 @@
  *     face or translated by the period); the face flux is weighted by the face length and the
  *     update divided by the cell area; tau_t takes Green-Gauss velocity gradients (face value the
  *     mean of the two cells) and a ghost cell the value of its source cell.
+ *   - Steady-state solver (Section 4 names local time stepping, LU-SGS after Yoon and Jameson and
+ *     4-level multigrid without formulas): see the block before curv_lts.
  */
 #include "gks_oracle.h"
 
@@ -1333,52 +1335,46 @@ double cdist(const CurvGeom& g, int i0, int j0, int i1, int j1) {
   return std::sqrt(dx * dx + dy * dy);
 }
 
-}  // namespace
+// Everything a curvilinear step or steady residual needs: geometry, the state with ghost cells,
+// tau_t per interior cell.
+struct CurvCtx {
+  const orc_problem* P;
+  CurvGeom g;
+  Grid G;
+  std::vector<double> Wp, taut;
+  // tau_t of a (possibly ghost) cell: a ghost cell takes its source cell's value
+  double tau_of(int i, int j) const {
+    const int n0 = g.n0, n1 = g.n1;
+    if (P->bc[0][0] == ORC_BC_PERIODIC) i = (i + n0) % n0; else i = std::min(std::max(i, 0), n0 - 1);
+    if (P->bc[1][0] == ORC_BC_PERIODIC) j = (j + n1) % n1; else j = std::min(std::max(j, 0), n1 - 1);
+    return taut[(long)j * n0 + i];
+  }
+  long src(int i, int j) const {  // source cell of a ghost (the cell itself inside)
+    const int n0 = g.n0, n1 = g.n1;
+    if (P->bc[0][0] == ORC_BC_PERIODIC) i = (i + n0) % n0; else i = std::min(std::max(i, 0), n0 - 1);
+    if (P->bc[1][0] == ORC_BC_PERIODIC) j = (j + n1) % n1; else j = std::min(std::max(j, 0), n1 - 1);
+    return (long)j * n0 + i;
+  }
+};
 
-extern "C" {
-
-int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt) {
-  if (P->dim != 2) return 1;
-  const CurvGeom g = curv_geometry(P, nodes);
-  if (!curv_valid(g)) return 2;
+int curv_prepare(const orc_problem* P, const double* nodes, const double* W, const double* f1, const double* f2,
+                 CurvCtx& C) {
+  if (P->dim != 2 || P->recon != ORC_RECON_MUSCL2) return 1;
+  C.P = P;
+  C.g = curv_geometry(P, nodes);
+  if (!curv_valid(C.g)) return 2;
+  C.G = make_grid(P);
+  const CurvGeom& g = C.g;
+  const Grid& G = C.G;
   const int n0 = g.n0, n1 = g.n1;
   const long ncell = (long)n0 * n1;
-  double rmax = 0.0;
-  for (int j = 0; j < n1; ++j)
-    for (int i = 0; i < n0; ++i) {
-      const long c = (long)j * n0 + i;
-      double w[4];
-      for (int v = 0; v < 4; ++v) w[v] = W[v * ncell + c];
-      const double p = pressure(2, P->gamma, w), cs = std::sqrt(P->gamma * p / w[0]);
-      const double u = w[1] / w[0], v = w[2] / w[0];
-      const long fi[2] = {(long)j * (n0 + 1) + i, (long)j * (n0 + 1) + i + 1};
-      const long fj[2] = {(long)j * n0 + i, (long)(j + 1) * n0 + i};
-      double r = 0.0;
-      for (int s = 0; s < 2; ++s) {
-        r += (std::fabs(u * g.inx[fi[s]] + v * g.iny[fi[s]]) + cs) * g.iL[fi[s]];
-        r += (std::fabs(u * g.jnx[fj[s]] + v * g.jny[fj[s]]) + cs) * g.jL[fj[s]];
-      }
-      rmax = std::max(rmax, r / (2.0 * g.area[c]));
-    }
-  *dt = cfl / rmax;
-  return 0;
-}
-
-int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
-                  double dt, int nthreads) {
-  if (P->dim != 2 || P->recon != ORC_RECON_MUSCL2) return 1;
-  const CurvGeom g = curv_geometry(P, nodes);
-  if (!curv_valid(g)) return 2;
-  Grid G = make_grid(P);
-  const int n0 = g.n0, n1 = g.n1, nv = 4;
-  const long ncell = (long)n0 * n1;
-  std::vector<double> Wp;
-  pad_state(G, W, Wp);
-  fill_ghosts(P, G, Wp);
+  pad_state(G, W, C.Wp);
+  fill_ghosts(P, G, C.Wp);
+  const std::vector<double>& Wp = C.Wp;
   std::vector<double> f1p = pad_scalar(P, G, f1), f2p = pad_scalar(P, G, f2);
-  // turbulent relaxation time per cell from Green-Gauss velocity gradients; ghosts take the
-  // value of their source cell
-  std::vector<double> taut(ncell, 0.0);
+  // turbulent relaxation time per cell from Green-Gauss velocity gradients
+  std::vector<double>& taut = C.taut;
+  taut.assign(ncell, 0.0);
   if (P->turb_model != ORC_TURB_NONE) {
     for (int j = 0; j < n1; ++j)
       for (int i = 0; i < n0; ++i) {
@@ -1426,13 +1422,21 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
         taut[c] = rho * nu_t / (p * std::sqrt(1.0 + eta * eta));
       }
   }
-  auto tau_of = [&](int i, int j) {  // ghost cells take their source cell's value
-    if (P->bc[0][0] == ORC_BC_PERIODIC) i = (i + n0) % n0; else i = std::min(std::max(i, 0), n0 - 1);
-    if (P->bc[1][0] == ORC_BC_PERIODIC) j = (j + n1) % n1; else j = std::min(std::max(j, 0), n1 - 1);
-    return taut[(long)j * n0 + i];
-  };
-  // fluxes times face length, per axis
-  std::vector<double> Fi((size_t)(n0 + 1) * n1 * nv), Fj((size_t)n0 * (n1 + 1) * nv);
+  return 0;
+}
+
+// Time-integrated flux times face length of every face, per axis ([face][v], faces x fastest), over
+// the window dt, or over the per-face windows win[0] (i-faces) and win[1] (j-faces) when win is
+// given; first_order: no slopes (the cell averages on both sides).
+void curv_fluxes(const CurvCtx& C, double dt, const std::vector<double>* win, bool first_order, int nthreads,
+                 std::vector<double>& Fi, std::vector<double>& Fj) {
+  const orc_problem* P = C.P;
+  const CurvGeom& g = C.g;
+  const Grid& G = C.G;
+  const std::vector<double>& Wp = C.Wp;
+  const int n0 = g.n0, n1 = g.n1, nv = 4;
+  Fi.assign((size_t)(n0 + 1) * n1 * nv, 0.0);
+  Fj.assign((size_t)n0 * (n1 + 1) * nv, 0.0);
   for (int d = 0; d < 2; ++d) {
     const int nf0 = d == 0 ? n0 + 1 : n0, nf1 = d == 0 ? n1 : n1 + 1;
     const long nfaces = (long)nf0 * nf1;
@@ -1466,8 +1470,8 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
       orc_face fc;
       std::memset(&fc, 0, sizeof(fc));
       for (int v = 0; v < nv; ++v) {
-        const double sl = limiter(P->limiter, (S4[1][v] - S4[0][v]) / d01, (S4[2][v] - S4[1][v]) / d12);
-        const double sr = limiter(P->limiter, (S4[2][v] - S4[1][v]) / d12, (S4[3][v] - S4[2][v]) / d23);
+        const double sl = first_order ? 0.0 : limiter(P->limiter, (S4[1][v] - S4[0][v]) / d01, (S4[2][v] - S4[1][v]) / d12);
+        const double sr = first_order ? 0.0 : limiter(P->limiter, (S4[2][v] - S4[1][v]) / d12, (S4[3][v] - S4[2][v]) / d23);
         fc.sl[v] = sl;
         fc.sr[v] = sr;
         fc.wl[v] = S4[1][v] + dl * sl;
@@ -1487,9 +1491,9 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
         }
       fc.dxl = dl;
       fc.dxr = dr;
-      fc.tau_t = 0.5 * (tau_of(ci[1], cj[1]) + tau_of(ci[2], cj[2]));
+      fc.tau_t = 0.5 * (C.tau_of(ci[1], cj[1]) + C.tau_of(ci[2], cj[2]));
       FaceWork Wk;
-      face_setup(2, P->gamma, P->mu, P->C_a, dt, 0, P->abar_mode, fc, Wk);
+      face_setup(2, P->gamma, P->mu, P->C_a, win ? win[d][f] : dt, 0, P->abar_mode, fc, Wk);
       double Fr[4];
       face_flux(Wk, Fr);
       double* Fo = d == 0 ? &Fi[f * nv] : &Fj[f * nv];
@@ -1499,6 +1503,270 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
       Fo[3] = Fr[3] * L;
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Steady-state solver on curvilinear grids (Section 4: local time steps, LU-SGS smoothing in the
+// form of Yoon and Jameson, multigrid after Jameson).  The readings of this build:
+//   - local explicit step s_i = 2 A_i / sum_faces (|U.n| + c) L (CFL 1); a face integrates its flux
+//     over the window cfl_flux min(s_l, s_r) (a ghost cell has its source cell's step) and divides by
+//     the window, so the steady operator does not depend on the pseudo-time step cfl s_i of the
+//     smoother (the time-accurate flux carries terms of the order of its window: with the window tied
+//     to a large pseudo-time step the iteration stalls);
+//   - residual R_i = sum over the faces of that flux rate times L, outward; dW/dt = -R / A;
+//   - LU-SGS on cell tiles (neighbours outside a tile enter neither sweep):
+//       D_i dW*_i = -R_i - sum_{lower j} 1/2 (dF_j - lambda_ij dW*_j) L_ij,
+//       dW_i = dW*_i - D_i^-1 sum_{upper j} 1/2 (dF_j - lambda_ij dW_j) L_ij,
+//     D_i = A_i/dt_i + 1/2 sum_faces lambda L, dF_j = F_n(W_j + dW_j) - F_n(W_j) the change of the
+//     Euler flux of cell j through the face with the normal pointing away from cell i, lower =
+//     (i-1, j) and (i, j-1); lambda = max over the two cells of |U.n| + c, plus 2 (mu + p tau_t)/
+//     (rho d) with face means of rho, p, tau_t and d the centroid distance;
+//   - multigrid: every coarse grid takes every second node; restriction of the state by area
+//     weights, of residuals by sums, of prescribed turbulence fields and Dirichlet data by plain
+//     means; FAS forcing P_c = sum R_f - R_c(W_c^0); coarse residuals first order; one LU-SGS
+//     smoothing per level on the way down, the corrections W_c - W_c^0 injected on the way up.
+// ---------------------------------------------------------------------------------------------
+void curv_lts(const CurvCtx& C, std::vector<double>& dtc) {
+  const CurvGeom& g = C.g;
+  const int n0 = g.n0, n1 = g.n1;
+  dtc.assign((size_t)n0 * n1, 0.0);
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      double w[5];
+      get_cell(C.G, C.Wp, i, j, 0, w);
+      const double p = pressure(2, C.P->gamma, w), cs = std::sqrt(C.P->gamma * p / w[0]);
+      const double u = w[1] / w[0], v = w[2] / w[0];
+      const long fi[2] = {(long)j * (n0 + 1) + i, (long)j * (n0 + 1) + i + 1};
+      const long fj[2] = {(long)j * n0 + i, (long)(j + 1) * n0 + i};
+      double r = 0.0;
+      for (int s2 = 0; s2 < 2; ++s2) {
+        r += (std::fabs(u * g.inx[fi[s2]] + v * g.iny[fi[s2]]) + cs) * g.iL[fi[s2]];
+        r += (std::fabs(u * g.jnx[fj[s2]] + v * g.jny[fj[s2]]) + cs) * g.jL[fj[s2]];
+      }
+      dtc[c] = 2.0 * g.area[c] / r;
+    }
+}
+
+void curv_residual(const CurvCtx& C, double cfl_flux, bool first_order, int nthreads, std::vector<double>& dtc,
+                   std::vector<double>& R) {
+  const CurvGeom& g = C.g;
+  const int n0 = g.n0, n1 = g.n1, nv = 4;
+  const long ncell = (long)n0 * n1;
+  curv_lts(C, dtc);
+  std::vector<double> win[2];
+  win[0].resize((size_t)(n0 + 1) * n1);
+  win[1].resize((size_t)n0 * (n1 + 1));
+  for (int j = 0; j < n1; ++j)
+    for (int fi = 0; fi <= n0; ++fi)
+      win[0][(long)j * (n0 + 1) + fi] = cfl_flux * std::min(dtc[C.src(fi - 1, j)], dtc[C.src(fi, j)]);
+  for (int fj = 0; fj <= n1; ++fj)
+    for (int i = 0; i < n0; ++i)
+      win[1][(long)fj * n0 + i] = cfl_flux * std::min(dtc[C.src(i, fj - 1)], dtc[C.src(i, fj)]);
+  std::vector<double> Fi, Fj;
+  curv_fluxes(C, 0.0, win, first_order, nthreads, Fi, Fj);
+  R.assign((size_t)nv * ncell, 0.0);
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      const long fa = (long)j * (n0 + 1) + i, fb = fa + 1, fc2 = (long)j * n0 + i, fd = (long)(j + 1) * n0 + i;
+      for (int v = 0; v < nv; ++v)
+        R[v * ncell + c] = Fi[fb * nv + v] / win[0][fb] - Fi[fa * nv + v] / win[0][fa] +
+                           Fj[fd * nv + v] / win[1][fd] - Fj[fc2 * nv + v] / win[1][fc2];
+    }
+}
+
+// Euler flux of state w through a face of unit normal (nx, ny).
+void euler_normal(double gamma, const double* w, double nx, double ny, double* F) {
+  const double un = (w[1] * nx + w[2] * ny) / w[0];
+  const double p = pressure(2, gamma, w);
+  F[0] = w[0] * un;
+  F[1] = w[1] * un + p * nx;
+  F[2] = w[2] * un + p * ny;
+  F[3] = (w[3] + p) * un;
+}
+
+// Spectral radius of the face between cells (ia, ja) and (ib, jb) (b on the side the normal points to).
+double face_lambda(const CurvCtx& C, double nx, double ny, double d, int ia, int ja, int ib, int jb) {
+  const double gamma = C.P->gamma;
+  double wa[5], wb[5];
+  get_cell(C.G, C.Wp, ia, ja, 0, wa);
+  get_cell(C.G, C.Wp, ib, jb, 0, wb);
+  auto sr = [&](const double* w) {
+    const double p = pressure(2, gamma, w);
+    return std::fabs((w[1] * nx + w[2] * ny) / w[0]) + std::sqrt(gamma * p / w[0]);
+  };
+  const double rho = 0.5 * (wa[0] + wb[0]);
+  const double p = 0.5 * (pressure(2, gamma, wa) + pressure(2, gamma, wb));
+  const double tau = 0.5 * (C.tau_of(ia, ja) + C.tau_of(ib, jb));
+  return std::max(sr(wa), sr(wb)) + 2.0 * (C.P->mu + p * tau) / (rho * d);
+}
+
+void curv_lusgs(const CurvCtx& C, const std::vector<double>& dtc, const std::vector<double>& R, int t0, int t1,
+                std::vector<double>& dW) {
+  const CurvGeom& g = C.g;
+  const int n0 = g.n0, n1 = g.n1, nv = 4;
+  const long ncell = (long)n0 * n1;
+  const double gamma = C.P->gamma;
+  // per face: lambda L / 2
+  std::vector<double> hli((size_t)(n0 + 1) * n1), hlj((size_t)n0 * (n1 + 1));
+  for (int j = 0; j < n1; ++j)
+    for (int fi = 0; fi <= n0; ++fi) {
+      const long f = (long)j * (n0 + 1) + fi;
+      hli[f] = 0.5 * g.iL[f] * face_lambda(C, g.inx[f], g.iny[f], cdist(g, fi - 1, j, fi, j), fi - 1, j, fi, j);
+    }
+  for (int fj = 0; fj <= n1; ++fj)
+    for (int i = 0; i < n0; ++i) {
+      const long f = (long)fj * n0 + i;
+      hlj[f] = 0.5 * g.jL[f] * face_lambda(C, g.jnx[f], g.jny[f], cdist(g, i, fj - 1, i, fj), i, fj - 1, i, fj);
+    }
+  std::vector<double> D(ncell);
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      const long fa = (long)j * (n0 + 1) + i, fc2 = (long)j * n0 + i;
+      D[c] = g.area[c] / dtc[c] + hli[fa] + hli[fa + 1] + hlj[fc2] + hlj[fc2 + n0];
+    }
+  dW.assign((size_t)nv * ncell, 0.0);
+  std::vector<double> dWs((size_t)nv * ncell, 0.0);
+  // contribution 1/2 (dF - lambda dX) L of neighbour (in, jn) through a face of normal +-n
+  auto offdiag = [&](int in, int jn, double nx, double ny, double hl, double L, const std::vector<double>& X,
+                     double* acc) {
+    const long cn = (long)jn * n0 + in;
+    double w[4], wp[4], F0[4], F1[4];
+    for (int v = 0; v < nv; ++v) {
+      w[v] = C.Wp[v * C.G.npad + C.G.idx(in, jn, 0)];
+      wp[v] = w[v] + X[v * ncell + cn];
+    }
+    euler_normal(gamma, wp, nx, ny, F1);
+    euler_normal(gamma, w, nx, ny, F0);
+    for (int v = 0; v < nv; ++v) acc[v] += 0.5 * (F1[v] - F0[v]) * L - hl * X[v * ncell + cn];
+  };
+  for (int tj0 = 0; tj0 < n1; tj0 += t1)
+    for (int ti0 = 0; ti0 < n0; ti0 += t0) {
+      const int ti1 = std::min(ti0 + t0, n0), tj1 = std::min(tj0 + t1, n1);
+      // forward sweep (lower neighbours inside the tile already done)
+      for (int j = tj0; j < tj1; ++j)
+        for (int i = ti0; i < ti1; ++i) {
+          const long c = (long)j * n0 + i;
+          double acc[4] = {0, 0, 0, 0};
+          if (i > ti0) {
+            const long f = (long)j * (n0 + 1) + i;  // face i - 1/2; normal away from cell i: -n
+            offdiag(i - 1, j, -g.inx[f], -g.iny[f], hli[f], g.iL[f], dWs, acc);
+          }
+          if (j > tj0) {
+            const long f = (long)j * n0 + i;
+            offdiag(i, j - 1, -g.jnx[f], -g.jny[f], hlj[f], g.jL[f], dWs, acc);
+          }
+          for (int v = 0; v < nv; ++v) dWs[v * ncell + c] = (-R[v * ncell + c] - acc[v]) / D[c];
+        }
+      // backward sweep
+      for (int j = tj1 - 1; j >= tj0; --j)
+        for (int i = ti1 - 1; i >= ti0; --i) {
+          const long c = (long)j * n0 + i;
+          double acc[4] = {0, 0, 0, 0};
+          if (i + 1 < ti1) {
+            const long f = (long)j * (n0 + 1) + i + 1;
+            offdiag(i + 1, j, g.inx[f], g.iny[f], hli[f], g.iL[f], dW, acc);
+          }
+          if (j + 1 < tj1) {
+            const long f = (long)(j + 1) * n0 + i;
+            offdiag(i, j + 1, g.jnx[f], g.jny[f], hlj[f], g.jL[f], dW, acc);
+          }
+          for (int v = 0; v < nv; ++v) dW[v * ncell + c] = dWs[v * ncell + c] - acc[v] / D[c];
+        }
+    }
+}
+
+// A coarse level: every second node, data restricted from the finer level.
+struct Level {
+  orc_problem P;
+  std::vector<double> nodes, f1, f2;
+  std::vector<double> dx[2];
+  std::vector<double> bcp[2][2];
+};
+
+void coarsen(const Level& F, Level& Cl) {
+  const int n0 = F.P.n[0], n1 = F.P.n[1], m0 = n0 / 2, m1 = n1 / 2;
+  Cl.P = F.P;
+  Cl.P.n[0] = m0;
+  Cl.P.n[1] = m1;
+  Cl.nodes.resize((size_t)(m0 + 1) * (m1 + 1) * 2);
+  for (int J = 0; J <= m1; ++J)
+    for (int I = 0; I <= m0; ++I)
+      for (int q = 0; q < 2; ++q)
+        Cl.nodes[((long)J * (m0 + 1) + I) * 2 + q] = F.nodes[((long)(2 * J) * (n0 + 1) + 2 * I) * 2 + q];
+  Cl.dx[0].assign(m0, 1.0);
+  Cl.dx[1].assign(m1, 1.0);
+  Cl.P.dx[0] = Cl.dx[0].data();
+  Cl.P.dx[1] = Cl.dx[1].data();
+  auto mean4 = [&](const std::vector<double>& f, std::vector<double>& out) {
+    out.clear();
+    if (f.empty()) return;
+    out.resize((size_t)m0 * m1);
+    for (int J = 0; J < m1; ++J)
+      for (int I = 0; I < m0; ++I)
+        out[(long)J * m0 + I] = 0.25 * (f[(long)(2 * J) * n0 + 2 * I] + f[(long)(2 * J) * n0 + 2 * I + 1] +
+                                        f[(long)(2 * J + 1) * n0 + 2 * I] + f[(long)(2 * J + 1) * n0 + 2 * I + 1]);
+  };
+  mean4(F.f1, Cl.f1);
+  mean4(F.f2, Cl.f2);
+  for (int a = 0; a < 2; ++a)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      Cl.P.bc_prim[a][s2] = nullptr;
+      if (F.P.bc[a][s2] != ORC_BC_DIRICHLET || !F.P.bc_prim[a][s2]) continue;
+      const int m = a == 0 ? m1 : m0;
+      Cl.bcp[a][s2].resize((size_t)m * 4);
+      for (int k = 0; k < m; ++k)
+        for (int v = 0; v < 4; ++v)
+          Cl.bcp[a][s2][k * 4 + v] = 0.5 * (F.P.bc_prim[a][s2][(2 * k) * 4 + v] + F.P.bc_prim[a][s2][(2 * k + 1) * 4 + v]);
+      Cl.P.bc_prim[a][s2] = Cl.bcp[a][s2].data();
+    }
+}
+
+const double* ptr_or_null(const std::vector<double>& v) { return v.empty() ? nullptr : v.data(); }
+
+}  // namespace
+
+extern "C" {
+
+int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt) {
+  if (P->dim != 2) return 1;
+  const CurvGeom g = curv_geometry(P, nodes);
+  if (!curv_valid(g)) return 2;
+  const int n0 = g.n0, n1 = g.n1;
+  const long ncell = (long)n0 * n1;
+  double rmax = 0.0;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      double w[4];
+      for (int v = 0; v < 4; ++v) w[v] = W[v * ncell + c];
+      const double p = pressure(2, P->gamma, w), cs = std::sqrt(P->gamma * p / w[0]);
+      const double u = w[1] / w[0], v = w[2] / w[0];
+      const long fi[2] = {(long)j * (n0 + 1) + i, (long)j * (n0 + 1) + i + 1};
+      const long fj[2] = {(long)j * n0 + i, (long)(j + 1) * n0 + i};
+      double r = 0.0;
+      for (int s = 0; s < 2; ++s) {
+        r += (std::fabs(u * g.inx[fi[s]] + v * g.iny[fi[s]]) + cs) * g.iL[fi[s]];
+        r += (std::fabs(u * g.jnx[fj[s]] + v * g.jny[fj[s]]) + cs) * g.jL[fj[s]];
+      }
+      rmax = std::max(rmax, r / (2.0 * g.area[c]));
+    }
+  *dt = cfl / rmax;
+  return 0;
+}
+
+int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
+                  double dt, int nthreads) {
+  CurvCtx C;
+  const int st = curv_prepare(P, nodes, W, f1, f2, C);
+  if (st) return st;
+  const CurvGeom& g = C.g;
+  const int n0 = g.n0, n1 = g.n1, nv = 4;
+  const long ncell = (long)n0 * n1;
+  std::vector<double> Fi, Fj;
+  curv_fluxes(C, dt, nullptr, false, nthreads, Fi, Fj);
   int status = 0;
   for (int j = 0; j < n1; ++j)
     for (int i = 0; i < n0; ++i) {
@@ -1512,6 +1780,123 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
       if (!(w[0] > 0.0) || !(pressure(2, P->gamma, w) > 0.0)) status = 4;
     }
   return status;
+}
+
+int orc_steady_residual(const orc_problem* P, const double* nodes, const double* W, const double* f1,
+                        const double* f2, double cfl_flux, int first_order, double* dt_cell, double* R, int nthreads) {
+  CurvCtx C;
+  const int st = curv_prepare(P, nodes, W, f1, f2, C);
+  if (st) return st;
+  std::vector<double> dtc, Rv;
+  curv_residual(C, cfl_flux, first_order != 0, nthreads, dtc, Rv);
+  if (dt_cell) std::memcpy(dt_cell, dtc.data(), sizeof(double) * dtc.size());
+  if (R) std::memcpy(R, Rv.data(), sizeof(double) * Rv.size());
+  return 0;
+}
+
+int orc_lusgs(const orc_problem* P, const double* nodes, const double* W, const double* f1, const double* f2,
+              const double* dt_cell, const double* R, int tile0, int tile1, double* dW) {
+  if (tile0 < 1 || tile1 < 1) return 1;
+  CurvCtx C;
+  const int st = curv_prepare(P, nodes, W, f1, f2, C);
+  if (st) return st;
+  const long ncell = (long)P->n[0] * P->n[1];
+  std::vector<double> dtc(dt_cell, dt_cell + ncell), Rv(R, R + 4 * ncell), out;
+  curv_lusgs(C, dtc, Rv, tile0, tile1, out);
+  std::memcpy(dW, out.data(), sizeof(double) * out.size());
+  return 0;
+}
+
+int orc_steady_cycle(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
+                     double cfl, double cfl_flux, int levels, int tile0, int tile1, int nthreads, double* res) {
+  if (P->dim != 2 || levels < 1 || levels > 6) return 1;
+  for (int l = 1; l < levels; ++l)
+    if (P->n[0] % (1 << l) || P->n[1] % (1 << l)) return 1;
+  std::vector<Level> L(levels);
+  L[0].P = *P;
+  const int n0 = P->n[0], n1 = P->n[1];
+  L[0].nodes.assign(nodes, nodes + (size_t)(n0 + 1) * (n1 + 1) * 2);
+  if (f1) L[0].f1.assign(f1, f1 + (size_t)n0 * n1);
+  if (f2) L[0].f2.assign(f2, f2 + (size_t)n0 * n1);
+  for (int l = 1; l < levels; ++l) coarsen(L[l - 1], L[l]);
+  std::vector<std::vector<double>> Ws(levels), W0(levels), Pf(levels);
+  Ws[0].assign(W, W + (size_t)4 * n0 * n1);
+  for (int l = 0; l < levels; ++l) {
+    const orc_problem& Pl = L[l].P;
+    const long nc = (long)Pl.n[0] * Pl.n[1];
+    const bool fo = l > 0;
+    CurvCtx C;
+    int st = curv_prepare(&Pl, L[l].nodes.data(), Ws[l].data(), ptr_or_null(L[l].f1), ptr_or_null(L[l].f2), C);
+    if (st) return st;
+    std::vector<double> dtc, R;
+    curv_residual(C, cfl_flux, fo, nthreads, dtc, R);
+    for (double& d : dtc) d *= cfl;  // pseudo-time steps of the smoother
+    if (l > 0)
+      for (size_t q = 0; q < R.size(); ++q) R[q] += Pf[l][q];
+    if (l == 0 && res) {
+      double s2 = 0.0;
+      for (long c = 0; c < nc; ++c) s2 += (R[c] / C.g.area[c]) * (R[c] / C.g.area[c]);
+      *res = std::sqrt(s2 / nc);
+    }
+    std::vector<double> dW;
+    curv_lusgs(C, dtc, R, tile0, tile1, dW);
+    for (size_t q = 0; q < dW.size(); ++q) Ws[l][q] += dW[q];
+    if (l + 1 == levels) break;
+    // restriction to level l + 1: the state by area weights, the residual after smoothing by sums
+    CurvCtx C2;
+    st = curv_prepare(&Pl, L[l].nodes.data(), Ws[l].data(), ptr_or_null(L[l].f1), ptr_or_null(L[l].f2), C2);
+    if (st) return st;
+    std::vector<double> dt2, R2;
+    curv_residual(C2, cfl_flux, fo, nthreads, dt2, R2);
+    if (l > 0)
+      for (size_t q = 0; q < R2.size(); ++q) R2[q] += Pf[l][q];
+    const int m0 = Pl.n[0] / 2, m1 = Pl.n[1] / 2, k0 = Pl.n[0];
+    const long mc = (long)m0 * m1;
+    W0[l + 1].assign((size_t)4 * mc, 0.0);
+    std::vector<double> Rs((size_t)4 * mc, 0.0);
+    for (int J = 0; J < m1; ++J)
+      for (int I = 0; I < m0; ++I) {
+        const long cc = (long)J * m0 + I;
+        double asum = 0.0;
+        for (int q = 0; q < 4; ++q) {
+          const long cf = (long)(2 * J + q / 2) * k0 + 2 * I + q % 2;
+          asum += C2.g.area[cf];
+          for (int v = 0; v < 4; ++v) {
+            W0[l + 1][v * mc + cc] += C2.g.area[cf] * Ws[l][v * nc + cf];
+            Rs[v * mc + cc] += R2[v * nc + cf];
+          }
+        }
+        for (int v = 0; v < 4; ++v) W0[l + 1][v * mc + cc] /= asum;
+      }
+    Ws[l + 1] = W0[l + 1];
+    CurvCtx C3;
+    st = curv_prepare(&L[l + 1].P, L[l + 1].nodes.data(), W0[l + 1].data(), ptr_or_null(L[l + 1].f1),
+                      ptr_or_null(L[l + 1].f2), C3);
+    if (st) return st;
+    std::vector<double> dt3, R3;
+    curv_residual(C3, cfl_flux, true, nthreads, dt3, R3);
+    Pf[l + 1].resize(R3.size());
+    for (size_t q = 0; q < R3.size(); ++q) Pf[l + 1][q] = Rs[q] - R3[q];
+  }
+  // prolongation: inject the coarse corrections
+  for (int l = levels - 1; l >= 1; --l) {
+    const int m0 = L[l].P.n[0], m1 = L[l].P.n[1], k0 = L[l - 1].P.n[0];
+    const long mc = (long)m0 * m1, nc = (long)k0 * L[l - 1].P.n[1];
+    for (int J = 0; J < m1; ++J)
+      for (int I = 0; I < m0; ++I) {
+        const long cc = (long)J * m0 + I;
+        for (int q = 0; q < 4; ++q) {
+          const long cf = (long)(2 * J + q / 2) * k0 + 2 * I + q % 2;
+          for (int v = 0; v < 4; ++v) Ws[l - 1][v * nc + cf] += Ws[l][v * mc + cc] - W0[l][v * mc + cc];
+        }
+      }
+  }
+  std::memcpy(W, Ws[0].data(), sizeof(double) * Ws[0].size());
+  for (long q = 0; q < (long)n0 * n1; ++q) {
+    double w[4] = {W[q], W[(long)n0 * n1 + q], W[2L * n0 * n1 + q], W[3L * n0 * n1 + q]};
+    if (!(w[0] > 0.0) || !(pressure(2, P->gamma, w) > 0.0)) return 4;
+  }
+  return 0;
 }
 
 int orc_reconstruct(int recon, int limiter, const double* v, const double* h, int n, double* wl, double* wr) {

@@ -123,6 +123,24 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
 /* CFL step on a curvilinear grid: dt = cfl / max_cells sum_faces (|U.n| + c) L / (2 A). */
 int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt);
 
+/* Steady-state solver on curvilinear grids (Section 4: local time stepping, LU-SGS, multigrid).
+ * orc_steady_residual: local explicit steps dt_cell[i] = 2 A_i / sum_faces (|U.n| + c) L and the
+ * residual R[v][i] = sum over faces of (flux over the face window cfl_flux min(dt_l, dt_r)) / window
+ * * L, outward (first_order: no slopes).  orc_lusgs: the LU-SGS increment dW for residual R and
+ * pseudo-time steps dt_cell,
+ * sweeping tiles of tile0 x tile1 cells independently (neighbours outside the tile enter neither
+ * sweep).  orc_steady_cycle: one FAS multigrid cycle over `levels` grids (every coarse grid takes
+ * every second node; n divisible by 2^(levels-1)): LU-SGS smoothing with pseudo-time steps cfl times
+ * the local explicit steps on the way down (fine level
+ * second order, coarse levels first order with the FAS forcing), corrections injected on the way
+ * up; *res = RMS over cells of R_rho / A before the cycle. */
+int orc_steady_residual(const orc_problem* P, const double* nodes, const double* W, const double* f1,
+                        const double* f2, double cfl, int first_order, double* dt_cell, double* R, int nthreads);
+int orc_lusgs(const orc_problem* P, const double* nodes, const double* W, const double* f1, const double* f2,
+              const double* dt_cell, const double* R, int tile0, int tile1, double* dW);
+int orc_steady_cycle(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
+                     double cfl, double cfl_flux, int levels, int tile0, int tile1, int nthreads, double* res);
+
 #ifdef __cplusplus
 }
 #endif
