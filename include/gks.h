@@ -131,6 +131,46 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
  * gks_get_tau_turb works on such grids, gks_get_rarefaction returns GKS_EUNSUPPORTED. */
 gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
 
+/* Steady-state solver on a body-fitted 2D grid (Section 4: the paper's solver is steady, with local
+ * time stepping, LU-SGS smoothing in the form of Yoon and Jameson and 4-level multigrid).  The
+ * readings of this library:
+ *   - local explicit step s_i = 2 A_i / sum_faces (|U.n| + c) L; the steady residual R_i = sum over
+ *     the faces of (the face flux integrated over the window cfl_flux min(s_l, s_r)) / window times
+ *     L, outward (a ghost cell has its source cell's step);
+ *   - LU-SGS with pseudo-time steps cfl s_i on tiles of 32 x 32 cells (neighbours outside a tile
+ *     enter neither sweep): D dW*_i = -R_i - sum_{(i-1,j),(i,j-1)} 1/2 (dF_j - lambda dW*_j) L,
+ *     dW_i = dW*_i - D^-1 sum_{(i+1,j),(i,j+1)} 1/2 (dF_j - lambda dW_j) L, D = A/dt + 1/2 sum lambda L,
+ *     dF_j the change of the Euler flux of cell j through the face (normal away from cell i),
+ *     lambda = max over the two cells of |U.n| + c, plus 2 (mu + p tau_t)/(rho d) (face means, d the
+ *     centroid distance);
+ *   - FAS multigrid over `levels` grids (each coarse grid takes every second node; n divisible by
+ *     2^(levels-1)): state restricted by area weights, residuals by sums, prescribed turbulence
+ *     fields and Dirichlet data by means; coarse residuals first order with the forcing
+ *     sum R_f - R_c(W_c^0); one LU-SGS smoothing per level on the way down, the corrections
+ *     W_c - W_c^0 injected on the way up.
+ * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), directional expansion,
+ * MUSCL2, turbulence models NONE, MUT, KEPS, KOMEGA (prescribed fields).  nodes: host,
+ * [(n1 + 1)][(n0 + 1)][2] as gks_set_nodes.  Errors: GKS_EUNSUPPORTED for other options, GKS_EINVAL
+ * for bad sizes, levels or a folded cell on any level. */
+typedef struct gks_steady gks_steady;
+gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb,
+                             const gks_numerics* num, const double* nodes, int levels, void* cuda_stream,
+                             gks_steady** out);
+/* Copy the fine-grid state in (as gks_set_state); the prescribed turbulence fields (as
+ * gks_set_turbulence; coarse levels take four-cell means). */
+gks_status gks_steady_set_state(gks_steady* s, const void* W, int layout, int memspace, int dtype);
+gks_status gks_steady_set_turbulence(gks_steady* s, const void* f1, const void* f2, int memspace, int dtype);
+/* Run ncycles multigrid cycles (one CUDA graph per cycle, captured once per (cfl, cfl_flux)); res_out
+ * (host, ncycles entries, or NULL) receives the RMS over fine cells of R_rho / A before each cycle.
+ * Synchronises the stream; GKS_ENONPHYS if the fine state is non-physical afterwards. */
+gks_status gks_steady_cycles(gks_steady* s, int ncycles, double cfl, double cfl_flux, double* res_out);
+/* The fine-level local steps (host, ncell) and residual (host, [4][ncell]) of the current state,
+ * second order unless first_order; either output may be NULL.  Synchronises. */
+gks_status gks_steady_residual(gks_steady* s, double cfl_flux, int first_order, double* dt_out, double* R_out);
+gks_status gks_steady_get_state(gks_steady* s, void* W_out, int layout, int memspace, int dtype);
+gks_status gks_steady_destroy(gks_steady* s);
+const char* gks_steady_last_error(const gks_steady* s);
+
 /* Copy out the current state in the requested layout and type. */
 gks_status gks_get_state(gks_handle* h, void* W_out, int layout, int memspace, int dtype);
 

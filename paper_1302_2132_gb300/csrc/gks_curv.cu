@@ -280,9 +280,13 @@ struct CurvTileGeom {
   }
 };
 
-template <int PREC, int V>
+// MODE 0: one time step (A.Win -> A.Wout, control block as the rectilinear step).  MODE 1: the
+// steady residual of A.Win (SteadyArgs): face windows cfl_flux min(s_l, s_r) from the local steps s,
+// flux rates times L summed per cell (plus the forcing) into R, tau_t of the tile cells stored.
+template <int PREC, int V, int MODE>
 __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / CurvTile<V>::T)
-    curv_step_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CurvGeom G) {
+    curv_step_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CurvGeom G,
+                     const __grid_constant__ SteadyArgs SA) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
   using TG = CurvTileGeom<V>;
@@ -326,7 +330,9 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
 #pragma unroll
     for (int q = 0; q < 8; ++q) cp_async<sizeof(R)>(&Gs[q * NF + l], &src[(long)q * nf + gf]);
   }
-  if (tid == 0) {
+  if (MODE == 1) {
+    if (tid == 0) s_dt = 1.0;
+  } else if (tid == 0) {
     const double dtv = step_dt(A);
     s_dt = dtv;
     if (blockIdx.x == 0) {
@@ -389,6 +395,8 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         t = tau_gg<R>(g, kc, G, A.f1, A.f2, si, sj, [&](int q, int v) { return nb[q][v]; });
       }
       Ts[l] = t;
+      if (MODE == 1 && ti >= 0 && ti < X && tj >= 0 && tj < Y && gi < n0 && gj < n1)
+        ((R*)SA.tau)[(long)gj * n0 + gi] = t;
     }
     __syncthreads();
   }
@@ -434,12 +442,13 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         S4[s][3] = w3;
       }
       R wl[4], wr[4], cl[4], cr[4], sl[4], sr[4];
+      const bool fo = MODE == 1 && SA.first_order;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const R dm = (S4[1][v] - S4[0][v]) * i01, dc = (S4[2][v] - S4[1][v]) * i12,
                 dp = (S4[3][v] - S4[2][v]) * i23;
-        sl[v] = limiter<R>(g.limiter, dm, dc);
-        sr[v] = limiter<R>(g.limiter, dc, dp);
+        sl[v] = fo ? R(0) : limiter<R>(g.limiter, dm, dc);
+        sr[v] = fo ? R(0) : limiter<R>(g.limiter, dc, dp);
         wl[v] = S4[1][v] + dl * sl[v];
         wr[v] = S4[2][v] - dr * sr[v];
         cl[v] = S4[1][v];
@@ -465,14 +474,48 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       }
       const R tl[1][4] = {{R(0), R(0), R(0), R(0)}}, trr[1][4] = {{R(0), R(0), R(0), R(0)}};
       R F[4], tau;
-      face_flux<2, R, false>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, dt, gas, g.abar_t0, F, &tau);
-      Fs[l] = F[0] * L;
-      Fs[NF + l] = (F[1] * nx - F[2] * ny) * L;
-      Fs[2 * NF + l] = (F[1] * ny + F[2] * nx) * L;
-      Fs[3 * NF + l] = F[3] * L;
+      R win = dt, Ls = L;
+      if (MODE == 1) {  // window of the face from the local steps of its two cells
+        const int ai = a == 0 ? ox + li - 1 : ox + li, aj = a == 0 ? oy + lj : oy + lj - 1;
+        const R* sloc = (const R*)SA.s_loc;
+        win = (R)SA.cfl_flux * fmin(sloc[field_cell(g, 2, ai, aj, 0)], sloc[field_cell(g, 2, ox + li, oy + lj, 0)]);
+        Ls = L / win;
+      }
+      face_flux<2, R, false>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+      const R L_ = Ls;
+      Fs[l] = F[0] * L_;
+      Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;
+      Fs[2 * NF + l] = (F[1] * ny + F[2] * nx) * L_;
+      Fs[3 * NF + l] = F[3] * L_;
     }
   }
   __syncthreads();
+
+  if (MODE == 1) {  // steady residual: sum of the outward flux rates times L, plus the forcing
+    double s2 = 0.0;
+    for (int l = tid; l < X * Y; l += T) {
+      const int li = l % X, lj = l / X;
+      const int gi = ox + li, gj = oy + lj;
+      if (gi >= n0 || gj >= n1) continue;
+      const long c = (long)gj * n0 + gi;
+      const int fa = lj * (X + 1) + li, fc = NFX + lj * X + li;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        R r = Fs[v * NF + fa + 1] - Fs[v * NF + fa] + Fs[v * NF + fc + X] - Fs[v * NF + fc];
+        if (SA.forcing) r += ((const R*)SA.forcing)[(long)v * g.ncell + c];
+        ((R*)SA.R)[(long)v * g.ncell + c] = r;
+        if (v == 0) {
+          const double rr = (double)r / G.area[c];
+          s2 += rr * rr;
+        }
+      }
+    }
+    if (SA.res_acc) {
+      const double bsum = block_sum(s2, red);
+      if (tid == 0) atomicAdd(SA.res_acc, bsum);
+    }
+    return;
+  }
 
   // ---- update, next CFL rate, physical check, residual norms ---------------------------------
   R rmax = R(0);
@@ -559,18 +602,32 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   }
 }
 
-template <int PREC, int V>
-void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s) {
+template <int PREC, int V, int MODE = 0>
+void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const SteadyArgs& SA = SteadyArgs{}) {
   using TG = CurvTileGeom<V>;
   const int nt = ((A.g.n[0] + TG::X - 1) / TG::X) * ((A.g.n[1] + TG::Y - 1) / TG::Y);
-  curv_step_kernel<PREC, V><<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R>(), s>>>(A, G);
+  curv_step_kernel<PREC, V, MODE><<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R>(), s>>>(A, G, SA);
 }
 
-template <int PREC, int V>
+template <int PREC, int V, int MODE = 0>
 cudaError_t prepare_fused() {
   using TG = CurvTileGeom<V>;
-  return cudaFuncSetAttribute(curv_step_kernel<PREC, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)TG::template smem_bytes<typename PrecT<PREC>::R>());
+}
+
+// Local explicit step (CFL 1) of every cell: 2 A / sum_faces (|U.n| + c) L.
+template <int PREC>
+__global__ void __launch_bounds__(kCurvThreads) lts_kernel(const __grid_constant__ StepArgs A,
+                                                           const __grid_constant__ CurvGeom G, void* s_out) {
+  using R = typename PrecT<PREC>::R;
+  const DevGrid& g = A.g;
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const Consts<R> kc = make_consts<R>(g);
+  R w[4];
+  load_stored<2, PREC>(g, A.Win, c, w);
+  ((R*)s_out)[c] = g_rcp(curv_rate<R>(w, kc.gamma, G, g.n[0], (int)(c % g.n[0]), (int)(c / g.n[0]), c));
 }
 
 inline unsigned blocks_for(long n) { return (unsigned)((n + kCurvThreads - 1) / kCurvThreads); }
@@ -604,8 +661,10 @@ cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodi
 
 cudaError_t prepare_curv() {
   cudaError_t e = cudaSuccess;
-  const cudaError_t r[6] = {prepare_fused<PREC_F64, 0>(), prepare_fused<PREC_F64, 1>(), prepare_fused<PREC_F32, 0>(),
-                            prepare_fused<PREC_F32, 1>(), prepare_fused<PREC_F32D, 0>(), prepare_fused<PREC_F32D, 1>()};
+  const cudaError_t r[8] = {prepare_fused<PREC_F64, 0>(),    prepare_fused<PREC_F64, 1>(),
+                            prepare_fused<PREC_F32, 0>(),    prepare_fused<PREC_F32, 1>(),
+                            prepare_fused<PREC_F32D, 0>(),   prepare_fused<PREC_F32D, 1>(),
+                            prepare_fused<PREC_F64, 0, 1>(), prepare_fused<PREC_F32, 0, 1>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
@@ -633,6 +692,20 @@ void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream
     curv_rate_kernel<PREC_F32><<<blocks, kCurvThreads, 0, s>>>(A, G);
   else
     curv_rate_kernel<PREC_F32D><<<blocks, kCurvThreads, 0, s>>>(A, G);
+}
+
+void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s) {
+  if (prec == PREC_F64)
+    launch_fused<PREC_F64, 0, 1>(A, G, s, SA);
+  else
+    launch_fused<PREC_F32, 0, 1>(A, G, s, SA);
+}
+
+void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s) {
+  if (prec == PREC_F64)
+    lts_kernel<PREC_F64><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, s_out);
+  else
+    lts_kernel<PREC_F32><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, s_out);
 }
 
 void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s) {

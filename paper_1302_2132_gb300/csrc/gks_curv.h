@@ -19,6 +19,17 @@ struct CurvGeom {
   void* flux[2];  // per axis [4][nf]: time-integrated face flux times face length, arithmetic type
 };
 
+// Steady-residual mode of the fused tile kernel (arithmetic-type arrays of the level).
+struct SteadyArgs {
+  const void* s_loc;      // local explicit steps (CFL 1) per cell
+  double cfl_flux;        // face window = cfl_flux min(s_l, s_r)
+  int first_order;        // no slopes
+  void* R;                // out: [4][ncell] sum over faces of the flux rate times L, outward (+ forcing)
+  const void* forcing;    // [4][ncell] or null
+  void* tau;              // out: tau_t per cell
+  double* res_acc;        // if set: += sum over cells of (R_rho / A)^2
+};
+
 // Metrics from nodes[(n1 + 1)][(n0 + 1)][2] (device, double); *bad (device) is or-ed with 1 if a
 // cell is not a convex counter-clockwise quadrilateral.
 cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int prec, CurvGeom& G,
@@ -30,5 +41,8 @@ void curv_tile_shape(int variant, int* x, int* y);
 constexpr int kCurvVariants = 2;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
 void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s);
+// steady solver pieces (FP64 and FP32 state): the residual of A.Win, the local explicit steps
+void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
+void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s);
 
 }  // namespace gks

@@ -72,6 +72,19 @@ def load():
     L.gks_get_state.argtypes = [H, _V, _I, _I, _I]
     L.gks_set_turbulence.argtypes = [H, _V, _V, _I, _I]
     L.gks_set_nodes.argtypes = [H, _V, _I]
+    L.gks_steady_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Gas), ctypes.POINTER(_Turb),
+                                    ctypes.POINTER(_Num), _PD, _I, _V, ctypes.POINTER(_V)]
+    L.gks_steady_set_state.argtypes = [_V, _V, _I, _I, _I]
+    L.gks_steady_set_turbulence.argtypes = [_V, _V, _V, _I, _I]
+    L.gks_steady_cycles.argtypes = [_V, _I, _D, _D, _PD]
+    L.gks_steady_residual.argtypes = [_V, _D, _I, _PD, _PD]
+    L.gks_steady_get_state.argtypes = [_V, _V, _I, _I, _I]
+    L.gks_steady_destroy.argtypes = [_V]
+    L.gks_steady_last_error.argtypes = [_V]
+    L.gks_steady_last_error.restype = ctypes.c_char_p
+    for name in ("gks_steady_create", "gks_steady_set_state", "gks_steady_set_turbulence", "gks_steady_cycles",
+                 "gks_steady_residual", "gks_steady_get_state", "gks_steady_destroy", "gks_set_nodes"):
+        getattr(L, name).restype = _I
     L.gks_compute_dt.argtypes = [H, _D, _PD]
     L.gks_step.argtypes = [H, _D, _D, _I, _D]
     L.gks_get_time.argtypes = [H, _PD, ctypes.POINTER(ctypes.c_longlong)]
@@ -134,6 +147,39 @@ def komega_defaults(**over):
     return c
 
 
+def _structs(dim, n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model, C_mu, beta_star, C_a, limiter, expand,
+             precision, abar_mode, reconstruction):
+    """gks_grid, gks_gas, gks_turb, gks_numerics and the arrays they point to."""
+    keep = []
+    g = _Grid()
+    g.dim = dim
+    for d in range(3):
+        g.n[d] = n[d] if d < dim else 1
+        g.lo[d] = lo[d] if lo is not None and d < dim else 0.0
+        g.hi[d] = hi[d] if hi is not None and d < dim else 1.0
+    for d in range(dim):
+        if dx is not None and dx[d] is not None:
+            w = _f64(np.broadcast_to(np.asarray(dx[d], dtype=np.float64), (n[d],)))
+            keep.append(w)
+            g.dx[d] = w.ctypes.data_as(_PD)
+        for s in range(2):
+            code = bc[d][s]
+            g.bc[d][s] = BC[code] if isinstance(code, str) else int(code)
+            if bc_data is not None and bc_data[d][s] is not None:
+                a = _f64(bc_data[d][s])
+                keep.append(a)
+                g.bc_data[d][s] = a.ctypes.data_as(_PD)
+    gas = _Gas(gamma, mu, 1.0, T_wall)
+    tm = TURB[turb_model] if isinstance(turb_model, str) else int(turb_model)
+    turb = _Turb(tm, C_mu, beta_star, C_a)
+    num = _Num(LIMITER[limiter] if isinstance(limiter, str) else int(limiter),
+               EXPAND[expand] if isinstance(expand, str) else int(expand),
+               PRECISION[precision] if isinstance(precision, str) else int(precision),
+               ABAR[abar_mode] if isinstance(abar_mode, str) else int(abar_mode),
+               RECON[reconstruction] if isinstance(reconstruction, str) else int(reconstruction))
+    return g, gas, turb, num, keep
+
+
 class Solver:
     """One grid problem on one GPU (see gks_create in include/gks.h for the meaning of each field).
 
@@ -147,33 +193,9 @@ class Solver:
         self.dim, self.nv = dim, dim + 2
         self.n = tuple(int(v) for v in n[:dim])
         self.ncell = int(np.prod(self.n))
-        self._keep = []
-        g = _Grid()
-        g.dim = dim
-        for d in range(3):
-            g.n[d] = self.n[d] if d < dim else 1
-            g.lo[d] = lo[d] if lo is not None and d < dim else 0.0
-            g.hi[d] = hi[d] if hi is not None and d < dim else 1.0
-        for d in range(dim):
-            if dx is not None and dx[d] is not None:
-                w = _f64(np.broadcast_to(np.asarray(dx[d], dtype=np.float64), (self.n[d],)))
-                self._keep.append(w)
-                g.dx[d] = w.ctypes.data_as(_PD)
-            for s in range(2):
-                code = bc[d][s]
-                g.bc[d][s] = BC[code] if isinstance(code, str) else int(code)
-                if bc_data is not None and bc_data[d][s] is not None:
-                    a = _f64(bc_data[d][s])
-                    self._keep.append(a)
-                    g.bc_data[d][s] = a.ctypes.data_as(_PD)
-        gas = _Gas(gamma, mu, 1.0, T_wall)
-        tm = TURB[turb_model] if isinstance(turb_model, str) else int(turb_model)
-        turb = _Turb(tm, C_mu, beta_star, C_a)
-        num = _Num(LIMITER[limiter] if isinstance(limiter, str) else int(limiter),
-                   EXPAND[expand] if isinstance(expand, str) else int(expand),
-                   PRECISION[precision] if isinstance(precision, str) else int(precision),
-                   ABAR[abar_mode] if isinstance(abar_mode, str) else int(abar_mode),
-                   RECON[reconstruction] if isinstance(reconstruction, str) else int(reconstruction))
+        g, gas, turb, num, self._keep = _structs(dim, self.n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model,
+                                                 C_mu, beta_star, C_a, limiter, expand, precision, abar_mode,
+                                                 reconstruction)
         self.precision = num.precision
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = _V()
@@ -403,3 +425,73 @@ def face_flux(dim, faces, dt, gamma=1.4, mu=1e-5, C_a=0.0, precision="fp64", exp
     if st != OK:
         raise GksError(st, "gks_face_flux failed")
     return F, tau
+
+
+class SteadySolver:
+    """Steady-state solver on a body-fitted 2D grid: local time stepping, LU-SGS smoothing and FAS
+    multigrid (gks_steady_* in include/gks.h).  nodes[(n1 + 1), (n0 + 1), 2] (host)."""
+
+    def __init__(self, n, bc, nodes, levels=4, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model="none",
+                 C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", stream=None):
+        import torch
+        L = load()
+        self.n = (int(n[0]), int(n[1]))
+        self.nv = 4
+        self.ncell = self.n[0] * self.n[1]
+        dx = [np.ones(self.n[0]), np.ones(self.n[1])]
+        g, gas, turb, num, self._keep = _structs(2, self.n, bc, dx, None, None, bc_data, gamma, mu, T_wall, turb_model,
+                                                 C_mu, beta_star, C_a, limiter, "directional", precision, "timeint",
+                                                 "muscl2")
+        nodes = _f64(nodes)
+        assert nodes.size == 2 * (self.n[0] + 1) * (self.n[1] + 1)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = _V()
+        st = L.gks_steady_create(ctypes.byref(g), ctypes.byref(gas), ctypes.byref(turb), ctypes.byref(num),
+                                 nodes.ctypes.data_as(_PD), int(levels), _V(self.stream.cuda_stream), ctypes.byref(h))
+        self._h = h if st == OK else None
+        if st != OK:
+            raise GksError(st, "gks_steady_create failed")
+
+    def _check(self, st):
+        if st != OK:
+            raise GksError(st, load().gks_steady_last_error(self._h).decode())
+
+    def set_state(self, W, layout="soa_cons"):
+        a = _f64(W)
+        self._check(load().gks_steady_set_state(self._h, _V(a.ctypes.data), LAYOUT[layout], MEM_HOST, F64))
+        self.stream.synchronize()
+
+    def set_turbulence(self, f1, f2=None):
+        a = _f64(f1)
+        b = _f64(f2) if f2 is not None else None
+        self._check(load().gks_steady_set_turbulence(self._h, _V(a.ctypes.data), _V(b.ctypes.data) if b is not None
+                                                     else None, MEM_HOST, F64))
+
+    def cycles(self, ncycles, cfl, cfl_flux=0.5):
+        """Run ncycles multigrid cycles; returns the fine residual norm before each."""
+        res = np.zeros(max(int(ncycles), 1))
+        self._check(load().gks_steady_cycles(self._h, int(ncycles), cfl, cfl_flux, res.ctypes.data_as(_PD)))
+        return res[:ncycles]
+
+    def residual(self, cfl_flux=0.5, first_order=False):
+        dt = np.zeros(self.ncell)
+        R = np.zeros(4 * self.ncell)
+        self._check(load().gks_steady_residual(self._h, cfl_flux, int(first_order), dt.ctypes.data_as(_PD),
+                                               R.ctypes.data_as(_PD)))
+        return dt, R
+
+    def get_state(self, layout="soa_cons"):
+        out = np.zeros(4 * self.ncell)
+        self._check(load().gks_steady_get_state(self._h, _V(out.ctypes.data), LAYOUT[layout], MEM_HOST, F64))
+        return out
+
+    def close(self):
+        if self._h is not None:
+            load().gks_steady_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
