@@ -46,10 +46,13 @@ def parse():
     p.add_argument("--precision", default=None, choices=["fp32", "fp32_acc64", "fp64"])
     p.add_argument("--workload", default="turb2d_1024",
                    choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
-                            "corner2d_528x136", "corner2d_2112x544"])
+                            "corner2d_528x136", "corner2d_2112x544", "steady_corner_528x136",
+                            "steady_corner_2112x544"])
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
                    help="face reconstruction (the default is the second-order MUSCL the metric is quoted on)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--lusgs-tile", type=int, default=16, choices=[16, 32],
+                   help="LU-SGS tile edge of the steady workloads")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--serving", action="store_true", help="measure the serving form only")
     p.add_argument("--no-serving", action="store_true", help="leave the serving summary out")
@@ -160,6 +163,15 @@ def make_workload(name, precision):
                     nsteps=5000, t_end=0.0, precision=precision or "fp32",
                     desc="Mach 2.85 boundary layer under a 24-degree shock, 1024x384 wall-clustered, k-omega tau_t, "
                          "5000 CFL steps")
+    if name.startswith("steady_corner_"):
+        nx, ny = (int(v) for v in name.split("_")[2].split("x"))
+        spec = inputs.compression_corner(nx, ny, alpha_deg=24.0)
+        return dict(spec=spec, steady=True, levels=4, precision=precision or "fp32",
+                    schedule=[(20, 1.0), (80, 4.0)],
+                    desc="steady solver (local time steps, LU-SGS on cell tiles, 4-level FAS multigrid) on the "
+                         "Mach 2.85 / 24-degree compression corner, body-fitted %dx%d wall-clustered grid, k-omega "
+                         "tau_t, 100 cycles from the inflow state (20 at CFL 1, 80 at CFL 4), flux windows CFL 0.5"
+                         % (nx, ny))
     if name.startswith("corner2d_"):
         nx, ny = (int(v) for v in name.split("_")[1].split("x"))
         spec = inputs.compression_corner(nx, ny, alpha_deg=24.0)
@@ -197,8 +209,155 @@ def faces_of(n):
     return tot
 
 
+def steady_faces_per_cycle(n, levels):
+    """Face flux evaluations of one multigrid cycle by level: (faces, cells, evaluations) per level.
+    The finest level evaluates its residual before and after smoothing, every coarser level that of
+    the restricted state, before smoothing and (except the coarsest) after it."""
+    out = []
+    for l in range(levels):
+        a, b = n[0] >> l, n[1] >> l
+        evals = (2 if levels > 1 else 1) if l == 0 else (2 if l == levels - 1 else 3)
+        out.append(((a + 1) * b + a * (b + 1), a * b, evals))
+    return out
+
+
+def run_steady(args, wl):
+    import torch
+    from paper_1302_2132_gb300 import build, gks
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    gks.load()
+    spec = wl["spec"]
+    n = tuple(spec["n"])
+    levels = wl["levels"]
+    s = gks.SteadySolver(n, spec["bc"], spec["nodes"], levels=levels, bc_data=spec["bc_prim"], gamma=1.4,
+                         mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega", beta_star=0.09, C_a=0.5,
+                         limiter="vanleer", precision=wl["precision"], lusgs_tile=args.lusgs_tile)
+    prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
+    s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sched = wl["schedule"]
+    ncyc = sum(k for k, _ in sched)
+    hist = None
+
+    def one_step():
+        nonlocal hist
+        s.set_state(prim_dev, layout="soa_prim")
+        hist = np.concatenate([s.cycles(k, cfl=c, cfl_flux=0.5) for k, c in sched])
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        s.stream.wait_stream(torch.cuda.current_stream())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        one_step()
+        e1.record(s.stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    clock_info = clocks.stop() if clocks else None
+    if world > 1:
+        ms = max_over_ranks(ms, dev)
+    e2e = None
+    if not args.no_e2e:
+        prim_host = torch.tensor(spec["prim"].ravel()).pin_memory()
+        out_host = np.zeros(4 * n[0] * n[1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_state(prim_host, layout="soa_prim")
+            for k, c in sched:
+                s.cycles(k, cfl=c, cfl_flux=0.5)
+            out_host = s.get_state()
+        e2e_s = time.perf_counter() - t0
+        assert np.isfinite(out_host).all()
+    per_level = steady_faces_per_cycle(n, levels)
+    faces_cycle = sum(f * e for f, _, e in per_level)
+    if not args.no_e2e:
+        e2e = {"value": faces_cycle * ncyc * args.steps * world / e2e_s, "unit": "face_flux_evals/s",
+               "h2d_bytes_per_step": int(prim_host.numel() * 8), "d2h_bytes_per_step": int(out_host.size * 8)}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    secs = ms / 1e3
+    value = faces_cycle * ncyc * args.steps * world / secs
+    fo_face = sum(gks.face_op_count(2, False, False)[:3])
+    so_face = sum(gks.face_op_count(2, False, True)[:3])
+    per_cell = CELL_OPS + sum(gks.cell_op_count(2)[:3])
+    ops_cycle = sum(e * (f * (so_face if l == 0 else fo_face) + c * per_cell) for l, (f, c, e) in enumerate(per_level))
+    achieved = ops_cycle * ncyc * args.steps / secs / 1e12
+    fp64 = wl["precision"] == "fp64"
+    lanes = 2 if fp64 else 128
+    peak = 152 * lanes * 2 * 2.070e9 / 1e12
+    line = {
+        "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
+        "value": value,
+        "unit": "face_flux_evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": "%s_%s" % (args.workload, wl["precision"]), "description": wl["desc"], "grid": list(n),
+                   "levels": levels, "lusgs_tile": args.lusgs_tile, "cycles_per_bench_step": ncyc,
+                   "precision": wl["precision"],
+                   "l2": "flushed between bench steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "cycles_per_s": ncyc * args.steps * world / secs,
+        "residual_drop": float(hist[-1] / hist[0]),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "kernel": "whole multigrid cycle (residual kernels, LU-SGS, transfers), operations of the "
+                               "residual evaluations only",
+                     "ops_per_cycle": ops_cycle,
+                     "peak_basis": "152 SMs x %d %s lanes x 2 (FMA) x 2070 MHz (derived)" % (lanes, "FP64" if fp64
+                                                                                            else "FP32")},
+        # per bench step: state_in; per cycle and level the local steps, residual, face spectral radii
+        # and LU-SGS, plus (above the coarsest) the residual after smoothing, restriction, coarse
+        # residual and forcing; the prolongations and the residual store; per cycles() call the
+        # physical-state check
+        "gpu_launches": args.steps * (1 + ncyc * (sum(4 + (6 if l + 1 < levels else 0) for l in range(levels))
+                                                  + (levels - 1) + 1) + len(sched)),
+        "clocks": clock_info,
+        "e2e": e2e,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
+    if args.workload.startswith("steady_"):
+        return run_steady(args, make_workload(args.workload, args.precision))
     rank, local_rank, world = dist_env()
     if world > 1:
         import torch.distributed as dist

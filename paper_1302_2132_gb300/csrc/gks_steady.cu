@@ -5,7 +5,7 @@
 //   face windows cfl_flux min(s_l, s_r) (the fused tile kernel in its residual mode; first order and
 //   with the FAS forcing on coarse levels), half spectral radius times length of every face
 //   (face_lambda_kernel), one LU-SGS smoothing with pseudo-time steps cfl s (lusgs_kernel: 32 x 32
-//   cell tiles, one warp, hyperplane by hyperplane), then the residual after smoothing restricted
+//   or 16 x 16 cell tiles, one lane per tile column, hyperplane by hyperplane), then the residual after smoothing restricted
 //   with the state to the next level (restrict_kernel) and the forcing formed (forcing_kernel);
 //   up: the coarse corrections injected (prolong_kernel).
 // Every launch of a cycle is captured once in a CUDA graph; the fine residual norm of each cycle
@@ -15,7 +15,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gks.h"
@@ -26,14 +28,15 @@
 namespace gks {
 namespace {
 
-constexpr int kLT = 32;  // LU-SGS tile edge: 32 x 32 cells, one warp
+// LU-SGS tile edge TL (16 or 32 cells; one lane per tile column)
 constexpr int kST = 128;
 
 inline unsigned nblk(long n, int t = kST) { return (unsigned)((n + t - 1) / t); }
 
+// (single precision divides with the fast reciprocal, double precision exactly)
 template <class R>
 __device__ __forceinline__ void euler_normal(R gamma, const R* w, R nx, R ny, R* F) {
-  const R un = (w[1] * nx + w[2] * ny) / w[0];
+  const R un = g_div(w[1] * nx + w[2] * ny, w[0]);
   const R p = pressure_of<R>(2, gamma, w);
   F[0] = w[0] * un;
   F[1] = w[1] * un + p * nx;
@@ -77,6 +80,14 @@ __global__ void __launch_bounds__(kST) face_lambda_kernel(const __grid_constant_
   ((R*)(a == 0 ? hli : hlj))[f] = R(0.5) * L * lam;
 }
 
+// dynamic shared memory of lusgs_kernel: dW, state (4 planes each) and the diagonal.  Rows are not
+// padded: the lanes of a sweep step touch one anti-diagonal of a plane, (k - l) TL + l, which with a
+// row pitch of TL falls into TL different banks (a pitch of TL + 1 would put them all in one).
+template <class R, int TL>
+constexpr size_t lusgs_smem() {
+  return sizeof(R) * 9 * TL * TL;
+}
+
 struct LusgsArgs {
   const void* s_loc;  // local explicit steps; pseudo step = cfl s
   double cfl;
@@ -97,16 +108,30 @@ __device__ __forceinline__ void offdiag(R gamma, const R* w, const R* X, R nx, R
   for (int v = 0; v < 4; ++v) acc[v] += R(0.5) * (F1[v] - F0[v]) * L - hl * X[v];
 }
 
-// LU-SGS on one 32 x 32 tile per warp: forward and backward sweeps hyperplane by hyperplane (lane l
-// takes tile column l), neighbours outside the tile left out; then W += dW on the tile.
-template <int PREC>
-__global__ void __launch_bounds__(kLT) lusgs_kernel(const __grid_constant__ StepArgs A,
-                                                    const __grid_constant__ CurvGeom G,
-                                                    const __grid_constant__ LusgsArgs LA) {
+// LU-SGS on one TL x TL tile per group of TL lanes: forward and backward sweeps hyperplane by hyperplane (lane l
+// takes tile column l), neighbours outside the tile left out; then W += dW on the tile.  The tile's
+// state and diagonal are staged in shared memory before the sweeps; each lane loads the residual
+// and face records of its next cell while it works on the current one, so that the sweeps wait
+// on shared memory and arithmetic only.
+template <class R>
+struct SweepIn {  // what a lane needs from global memory for one cell of a sweep
+  R r[4];         // forward: the residual
+  R f[2][4];      // the two faces towards the sweep's neighbours: n_x, n_y, L, 1/2 lambda L
+};
+
+template <int PREC, int TL>
+__global__ void __launch_bounds__(TL) lusgs_kernel(const __grid_constant__ StepArgs A,
+                                                   const __grid_constant__ CurvGeom G,
+                                                   const __grid_constant__ LusgsArgs LA) {
+  constexpr int kLT = TL;
+  constexpr unsigned kMask = TL == 32 ? 0xffffffffu : (1u << TL) - 1u;  // the lanes of the block
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
-  __shared__ R X[4][kLT][kLT + 1];  // dW* in the forward sweep, dW after the backward one
-  __shared__ R Dg[kLT][kLT + 1];
+  extern __shared__ __align__(16) unsigned char lu_raw[];
+  using Plane = R[kLT][kLT];
+  Plane* X = (Plane*)lu_raw;  // [4]: dW* in the forward sweep, dW after the backward one
+  Plane* Ws = X + 4;          // [4]: the tile's state
+  Plane& Dg = Ws[4];
   const DevGrid& g = A.g;
   const int lane = threadIdx.x;
   const int n0 = g.n[0], n1 = g.n[1];
@@ -121,76 +146,102 @@ __global__ void __launch_bounds__(kLT) lusgs_kernel(const __grid_constant__ Step
   const long nf0 = G.nf[0], nf1 = G.nf[1];
   const R* Rr = (const R*)LA.R;
   const R* sl = (const R*)LA.s_loc;
-  const S* Wg = (const S*)LA.W;
-  auto state = [&](int i, int j, R* w) {
+  S* Wg = (S*)LA.W;
+  // stage the state and the diagonal D = A / (cfl s) + 1/2 sum lambda L
+  for (int q = lane; q < ex * ey; q += kLT) {
+    const int li = q % ex, lj = q / ex;
+    const int i = ox + li, j = oy + lj;
     const long c = (long)j * n0 + i;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) w[v] = (R)Wg[(long)v * g.ncell + c];
+    for (int v = 0; v < 4; ++v) Ws[v][lj][li] = (R)Wg[(long)v * g.ncell + c];
+    const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+    const R dt = sl[c] * (R)LA.cfl;
+    Dg[lj][li] = (R)G.area[c] / dt + hli[fa] + hli[fa + 1] + hlj[fc] + hlj[fc + n0];
+  }
+  __syncwarp(kMask);
+  const int nk = ex + ey - 1;
+  // loads of the cell of hyperplane k (forward: lower faces and the residual; backward: upper faces)
+  auto fetch = [&](int k, bool fwd, SweepIn<R>& in) {
+    const int li = lane, lj = k - lane;
+    if (!(k >= 0 && k < nk && li < ex && lj >= 0 && lj < ey)) return;
+    const int i = ox + li, j = oy + lj;
+    const long c = (long)j * n0 + i;
+    const long fi = (long)j * (n0 + 1) + i + (fwd ? 0 : 1), fj = (long)(j + (fwd ? 0 : 1)) * n0 + i;
+    if (fwd) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) in.r[v] = Rr[(long)v * g.ncell + c];
+    }
+    in.f[0][0] = fi_rec[fi];
+    in.f[0][1] = fi_rec[nf0 + fi];
+    in.f[0][2] = fi_rec[2 * nf0 + fi];
+    in.f[0][3] = hli[fi];
+    in.f[1][0] = fj_rec[fj];
+    in.f[1][1] = fj_rec[nf1 + fj];
+    in.f[1][2] = fj_rec[2 * nf1 + fj];
+    in.f[1][3] = hlj[fj];
+  };
+  auto nbr = [&](int li, int lj, R* w, R* x) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      w[v] = Ws[v][lj][li];
+      x[v] = X[v][lj][li];
+    }
   };
   // forward sweep
-  for (int k = 0; k <= ex + ey - 2; ++k) {
+  SweepIn<R> cur, nxt;
+  fetch(0, true, cur);
+  for (int k = 0; k < nk; ++k) {
+    fetch(k + 1, true, nxt);
     const int li = lane, lj = k - lane;
     if (li < ex && lj >= 0 && lj < ey) {
-      const int i = ox + li, j = oy + lj;
-      const long c = (long)j * n0 + i;
-      const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
-      const R dt = sl[c] * (R)LA.cfl;
-      const R D = (R)G.area[c] / dt + hli[fa] + hli[fa + 1] + hlj[fc] + hlj[fc + n0];
-      Dg[lj][li] = D;
       R acc[4] = {R(0), R(0), R(0), R(0)};
-      if (li > 0) {
+      if (li > 0) {  // face i - 1/2, normal away from the cell: -n
         R w[4], x[4];
-        state(i - 1, j, w);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) x[v] = X[v][lj][li - 1];
-        offdiag<R>(kc.gamma, w, x, -fi_rec[fa], -fi_rec[nf0 + fa], hli[fa], fi_rec[2 * nf0 + fa], acc);
+        nbr(li - 1, lj, w, x);
+        offdiag<R>(kc.gamma, w, x, -cur.f[0][0], -cur.f[0][1], cur.f[0][3], cur.f[0][2], acc);
       }
       if (lj > 0) {
         R w[4], x[4];
-        state(i, j - 1, w);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) x[v] = X[v][lj - 1][li];
-        offdiag<R>(kc.gamma, w, x, -fj_rec[fc], -fj_rec[nf1 + fc], hlj[fc], fj_rec[2 * nf1 + fc], acc);
-      }
-#pragma unroll
-      for (int v = 0; v < 4; ++v) X[v][lj][li] = (-Rr[(long)v * g.ncell + c] - acc[v]) / D;
-    }
-    __syncwarp();
-  }
-  // backward sweep
-  for (int k = ex + ey - 2; k >= 0; --k) {
-    const int li = lane, lj = k - lane;
-    if (li < ex && lj >= 0 && lj < ey) {
-      const int i = ox + li, j = oy + lj;
-      const long fb = (long)j * (n0 + 1) + i + 1, fd = (long)(j + 1) * n0 + i;
-      R acc[4] = {R(0), R(0), R(0), R(0)};
-      if (li + 1 < ex) {
-        R w[4], x[4];
-        state(i + 1, j, w);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) x[v] = X[v][lj][li + 1];
-        offdiag<R>(kc.gamma, w, x, fi_rec[fb], fi_rec[nf0 + fb], hli[fb], fi_rec[2 * nf0 + fb], acc);
-      }
-      if (lj + 1 < ey) {
-        R w[4], x[4];
-        state(i, j + 1, w);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) x[v] = X[v][lj + 1][li];
-        offdiag<R>(kc.gamma, w, x, fj_rec[fd], fj_rec[nf1 + fd], hlj[fd], fj_rec[2 * nf1 + fd], acc);
+        nbr(li, lj - 1, w, x);
+        offdiag<R>(kc.gamma, w, x, -cur.f[1][0], -cur.f[1][1], cur.f[1][3], cur.f[1][2], acc);
       }
       const R D = Dg[lj][li];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) X[v][lj][li] = X[v][lj][li] - acc[v] / D;
+      for (int v = 0; v < 4; ++v) X[v][lj][li] = g_div(-cur.r[v] - acc[v], D);
     }
-    __syncwarp();
+    cur = nxt;
+    __syncwarp(kMask);
+  }
+  // backward sweep
+  fetch(nk - 1, false, cur);
+  for (int k = nk - 1; k >= 0; --k) {
+    fetch(k - 1, false, nxt);
+    const int li = lane, lj = k - lane;
+    if (li < ex && lj >= 0 && lj < ey) {
+      R acc[4] = {R(0), R(0), R(0), R(0)};
+      if (li + 1 < ex) {
+        R w[4], x[4];
+        nbr(li + 1, lj, w, x);
+        offdiag<R>(kc.gamma, w, x, cur.f[0][0], cur.f[0][1], cur.f[0][3], cur.f[0][2], acc);
+      }
+      if (lj + 1 < ey) {
+        R w[4], x[4];
+        nbr(li, lj + 1, w, x);
+        offdiag<R>(kc.gamma, w, x, cur.f[1][0], cur.f[1][1], cur.f[1][3], cur.f[1][2], acc);
+      }
+      const R D = Dg[lj][li];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) X[v][lj][li] = X[v][lj][li] - g_div(acc[v], D);
+    }
+    cur = nxt;
+    __syncwarp(kMask);
   }
   // W += dW
   for (int q = lane; q < ex * ey; q += kLT) {
     const int li = q % ex, lj = q / ex;
     const long c = (long)(oy + lj) * n0 + ox + li;
-    S* Wo = (S*)LA.W;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) Wo[(long)v * g.ncell + c] = (S)((R)Wo[(long)v * g.ncell + c] + X[v][lj][li]);
+    for (int v = 0; v < 4; ++v) Wg[(long)v * g.ncell + c] = (S)(Ws[v][lj][li] + X[v][lj][li]);
   }
 }
 
@@ -297,6 +348,7 @@ struct gks_steady {
   int dev = 0;
   int prec = PREC_F64;
   int levels = 1;
+  int tile = 16;  // LU-SGS tile edge
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<SteadyLevel> L;
@@ -308,8 +360,7 @@ struct gks_steady {
   void* staging = nullptr;
   size_t staging_bytes = 0;
   bool has_state = false, has_turb = false;
-  cudaGraphExec_t graph = nullptr;
-  double graph_cfl = 0.0, graph_cfl_flux = 0.0;
+  std::map<std::pair<double, double>, cudaGraphExec_t> graphs;  // one captured cycle per (cfl, cfl_flux)
   std::string err;
 };
 
@@ -340,9 +391,13 @@ void free_level(SteadyLevel& l) {
   l = SteadyLevel{};
 }
 
+void drop_graphs(gks_steady* s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
+}
+
 void free_steady(gks_steady* s) {
-  if (s->graph) cudaGraphExecDestroy(s->graph);
-  s->graph = nullptr;
+  drop_graphs(s);
   for (auto& l : s->L) free_level(l);
   s->L.clear();
   void* ps[] = {s->acc, s->counter, s->bad, s->history, s->staging};
@@ -401,8 +456,12 @@ void cycle_prec(gks_steady* s, double cfl, double cfl_flux) {
     LA.hl[0] = lev.hl[0];
     LA.hl[1] = lev.hl[1];
     LA.W = lev.W;
-    const int tiles = ((lev.n0 + kLT - 1) / kLT) * ((lev.n1 + kLT - 1) / kLT);
-    lusgs_kernel<PREC><<<tiles, kLT, 0, s->stream>>>(A, lev.G, LA);
+    const int TLs = s->tile;
+    const int tiles = ((lev.n0 + TLs - 1) / TLs) * ((lev.n1 + TLs - 1) / TLs);
+    if (TLs == 16)
+      lusgs_kernel<PREC, 16><<<tiles, 16, lusgs_smem<R, 16>(), s->stream>>>(A, lev.G, LA);
+    else
+      lusgs_kernel<PREC, 32><<<tiles, 32, lusgs_smem<R, 32>(), s->stream>>>(A, lev.G, LA);
     if (l + 1 == nl) break;
     // residual after smoothing, restricted with the state; coarse residual of W_c^0; forcing
     residual(s, l, lev.W, forcing, cfl_flux, nullptr);
@@ -439,9 +498,7 @@ gks_status ensure_history(gks_steady* s, int n) {
     return sfail(s, GKS_ENOMEM, "history allocation failed");
   }
   s->history_len = n;
-  // the captured cycle names the history buffer: capture again
-  if (s->graph) cudaGraphExecDestroy(s->graph);
-  s->graph = nullptr;
+  drop_graphs(s);  // the captured cycles name the history buffer: capture again
   return GKS_OK;
 }
 
@@ -463,8 +520,8 @@ gks_status ensure_stage(gks_steady* s, size_t bytes) {
 extern "C" {
 
 gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb,
-                             const gks_numerics* num, const double* nodes, int levels, void* cuda_stream,
-                             gks_steady** out) {
+                             const gks_numerics* num, const double* nodes, int levels, int lusgs_tile,
+                             void* cuda_stream, gks_steady** out) {
   if (!out) return GKS_EINVAL;
   *out = nullptr;
   if (!grid || !gas || !num || !nodes) return GKS_EINVAL;
@@ -474,6 +531,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   const int model = turb ? turb->model : GKS_TURB_NONE;
   if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA) return GKS_EUNSUPPORTED;
   if (levels < 1 || levels > 6) return GKS_EINVAL;
+  if (lusgs_tile != 0 && lusgs_tile != 16 && lusgs_tile != 32) return GKS_EINVAL;
   const int n0 = grid->n[0], n1 = grid->n[1];
   if (n0 < 2 || n1 < 2) return GKS_EINVAL;
   for (int l = 1; l < levels; ++l)
@@ -490,6 +548,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   cudaGetDevice(&s->dev);
   s->prec = num->precision == GKS_FP64 ? PREC_F64 : PREC_F32;
   s->levels = levels;
+  s->tile = lusgs_tile == 32 ? 32 : 16;
   auto bad = [&](gks_status st) {
     free_steady(s);
     delete s;
@@ -504,7 +563,11 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     }
     s->own_stream = true;
   }
-  if (prepare_curv() != cudaSuccess) {
+  if (prepare_curv() != cudaSuccess ||
+      cudaFuncSetAttribute(lusgs_kernel<PREC_F64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)lusgs_smem<double, 32>()) != cudaSuccess ||
+      cudaFuncSetAttribute(lusgs_kernel<PREC_F32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)lusgs_smem<float, 32>()) != cudaSuccess) {
     cudaGetLastError();
     return bad(GKS_ECUDA);
   }
@@ -724,9 +787,9 @@ gks_status gks_steady_cycles(gks_steady* s, int ncycles, double cfl, double cfl_
   if (st) return st;
   GKS_SCK(s, cudaMemsetAsync(s->acc, 0, sizeof(double), s->stream));
   GKS_SCK(s, cudaMemsetAsync(s->counter, 0, sizeof(int), s->stream));
-  if (!s->graph || s->graph_cfl != cfl || s->graph_cfl_flux != cfl_flux) {
-    if (s->graph) cudaGraphExecDestroy(s->graph);
-    s->graph = nullptr;
+  auto key = std::make_pair(cfl, cfl_flux);
+  auto it = s->graphs.find(key);
+  if (it == s->graphs.end()) {
     cudaGraph_t graph;
     GKS_SCK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     launch_cycle(s, cfl, cfl_flux);
@@ -735,17 +798,16 @@ gks_status gks_steady_cycles(gks_steady* s, int ncycles, double cfl, double cfl_
       cudaGetLastError();
       return sfail(s, GKS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
-    e = cudaGraphInstantiate(&s->graph, graph, 0);
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      s->graph = nullptr;
       return sfail(s, GKS_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
     }
-    s->graph_cfl = cfl;
-    s->graph_cfl_flux = cfl_flux;
+    it = s->graphs.emplace(key, exec).first;
   }
-  for (int k = 0; k < ncycles; ++k) GKS_SCK(s, cudaGraphLaunch(s->graph, s->stream));
+  for (int k = 0; k < ncycles; ++k) GKS_SCK(s, cudaGraphLaunch(it->second, s->stream));
   GKS_SCK(s, cudaMemsetAsync(s->bad, 0, sizeof(unsigned), s->stream));
   if (s->prec == PREC_F64)
     physical_kernel<double><<<nblk(s->L[0].ncell), kST, 0, s->stream>>>((const double*)s->L[0].W, s->L[0].ncell,

@@ -73,7 +73,7 @@ def load():
     L.gks_set_turbulence.argtypes = [H, _V, _V, _I, _I]
     L.gks_set_nodes.argtypes = [H, _V, _I]
     L.gks_steady_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Gas), ctypes.POINTER(_Turb),
-                                    ctypes.POINTER(_Num), _PD, _I, _V, ctypes.POINTER(_V)]
+                                    ctypes.POINTER(_Num), _PD, _I, _I, _V, ctypes.POINTER(_V)]
     L.gks_steady_set_state.argtypes = [_V, _V, _I, _I, _I]
     L.gks_steady_set_turbulence.argtypes = [_V, _V, _V, _I, _I]
     L.gks_steady_cycles.argtypes = [_V, _I, _D, _D, _PD]
@@ -432,7 +432,7 @@ class SteadySolver:
     multigrid (gks_steady_* in include/gks.h).  nodes[(n1 + 1), (n0 + 1), 2] (host)."""
 
     def __init__(self, n, bc, nodes, levels=4, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model="none",
-                 C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", stream=None):
+                 C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", lusgs_tile=16, stream=None):
         import torch
         L = load()
         self.n = (int(n[0]), int(n[1]))
@@ -447,7 +447,8 @@ class SteadySolver:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = _V()
         st = L.gks_steady_create(ctypes.byref(g), ctypes.byref(gas), ctypes.byref(turb), ctypes.byref(num),
-                                 nodes.ctypes.data_as(_PD), int(levels), _V(self.stream.cuda_stream), ctypes.byref(h))
+                                 nodes.ctypes.data_as(_PD), int(levels), int(lusgs_tile), _V(self.stream.cuda_stream),
+                                 ctypes.byref(h))
         self._h = h if st == OK else None
         if st != OK:
             raise GksError(st, "gks_steady_create failed")
@@ -457,6 +458,16 @@ class SteadySolver:
             raise GksError(st, load().gks_steady_last_error(self._h).decode())
 
     def set_state(self, W, layout="soa_cons"):
+        """W: numpy array or torch tensor (host or CUDA, float64 or float32)."""
+        if _is_torch(W):
+            import torch
+            assert W.is_contiguous()
+            dt = {torch.float64: F64, torch.float32: F32}[W.dtype]
+            if W.is_cuda:
+                self.stream.wait_stream(torch.cuda.current_stream(W.device))
+            self._check(load().gks_steady_set_state(self._h, _V(W.data_ptr()), LAYOUT[layout],
+                                                    MEM_DEVICE if W.is_cuda else MEM_HOST, dt))
+            return
         a = _f64(W)
         self._check(load().gks_steady_set_state(self._h, _V(a.ctypes.data), LAYOUT[layout], MEM_HOST, F64))
         self.stream.synchronize()

@@ -1,5 +1,5 @@
 """Parity of the CUDA steady-state solver (gks_steady_*: local time stepping, LU-SGS smoothing on
-32 x 32 tiles, FAS multigrid; the paper's solver mode, Section 4) with the oracle."""
+32 x 32 or 16 x 16 tiles, FAS multigrid; the paper's solver mode, Section 4) with the oracle."""
 import numpy as np
 import pytest
 
@@ -32,12 +32,12 @@ def corner(nx, ny, mu=5e-3, turb=0, laminar_start=True):
                 C_a=0.5)
 
 
-def both(sp, levels, precision="fp64", limiter=0):
+def both(sp, levels, precision="fp64", limiter=0, tile=32):
     from paper_1302_2132_gb300 import gks
     n0, n1 = sp["n"]
     s = gks.SteadySolver(sp["n"], sp["bc"], sp["nodes"], levels=levels, bc_data=sp["bc_prim"], gamma=GAMMA,
                          mu=sp["mu"], T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=sp["C_a"], limiter=limiter,
-                         precision=precision)
+                         precision=precision, lusgs_tile=tile)
     c = oracle.Case(2, sp["n"], [np.full(n0, 1.0 / n0), np.full(n1, 1.0 / n1)], sp["bc"], gamma=GAMMA, mu=sp["mu"],
                     T_wall=sp["T_wall"], turb_model=sp["turb"], multid=0, C_a=sp["C_a"], limiter=limiter,
                     bc_prim=sp["bc_prim"])
@@ -70,20 +70,21 @@ def test_residual_matches_oracle(name, first_order):
     s.close()
 
 
-@pytest.mark.parametrize("name,levels,cycles", [("wavy_keps", 1, 2), ("corner_komega", 1, 2), ("corner_laminar", 3, 3),
-                                                ("corner_komega", 4, 2)])
-def test_cycles_match_oracle(name, levels, cycles):
-    """LU-SGS on 32 x 32 tiles (several tiles and ragged edges) and the multigrid transfers: the state
-    after a few cycles equals the oracle's."""
+@pytest.mark.parametrize("name,levels,cycles,tile", [("wavy_keps", 1, 2, 32), ("corner_komega", 1, 2, 32),
+                                                     ("corner_laminar", 3, 3, 32), ("corner_komega", 4, 2, 32),
+                                                     ("wavy_keps", 1, 2, 16), ("corner_komega", 3, 2, 16)])
+def test_cycles_match_oracle(name, levels, cycles, tile):
+    """LU-SGS on 32 x 32 and 16 x 16 tiles (several tiles and ragged edges) and the multigrid
+    transfers: the state after a few cycles equals the oracle's."""
     sp = {"wavy_keps": lambda: wavy(48, 40, seed=5, turb=2), "corner_komega": lambda: corner(72, 40, turb=3),
           "corner_laminar": lambda: corner(64, 40)}[name]()
-    s, c, W, f1, f2 = both(sp, levels=levels)
+    s, c, W, f1, f2 = both(sp, levels=levels, tile=tile)
     res_g = s.cycles(cycles, cfl=3.0, cfl_flux=0.5)
     Wo = W
     res_o = []
     for _ in range(cycles):
-        Wo, r, st = c.steady_cycle(sp["nodes"], Wo, 3.0, cfl_flux=0.5, levels=levels, tiles=(32, 32), f1=f1, f2=f2,
-                                   nthreads=8)
+        Wo, r, st = c.steady_cycle(sp["nodes"], Wo, 3.0, cfl_flux=0.5, levels=levels, tiles=(tile, tile), f1=f1,
+                                   f2=f2, nthreads=8)
         assert st == 0
         res_o.append(r)
     assert np.allclose(res_g, res_o, rtol=1e-11, atol=0)
