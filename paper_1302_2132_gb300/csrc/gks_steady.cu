@@ -5,8 +5,9 @@
 //   face windows cfl_flux min(s_l, s_r) (the fused tile kernel in its residual mode; first order and
 //   with the FAS forcing on coarse levels), half spectral radius times length of every face
 //   (face_lambda_kernel), one LU-SGS smoothing with pseudo-time steps cfl s (lusgs_kernel: 32 x 32
-//   or 16 x 16 cell tiles, one lane per tile column, hyperplane by hyperplane), then the residual after smoothing restricted
-//   with the state to the next level (restrict_kernel) and the forcing formed (forcing_kernel);
+//   or 16 x 16 cell tiles, one lane per tile column, hyperplane by hyperplane), then the residual
+//   after smoothing restricted with the state to the next level (restrict_kernel) and the forcing
+//   formed (forcing_kernel);
 //   up: the coarse corrections injected (prolong_kernel).
 // Every launch of a cycle is captured once in a CUDA graph; the fine residual norm of each cycle
 // is appended to a device history by the last node.
@@ -108,8 +109,9 @@ __device__ __forceinline__ void offdiag(R gamma, const R* w, const R* X, R nx, R
   for (int v = 0; v < 4; ++v) acc[v] += R(0.5) * (F1[v] - F0[v]) * L - hl * X[v];
 }
 
-// LU-SGS on one TL x TL tile per group of TL lanes: forward and backward sweeps hyperplane by hyperplane (lane l
-// takes tile column l), neighbours outside the tile left out; then W += dW on the tile.  The tile's
+// LU-SGS on one TL x TL tile per group of TL lanes: forward and backward sweeps hyperplane by
+// hyperplane (lane l takes tile column l), neighbours outside the tile left out; then W += dW on the
+// tile.  The tile's
 // state and diagonal are staged in shared memory before the sweeps; each lane loads the residual
 // and face records of its next cell while it works on the current one, so that the sweeps wait
 // on shared memory and arithmetic only.
