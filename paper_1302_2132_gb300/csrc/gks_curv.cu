@@ -276,7 +276,7 @@ struct CurvTileGeom {
   static constexpr int NFX = (X + 1) * Y, NFY = X * (Y + 1), NF = NFX + NFY;
   static constexpr int TX = X + 2, TY = Y + 2, NT = TX * TY;  // tile and first ring (tau)
   template <class R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * (4 * (size_t)NH + 8 * (size_t)NF + 4 * (size_t)NF + NT);
+    return sizeof(R) * (4 * (size_t)NH + 8 * (size_t)NF + 4 * (size_t)NF + NT) + sizeof(float) * 4 * X * Y;
   }
 };
 
@@ -297,6 +297,7 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   R* Gs = Ws + 4 * NH;     // [8][NF] face records: i-faces (X + 1) x Y, then j-faces X x (Y + 1)
   R* Fs = Gs + 8 * NF;     // [4][NF] face fluxes times length
   R* Ts = Fs + 4 * NF;     // [TY][TX] tau_t of the tile and its first ring
+  float* Lo = (float*)(Ts + NT);  // [4][X * Y] low words of the tile's state (float pair form)
   __shared__ double red[kMaxWarps];
   __shared__ double s_dt;
   const DevGrid& g = A.g;
@@ -343,10 +344,18 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
     }
   }
   // ---- state of the tile and two halo layers, boundary rules applied -------------------------
+  // (cells inside the grid by asynchronous copies where the stored type is the arithmetic one;
+  // ghost cells through the boundary rules)
   for (int l = tid; l < NH; l += T) {
     const int hi = l % HX, hj = l / HX;
     const int gi = ox + hi - H, gj = oy + hj - H;
     R w[4];
+    if (PREC != PREC_F32D && gi >= 0 && gi < n0 && gj >= 0 && gj < n1) {
+      const S* src = (const S*)A.Win + (long)gj * n0 + gi;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cp_async<sizeof(R)>(&Ws[v * NH + l], src + (long)v * g.ncell);
+      continue;
+    }
     if (gi >= -H && gi < n0 + H && gj >= -H && gj < n1 + H) {
       load_cell<2, PREC>(g, A.Win, kc, gi, gj, 0, w);
     } else {
@@ -357,6 +366,13 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
 #pragma unroll
     for (int v = 0; v < 4; ++v) Ws[v * NH + l] = w[v];
   }
+  if (PREC == PREC_F32 && MODE == 0)
+    for (int l = tid; l < X * Y; l += T) {
+      const int gi = ox + l % X, gj = oy + l / X;
+      if (gi >= n0 || gj >= n1) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cp_async<4>(&Lo[v * X * Y + l], &A.Win_lo[(long)v * g.ncell + (long)gj * n0 + gi]);
+    }
   cp_async_wait_all();
   __syncthreads();
   const double dt_d = s_dt;
@@ -551,7 +567,7 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       } else {
         const R inc = -net * ia;
         if (PREC == PREC_F32) {
-          const float hi = (float)Ws[v * NH + hidx], lo = A.Win_lo[gidx];
+          const float hi = (float)Ws[v * NH + hidx], lo = Lo[v * X * Y + l];
           const float s_ = hi + inc;
           const float bb = s_ - hi;
           const float err = (hi - (s_ - bb)) + (inc - bb);

@@ -130,3 +130,34 @@ def test_unsupported_and_invalid_options_are_rejected():
     bad[5, 6] = bad[5, 7] + np.array([0.05, 0.0])
     with pytest.raises(gks.GksError):
         gks.SteadySolver(sp["n"], sp["bc"], bad, levels=1, bc_data=sp["bc_prim"])
+
+
+def test_full_size_steady_corner_matches_oracle():
+    """The bench configuration: the 24-degree corner on the 528 x 136 grid with k-omega tau_t, four
+    levels, 16 x 16 LU-SGS tiles.  FP64: one cycle element by element; FP32 (the bench's precision):
+    five cycles, L1 of the density against the FP64 oracle."""
+    spec = inputs.compression_corner(528, 136, alpha_deg=24.0)
+    sp = dict(n=spec["n"], bc=spec["bc"], bc_prim=spec["bc_prim"], nodes=spec["nodes"], prim=spec["prim"],
+              f1=spec["f1"].ravel(), f2=spec["f2"].ravel(), mu=spec["mu"], T_wall=spec["T_wall"], turb=3, C_a=0.5)
+    s, c, W, f1, f2 = both(sp, levels=4, limiter=1, tile=16)
+    res_g = s.cycles(1, cfl=1.0, cfl_flux=0.5)
+    Wo, r, st = c.steady_cycle(sp["nodes"], W, 1.0, cfl_flux=0.5, levels=4, tiles=(16, 16), f1=f1, f2=f2,
+                               nthreads=16)
+    assert st == 0
+    assert abs(res_g[0] / r - 1.0) < 1e-11
+    Wg = s.get_state()
+    nc = W.size // 4
+    for v in range(4):
+        a, b = Wg[v * nc:(v + 1) * nc], Wo[v * nc:(v + 1) * nc]
+        assert np.abs(a - b).max() < 1e-11 * np.abs(b).max()
+    s.close()
+    s32, _, _, _, _ = both(sp, levels=4, limiter=1, tile=16, precision="fp32")
+    s32.cycles(5, cfl=1.0, cfl_flux=0.5)
+    Wo = W
+    for _ in range(5):
+        Wo, r, st = c.steady_cycle(sp["nodes"], Wo, 1.0, cfl_flux=0.5, levels=4, tiles=(16, 16), f1=f1, f2=f2,
+                                   nthreads=16)
+        assert st == 0
+    Wg = s32.get_state()
+    assert np.abs(Wg[:nc] - Wo[:nc]).sum() / np.abs(Wo[:nc]).sum() < 1e-5
+    s32.close()
