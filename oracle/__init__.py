@@ -71,6 +71,7 @@ class Problem(ctypes.Structure):
         ("multid", ctypes.c_int),
         ("abar_mode", ctypes.c_int),
         ("recon", ctypes.c_int),
+        ("wake_cut", ctypes.c_int),
     ]
 
 
@@ -243,7 +244,7 @@ class Case:
 
     def __init__(self, dim, n, dx, bc, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model=TURB_NONE,
                  C_mu=0.09, beta_star=0.09, C_a=0.0, limiter=LIM_VANLEER, multid=1,
-                 abar_mode=ABAR_TIMEINT, bc_prim=None, recon=RECON_MUSCL2):
+                 abar_mode=ABAR_TIMEINT, bc_prim=None, recon=RECON_MUSCL2, wake_cut=0):
         self.dim = dim
         self.n = tuple(n)
         self.P = Problem()
@@ -265,6 +266,7 @@ class Case:
         self.P.turb_model, self.P.C_mu, self.P.beta_star, self.P.C_a = turb_model, C_mu, beta_star, C_a
         self.P.limiter, self.P.multid, self.P.abar_mode = limiter, multid, abar_mode
         self.P.recon = recon
+        self.P.wake_cut = int(wake_cut)
         self.ncell = int(np.prod(n[:dim]))
         self.nv = dim + 2
 

@@ -482,6 +482,11 @@ void prim_from_cons(int D, double gamma, const double* w, double* pr) {
 // range over interior cells and higher axes over the padded range, so corners take the lower
 // axis' rule.  Wall: no-slip mirror with p_g = p_i and T_g = T_w^2 / T_i (T = p/rho), so that the
 // geometric mean of the two temperatures is the wall temperature.
+// Cell i of the j-lo side lies on the wake cut of a C-grid.
+bool in_cut(const orc_problem* P, int i) {
+  return P->wake_cut > 0 && i >= 0 && i < P->n[0] && (i < P->wake_cut || i >= P->n[0] - P->wake_cut);
+}
+
 void fill_ghosts(const orc_problem* P, const Grid& G, std::vector<double>& Wp) {
   const int D = G.D, nv = G.nv;
   for (int a = D - 1; a >= 0; --a) {
@@ -509,7 +514,11 @@ void fill_ghosts(const orc_problem* P, const Grid& G, std::vector<double>& Wp) {
               dst[a] = gidx;
               int src[3] = {c[0], c[1], c[2]};
               double wv[5];
-              if (bc == ORC_BC_PERIODIC) {
+              if (D == 2 && a == 1 && side == 0 && in_cut(P, c[0])) {  // C-grid wake cut
+                src[0] = P->n[0] - 1 - c[0];
+                src[1] = gi - 1;
+                for (int v = 0; v < nv; ++v) wv[v] = Wp[v * G.npad + G.idx(src[0], src[1], src[2])];
+              } else if (bc == ORC_BC_PERIODIC) {
                 src[a] = side == 0 ? n - gi : gi - 1;
                 for (int v = 0; v < nv; ++v) wv[v] = Wp[v * G.npad + G.idx(src[0], src[1], src[2])];
               } else if (bc == ORC_BC_TRANSMISSIVE || bc == ORC_BC_OUTFLOW) {
@@ -552,7 +561,8 @@ void pad_state(const Grid& G, const double* W, std::vector<double>& Wp) {
           Wp[v * G.npad + G.idx(i, j, k)] = W[v * G.ncell + ((long)k * G.n[1] + j) * G.n[0] + i];
 }
 
-// Turbulence fields with ghosts: periodic axes wrap, other axes repeat the nearest interior cell.
+// Turbulence fields with ghosts: periodic axes wrap, other axes repeat the nearest interior cell (a
+// C-grid wake cut takes the cell across the cut).
 std::vector<double> pad_scalar(const orc_problem* P, const Grid& G, const double* f) {
   std::vector<double> out(G.npad, 0.0);
   if (!f) return out;
@@ -560,12 +570,17 @@ std::vector<double> pad_scalar(const orc_problem* P, const Grid& G, const double
     for (int j = -G.g[1]; j < G.n[1] + G.g[1]; ++j)
       for (int i = -G.g[0]; i < G.n[0] + G.g[0]; ++i) {
         int c[3] = {i, j, k};
-        for (int d = 0; d < G.D; ++d) {
-          int n = G.n[d];
-          if (P->bc[d][0] == ORC_BC_PERIODIC)
-            c[d] = (c[d] + n) % n;
-          else
-            c[d] = std::min(std::max(c[d], 0), n - 1);
+        if (G.D == 2 && j < 0 && in_cut(P, i)) {  // C-grid wake cut: the cell across the cut
+          c[0] = G.n[0] - 1 - i;
+          c[1] = -j - 1;
+        } else {
+          for (int d = 0; d < G.D; ++d) {
+            int n = G.n[d];
+            if (P->bc[d][0] == ORC_BC_PERIODIC)
+              c[d] = (c[d] + n) % n;
+            else
+              c[d] = std::min(std::max(c[d], 0), n - 1);
+          }
         }
         out[G.idx(i, j, k)] = f[((long)c[2] * G.n[1] + c[1]) * G.n[0] + c[0]];
       }
@@ -1314,6 +1329,7 @@ CurvGeom curv_geometry(const orc_problem* P, const double* nodes) {
           X[q][g.pidx(i, -k)] = 2.0 * mb[q] - X[q][g.pidx(i, k - 1)];
           X[q][g.pidx(i, n1 - 1 + k)] = 2.0 * mt[q] - X[q][g.pidx(i, n1 - k)];
         }
+        if (in_cut(P, i)) X[q][g.pidx(i, -k)] = X[q][g.pidx(n0 - 1 - i, k - 1)];  // the cell across the cut
       }
     }
   return g;
@@ -1343,14 +1359,10 @@ struct CurvCtx {
   Grid G;
   std::vector<double> Wp, taut;
   // tau_t of a (possibly ghost) cell: a ghost cell takes its source cell's value
-  double tau_of(int i, int j) const {
-    const int n0 = g.n0, n1 = g.n1;
-    if (P->bc[0][0] == ORC_BC_PERIODIC) i = (i + n0) % n0; else i = std::min(std::max(i, 0), n0 - 1);
-    if (P->bc[1][0] == ORC_BC_PERIODIC) j = (j + n1) % n1; else j = std::min(std::max(j, 0), n1 - 1);
-    return taut[(long)j * n0 + i];
-  }
+  double tau_of(int i, int j) const { return taut[src(i, j)]; }
   long src(int i, int j) const {  // source cell of a ghost (the cell itself inside)
     const int n0 = g.n0, n1 = g.n1;
+    if (j < 0 && in_cut(P, i)) return (long)(-j - 1) * n0 + (n0 - 1 - i);  // across the wake cut
     if (P->bc[0][0] == ORC_BC_PERIODIC) i = (i + n0) % n0; else i = std::min(std::max(i, 0), n0 - 1);
     if (P->bc[1][0] == ORC_BC_PERIODIC) j = (j + n1) % n1; else j = std::min(std::max(j, 0), n1 - 1);
     return (long)j * n0 + i;
@@ -1691,6 +1703,7 @@ void coarsen(const Level& F, Level& Cl) {
   Cl.P = F.P;
   Cl.P.n[0] = m0;
   Cl.P.n[1] = m1;
+  Cl.P.wake_cut = F.P.wake_cut / 2;
   Cl.nodes.resize((size_t)(m0 + 1) * (m1 + 1) * 2);
   for (int J = 0; J <= m1; ++J)
     for (int I = 0; I <= m0; ++I)
@@ -1811,7 +1824,7 @@ int orc_steady_cycle(const orc_problem* P, const double* nodes, double* W, const
                      double cfl, double cfl_flux, int levels, int tile0, int tile1, int nthreads, double* res) {
   if (P->dim != 2 || levels < 1 || levels > 6) return 1;
   for (int l = 1; l < levels; ++l)
-    if (P->n[0] % (1 << l) || P->n[1] % (1 << l)) return 1;
+    if (P->n[0] % (1 << l) || P->n[1] % (1 << l) || P->wake_cut % (1 << l)) return 1;
   std::vector<Level> L(levels);
   L[0].P = *P;
   const int n0 = P->n[0], n1 = P->n[1];

@@ -37,6 +37,8 @@ typedef struct {
   double C_mu, beta_star, C_a;
   int limiter, multid, abar_mode;
   int recon;                    /* ORC_RECON_*; MUSCL2 uses `limiter` */
+  int wake_cut;                 /* 2D C-grids: the first and last wake_cut cells of the j-lo side are a
+                                   wake cut, ghost (i, -k) = cell (n0 - 1 - i, k - 1); 0: none */
 } orc_problem;
 
 /* Per-face record, normal frame (velocity index 0 is the face normal):

@@ -16,6 +16,7 @@ inputs of this library):
                     wall-clustered grid, with log-law k-omega profiles
   compression_corner  Mach 2.85 boundary layer over a ramp of alpha degrees on a body-fitted,
                     wall-clustered channel grid (nodes given), log-law k-omega profiles
+  naca0012_case     C-grid round a NACA 0012 section with a wake cut (transonic free stream)
   wavy_nodes        smoothly skewed periodic grids (with smooth_state_at, positive_fields_at) for the
                     curvilinear invariance and parity tests
 """
@@ -365,6 +366,70 @@ def compression_corner(nx, ny, alpha_deg=24.0, M=2.85, delta=0.1, Re_delta=1.6e6
     bc_prim = [[inflow, None], [None, None]]
     return dict(dim=2, n=(nx, ny), nodes=nodes, bc=bc, bc_prim=bc_prim, prim=prim, T_wall=T_wall, mu=mu,
                 f1=kk.astype(np.float32).astype(np.float64), f2=om.astype(np.float32).astype(np.float64))
+
+
+def naca0012_thickness(x):
+    """Half thickness of the NACA 0012 section (closed trailing edge form of the four-digit formula)."""
+    return 0.6 * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+
+
+def naca0012_cgrid(n_wake, n_surf, n_normal, R=5.0, x_out=6.0, dy1=2e-3, ratio=1.15):
+    """A C-grid around a NACA 0012 section of unit chord (the grid type of the paper's aerofoil cases;
+    the paper's own grids are not inputs here).  The inner grid line (j = 0) runs along the lower
+    wake from x_out to the trailing edge, round the section (cosine spacing) and back along the
+    upper wake; the outer line is y = -R for the lower wake, the half ellipse with centre (1, 0) and
+    semi-axes (1 + R, R) round the section, and y = +R for the upper wake; grid lines join the two
+    (vertical in the wake), rows clustered at the inner line.  n0 = 2 n_wake + n_surf (n_surf even),
+    the first and last n_wake cells of the j-lo side form the wake cut."""
+    assert n_surf % 2 == 0
+    n0 = 2 * n_wake + n_surf
+    xw = x_out - np.arange(n_wake + 1) * ((x_out - 1.0) / n_wake)  # x_out .. 1
+    th_lo = np.linspace(0.0, math.pi, n_surf // 2 + 1)              # trailing edge -> leading edge
+    th_up = np.linspace(math.pi, 2 * math.pi, n_surf // 2 + 1)
+    inner, outer = [], []
+    a = 1.0 + R
+    for x in xw[:-1]:
+        inner.append((x, 0.0))
+        outer.append((x, -R))
+    for th in th_lo[:-1]:
+        x = 0.5 * (1.0 + math.cos(th))
+        al = -0.5 * math.pi - 0.5 * th
+        inner.append((x, -naca0012_thickness(x)))
+        outer.append((1.0 + a * math.cos(al), R * math.sin(al)))
+    for th in th_up[:-1]:
+        x = 0.5 * (1.0 + math.cos(th))
+        al = -math.pi - 0.5 * (th - math.pi)
+        inner.append((x, naca0012_thickness(x)))
+        outer.append((1.0 + a * math.cos(al), R * math.sin(al)))
+    for x in xw[::-1]:
+        inner.append((x, 0.0))
+        outer.append((x, R))
+    inner, outer = np.array(inner), np.array(outer)
+    assert inner.shape[0] == n0 + 1
+    inner[n_wake] = (1.0, 0.0)
+    inner[n0 - n_wake] = (1.0, 0.0)
+    eta = np.concatenate([[0.0], np.cumsum(_row_heights(n_normal, dy1, ratio, 1.0))])
+    nodes = inner[None, :, :] + eta[:, None, None] * (outer - inner)[None, :, :]
+    return nodes
+
+
+def naca0012_case(n_wake, n_surf, n_normal, mach=0.8, alpha_deg=2.26, Re=9.0e6, gamma=GAMMA, **grid):
+    """Flow round the C-grid section: uniform free stream (rho = 1, p = 1/gamma, |U| = mach) at
+    incidence alpha, isothermal no-slip section at the free-stream stagnation temperature, wake cut,
+    Dirichlet free stream on the outer line, outflow at the two wake ends; mu from Re on the chord."""
+    nodes = naca0012_cgrid(n_wake, n_surf, n_normal, **grid)
+    n0, n1 = nodes.shape[1] - 1, nodes.shape[0] - 1
+    al = math.radians(alpha_deg)
+    free = (1.0, mach * math.cos(al), mach * math.sin(al), 1.0 / gamma)
+    prim = np.zeros((4, n1, n0))
+    for v in range(4):
+        prim[v] = free[v]
+    T_inf = 1.0 / gamma
+    T_wall = T_inf * (1.0 + 0.5 * (gamma - 1.0) * mach * mach)
+    outer = np.tile(free, (n0, 1))
+    return dict(dim=2, n=(n0, n1), nodes=nodes, bc=[[4, 4], [2, 3]], bc_prim=[[None, None], [None, outer]],
+                prim=prim, T_wall=T_wall, mu=mach / Re, wake_cut=n_wake,
+                dx=[np.full(n0, 1.0 / n0), np.full(n1, 1.0 / n1)])
 
 
 # ------------------------------------------------------------------------------------------------
