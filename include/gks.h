@@ -79,6 +79,10 @@ typedef struct {
   int bc[3][2];                  /* GKS_BC_* for [axis][lo, hi]; periodic must be set on both sides */
   const double* bc_data[3][2];   /* host, GKS_BC_DIRICHLET only: primitive (rho, u.., p) per boundary
                                     cell, cells ordered by the other axes in increasing order, [cell][nv] */
+  int wake_cut;                  /* body-fitted 2D C-grids (gks_set_nodes, gks_steady_create): the first
+                                    and last wake_cut cells of the j-lo side form a wake cut, the ghost
+                                    cell (i, -k) being the cell (n0 - 1 - i, k - 1) across it (state,
+                                    fields, centroid); the rest of that side keeps bc[1][0].  0: none */
 } gks_grid;
 
 typedef struct {

@@ -497,6 +497,8 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     h->ncell *= h->n[d];
   }
   if (!(gas->gamma > 1.0)) return bad(GKS_EINVAL, "gamma must exceed 1");
+  if (grid->wake_cut < 0 || (grid->wake_cut > 0 && (D != 2 || 2 * grid->wake_cut > h->n[0])))
+    return bad(GKS_EINVAL, "a wake cut needs 2D and at most half the j-lo side on each end");
   const double bK = 2.0 / (gas->gamma - 1.0), K = bK - D;
   if (K < 0.0) return bad(GKS_EINVAL, "gamma leaves a negative number of internal degrees of freedom");
   if (!(gas->mu >= 0.0)) return bad(GKS_EINVAL, "mu must be >= 0");
@@ -660,6 +662,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   g.turb_cons = h->transport ? 1 : 0;
   g.limiter = num->limiter;
   g.abar_t0 = num->abar_mode == GKS_ABAR_T0;
+  g.wake_cut = grid->wake_cut;
   set_consts(g);
   h->base.f1 = h->f1;
   h->base.f2 = h->f2;
@@ -907,6 +910,7 @@ gks_status gks_step(gks_handle* h, double dt, double cfl, int nsteps, double t_e
   if (!h->has_state) return fail(h, GKS_EINVAL, "no state set");
   if (!(dt > 0.0) && !(cfl > 0.0)) return fail(h, GKS_EINVAL, "need dt > 0 or cfl > 0");
   if (h->base.g.turb_model != GKS_TURB_NONE && !h->has_turb) return fail(h, GKS_EINVAL, "turbulence fields not set");
+  if (h->base.g.wake_cut > 0 && !h->curv) return fail(h, GKS_EINVAL, "a wake cut needs a body-fitted grid");
   if (nsteps == 0) return GKS_OK;
   DeviceGuard dg(h->dev);
   {
@@ -1109,7 +1113,7 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
   int* bad_dev = (int*)((char*)h->staging + ((nb + 7) / 8) * 8);
   GKS_CK(h, cudaMemsetAsync(bad_dev, 0, sizeof(int), h->stream));
   const bool periodic[2] = {h->base.g.bc[0][0] == GKS_BC_PERIODIC, h->base.g.bc[1][0] == GKS_BC_PERIODIC};
-  cudaError_t e = curv_metrics(src, n0, n1, periodic, h->prec, G, bad_dev, h->stream);
+  cudaError_t e = curv_metrics(src, n0, n1, periodic, h->base.g.wake_cut, h->prec, G, bad_dev, h->stream);
   if (e != cudaSuccess) {
     free_curv(h);
     return cuda_fail(h, e, "curvilinear metrics");

@@ -52,12 +52,16 @@ __device__ void mid(const double* nodes, int n0, int i0, int j0, int i1, int j1,
 
 // Centroid of cell (i, j) of a stencil along axis a: at most two layers outside the grid along a,
 // the other index inside.
-__device__ void centroid(const double* nodes, int n0, int n1, int a, bool periodic, int i, int j, double& x,
-                         double& y) {
+__device__ void centroid(const double* nodes, int n0, int n1, int a, bool periodic, int cut, int i, int j,
+                         double& x, double& y) {
   const int n = a == 0 ? n0 : n1;
   const int c = a == 0 ? i : j;
   if (c >= 0 && c < n) {
     centroid_in(nodes, n0, i, j, x, y);
+    return;
+  }
+  if (a == 1 && c < 0 && cut > 0 && (i < cut || i >= n0 - cut)) {  // across a C-grid wake cut
+    centroid_in(nodes, n0, n0 - 1 - i, -c - 1, x, y);
     return;
   }
   double lx, ly, hx, hy;  // midpoints of the low and high boundary faces of this grid line
@@ -117,7 +121,8 @@ __global__ void metrics_cell_kernel(const double* nodes, int n0, int n1, double*
 
 // Per-face metrics along axis a, in the order of CurvGeom::face.
 template <class R>
-__global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, bool periodic, R* out, long nf) {
+__global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, bool periodic, int cut, R* out,
+                                    long nf) {
   const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   const int nfa = a == 0 ? n0 + 1 : n0;
@@ -133,7 +138,7 @@ __global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, 
   double cx[4], cy[4];
   for (int s = 0; s < 4; ++s) {
     const int ci = a == 0 ? fi - 2 + s : fi, cj = a == 0 ? fj : fj - 2 + s;
-    centroid(nodes, n0, n1, a, periodic, ci, cj, cx[s], cy[s]);
+    centroid(nodes, n0, n1, a, periodic, cut, ci, cj, cx[s], cy[s]);
   }
   const double g[8] = {nx,
                        ny,
@@ -658,18 +663,18 @@ void step_prec(const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s
 
 }  // namespace
 
-cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int prec, CurvGeom& G,
-                         int* bad, cudaStream_t s) {
+cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int cut, int prec,
+                         CurvGeom& G, int* bad, cudaStream_t s) {
   const long nc = (long)n0 * n1;
   if (prec == PREC_F64) {
     metrics_cell_kernel<double><<<blocks_for(nc), kCurvThreads, 0, s>>>(nodes, n0, n1, G.area, (double*)G.iarea, bad);
     for (int a = 0; a < 2; ++a)
-      metrics_face_kernel<double><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a],
+      metrics_face_kernel<double><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a], cut,
                                                                                (double*)G.face[a], G.nf[a]);
   } else {
     metrics_cell_kernel<float><<<blocks_for(nc), kCurvThreads, 0, s>>>(nodes, n0, n1, G.area, (float*)G.iarea, bad);
     for (int a = 0; a < 2; ++a)
-      metrics_face_kernel<float><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a],
+      metrics_face_kernel<float><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a], cut,
                                                                              (float*)G.face[a], G.nf[a]);
   }
   return cudaGetLastError();

@@ -31,9 +31,10 @@ struct SteadyArgs {
 };
 
 // Metrics from nodes[(n1 + 1)][(n0 + 1)][2] (device, double); *bad (device) is or-ed with 1 if a
-// cell is not a convex counter-clockwise quadrilateral.
-cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int prec, CurvGeom& G,
-                         int* bad, cudaStream_t s);
+// cell is not a convex counter-clockwise quadrilateral.  cut: cells of a C-grid wake cut at each end
+// of the j-lo side (their ghost centroids are the centroids of the cells across the cut).
+cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int cut, int prec,
+                         CurvGeom& G, int* bad, cudaStream_t s);
 // The fused tile step (variant 0: 32 x 15 cells, 256 threads; variant 1: 16 x 7, 128 threads).
 cudaError_t prepare_curv();
 void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s);

@@ -537,7 +537,9 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   const int n0 = grid->n[0], n1 = grid->n[1];
   if (n0 < 2 || n1 < 2) return GKS_EINVAL;
   for (int l = 1; l < levels; ++l)
-    if ((n0 >> l) < 2 || (n1 >> l) < 2 || n0 % (1 << l) || n1 % (1 << l)) return GKS_EINVAL;
+    if ((n0 >> l) < 2 || (n1 >> l) < 2 || n0 % (1 << l) || n1 % (1 << l) || grid->wake_cut % (1 << l))
+      return GKS_EINVAL;
+  if (grid->wake_cut < 0 || 2 * grid->wake_cut > n0) return GKS_EINVAL;
   for (int d = 0; d < 2; ++d)
     for (int sd = 0; sd < 2; ++sd) {
       const int b = grid->bc[d][sd];
@@ -663,6 +665,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     g.turb_model = model;
     g.limiter = num->limiter;
     g.abar_t0 = num->abar_mode == GKS_ABAR_T0;
+    g.wake_cut = grid->wake_cut >> l;
     set_consts(g);
   }
   alloc((void**)&s->acc, sizeof(double));
@@ -677,8 +680,8 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   cudaMemsetAsync(s->bad, 0, sizeof(unsigned), s->stream);
   for (int l = 0; l < levels; ++l) {
     const bool periodic[2] = {grid->bc[0][0] == GKS_BC_PERIODIC, grid->bc[1][0] == GKS_BC_PERIODIC};
-    if (curv_metrics(s->L[l].nodes, s->L[l].n0, s->L[l].n1, periodic, s->prec, s->L[l].G, (int*)s->bad, s->stream) !=
-        cudaSuccess) {
+    if (curv_metrics(s->L[l].nodes, s->L[l].n0, s->L[l].n1, periodic, s->L[l].g.wake_cut, s->prec, s->L[l].G,
+                     (int*)s->bad, s->stream) != cudaSuccess) {
       cudaGetLastError();
       return bad(GKS_ECUDA);
     }

@@ -103,6 +103,7 @@ struct DevGrid {
   double gamma, bK, K, mu, C_a, T_wall, C_mu, beta_star;
   int turb_model, limiter, abar_t0;
   int turb_cons;  // the turbulence fields hold rho k and rho omega (k-omega transport), not k and omega
+  int wake_cut;   // 2D C-grids: the first and last wake_cut cells of the j-lo side form a wake cut
   // the constants above in each arithmetic type, filled by set_consts on the host (kernels read
   // them from the parameter bank instead of converting)
   Consts<float> kf;
@@ -284,6 +285,12 @@ __device__ void load_cell(const DevGrid& g, const void* Win, const Consts<typena
       }
     }
   }
+  if (D == 2 && g.wake_cut > 0 && c[1] < 0 && c[0] >= 0 && c[0] < g.n[0] &&
+      (c[0] < g.wake_cut || c[0] >= g.n[0] - g.wake_cut)) {  // C-grid wake cut: the cell across it
+    src[0] = g.n[0] - 1 - c[0];
+    src[1] = -c[1] - 1;
+    xf[1] = 0;
+  }
   load_stored<D, PREC>(g, Win, cell_index(g, src[0], src[1], src[2]), out);
   if (inside) return;
 #pragma unroll
@@ -307,8 +314,10 @@ __device__ void load_cell(const DevGrid& g, const void* Win, const Consts<typena
 }
 
 // Cell whose turbulence field value a (possibly ghost) cell takes: periodic axes wrap, other axes
-// the nearest interior cell.
+// the nearest interior cell, a C-grid wake cut the cell across the cut.
 __device__ __forceinline__ long field_cell(const DevGrid& g, int D, int i, int j, int k) {
+  if (D == 2 && g.wake_cut > 0 && j < 0 && i >= 0 && i < g.n[0] && (i < g.wake_cut || i >= g.n[0] - g.wake_cut))
+    return cell_index(g, g.n[0] - 1 - i, -j - 1, 0);  // across a C-grid wake cut
   int c[3] = {i, j, k};
   for (int a = 0; a < D; ++a) {
     const int n = g.n[a];

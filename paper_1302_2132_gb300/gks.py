@@ -39,7 +39,7 @@ class GksError(RuntimeError):
 
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", _I), ("n", _I * 3), ("lo", _D * 3), ("hi", _D * 3), ("dx", _PD * 3),
-                ("bc", (_I * 2) * 3), ("bc_data", (_PD * 2) * 3)]
+                ("bc", (_I * 2) * 3), ("bc_data", (_PD * 2) * 3), ("wake_cut", _I)]
 
 
 class _Gas(ctypes.Structure):
@@ -148,11 +148,12 @@ def komega_defaults(**over):
 
 
 def _structs(dim, n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model, C_mu, beta_star, C_a, limiter, expand,
-             precision, abar_mode, reconstruction):
+             precision, abar_mode, reconstruction, wake_cut=0):
     """gks_grid, gks_gas, gks_turb, gks_numerics and the arrays they point to."""
     keep = []
     g = _Grid()
     g.dim = dim
+    g.wake_cut = int(wake_cut)
     for d in range(3):
         g.n[d] = n[d] if d < dim else 1
         g.lo[d] = lo[d] if lo is not None and d < dim else 0.0
@@ -187,7 +188,7 @@ class Solver:
 
     def __init__(self, dim, n, bc, dx=None, lo=None, hi=None, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0,
                  turb_model="none", C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", expand="multid",
-                 precision="fp64", abar_mode="timeint", reconstruction="muscl2", stream=None):
+                 precision="fp64", abar_mode="timeint", reconstruction="muscl2", wake_cut=0, stream=None):
         import torch
         L = load()
         self.dim, self.nv = dim, dim + 2
@@ -195,7 +196,7 @@ class Solver:
         self.ncell = int(np.prod(self.n))
         g, gas, turb, num, self._keep = _structs(dim, self.n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model,
                                                  C_mu, beta_star, C_a, limiter, expand, precision, abar_mode,
-                                                 reconstruction)
+                                                 reconstruction, wake_cut)
         self.precision = num.precision
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = _V()
@@ -432,7 +433,8 @@ class SteadySolver:
     multigrid (gks_steady_* in include/gks.h).  nodes[(n1 + 1), (n0 + 1), 2] (host)."""
 
     def __init__(self, n, bc, nodes, levels=4, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model="none",
-                 C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", lusgs_tile=16, stream=None):
+                 C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", lusgs_tile=16, wake_cut=0,
+                 stream=None):
         import torch
         L = load()
         self.n = (int(n[0]), int(n[1]))
@@ -441,7 +443,7 @@ class SteadySolver:
         dx = [np.ones(self.n[0]), np.ones(self.n[1])]
         g, gas, turb, num, self._keep = _structs(2, self.n, bc, dx, None, None, bc_data, gamma, mu, T_wall, turb_model,
                                                  C_mu, beta_star, C_a, limiter, "directional", precision, "timeint",
-                                                 "muscl2")
+                                                 "muscl2", wake_cut)
         nodes = _f64(nodes)
         assert nodes.size == 2 * (self.n[0] + 1) * (self.n[1] + 1)
         self.stream = stream if stream is not None else torch.cuda.Stream()
