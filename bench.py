@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--workload", default="turb2d_1024",
                    choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
                             "corner2d_528x136", "corner2d_2112x544", "steady_corner_528x136",
-                            "steady_corner_2112x544"])
+                            "steady_corner_2112x544", "naca2d_608x160", "steady_naca_608x160"])
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
                    help="face reconstruction (the default is the second-order MUSCL the metric is quoted on)")
     p.add_argument("--no-e2e", action="store_true")
@@ -172,6 +172,22 @@ def make_workload(name, precision):
                          "Mach 2.85 / 24-degree compression corner, body-fitted %dx%d wall-clustered grid, k-omega "
                          "tau_t, 100 cycles from the inflow state (20 at CFL 1, 80 at CFL 4), flux windows CFL 0.5"
                          % (nx, ny))
+    if name in ("naca2d_608x160", "steady_naca_608x160"):
+        # the fine NACA 0012 C-grid size of the paper's Table 2: 2 x 112 wake + 384 surface cells, 160 rows
+        spec = inputs.naca0012_case(112, 384, 160, mach=0.8, alpha_deg=2.26, Re=9.0e6, dy1=2e-4, ratio=1.05,
+                                    R=10.0, x_out=10.0)
+        if name.startswith("steady_"):
+            return dict(spec=spec, steady=True, levels=4, precision=precision or "fp32",
+                        schedule=[(20, 1.0), (80, 4.0)],
+                        desc="steady solver (local time steps, LU-SGS on cell tiles, 4-level FAS multigrid) on a "
+                             "NACA 0012 C-grid 608x160 with a wake cut, M 0.8, incidence 2.26 degrees, Re 9e6, "
+                             "k-omega tau_t from free-stream fields, 100 cycles (20 at CFL 1, 80 at CFL 4)")
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega",
+                                       beta_star=0.09, C_a=0.5, limiter="vanleer", expand="directional",
+                                       wake_cut=spec["wake_cut"]),
+                    nsteps=2000, t_end=0.0, precision=precision or "fp32", nodes=spec["nodes"],
+                    desc="NACA 0012 C-grid 608x160 with a wake cut, M 0.8, incidence 2.26 degrees, Re 9e6, "
+                         "k-omega tau_t, directional expansion in each face's frame, 2000 CFL steps")
     if name.startswith("corner2d_"):
         nx, ny = (int(v) for v in name.split("_")[1].split("x"))
         spec = inputs.compression_corner(nx, ny, alpha_deg=24.0)
@@ -240,7 +256,8 @@ def run_steady(args, wl):
     levels = wl["levels"]
     s = gks.SteadySolver(n, spec["bc"], spec["nodes"], levels=levels, bc_data=spec["bc_prim"], gamma=1.4,
                          mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega", beta_star=0.09, C_a=0.5,
-                         limiter="vanleer", precision=wl["precision"], lusgs_tile=args.lusgs_tile)
+                         limiter="vanleer", precision=wl["precision"], lusgs_tile=args.lusgs_tile,
+                         wake_cut=spec.get("wake_cut", 0))
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
     s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

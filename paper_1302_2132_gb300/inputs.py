@@ -416,7 +416,8 @@ def naca0012_cgrid(n_wake, n_surf, n_normal, R=5.0, x_out=6.0, dy1=2e-3, ratio=1
 def naca0012_case(n_wake, n_surf, n_normal, mach=0.8, alpha_deg=2.26, Re=9.0e6, gamma=GAMMA, **grid):
     """Flow round the C-grid section: uniform free stream (rho = 1, p = 1/gamma, |U| = mach) at
     incidence alpha, isothermal no-slip section at the free-stream stagnation temperature, wake cut,
-    Dirichlet free stream on the outer line, outflow at the two wake ends; mu from Re on the chord."""
+    Dirichlet free stream on the outer line, outflow at the two wake ends; mu from Re on the chord;
+    uniform free-stream k = 1e-4 |U|^2 and omega = 10 |U| (per unit chord)."""
     nodes = naca0012_cgrid(n_wake, n_surf, n_normal, **grid)
     n0, n1 = nodes.shape[1] - 1, nodes.shape[0] - 1
     al = math.radians(alpha_deg)
@@ -429,7 +430,8 @@ def naca0012_case(n_wake, n_surf, n_normal, mach=0.8, alpha_deg=2.26, Re=9.0e6, 
     outer = np.tile(free, (n0, 1))
     return dict(dim=2, n=(n0, n1), nodes=nodes, bc=[[4, 4], [2, 3]], bc_prim=[[None, None], [None, outer]],
                 prim=prim, T_wall=T_wall, mu=mach / Re, wake_cut=n_wake,
-                dx=[np.full(n0, 1.0 / n0), np.full(n1, 1.0 / n1)])
+                dx=[np.full(n0, 1.0 / n0), np.full(n1, 1.0 / n1)],
+                f1=np.full(n0 * n1, 1e-4 * mach * mach), f2=np.full(n0 * n1, 10.0 * mach))
 
 
 # ------------------------------------------------------------------------------------------------
