@@ -273,6 +273,9 @@ __global__ void __launch_bounds__(kCurvThreads) curv_rate_kernel(const __grid_co
 template <int V> struct CurvTile;
 template <> struct CurvTile<0> { static constexpr int X = 32, Y = 15, T = 256; };
 template <> struct CurvTile<1> { static constexpr int X = 16, Y = 7, T = 128; };
+// 16 x 11: 379 faces fill three rounds of 128 threads; one wave of 4 CTAs per SM covers the paper's
+// fine aerofoil grid (608 x 160: 570 tiles)
+template <> struct CurvTile<2> { static constexpr int X = 16, Y = 11, T = 128; };
 
 template <int V>
 struct CurvTileGeom {
@@ -657,8 +660,10 @@ template <int PREC>
 void step_prec(const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s) {
   if (variant == 0)
     launch_fused<PREC, 0>(A, G, s);
-  else
+  else if (variant == 1)
     launch_fused<PREC, 1>(A, G, s);
+  else
+    launch_fused<PREC, 2>(A, G, s);
 }
 
 }  // namespace
@@ -682,9 +687,12 @@ cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodi
 
 cudaError_t prepare_curv() {
   cudaError_t e = cudaSuccess;
-  const cudaError_t r[8] = {prepare_fused<PREC_F64, 0>(),    prepare_fused<PREC_F64, 1>(),
+  const cudaError_t r[13] = {prepare_fused<PREC_F64, 0>(),   prepare_fused<PREC_F64, 1>(),
                             prepare_fused<PREC_F32, 0>(),    prepare_fused<PREC_F32, 1>(),
                             prepare_fused<PREC_F32D, 0>(),   prepare_fused<PREC_F32D, 1>(),
+                            prepare_fused<PREC_F64, 2>(),    prepare_fused<PREC_F32, 2>(),
+                            prepare_fused<PREC_F32D, 2>(),   prepare_fused<PREC_F64, 2, 1>(),
+                            prepare_fused<PREC_F32, 2, 1>(),
                             prepare_fused<PREC_F64, 0, 1>(), prepare_fused<PREC_F32, 0, 1>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
@@ -701,8 +709,8 @@ void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int varian
 }
 
 void curv_tile_shape(int variant, int* x, int* y) {
-  *x = variant == 0 ? CurvTile<0>::X : CurvTile<1>::X;
-  *y = variant == 0 ? CurvTile<0>::Y : CurvTile<1>::Y;
+  *x = variant == 0 ? CurvTile<0>::X : (variant == 1 ? CurvTile<1>::X : CurvTile<2>::X);
+  *y = variant == 0 ? CurvTile<0>::Y : (variant == 1 ? CurvTile<1>::Y : CurvTile<2>::Y);
 }
 
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s) {
@@ -716,10 +724,13 @@ void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream
 }
 
 void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s) {
+  // 32 x 15 tiles on grids of two or more waves of them, 16 x 11 tiles (one wave of four CTAs per SM
+  // covers 107k cells) on the smaller grids and coarse multigrid levels
+  const bool big = A.g.ncell >= 300000;
   if (prec == PREC_F64)
-    launch_fused<PREC_F64, 0, 1>(A, G, s, SA);
+    big ? launch_fused<PREC_F64, 0, 1>(A, G, s, SA) : launch_fused<PREC_F64, 2, 1>(A, G, s, SA);
   else
-    launch_fused<PREC_F32, 0, 1>(A, G, s, SA);
+    big ? launch_fused<PREC_F32, 0, 1>(A, G, s, SA) : launch_fused<PREC_F32, 2, 1>(A, G, s, SA);
 }
 
 void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s) {

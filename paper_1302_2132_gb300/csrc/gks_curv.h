@@ -35,11 +35,12 @@ struct SteadyArgs {
 // of the j-lo side (their ghost centroids are the centroids of the cells across the cut).
 cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodic[2], int cut, int prec,
                          CurvGeom& G, int* bad, cudaStream_t s);
-// The fused tile step (variant 0: 32 x 15 cells, 256 threads; variant 1: 16 x 7, 128 threads).
+// The fused tile step (variant 0: 32 x 15 cells, 256 threads; variant 1: 16 x 7, 128 threads;
+// variant 2: 16 x 11, 128 threads).
 cudaError_t prepare_curv();
 void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s);
 void curv_tile_shape(int variant, int* x, int* y);
-constexpr int kCurvVariants = 2;
+constexpr int kCurvVariants = 3;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
 void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s);
 // steady solver pieces (FP64 and FP32 state): the residual of A.Win, the local explicit steps

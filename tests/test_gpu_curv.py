@@ -179,3 +179,15 @@ def test_invalid_and_unsupported_grids_are_rejected():
         gpu_solver(spec, multid=0, recon=2).set_nodes(spec["nodes"])
     with pytest.raises(gks.GksError):
         gpu_solver(spec, multid=0, turb_model=4).set_nodes(spec["nodes"])
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2"])
+def test_every_tile_shape_matches_oracle(monkeypatch, variant):
+    """The three tile shapes of the curvilinear step (32 x 15, 16 x 7, 16 x 11; forced instead of
+    autotuned) evaluate the same faces: FP64 parity on a corner grid that none of them divides."""
+    monkeypatch.setenv("GKS_TILE_VARIANT", variant)
+    spec = corner_spec(70, 37)
+    s, Wg, Wo = curv_both(spec, 3, turb_model=3, C_a=0.5)
+    assert s.tile_shape()[0] == int(variant)
+    assert np.all(rel_err_per_var(Wg, Wo, 4) < 1e-12)
+    s.close()
