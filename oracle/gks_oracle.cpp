@@ -1065,7 +1065,7 @@ int flow_step(const orc_problem* P, double* W, const double* f1, const double* f
 //   mu_T = rho k / omega~, omega~ = max(omega, C_lim sqrt(2 Sbar:Sbar / beta*)), Sbar = S - (div U)/3 I,
 //   beta = beta0 f_beta, f_beta = (1 + 85 chi)/(1 + 100 chi), chi = |Omega_ij Omega_jk Shat_ki| / (beta* omega)^3,
 //   Shat = S - (div U)/2 I, sigma_d = sigma_do where grad k . grad omega > 0, else 0.
-// Discretisation (the reading of this build): convective flux F_rho * phi_face with F_rho the
+// Discretisation (a reading; the paper gives none): convective flux F_rho * phi_face with F_rho the
 // face's time-integrated GKS mass flux and phi_face the upwind cell's value plus half its limited
 // slope times (width - F_rho / rho), the face value at the half time (MUSCL-Hancock, second order
 // for smooth advection); diffusive flux dt (mu + sigma rho k / omega |face) (phi_R - phi_L) /
@@ -1519,7 +1519,7 @@ void curv_fluxes(const CurvCtx& C, double dt, const std::vector<double>* win, bo
 
 // ---------------------------------------------------------------------------------------------
 // Steady-state solver on curvilinear grids (Section 4: local time steps, LU-SGS smoothing in the
-// form of Yoon and Jameson, multigrid after Jameson).  The readings of this build:
+// form of Yoon and Jameson, multigrid after Jameson; the paper gives no formulas).  The readings:
 //   - local explicit step s_i = 2 A_i / sum_faces (|U.n| + c) L (CFL 1); a face integrates its flux
 //     over the window cfl_flux min(s_l, s_r) (a ghost cell has its source cell's step) and divides by
 //     the window, so the steady operator does not depend on the pseudo-time step cfl s_i of the
