@@ -36,7 +36,9 @@
  *     line with centroid distances (vertex-average centroids, ghosts mirrored through the boundary
  *     face or translated by the period); the face flux is weighted by the face length and the
  *     update divided by the cell area; tau_t takes Green-Gauss velocity gradients (face value the
- *     mean of the two cells) and a ghost cell the value of its source cell.
+ *     mean of the two cells) and a ghost cell the value of its source cell.  The multi-dimensional
+ *     expansion takes tangential slopes in the face frame: limited differences along the transverse
+ *     grid line, each over the centroid step projected on the face tangent.
  *   - Steady-state solver (Section 4 names local time stepping, LU-SGS after Yoon and Jameson and
  *     4-level multigrid without formulas): see the block before curv_lts.
  */
@@ -1291,7 +1293,7 @@ CurvGeom curv_geometry(const orc_problem* P, const double* nodes) {
   // centroids with ghosts: on a periodic axis a ghost is its source cell translated by the period
   // (the difference of the two boundary face midpoints), on other axes the mirror image of the
   // interior cell through the boundary face midpoint -- the positions the ghost widths of a
-  // rectilinear grid give.  The i ghosts first, then the j ghosts over the padded i range.
+  // rectilinear grid give.  The i ghosts first, then the j ghosts, then the corners.
   g.pcx.assign((size_t)(n0 + 4) * (n1 + 4), 0.0);
   g.pcy.assign(g.pcx.size(), 0.0);
   for (int j = 0; j < n1; ++j)
@@ -1331,6 +1333,20 @@ CurvGeom curv_geometry(const orc_problem* P, const double* nodes) {
         }
         if (in_cut(P, i)) X[q][g.pidx(i, -k)] = X[q][g.pidx(n0 - 1 - i, k - 1)];  // the cell across the cut
       }
+    }
+  // corners (both indices outside): the parallelogram of the i ghost, the j ghost and their common
+  // source cell, c(i, j) = c(i, js) + c(is, j) - c(is, js) (on a rectilinear grid the ghost widths'
+  // corner; only the multi-dimensional expansion reaches corners)
+  auto src_of = [](int c, int n, bool per) {
+    const int k = c < 0 ? -c : c - n + 1;
+    return per ? (c < 0 ? n - k : k - 1) : (c < 0 ? k - 1 : n - k);
+  };
+  for (int j = -2; j < n1 + 2; ++j)
+    for (int i = -2; i < n0 + 2; ++i) {
+      if ((i >= 0 && i < n0) || (j >= 0 && j < n1)) continue;
+      const int is = src_of(i, n0, per0), js = src_of(j, n1, per1);
+      g.pcx[g.pidx(i, j)] = g.pcx[g.pidx(i, js)] + g.pcx[g.pidx(is, j)] - g.pcx[g.pidx(is, js)];
+      g.pcy[g.pidx(i, j)] = g.pcy[g.pidx(i, js)] + g.pcy[g.pidx(is, j)] - g.pcy[g.pidx(is, js)];
     }
   return g;
 }
@@ -1504,8 +1520,48 @@ void curv_fluxes(const CurvCtx& C, double dt, const std::vector<double>* win, bo
       fc.dxl = dl;
       fc.dxr = dr;
       fc.tau_t = 0.5 * (C.tau_of(ci[1], cj[1]) + C.tau_of(ci[2], cj[2]));
+      if (P->multid && !first_order) {
+        // tangential slopes of the two cells in the face frame: limited differences along the
+        // transverse grid line, each divided by the centroid step projected on the tangent
+        // t = (-n_y, n_x)
+        const double tx = -nyf, ty = nxf;
+        for (int side = 0; side < 2; ++side) {
+          const int i0 = ci[1 + side], j0 = cj[1 + side];
+          int im = i0, jm = j0, ip = i0, jp = j0;
+          if (d == 0) {
+            jm -= 1;
+            jp += 1;
+          } else {
+            im -= 1;
+            ip += 1;
+          }
+          double rm[4], r0[4], rp[4];
+          const int cc[3][2] = {{im, jm}, {i0, j0}, {ip, jp}};
+          double* rr[3] = {rm, r0, rp};
+          for (int q = 0; q < 3; ++q) {
+            double w[5];
+            get_cell(G, Wp, cc[q][0], cc[q][1], 0, w);
+            rr[q][0] = w[0];
+            rr[q][1] = w[1] * nxf + w[2] * nyf;
+            rr[q][2] = -w[1] * nyf + w[2] * nxf;
+            rr[q][3] = w[3];
+          }
+          auto proj = [&](int ia, int ja, int ib, int jb) {
+            return (g.pcx[g.pidx(ib, jb)] - g.pcx[g.pidx(ia, ja)]) * tx + (g.pcy[g.pidx(ib, jb)] - g.pcy[g.pidx(ia, ja)]) * ty;
+          };
+          const double hm = proj(im, jm, i0, j0), hp = proj(i0, j0, ip, jp);
+          for (int v = 0; v < nv; ++v) {
+            const double s = limiter(P->limiter, (r0[v] - rm[v]) / hm, (rp[v] - r0[v]) / hp);
+            if (side == 0)
+              fc.tl[0][v] = s;
+            else
+              fc.tr[0][v] = s;
+          }
+        }
+      }
       FaceWork Wk;
-      face_setup(2, P->gamma, P->mu, P->C_a, win ? win[d][f] : dt, 0, P->abar_mode, fc, Wk);
+      face_setup(2, P->gamma, P->mu, P->C_a, win ? win[d][f] : dt, P->multid && !first_order ? 1 : 0, P->abar_mode,
+                 fc, Wk);
       double Fr[4];
       face_flux(Wk, Fr);
       double* Fo = d == 0 ? &Fi[f * nv] : &Fj[f * nv];

@@ -117,8 +117,11 @@ int orc_step_komega(const orc_problem* P, const orc_komega* c, double* W, double
  * evaluates the face flux with the centroid-to-midpoint distances, rotates the momentum flux back
  * and weights it by the face length; a cell's update divides by its area.  Ghost cells follow
  * the boundary rules of the index lattice; ghost centroids are interior centroids reflected
- * through the boundary face midpoints; the turbulent relaxation time uses Green-Gauss gradients
- * (face velocity = mean of the two cells) and a ghost cell takes its source cell's value. */
+ * through the boundary face midpoints (translated by the period on periodic axes; corners by the
+ * parallelogram rule); the turbulent relaxation time uses Green-Gauss gradients (face velocity =
+ * mean of the two cells) and a ghost cell takes its source cell's value.  With P->multid the face
+ * also takes tangential slopes of its two cells: limited differences along the transverse grid
+ * line over the centroid steps projected on the face tangent. */
 /* Status 2 (nothing updated): a cell that is not a convex counter-clockwise quadrilateral. */
 int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
                   double dt, int nthreads);

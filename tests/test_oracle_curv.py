@@ -14,24 +14,26 @@ from paper_1302_2132_gb300 import inputs
 GAMMA = 1.4
 
 
-def case_for(n0, n1, bc, turb=oracle.TURB_NONE, mu=1e-5, dx=None, **kw):
+def case_for(n0, n1, bc, turb=oracle.TURB_NONE, mu=1e-5, dx=None, multid=0, **kw):
     dx = dx if dx is not None else [np.full(n0, 1.0 / n0), np.full(n1, 1.0 / n1)]
-    return oracle.Case(2, (n0, n1), dx, bc, gamma=GAMMA, mu=mu, turb_model=turb, multid=0, **kw)
+    return oracle.Case(2, (n0, n1), dx, bc, gamma=GAMMA, mu=mu, turb_model=turb, multid=multid, **kw)
 
 
 def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+@pytest.mark.parametrize("multid", [0, 1])
 @pytest.mark.parametrize("turb", [oracle.TURB_NONE, oracle.TURB_KEPS, oracle.TURB_KOMEGA])
-def test_uniform_grid_equals_the_rectilinear_step(turb):
-    """On a uniform grid the face frames are the axes, centroid distances the widths and the
-    Green-Gauss velocity gradient the central difference, so a step equals the rectilinear
-    directional step to rounding (periodic turbulence with gradient-based tau_t)."""
+def test_uniform_grid_equals_the_rectilinear_step(turb, multid):
+    """On a uniform grid the face frames are the axes (a j-face's tangent is -x, the mirror image
+    of the rectilinear frame), centroid distances the widths and the Green-Gauss velocity gradient
+    the central difference, so a step equals the rectilinear step to rounding, with the directional
+    and with the multi-dimensional expansion (periodic turbulence with gradient-based tau_t)."""
     n = 20
     spec = inputs.turbulence(n, 2, seed=4)
     h = spec["dx"][0][0]
-    c = case_for(n, n, [(0, 0), (0, 0)], turb=turb, dx=spec["dx"], C_a=0.3)
+    c = case_for(n, n, [(0, 0), (0, 0)], turb=turb, dx=spec["dx"], C_a=0.3, multid=multid)
     nodes = inputs.uniform_nodes(n, n, n * h, n * h)
     W = c.prim_to_cons(spec["prim"].ravel())
     f1, f2 = spec["f1"].ravel(), spec["f2"].ravel()
@@ -46,14 +48,16 @@ def test_uniform_grid_equals_the_rectilinear_step(turb):
     assert rel(Wc, Wr) < 1e-14
 
 
-def test_stretched_rectilinear_grid_with_walls_equals_the_rectilinear_step():
+@pytest.mark.parametrize("multid", [0, 1])
+def test_stretched_rectilinear_grid_with_walls_equals_the_rectilinear_step(multid):
     """The Mach 2.85 shock / boundary-layer case on its wall-clustered grid (no-slip wall, Dirichlet
     inflow and top, outflow): ghost centroids mirrored through the boundary faces reproduce the
-    ghost widths, so the curvilinear step equals the rectilinear one (no turbulence model)."""
+    ghost widths (corner ghosts too, which the multi-dimensional expansion reaches), so the
+    curvilinear step equals the rectilinear one (no turbulence model)."""
     spec = inputs.shock_boundary_layer(24, 30)
     n0, n1 = spec["n"]
     c = oracle.Case(2, spec["n"], spec["dx"], spec["bc"], gamma=GAMMA, mu=spec["mu"], T_wall=spec["T_wall"],
-                    multid=0, C_a=0.5, bc_prim=spec["bc_prim"])
+                    multid=multid, C_a=0.5, bc_prim=spec["bc_prim"])
     nodes = inputs.rectilinear_nodes(spec["dx"][0], spec["dx"][1])
     W = c.prim_to_cons(spec["prim"].ravel())
     for _ in range(3):
@@ -69,14 +73,15 @@ def test_stretched_rectilinear_grid_with_walls_equals_the_rectilinear_step():
         W = Wc
 
 
+@pytest.mark.parametrize("multid", [0, 1])
 @pytest.mark.parametrize("bc", [(0, 0), (1, 1)])
-def test_free_stream_is_preserved_on_a_skewed_grid(bc):
+def test_free_stream_is_preserved_on_a_skewed_grid(bc, multid):
     """Uniform flow through a smoothly skewed grid stays uniform: every cell's face normals times
     lengths sum to zero, and a uniform state has zero slopes, so only rounding remains (periodic and
     transmissive boundaries; k-epsilon tau_t is active but the strain rate is zero)."""
     n0, n1 = 18, 14
     nodes = inputs.wavy_nodes(n0, n1, amp=0.04, shear=0.06)
-    c = case_for(n0, n1, [bc, bc], turb=oracle.TURB_KEPS)
+    c = case_for(n0, n1, [bc, bc], turb=oracle.TURB_KEPS, multid=multid)
     prim = np.zeros((4, n1, n0))
     prim[0], prim[1], prim[2], prim[3] = 1.2, 0.45, -0.3, 1.0 / GAMMA
     W0 = c.prim_to_cons(prim.ravel())
@@ -90,7 +95,8 @@ def test_free_stream_is_preserved_on_a_skewed_grid(bc):
     assert np.abs(W - W0).max() < 1e-13
 
 
-def test_rotating_grid_and_flow_rotates_the_result():
+@pytest.mark.parametrize("multid", [0, 1])
+def test_rotating_grid_and_flow_rotates_the_result(multid):
     """Turning the grid nodes and the velocity by the same angle turns the momentum of the result
     and leaves density and energy unchanged (periodic box, k-omega tau_t from Green-Gauss
     gradients, whose strain-rate magnitude is frame invariant)."""
@@ -101,7 +107,7 @@ def test_rotating_grid_and_flow_rotates_the_result():
     prim = inputs.smooth_state_at(pts, seed=3)
     f1, f2 = inputs.positive_fields_at(pts, seed=5)
     f1, f2 = f1.ravel(), f2.ravel()
-    c = case_for(n0, n1, [(0, 0), (0, 0)], turb=oracle.TURB_KOMEGA, C_a=0.2)
+    c = case_for(n0, n1, [(0, 0), (0, 0)], turb=oracle.TURB_KOMEGA, C_a=0.2, multid=multid)
     W = c.prim_to_cons(prim.ravel())
     Wt = c.prim_to_cons(inputs.rotate_prim(prim, theta).ravel())
     nodes_t = inputs.rotate_nodes(nodes, theta)
@@ -181,3 +187,20 @@ def test_folded_cells_are_rejected():
     W = c.prim_to_cons(prim.ravel())
     _, st = c.step_curv(nodes, W, 1e-3)
     assert st == 2
+
+
+def test_multidimensional_expansion_changes_the_skewed_grid_step():
+    """The tangential slopes are in effect: on a skewed grid with a smooth flow the multi-dimensional
+    step differs from the directional one by far more than rounding, and both conserve."""
+    n0, n1 = 16, 12
+    nodes = inputs.wavy_nodes(n0, n1)
+    prim = inputs.smooth_state_at(inputs.cell_points(nodes), seed=8, amp=0.2)
+    out = []
+    for md in (0, 1):
+        c = case_for(n0, n1, [(0, 0), (0, 0)], multid=md, mu=1e-3)
+        W = c.prim_to_cons(prim.ravel())
+        dt = c.compute_dt_curv(nodes, W, 0.5)
+        Wn, st = c.step_curv(nodes, W, dt)
+        assert st == 0
+        out.append(Wn - W)
+    assert np.abs(out[1] - out[0]).max() > 1e-4 * np.abs(out[0]).max()
