@@ -127,8 +127,11 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
  * the grid line over centroid distances (vertex-average centroids; ghost centroids mirrored
  * through the boundary face midpoint, or translated by the period), the flux weighted by the face
  * length and the update divided by the cell area; tau_t from Green-Gauss velocity gradients (a
- * ghost cell takes its source cell's value); CFL rate sum_faces (|U.n| + c) L / (2 A).  Built for
- * dim 2, GKS_EXPAND_DIRECTIONAL, GKS_RECON_MUSCL2, no k-omega transport (GKS_EUNSUPPORTED
+ * ghost cell takes its source cell's value); CFL rate sum_faces (|U.n| + c) L / (2 A).  With
+ * GKS_EXPAND_MULTID each face also takes tangential slopes of its two cells in the face frame: limited
+ * differences along the transverse grid line over the centroid steps projected on the face tangent
+ * (corner ghost centroids by the parallelogram of the i ghost, the j ghost and their source cell).
+ * Built for dim 2, both expansions, GKS_RECON_MUSCL2, no k-omega transport (GKS_EUNSUPPORTED
  * otherwise), every precision.  May be called before or after gks_set_state; a second call
  * replaces the grid.  GKS_EINVAL for a folded or clockwise cell (the handle's grid is then the
  * rectilinear one again).
@@ -153,8 +156,8 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
  *     fields and Dirichlet data by means; coarse residuals first order with the forcing
  *     sum R_f - R_c(W_c^0); one LU-SGS smoothing per level on the way down, the corrections
  *     W_c - W_c^0 injected on the way up.
- * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), directional expansion,
- * MUSCL2, turbulence models NONE, MUT, KEPS, KOMEGA (prescribed fields).  nodes: host,
+ * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), both expansions (the
+ * multi-dimensional one on the finest level; coarse levels are first order), MUSCL2, turbulence models NONE, MUT, KEPS, KOMEGA (prescribed fields).  nodes: host,
  * [(n1 + 1)][(n0 + 1)][2] as gks_set_nodes.  Errors: GKS_EUNSUPPORTED for other options, GKS_EINVAL
  * for bad sizes, levels or a folded cell on any level. */
 typedef struct gks_steady gks_steady;

@@ -183,7 +183,7 @@ int tiles_for(const gks_handle* h, int variant) {
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
   if (h->curv) {
-    launch_curv_step(h->prec, A, h->cg, variant, h->stream);
+    launch_curv_step(h->prec, A, h->cg, variant, h->multid, h->stream);
     return;
   }
   if (h->recon == GKS_RECON_MUSCL3) {
@@ -323,6 +323,7 @@ void free_curv(gks_handle* h) {
   CurvGeom& G = h->cg;
   for (int a = 0; a < 2; ++a) {
     if (G.face[a]) cudaFree(G.face[a]);
+    if (G.tang[a]) cudaFree(G.tang[a]);
     if (G.flux[a]) cudaFree(G.flux[a]);
   }
   if (G.iarea) cudaFree(G.iarea);
@@ -1067,7 +1068,6 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
   if (!h || !nodes) return fail(h, GKS_EINVAL, "null argument");
   if (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE) return fail(h, GKS_EINVAL, "memspace");
   if (h->D != 2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids are built in 2D");
-  if (h->multid) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids take the directional expansion");
   if (h->recon != GKS_RECON_MUSCL2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids take MUSCL2 reconstruction");
   if (h->transport) return fail(h, GKS_EUNSUPPORTED, "k-omega transport on a curvilinear grid");
   DeviceGuard dg(h->dev);
@@ -1090,6 +1090,7 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
   };
   for (int a = 0; a < 2; ++a) {
     alloc(&G.face[a], rb * 8 * G.nf[a]);
+    alloc(&G.tang[a], rb * 4 * G.nf[a]);
     alloc(&G.flux[a], rb * 4 * G.nf[a]);
   }
   alloc(&G.iarea, rb * h->ncell);

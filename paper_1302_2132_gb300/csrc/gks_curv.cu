@@ -94,6 +94,32 @@ __device__ void centroid(const double* nodes, int n0, int n1, int a, bool period
   }
 }
 
+// Centroid of any cell at most two layers outside the grid: along one axis as above; a corner by the
+// parallelogram of its i ghost, its j ghost and their common source cell.
+__device__ int ghost_source(int c, int n, bool per) {
+  const int k = c < 0 ? -c : c - n + 1;
+  return per ? (c < 0 ? n - k : k - 1) : (c < 0 ? k - 1 : n - k);
+}
+__device__ void centroid_any(const double* nodes, int n0, int n1, bool per0, bool per1, int cut, int i, int j,
+                             double& x, double& y) {
+  const bool iin = i >= 0 && i < n0, jin = j >= 0 && j < n1;
+  if (jin) {
+    centroid(nodes, n0, n1, 0, per0, cut, i, j, x, y);
+    return;
+  }
+  if (iin) {
+    centroid(nodes, n0, n1, 1, per1, cut, i, j, x, y);
+    return;
+  }
+  const int is = ghost_source(i, n0, per0), js = ghost_source(j, n1, per1);
+  double ax, ay, bx, by, cx, cy;
+  centroid(nodes, n0, n1, 0, per0, cut, i, js, ax, ay);
+  centroid(nodes, n0, n1, 1, per1, cut, is, j, bx, by);
+  centroid_in(nodes, n0, is, js, cx, cy);
+  x = ax + bx - cx;
+  y = ay + by - cy;
+}
+
 __device__ __forceinline__ double dist(double ax, double ay, double bx, double by) {
   return sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
 }
@@ -121,8 +147,9 @@ __global__ void metrics_cell_kernel(const double* nodes, int n0, int n1, double*
 
 // Per-face metrics along axis a, in the order of CurvGeom::face.
 template <class R>
-__global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, bool periodic, int cut, R* out,
-                                    long nf) {
+__global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, bool per0, bool per1, int cut,
+                                    R* out, R* tang, long nf) {
+  const bool periodic = a == 0 ? per0 : per1;
   const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   const int nfa = a == 0 ? n0 + 1 : n0;
@@ -149,6 +176,19 @@ __global__ void metrics_face_kernel(const double* nodes, int n0, int n1, int a, 
                        dist(mx, my, cx[1], cy[1]),
                        dist(mx, my, cx[2], cy[2])};
   for (int q = 0; q < 8; ++q) out[(long)q * nf + f] = (R)g[q];
+  // tangential steps of the two cells beside the face: centroid steps to the transverse neighbours
+  // projected on the tangent t = (-n_y, n_x), inverted (the multi-dimensional expansion)
+  const double tx = -ny, ty = nx;
+  for (int side = 0; side < 2; ++side) {
+    const int i0 = a == 0 ? fi - 1 + side : fi, j0 = a == 0 ? fj : fj - 1 + side;
+    const int di = a == 0 ? 0 : 1, dj = a == 0 ? 1 : 0;
+    double mxx, myy, c0x, c0y, pxx, pyy;
+    centroid_any(nodes, n0, n1, per0, per1, cut, i0 - di, j0 - dj, mxx, myy);
+    centroid_any(nodes, n0, n1, per0, per1, cut, i0, j0, c0x, c0y);
+    centroid_any(nodes, n0, n1, per0, per1, cut, i0 + di, j0 + dj, pxx, pyy);
+    tang[(long)(2 * side) * nf + f] = (R)(1.0 / ((c0x - mxx) * tx + (c0y - myy) * ty));
+    tang[(long)(2 * side + 1) * nf + f] = (R)(1.0 / ((pxx - c0x) * tx + (pyy - c0y) * ty));
+  }
 }
 
 template <class R>
@@ -291,7 +331,8 @@ struct CurvTileGeom {
 // MODE 0: one time step (A.Win -> A.Wout, control block as the rectilinear step).  MODE 1: the
 // steady residual of A.Win (SteadyArgs): face windows cfl_flux min(s_l, s_r) from the local steps s,
 // flux rates times L summed per cell (plus the forcing) into R, tau_t of the tile cells stored.
-template <int PREC, int V, int MODE>
+// MD: the multi-dimensional expansion (tangential slopes of the two cells in the face frame).
+template <int PREC, int V, int MODE, bool MD>
 __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / CurvTile<V>::T)
     curv_step_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CurvGeom G,
                      const __grid_constant__ SteadyArgs SA) {
@@ -496,7 +537,40 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         const int tr_ = (lj + 1) * TX + li + 1;
         tau_t = R(0.5) * (Ts[tr_ - (a == 0 ? 1 : TX)] + Ts[tr_]);
       }
-      const R tl[1][4] = {{R(0), R(0), R(0), R(0)}}, trr[1][4] = {{R(0), R(0), R(0), R(0)}};
+      R tl[1][4] = {{R(0), R(0), R(0), R(0)}}, trr[1][4] = {{R(0), R(0), R(0), R(0)}};
+      if (MD && !fo) {
+        // tangential slopes: limited differences of the rotated states along the transverse grid
+        // line over the projected centroid steps (face records tang)
+        const long gf = a == 0 ? (long)(oy + lj) * (n0 + 1) + ox + li : (long)(oy + lj) * n0 + ox + li;
+        const R* tg = (const R*)G.tang[a];
+        const long nfa = a == 0 ? G.nf[0] : G.nf[1];
+        const int step = a == 0 ? HX : 1;  // transverse neighbour in the halo
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int h0 = a == 0 ? (lj + H) * HX + li + H - 1 + side : (lj + H - 1 + side) * HX + li + H;
+          const R ihm = tg[(long)(2 * side) * nfa + gf], ihp = tg[(long)(2 * side + 1) * nfa + gf];
+          R rm[4], rp[4];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int h = q == 0 ? h0 - step : h0 + step;
+            const R w0 = Ws[h], w1 = Ws[NH + h], w2 = Ws[2 * NH + h], w3 = Ws[3 * NH + h];
+            R* r = q == 0 ? rm : rp;
+            r[0] = w0;
+            r[1] = w1 * nx + w2 * ny;
+            r[2] = -w1 * ny + w2 * nx;
+            r[3] = w3;
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const R c0 = S4[1 + side][v];
+            const R t = limiter<R>(g.limiter, (c0 - rm[v]) * ihm, (rp[v] - c0) * ihp);
+            if (side == 0)
+              tl[0][v] = t;
+            else
+              trr[0][v] = t;
+          }
+        }
+      }
       R F[4], tau;
       R win = dt, Ls = L;
       if (MODE == 1) {  // window of the face from the local steps of its two cells
@@ -505,7 +579,10 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         win = (R)SA.cfl_flux * fmin(sloc[field_cell(g, 2, ai, aj, 0)], sloc[field_cell(g, 2, ox + li, oy + lj, 0)]);
         Ls = L / win;
       }
-      face_flux<2, R, false>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+      if (MD && !fo)
+        face_flux<2, R, true>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+      else
+        face_flux<2, R, false>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
       const R L_ = Ls;
       Fs[l] = F[0] * L_;
       Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;
@@ -626,18 +703,25 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   }
 }
 
-template <int PREC, int V, int MODE = 0>
+template <int PREC, int V, int MODE = 0, bool MD = false>
 void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const SteadyArgs& SA = SteadyArgs{}) {
   using TG = CurvTileGeom<V>;
   const int nt = ((A.g.n[0] + TG::X - 1) / TG::X) * ((A.g.n[1] + TG::Y - 1) / TG::Y);
-  curv_step_kernel<PREC, V, MODE><<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R>(), s>>>(A, G, SA);
+  curv_step_kernel<PREC, V, MODE, MD>
+      <<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R>(), s>>>(A, G, SA);
+}
+
+template <int PREC, int V, int MODE, bool MD>
+cudaError_t prepare_one() {
+  using TG = CurvTileGeom<V>;
+  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TG::template smem_bytes<typename PrecT<PREC>::R>());
 }
 
 template <int PREC, int V, int MODE = 0>
 cudaError_t prepare_fused() {
-  using TG = CurvTileGeom<V>;
-  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)TG::template smem_bytes<typename PrecT<PREC>::R>());
+  const cudaError_t a = prepare_one<PREC, V, MODE, false>(), b = prepare_one<PREC, V, MODE, true>();
+  return a != cudaSuccess ? a : b;
 }
 
 // Local explicit step (CFL 1) of every cell: 2 A / sum_faces (|U.n| + c) L.
@@ -656,14 +740,22 @@ __global__ void __launch_bounds__(kCurvThreads) lts_kernel(const __grid_constant
 
 inline unsigned blocks_for(long n) { return (unsigned)((n + kCurvThreads - 1) / kCurvThreads); }
 
-template <int PREC>
-void step_prec(const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s) {
+template <int PREC, bool MD>
+void step_prec_md(const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s) {
   if (variant == 0)
-    launch_fused<PREC, 0>(A, G, s);
+    launch_fused<PREC, 0, 0, MD>(A, G, s);
   else if (variant == 1)
-    launch_fused<PREC, 1>(A, G, s);
+    launch_fused<PREC, 1, 0, MD>(A, G, s);
   else
-    launch_fused<PREC, 2>(A, G, s);
+    launch_fused<PREC, 2, 0, MD>(A, G, s);
+}
+
+template <int PREC>
+void step_prec(const StepArgs& A, const CurvGeom& G, int variant, bool md, cudaStream_t s) {
+  if (md)
+    step_prec_md<PREC, true>(A, G, variant, s);
+  else
+    step_prec_md<PREC, false>(A, G, variant, s);
 }
 
 }  // namespace
@@ -674,13 +766,13 @@ cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodi
   if (prec == PREC_F64) {
     metrics_cell_kernel<double><<<blocks_for(nc), kCurvThreads, 0, s>>>(nodes, n0, n1, G.area, (double*)G.iarea, bad);
     for (int a = 0; a < 2; ++a)
-      metrics_face_kernel<double><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a], cut,
-                                                                               (double*)G.face[a], G.nf[a]);
+      metrics_face_kernel<double><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(
+          nodes, n0, n1, a, periodic[0], periodic[1], cut, (double*)G.face[a], (double*)G.tang[a], G.nf[a]);
   } else {
     metrics_cell_kernel<float><<<blocks_for(nc), kCurvThreads, 0, s>>>(nodes, n0, n1, G.area, (float*)G.iarea, bad);
     for (int a = 0; a < 2; ++a)
-      metrics_face_kernel<float><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(nodes, n0, n1, a, periodic[a], cut,
-                                                                             (float*)G.face[a], G.nf[a]);
+      metrics_face_kernel<float><<<blocks_for(G.nf[a]), kCurvThreads, 0, s>>>(
+          nodes, n0, n1, a, periodic[0], periodic[1], cut, (float*)G.face[a], (float*)G.tang[a], G.nf[a]);
   }
   return cudaGetLastError();
 }
@@ -699,13 +791,13 @@ cudaError_t prepare_curv() {
   return e;
 }
 
-void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s) {
+void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, bool multid, cudaStream_t s) {
   if (prec == PREC_F64)
-    step_prec<PREC_F64>(A, G, variant, s);
+    step_prec<PREC_F64>(A, G, variant, multid, s);
   else if (prec == PREC_F32)
-    step_prec<PREC_F32>(A, G, variant, s);
+    step_prec<PREC_F32>(A, G, variant, multid, s);
   else
-    step_prec<PREC_F32D>(A, G, variant, s);
+    step_prec<PREC_F32D>(A, G, variant, multid, s);
 }
 
 void curv_tile_shape(int variant, int* x, int* y) {
@@ -727,10 +819,17 @@ void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const 
   // 32 x 15 tiles on grids of two or more waves of them, 16 x 11 tiles (one wave of four CTAs per SM
   // covers 107k cells) on the smaller grids and coarse multigrid levels
   const bool big = A.g.ncell >= 300000;
-  if (prec == PREC_F64)
-    big ? launch_fused<PREC_F64, 0, 1>(A, G, s, SA) : launch_fused<PREC_F64, 2, 1>(A, G, s, SA);
-  else
-    big ? launch_fused<PREC_F32, 0, 1>(A, G, s, SA) : launch_fused<PREC_F32, 2, 1>(A, G, s, SA);
+  if (SA.multid) {
+    if (prec == PREC_F64)
+      big ? launch_fused<PREC_F64, 0, 1, true>(A, G, s, SA) : launch_fused<PREC_F64, 2, 1, true>(A, G, s, SA);
+    else
+      big ? launch_fused<PREC_F32, 0, 1, true>(A, G, s, SA) : launch_fused<PREC_F32, 2, 1, true>(A, G, s, SA);
+  } else {
+    if (prec == PREC_F64)
+      big ? launch_fused<PREC_F64, 0, 1>(A, G, s, SA) : launch_fused<PREC_F64, 2, 1>(A, G, s, SA);
+    else
+      big ? launch_fused<PREC_F32, 0, 1>(A, G, s, SA) : launch_fused<PREC_F32, 2, 1>(A, G, s, SA);
+  }
 }
 
 void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s) {

@@ -13,6 +13,8 @@ struct CurvGeom {
   void* face[2];  // per axis [8][nf], arithmetic type: n_x, n_y, L, 1/d01, 1/d12, 1/d23, d_l, d_r
                   // (d01, d12, d23 the centroid distances of the four-cell stencil along the grid
                   // line, d_l, d_r the distances from the two adjacent centroids to the face midpoint)
+  void* tang[2];  // per axis [4][nf], arithmetic type: 1/hm, 1/hp of the left and of the right cell,
+                  // hm, hp the centroid steps to the transverse neighbours projected on the tangent
   void* iarea;    // 1 / area per cell, arithmetic type
   double* area;   // area per cell
   void* tau;      // per-cell turbulent relaxation time of the current step, arithmetic type
@@ -28,6 +30,7 @@ struct SteadyArgs {
   const void* forcing;    // [4][ncell] or null
   void* tau;              // out: tau_t per cell
   double* res_acc;        // if set: += sum over cells of (R_rho / A)^2
+  int multid;             // multi-dimensional expansion (second-order levels only)
 };
 
 // Metrics from nodes[(n1 + 1)][(n0 + 1)][2] (device, double); *bad (device) is or-ed with 1 if a
@@ -38,7 +41,7 @@ cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodi
 // The fused tile step (variant 0: 32 x 15 cells, 256 threads; variant 1: 16 x 7, 128 threads;
 // variant 2: 16 x 11, 128 threads).
 cudaError_t prepare_curv();
-void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s);
+void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, bool multid, cudaStream_t s);
 void curv_tile_shape(int variant, int* x, int* y);
 constexpr int kCurvVariants = 3;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);

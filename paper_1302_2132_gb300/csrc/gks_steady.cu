@@ -351,6 +351,7 @@ struct gks_steady {
   int prec = PREC_F64;
   int levels = 1;
   int tile = 16;  // LU-SGS tile edge
+  int multid = 0;  // multi-dimensional expansion on the finest level
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<SteadyLevel> L;
@@ -386,7 +387,8 @@ size_t rbytes(int prec) { return prec == PREC_F64 ? 8 : 4; }
 
 void free_level(SteadyLevel& l) {
   void* ps[] = {l.nodes, l.W, l.W0, l.R, l.P, l.s, l.hl[0], l.hl[1], l.f1, l.f2, l.G.face[0], l.G.face[1],
-                l.G.iarea, l.G.area, l.G.tau, l.G.flux[0], l.G.flux[1], l.dir[0][0], l.dir[0][1], l.dir[1][0],
+                l.G.iarea, l.G.area, l.G.tau, l.G.flux[0], l.G.flux[1], l.G.tang[0], l.G.tang[1], l.dir[0][0],
+                l.dir[0][1], l.dir[1][0],
                 l.dir[1][1]};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -436,6 +438,7 @@ void residual(gks_steady* s, int l, const void* Win, const void* forcing, double
   SA.forcing = forcing;
   SA.tau = lev.G.tau;
   SA.res_acc = acc;
+  SA.multid = s->multid;
   launch_curv_residual(s->prec, A, lev.G, SA, s->stream);
 }
 
@@ -527,8 +530,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   if (!out) return GKS_EINVAL;
   *out = nullptr;
   if (!grid || !gas || !num || !nodes) return GKS_EINVAL;
-  if (grid->dim != 2 || num->expand != GKS_EXPAND_DIRECTIONAL || num->reconstruction != GKS_RECON_MUSCL2)
-    return GKS_EUNSUPPORTED;
+  if (grid->dim != 2 || num->reconstruction != GKS_RECON_MUSCL2) return GKS_EUNSUPPORTED;
   if (num->precision != GKS_FP64 && num->precision != GKS_FP32) return GKS_EUNSUPPORTED;
   const int model = turb ? turb->model : GKS_TURB_NONE;
   if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA) return GKS_EUNSUPPORTED;
@@ -553,6 +555,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   s->prec = num->precision == GKS_FP64 ? PREC_F64 : PREC_F32;
   s->levels = levels;
   s->tile = lusgs_tile == 32 ? 32 : 16;
+  s->multid = num->expand == GKS_EXPAND_MULTID;
   auto bad = [&](gks_status st) {
     free_steady(s);
     delete s;
@@ -614,6 +617,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     alloc((void**)&lev.nodes, sizeof(double) * 2 * (size_t)(lev.n0 + 1) * (lev.n1 + 1));
     for (int a = 0; a < 2; ++a) {
       alloc(&G.face[a], rb * 8 * G.nf[a]);
+      alloc(&G.tang[a], rb * 4 * G.nf[a]);
       alloc(&lev.hl[a], rb * G.nf[a]);
     }
     alloc(&G.iarea, rb * lev.ncell);
@@ -839,6 +843,7 @@ gks_status gks_steady_residual(gks_steady* s, double cfl_flux, int first_order, 
   SA.s_loc = f.s;
   SA.cfl_flux = cfl_flux;
   SA.first_order = first_order != 0;
+  SA.multid = s->multid;
   SA.R = f.R;
   SA.tau = f.G.tau;
   launch_curv_residual(s->prec, A, f.G, SA, s->stream);

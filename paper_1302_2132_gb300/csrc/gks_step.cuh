@@ -285,9 +285,9 @@ __device__ void load_cell(const DevGrid& g, const void* Win, const Consts<typena
       }
     }
   }
-  if (D == 2 && g.wake_cut > 0 && c[1] < 0 && c[0] >= 0 && c[0] < g.n[0] &&
-      (c[0] < g.wake_cut || c[0] >= g.n[0] - g.wake_cut)) {  // C-grid wake cut: the cell across it
-    src[0] = g.n[0] - 1 - c[0];
+  // C-grid wake cut: the cell across it (for a corner, across from the column the i rule picks)
+  if (D == 2 && g.wake_cut > 0 && c[1] < 0 && (src[0] < g.wake_cut || src[0] >= g.n[0] - g.wake_cut)) {
+    src[0] = g.n[0] - 1 - src[0];
     src[1] = -c[1] - 1;
     xf[1] = 0;
   }

@@ -18,9 +18,9 @@ def case(nw=16, ns=64, n1=24, turb=3):
     return sp
 
 
-def oracle_of(sp, limiter=1):
+def oracle_of(sp, limiter=1, multid=0):
     return oracle.Case(2, sp["n"], sp["dx"], sp["bc"], gamma=GAMMA, mu=sp["mu"], T_wall=sp["T_wall"],
-                       turb_model=sp["turb"], multid=0, C_a=0.5, limiter=limiter, bc_prim=sp["bc_prim"],
+                       turb_model=sp["turb"], multid=multid, C_a=0.5, limiter=limiter, bc_prim=sp["bc_prim"],
                        wake_cut=sp["wake_cut"])
 
 
@@ -29,15 +29,16 @@ def rel_per_var(a, b):
     return np.array([np.abs(a[v] - b[v]).max() / np.abs(b[v]).max() for v in range(4)])
 
 
+@pytest.mark.parametrize("expand", ["directional", "multid"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_time_steps_on_a_c_grid_match_oracle(precision):
+def test_time_steps_on_a_c_grid_match_oracle(precision, expand):
     from paper_1302_2132_gb300 import gks
     sp = case()
     s = gks.Solver(2, sp["n"], sp["bc"], dx=sp["dx"], bc_data=sp["bc_prim"], gamma=GAMMA, mu=sp["mu"],
-                   T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=0.5, limiter="vanleer", expand="directional",
+                   T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=0.5, limiter="vanleer", expand=expand,
                    precision=precision, wake_cut=sp["wake_cut"])
     s.set_nodes(sp["nodes"])
-    c = oracle_of(sp)
+    c = oracle_of(sp, multid=int(expand == "multid"))
     s.set_state(np.asarray(sp["prim"], dtype=np.float64).ravel(), layout="soa_prim")
     s.set_turbulence(sp["f1"], sp["f2"])
     W = c.prim_to_cons(np.asarray(sp["prim"], dtype=np.float64).ravel())
@@ -58,13 +59,14 @@ def test_time_steps_on_a_c_grid_match_oracle(precision):
     s.close()
 
 
-def test_steady_cycles_on_a_c_grid_match_oracle():
+@pytest.mark.parametrize("multid", [0, 1])
+def test_steady_cycles_on_a_c_grid_match_oracle(multid):
     from paper_1302_2132_gb300 import gks
     sp = case(nw=16, ns=64, n1=24)
     s = gks.SteadySolver(sp["n"], sp["bc"], sp["nodes"], levels=3, bc_data=sp["bc_prim"], gamma=GAMMA, mu=sp["mu"],
                          T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=0.5, limiter="vanleer", precision="fp64",
-                         lusgs_tile=16, wake_cut=sp["wake_cut"])
-    c = oracle_of(sp)
+                         lusgs_tile=16, wake_cut=sp["wake_cut"], expand="multid" if multid else "directional")
+    c = oracle_of(sp, multid=multid)
     W = c.prim_to_cons(np.asarray(sp["prim"], dtype=np.float64).ravel())
     s.set_state(W)
     s.set_turbulence(sp["f1"], sp["f2"])

@@ -25,10 +25,10 @@ def corner_spec(nx, ny, alpha=24.0):
     return spec
 
 
-def curv_both(spec, nsteps, turb_model=0, precision="fp64", cfl=0.5, C_a=0.0, mu=None, check_dt=True):
+def curv_both(spec, nsteps, turb_model=0, precision="fp64", cfl=0.5, C_a=0.0, mu=None, check_dt=True, multid=0):
     mu = spec.get("mu", 1e-5) if mu is None else mu
-    s = gpu_solver(spec, turb_model=turb_model, multid=0, precision=precision, C_a=C_a, mu=mu)
-    c = oracle_case(spec, turb_model=turb_model, multid=0, C_a=C_a, mu=mu)
+    s = gpu_solver(spec, turb_model=turb_model, multid=multid, precision=precision, C_a=C_a, mu=mu)
+    c = oracle_case(spec, turb_model=turb_model, multid=multid, C_a=C_a, mu=mu)
     s.set_nodes(spec["nodes"])
     prim = np.asarray(spec["prim"], dtype=np.float64).ravel()
     s.set_state(prim, layout="soa_prim")
@@ -60,18 +60,20 @@ def cases():
     }
 
 
+@pytest.mark.parametrize("multid", [0, 1])
 @pytest.mark.parametrize("name", list(cases()))
-def test_fp64_curvilinear_step_matches_oracle(name):
+def test_fp64_curvilinear_step_matches_oracle(name, multid):
     spec, kw, steps = cases()[name]
-    s, Wg, Wo = curv_both(spec, steps, **kw)
+    s, Wg, Wo = curv_both(spec, steps, multid=multid, **kw)
     assert np.all(rel_err_per_var(Wg, Wo, 4) < 1e-12)
     s.close()
 
 
+@pytest.mark.parametrize("multid", [0, 1])
 @pytest.mark.parametrize("precision", ["fp32", "fp32_acc64"])
-def test_fp32_curvilinear_close_to_oracle(precision):
+def test_fp32_curvilinear_close_to_oracle(precision, multid):
     spec = wavy_spec(64, 48, seed=21)
-    s, Wg, Wo = curv_both(spec, 30, turb_model=2, precision=precision, check_dt=False)
+    s, Wg, Wo = curv_both(spec, 30, turb_model=2, precision=precision, check_dt=False, multid=multid)
     n = Wo.size // 4
     assert np.abs(Wg[:n] - Wo[:n]).sum() / np.abs(Wo[:n]).sum() < 1e-5
     s.close()
@@ -173,8 +175,6 @@ def test_invalid_and_unsupported_grids_are_rejected():
         s.set_nodes(bad)
     s.set_nodes(spec["nodes"])  # the handle stays usable
     s.close()
-    with pytest.raises(gks.GksError):
-        gpu_solver(spec, multid=1).set_nodes(spec["nodes"])
     with pytest.raises(gks.GksError):
         gpu_solver(spec, multid=0, recon=2).set_nodes(spec["nodes"])
     with pytest.raises(gks.GksError):
