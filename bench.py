@@ -48,6 +48,8 @@ def parse():
                    choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
                             "corner2d_528x136", "corner2d_2112x544", "steady_corner_528x136",
                             "steady_corner_2112x544", "naca2d_608x160", "steady_naca_608x160"])
+    p.add_argument("--expand", default=None, choices=["directional", "multid"],
+                   help="expansion of the body-fitted and steady workloads (default: directional)")
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
                    help="face reconstruction (the default is the second-order MUSCL the metric is quoted on)")
     p.add_argument("--no-e2e", action="store_true")
@@ -257,7 +259,7 @@ def run_steady(args, wl):
     s = gks.SteadySolver(n, spec["bc"], spec["nodes"], levels=levels, bc_data=spec["bc_prim"], gamma=1.4,
                          mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega", beta_star=0.09, C_a=0.5,
                          limiter="vanleer", precision=wl["precision"], lusgs_tile=args.lusgs_tile,
-                         wake_cut=spec.get("wake_cut", 0))
+                         wake_cut=spec.get("wake_cut", 0), expand=args.expand or "directional")
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
     s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -341,7 +343,9 @@ def run_steady(args, wl):
         "vs_baseline": None,
         "dtype": "f64" if fp64 else "f32",
         "data": "synthetic",
-        "config": {"workload": "%s_%s" % (args.workload, wl["precision"]), "description": wl["desc"], "grid": list(n),
+        "config": {"workload": "%s_%s" % (args.workload, wl["precision"]) + ("_multid" if args.expand == "multid"
+                                                                             else ""),
+                   "description": wl["desc"], "grid": list(n), "expand": args.expand or "directional",
                    "levels": levels, "lusgs_tile": args.lusgs_tile, "cycles_per_bench_step": ncyc,
                    "precision": wl["precision"],
                    "l2": "flushed between bench steps (256 MiB write)",
@@ -388,6 +392,8 @@ def run_ours(args):
         dist.barrier()
     gks.load()
     wl = make_workload(args.workload, args.precision)
+    if args.expand and wl.get("nodes") is not None:
+        wl["kw"]["expand"] = args.expand
     spec = wl["spec"]
     D = spec["dim"]
     n = tuple(spec["n"])
@@ -507,6 +513,8 @@ def run_ours(args):
                      else "%s_%s" % (args.workload, wl["precision"]))
     if args.reconstruction != "muscl2":
         workload_name += "_" + args.reconstruction
+    if args.expand == "multid" and curv:
+        workload_name += "_multid"
     tile = solver.tile_shape()
     tile_info = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
     line = {
