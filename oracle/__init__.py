@@ -135,6 +135,7 @@ def lib():
             L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
             L.orc_step_curv.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I]
             L.orc_compute_dt_curv.argtypes = [P, _PD, _PD, _D, _PD]
+            L.orc_step_komega_curv.argtypes = [P, _PD, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _I]
             L.orc_steady_residual.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I, _PD, _PD, _I]
             L.orc_lusgs.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD, _I, _I, _PD]
             L.orc_steady_cycle.argtypes = [P, _PD, _PD, _PD, _PD, _D, _D, _I, _I, _I, _I, _PD]
@@ -365,6 +366,18 @@ class Case:
         assert st == 0
         return dt.value
 
+
+    def step_komega_curv(self, nodes, W, RK, RW, dt, coeffs=None, nthreads=1):
+        """One flow step plus the k-omega transport step on a curvilinear grid; returns (W, RK, RW,
+        status)."""
+        nodes = self._nodes(nodes)
+        W = self._state(W).copy()
+        RK = self._field(RK).copy()
+        RW = self._field(RW).copy()
+        c = coeffs if coeffs is not None else komega_defaults()
+        st = lib().orc_step_komega_curv(ctypes.byref(self.P), _ptr(nodes), ctypes.byref(c), _ptr(W), _ptr(RK),
+                                        _ptr(RW), dt, nthreads)
+        return W, RK, RW, st
 
     def steady_residual(self, nodes, W, cfl_flux=0.5, first_order=False, f1=None, f2=None, nthreads=1):
         """Local explicit steps (CFL 1) and the steady residual (flux rates over the face windows

@@ -1851,6 +1851,158 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
   return status;
 }
 
+// k-omega transport on a body-fitted grid (the rectilinear transport of orc_step_komega in each
+// face's frame): the flow step with tau_t from k = rho k / rho and omega = rho omega / rho, then per
+// face the convective flux F_rho * phi (F_rho the face's time-integrated mass flux times its length,
+// phi the upwind cell's value plus its limited slope along the grid line times (centroid-to-face
+// distance - F_rho / (2 rho L)), the half-time value) minus dt (mu + sigma rho k / omega |face)
+// (phi_r - phi_l) / d12 L; per cell the divergence over the area, Wilcox's sources with
+// Green-Gauss gradients (face values the means of the two cells) and the point-implicit destruction.
+int orc_step_komega_curv(const orc_problem* P, const double* nodes, const orc_komega* K, double* W, double* RK,
+                         double* RW, double dt, int nthreads) {
+  if (P->turb_model != ORC_TURB_KOMEGA) return 1;
+  const int n0 = P->n[0], n1 = P->n[1], nv = 4;
+  const long ncell = (long)n0 * n1;
+  std::vector<double> kk(ncell), om(ncell);
+  for (long c = 0; c < ncell; ++c) {
+    kk[c] = RK[c] / W[c];
+    om[c] = RW[c] / W[c];
+  }
+  CurvCtx C;
+  const int st0 = curv_prepare(P, nodes, W, kk.data(), om.data(), C);
+  if (st0) return st0;
+  const CurvGeom& g = C.g;
+  const Grid& G = C.G;
+  std::vector<double> Fi, Fj;
+  curv_fluxes(C, dt, nullptr, false, nthreads, Fi, Fj);
+  std::vector<double> Wnew(W, W + (size_t)nv * ncell);
+  int status = 0;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      const long fa = (long)j * (n0 + 1) + i, fb = fa + 1, fc2 = (long)j * n0 + i, fd = (long)(j + 1) * n0 + i;
+      double w[4];
+      for (int v = 0; v < nv; ++v) {
+        Wnew[v * ncell + c] -= (Fi[fb * nv + v] - Fi[fa * nv + v] + Fj[fd * nv + v] - Fj[fc2 * nv + v]) / g.area[c];
+        w[v] = Wnew[v * ncell + c];
+      }
+      if (!(w[0] > 0.0) || !(pressure(2, P->gamma, w) > 0.0)) status = 4;
+    }
+  // the transport sees the state at the start of the step (with the flow's ghost cells)
+  const std::vector<double>& Wp = C.Wp;
+  std::vector<double> kp = pad_scalar(P, G, kk.data()), wp = pad_scalar(P, G, om.data());
+  std::vector<double> Gk[2], Gw[2];
+  for (int d = 0; d < 2; ++d) {
+    const int nf0 = d == 0 ? n0 + 1 : n0, nf1 = d == 0 ? n1 : n1 + 1;
+    const long nfaces = (long)nf0 * nf1;
+    Gk[d].assign(nfaces, 0.0);
+    Gw[d].assign(nfaces, 0.0);
+    for (long f = 0; f < nfaces; ++f) {
+      const int fi = (int)(f % nf0), fj = (int)(f / nf0);
+      const double L = d == 0 ? g.iL[f] : g.jL[f];
+      const double mx = d == 0 ? g.imx[f] : g.jmx[f], my = d == 0 ? g.imy[f] : g.jmy[f];
+      int ci[4], cj[4];
+      for (int t = 0; t < 4; ++t) {
+        ci[t] = d == 0 ? fi - 2 + t : fi;
+        cj[t] = d == 0 ? fj : fj - 2 + t;
+      }
+      const double d01 = cdist(g, ci[0], cj[0], ci[1], cj[1]), d12 = cdist(g, ci[1], cj[1], ci[2], cj[2]);
+      const double d23 = cdist(g, ci[2], cj[2], ci[3], cj[3]);
+      const double dl = std::hypot(mx - g.pcx[g.pidx(ci[1], cj[1])], my - g.pcy[g.pidx(ci[1], cj[1])]);
+      const double dr = std::hypot(mx - g.pcx[g.pidx(ci[2], cj[2])], my - g.pcy[g.pidx(ci[2], cj[2])]);
+      const double fr = (d == 0 ? Fi : Fj)[f * nv];
+      const long il = G.idx(ci[1], cj[1], 0), ir = G.idx(ci[2], cj[2], 0);
+      const double rl0 = Wp[il], rr0 = Wp[ir];
+      for (int q = 0; q < 2; ++q) {
+        const std::vector<double>& fp = q == 0 ? kp : wp;
+        double v[4];
+        for (int t = 0; t < 4; ++t) v[t] = fp[G.idx(ci[t], cj[t], 0)];
+        const double s0 = limiter(P->limiter, (v[1] - v[0]) / d01, (v[2] - v[1]) / d12);
+        const double s1 = limiter(P->limiter, (v[2] - v[1]) / d12, (v[3] - v[2]) / d23);
+        const double phiL = v[1] + s0 * (dl - 0.5 * fr / (rl0 * L));
+        const double phiR = v[2] - s1 * (dr + 0.5 * fr / (rr0 * L));
+        double gq = fr * (fr >= 0.0 ? phiL : phiR);
+        if (K->diffusion) {
+          const double sig = q == 0 ? K->sigma_star : K->sigma;
+          const double mdl = rl0 * kp[il] / wp[il], mdr = rr0 * kp[ir] / wp[ir];
+          const double coef = P->mu + sig * 0.5 * (mdl + mdr);
+          gq -= dt * coef * (v[2] - v[1]) / d12 * L;
+        }
+        (q == 0 ? Gk : Gw)[d][f] = gq;
+      }
+    }
+  }
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      const long id = G.idx(i, j, 0);
+      const long fa = (long)j * (n0 + 1) + i, fb = fa + 1, fc2 = (long)j * n0 + i, fd = (long)(j + 1) * n0 + i;
+      const double A = g.area[c];
+      double ak = RK[c] - (Gk[0][fb] - Gk[0][fa] + Gk[1][fd] - Gk[1][fc2]) / A;
+      double aw = RW[c] - (Gw[0][fb] - Gw[0][fa] + Gw[1][fd] - Gw[1][fc2]) / A;
+      double rate_k = 0.0, rate_w = 0.0;
+      if (K->sources) {
+        double w[5];
+        get_cell(G, Wp, i, j, 0, w);
+        const double rho = w[0], k0 = kp[id], w0 = wp[id];
+        // Green-Gauss gradients: velocity (gu[a][b] = dU_b/dx_a), k and omega
+        double gu[2][2] = {{0, 0}, {0, 0}}, gk[2] = {0, 0}, gw[2] = {0, 0};
+        const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+        const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
+        const long fid[4] = {fa, fb, fc2, fd};
+        for (int q = 0; q < 4; ++q) {
+          double wn[5];
+          get_cell(G, Wp, nb[q][0], nb[q][1], 0, wn);
+          const long nid = G.idx(nb[q][0], nb[q][1], 0);
+          const double nx = q < 2 ? g.inx[fid[q]] : g.jnx[fid[q]], ny = q < 2 ? g.iny[fid[q]] : g.jny[fid[q]];
+          const double L = q < 2 ? g.iL[fid[q]] : g.jL[fid[q]];
+          const double sx = sgn[q] * nx * L, sy = sgn[q] * ny * L;
+          for (int b = 0; b < 2; ++b) {
+            const double uf = 0.5 * (w[1 + b] / w[0] + wn[1 + b] / wn[0]);
+            gu[0][b] += uf * sx;
+            gu[1][b] += uf * sy;
+          }
+          const double kf = 0.5 * (k0 + kp[nid]), wf = 0.5 * (w0 + wp[nid]);
+          gk[0] += kf * sx;
+          gk[1] += kf * sy;
+          gw[0] += wf * sx;
+          gw[1] += wf * sy;
+        }
+        for (int a = 0; a < 2; ++a) {
+          gk[a] /= A;
+          gw[a] /= A;
+          for (int b = 0; b < 2; ++b) gu[a][b] /= A;
+        }
+        const double div = gu[0][0] + gu[1][1];
+        double SS = 0.0, SbSb = 0.0;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) {
+            const double sab = 0.5 * (gu[a][b] + gu[b][a]);
+            SS += sab * sab;
+            const double sb = sab - (a == b ? div / 3.0 : 0.0);
+            SbSb += sb * sb;
+          }
+        const double X = 2.0 * SS - 2.0 / 3.0 * div * div;
+        const double wt = std::max(w0, K->C_lim * std::sqrt(2.0 * SbSb / K->beta_star));
+        const double muT = rho * k0 / wt;
+        const double Pk = muT * X - 2.0 / 3.0 * rho * k0 * div;
+        const double dkdw = gk[0] * gw[0] + gk[1] * gw[1];
+        const double sd = dkdw > 0.0 ? K->sigma_do : 0.0;
+        const double CD = sd * rho / w0 * dkdw;
+        ak += dt * Pk;
+        aw += dt * (K->alpha * rho * (w0 / wt) * X - 2.0 / 3.0 * K->alpha * rho * w0 * div + CD);
+        rate_k = K->beta_star * w0;
+        rate_w = K->beta0 * w0;  // the vortex-stretching factor is 1 in 2D
+      }
+      ak /= 1.0 + dt * rate_k;
+      aw /= 1.0 + dt * rate_w;
+      RK[c] = std::max(ak, 0.0);
+      RW[c] = std::max(aw, Wnew[c] * K->omega_floor);
+    }
+  std::memcpy(W, Wnew.data(), sizeof(double) * Wnew.size());
+  return status;
+}
+
 int orc_steady_residual(const orc_problem* P, const double* nodes, const double* W, const double* f1,
                         const double* f2, double cfl_flux, int first_order, double* dt_cell, double* R, int nthreads) {
   CurvCtx C;

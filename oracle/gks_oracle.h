@@ -128,6 +128,13 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
 /* CFL step on a curvilinear grid: dt = cfl / max_cells sum_faces (|U.n| + c) L / (2 A). */
 int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt);
 
+/* k-omega transport on a curvilinear grid (orc_step_komega in each face's frame; P->turb_model must be
+ * ORC_TURB_KOMEGA): the flow step with tau_t from RK / rho, RW / rho, then RK, RW advanced with the
+ * face mass fluxes, half-time upwind face values along the grid lines, normal diffusion over the
+ * centroid distance, Wilcox's sources with Green-Gauss gradients, point-implicit destruction. */
+int orc_step_komega_curv(const orc_problem* P, const double* nodes, const orc_komega* K, double* W, double* RK,
+                         double* RW, double dt, int nthreads);
+
 /* Steady-state solver on curvilinear grids (Section 4: local time stepping, LU-SGS, multigrid).
  * orc_steady_residual: local explicit steps dt_cell[i] = 2 A_i / sum_faces (|U.n| + c) L and the
  * residual R[v][i] = sum over faces of (flux over the face window cfl_flux min(dt_l, dt_r)) / window
