@@ -131,8 +131,11 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
  * GKS_EXPAND_MULTID each face also takes tangential slopes of its two cells in the face frame: limited
  * differences along the transverse grid line over the centroid steps projected on the face tangent
  * (corner ghost centroids by the parallelogram of the i ghost, the j ghost and their source cell).
- * Built for dim 2, both expansions, GKS_RECON_MUSCL2, no k-omega transport (GKS_EUNSUPPORTED
- * otherwise), every precision.  May be called before or after gks_set_state; a second call
+ * With GKS_TURB_KOMEGA_TRANSPORT, rho k and rho omega are advanced after each flow step as on
+ * rectilinear grids, in each face's frame: convection by the face mass flux times L with half-time
+ * upwind values along the grid line (the swept length F_rho / (rho L)), normal diffusion over the
+ * centroid distance, sources with Green-Gauss gradients, each divergence over the cell area.
+ * Built for dim 2, both expansions, GKS_RECON_MUSCL2 (GKS_EUNSUPPORTED otherwise), every precision.  May be called before or after gks_set_state; a second call
  * replaces the grid.  GKS_EINVAL for a folded or clockwise cell (the handle's grid is then the
  * rectilinear one again).
  * gks_get_tau_turb works on such grids, gks_get_rarefaction returns GKS_EUNSUPPORTED. */

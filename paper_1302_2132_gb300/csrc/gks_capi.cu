@@ -243,7 +243,10 @@ void launch_step(gks_handle* h, const StepArgs& A) {
   K.fsigma_do = (float)K.sigma_do;
   K.fC_lim = (float)K.C_lim;
   K.fomega_floor = (float)K.omega_floor;
-  launch_komega(h->D, h->prec, K, h->stream);
+  if (h->curv)
+    launch_curv_komega(h->prec, K, h->cg, h->stream);
+  else
+    launch_komega(h->D, h->prec, K, h->stream);
 }
 
 // Arguments of the step that starts at absolute step index s.
@@ -1069,7 +1072,6 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
   if (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE) return fail(h, GKS_EINVAL, "memspace");
   if (h->D != 2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids are built in 2D");
   if (h->recon != GKS_RECON_MUSCL2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids take MUSCL2 reconstruction");
-  if (h->transport) return fail(h, GKS_EUNSUPPORTED, "k-omega transport on a curvilinear grid");
   DeviceGuard dg(h->dev);
   GKS_CK(h, cudaStreamSynchronize(h->stream));
   free_curv(h);

@@ -209,9 +209,11 @@ __device__ __forceinline__ R tau_gg(const DevGrid& g, const Consts<R>& kc, const
 #pragma unroll
   for (int v = 0; v < 4; ++v) w[v] = st(4, v);
   const R p = pressure_of<R>(2, kc.gamma, w);
-  const R f1 = ((const R*)f1p)[c];
+  R f1 = ((const R*)f1p)[c];
+  if (g.turb_cons) f1 = g_div(f1, w[0]);  // rho k -> k (k-omega transport)
   if (g.turb_model == TURB_MUT) return g_div(f1, p);
-  const R f2 = ((const R*)f2p)[c];
+  R f2 = ((const R*)f2p)[c];
+  if (g.turb_cons) f2 = g_div(f2, w[0]);
   const FaceView<R> fi{(const R*)G.face[0], G.nf[0]}, fj{(const R*)G.face[1], G.nf[1]};
   const long fa = (long)gj * (n0 + 1) + gi, fc = (long)gj * n0 + gi;
   const long fid[4] = {fa, fa + 1, fc, fc + n0};
@@ -588,6 +590,10 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;
       Fs[2 * NF + l] = (F[1] * ny + F[2] * nx) * L_;
       Fs[3 * NF + l] = F[3] * L_;
+      if (MODE == 0 && A.mflux[0]) {  // the face's time-integrated mass flux times L (k-omega transport)
+        const long gfm = a == 0 ? (long)(oy + lj) * (n0 + 1) + ox + li : (long)(oy + lj) * n0 + ox + li;
+        ((R*)A.mflux[a])[gfm] = Fs[l];
+      }
     }
   }
   __syncthreads();
@@ -724,6 +730,165 @@ cudaError_t prepare_fused() {
   return a != cudaSuccess ? a : b;
 }
 
+// ---- k-omega transport after a flow step --------------------------------------------------------
+// One thread per cell: the convective-diffusive fluxes of rho k and rho omega through its four faces
+// (each face evaluated by both of its cells, with the same arithmetic, so the transport conserves),
+// Wilcox's sources with Green-Gauss gradients, the point-implicit destruction and the floors.
+
+// k and omega of a (possibly ghost) cell: those of its source cell (rho k / rho of that cell).
+template <int PREC>
+__device__ __forceinline__ void cell_kw(const KOmegaArgs& K, int i, int j, typename PrecT<PREC>::R& k,
+                                        typename PrecT<PREC>::R& om) {
+  using R = typename PrecT<PREC>::R;
+  using S = typename PrecT<PREC>::S;
+  const long c = field_cell(K.g, 2, i, j, 0);
+  const R rho = (R)((const S*)K.Win)[c];
+  k = g_div(((const R*)K.RKin)[c], rho);
+  om = g_div(((const R*)K.RWin)[c], rho);
+}
+
+// Fluxes (rho k, rho omega) through face (fi, fj) of axis a, towards increasing index.
+template <int PREC>
+__device__ void face_kw(const KOmegaArgs& K, const CurvGeom& G, const Consts<typename PrecT<PREC>::R>& kc, int a,
+                        int fi, int fj, typename PrecT<PREC>::R dt, typename PrecT<PREC>::R* gkw) {
+  using R = typename PrecT<PREC>::R;
+  const DevGrid& g = K.g;
+  const int n0 = g.n[0];
+  const long nf = G.nf[a];
+  const long f = a == 0 ? (long)fj * (n0 + 1) + fi : (long)fj * n0 + fi;
+  const R* rec = (const R*)G.face[a];
+  const R L = rec[2 * nf + f], i01 = rec[3 * nf + f], i12 = rec[4 * nf + f], i23 = rec[5 * nf + f];
+  const R dl = rec[6 * nf + f], dr = rec[7 * nf + f];
+  const R fr = ((const R*)K.mflux[a])[f];
+  R vk[4], vw[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int ci = a == 0 ? fi - 2 + t : fi, cj = a == 0 ? fj : fj - 2 + t;
+    cell_kw<PREC>(K, ci, cj, vk[t], vw[t]);
+  }
+  R wl[4], wr[4];
+  load_cell<2, PREC>(g, K.Win, kc, a == 0 ? fi - 1 : fi, a == 0 ? fj : fj - 1, 0, wl);
+  load_cell<2, PREC>(g, K.Win, kc, fi, fj, 0, wr);
+  const R rl0 = wl[0], rr0 = wr[0];
+  const bool kf = sizeof(R) == sizeof(float);
+  const R sigk = kf ? (R)K.fsigma_star : (R)K.sigma_star, sigw = kf ? (R)K.fsigma : (R)K.sigma;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const R* v = q == 0 ? vk : vw;
+    const R s0 = limiter<R>(g.limiter, (v[1] - v[0]) * i01, (v[2] - v[1]) * i12);
+    const R s1 = limiter<R>(g.limiter, (v[2] - v[1]) * i12, (v[3] - v[2]) * i23);
+    const R phiL = v[1] + s0 * (dl - R(0.5) * g_div(fr, rl0 * L));
+    const R phiR = v[2] - s1 * (dr + R(0.5) * g_div(fr, rr0 * L));
+    R gq = fr * (fr >= R(0) ? phiL : phiR);
+    if (K.diffusion) {
+      const R mdl = g_div(rl0 * vk[1], vw[1]), mdr = g_div(rr0 * vk[2], vw[2]);
+      const R coef = kc.mu + (q == 0 ? sigk : sigw) * R(0.5) * (mdl + mdr);
+      gq -= dt * coef * (v[2] - v[1]) * i12 * L;
+    }
+    gkw[q] = gq;
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kCurvThreads) curv_komega_kernel(const __grid_constant__ KOmegaArgs K,
+                                                                   const __grid_constant__ CurvGeom G) {
+  using R = typename PrecT<PREC>::R;
+  using S = typename PrecT<PREC>::S;
+  const DevGrid& g = K.g;
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const Consts<R> kc = make_consts<R>(g);
+  const bool kf = sizeof(R) == sizeof(float);
+  const R alpha = kf ? (R)K.falpha : (R)K.alpha, beta0 = kf ? (R)K.fbeta0 : (R)K.beta0;
+  const R beta_star = kf ? (R)K.fbeta_star : (R)K.beta_star, sigma_do = kf ? (R)K.fsigma_do : (R)K.sigma_do;
+  const R C_lim = kf ? (R)K.fC_lim : (R)K.C_lim, omega_floor = kf ? (R)K.fomega_floor : (R)K.omega_floor;
+  const R dt = (R)K.ctrl->last_dt;
+  const int n0 = g.n[0];
+  const int i = (int)(c % n0), j = (int)(c / n0);
+  const R* RKi = (const R*)K.RKin;
+  const R* RWi = (const R*)K.RWin;
+  if (dt == R(0)) {  // t_end reached: carry the fields over
+    ((R*)K.RKout)[c] = RKi[c];
+    ((R*)K.RWout)[c] = RWi[c];
+    return;
+  }
+  R ga[2], gb[2], gc[2], gd[2];  // fluxes through faces i-1/2, i+1/2, j-1/2, j+1/2
+  face_kw<PREC>(K, G, kc, 0, i, j, dt, ga);
+  face_kw<PREC>(K, G, kc, 0, i + 1, j, dt, gb);
+  face_kw<PREC>(K, G, kc, 1, i, j, dt, gc);
+  face_kw<PREC>(K, G, kc, 1, i, j + 1, dt, gd);
+  const R A = (R)G.area[c];
+  R ak = RKi[c] - (gb[0] - ga[0] + gd[0] - gc[0]) / A;
+  R aw = RWi[c] - (gb[1] - ga[1] + gd[1] - gc[1]) / A;
+  R rate_k = R(0), rate_w = R(0);
+  if (K.sources) {
+    R w[4];
+    load_stored<2, PREC>(g, K.Win, c, w);
+    const R rho = w[0];
+    R k0, w0;
+    cell_kw<PREC>(K, i, j, k0, w0);
+    const FaceView<R> fvi{(const R*)G.face[0], G.nf[0]}, fvj{(const R*)G.face[1], G.nf[1]};
+    const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+    const long fid[4] = {fa, fa + 1, fc, fc + n0};
+    const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+    R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      R wn[4], kn, omn;
+      load_cell<2, PREC>(g, K.Win, kc, nb[q][0], nb[q][1], 0, wn);
+      cell_kw<PREC>(K, nb[q][0], nb[q][1], kn, omn);
+      const FaceView<R>& fv = q < 2 ? fvi : fvj;
+      const R sgn = (q & 1) ? R(1) : R(-1);
+      const R sx = sgn * fv(0, fid[q]) * fv(2, fid[q]), sy = sgn * fv(1, fid[q]) * fv(2, fid[q]);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const R uf = R(0.5) * (g_div(w[1 + b], w[0]) + g_div(wn[1 + b], wn[0]));
+        gu[0][b] += uf * sx;
+        gu[1][b] += uf * sy;
+      }
+      const R kff = R(0.5) * (k0 + kn), wff = R(0.5) * (w0 + omn);
+      gk[0] += kff * sx;
+      gk[1] += kff * sy;
+      gw[0] += wff * sx;
+      gw[1] += wff * sy;
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      gk[a] /= A;
+      gw[a] /= A;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) gu[a][b] /= A;
+    }
+    const R div = gu[0][0] + gu[1][1];
+    R SS = R(0), SbSb = R(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const R sab = R(0.5) * (gu[a][b] + gu[b][a]);
+        SS += sab * sab;
+        const R sb = sab - (a == b ? div / R(3) : R(0));
+        SbSb += sb * sb;
+      }
+    const R X = R(2) * SS - R(2) / R(3) * div * div;
+    const R wt = fmax(w0, C_lim * g_sqrt(R(2) * SbSb / beta_star));
+    const R muT = rho * k0 / wt;
+    const R Pk = muT * X - R(2) / R(3) * rho * k0 * div;
+    const R dkdw = gk[0] * gw[0] + gk[1] * gw[1];
+    const R sd = dkdw > R(0) ? sigma_do : R(0);
+    const R CD = sd * rho / w0 * dkdw;
+    ak += dt * Pk;
+    aw += dt * (alpha * rho * (w0 / wt) * X - R(2) / R(3) * alpha * rho * w0 * div + CD);
+    rate_k = beta_star * w0;
+    rate_w = beta0 * w0;
+  }
+  ak /= R(1) + dt * rate_k;
+  aw /= R(1) + dt * rate_w;
+  const R rho_new = (R)((const S*)K.Wnew)[c];
+  ((R*)K.RKout)[c] = fmax(ak, R(0));
+  ((R*)K.RWout)[c] = fmax(aw, rho_new * omega_floor);
+}
+
 // Local explicit step (CFL 1) of every cell: 2 A / sum_faces (|U.n| + c) L.
 template <int PREC>
 __global__ void __launch_bounds__(kCurvThreads) lts_kernel(const __grid_constant__ StepArgs A,
@@ -837,6 +1002,15 @@ void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out
     lts_kernel<PREC_F64><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, s_out);
   else
     lts_kernel<PREC_F32><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, s_out);
+}
+
+void launch_curv_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, cudaStream_t s) {
+  if (prec == PREC_F64)
+    curv_komega_kernel<PREC_F64><<<blocks_for(K.g.ncell), kCurvThreads, 0, s>>>(K, G);
+  else if (prec == PREC_F32)
+    curv_komega_kernel<PREC_F32><<<blocks_for(K.g.ncell), kCurvThreads, 0, s>>>(K, G);
+  else
+    curv_komega_kernel<PREC_F32D><<<blocks_for(K.g.ncell), kCurvThreads, 0, s>>>(K, G);
 }
 
 void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s) {

@@ -6,6 +6,7 @@
 namespace gks {
 
 struct StepArgs;
+struct KOmegaArgs;
 
 // Device buffers of a curvilinear grid, owned by the handle.
 struct CurvGeom {
@@ -49,5 +50,7 @@ void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, 
 // steady solver pieces (FP64 and FP32 state): the residual of A.Win, the local explicit steps
 void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
 void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s);
+// k-omega transport after a flow step on the grid (K.mflux: the step's face mass fluxes times length)
+void launch_curv_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, cudaStream_t s);
 
 }  // namespace gks
