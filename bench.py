@@ -47,7 +47,8 @@ def parse():
     p.add_argument("--workload", default="turb2d_1024",
                    choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
                             "corner2d_528x136", "corner2d_2112x544", "steady_corner_528x136",
-                            "steady_corner_2112x544", "naca2d_608x160", "steady_naca_608x160"])
+                            "steady_corner_2112x544", "naca2d_608x160", "naca2d_608x160_transport",
+                            "steady_naca_608x160"])
     p.add_argument("--expand", default=None, choices=["directional", "multid"],
                    help="expansion of the body-fitted and steady workloads (default: directional)")
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
@@ -174,7 +175,7 @@ def make_workload(name, precision):
                          "Mach 2.85 / 24-degree compression corner, body-fitted %dx%d wall-clustered grid, k-omega "
                          "tau_t, 100 cycles from the inflow state (20 at CFL 1, 80 at CFL 4), flux windows CFL 0.5"
                          % (nx, ny))
-    if name in ("naca2d_608x160", "steady_naca_608x160"):
+    if name in ("naca2d_608x160", "naca2d_608x160_transport", "steady_naca_608x160"):
         # the fine NACA 0012 C-grid size of the paper's Table 2: 2 x 112 wake + 384 surface cells, 160 rows
         spec = inputs.naca0012_case(112, 384, 160, mach=0.8, alpha_deg=2.26, Re=9.0e6, dy1=2e-4, ratio=1.05,
                                     R=10.0, x_out=10.0)
@@ -184,6 +185,14 @@ def make_workload(name, precision):
                         desc="steady solver (local time steps, LU-SGS on cell tiles, 4-level FAS multigrid) on a "
                              "NACA 0012 C-grid 608x160 with a wake cut, M 0.8, incidence 2.26 degrees, Re 9e6, "
                              "k-omega tau_t from free-stream fields, 100 cycles (20 at CFL 1, 80 at CFL 4)")
+        if name.endswith("_transport"):
+            return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"],
+                                           turb_model="komega_transport", beta_star=0.09, C_a=0.5, limiter="vanleer",
+                                           expand="directional", wake_cut=spec["wake_cut"]),
+                        nsteps=2000, t_end=0.0, precision=precision or "fp32", nodes=spec["nodes"], transport=True,
+                        desc="NACA 0012 C-grid 608x160 with a wake cut, M 0.8, incidence 2.26 degrees, Re 9e6, "
+                             "k and omega transported from free-stream values (Wilcox 2006 k-omega), directional "
+                             "expansion in each face's frame, 2000 CFL steps")
         return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega",
                                        beta_star=0.09, C_a=0.5, limiter="vanleer", expand="directional",
                                        wake_cut=spec["wake_cut"]),
@@ -544,15 +553,16 @@ def run_ours(args):
                      "kernel": (("step_kernel<%d, %s, %s>%s" % (D, prec_name, "multid" if multid else "directional",
                                                                  " + komega_kernel (timed together)" if transport
                                                                  else "")) if not curv else
-                                "curv_step_kernel<%s, variant %d>" % (prec_name, tile[0])),
+                                "curv_step_kernel<%s, variant %d>%s" % (prec_name, tile[0],
+                                                                         " + curv_komega_kernel (timed together)"
+                                                                         if transport else "")),
                      "avg_launch_us": avg_launch_s * 1e6,
                      "ops_per_face": per_face, "ops_per_cell": per_cell,
                      "peak_basis": "152 SMs x %d %s lanes x 2 (FMA) x 2070 MHz (derived)" % (lanes, "FP64" if fp64
                                                                                             else "FP32")},
-        # per bench step: state_in + rate kernels, the step kernels (plus the transport kernels and
-        # the two field conversions of set_turbulence with k-omega transport)
-        "gpu_launches": args.steps * ((2 * nsteps + 2 + 4) if transport else
-                                      ((3 * nsteps + 3) if curv else (nsteps + 3))),
+        # per bench step: state_in + rate kernels, one step kernel per time step (plus the transport
+        # kernel and the four field conversions of set_turbulence with k-omega transport)
+        "gpu_launches": args.steps * ((2 * nsteps + 2 + 4) if transport else (nsteps + 3)),
         "clocks": clock_info,
         "e2e": e2e,
         "final_time": t_end,

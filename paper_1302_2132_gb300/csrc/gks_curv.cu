@@ -731,9 +731,16 @@ cudaError_t prepare_fused() {
 }
 
 // ---- k-omega transport after a flow step --------------------------------------------------------
-// One thread per cell: the convective-diffusive fluxes of rho k and rho omega through its four faces
-// (each face evaluated by both of its cells, with the same arithmetic, so the transport conserves),
-// Wilcox's sources with Green-Gauss gradients, the point-implicit destruction and the floors.
+// One CTA per tile of KwTile::X x KwTile::Y cells in four phases: stage k, omega (of each cell's
+// source cell) and the ghost-rule density and velocity of the tile and its two-cell halo (corners
+// left out: no face stencil or neighbour reaches them); the convective-diffusive fluxes of rho k
+// and rho omega through every face of the tile, once per face; per cell the divergence, Wilcox's
+// sources with Green-Gauss gradients, the point-implicit destruction and the floors.
+
+struct KwTile {
+  static constexpr int X = 32, Y = 8, T = X * Y;
+  static constexpr int SX = X + 4, SY = Y + 4;  // staged cells with the halo
+};
 
 // k and omega of a (possibly ghost) cell: those of its source cell (rho k / rho of that cell).
 template <int PREC>
@@ -747,106 +754,133 @@ __device__ __forceinline__ void cell_kw(const KOmegaArgs& K, int i, int j, typen
   om = g_div(((const R*)K.RWin)[c], rho);
 }
 
-// Fluxes (rho k, rho omega) through face (fi, fj) of axis a, towards increasing index.
-template <int PREC>
-__device__ void face_kw(const KOmegaArgs& K, const CurvGeom& G, const Consts<typename PrecT<PREC>::R>& kc, int a,
-                        int fi, int fj, typename PrecT<PREC>::R dt, typename PrecT<PREC>::R* gkw) {
-  using R = typename PrecT<PREC>::R;
-  const DevGrid& g = K.g;
-  const int n0 = g.n[0];
-  const long nf = G.nf[a];
-  const long f = a == 0 ? (long)fj * (n0 + 1) + fi : (long)fj * n0 + fi;
-  const R* rec = (const R*)G.face[a];
+// Fluxes (rho k, rho omega) through one face, towards increasing index: v*[0..3] the four cells
+// along the grid line, rl, rr the densities of the two cells beside the face, rec the face record.
+template <class R>
+__device__ __forceinline__ void kw_face(const R* vk, const R* vw, R rl, R rr, const R* rec, long nf, long f, R fr,
+                                        R dt, R mu, R sigk, R sigw, int limiter_kind, bool diffusion, R* out) {
   const R L = rec[2 * nf + f], i01 = rec[3 * nf + f], i12 = rec[4 * nf + f], i23 = rec[5 * nf + f];
   const R dl = rec[6 * nf + f], dr = rec[7 * nf + f];
-  const R fr = ((const R*)K.mflux[a])[f];
-  R vk[4], vw[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int ci = a == 0 ? fi - 2 + t : fi, cj = a == 0 ? fj : fj - 2 + t;
-    cell_kw<PREC>(K, ci, cj, vk[t], vw[t]);
-  }
-  R wl[4], wr[4];
-  load_cell<2, PREC>(g, K.Win, kc, a == 0 ? fi - 1 : fi, a == 0 ? fj : fj - 1, 0, wl);
-  load_cell<2, PREC>(g, K.Win, kc, fi, fj, 0, wr);
-  const R rl0 = wl[0], rr0 = wr[0];
-  const bool kf = sizeof(R) == sizeof(float);
-  const R sigk = kf ? (R)K.fsigma_star : (R)K.sigma_star, sigw = kf ? (R)K.fsigma : (R)K.sigma;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const R* v = q == 0 ? vk : vw;
-    const R s0 = limiter<R>(g.limiter, (v[1] - v[0]) * i01, (v[2] - v[1]) * i12);
-    const R s1 = limiter<R>(g.limiter, (v[2] - v[1]) * i12, (v[3] - v[2]) * i23);
-    const R phiL = v[1] + s0 * (dl - R(0.5) * g_div(fr, rl0 * L));
-    const R phiR = v[2] - s1 * (dr + R(0.5) * g_div(fr, rr0 * L));
+    const R s0 = limiter<R>(limiter_kind, (v[1] - v[0]) * i01, (v[2] - v[1]) * i12);
+    const R s1 = limiter<R>(limiter_kind, (v[2] - v[1]) * i12, (v[3] - v[2]) * i23);
+    const R phiL = v[1] + s0 * (dl - R(0.5) * g_div(fr, rl * L));
+    const R phiR = v[2] - s1 * (dr + R(0.5) * g_div(fr, rr * L));
     R gq = fr * (fr >= R(0) ? phiL : phiR);
-    if (K.diffusion) {
-      const R mdl = g_div(rl0 * vk[1], vw[1]), mdr = g_div(rr0 * vk[2], vw[2]);
-      const R coef = kc.mu + (q == 0 ? sigk : sigw) * R(0.5) * (mdl + mdr);
+    if (diffusion) {
+      const R mdl = g_div(rl * vk[1], vw[1]), mdr = g_div(rr * vk[2], vw[2]);
+      const R coef = mu + (q == 0 ? sigk : sigw) * R(0.5) * (mdl + mdr);
       gq -= dt * coef * (v[2] - v[1]) * i12 * L;
     }
-    gkw[q] = gq;
+    out[q] = gq;
   }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kCurvThreads) curv_komega_kernel(const __grid_constant__ KOmegaArgs K,
-                                                                   const __grid_constant__ CurvGeom G) {
+__global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_constant__ KOmegaArgs K,
+                                                                const __grid_constant__ CurvGeom G) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
+  constexpr int TX = KwTile::X, TY = KwTile::Y, SX = KwTile::SX, NS = KwTile::SX * KwTile::SY;
+  constexpr int NFI = (TX + 1) * TY, NFJ = TX * (TY + 1);
+  __shared__ R sk[NS], sw[NS], sr[NS], su[NS], sv[NS];
+  __shared__ R fi_k[NFI], fi_w[NFI], fj_k[NFJ], fj_w[NFJ];
   const DevGrid& g = K.g;
-  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int tiles_x = (n0 + TX - 1) / TX;
+  const int i0 = (blockIdx.x % tiles_x) * TX, j0 = (blockIdx.x / tiles_x) * TY;
+  const int tid = threadIdx.x;
+  const R dt = (R)K.ctrl->last_dt;
+  const R* RKi = (const R*)K.RKin;
+  const R* RWi = (const R*)K.RWin;
+  const int li = tid % TX, lj = tid / TX;
+  const int i = i0 + li, j = j0 + lj;
+  const bool mine = i < n0 && j < n1;
+  const long c = (long)j * n0 + i;
+  if (dt == R(0)) {  // t_end reached: carry the fields over (dt is the same for every CTA)
+    if (mine) {
+      ((R*)K.RKout)[c] = RKi[c];
+      ((R*)K.RWout)[c] = RWi[c];
+    }
+    return;
+  }
   const Consts<R> kc = make_consts<R>(g);
+  // phase 1: stage the tile with its halo
+  for (int q = tid; q < NS; q += KwTile::T) {
+    const int qi = q % SX, qj = q / SX;
+    const bool corner = (qi < 2 || qi >= TX + 2) && (qj < 2 || qj >= TY + 2);
+    const int gi = i0 - 2 + qi, gj = j0 - 2 + qj;
+    if (corner || gi > n0 + 1 || gj > n1 + 1) continue;
+    R w[4], k, om;
+    load_cell<2, PREC>(g, K.Win, kc, gi, gj, 0, w);
+    cell_kw<PREC>(K, gi, gj, k, om);
+    sk[q] = k;
+    sw[q] = om;
+    sr[q] = w[0];
+    su[q] = g_div(w[1], w[0]);
+    sv[q] = g_div(w[2], w[0]);
+  }
+  __syncthreads();
+  // phase 2: every face of the tile once
   const bool kf = sizeof(R) == sizeof(float);
+  const R sigk = kf ? (R)K.fsigma_star : (R)K.sigma_star, sigw = kf ? (R)K.fsigma : (R)K.sigma;
+  for (int q = tid; q < NFI + NFJ; q += KwTile::T) {
+    const bool ia = q < NFI;
+    const int r = ia ? q : q - NFI;
+    const int fl = ia ? r % (TX + 1) : r % TX, fm = ia ? r / (TX + 1) : r / TX;  // local face index
+    const int fi = i0 + fl, fj = j0 + fm;
+    if (ia ? (fi > n0 || fj >= n1) : (fi >= n0 || fj > n1)) continue;
+    const int a = ia ? 0 : 1;
+    const long f = ia ? (long)fj * (n0 + 1) + fi : (long)fj * n0 + fi;
+    // staged index of the first stencil cell (fi - 2 or fj - 2) and the step along the grid line
+    const int s0 = ia ? (fm + 2) * SX + fl : fm * SX + fl + 2, st = ia ? 1 : SX;
+    R vk[4], vw[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      vk[t] = sk[s0 + t * st];
+      vw[t] = sw[s0 + t * st];
+    }
+    R out[2];
+    kw_face<R>(vk, vw, sr[s0 + st], sr[s0 + 2 * st], (const R*)G.face[a], G.nf[a], f, ((const R*)K.mflux[a])[f], dt,
+               kc.mu, sigk, sigw, g.limiter, K.diffusion, out);
+    (ia ? fi_k : fj_k)[r] = out[0];
+    (ia ? fi_w : fj_w)[r] = out[1];
+  }
+  __syncthreads();
+  if (!mine) return;
+  // phase 3: divergence, sources, point-implicit destruction
   const R alpha = kf ? (R)K.falpha : (R)K.alpha, beta0 = kf ? (R)K.fbeta0 : (R)K.beta0;
   const R beta_star = kf ? (R)K.fbeta_star : (R)K.beta_star, sigma_do = kf ? (R)K.fsigma_do : (R)K.sigma_do;
   const R C_lim = kf ? (R)K.fC_lim : (R)K.C_lim, omega_floor = kf ? (R)K.fomega_floor : (R)K.omega_floor;
-  const R dt = (R)K.ctrl->last_dt;
-  const int n0 = g.n[0];
-  const int i = (int)(c % n0), j = (int)(c / n0);
-  const R* RKi = (const R*)K.RKin;
-  const R* RWi = (const R*)K.RWin;
-  if (dt == R(0)) {  // t_end reached: carry the fields over
-    ((R*)K.RKout)[c] = RKi[c];
-    ((R*)K.RWout)[c] = RWi[c];
-    return;
-  }
-  R ga[2], gb[2], gc[2], gd[2];  // fluxes through faces i-1/2, i+1/2, j-1/2, j+1/2
-  face_kw<PREC>(K, G, kc, 0, i, j, dt, ga);
-  face_kw<PREC>(K, G, kc, 0, i + 1, j, dt, gb);
-  face_kw<PREC>(K, G, kc, 1, i, j, dt, gc);
-  face_kw<PREC>(K, G, kc, 1, i, j + 1, dt, gd);
+  const int ra = lj * (TX + 1) + li, rc = lj * TX + li;
   const R A = (R)G.area[c];
-  R ak = RKi[c] - (gb[0] - ga[0] + gd[0] - gc[0]) / A;
-  R aw = RWi[c] - (gb[1] - ga[1] + gd[1] - gc[1]) / A;
+  R ak = RKi[c] - (fi_k[ra + 1] - fi_k[ra] + fj_k[rc + TX] - fj_k[rc]) / A;
+  R aw = RWi[c] - (fi_w[ra + 1] - fi_w[ra] + fj_w[rc + TX] - fj_w[rc]) / A;
   R rate_k = R(0), rate_w = R(0);
   if (K.sources) {
-    R w[4];
-    load_stored<2, PREC>(g, K.Win, c, w);
-    const R rho = w[0];
-    R k0, w0;
-    cell_kw<PREC>(K, i, j, k0, w0);
+    const int sc = (lj + 2) * SX + li + 2;
+    const R rho = sr[sc], k0 = sk[sc], w0 = sw[sc];
     const FaceView<R> fvi{(const R*)G.face[0], G.nf[0]}, fvj{(const R*)G.face[1], G.nf[1]};
     const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
     const long fid[4] = {fa, fa + 1, fc, fc + n0};
-    const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+    const int nb[4] = {sc - 1, sc + 1, sc - SX, sc + SX};
+    const R uc[2] = {su[sc], sv[sc]};
     R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      R wn[4], kn, omn;
-      load_cell<2, PREC>(g, K.Win, kc, nb[q][0], nb[q][1], 0, wn);
-      cell_kw<PREC>(K, nb[q][0], nb[q][1], kn, omn);
       const FaceView<R>& fv = q < 2 ? fvi : fvj;
       const R sgn = (q & 1) ? R(1) : R(-1);
       const R sx = sgn * fv(0, fid[q]) * fv(2, fid[q]), sy = sgn * fv(1, fid[q]) * fv(2, fid[q]);
+      const R un[2] = {su[nb[q]], sv[nb[q]]};
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        const R uf = R(0.5) * (g_div(w[1 + b], w[0]) + g_div(wn[1 + b], wn[0]));
+        const R uf = R(0.5) * (uc[b] + un[b]);
         gu[0][b] += uf * sx;
         gu[1][b] += uf * sy;
       }
-      const R kff = R(0.5) * (k0 + kn), wff = R(0.5) * (w0 + omn);
+      const R kff = R(0.5) * (k0 + sk[nb[q]]), wff = R(0.5) * (w0 + sw[nb[q]]);
       gk[0] += kff * sx;
       gk[1] += kff * sy;
       gw[0] += wff * sx;
@@ -904,6 +938,10 @@ __global__ void __launch_bounds__(kCurvThreads) lts_kernel(const __grid_constant
 }
 
 inline unsigned blocks_for(long n) { return (unsigned)((n + kCurvThreads - 1) / kCurvThreads); }
+
+inline unsigned kw_tiles(const DevGrid& g) {
+  return (unsigned)(((g.n[0] + KwTile::X - 1) / KwTile::X) * ((g.n[1] + KwTile::Y - 1) / KwTile::Y));
+}
 
 template <int PREC, bool MD>
 void step_prec_md(const StepArgs& A, const CurvGeom& G, int variant, cudaStream_t s) {
@@ -1006,11 +1044,11 @@ void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out
 
 void launch_curv_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, cudaStream_t s) {
   if (prec == PREC_F64)
-    curv_komega_kernel<PREC_F64><<<blocks_for(K.g.ncell), kCurvThreads, 0, s>>>(K, G);
+    curv_komega_kernel<PREC_F64><<<kw_tiles(K.g), KwTile::T, 0, s>>>(K, G);
   else if (prec == PREC_F32)
-    curv_komega_kernel<PREC_F32><<<blocks_for(K.g.ncell), kCurvThreads, 0, s>>>(K, G);
+    curv_komega_kernel<PREC_F32><<<kw_tiles(K.g), KwTile::T, 0, s>>>(K, G);
   else
-    curv_komega_kernel<PREC_F32D><<<blocks_for(K.g.ncell), kCurvThreads, 0, s>>>(K, G);
+    curv_komega_kernel<PREC_F32D><<<kw_tiles(K.g), KwTile::T, 0, s>>>(K, G);
 }
 
 void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s) {
