@@ -755,12 +755,12 @@ __device__ __forceinline__ void cell_kw(const KOmegaArgs& K, int i, int j, typen
 }
 
 // Fluxes (rho k, rho omega) through one face, towards increasing index: v*[0..3] the four cells
-// along the grid line, rl, rr the densities of the two cells beside the face, rec the face record.
+// along the grid line, rl, rr the densities of the two cells beside the face, fv the face's mass flux
+// followed by L, 1/d01, 1/d12, 1/d23, d_l, d_r of its record.
 template <class R>
-__device__ __forceinline__ void kw_face(const R* vk, const R* vw, R rl, R rr, const R* rec, long nf, long f, R fr,
-                                        R dt, R mu, R sigk, R sigw, int limiter_kind, bool diffusion, R* out) {
-  const R L = rec[2 * nf + f], i01 = rec[3 * nf + f], i12 = rec[4 * nf + f], i23 = rec[5 * nf + f];
-  const R dl = rec[6 * nf + f], dr = rec[7 * nf + f];
+__device__ __forceinline__ void kw_face(const R* vk, const R* vw, R rl, R rr, const R* fv, R dt, R mu, R sigk, R sigw,
+                                        int limiter_kind, bool diffusion, R* out) {
+  const R fr = fv[0], L = fv[1], i01 = fv[2], i12 = fv[3], i23 = fv[4], dl = fv[5], dr = fv[6];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const R* v = q == 0 ? vk : vw;
@@ -792,19 +792,50 @@ __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_con
   const int tiles_x = (n0 + TX - 1) / TX;
   const int i0 = (blockIdx.x % tiles_x) * TX, j0 = (blockIdx.x / tiles_x) * TY;
   const int tid = threadIdx.x;
-  const R dt = (R)K.ctrl->last_dt;
   const R* RKi = (const R*)K.RKin;
   const R* RWi = (const R*)K.RWin;
   const int li = tid % TX, lj = tid / TX;
   const int i = i0 + li, j = j0 + lj;
   const bool mine = i < n0 && j < n1;
   const long c = (long)j * n0 + i;
-  if (dt == R(0)) {  // t_end reached: carry the fields over (dt is the same for every CTA)
-    if (mine) {
-      ((R*)K.RKout)[c] = RKi[c];
-      ((R*)K.RWout)[c] = RWi[c];
+  const R dt = (R)K.ctrl->last_dt;  // in flight during the staging
+  // the face data of this thread's faces and the cell data of its cell, loaded before the staging
+  // so that their latency overlaps it
+  constexpr int FPT = (NFI + NFJ + KwTile::T - 1) / KwTile::T;
+  R fv[FPT][7];
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) {
+    const int q = tid + u * KwTile::T;
+    const bool ia = q < NFI;
+    const int r = ia ? q : q - NFI;
+    const int fl = ia ? r % (TX + 1) : r % TX, fm = ia ? r / (TX + 1) : r / TX;
+    const int fi = i0 + fl, fj = j0 + fm;
+    if (q >= NFI + NFJ || (ia ? (fi > n0 || fj >= n1) : (fi >= n0 || fj > n1))) continue;
+    const int a = ia ? 0 : 1;
+    const long nf = G.nf[a];
+    const long f = ia ? (long)fj * (n0 + 1) + fi : (long)fj * n0 + fi;
+    const R* rec = (const R*)G.face[a];
+    fv[u][0] = ((const R*)K.mflux[a])[f];
+#pragma unroll
+    for (int v = 1; v < 7; ++v) fv[u][v] = rec[(v + 1) * nf + f];
+  }
+  const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+  const long fid[4] = {fa, fa + 1, fc, fc + n0};
+  R A = R(1), rk0 = R(0), rw0 = R(0), gsx[4], gsy[4];
+  if (mine) {
+    A = (R)G.area[c];
+    rk0 = RKi[c];
+    rw0 = RWi[c];
+    if (K.sources) {
+      const FaceView<R> fvi{(const R*)G.face[0], G.nf[0]}, fvj{(const R*)G.face[1], G.nf[1]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const FaceView<R>& fw = q < 2 ? fvi : fvj;
+        const R sgn = (q & 1) ? R(1) : R(-1);
+        gsx[q] = sgn * fw(0, fid[q]) * fw(2, fid[q]);
+        gsy[q] = sgn * fw(1, fid[q]) * fw(2, fid[q]);
+      }
     }
-    return;
   }
   const Consts<R> kc = make_consts<R>(g);
   // phase 1: stage the tile with its halo
@@ -822,18 +853,25 @@ __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_con
     su[q] = g_div(w[1], w[0]);
     sv[q] = g_div(w[2], w[0]);
   }
+  if (dt == R(0)) {  // t_end reached: carry the fields over (dt is the same for every CTA)
+    if (mine) {
+      ((R*)K.RKout)[c] = rk0;
+      ((R*)K.RWout)[c] = rw0;
+    }
+    return;
+  }
   __syncthreads();
   // phase 2: every face of the tile once
   const bool kf = sizeof(R) == sizeof(float);
   const R sigk = kf ? (R)K.fsigma_star : (R)K.sigma_star, sigw = kf ? (R)K.fsigma : (R)K.sigma;
-  for (int q = tid; q < NFI + NFJ; q += KwTile::T) {
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) {
+    const int q = tid + u * KwTile::T;
     const bool ia = q < NFI;
     const int r = ia ? q : q - NFI;
     const int fl = ia ? r % (TX + 1) : r % TX, fm = ia ? r / (TX + 1) : r / TX;  // local face index
     const int fi = i0 + fl, fj = j0 + fm;
-    if (ia ? (fi > n0 || fj >= n1) : (fi >= n0 || fj > n1)) continue;
-    const int a = ia ? 0 : 1;
-    const long f = ia ? (long)fj * (n0 + 1) + fi : (long)fj * n0 + fi;
+    if (q >= NFI + NFJ || (ia ? (fi > n0 || fj >= n1) : (fi >= n0 || fj > n1))) continue;
     // staged index of the first stencil cell (fi - 2 or fj - 2) and the step along the grid line
     const int s0 = ia ? (fm + 2) * SX + fl : fm * SX + fl + 2, st = ia ? 1 : SX;
     R vk[4], vw[4];
@@ -843,8 +881,7 @@ __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_con
       vw[t] = sw[s0 + t * st];
     }
     R out[2];
-    kw_face<R>(vk, vw, sr[s0 + st], sr[s0 + 2 * st], (const R*)G.face[a], G.nf[a], f, ((const R*)K.mflux[a])[f], dt,
-               kc.mu, sigk, sigw, g.limiter, K.diffusion, out);
+    kw_face<R>(vk, vw, sr[s0 + st], sr[s0 + 2 * st], fv[u], dt, kc.mu, sigk, sigw, g.limiter, K.diffusion, out);
     (ia ? fi_k : fj_k)[r] = out[0];
     (ia ? fi_w : fj_w)[r] = out[1];
   }
@@ -855,24 +892,18 @@ __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_con
   const R beta_star = kf ? (R)K.fbeta_star : (R)K.beta_star, sigma_do = kf ? (R)K.fsigma_do : (R)K.sigma_do;
   const R C_lim = kf ? (R)K.fC_lim : (R)K.C_lim, omega_floor = kf ? (R)K.fomega_floor : (R)K.omega_floor;
   const int ra = lj * (TX + 1) + li, rc = lj * TX + li;
-  const R A = (R)G.area[c];
-  R ak = RKi[c] - (fi_k[ra + 1] - fi_k[ra] + fj_k[rc + TX] - fj_k[rc]) / A;
-  R aw = RWi[c] - (fi_w[ra + 1] - fi_w[ra] + fj_w[rc + TX] - fj_w[rc]) / A;
+  R ak = rk0 - (fi_k[ra + 1] - fi_k[ra] + fj_k[rc + TX] - fj_k[rc]) / A;
+  R aw = rw0 - (fi_w[ra + 1] - fi_w[ra] + fj_w[rc + TX] - fj_w[rc]) / A;
   R rate_k = R(0), rate_w = R(0);
   if (K.sources) {
     const int sc = (lj + 2) * SX + li + 2;
     const R rho = sr[sc], k0 = sk[sc], w0 = sw[sc];
-    const FaceView<R> fvi{(const R*)G.face[0], G.nf[0]}, fvj{(const R*)G.face[1], G.nf[1]};
-    const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
-    const long fid[4] = {fa, fa + 1, fc, fc + n0};
     const int nb[4] = {sc - 1, sc + 1, sc - SX, sc + SX};
     const R uc[2] = {su[sc], sv[sc]};
     R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const FaceView<R>& fv = q < 2 ? fvi : fvj;
-      const R sgn = (q & 1) ? R(1) : R(-1);
-      const R sx = sgn * fv(0, fid[q]) * fv(2, fid[q]), sy = sgn * fv(1, fid[q]) * fv(2, fid[q]);
+      const R sx = gsx[q], sy = gsy[q];
       const R un[2] = {su[nb[q]], sv[nb[q]]};
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
