@@ -82,6 +82,56 @@ def test_steady_cycles_on_a_c_grid_match_oracle(multid):
     s.close()
 
 
+def test_full_size_c_grid_steps_and_cycles_match_oracle():
+    """The benchmarked 608 x 160 NACA 0012 C-grid (M 0.8, 2.26 degrees, Re 9e6, k-omega tau_t from
+    free-stream fields): two FP64 time steps and two FP64 steady cycles (4 levels, 16 x 16 LU-SGS
+    tiles) equal the oracle's; the FP32 time steps in the autotuned launch configuration stay within
+    1e-5 (L1 of rho) over ten steps."""
+    from paper_1302_2132_gb300 import gks
+    sp = inputs.naca0012_case(112, 384, 160, mach=0.8, alpha_deg=2.26, Re=9.0e6, dy1=2e-4, ratio=1.05, R=10.0,
+                              x_out=10.0)
+    sp["turb"] = 3
+    f1, f2 = np.asarray(sp["f1"], dtype=np.float64).ravel(), np.asarray(sp["f2"], dtype=np.float64).ravel()
+    prim = np.asarray(sp["prim"], dtype=np.float64).ravel()
+    c = oracle_of(sp)
+    for precision, nsteps in (("fp64", 2), ("fp32", 10)):
+        s = gks.Solver(2, sp["n"], sp["bc"], dx=sp["dx"], bc_data=sp["bc_prim"], gamma=GAMMA, mu=sp["mu"],
+                       T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=0.5, limiter="vanleer", expand="directional",
+                       precision=precision, wake_cut=sp["wake_cut"])
+        s.set_nodes(sp["nodes"])
+        s.set_state(prim, layout="soa_prim")
+        s.set_turbulence(f1, f2)
+        W = c.prim_to_cons(prim)
+        for _ in range(nsteps):
+            dt = c.compute_dt_curv(sp["nodes"], W, 0.5)
+            s.step(nsteps=1, dt=dt)
+            W, st = c.step_curv(sp["nodes"], W, dt, f1=f1, f2=f2, nthreads=8)
+            assert st == 0
+        Wg = s.get_state()
+        s.close()
+        if precision == "fp64":
+            assert np.all(rel_per_var(Wg, W) < 1e-12)
+        else:
+            n = W.size // 4
+            assert np.abs(Wg[:n] - W[:n]).sum() / np.abs(W[:n]).sum() < 1e-5
+    s = gks.SteadySolver(sp["n"], sp["bc"], sp["nodes"], levels=4, bc_data=sp["bc_prim"], gamma=GAMMA, mu=sp["mu"],
+                         T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=0.5, limiter="vanleer", precision="fp64",
+                         lusgs_tile=16, wake_cut=sp["wake_cut"])
+    W = c.prim_to_cons(prim)
+    s.set_state(W)
+    s.set_turbulence(f1, f2)
+    res_g = s.cycles(2, cfl=1.0, cfl_flux=0.5)
+    res_o = []
+    for _ in range(2):
+        W, r, st = c.steady_cycle(sp["nodes"], W, 1.0, cfl_flux=0.5, levels=4, tiles=(16, 16), f1=f1, f2=f2,
+                                  nthreads=8)
+        assert st == 0
+        res_o.append(r)
+    assert np.allclose(res_g, res_o, rtol=1e-11, atol=0)
+    assert np.all(rel_per_var(s.get_state(), W) < 1e-11)
+    s.close()
+
+
 def test_a_wake_cut_needs_a_body_fitted_grid():
     from paper_1302_2132_gb300 import gks
     sp = case(nw=8, ns=16, n1=8, turb=0)
