@@ -139,6 +139,7 @@ def lib():
             L.orc_steady_residual.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I, _PD, _PD, _I]
             L.orc_lusgs.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD, _I, _I, _PD]
             L.orc_steady_cycle.argtypes = [P, _PD, _PD, _PD, _PD, _D, _D, _I, _I, _I, _I, _PD]
+            L.orc_steady_komega.argtypes = [P, _PD, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _D, _I]
             L.orc_komega_defaults.argtypes = [ctypes.POINTER(KOmega)]
             L.orc_step_komega.argtypes = [P, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _I]
             _lib = L
@@ -415,6 +416,32 @@ class Case:
                                     nthreads,
                                     ctypes.byref(res))
         return W, res.value, st
+
+    def steady_komega(self, nodes, W, RK, RW, cfl, cfl_flux=0.5, coeffs=None, nthreads=1):
+        """The steady k-omega update (one diagonal-implicit step with the flow residual's mass flux
+        rates and local steps) of RK, RW for the state W; returns (RK, RW, status)."""
+        nodes = self._nodes(nodes)
+        W = self._state(W)
+        RK = self._field(RK).copy()
+        RW = self._field(RW).copy()
+        c = coeffs if coeffs is not None else komega_defaults()
+        st = lib().orc_steady_komega(ctypes.byref(self.P), _ptr(nodes), ctypes.byref(c), _ptr(W), _ptr(RK), _ptr(RW),
+                                     cfl, cfl_flux, nthreads)
+        return RK, RW, st
+
+    def steady_cycle_komega(self, nodes, W, RK, RW, cfl, cfl_flux=0.5, levels=4, tiles=(32, 32), coeffs=None,
+                            nthreads=1):
+        """One steady cycle with k-omega transport: the k-omega update from the cycle's starting state,
+        then the flow cycle with the fields k = RK / rho, omega = RW / rho of that state; returns (W,
+        RK, RW, flow residual before the cycle, status)."""
+        W0 = self._state(W)
+        n = self.ncell
+        k, om = self._field(RK).ravel() / W0[:n], self._field(RW).ravel() / W0[:n]
+        RK, RW, st = self.steady_komega(nodes, W0, RK, RW, cfl, cfl_flux, coeffs, nthreads)
+        if st:
+            return W0.copy(), RK, RW, float("nan"), st
+        W, res, st = self.steady_cycle(nodes, W0, cfl, cfl_flux, levels, tiles, k, om, nthreads)
+        return W, RK, RW, res, st
 
 
 def komega_defaults(**over):

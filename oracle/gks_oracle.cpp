@@ -1617,7 +1617,7 @@ void curv_lts(const CurvCtx& C, std::vector<double>& dtc) {
 }
 
 void curv_residual(const CurvCtx& C, double cfl_flux, bool first_order, int nthreads, std::vector<double>& dtc,
-                   std::vector<double>& R) {
+                   std::vector<double>& R, std::vector<double>* mrate = nullptr) {
   const CurvGeom& g = C.g;
   const int n0 = g.n0, n1 = g.n1, nv = 4;
   const long ncell = (long)n0 * n1;
@@ -1633,6 +1633,12 @@ void curv_residual(const CurvCtx& C, double cfl_flux, bool first_order, int nthr
       win[1][(long)fj * n0 + i] = cfl_flux * std::min(dtc[C.src(i, fj - 1)], dtc[C.src(i, fj)]);
   std::vector<double> Fi, Fj;
   curv_fluxes(C, 0.0, win, first_order, nthreads, Fi, Fj);
+  if (mrate)  // mass flux rate times L of every face, one array per axis
+    for (int d = 0; d < 2; ++d) {
+      const std::vector<double>& F = d == 0 ? Fi : Fj;
+      mrate[d].resize(win[d].size());
+      for (size_t f = 0; f < win[d].size(); ++f) mrate[d][f] = F[f * nv] / win[d][f];
+    }
   R.assign((size_t)nv * ncell, 0.0);
   for (int j = 0; j < n1; ++j)
     for (int i = 0; i < n0; ++i) {
@@ -1851,6 +1857,66 @@ int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const do
   return status;
 }
 
+// Wilcox's production terms of cell (i, j) on a curvilinear grid (destruction left to the caller):
+// Sk = P_k, Sw = alpha (omega / omega~) rho X - 2/3 alpha rho omega div U + the cross diffusion, with
+// Green-Gauss gradients of U, k and omega (face values the means of the two cells).
+void kw_sources_curv(const orc_komega* K, const CurvGeom& g, const Grid& G, const std::vector<double>& Wp,
+                     const std::vector<double>& kp, const std::vector<double>& wp, int i, int j, double& Sk,
+                     double& Sw) {
+  const int n0 = g.n0;
+  const long c = (long)j * n0 + i, id = G.idx(i, j, 0);
+  const long fa = (long)j * (n0 + 1) + i, fb = fa + 1, fc2 = (long)j * n0 + i, fd = (long)(j + 1) * n0 + i;
+  const double A = g.area[c];
+  double w[5];
+  get_cell(G, Wp, i, j, 0, w);
+  const double rho = w[0], k0 = kp[id], w0 = wp[id];
+  // Green-Gauss gradients: velocity (gu[a][b] = dU_b/dx_a), k and omega
+  double gu[2][2] = {{0, 0}, {0, 0}}, gk[2] = {0, 0}, gw[2] = {0, 0};
+  const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+  const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
+  const long fid[4] = {fa, fb, fc2, fd};
+  for (int q = 0; q < 4; ++q) {
+    double wn[5];
+    get_cell(G, Wp, nb[q][0], nb[q][1], 0, wn);
+    const long nid = G.idx(nb[q][0], nb[q][1], 0);
+    const double nx = q < 2 ? g.inx[fid[q]] : g.jnx[fid[q]], ny = q < 2 ? g.iny[fid[q]] : g.jny[fid[q]];
+    const double L = q < 2 ? g.iL[fid[q]] : g.jL[fid[q]];
+    const double sx = sgn[q] * nx * L, sy = sgn[q] * ny * L;
+    for (int b = 0; b < 2; ++b) {
+      const double uf = 0.5 * (w[1 + b] / w[0] + wn[1 + b] / wn[0]);
+      gu[0][b] += uf * sx;
+      gu[1][b] += uf * sy;
+    }
+    const double kf = 0.5 * (k0 + kp[nid]), wf = 0.5 * (w0 + wp[nid]);
+    gk[0] += kf * sx;
+    gk[1] += kf * sy;
+    gw[0] += wf * sx;
+    gw[1] += wf * sy;
+  }
+  for (int a = 0; a < 2; ++a) {
+    gk[a] /= A;
+    gw[a] /= A;
+    for (int b = 0; b < 2; ++b) gu[a][b] /= A;
+  }
+  const double div = gu[0][0] + gu[1][1];
+  double SS = 0.0, SbSb = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const double sab = 0.5 * (gu[a][b] + gu[b][a]);
+      SS += sab * sab;
+      const double sb = sab - (a == b ? div / 3.0 : 0.0);
+      SbSb += sb * sb;
+    }
+  const double X = 2.0 * SS - 2.0 / 3.0 * div * div;
+  const double wt = std::max(w0, K->C_lim * std::sqrt(2.0 * SbSb / K->beta_star));
+  const double muT = rho * k0 / wt;
+  Sk = muT * X - 2.0 / 3.0 * rho * k0 * div;
+  const double dkdw = gk[0] * gw[0] + gk[1] * gw[1];
+  const double sd = dkdw > 0.0 ? K->sigma_do : 0.0;
+  const double CD = sd * rho / w0 * dkdw;
+  Sw = K->alpha * rho * (w0 / wt) * X - 2.0 / 3.0 * K->alpha * rho * w0 * div + CD;
+}
+
 // k-omega transport on a body-fitted grid (the rectilinear transport of orc_step_komega in each
 // face's frame): the flow step with tau_t from k = rho k / rho and omega = rho omega / rho, then per
 // face the convective flux F_rho * phi (F_rho the face's time-integrated mass flux times its length,
@@ -1942,57 +2008,12 @@ int orc_step_komega_curv(const orc_problem* P, const double* nodes, const orc_ko
       double aw = RW[c] - (Gw[0][fb] - Gw[0][fa] + Gw[1][fd] - Gw[1][fc2]) / A;
       double rate_k = 0.0, rate_w = 0.0;
       if (K->sources) {
-        double w[5];
-        get_cell(G, Wp, i, j, 0, w);
-        const double rho = w[0], k0 = kp[id], w0 = wp[id];
-        // Green-Gauss gradients: velocity (gu[a][b] = dU_b/dx_a), k and omega
-        double gu[2][2] = {{0, 0}, {0, 0}}, gk[2] = {0, 0}, gw[2] = {0, 0};
-        const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
-        const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
-        const long fid[4] = {fa, fb, fc2, fd};
-        for (int q = 0; q < 4; ++q) {
-          double wn[5];
-          get_cell(G, Wp, nb[q][0], nb[q][1], 0, wn);
-          const long nid = G.idx(nb[q][0], nb[q][1], 0);
-          const double nx = q < 2 ? g.inx[fid[q]] : g.jnx[fid[q]], ny = q < 2 ? g.iny[fid[q]] : g.jny[fid[q]];
-          const double L = q < 2 ? g.iL[fid[q]] : g.jL[fid[q]];
-          const double sx = sgn[q] * nx * L, sy = sgn[q] * ny * L;
-          for (int b = 0; b < 2; ++b) {
-            const double uf = 0.5 * (w[1 + b] / w[0] + wn[1 + b] / wn[0]);
-            gu[0][b] += uf * sx;
-            gu[1][b] += uf * sy;
-          }
-          const double kf = 0.5 * (k0 + kp[nid]), wf = 0.5 * (w0 + wp[nid]);
-          gk[0] += kf * sx;
-          gk[1] += kf * sy;
-          gw[0] += wf * sx;
-          gw[1] += wf * sy;
-        }
-        for (int a = 0; a < 2; ++a) {
-          gk[a] /= A;
-          gw[a] /= A;
-          for (int b = 0; b < 2; ++b) gu[a][b] /= A;
-        }
-        const double div = gu[0][0] + gu[1][1];
-        double SS = 0.0, SbSb = 0.0;
-        for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b) {
-            const double sab = 0.5 * (gu[a][b] + gu[b][a]);
-            SS += sab * sab;
-            const double sb = sab - (a == b ? div / 3.0 : 0.0);
-            SbSb += sb * sb;
-          }
-        const double X = 2.0 * SS - 2.0 / 3.0 * div * div;
-        const double wt = std::max(w0, K->C_lim * std::sqrt(2.0 * SbSb / K->beta_star));
-        const double muT = rho * k0 / wt;
-        const double Pk = muT * X - 2.0 / 3.0 * rho * k0 * div;
-        const double dkdw = gk[0] * gw[0] + gk[1] * gw[1];
-        const double sd = dkdw > 0.0 ? K->sigma_do : 0.0;
-        const double CD = sd * rho / w0 * dkdw;
-        ak += dt * Pk;
-        aw += dt * (K->alpha * rho * (w0 / wt) * X - 2.0 / 3.0 * K->alpha * rho * w0 * div + CD);
-        rate_k = K->beta_star * w0;
-        rate_w = K->beta0 * w0;  // the vortex-stretching factor is 1 in 2D
+        double Sk, Sw;
+        kw_sources_curv(K, g, G, Wp, kp, wp, i, j, Sk, Sw);
+        ak += dt * Sk;
+        aw += dt * Sw;
+        rate_k = K->beta_star * wp[id];
+        rate_w = K->beta0 * wp[id];  // the vortex-stretching factor is 1 in 2D
       }
       ak /= 1.0 + dt * rate_k;
       aw /= 1.0 + dt * rate_w;
@@ -2001,6 +2022,115 @@ int orc_step_komega_curv(const orc_problem* P, const double* nodes, const orc_ko
     }
   std::memcpy(W, Wnew.data(), sizeof(double) * Wnew.size());
   return status;
+}
+
+// Steady k-omega update on a body-fitted grid (the turbulence half of a steady cycle): from the
+// state W and k = RK / rho, omega = RW / rho, the flow residual gives the face mass flux rates m (times
+// L) and the local explicit steps; per face the rate G = m phi - (mu + sigma rho k / omega |face)
+// (phi_r - phi_l) / d12 L, phi the upwind cell's value plus its limited slope along the grid line
+// times the centroid-to-face distance; per cell the residual R = sum_faces G (outward) - A (S - beta
+// omega RK) with Wilcox's production terms S, and one diagonal-implicit step RK -= R / D,
+// D = A / (cfl dt_loc) + sum_faces (max(m_out, 0) + (mu + sigma rho k / omega |face) L / d12) / rho
+// + A beta omega (beta = beta* for k, beta0 for omega), then the floors.
+int orc_steady_komega(const orc_problem* P, const double* nodes, const orc_komega* K, const double* W, double* RK,
+                      double* RW, double cfl, double cfl_flux, int nthreads) {
+  if (P->turb_model != ORC_TURB_KOMEGA || P->dim != 2) return 1;
+  const int n0 = P->n[0], n1 = P->n[1];
+  const long ncell = (long)n0 * n1;
+  std::vector<double> kk(ncell), om(ncell);
+  for (long c = 0; c < ncell; ++c) {
+    kk[c] = RK[c] / W[c];
+    om[c] = RW[c] / W[c];
+  }
+  CurvCtx C;
+  const int st0 = curv_prepare(P, nodes, W, kk.data(), om.data(), C);
+  if (st0) return st0;
+  const CurvGeom& g = C.g;
+  const Grid& G = C.G;
+  std::vector<double> dtc, R, mr[2];
+  curv_residual(C, cfl_flux, false, nthreads, dtc, R, mr);
+  const std::vector<double>& Wp = C.Wp;
+  std::vector<double> kp = pad_scalar(P, G, kk.data()), wp = pad_scalar(P, G, om.data());
+  // per face: the rates of rho k and rho omega and the diffusive conductances (mu + sigma ...) L / d12
+  std::vector<double> Gk[2], Gw[2], Ck[2], Cw[2];
+  for (int d = 0; d < 2; ++d) {
+    const int nf0 = d == 0 ? n0 + 1 : n0, nf1 = d == 0 ? n1 : n1 + 1;
+    const long nfaces = (long)nf0 * nf1;
+    Gk[d].assign(nfaces, 0.0);
+    Gw[d].assign(nfaces, 0.0);
+    Ck[d].assign(nfaces, 0.0);
+    Cw[d].assign(nfaces, 0.0);
+    for (long f = 0; f < nfaces; ++f) {
+      const int fi = (int)(f % nf0), fj = (int)(f / nf0);
+      const double L = d == 0 ? g.iL[f] : g.jL[f];
+      const double mx = d == 0 ? g.imx[f] : g.jmx[f], my = d == 0 ? g.imy[f] : g.jmy[f];
+      int ci[4], cj[4];
+      for (int t = 0; t < 4; ++t) {
+        ci[t] = d == 0 ? fi - 2 + t : fi;
+        cj[t] = d == 0 ? fj : fj - 2 + t;
+      }
+      const double d01 = cdist(g, ci[0], cj[0], ci[1], cj[1]), d12 = cdist(g, ci[1], cj[1], ci[2], cj[2]);
+      const double d23 = cdist(g, ci[2], cj[2], ci[3], cj[3]);
+      const double dl = std::hypot(mx - g.pcx[g.pidx(ci[1], cj[1])], my - g.pcy[g.pidx(ci[1], cj[1])]);
+      const double dr = std::hypot(mx - g.pcx[g.pidx(ci[2], cj[2])], my - g.pcy[g.pidx(ci[2], cj[2])]);
+      const double m = mr[d][f];
+      const long il = G.idx(ci[1], cj[1], 0), ir = G.idx(ci[2], cj[2], 0);
+      const double rl0 = Wp[il], rr0 = Wp[ir];
+      for (int q = 0; q < 2; ++q) {
+        const std::vector<double>& fp = q == 0 ? kp : wp;
+        double v[4];
+        for (int t = 0; t < 4; ++t) v[t] = fp[G.idx(ci[t], cj[t], 0)];
+        const double s0 = limiter(P->limiter, (v[1] - v[0]) / d01, (v[2] - v[1]) / d12);
+        const double s1 = limiter(P->limiter, (v[2] - v[1]) / d12, (v[3] - v[2]) / d23);
+        const double phiL = v[1] + s0 * dl, phiR = v[2] - s1 * dr;
+        double gq = m * (m >= 0.0 ? phiL : phiR);
+        if (K->diffusion) {
+          const double sig = q == 0 ? K->sigma_star : K->sigma;
+          const double mdl = rl0 * kp[il] / wp[il], mdr = rr0 * kp[ir] / wp[ir];
+          const double cond = (P->mu + sig * 0.5 * (mdl + mdr)) * L / d12;
+          gq -= cond * (v[2] - v[1]);
+          (q == 0 ? Ck : Cw)[d][f] = cond;
+        }
+        (q == 0 ? Gk : Gw)[d][f] = gq;
+      }
+    }
+  }
+  std::vector<double> RKn(RK, RK + ncell), RWn(RW, RW + ncell);
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      const long id = G.idx(i, j, 0);
+      const long fa = (long)j * (n0 + 1) + i, fb = fa + 1, fc2 = (long)j * n0 + i, fd = (long)(j + 1) * n0 + i;
+      const double A = g.area[c], rho = W[c];
+      double rk = Gk[0][fb] - Gk[0][fa] + Gk[1][fd] - Gk[1][fc2];
+      double rw = Gw[0][fb] - Gw[0][fa] + Gw[1][fd] - Gw[1][fc2];
+      // outward mass rates and conductances of the four faces
+      const double mout[4] = {-mr[0][fa], mr[0][fb], -mr[1][fc2], mr[1][fd]};
+      const double ck[4] = {Ck[0][fa], Ck[0][fb], Ck[1][fc2], Ck[1][fd]};
+      const double cw[4] = {Cw[0][fa], Cw[0][fb], Cw[1][fc2], Cw[1][fd]};
+      const double base = A / (cfl * dtc[c]);
+      double Dk = 0.0, Dw = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        Dk += std::max(mout[q], 0.0) + ck[q];
+        Dw += std::max(mout[q], 0.0) + cw[q];
+      }
+      Dk = base + Dk / rho;
+      Dw = base + Dw / rho;
+      if (K->sources) {
+        double Sk, Sw;
+        kw_sources_curv(K, g, G, Wp, kp, wp, i, j, Sk, Sw);
+        const double w0 = wp[id];
+        rk -= A * (Sk - K->beta_star * w0 * RK[c]);
+        rw -= A * (Sw - K->beta0 * w0 * RW[c]);
+        Dk += A * K->beta_star * w0;
+        Dw += A * K->beta0 * w0;
+      }
+      RKn[c] = std::max(RK[c] - rk / Dk, 0.0);
+      RWn[c] = std::max(RW[c] - rw / Dw, rho * K->omega_floor);
+    }
+  std::memcpy(RK, RKn.data(), sizeof(double) * ncell);
+  std::memcpy(RW, RWn.data(), sizeof(double) * ncell);
+  return 0;
 }
 
 int orc_steady_residual(const orc_problem* P, const double* nodes, const double* W, const double* f1,

@@ -153,6 +153,18 @@ int orc_lusgs(const orc_problem* P, const double* nodes, const double* W, const 
 int orc_steady_cycle(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
                      double cfl, double cfl_flux, int levels, int tile0, int tile1, int nthreads, double* res);
 
+/* Steady k-omega update (P->turb_model ORC_TURB_KOMEGA): with k = RK / rho, omega = RW / rho and the
+ * flow residual of W (face mass flux rates m over the windows cfl_flux min(dt_l, dt_r), local explicit
+ * steps dt_loc), one diagonal-implicit step of the steady k-omega equations on the finest grid:
+ * per face G = m phi_upwind - (mu + sigma rho k / omega |face) (phi_r - phi_l) / d12 L (phi the
+ * cell value plus its limited slope times the centroid-to-face distance); per cell R = sum G
+ * (outward) - A (S - beta omega RK), RK -= R / D with D = A / (cfl dt_loc) + sum (max(m_out, 0) +
+ * conductance) / rho + A beta omega; floors RK >= 0, RW >= rho omega_floor.  W is not changed.  A
+ * steady cycle with k-omega transport is this update followed by orc_steady_cycle with the fields
+ * k, omega of the cycle's start. */
+int orc_steady_komega(const orc_problem* P, const double* nodes, const orc_komega* K, const double* W, double* RK,
+                      double* RW, double cfl, double cfl_flux, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
