@@ -159,8 +159,19 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
  *     fields and Dirichlet data by means; coarse residuals first order with the forcing
  *     sum R_f - R_c(W_c^0); one LU-SGS smoothing per level on the way down, the corrections
  *     W_c - W_c^0 injected on the way up.
+ *   - GKS_TURB_KOMEGA_TRANSPORT: each cycle first takes k = rho k / rho, omega = rho omega / rho of
+ *     its starting state on the finest grid (four-cell means below), evaluates the fine residual
+ *     with them, and from the same residual (its face mass flux rates m, times L, and local steps)
+ *     makes one diagonal-implicit step of the steady k-omega equations (the model of gks_komega):
+ *     per face G = m phi_upwind - (mu + sigma rho k / omega |face) L / d12 (phi_r - phi_l), phi the
+ *     cell value plus its limited slope along the grid line times the centroid-to-face distance;
+ *     per cell R = sum G (outward) - A (S - beta omega rho k) with Wilcox's production terms S,
+ *     rho k -= R / D, D = A / (cfl s) + sum_faces (max(m_out, 0) + conductance) / rho + A beta omega
+ *     (beta* for k, beta0 for omega), then the floors; the flow cycle keeps the fields of the
+ *     cycle's start.
  * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), both expansions (the
- * multi-dimensional one on the finest level; coarse levels are first order), MUSCL2, turbulence models NONE, MUT, KEPS, KOMEGA (prescribed fields).  nodes: host,
+ * multi-dimensional one on the finest level; coarse levels are first order), MUSCL2, turbulence
+ * models NONE, MUT, KEPS, KOMEGA (prescribed fields) and KOMEGA_TRANSPORT.  nodes: host,
  * [(n1 + 1)][(n0 + 1)][2] as gks_set_nodes.  Errors: GKS_EUNSUPPORTED for other options, GKS_EINVAL
  * for bad sizes, levels or a folded cell on any level. */
 typedef struct gks_steady gks_steady;
@@ -168,7 +179,9 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
                              const gks_numerics* num, const double* nodes, int levels, int lusgs_tile,
                              void* cuda_stream, gks_steady** out);
 /* Copy the fine-grid state in (as gks_set_state); the prescribed turbulence fields (as
- * gks_set_turbulence; coarse levels take four-cell means). */
+ * gks_set_turbulence; coarse levels take four-cell means).  With GKS_TURB_KOMEGA_TRANSPORT the fields
+ * are the initial k and omega, stored as rho k and rho omega with the density of the current state:
+ * set the state first (gks_steady_set_state clears them); GKS_EINVAL otherwise. */
 gks_status gks_steady_set_state(gks_steady* s, const void* W, int layout, int memspace, int dtype);
 gks_status gks_steady_set_turbulence(gks_steady* s, const void* f1, const void* f2, int memspace, int dtype);
 /* Run ncycles multigrid cycles (one CUDA graph per cycle, captured once per (cfl, cfl_flux)); res_out
@@ -221,6 +234,12 @@ gks_status gks_set_komega(gks_handle* h, const gks_komega* c);
 
 /* Copy out the transported k and omega (GKS_TURB_KOMEGA_TRANSPORT), one value per cell. */
 gks_status gks_get_turbulence(gks_handle* h, void* k_out, void* omega_out, int memspace, int dtype);
+
+/* Steady solver handles with GKS_TURB_KOMEGA_TRANSPORT: replace the closure coefficients (defaults gks_komega_defaults;
+ * effective from the next cycle), and copy out k = rho k / rho, omega = rho omega / rho of the
+ * current state (either output may be NULL; synchronises).  GKS_EINVAL for other handles. */
+gks_status gks_steady_set_komega(gks_steady* s, const gks_komega* c);
+gks_status gks_steady_get_turbulence(gks_steady* s, void* k_out, void* omega_out, int memspace, int dtype);
 
 /* CFL time step of the current state: dt = cfl / max_cells sum_d (|U_d| + c) / dx_d. Synchronises. */
 gks_status gks_compute_dt(gks_handle* h, double cfl, double* dt_out);

@@ -590,7 +590,8 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;
       Fs[2 * NF + l] = (F[1] * ny + F[2] * nx) * L_;
       Fs[3 * NF + l] = F[3] * L_;
-      if (MODE == 0 && A.mflux[0]) {  // the face's time-integrated mass flux times L (k-omega transport)
+      if (A.mflux[0]) {  // the face's mass flux times L (k-omega transport): time-integrated, or the
+                         // rate over the window in the residual mode
         const long gfm = a == 0 ? (long)(oy + lj) * (n0 + 1) + ox + li : (long)(oy + lj) * n0 + ox + li;
         ((R*)A.mflux[a])[gfm] = Fs[l];
       }
@@ -778,6 +779,62 @@ __device__ __forceinline__ void kw_face(const R* vk, const R* vw, R rl, R rr, co
   }
 }
 
+// Wilcox's production terms of the cell at staged index sc (destruction left to the caller):
+// Sk = P_k, Sw = alpha rho (omega / omega~) X - 2/3 alpha rho omega div U + the cross diffusion, with
+// Green-Gauss gradients from the staged neighbours (face values the means of the two cells);
+// gsx, gsy: the outward n_x L, n_y L of the faces i-1/2, i+1/2, j-1/2, j+1/2.
+template <class R, int SX>
+__device__ __forceinline__ void kw_sources(const R* sk, const R* sw, const R* sr, const R* su, const R* sv, int sc,
+                                           const R* gsx, const R* gsy, R A, R alpha, R beta_star, R sigma_do, R C_lim,
+                                           R& Sk, R& Sw) {
+  const R rho = sr[sc], k0 = sk[sc], w0 = sw[sc];
+  const int nb[4] = {sc - 1, sc + 1, sc - SX, sc + SX};
+  const R uc[2] = {su[sc], sv[sc]};
+  R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R sx = gsx[q], sy = gsy[q];
+    const R un[2] = {su[nb[q]], sv[nb[q]]};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const R uf = R(0.5) * (uc[b] + un[b]);
+      gu[0][b] += uf * sx;
+      gu[1][b] += uf * sy;
+    }
+    const R kff = R(0.5) * (k0 + sk[nb[q]]), wff = R(0.5) * (w0 + sw[nb[q]]);
+    gk[0] += kff * sx;
+    gk[1] += kff * sy;
+    gw[0] += wff * sx;
+    gw[1] += wff * sy;
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    gk[a] /= A;
+    gw[a] /= A;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) gu[a][b] /= A;
+  }
+  const R div = gu[0][0] + gu[1][1];
+  R SS = R(0), SbSb = R(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const R sab = R(0.5) * (gu[a][b] + gu[b][a]);
+      SS += sab * sab;
+      const R sb = sab - (a == b ? div / R(3) : R(0));
+      SbSb += sb * sb;
+    }
+  const R X = R(2) * SS - R(2) / R(3) * div * div;
+  const R wt = fmax(w0, C_lim * g_sqrt(R(2) * SbSb / beta_star));
+  const R muT = rho * k0 / wt;
+  Sk = muT * X - R(2) / R(3) * rho * k0 * div;
+  const R dkdw = gk[0] * gw[0] + gk[1] * gw[1];
+  const R sd = dkdw > R(0) ? sigma_do : R(0);
+  const R CD = sd * rho / w0 * dkdw;
+  Sw = alpha * rho * (w0 / wt) * X - R(2) / R(3) * alpha * rho * w0 * div + CD;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_constant__ KOmegaArgs K,
                                                                 const __grid_constant__ CurvGeom G) {
@@ -897,53 +954,11 @@ __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_con
   R rate_k = R(0), rate_w = R(0);
   if (K.sources) {
     const int sc = (lj + 2) * SX + li + 2;
-    const R rho = sr[sc], k0 = sk[sc], w0 = sw[sc];
-    const int nb[4] = {sc - 1, sc + 1, sc - SX, sc + SX};
-    const R uc[2] = {su[sc], sv[sc]};
-    R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const R sx = gsx[q], sy = gsy[q];
-      const R un[2] = {su[nb[q]], sv[nb[q]]};
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const R uf = R(0.5) * (uc[b] + un[b]);
-        gu[0][b] += uf * sx;
-        gu[1][b] += uf * sy;
-      }
-      const R kff = R(0.5) * (k0 + sk[nb[q]]), wff = R(0.5) * (w0 + sw[nb[q]]);
-      gk[0] += kff * sx;
-      gk[1] += kff * sy;
-      gw[0] += wff * sx;
-      gw[1] += wff * sy;
-    }
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      gk[a] /= A;
-      gw[a] /= A;
-#pragma unroll
-      for (int b = 0; b < 2; ++b) gu[a][b] /= A;
-    }
-    const R div = gu[0][0] + gu[1][1];
-    R SS = R(0), SbSb = R(0);
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const R sab = R(0.5) * (gu[a][b] + gu[b][a]);
-        SS += sab * sab;
-        const R sb = sab - (a == b ? div / R(3) : R(0));
-        SbSb += sb * sb;
-      }
-    const R X = R(2) * SS - R(2) / R(3) * div * div;
-    const R wt = fmax(w0, C_lim * g_sqrt(R(2) * SbSb / beta_star));
-    const R muT = rho * k0 / wt;
-    const R Pk = muT * X - R(2) / R(3) * rho * k0 * div;
-    const R dkdw = gk[0] * gw[0] + gk[1] * gw[1];
-    const R sd = dkdw > R(0) ? sigma_do : R(0);
-    const R CD = sd * rho / w0 * dkdw;
-    ak += dt * Pk;
-    aw += dt * (alpha * rho * (w0 / wt) * X - R(2) / R(3) * alpha * rho * w0 * div + CD);
+    R Sk, Sw;
+    kw_sources<R, SX>(sk, sw, sr, su, sv, sc, gsx, gsy, A, alpha, beta_star, sigma_do, C_lim, Sk, Sw);
+    const R w0 = sw[sc];
+    ak += dt * Sk;
+    aw += dt * Sw;
     rate_k = beta_star * w0;
     rate_w = beta0 * w0;
   }
@@ -952,6 +967,170 @@ __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_con
   const R rho_new = (R)((const S*)K.Wnew)[c];
   ((R*)K.RKout)[c] = fmax(ak, R(0));
   ((R*)K.RWout)[c] = fmax(aw, rho_new * omega_floor);
+}
+
+// ---- steady k-omega update ---------------------------------------------------------------------
+// One diagonal-implicit step of the steady k-omega equations on the finest grid of the steady solver,
+// in place, with the fine residual's face mass flux rates (times L) and local steps: per face the
+// rates G = m phi_upwind - (mu + sigma rho k / omega |face) L / d12 (phi_r - phi_l); per cell
+// R = sum G (outward) - A (S - beta omega RK), RK -= R / D, D = A / (cfl s_loc) + sum_faces
+// (max(m_out, 0) + conductance) / rho + A beta omega; then the floors.  Tiles and staging as the
+// transport kernel; k and omega come from the field arrays (RK / rho of the cycle's start), so the
+// in-place update reads no value another thread writes.
+struct SteadyKw {
+  const void* k;      // k, omega per cell (arithmetic type)
+  const void* om;
+  void* RK;           // rho k, rho omega, updated in place
+  void* RW;
+  const void* s_loc;  // local explicit steps
+  double cfl;         // pseudo-time steps cfl s_loc
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(KwTile::T) steady_komega_kernel(const __grid_constant__ KOmegaArgs K,
+                                                                  const __grid_constant__ CurvGeom G,
+                                                                  const __grid_constant__ SteadyKw Q) {
+  using R = typename PrecT<PREC>::R;
+  constexpr int TX = KwTile::X, TY = KwTile::Y, SX = KwTile::SX, NS = KwTile::SX * KwTile::SY;
+  constexpr int NFI = (TX + 1) * TY, NFJ = TX * (TY + 1);
+  __shared__ R sk[NS], sw[NS], sr[NS], su[NS], sv[NS];
+  // per face: rates of rho k and rho omega, mass rate, conductances of k and omega
+  __shared__ R fg[5][NFI + NFJ];
+  const DevGrid& g = K.g;
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int tiles_x = (n0 + TX - 1) / TX;
+  const int i0 = (blockIdx.x % tiles_x) * TX, j0 = (blockIdx.x / tiles_x) * TY;
+  const int tid = threadIdx.x;
+  const int li = tid % TX, lj = tid / TX;
+  const int i = i0 + li, j = j0 + lj;
+  const bool mine = i < n0 && j < n1;
+  const long c = (long)j * n0 + i;
+  R* RK = (R*)Q.RK;
+  R* RW = (R*)Q.RW;
+  constexpr int FPT = (NFI + NFJ + KwTile::T - 1) / KwTile::T;
+  R fv[FPT][7];
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) {
+    const int q = tid + u * KwTile::T;
+    const bool ia = q < NFI;
+    const int r = ia ? q : q - NFI;
+    const int fl = ia ? r % (TX + 1) : r % TX, fm = ia ? r / (TX + 1) : r / TX;
+    const int fi = i0 + fl, fj = j0 + fm;
+    if (q >= NFI + NFJ || (ia ? (fi > n0 || fj >= n1) : (fi >= n0 || fj > n1))) continue;
+    const int a = ia ? 0 : 1;
+    const long nf = G.nf[a];
+    const long f = ia ? (long)fj * (n0 + 1) + fi : (long)fj * n0 + fi;
+    const R* rec = (const R*)G.face[a];
+    fv[u][0] = ((const R*)K.mflux[a])[f];
+#pragma unroll
+    for (int v = 1; v < 7; ++v) fv[u][v] = rec[(v + 1) * nf + f];
+  }
+  const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+  const long fid[4] = {fa, fa + 1, fc, fc + n0};
+  R A = R(1), rk0 = R(0), rw0 = R(0), sl = R(1), gsx[4], gsy[4];
+  if (mine) {
+    A = (R)G.area[c];
+    rk0 = RK[c];
+    rw0 = RW[c];
+    sl = ((const R*)Q.s_loc)[c];
+    const FaceView<R> fvi{(const R*)G.face[0], G.nf[0]}, fvj{(const R*)G.face[1], G.nf[1]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const FaceView<R>& fw = q < 2 ? fvi : fvj;
+      const R sgn = (q & 1) ? R(1) : R(-1);
+      gsx[q] = sgn * fw(0, fid[q]) * fw(2, fid[q]);
+      gsy[q] = sgn * fw(1, fid[q]) * fw(2, fid[q]);
+    }
+  }
+  const Consts<R> kc = make_consts<R>(g);
+  for (int q = tid; q < NS; q += KwTile::T) {
+    const int qi = q % SX, qj = q / SX;
+    const bool corner = (qi < 2 || qi >= TX + 2) && (qj < 2 || qj >= TY + 2);
+    const int gi = i0 - 2 + qi, gj = j0 - 2 + qj;
+    if (corner || gi > n0 + 1 || gj > n1 + 1) continue;
+    R w[4];
+    load_cell<2, PREC>(g, K.Win, kc, gi, gj, 0, w);
+    const long src = field_cell(g, 2, gi, gj, 0);
+    sk[q] = ((const R*)Q.k)[src];
+    sw[q] = ((const R*)Q.om)[src];
+    sr[q] = w[0];
+    su[q] = g_div(w[1], w[0]);
+    sv[q] = g_div(w[2], w[0]);
+  }
+  __syncthreads();
+  const bool kf = sizeof(R) == sizeof(float);
+  const R sigk = kf ? (R)K.fsigma_star : (R)K.sigma_star, sigw = kf ? (R)K.fsigma : (R)K.sigma;
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) {
+    const int q = tid + u * KwTile::T;
+    const bool ia = q < NFI;
+    const int r = ia ? q : q - NFI;
+    const int fl = ia ? r % (TX + 1) : r % TX, fm = ia ? r / (TX + 1) : r / TX;
+    const int fi = i0 + fl, fj = j0 + fm;
+    if (q >= NFI + NFJ || (ia ? (fi > n0 || fj >= n1) : (fi >= n0 || fj > n1))) continue;
+    const int s0 = ia ? (fm + 2) * SX + fl : fm * SX + fl + 2, st = ia ? 1 : SX;
+    const R m = fv[u][0], L = fv[u][1], i01 = fv[u][2], i12 = fv[u][3], i23 = fv[u][4], dl = fv[u][5],
+            dr = fv[u][6];
+    const R rl = sr[s0 + st], rr = sr[s0 + 2 * st];
+    R vk[4], vw[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      vk[t] = sk[s0 + t * st];
+      vw[t] = sw[s0 + t * st];
+    }
+    R cond[2] = {R(0), R(0)}, gq[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const R* v = e == 0 ? vk : vw;
+      const R sa = limiter<R>(g.limiter, (v[1] - v[0]) * i01, (v[2] - v[1]) * i12);
+      const R sb = limiter<R>(g.limiter, (v[2] - v[1]) * i12, (v[3] - v[2]) * i23);
+      const R phiL = v[1] + sa * dl, phiR = v[2] - sb * dr;
+      gq[e] = m * (m >= R(0) ? phiL : phiR);
+      if (K.diffusion) {
+        const R mdl = g_div(rl * vk[1], vw[1]), mdr = g_div(rr * vk[2], vw[2]);
+        cond[e] = (kc.mu + (e == 0 ? sigk : sigw) * R(0.5) * (mdl + mdr)) * L * i12;
+        gq[e] -= cond[e] * (v[2] - v[1]);
+      }
+    }
+    fg[0][q] = gq[0];
+    fg[1][q] = gq[1];
+    fg[2][q] = m;
+    fg[3][q] = cond[0];
+    fg[4][q] = cond[1];
+  }
+  __syncthreads();
+  if (!mine) return;
+  const R alpha = kf ? (R)K.falpha : (R)K.alpha, beta0 = kf ? (R)K.fbeta0 : (R)K.beta0;
+  const R beta_star = kf ? (R)K.fbeta_star : (R)K.beta_star, sigma_do = kf ? (R)K.fsigma_do : (R)K.sigma_do;
+  const R C_lim = kf ? (R)K.fC_lim : (R)K.C_lim, omega_floor = kf ? (R)K.fomega_floor : (R)K.omega_floor;
+  // faces i-1/2, i+1/2, j-1/2, j+1/2 in the face arrays, and the outward sign
+  const int ra = lj * (TX + 1) + li, rc = NFI + lj * TX + li;
+  const int fq[4] = {ra, ra + 1, rc, rc + TX};
+  const int sc = (lj + 2) * SX + li + 2;
+  const R rho = sr[sc];
+  R rk = fg[0][fq[1]] - fg[0][fq[0]] + fg[0][fq[3]] - fg[0][fq[2]];
+  R rw = fg[1][fq[1]] - fg[1][fq[0]] + fg[1][fq[3]] - fg[1][fq[2]];
+  R dk = R(0), dw = R(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R mo = (q & 1) ? fg[2][fq[q]] : -fg[2][fq[q]];
+    dk += fmax(mo, R(0)) + fg[3][fq[q]];
+    dw += fmax(mo, R(0)) + fg[4][fq[q]];
+  }
+  const R base = A / ((R)Q.cfl * sl);
+  dk = base + dk / rho;
+  dw = base + dw / rho;
+  if (K.sources) {
+    R Sk, Sw;
+    kw_sources<R, SX>(sk, sw, sr, su, sv, sc, gsx, gsy, A, alpha, beta_star, sigma_do, C_lim, Sk, Sw);
+    const R w0 = sw[sc];
+    rk -= A * (Sk - beta_star * w0 * rk0);
+    rw -= A * (Sw - beta0 * w0 * rw0);
+    dk += A * beta_star * w0;
+    dw += A * beta0 * w0;
+  }
+  RK[c] = fmax(rk0 - rk / dk, R(0));
+  RW[c] = fmax(rw0 - rw / dw, rho * omega_floor);
 }
 
 // Local explicit step (CFL 1) of every cell: 2 A / sum_faces (|U.n| + c) L.
@@ -1032,6 +1211,15 @@ void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int varian
     step_prec<PREC_F32>(A, G, variant, multid, s);
   else
     step_prec<PREC_F32D>(A, G, variant, multid, s);
+}
+
+void launch_steady_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, const void* k, const void* om, void* RK,
+                          void* RW, const void* s_loc, double cfl, cudaStream_t s) {
+  const SteadyKw Q{k, om, RK, RW, s_loc, cfl};
+  if (prec == PREC_F64)
+    steady_komega_kernel<PREC_F64><<<kw_tiles(K.g), KwTile::T, 0, s>>>(K, G, Q);
+  else
+    steady_komega_kernel<PREC_F32><<<kw_tiles(K.g), KwTile::T, 0, s>>>(K, G, Q);
 }
 
 void curv_tile_shape(int variant, int* x, int* y) {

@@ -52,5 +52,10 @@ void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const 
 void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s);
 // k-omega transport after a flow step on the grid (K.mflux: the step's face mass fluxes times length)
 void launch_curv_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, cudaStream_t s);
+// Steady k-omega update on the finest grid of the steady solver, in place (K.mflux: the residual's
+// face mass flux rates times length; k, om: the fields of the cycle's start; pseudo-time steps
+// cfl s_loc; PREC_F64 or PREC_F32)
+void launch_steady_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, const void* k, const void* om, void* RK,
+                          void* RW, const void* s_loc, double cfl, cudaStream_t s);
 
 }  // namespace gks

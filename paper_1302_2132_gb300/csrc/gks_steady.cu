@@ -363,6 +363,10 @@ struct gks_steady {
   void* staging = nullptr;
   size_t staging_bytes = 0;
   bool has_state = false, has_turb = false;
+  bool transport = false;            // GKS_TURB_KOMEGA_TRANSPORT: rho k, rho omega evolved each cycle
+  void *RK = nullptr, *RW = nullptr;  // finest grid, arithmetic type
+  void* mflux[2] = {nullptr, nullptr};  // fine residual's face mass flux rates times L, per axis
+  gks_komega kw{};
   std::map<std::pair<double, double>, cudaGraphExec_t> graphs;  // one captured cycle per (cfl, cfl_flux)
   std::string err;
 };
@@ -404,9 +408,10 @@ void free_steady(gks_steady* s) {
   drop_graphs(s);
   for (auto& l : s->L) free_level(l);
   s->L.clear();
-  void* ps[] = {s->acc, s->counter, s->bad, s->history, s->staging};
+  void* ps[] = {s->acc, s->counter, s->bad, s->history, s->staging, s->RK, s->RW, s->mflux[0], s->mflux[1]};
   for (void* p : ps)
     if (p) cudaFree(p);
+  s->RK = s->RW = s->mflux[0] = s->mflux[1] = nullptr;
   s->acc = nullptr;
   s->counter = nullptr;
   s->bad = nullptr;
@@ -426,9 +431,12 @@ StepArgs level_args(const gks_steady* s, int l, const void* Win) {
 }
 
 // Residual of level l's state Win into lev.R (forcing on coarse levels), with the local steps.
-void residual(gks_steady* s, int l, const void* Win, const void* forcing, double cfl_flux, double* acc) {
+void residual(gks_steady* s, int l, const void* Win, const void* forcing, double cfl_flux, double* acc,
+              bool mass_flux = false) {
   SteadyLevel& lev = s->L[l];
-  const StepArgs A = level_args(s, l, Win);
+  StepArgs A = level_args(s, l, Win);
+  if (mass_flux)
+    for (int a = 0; a < 2; ++a) A.mflux[a] = s->mflux[a];
   launch_curv_lts(s->prec, A, lev.G, lev.s, s->stream);
   SteadyArgs SA{};
   SA.s_loc = lev.s;
@@ -442,15 +450,78 @@ void residual(gks_steady* s, int l, const void* Win, const void* forcing, double
   launch_curv_residual(s->prec, A, lev.G, SA, s->stream);
 }
 
+// Four-cell means of the turbulence fields down the levels.
+void restrict_fields(gks_steady* s) {
+  for (int l = 1; l < s->levels; ++l) {
+    SteadyLevel& c = s->L[l];
+    SteadyLevel& p = s->L[l - 1];
+    for (int q = 0; q < 2; ++q) {
+      const void* src = q == 0 ? p.f1 : p.f2;
+      void* dst = q == 0 ? c.f1 : c.f2;
+      if (s->prec == PREC_F64)
+        mean4_kernel<double><<<nblk(c.ncell), kST, 0, s->stream>>>(c.n0, c.n1, p.n0, (const double*)src, (double*)dst);
+      else
+        mean4_kernel<float><<<nblk(c.ncell), kST, 0, s->stream>>>(c.n0, c.n1, p.n0, (const float*)src, (float*)dst);
+    }
+  }
+}
+
+// Arguments of the steady k-omega update on the finest grid.
+KOmegaArgs kw_args(const gks_steady* s) {
+  KOmegaArgs K;
+  std::memset(&K, 0, sizeof(K));
+  const SteadyLevel& f = s->L[0];
+  K.g = f.g;
+  K.Win = f.W;
+  K.Wnew = f.W;
+  K.RKin = s->RK;
+  K.RWin = s->RW;
+  K.RKout = s->RK;
+  K.RWout = s->RW;
+  K.mflux[0] = s->mflux[0];
+  K.mflux[1] = s->mflux[1];
+  K.alpha = s->kw.alpha;
+  K.beta0 = s->kw.beta0;
+  K.beta_star = f.g.beta_star;
+  K.sigma = s->kw.sigma;
+  K.sigma_star = s->kw.sigma_star;
+  K.sigma_do = s->kw.sigma_do;
+  K.C_lim = s->kw.C_lim;
+  K.omega_floor = s->kw.omega_floor;
+  K.sources = s->kw.sources;
+  K.diffusion = s->kw.diffusion;
+  K.falpha = (float)K.alpha;
+  K.fbeta0 = (float)K.beta0;
+  K.fbeta_star = (float)K.beta_star;
+  K.fsigma = (float)K.sigma;
+  K.fsigma_star = (float)K.sigma_star;
+  K.fsigma_do = (float)K.sigma_do;
+  K.fC_lim = (float)K.C_lim;
+  K.fomega_floor = (float)K.omega_floor;
+  return K;
+}
+
 template <int PREC>
 void cycle_prec(gks_steady* s, double cfl, double cfl_flux) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
   const int nl = s->levels;
+  if (s->transport) {  // k = rho k / rho, omega = rho omega / rho of the cycle's start, on every level
+    SteadyLevel& f = s->L[0];
+    aux::density_unscale_kernel<R, S, R><<<nblk(f.ncell), kST, 0, s->stream>>>((const R*)s->RK, (const S*)f.W,
+                                                                               (R*)f.f1, f.ncell);
+    aux::density_unscale_kernel<R, S, R><<<nblk(f.ncell), kST, 0, s->stream>>>((const R*)s->RW, (const S*)f.W,
+                                                                               (R*)f.f2, f.ncell);
+    restrict_fields(s);
+  }
   for (int l = 0; l < nl; ++l) {
     SteadyLevel& lev = s->L[l];
     const void* forcing = l > 0 ? lev.P : nullptr;
-    residual(s, l, lev.W, forcing, cfl_flux, l == 0 ? s->acc : nullptr);
+    residual(s, l, lev.W, forcing, cfl_flux, l == 0 ? s->acc : nullptr, l == 0 && s->transport);
+    if (l == 0 && s->transport) {  // the k-omega update from the same state, fields and residual
+      const KOmegaArgs K = kw_args(s);
+      launch_steady_komega(s->prec, K, lev.G, lev.f1, lev.f2, s->RK, s->RW, lev.s, cfl, s->stream);
+    }
     const StepArgs A = level_args(s, l, lev.W);
     face_lambda_kernel<PREC><<<nblk(lev.G.nf[0] + lev.G.nf[1]), kST, 0, s->stream>>>(A, lev.G, lev.G.tau, lev.hl[0],
                                                                                       lev.hl[1]);
@@ -532,8 +603,10 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   if (!grid || !gas || !num || !nodes) return GKS_EINVAL;
   if (grid->dim != 2 || num->reconstruction != GKS_RECON_MUSCL2) return GKS_EUNSUPPORTED;
   if (num->precision != GKS_FP64 && num->precision != GKS_FP32) return GKS_EUNSUPPORTED;
-  const int model = turb ? turb->model : GKS_TURB_NONE;
-  if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA) return GKS_EUNSUPPORTED;
+  const int model_in = turb ? turb->model : GKS_TURB_NONE;
+  if (model_in < GKS_TURB_NONE || model_in > GKS_TURB_KOMEGA_TRANSPORT) return GKS_EUNSUPPORTED;
+  // with transport the levels take tau_t from the fields k, omega of each cycle's start
+  const int model = model_in == GKS_TURB_KOMEGA_TRANSPORT ? (int)GKS_TURB_KOMEGA : model_in;
   if (levels < 1 || levels > 6) return GKS_EINVAL;
   if (lusgs_tile != 0 && lusgs_tile != 16 && lusgs_tile != 32) return GKS_EINVAL;
   const int n0 = grid->n[0], n1 = grid->n[1];
@@ -556,6 +629,8 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   s->levels = levels;
   s->tile = lusgs_tile == 32 ? 32 : 16;
   s->multid = num->expand == GKS_EXPAND_MULTID;
+  s->transport = model_in == GKS_TURB_KOMEGA_TRANSPORT;
+  gks_komega_defaults(&s->kw);
   auto bad = [&](gks_status st) {
     free_steady(s);
     delete s;
@@ -672,6 +747,11 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     g.wake_cut = grid->wake_cut >> l;
     set_consts(g);
   }
+  if (s->transport) {
+    alloc(&s->RK, rb * s->L[0].ncell);
+    alloc(&s->RW, rb * s->L[0].ncell);
+    for (int a = 0; a < 2; ++a) alloc(&s->mflux[a], rb * s->L[0].G.nf[a]);
+  }
   alloc((void**)&s->acc, sizeof(double));
   alloc((void**)&s->counter, sizeof(int));
   alloc((void**)&s->bad, sizeof(unsigned));
@@ -736,6 +816,7 @@ gks_status gks_steady_set_state(gks_steady* s, const void* W, int layout, int me
                                                                           f.g.gamma, prec, f.W, lo_scratch);
   GKS_SCK(s, cudaGetLastError());
   s->has_state = true;
+  if (s->transport) s->has_turb = false;  // rho k, rho omega belong to the previous state
   return GKS_OK;
 }
 
@@ -745,6 +826,7 @@ gks_status gks_steady_set_turbulence(gks_steady* s, const void* f1, const void* 
   if (s->L[0].g.turb_model != GKS_TURB_MUT && !f2) return sfail(s, GKS_EINVAL, "second field missing");
   if ((dtype != GKS_F64 && dtype != GKS_F32) || (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
     return sfail(s, GKS_EINVAL, "memspace or dtype");
+  if (s->transport && !s->has_state) return sfail(s, GKS_EINVAL, "k-omega transport: set the state first");
   SteadyLevel& f = s->L[0];
   const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * (size_t)f.ncell;
   const void* srcs[2] = {f1, f2};
@@ -768,22 +850,72 @@ gks_status gks_steady_set_turbulence(gks_steady* s, const void* f1, const void* 
     else
       aux::field_kernel<float, float><<<blocks, 256, 0, s->stream>>>((const float*)src, (float*)dsts[q], f.ncell);
   }
-  for (int l = 1; l < s->levels; ++l) {
-    SteadyLevel& c = s->L[l];
-    SteadyLevel& p = s->L[l - 1];
+  if (s->transport) {  // rho k = k rho, rho omega = omega rho with the density of the current state
+    const unsigned blocks = nblk(f.ncell, 256);
     for (int q = 0; q < 2; ++q) {
-      if (!srcs[q]) continue;
-      void* src = q == 0 ? p.f1 : p.f2;
-      void* dst = q == 0 ? c.f1 : c.f2;
-      if (s->prec == PREC_F64)
-        mean4_kernel<double><<<nblk(c.ncell), kST, 0, s->stream>>>(c.n0, c.n1, p.n0, (const double*)src, (double*)dst);
-      else
-        mean4_kernel<float><<<nblk(c.ncell), kST, 0, s->stream>>>(c.n0, c.n1, p.n0, (const float*)src, (float*)dst);
+      void* dst = q == 0 ? s->RK : s->RW;
+      const void* src = q == 0 ? f.f1 : f.f2;
+      if (s->prec == PREC_F64) {
+        aux::copy_kernel<double><<<blocks, 256, 0, s->stream>>>((const double*)src, (double*)dst, f.ncell);
+        aux::density_scale_kernel<double, double><<<blocks, 256, 0, s->stream>>>((double*)dst, (const double*)f.W,
+                                                                                 f.ncell);
+      } else {
+        aux::copy_kernel<float><<<blocks, 256, 0, s->stream>>>((const float*)src, (float*)dst, f.ncell);
+        aux::density_scale_kernel<float, float><<<blocks, 256, 0, s->stream>>>((float*)dst, (const float*)f.W,
+                                                                               f.ncell);
+      }
     }
   }
+  restrict_fields(s);
   GKS_SCK(s, cudaGetLastError());
   GKS_SCK(s, cudaStreamSynchronize(s->stream));
   s->has_turb = true;
+  return GKS_OK;
+}
+
+gks_status gks_steady_set_komega(gks_steady* s, const gks_komega* c) {
+  if (!s || !c) return sfail(s, GKS_EINVAL, "null argument");
+  if (!s->transport) return sfail(s, GKS_EINVAL, "handle created without k-omega transport");
+  s->kw = *c;
+  drop_graphs(s);  // captured cycles hold the old coefficients
+  return GKS_OK;
+}
+
+gks_status gks_steady_get_turbulence(gks_steady* s, void* k_out, void* omega_out, int memspace, int dtype) {
+  if (!s || (!k_out && !omega_out)) return sfail(s, GKS_EINVAL, "null argument");
+  if (!s->transport) return sfail(s, GKS_EINVAL, "handle created without k-omega transport");
+  if (!s->has_turb) return sfail(s, GKS_EINVAL, "turbulence fields not set");
+  if ((dtype != GKS_F64 && dtype != GKS_F32) || (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE))
+    return sfail(s, GKS_EINVAL, "memspace or dtype");
+  SteadyLevel& f = s->L[0];
+  const size_t eb = dtype == GKS_F64 ? 8 : 4, bytes = eb * (size_t)f.ncell;
+  gks_status st = ensure_stage(s, bytes);
+  if (st) return st;
+  void* outs[2] = {k_out, omega_out};
+  for (int q = 0; q < 2; ++q) {
+    if (!outs[q]) continue;
+    void* dst = memspace == GKS_MEM_HOST ? s->staging : outs[q];
+    const void* src = q == 0 ? s->RK : s->RW;
+    const unsigned blocks = nblk(f.ncell, 256);
+    if (s->prec == PREC_F64 && dtype == GKS_F64)
+      aux::density_unscale_kernel<double, double, double><<<blocks, 256, 0, s->stream>>>(
+          (const double*)src, (const double*)f.W, (double*)dst, f.ncell);
+    else if (s->prec == PREC_F64)
+      aux::density_unscale_kernel<double, double, float><<<blocks, 256, 0, s->stream>>>(
+          (const double*)src, (const double*)f.W, (float*)dst, f.ncell);
+    else if (dtype == GKS_F64)
+      aux::density_unscale_kernel<float, float, double><<<blocks, 256, 0, s->stream>>>(
+          (const float*)src, (const float*)f.W, (double*)dst, f.ncell);
+    else
+      aux::density_unscale_kernel<float, float, float><<<blocks, 256, 0, s->stream>>>(
+          (const float*)src, (const float*)f.W, (float*)dst, f.ncell);
+    GKS_SCK(s, cudaGetLastError());
+    if (memspace == GKS_MEM_HOST) {
+      GKS_SCK(s, cudaMemcpyAsync(outs[q], s->staging, bytes, cudaMemcpyDeviceToHost, s->stream));
+      GKS_SCK(s, cudaStreamSynchronize(s->stream));
+    }
+  }
+  GKS_SCK(s, cudaStreamSynchronize(s->stream));
   return GKS_OK;
 }
 

@@ -77,13 +77,15 @@ def load():
     L.gks_steady_set_state.argtypes = [_V, _V, _I, _I, _I]
     L.gks_steady_set_turbulence.argtypes = [_V, _V, _V, _I, _I]
     L.gks_steady_cycles.argtypes = [_V, _I, _D, _D, _PD]
+    L.gks_steady_get_turbulence.argtypes = [_V, _V, _V, _I, _I]
     L.gks_steady_residual.argtypes = [_V, _D, _I, _PD, _PD]
     L.gks_steady_get_state.argtypes = [_V, _V, _I, _I, _I]
     L.gks_steady_destroy.argtypes = [_V]
     L.gks_steady_last_error.argtypes = [_V]
     L.gks_steady_last_error.restype = ctypes.c_char_p
     for name in ("gks_steady_create", "gks_steady_set_state", "gks_steady_set_turbulence", "gks_steady_cycles",
-                 "gks_steady_residual", "gks_steady_get_state", "gks_steady_destroy", "gks_set_nodes"):
+                 "gks_steady_residual", "gks_steady_get_state", "gks_steady_destroy", "gks_set_nodes",
+                 "gks_steady_set_komega", "gks_steady_get_turbulence"):
         getattr(L, name).restype = _I
     L.gks_compute_dt.argtypes = [H, _D, _PD]
     L.gks_step.argtypes = [H, _D, _D, _I, _D]
@@ -96,6 +98,7 @@ def load():
     L.gks_komega_defaults.argtypes = [ctypes.POINTER(KOmega)]
     L.gks_set_komega.argtypes = [H, ctypes.POINTER(KOmega)]
     L.gks_get_turbulence.argtypes = [H, _V, _V, _I, _I]
+    L.gks_steady_set_komega.argtypes = [_V, ctypes.POINTER(KOmega)]
     L.gks_enable_timing.argtypes = [H, _I]
     L.gks_kernel_time.argtypes = [H, _PD, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_destroy.argtypes = [H]
@@ -479,6 +482,16 @@ class SteadySolver:
         b = _f64(f2) if f2 is not None else None
         self._check(load().gks_steady_set_turbulence(self._h, _V(a.ctypes.data), _V(b.ctypes.data) if b is not None
                                                      else None, MEM_HOST, F64))
+
+    def set_komega(self, **coeffs):
+        """Closure coefficients of the steady k-omega transport (keywords of gks_komega)."""
+        self._check(load().gks_steady_set_komega(self._h, ctypes.byref(komega_defaults(**coeffs))))
+
+    def get_turbulence(self):
+        """k and omega of the current state (k-omega transport handles), host float64."""
+        k, om = np.zeros(self.ncell), np.zeros(self.ncell)
+        self._check(load().gks_steady_get_turbulence(self._h, _V(k.ctypes.data), _V(om.ctypes.data), MEM_HOST, F64))
+        return k, om
 
     def cycles(self, ncycles, cfl, cfl_flux=0.5):
         """Run ncycles multigrid cycles; returns the fine residual norm before each."""
