@@ -48,7 +48,7 @@ def parse():
                    choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
                             "corner2d_528x136", "corner2d_2112x544", "steady_corner_528x136",
                             "steady_corner_2112x544", "naca2d_608x160", "naca2d_608x160_transport",
-                            "steady_naca_608x160"])
+                            "steady_naca_608x160", "steady_naca_608x160_transport"])
     p.add_argument("--expand", default=None, choices=["directional", "multid"],
                    help="expansion of the body-fitted and steady workloads (default: directional)")
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
@@ -175,10 +175,18 @@ def make_workload(name, precision):
                          "Mach 2.85 / 24-degree compression corner, body-fitted %dx%d wall-clustered grid, k-omega "
                          "tau_t, 100 cycles from the inflow state (20 at CFL 1, 80 at CFL 4), flux windows CFL 0.5"
                          % (nx, ny))
-    if name in ("naca2d_608x160", "naca2d_608x160_transport", "steady_naca_608x160"):
+    if name in ("naca2d_608x160", "naca2d_608x160_transport", "steady_naca_608x160",
+                "steady_naca_608x160_transport"):
         # the fine NACA 0012 C-grid size of the paper's Table 2: 2 x 112 wake + 384 surface cells, 160 rows
         spec = inputs.naca0012_case(112, 384, 160, mach=0.8, alpha_deg=2.26, Re=9.0e6, dy1=2e-4, ratio=1.05,
                                     R=10.0, x_out=10.0)
+        if name == "steady_naca_608x160_transport":
+            return dict(spec=spec, steady=True, levels=4, precision=precision or "fp32", transport=True,
+                        schedule=[(20, 1.0), (80, 4.0)],
+                        desc="steady solver (local time steps, LU-SGS on cell tiles, 4-level FAS multigrid) with "
+                             "k and omega transported (one diagonal-implicit steady k-omega update per cycle) on a "
+                             "NACA 0012 C-grid 608x160 with a wake cut, M 0.8, incidence 2.26 degrees, Re 9e6, "
+                             "from free-stream k and omega, 100 cycles (20 at CFL 1, 80 at CFL 4)")
         if name.startswith("steady_"):
             return dict(spec=spec, steady=True, levels=4, precision=precision or "fp32",
                         schedule=[(20, 1.0), (80, 4.0)],
@@ -265,12 +273,17 @@ def run_steady(args, wl):
     spec = wl["spec"]
     n = tuple(spec["n"])
     levels = wl["levels"]
+    transport = wl.get("transport", False)
     s = gks.SteadySolver(n, spec["bc"], spec["nodes"], levels=levels, bc_data=spec["bc_prim"], gamma=1.4,
-                         mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega", beta_star=0.09, C_a=0.5,
+                         mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega_transport" if transport
+                         else "komega", beta_star=0.09, C_a=0.5,
                          limiter="vanleer", precision=wl["precision"], lusgs_tile=args.lusgs_tile,
                          wake_cut=spec.get("wake_cut", 0), expand=args.expand or "directional")
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
-    s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
+    f1_dev = torch.tensor(np.ravel(spec["f1"]), dtype=torch.float64, device=dev)
+    f2_dev = torch.tensor(np.ravel(spec["f2"]), dtype=torch.float64, device=dev)
+    if not transport:  # transported fields are set after each set_state
+        s.set_turbulence(f1_dev, f2_dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sched = wl["schedule"]
     ncyc = sum(k for k, _ in sched)
@@ -279,6 +292,8 @@ def run_steady(args, wl):
     def one_step():
         nonlocal hist
         s.set_state(prim_dev, layout="soa_prim")
+        if transport:
+            s.set_turbulence(f1_dev, f2_dev)
         hist = np.concatenate([s.cycles(k, cfl=c, cfl_flux=0.5) for k, c in sched])
 
     for _ in range(args.warmup):
@@ -313,8 +328,12 @@ def run_steady(args, wl):
         out_host = np.zeros(4 * n[0] * n[1])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        f1_host = torch.tensor(np.ravel(spec["f1"]), dtype=torch.float64).pin_memory()
+        f2_host = torch.tensor(np.ravel(spec["f2"]), dtype=torch.float64).pin_memory()
         for _ in range(args.steps):
             s.set_state(prim_host, layout="soa_prim")
+            if transport:
+                s.set_turbulence(f1_host, f2_host)
             for k, c in sched:
                 s.cycles(k, cfl=c, cfl_flux=0.5)
             out_host = s.get_state()
@@ -324,7 +343,8 @@ def run_steady(args, wl):
     faces_cycle = sum(f * e for f, _, e in per_level)
     if not args.no_e2e:
         e2e = {"value": faces_cycle * ncyc * args.steps * world / e2e_s, "unit": "face_flux_evals/s",
-               "h2d_bytes_per_step": int(prim_host.numel() * 8), "d2h_bytes_per_step": int(out_host.size * 8)}
+               "h2d_bytes_per_step": int((prim_host.numel() + (2 * n[0] * n[1] if transport else 0)) * 8),
+               "d2h_bytes_per_step": int(out_host.size * 8)}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -335,6 +355,8 @@ def run_steady(args, wl):
     so_face = sum(gks.face_op_count(2, False, True)[:3])
     per_cell = CELL_OPS + sum(gks.cell_op_count(2)[:3])
     ops_cycle = sum(e * (f * (so_face if l == 0 else fo_face) + c * per_cell) for l, (f, c, e) in enumerate(per_level))
+    if transport:  # the k-omega update of the finest grid
+        ops_cycle += per_level[0][1] * KOMEGA_CELL_OPS[2]
     achieved = ops_cycle * ncyc * args.steps / secs / 1e12
     fp64 = wl["precision"] == "fp64"
     lanes = 2 if fp64 else 128
@@ -372,8 +394,12 @@ def run_steady(args, wl):
         # and LU-SGS, plus (above the coarsest) the residual after smoothing, restriction, coarse
         # residual and forcing; the prolongations and the residual store; per cycles() call the
         # physical-state check
+        # (with k-omega transport: per cycle the two field conversions, their restrictions and the
+        # update; per bench step the six conversions of set_turbulence and their restrictions)
         "gpu_launches": args.steps * (1 + ncyc * (sum(4 + (6 if l + 1 < levels else 0) for l in range(levels))
-                                                  + (levels - 1) + 1) + len(sched)),
+                                                  + (levels - 1) + 1
+                                                  + ((2 + 2 * (levels - 1) + 1) if transport else 0))
+                                      + len(sched) + ((6 + 2 * (levels - 1)) if transport else 0)),
         "clocks": clock_info,
         "e2e": e2e,
     }

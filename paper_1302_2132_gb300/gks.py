@@ -478,6 +478,16 @@ class SteadySolver:
         self.stream.synchronize()
 
     def set_turbulence(self, f1, f2=None):
+        """f1, f2: numpy arrays or torch tensors (host or CUDA, float64), one value per cell."""
+        if _is_torch(f1):
+            import torch
+            assert f1.dtype == torch.float64 and (f2 is None or f2.dtype == torch.float64)
+            if f1.is_cuda:
+                self.stream.wait_stream(torch.cuda.current_stream(f1.device))
+            self._check(load().gks_steady_set_turbulence(self._h, _V(f1.data_ptr()),
+                                                         _V(f2.data_ptr()) if f2 is not None else None,
+                                                         MEM_DEVICE if f1.is_cuda else MEM_HOST, F64))
+            return
         a = _f64(f1)
         b = _f64(f2) if f2 is not None else None
         self._check(load().gks_steady_set_turbulence(self._h, _V(a.ctypes.data), _V(b.ctypes.data) if b is not None
