@@ -135,6 +135,7 @@ def lib():
             L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
             L.orc_step_curv.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I]
             L.orc_compute_dt_curv.argtypes = [P, _PD, _PD, _D, _PD]
+            L.orc_rarefaction_curv.argtypes = [P, _PD, _PD, _PD, _PD, _PD]
             L.orc_step_komega_curv.argtypes = [P, _PD, ctypes.POINTER(KOmega), _PD, _PD, _PD, _D, _I]
             L.orc_steady_residual.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I, _PD, _PD, _I]
             L.orc_lusgs.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD, _I, _I, _PD]
@@ -367,6 +368,16 @@ class Case:
         assert st == 0
         return dt.value
 
+
+    def rarefaction_curv(self, nodes, W, f1=None, f2=None):
+        """eps = (mu / p + tau_t) |div U| per cell on a curvilinear grid (Green-Gauss divergence)."""
+        nodes = self._nodes(nodes)
+        W = self._state(W)
+        eps = np.zeros(self.ncell)
+        st = lib().orc_rarefaction_curv(ctypes.byref(self.P), _ptr(nodes), _ptr(W), _ptr(self._field(f1)),
+                                        _ptr(self._field(f2)), _ptr(eps))
+        assert st == 0, st
+        return eps
 
     def step_komega_curv(self, nodes, W, RK, RW, dt, coeffs=None, nthreads=1):
         """One flow step plus the k-omega transport step on a curvilinear grid; returns (W, RK, RW,

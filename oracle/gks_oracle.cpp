@@ -2133,6 +2133,42 @@ int orc_steady_komega(const orc_problem* P, const double* nodes, const orc_komeg
   return 0;
 }
 
+// Rarefaction diagnostic on a body-fitted grid (Eqs. tautautilde, tautilde with D rho = -rho div U):
+// eps = (mu / p + tau_t) |div U| per cell, div U from Green-Gauss (face values the means of the two
+// cells, ghost cells by the boundary rules).
+int orc_rarefaction_curv(const orc_problem* P, const double* nodes, const double* W, const double* f1,
+                         const double* f2, double* eps) {
+  if (P->dim != 2) return 1;
+  CurvCtx C;
+  const int st = curv_prepare(P, nodes, W, f1, f2, C);
+  if (st) return st;
+  const CurvGeom& g = C.g;
+  const Grid& G = C.G;
+  const int n0 = g.n0, n1 = g.n1;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const long c = (long)j * n0 + i;
+      double w[5];
+      get_cell(G, C.Wp, i, j, 0, w);
+      const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+      const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
+      const long fidx[4] = {(long)j * (n0 + 1) + i, (long)j * (n0 + 1) + i + 1, (long)j * n0 + i,
+                            (long)(j + 1) * n0 + i};
+      double div = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        double wn[5];
+        get_cell(G, C.Wp, nb[q][0], nb[q][1], 0, wn);
+        const double nxq = q < 2 ? g.inx[fidx[q]] : g.jnx[fidx[q]], nyq = q < 2 ? g.iny[fidx[q]] : g.jny[fidx[q]];
+        const double L = q < 2 ? g.iL[fidx[q]] : g.jL[fidx[q]];
+        const double ux = 0.5 * (w[1] / w[0] + wn[1] / wn[0]), uy = 0.5 * (w[2] / w[0] + wn[2] / wn[0]);
+        div += sgn[q] * (ux * nxq + uy * nyq) * L;
+      }
+      div /= g.area[c];
+      eps[c] = (P->mu / pressure(2, P->gamma, w) + C.taut[c]) * std::fabs(div);
+    }
+  return 0;
+}
+
 int orc_steady_residual(const orc_problem* P, const double* nodes, const double* W, const double* f1,
                         const double* f2, double cfl_flux, int first_order, double* dt_cell, double* R, int nthreads) {
   CurvCtx C;

@@ -125,6 +125,10 @@ int orc_step_komega(const orc_problem* P, const orc_komega* c, double* W, double
 /* Status 2 (nothing updated): a cell that is not a convex counter-clockwise quadrilateral. */
 int orc_step_curv(const orc_problem* P, const double* nodes, double* W, const double* f1, const double* f2,
                   double dt, int nthreads);
+/* Rarefaction diagnostic on a curvilinear grid: eps = (mu / p + tau_t) |div U| per cell, div U by
+ * Green-Gauss with face values the means of the two cells. */
+int orc_rarefaction_curv(const orc_problem* P, const double* nodes, const double* W, const double* f1,
+                         const double* f2, double* eps);
 /* CFL step on a curvilinear grid: dt = cfl / max_cells sum_faces (|U.n| + c) L / (2 A). */
 int orc_compute_dt_curv(const orc_problem* P, const double* nodes, const double* W, double cfl, double* dt);
 
