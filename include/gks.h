@@ -138,7 +138,8 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
  * Built for dim 2, both expansions, GKS_RECON_MUSCL2 (GKS_EUNSUPPORTED otherwise), every precision.  May be called before or after gks_set_state; a second call
  * replaces the grid.  GKS_EINVAL for a folded or clockwise cell (the handle's grid is then the
  * rectilinear one again).
- * gks_get_tau_turb works on such grids, gks_get_rarefaction returns GKS_EUNSUPPORTED. */
+ * gks_get_tau_turb and gks_get_rarefaction work on such grids (Green-Gauss gradients and divergence,
+ * face values the means of the two cells). */
 gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
 
 /* Steady-state solver on a body-fitted 2D grid (Section 4: the paper's solver is steady, with local

@@ -1030,11 +1030,10 @@ static gks_status get_diag(gks_handle* h, int what, void* out, int memspace, int
   }
   const StepArgs A = step_args(h, h->step, 0);
   if (h->curv) {
-    if (what != 0) return fail(h, GKS_EUNSUPPORTED, "rarefaction diagnostic on a curvilinear grid");
-    if (h->base.g.turb_model == GKS_TURB_NONE) {
+    if (what == 0 && h->base.g.turb_model == GKS_TURB_NONE) {
       GKS_CK(h, cudaMemsetAsync(dst, 0, bytes, h->stream));
     } else {
-      launch_curv_tau(h->prec, A, h->cg, h->cg.tau, h->stream);
+      launch_curv_tau(h->prec, A, h->cg, h->cg.tau, h->stream, what);
       const unsigned blocks = grid_for(h->ncell, 256);
       if (h->prec == PREC_F64 && dtype == GKS_F64)
         field_kernel<double, double><<<blocks, 256, 0, h->stream>>>((const double*)h->cg.tau, (double*)dst, h->ncell);

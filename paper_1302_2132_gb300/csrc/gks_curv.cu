@@ -254,21 +254,47 @@ __device__ __forceinline__ R tau_gg(const DevGrid& g, const Consts<R>& kc, const
   return (f1 > R(0) && f2 > R(0)) ? g_div(w[0] * nu, p * g_sqrt(R(1) + eta * eta)) : R(0);
 }
 
-// Turbulent relaxation time of every cell (the diagnostic gks_get_tau_turb).
+// Per-cell diagnostics: what = 0 the turbulent relaxation time (gks_get_tau_turb), what = 1 the
+// rarefaction eps = (mu / p + tau_t) |div U| with the Green-Gauss divergence (face values the means of
+// the two cells; gks_get_rarefaction).
 template <int PREC>
 __global__ void __launch_bounds__(kCurvThreads) curv_tau_kernel(const __grid_constant__ StepArgs A,
-                                                                const __grid_constant__ CurvGeom G, void* tau_out) {
+                                                                const __grid_constant__ CurvGeom G, void* out,
+                                                                int what) {
   using R = typename PrecT<PREC>::R;
   const DevGrid& g = A.g;
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const Consts<R> kc = make_consts<R>(g);
-  const int i = (int)(c % g.n[0]), j = (int)(c / g.n[0]);
+  const int n0 = g.n[0];
+  const int i = (int)(c % n0), j = (int)(c / n0);
   R nb[5][4];
   const int di[5] = {-1, 1, 0, 0, 0}, dj[5] = {0, 0, -1, 1, 0};
 #pragma unroll
   for (int q = 0; q < 5; ++q) load_cell<2, PREC>(g, A.Win, kc, i + di[q], j + dj[q], 0, nb[q]);
-  ((R*)tau_out)[c] = tau_gg<R>(g, kc, G, A.f1, A.f2, i, j, [&](int q, int v) { return nb[q][v]; });
+  const R tau_t = g.turb_model == TURB_NONE
+                      ? R(0)
+                      : tau_gg<R>(g, kc, G, A.f1, A.f2, i, j, [&](int q, int v) { return nb[q][v]; });
+  if (what == 0) {
+    ((R*)out)[c] = tau_t;
+    return;
+  }
+  const FaceView<R> fi{(const R*)G.face[0], G.nf[0]}, fj{(const R*)G.face[1], G.nf[1]};
+  const long fa = (long)j * (n0 + 1) + i, fc = (long)j * n0 + i;
+  const long fid[4] = {fa, fa + 1, fc, fc + n0};
+  const R* w = nb[4];
+  R div = R(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const FaceView<R>& fv = q < 2 ? fi : fj;
+    const R sgn = (q & 1) ? R(1) : R(-1);
+    const R ux = R(0.5) * (g_div(w[1], w[0]) + g_div(nb[q][1], nb[q][0]));
+    const R uy = R(0.5) * (g_div(w[2], w[0]) + g_div(nb[q][2], nb[q][0]));
+    div += sgn * (ux * fv(0, fid[q]) + uy * fv(1, fid[q])) * fv(2, fid[q]);
+  }
+  div = g_div(div, (R)G.area[c]);
+  const R p = pressure_of<R>(2, kc.gamma, w);
+  ((R*)out)[c] = (g_div(kc.mu, p) + tau_t) * g_abs(div);
 }
 
 // CFL rate of a cell on the curvilinear grid: sum over its faces of (|U.n| + c) L / (2 A).
@@ -1270,13 +1296,13 @@ void launch_curv_komega(int prec, const KOmegaArgs& K, const CurvGeom& G, cudaSt
     curv_komega_kernel<PREC_F32D><<<kw_tiles(K.g), KwTile::T, 0, s>>>(K, G);
 }
 
-void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s) {
+void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s, int what) {
   if (prec == PREC_F64)
-    curv_tau_kernel<PREC_F64><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out);
+    curv_tau_kernel<PREC_F64><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out, what);
   else if (prec == PREC_F32)
-    curv_tau_kernel<PREC_F32><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out);
+    curv_tau_kernel<PREC_F32><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out, what);
   else
-    curv_tau_kernel<PREC_F32D><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out);
+    curv_tau_kernel<PREC_F32D><<<blocks_for(A.g.ncell), kCurvThreads, 0, s>>>(A, G, out, what);
 }
 
 }  // namespace gks

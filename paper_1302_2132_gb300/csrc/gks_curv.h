@@ -46,7 +46,7 @@ void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int varian
 void curv_tile_shape(int variant, int* x, int* y);
 constexpr int kCurvVariants = 3;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
-void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s);
+void launch_curv_tau(int prec, const StepArgs& A, const CurvGeom& G, void* out, cudaStream_t s, int what = 0);
 // steady solver pieces (FP64 and FP32 state): the residual of A.Win, the local explicit steps
 void launch_curv_residual(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
 void launch_curv_lts(int prec, const StepArgs& A, const CurvGeom& G, void* s_out, cudaStream_t s);

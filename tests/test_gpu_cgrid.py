@@ -132,6 +132,28 @@ def test_full_size_c_grid_steps_and_cycles_match_oracle():
     s.close()
 
 
+def test_diagnostics_on_a_c_grid_match_oracle():
+    """tau_t and the rarefaction diagnostic with the wake cut (Green-Gauss across the cut), FP64."""
+    from paper_1302_2132_gb300 import gks
+    sp = case()
+    s = gks.Solver(2, sp["n"], sp["bc"], dx=sp["dx"], bc_data=sp["bc_prim"], gamma=GAMMA, mu=sp["mu"],
+                   T_wall=sp["T_wall"], turb_model=sp["turb"], C_a=0.5, limiter="vanleer", expand="directional",
+                   precision="fp64", wake_cut=sp["wake_cut"])
+    s.set_nodes(sp["nodes"])
+    prim = np.asarray(sp["prim"], dtype=np.float64).ravel()
+    pts = inputs.cell_points(sp["nodes"])
+    prim = prim.reshape(4, *pts.shape[:2])
+    prim[1] *= 1.0 + 0.2 * np.sin(2.0 * pts[..., 0]) * np.cos(3.0 * pts[..., 1])  # a divergent field
+    prim = prim.ravel()
+    s.set_state(prim, layout="soa_prim")
+    s.set_turbulence(sp["f1"], sp["f2"])
+    c = oracle_of(sp)
+    W = c.prim_to_cons(prim)
+    eo = c.rarefaction_curv(sp["nodes"], W, sp["f1"], sp["f2"])
+    assert np.abs(s.rarefaction() - eo).max() <= 1e-12 * np.abs(eo).max()
+    s.close()
+
+
 def test_a_wake_cut_needs_a_body_fitted_grid():
     from paper_1302_2132_gb300 import gks
     sp = case(nw=8, ns=16, n1=8, turb=0)

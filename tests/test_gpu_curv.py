@@ -132,6 +132,29 @@ def test_uniform_grid_tau_matches_the_rectilinear_solver():
     assert out[0].max() > 0
 
 
+@pytest.mark.parametrize("turb_model", [0, 2, 3])
+def test_rarefaction_on_body_fitted_grids_matches_oracle(turb_model):
+    """The rarefaction diagnostic (Green-Gauss divergence) on a skewed periodic grid and on the
+    corner grid with walls and Dirichlet sides, FP64, against the oracle."""
+    for spec, mu in ((wavy_spec(40, 30, seed=5), 2e-3), (corner_spec(64, 40), None)):
+        mu = spec["mu"] if mu is None else mu
+        s = gpu_solver(spec, turb_model=turb_model, multid=0, mu=mu, C_a=0.5)
+        c = oracle_case(spec, turb_model=turb_model, multid=0, mu=mu, C_a=0.5)
+        s.set_nodes(spec["nodes"])
+        prim = np.asarray(spec["prim"], dtype=np.float64).ravel()
+        s.set_state(prim, layout="soa_prim")
+        f1 = np.asarray(spec["f1"], dtype=np.float64).ravel()
+        f2 = np.asarray(spec["f2"], dtype=np.float64).ravel()
+        if turb_model:
+            s.set_turbulence(f1, f2)
+        eg = s.rarefaction()
+        eo = c.rarefaction_curv(spec["nodes"], c.prim_to_cons(prim), f1 if turb_model else None,
+                                f2 if turb_model else None)
+        assert np.abs(eg - eo).max() <= 1e-12 * np.abs(eo).max()
+        assert np.abs(eo).max() > 0
+        s.close()
+
+
 def test_graph_and_eager_curvilinear_steps_are_bitwise_equal():
     spec = corner_spec(80, 44)
     out = []
