@@ -1387,7 +1387,7 @@ struct CurvCtx {
 
 int curv_prepare(const orc_problem* P, const double* nodes, const double* W, const double* f1, const double* f2,
                  CurvCtx& C) {
-  if (P->dim != 2 || P->recon != ORC_RECON_MUSCL2) return 1;
+  if (P->dim != 2) return 1;
   C.P = P;
   C.g = curv_geometry(P, nodes);
   if (!curv_valid(C.g)) return 2;
@@ -1497,15 +1497,43 @@ void curv_fluxes(const CurvCtx& C, double dt, const std::vector<double>* win, bo
                                   (my - g.pcy[g.pidx(ci[2], cj[2])]) * (my - g.pcy[g.pidx(ci[2], cj[2])]));
       orc_face fc;
       std::memset(&fc, 0, sizeof(fc));
-      for (int v = 0; v < nv; ++v) {
-        const double sl = first_order ? 0.0 : limiter(P->limiter, (S4[1][v] - S4[0][v]) / d01, (S4[2][v] - S4[1][v]) / d12);
-        const double sr = first_order ? 0.0 : limiter(P->limiter, (S4[2][v] - S4[1][v]) / d12, (S4[3][v] - S4[2][v]) / d23);
-        fc.sl[v] = sl;
-        fc.sr[v] = sr;
-        fc.wl[v] = S4[1][v] + dl * sl;
-        fc.wr[v] = S4[2][v] - dr * sr;
-        fc.cl[v] = S4[1][v];
-        fc.cr[v] = S4[2][v];
+      if (P->recon != ORC_RECON_MUSCL2 && !first_order) {
+        // MUSCL-3 / WENO-5 along the grid line in index space on the six rotated cells
+        // (face index) - 3 .. (face index) + 2; the normal slopes are the one-sided differences to
+        // the face values over the centroid-to-face distances
+        double S6[6][4];
+        for (int s6 = 0; s6 < 6; ++s6) {
+          const int ii = d == 0 ? fi - 3 + s6 : fi, jj = d == 0 ? fj : fj - 3 + s6;
+          double w[5];
+          get_cell(G, Wp, ii, jj, 0, w);
+          S6[s6][0] = w[0];
+          S6[s6][1] = w[1] * nxf + w[2] * nyf;
+          S6[s6][2] = -w[1] * nyf + w[2] * nxf;
+          S6[s6][3] = w[3];
+        }
+        const double unused[6] = {1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+        for (int v = 0; v < nv; ++v) {
+          double st[6];
+          for (int s6 = 0; s6 < 6; ++s6) st[s6] = S6[s6][v];
+          recon_face(P->recon, P->limiter, st, unused, fc.wl[v], fc.wr[v]);
+          fc.sl[v] = (fc.wl[v] - S6[2][v]) / dl;
+          fc.sr[v] = (S6[3][v] - fc.wr[v]) / dr;
+          fc.cl[v] = S6[2][v];
+          fc.cr[v] = S6[3][v];
+        }
+      } else {
+        for (int v = 0; v < nv; ++v) {
+          const double sl =
+              first_order ? 0.0 : limiter(P->limiter, (S4[1][v] - S4[0][v]) / d01, (S4[2][v] - S4[1][v]) / d12);
+          const double sr =
+              first_order ? 0.0 : limiter(P->limiter, (S4[2][v] - S4[1][v]) / d12, (S4[3][v] - S4[2][v]) / d23);
+          fc.sl[v] = sl;
+          fc.sr[v] = sr;
+          fc.wl[v] = S4[1][v] + dl * sl;
+          fc.wr[v] = S4[2][v] - dr * sr;
+          fc.cl[v] = S4[1][v];
+          fc.cr[v] = S4[2][v];
+        }
       }
       if (!(fc.wl[0] > 0.0) || !(pressure(2, P->gamma, fc.wl) > 0.0))
         for (int v = 0; v < nv; ++v) {
