@@ -183,7 +183,10 @@ int tiles_for(const gks_handle* h, int variant) {
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
   if (h->curv) {
-    launch_curv_step(h->prec, A, h->cg, variant, h->multid, h->stream);
+    if (h->recon != GKS_RECON_MUSCL2)
+      launch_curv_step_recon(h->prec, h->recon, A, h->cg, variant, h->multid, h->stream);
+    else
+      launch_curv_step(h->prec, A, h->cg, variant, h->multid, h->stream);
     return;
   }
   if (h->recon == GKS_RECON_MUSCL3) {
@@ -393,6 +396,7 @@ std::mutex g_tuned_mutex;
 std::vector<int> tile_candidates(const gks_handle* h) {
   std::vector<int> c;
   if (h->curv) {
+    if (h->recon != GKS_RECON_MUSCL2) return {0, 2};  // the tiles the reconstruction kernels are built for
     for (int v = 0; v < kCurvVariants; ++v) c.push_back(v);
     return c;
   }
@@ -409,7 +413,7 @@ std::vector<int> tile_candidates(const gks_handle* h) {
 }
 
 int n_variants(const gks_handle* h) {
-  if (h->curv) return kCurvVariants;
+  if (h->curv) return h->recon != GKS_RECON_MUSCL2 ? 2 : kCurvVariants;
   if (h->recon != GKS_RECON_MUSCL2) return (int)tile_candidates(h).size();
   if (h->D == 1) return kTileVariants1D;
   if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
@@ -428,7 +432,7 @@ gks_status autotune(gks_handle* h) {
       if (c == v) h->tile_variant = v;
     return GKS_OK;
   }
-  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, h->curv ? 2 : (int)h->multid};
+  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, h->curv ? 2 + 4 * h->recon : (int)h->multid};
   {
     std::lock_guard<std::mutex> lk(g_tuned_mutex);
     auto it = g_tuned.find(key);
@@ -556,6 +560,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     cudaError_t e = D == 1 ? prepare_step_d1() : (D == 2 ? prepare_step_d2() : prepare_step_d3());
     if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
     if (e == cudaSuccess && D == 2) e = prepare_curv();
+    if (e == cudaSuccess && D == 2) e = prepare_curv_recon();
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess) e = prepare_komega();
@@ -1070,7 +1075,6 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
   if (!h || !nodes) return fail(h, GKS_EINVAL, "null argument");
   if (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE) return fail(h, GKS_EINVAL, "memspace");
   if (h->D != 2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids are built in 2D");
-  if (h->recon != GKS_RECON_MUSCL2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids take MUSCL2 reconstruction");
   DeviceGuard dg(h->dev);
   GKS_CK(h, cudaStreamSynchronize(h->stream));
   free_curv(h);

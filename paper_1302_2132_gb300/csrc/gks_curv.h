@@ -43,6 +43,11 @@ cudaError_t curv_metrics(const double* nodes, int n0, int n1, const bool periodi
 // variant 2: 16 x 11, 128 threads).
 cudaError_t prepare_curv();
 void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int variant, bool multid, cudaStream_t s);
+// The same step with MUSCL-3 (recon 1) or WENO-5 (recon 2) along the grid lines: PREC_F64 or PREC_F32,
+// tile variants 0 and 2 (any other variant runs as 2); prepare_curv_recon sets their shared memory.
+cudaError_t prepare_curv_recon();
+void launch_curv_step_recon(int prec, int recon, const StepArgs& A, const CurvGeom& G, int variant, bool multid,
+                            cudaStream_t s);
 void curv_tile_shape(int variant, int* x, int* y);
 constexpr int kCurvVariants = 3;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);
