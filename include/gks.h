@@ -135,7 +135,11 @@ gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace,
  * rectilinear grids, in each face's frame: convection by the face mass flux times L with half-time
  * upwind values along the grid line (the swept length F_rho / (rho L)), normal diffusion over the
  * centroid distance, sources with Green-Gauss gradients, each divergence over the cell area.
- * Built for dim 2, both expansions, GKS_RECON_MUSCL2 (GKS_EUNSUPPORTED otherwise), every precision.  May be called before or after gks_set_state; a second call
+ * With GKS_RECON_MUSCL3 or GKS_RECON_WENO5 the face values come from the index-space formulas on
+ * the four or six rotated cells along the grid line, the normal slopes being the one-sided
+ * differences to the face values over the centroid-to-face distances (tangential slopes as for
+ * MUSCL2).  Built for dim 2 (GKS_EUNSUPPORTED otherwise), both expansions, every reconstruction and
+ * precision the handle allows.  May be called before or after gks_set_state; a second call
  * replaces the grid.  GKS_EINVAL for a folded or clockwise cell (the handle's grid is then the
  * rectilinear one again).
  * gks_get_tau_turb and gks_get_rarefaction work on such grids (Green-Gauss gradients and divergence,
@@ -170,9 +174,10 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
  *     rho k -= R / D, D = A / (cfl s) + sum_faces (max(m_out, 0) + conductance) / rho + A beta omega
  *     (beta* for k, beta0 for omega), then the floors; the flow cycle keeps the fields of the
  *     cycle's start.
- * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), both expansions (the
- * multi-dimensional one on the finest level; coarse levels are first order), MUSCL2, turbulence
- * models NONE, MUT, KEPS, KOMEGA (prescribed fields) and KOMEGA_TRANSPORT.  nodes: host,
+ * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), both expansions and the
+ * three reconstructions (MUSCL2, MUSCL3, WENO5 as for gks_set_nodes) on the finest level (coarse
+ * levels are first order), turbulence models NONE, MUT, KEPS, KOMEGA (prescribed fields) and
+ * KOMEGA_TRANSPORT.  nodes: host,
  * [(n1 + 1)][(n0 + 1)][2] as gks_set_nodes.  Errors: GKS_EUNSUPPORTED for other options, GKS_EINVAL
  * for bad sizes, levels or a folded cell on any level. */
 typedef struct gks_steady gks_steady;

@@ -32,6 +32,7 @@ struct SteadyArgs {
   void* tau;              // out: tau_t per cell
   double* res_acc;        // if set: += sum over cells of (R_rho / A)^2
   int multid;             // multi-dimensional expansion (second-order levels only)
+  int recon;              // GKS_RECON_* of the second-order level (MUSCL-3, WENO-5: launch_curv_residual_recon)
 };
 
 // Metrics from nodes[(n1 + 1)][(n0 + 1)][2] (device, double); *bad (device) is or-ed with 1 if a
@@ -46,6 +47,8 @@ void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int varian
 // The same step with MUSCL-3 (recon 1) or WENO-5 (recon 2) along the grid lines: PREC_F64 or PREC_F32,
 // tile variants 0 and 2 (any other variant runs as 2); prepare_curv_recon sets their shared memory.
 cudaError_t prepare_curv_recon();
+// The steady residual (SteadyArgs, second-order level) with MUSCL-3 or WENO-5.
+void launch_curv_residual_recon(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
 void launch_curv_step_recon(int prec, int recon, const StepArgs& A, const CurvGeom& G, int variant, bool multid,
                             cudaStream_t s);
 void curv_tile_shape(int variant, int* x, int* y);

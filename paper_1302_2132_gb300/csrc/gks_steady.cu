@@ -352,6 +352,7 @@ struct gks_steady {
   int levels = 1;
   int tile = 16;  // LU-SGS tile edge
   int multid = 0;  // multi-dimensional expansion on the finest level
+  int recon = 0;   // GKS_RECON_* on the finest level (coarse levels are first order)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<SteadyLevel> L;
@@ -447,7 +448,11 @@ void residual(gks_steady* s, int l, const void* Win, const void* forcing, double
   SA.tau = lev.G.tau;
   SA.res_acc = acc;
   SA.multid = s->multid;
-  launch_curv_residual(s->prec, A, lev.G, SA, s->stream);
+  SA.recon = l == 0 ? s->recon : GKS_RECON_MUSCL2;
+  if (SA.recon != GKS_RECON_MUSCL2)
+    launch_curv_residual_recon(s->prec, A, lev.G, SA, s->stream);
+  else
+    launch_curv_residual(s->prec, A, lev.G, SA, s->stream);
 }
 
 // Four-cell means of the turbulence fields down the levels.
@@ -601,7 +606,8 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   if (!out) return GKS_EINVAL;
   *out = nullptr;
   if (!grid || !gas || !num || !nodes) return GKS_EINVAL;
-  if (grid->dim != 2 || num->reconstruction != GKS_RECON_MUSCL2) return GKS_EUNSUPPORTED;
+  if (grid->dim != 2) return GKS_EUNSUPPORTED;
+  if (num->reconstruction < GKS_RECON_MUSCL2 || num->reconstruction > GKS_RECON_WENO5) return GKS_EINVAL;
   if (num->precision != GKS_FP64 && num->precision != GKS_FP32) return GKS_EUNSUPPORTED;
   const int model_in = turb ? turb->model : GKS_TURB_NONE;
   if (model_in < GKS_TURB_NONE || model_in > GKS_TURB_KOMEGA_TRANSPORT) return GKS_EUNSUPPORTED;
@@ -629,6 +635,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   s->levels = levels;
   s->tile = lusgs_tile == 32 ? 32 : 16;
   s->multid = num->expand == GKS_EXPAND_MULTID;
+  s->recon = num->reconstruction;
   s->transport = model_in == GKS_TURB_KOMEGA_TRANSPORT;
   gks_komega_defaults(&s->kw);
   auto bad = [&](gks_status st) {
@@ -645,7 +652,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     }
     s->own_stream = true;
   }
-  if (prepare_curv() != cudaSuccess ||
+  if (prepare_curv() != cudaSuccess || prepare_curv_recon() != cudaSuccess ||
       cudaFuncSetAttribute(lusgs_kernel<PREC_F64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)lusgs_smem<double, 32>()) != cudaSuccess ||
       cudaFuncSetAttribute(lusgs_kernel<PREC_F32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -976,9 +983,13 @@ gks_status gks_steady_residual(gks_steady* s, double cfl_flux, int first_order, 
   SA.cfl_flux = cfl_flux;
   SA.first_order = first_order != 0;
   SA.multid = s->multid;
+  SA.recon = first_order ? GKS_RECON_MUSCL2 : s->recon;
   SA.R = f.R;
   SA.tau = f.G.tau;
-  launch_curv_residual(s->prec, A, f.G, SA, s->stream);
+  if (SA.recon != GKS_RECON_MUSCL2)
+    launch_curv_residual_recon(s->prec, A, f.G, SA, s->stream);
+  else
+    launch_curv_residual(s->prec, A, f.G, SA, s->stream);
   GKS_SCK(s, cudaGetLastError());
   // out in double: convert through the staging buffer in single precision
   const long n = f.ncell;

@@ -437,7 +437,7 @@ class SteadySolver:
 
     def __init__(self, n, bc, nodes, levels=4, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model="none",
                  C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", lusgs_tile=16, wake_cut=0,
-                 expand="directional", stream=None):
+                 expand="directional", stream=None, reconstruction="muscl2"):
         import torch
         L = load()
         self.n = (int(n[0]), int(n[1]))
@@ -446,7 +446,7 @@ class SteadySolver:
         dx = [np.ones(self.n[0]), np.ones(self.n[1])]
         g, gas, turb, num, self._keep = _structs(2, self.n, bc, dx, None, None, bc_data, gamma, mu, T_wall, turb_model,
                                                  C_mu, beta_star, C_a, limiter, expand, precision, "timeint",
-                                                 "muscl2", wake_cut)
+                                                 reconstruction, wake_cut)
         nodes = _f64(nodes)
         assert nodes.size == 2 * (self.n[0] + 1) * (self.n[1] + 1)
         self.stream = stream if stream is not None else torch.cuda.Stream()
