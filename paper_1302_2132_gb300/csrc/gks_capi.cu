@@ -181,7 +181,17 @@ int tiles_for(const gks_handle* h, int variant) {
   return (int)n;
 }
 
+// k-omega transport fused into the body-fitted step (MUSCL-2, FP64 or the FP32 float-pair form);
+// other combinations run the step and the transport kernel one after the other.
+bool fused_transport(const gks_handle* h) {
+  return h->curv && h->transport && h->recon == GKS_RECON_MUSCL2 && h->prec != PREC_F32D;
+}
+
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
+  if (fused_transport(h)) {
+    launch_curv_step_transport(h->prec, A, h->cg, variant, h->multid, h->stream);
+    return;
+  }
   if (h->curv) {
     if (h->recon != GKS_RECON_MUSCL2)
       launch_curv_step_recon(h->prec, h->recon, A, h->cg, variant, h->multid, h->stream);
@@ -215,7 +225,7 @@ void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
 // rho omega (into the other buffer pair) with the same dt and the flow step's mass fluxes.
 void launch_step(gks_handle* h, const StepArgs& A) {
   launch_step_variant(h, A, h->tile_variant);
-  if (!h->transport) return;
+  if (!h->transport || fused_transport(h)) return;
   const int cur = A.Win == h->W[0] ? 0 : 1;
   KOmegaArgs K;
   std::memset(&K, 0, sizeof(K));
@@ -266,7 +276,28 @@ StepArgs step_args(const gks_handle* h, long long s, int resid) {
   if (h->transport) {
     A.f1 = h->RK[cur];
     A.f2 = h->RW[cur];
-    for (int d = 0; d < 3; ++d) A.mflux[d] = h->mflux[d];
+    if (fused_transport(h)) {  // the step advances rho k, rho omega itself
+      A.RKout = h->RK[cur ^ 1];
+      A.RWout = h->RW[cur ^ 1];
+      A.kw_alpha = h->kw.alpha;
+      A.kw_beta0 = h->kw.beta0;
+      A.kw_sigma = h->kw.sigma;
+      A.kw_sigma_star = h->kw.sigma_star;
+      A.kw_sigma_do = h->kw.sigma_do;
+      A.kw_C_lim = h->kw.C_lim;
+      A.kw_omega_floor = h->kw.omega_floor;
+      A.kw_falpha = (float)h->kw.alpha;
+      A.kw_fbeta0 = (float)h->kw.beta0;
+      A.kw_fsigma = (float)h->kw.sigma;
+      A.kw_fsigma_star = (float)h->kw.sigma_star;
+      A.kw_fsigma_do = (float)h->kw.sigma_do;
+      A.kw_fC_lim = (float)h->kw.C_lim;
+      A.kw_fomega_floor = (float)h->kw.omega_floor;
+      A.kw_sources = h->kw.sources;
+      A.kw_diffusion = h->kw.diffusion;
+    } else {
+      for (int d = 0; d < 3; ++d) A.mflux[d] = h->mflux[d];
+    }
   }
   return A;
 }
@@ -396,7 +427,8 @@ std::mutex g_tuned_mutex;
 std::vector<int> tile_candidates(const gks_handle* h) {
   std::vector<int> c;
   if (h->curv) {
-    if (h->recon != GKS_RECON_MUSCL2) return {0, 2};  // the tiles the reconstruction kernels are built for
+    // the tiles the reconstruction and fused-transport kernels are built for
+    if (h->recon != GKS_RECON_MUSCL2 || fused_transport(h)) return {0, 2};
     for (int v = 0; v < kCurvVariants; ++v) c.push_back(v);
     return c;
   }
@@ -413,7 +445,7 @@ std::vector<int> tile_candidates(const gks_handle* h) {
 }
 
 int n_variants(const gks_handle* h) {
-  if (h->curv) return h->recon != GKS_RECON_MUSCL2 ? 2 : kCurvVariants;
+  if (h->curv) return (h->recon != GKS_RECON_MUSCL2 || fused_transport(h)) ? 2 : kCurvVariants;
   if (h->recon != GKS_RECON_MUSCL2) return (int)tile_candidates(h).size();
   if (h->D == 1) return kTileVariants1D;
   if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
@@ -432,7 +464,8 @@ gks_status autotune(gks_handle* h) {
       if (c == v) h->tile_variant = v;
     return GKS_OK;
   }
-  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D, h->curv ? 2 + 4 * h->recon : (int)h->multid};
+  const TuneKey key{h->n[0] + 100000 * h->prec, h->n[1] * 4 + h->D,
+                    h->curv ? 2 + 4 * h->recon + 16 * (int)fused_transport(h) : (int)h->multid};
   {
     std::lock_guard<std::mutex> lk(g_tuned_mutex);
     auto it = g_tuned.find(key);
@@ -561,6 +594,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     if (e == cudaSuccess && D == 2) e = prepare_step_d2_variants();
     if (e == cudaSuccess && D == 2) e = prepare_curv();
     if (e == cudaSuccess && D == 2) e = prepare_curv_recon();
+    if (e == cudaSuccess && D == 2) e = prepare_curv_transport();
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess) e = prepare_komega();

@@ -295,86 +295,6 @@ __device__ __forceinline__ void cell_kw(const KOmegaArgs& K, int i, int j, typen
   om = g_div(((const R*)K.RWin)[c], rho);
 }
 
-// Fluxes (rho k, rho omega) through one face, towards increasing index: v*[0..3] the four cells
-// along the grid line, rl, rr the densities of the two cells beside the face, fv the face's mass flux
-// followed by L, 1/d01, 1/d12, 1/d23, d_l, d_r of its record.
-template <class R>
-__device__ __forceinline__ void kw_face(const R* vk, const R* vw, R rl, R rr, const R* fv, R dt, R mu, R sigk, R sigw,
-                                        int limiter_kind, bool diffusion, R* out) {
-  const R fr = fv[0], L = fv[1], i01 = fv[2], i12 = fv[3], i23 = fv[4], dl = fv[5], dr = fv[6];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const R* v = q == 0 ? vk : vw;
-    const R s0 = limiter<R>(limiter_kind, (v[1] - v[0]) * i01, (v[2] - v[1]) * i12);
-    const R s1 = limiter<R>(limiter_kind, (v[2] - v[1]) * i12, (v[3] - v[2]) * i23);
-    const R phiL = v[1] + s0 * (dl - R(0.5) * g_div(fr, rl * L));
-    const R phiR = v[2] - s1 * (dr + R(0.5) * g_div(fr, rr * L));
-    R gq = fr * (fr >= R(0) ? phiL : phiR);
-    if (diffusion) {
-      const R mdl = g_div(rl * vk[1], vw[1]), mdr = g_div(rr * vk[2], vw[2]);
-      const R coef = mu + (q == 0 ? sigk : sigw) * R(0.5) * (mdl + mdr);
-      gq -= dt * coef * (v[2] - v[1]) * i12 * L;
-    }
-    out[q] = gq;
-  }
-}
-
-// Wilcox's production terms of the cell at staged index sc (destruction left to the caller):
-// Sk = P_k, Sw = alpha rho (omega / omega~) X - 2/3 alpha rho omega div U + the cross diffusion, with
-// Green-Gauss gradients from the staged neighbours (face values the means of the two cells);
-// gsx, gsy: the outward n_x L, n_y L of the faces i-1/2, i+1/2, j-1/2, j+1/2.
-template <class R, int SX>
-__device__ __forceinline__ void kw_sources(const R* sk, const R* sw, const R* sr, const R* su, const R* sv, int sc,
-                                           const R* gsx, const R* gsy, R A, R alpha, R beta_star, R sigma_do, R C_lim,
-                                           R& Sk, R& Sw) {
-  const R rho = sr[sc], k0 = sk[sc], w0 = sw[sc];
-  const int nb[4] = {sc - 1, sc + 1, sc - SX, sc + SX};
-  const R uc[2] = {su[sc], sv[sc]};
-  R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const R sx = gsx[q], sy = gsy[q];
-    const R un[2] = {su[nb[q]], sv[nb[q]]};
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const R uf = R(0.5) * (uc[b] + un[b]);
-      gu[0][b] += uf * sx;
-      gu[1][b] += uf * sy;
-    }
-    const R kff = R(0.5) * (k0 + sk[nb[q]]), wff = R(0.5) * (w0 + sw[nb[q]]);
-    gk[0] += kff * sx;
-    gk[1] += kff * sy;
-    gw[0] += wff * sx;
-    gw[1] += wff * sy;
-  }
-#pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    gk[a] /= A;
-    gw[a] /= A;
-#pragma unroll
-    for (int b = 0; b < 2; ++b) gu[a][b] /= A;
-  }
-  const R div = gu[0][0] + gu[1][1];
-  R SS = R(0), SbSb = R(0);
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const R sab = R(0.5) * (gu[a][b] + gu[b][a]);
-      SS += sab * sab;
-      const R sb = sab - (a == b ? div / R(3) : R(0));
-      SbSb += sb * sb;
-    }
-  const R X = R(2) * SS - R(2) / R(3) * div * div;
-  const R wt = fmax(w0, C_lim * g_sqrt(R(2) * SbSb / beta_star));
-  const R muT = rho * k0 / wt;
-  Sk = muT * X - R(2) / R(3) * rho * k0 * div;
-  const R dkdw = gk[0] * gw[0] + gk[1] * gw[1];
-  const R sd = dkdw > R(0) ? sigma_do : R(0);
-  const R CD = sd * rho / w0 * dkdw;
-  Sw = alpha * rho * (w0 / wt) * X - R(2) / R(3) * alpha * rho * w0 * div + CD;
-}
-
 template <int PREC>
 __global__ void __launch_bounds__(KwTile::T) curv_komega_kernel(const __grid_constant__ KOmegaArgs K,
                                                                 const __grid_constant__ CurvGeom G) {

@@ -47,6 +47,11 @@ void launch_curv_step(int prec, const StepArgs& A, const CurvGeom& G, int varian
 // The same step with MUSCL-3 (recon 1) or WENO-5 (recon 2) along the grid lines: PREC_F64 or PREC_F32,
 // tile variants 0 and 2 (any other variant runs as 2); prepare_curv_recon sets their shared memory.
 cudaError_t prepare_curv_recon();
+// The body-fitted MUSCL-2 time step with k-omega transport fused in (A.f1, A.f2: rho k, rho omega in;
+// A.RKout, A.RWout and the kw_* coefficients of StepArgs): PREC_F64 or PREC_F32, tile variants 0 and 2.
+cudaError_t prepare_curv_transport();
+void launch_curv_step_transport(int prec, const StepArgs& A, const CurvGeom& G, int variant, bool multid,
+                                cudaStream_t s);
 // The steady residual (SteadyArgs, second-order level) with MUSCL-3 or WENO-5.
 void launch_curv_residual_recon(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
 void launch_curv_step_recon(int prec, int recon, const StepArgs& A, const CurvGeom& G, int variant, bool multid,

@@ -73,6 +73,87 @@ __device__ __forceinline__ R tau_gg(const DevGrid& g, const Consts<R>& kc, const
   return (f1 > R(0) && f2 > R(0)) ? g_div(w[0] * nu, p * g_sqrt(R(1) + eta * eta)) : R(0);
 }
 
+// ---- k-omega transport pieces (the transport kernels and the fused step) ----------------------
+// Fluxes (rho k, rho omega) through one face, towards increasing index: v*[0..3] the four cells
+// along the grid line, rl, rr the densities of the two cells beside the face, fv the face's mass flux
+// followed by L, 1/d01, 1/d12, 1/d23, d_l, d_r of its record.
+template <class R>
+__device__ __forceinline__ void kw_face(const R* vk, const R* vw, R rl, R rr, const R* fv, R dt, R mu, R sigk, R sigw,
+                                        int limiter_kind, bool diffusion, R* out) {
+  const R fr = fv[0], L = fv[1], i01 = fv[2], i12 = fv[3], i23 = fv[4], dl = fv[5], dr = fv[6];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const R* v = q == 0 ? vk : vw;
+    const R s0 = limiter<R>(limiter_kind, (v[1] - v[0]) * i01, (v[2] - v[1]) * i12);
+    const R s1 = limiter<R>(limiter_kind, (v[2] - v[1]) * i12, (v[3] - v[2]) * i23);
+    const R phiL = v[1] + s0 * (dl - R(0.5) * g_div(fr, rl * L));
+    const R phiR = v[2] - s1 * (dr + R(0.5) * g_div(fr, rr * L));
+    R gq = fr * (fr >= R(0) ? phiL : phiR);
+    if (diffusion) {
+      const R mdl = g_div(rl * vk[1], vw[1]), mdr = g_div(rr * vk[2], vw[2]);
+      const R coef = mu + (q == 0 ? sigk : sigw) * R(0.5) * (mdl + mdr);
+      gq -= dt * coef * (v[2] - v[1]) * i12 * L;
+    }
+    out[q] = gq;
+  }
+}
+
+// Wilcox's production terms of the cell at staged index sc (destruction left to the caller):
+// Sk = P_k, Sw = alpha rho (omega / omega~) X - 2/3 alpha rho omega div U + the cross diffusion, with
+// Green-Gauss gradients from the staged neighbours (face values the means of the two cells);
+// gsx, gsy: the outward n_x L, n_y L of the faces i-1/2, i+1/2, j-1/2, j+1/2.
+template <class R, int SX>
+__device__ __forceinline__ void kw_sources(const R* sk, const R* sw, const R* sr, const R* su, const R* sv, int sc,
+                                           const R* gsx, const R* gsy, R A, R alpha, R beta_star, R sigma_do, R C_lim,
+                                           R& Sk, R& Sw) {
+  const R rho = sr[sc], k0 = sk[sc], w0 = sw[sc];
+  const int nb[4] = {sc - 1, sc + 1, sc - SX, sc + SX};
+  const R uc[2] = {su[sc], sv[sc]};
+  R gu[2][2] = {{R(0), R(0)}, {R(0), R(0)}}, gk[2] = {R(0), R(0)}, gw[2] = {R(0), R(0)};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R sx = gsx[q], sy = gsy[q];
+    const R un[2] = {su[nb[q]], sv[nb[q]]};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const R uf = R(0.5) * (uc[b] + un[b]);
+      gu[0][b] += uf * sx;
+      gu[1][b] += uf * sy;
+    }
+    const R kff = R(0.5) * (k0 + sk[nb[q]]), wff = R(0.5) * (w0 + sw[nb[q]]);
+    gk[0] += kff * sx;
+    gk[1] += kff * sy;
+    gw[0] += wff * sx;
+    gw[1] += wff * sy;
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    gk[a] /= A;
+    gw[a] /= A;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) gu[a][b] /= A;
+  }
+  const R div = gu[0][0] + gu[1][1];
+  R SS = R(0), SbSb = R(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const R sab = R(0.5) * (gu[a][b] + gu[b][a]);
+      SS += sab * sab;
+      const R sb = sab - (a == b ? div / R(3) : R(0));
+      SbSb += sb * sb;
+    }
+  const R X = R(2) * SS - R(2) / R(3) * div * div;
+  const R wt = fmax(w0, C_lim * g_sqrt(R(2) * SbSb / beta_star));
+  const R muT = rho * k0 / wt;
+  Sk = muT * X - R(2) / R(3) * rho * k0 * div;
+  const R dkdw = gk[0] * gw[0] + gk[1] * gw[1];
+  const R sd = dkdw > R(0) ? sigma_do : R(0);
+  const R CD = sd * rho / w0 * dkdw;
+  Sw = alpha * rho * (w0 / wt) * X - R(2) / R(3) * alpha * rho * w0 * div + CD;
+}
+
 // ---- fused tile step ---------------------------------------------------------------------------
 // One CTA advances an X x Y tile of cells: the state of the tile and two halo layers (boundary rules
 // applied) and the geometry records of the tile's faces are staged in shared memory, then the
@@ -92,8 +173,9 @@ struct CurvTileGeom {
   static constexpr int HX = X + 2 * H, HY = Y + 2 * H, NH = HX * HY;
   static constexpr int NFX = (X + 1) * Y, NFY = X * (Y + 1), NF = NFX + NFY;
   static constexpr int TX = X + 2, TY = Y + 2, NT = TX * TY;  // tile and first ring (tau)
-  template <class R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * (4 * (size_t)NH + 8 * (size_t)NF + 4 * (size_t)NF + NT) + sizeof(float) * 4 * X * Y;
+  template <class R, bool TR = false> static constexpr size_t smem_bytes() {
+    return sizeof(R) * (4 * (size_t)NH + 8 * (size_t)NF + 4 * (size_t)NF + NT + (TR ? 4 * (size_t)NH + 2 * (size_t)NF : 0)) +
+           sizeof(float) * 4 * X * Y;
   }
 };
 
@@ -106,7 +188,11 @@ struct CurvTileGeom {
 // one-sided differences to the face values over the centroid-to-face distances).
 __host__ __device__ constexpr int halo_for(int rc) { return rc == 2 ? 3 : 2; }
 
-template <int PREC, int V, int MODE, bool MD, int RC = 0>
+// TR (MODE 0): k-omega transport fused into the step: f1, f2 are rho k, rho omega; k, omega, u, v of
+// the tile and its halo are staged, each face also evaluates the transport fluxes of rho k and
+// rho omega with its mass flux, and each cell's update advances them (the transport kernel's
+// arithmetic) into A.RKout, A.RWout.
+template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false>
 __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / CurvTile<V>::T)
     curv_step_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CurvGeom G,
                      const __grid_constant__ SteadyArgs SA) {
@@ -121,6 +207,13 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   R* Fs = Gs + 8 * NF;     // [4][NF] face fluxes times length
   R* Ts = Fs + 4 * NF;     // [TY][TX] tau_t of the tile and its first ring
   float* Lo = (float*)(Ts + NT);  // [4][X * Y] low words of the tile's state (float pair form)
+  // fused transport: k, omega, u, v of the tile and its halo, face fluxes of rho k and rho omega
+  R* Ks = (R*)(Lo + 4 * X * Y);
+  R* Os = Ks + (TR ? NH : 0);
+  R* Us = Os + (TR ? NH : 0);
+  R* Vs = Us + (TR ? NH : 0);
+  R* Gk = Vs + (TR ? NH : 0);
+  R* Gw = Gk + (TR ? NF : 0);
   __shared__ double red[kMaxWarps];
   __shared__ double s_dt;
   const DevGrid& g = A.g;
@@ -208,11 +301,27 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         ((S*)A.Wout)[(long)v * g.ncell + c] = ((const S*)A.Win)[(long)v * g.ncell + c];
         if (PREC == PREC_F32) A.Wout_lo[(long)v * g.ncell + c] = A.Win_lo[(long)v * g.ncell + c];
       }
+      if (TR) {
+        ((R*)A.RKout)[c] = ((const R*)A.f1)[c];
+        ((R*)A.RWout)[c] = ((const R*)A.f2)[c];
+      }
     }
     return;
   }
   const R dt = (R)dt_d;
 
+  if (TR) {  // k, omega of each cell's source cell (rho k / rho there), velocities by the ghost rules
+    for (int l = tid; l < NH; l += T) {
+      const int gi = ox + l % HX - H, gj = oy + l / HX - H;
+      const long sc = field_cell(g, 2, gi, gj, 0);
+      const R rho_s = (R)((const S*)A.Win)[sc];
+      Ks[l] = g_div(((const R*)A.f1)[sc], rho_s);
+      Os[l] = g_div(((const R*)A.f2)[sc], rho_s);
+      Us[l] = g_div(Ws[NH + l], Ws[l]);
+      Vs[l] = g_div(Ws[2 * NH + l], Ws[l]);
+    }
+    if (g.turb_model == TURB_NONE) __syncthreads();  // else the tau phase's barrier follows
+  }
   // ---- tau_t of the tile and its first ring (corners unused) ---------------------------------
   if (g.turb_model != TURB_NONE) {
     for (int l = tid; l < NT; l += T) {
@@ -385,6 +494,21 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;
       Fs[2 * NF + l] = (F[1] * ny + F[2] * nx) * L_;
       Fs[3 * NF + l] = F[3] * L_;
+      if (TR) {
+        R vk[4], vw[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          vk[t] = Ks[base + t * stride];
+          vw[t] = Os[base + t * stride];
+        }
+        const bool kf = sizeof(R) == sizeof(float);
+        const R sigk = kf ? (R)A.kw_fsigma_star : (R)A.kw_sigma_star, sigw = kf ? (R)A.kw_fsigma : (R)A.kw_sigma;
+        const R fvr[7] = {Fs[l], L, i01, i12, i23, dl, dr};
+        R out[2];
+        kw_face<R>(vk, vw, S4[1][0], S4[2][0], fvr, dt, kc.mu, sigk, sigw, g.limiter, A.kw_diffusion, out);
+        Gk[l] = out[0];
+        Gw[l] = out[1];
+      }
       if (A.mflux[0]) {  // the face's mass flux times L (k-omega transport): time-integrated, or the
                          // rate over the window in the residual mode
         const long gfm = a == 0 ? (long)(oy + lj) * (n0 + 1) + ox + li : (long)(oy + lj) * n0 + ox + li;
@@ -480,6 +604,38 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       if (A.resid) racc[8 + v] += wd * G.area[c];
     }
     if (!physical<2, R>(kc.gamma, wn)) bad = 1u;
+    if (TR) {  // rho k, rho omega (the transport kernel's arithmetic)
+      const bool kf = sizeof(R) == sizeof(float);
+      const R alpha = kf ? (R)A.kw_falpha : (R)A.kw_alpha, beta0 = kf ? (R)A.kw_fbeta0 : (R)A.kw_beta0;
+      const R sigma_do = kf ? (R)A.kw_fsigma_do : (R)A.kw_sigma_do, C_lim = kf ? (R)A.kw_fC_lim : (R)A.kw_C_lim;
+      const R omega_floor = kf ? (R)A.kw_fomega_floor : (R)A.kw_omega_floor;
+      const R Ac = (R)G.area[c];
+      const R rk0 = ((const R*)A.f1)[c], rw0 = ((const R*)A.f2)[c];
+      R ak = rk0 - (Gk[fa + 1] - Gk[fa] + Gk[fc + X] - Gk[fc]) / Ac;
+      R aw = rw0 - (Gw[fa + 1] - Gw[fa] + Gw[fc + X] - Gw[fc]) / Ac;
+      R rate_k = R(0), rate_w = R(0);
+      if (A.kw_sources) {
+        const int fq[4] = {fa, fa + 1, fc, fc + X};
+        R gsx[4], gsy[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const R sgn = (q & 1) ? R(1) : R(-1);
+          gsx[q] = sgn * Gs[fq[q]] * Gs[2 * NF + fq[q]];
+          gsy[q] = sgn * Gs[NF + fq[q]] * Gs[2 * NF + fq[q]];
+        }
+        R Sk, Sw;
+        kw_sources<R, HX>(Ks, Os, Ws, Us, Vs, hidx, gsx, gsy, Ac, alpha, kc.beta_star, sigma_do, C_lim, Sk, Sw);
+        const R w0 = Os[hidx];
+        ak += dt * Sk;
+        aw += dt * Sw;
+        rate_k = kc.beta_star * w0;
+        rate_w = beta0 * w0;
+      }
+      ak /= R(1) + dt * rate_k;
+      aw /= R(1) + dt * rate_w;
+      ((R*)A.RKout)[c] = fmax(ak, R(0));
+      ((R*)A.RWout)[c] = fmax(aw, wn[0] * omega_floor);
+    }
     // CFL rate: sum over the four faces of (|U.n| + c) L, over 2 A
     const R ir = g_rcp(wn[0]);
     const R u = wn[1] * ir, vv = wn[2] * ir;
@@ -505,19 +661,20 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   }
 }
 
-template <int PREC, int V, int MODE = 0, bool MD = false, int RC = 0>
+template <int PREC, int V, int MODE = 0, bool MD = false, int RC = 0, bool TR = false>
 void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const SteadyArgs& SA = SteadyArgs{}) {
   using TG = CurvTileGeom<V, halo_for(RC)>;
   const int nt = ((A.g.n[0] + TG::X - 1) / TG::X) * ((A.g.n[1] + TG::Y - 1) / TG::Y);
-  curv_step_kernel<PREC, V, MODE, MD, RC>
-      <<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R>(), s>>>(A, G, SA);
+  curv_step_kernel<PREC, V, MODE, MD, RC, TR>
+      <<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R, TR>(), s>>>(A, G, SA);
 }
 
-template <int PREC, int V, int MODE, bool MD, int RC = 0>
+template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false>
 cudaError_t prepare_one() {
   using TG = CurvTileGeom<V, halo_for(RC)>;
-  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE, MD, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)TG::template smem_bytes<typename PrecT<PREC>::R>());
+  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE, MD, RC, TR>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TG::template smem_bytes<typename PrecT<PREC>::R, TR>());
 }
 
 template <int PREC, int V, int MODE = 0>

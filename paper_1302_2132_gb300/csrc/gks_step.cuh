@@ -150,6 +150,13 @@ struct StepArgs {
   int slot;    // rate slot read by this step (step index mod 3)
   int tslot;   // time slot read by this step (step index mod 2)
   int resid;   // accumulate residual norms in this step
+  // k-omega transport fused into the body-fitted step (f1, f2 are then rho k, rho omega): outputs
+  // and the closure coefficients (double, and float for the single-precision kernels)
+  void* RKout;
+  void* RWout;
+  double kw_alpha, kw_beta0, kw_sigma, kw_sigma_star, kw_sigma_do, kw_C_lim, kw_omega_floor;
+  float kw_falpha, kw_fbeta0, kw_fsigma, kw_fsigma_star, kw_fsigma_do, kw_fC_lim, kw_fomega_floor;
+  int kw_sources, kw_diffusion;
 };
 
 // Arguments of the k-omega transport step that follows a flow step (closure coefficients in

@@ -35,17 +35,18 @@ def cgrid():
                 om=om.ravel(), mu=sp["mu"], T_wall=sp["T_wall"], wake_cut=sp["wake_cut"], C_a=0.5)
 
 
-def run_both(sp, nsteps, precision="fp64", expand="directional", cfl=0.5):
+def run_both(sp, nsteps, precision="fp64", expand="directional", cfl=0.5, recon="muscl2"):
     from paper_1302_2132_gb300 import gks
     n0, n1 = sp["n"]
     dx = [np.full(n0, 1.0 / n0), np.full(n1, 1.0 / n1)]
     s = gks.Solver(2, sp["n"], sp["bc"], dx=dx, bc_data=sp["bc_prim"], gamma=GAMMA, mu=sp["mu"], T_wall=sp["T_wall"],
                    turb_model=TRANSPORT, C_a=sp["C_a"], limiter="vanleer", expand=expand, precision=precision,
-                   wake_cut=sp["wake_cut"])
+                   wake_cut=sp["wake_cut"], reconstruction=recon)
     s.set_nodes(sp["nodes"])
     c = oracle.Case(2, sp["n"], dx, sp["bc"], gamma=GAMMA, mu=sp["mu"], T_wall=sp["T_wall"],
                     turb_model=oracle.TURB_KOMEGA, multid=int(expand == "multid"), C_a=sp["C_a"],
-                    limiter=oracle.LIM_VANLEER, bc_prim=sp["bc_prim"], wake_cut=sp["wake_cut"])
+                    limiter=oracle.LIM_VANLEER, bc_prim=sp["bc_prim"], wake_cut=sp["wake_cut"],
+                    recon={"muscl2": 0, "muscl3": 1, "weno5": 2}[recon])
     prim = np.asarray(sp["prim"], dtype=np.float64).ravel()
     s.set_state(prim, layout="soa_prim")
     s.set_turbulence(sp["k"], sp["om"])
@@ -109,3 +110,35 @@ def test_full_size_c_grid_transport_matches_oracle():
     Wg, kg, wg, Wo, ko, wo = run_both(sp, 10, precision="fp32")
     l1 = lambda a, b: np.abs(a - b).sum() / np.abs(b).sum()
     assert l1(Wg[:nc], Wo[:nc]) < 1e-5 and l1(kg, ko) < 1e-5 and l1(wg, wo) < 1e-5
+
+
+@pytest.mark.parametrize("recon", ["muscl3", "weno5"])
+def test_transport_with_higher_order_flow_matches_oracle(recon):
+    """The step and transport kernels one after the other (the transport is fused into the MUSCL-2
+    step only): WENO-5 / MUSCL-3 flow with transported k, omega on the C-grid, FP64."""
+    sp = cgrid()
+    Wg, kg, wg, Wo, ko, wo = run_both(sp, 3, recon=recon)
+    nc = ko.size
+    for v in range(4):
+        assert relmax(Wg[v * nc:(v + 1) * nc], Wo[v * nc:(v + 1) * nc]) < 1e-12
+    assert relmax(kg, ko) < 1e-12 and relmax(wg, wo) < 1e-12
+
+
+def test_transport_with_double_state_close_to_oracle():
+    """FP32 flux with an IEEE double state (separate transport kernel) on a skewed grid."""
+    sp = wavy(64, 48, seed=23)
+    Wg, kg, wg, Wo, ko, wo = run_both(sp, 20, precision="fp32_acc64")
+    l1 = lambda a, b: np.abs(a - b).sum() / np.abs(b).sum()
+    assert l1(Wg[:ko.size], Wo[:ko.size]) < 1e-5
+    assert l1(kg, ko) < 1e-5 and l1(wg, wo) < 1e-5
+
+
+@pytest.mark.parametrize("variant", ["0", "2"])
+def test_fused_transport_tile_shapes_match_oracle(monkeypatch, variant):
+    monkeypatch.setenv("GKS_TILE_VARIANT", variant)
+    sp = corner(70, 37)
+    Wg, kg, wg, Wo, ko, wo = run_both(sp, 3, expand="multid")
+    nc = ko.size
+    for v in range(4):
+        assert relmax(Wg[v * nc:(v + 1) * nc], Wo[v * nc:(v + 1) * nc]) < 1e-12
+    assert relmax(kg, ko) < 1e-12 and relmax(wg, wo) < 1e-12
