@@ -25,15 +25,17 @@ def cgrid(nw=16, ns=64, n1=24, Re=2e4, **kw):
     return sp
 
 
-def both(sp, levels, precision="fp64", expand="directional"):
+def both(sp, levels, precision="fp64", expand="directional", recon="muscl2"):
     from paper_1302_2132_gb300 import gks
     n0, n1 = sp["n"]
     s = gks.SteadySolver(sp["n"], sp["bc"], sp["nodes"], levels=levels, bc_data=sp["bc_prim"], gamma=GAMMA,
                          mu=sp["mu"], T_wall=sp["T_wall"], turb_model="komega_transport", C_a=0.5, limiter="vanleer",
-                         precision=precision, lusgs_tile=16, wake_cut=sp["wake_cut"], expand=expand)
+                         precision=precision, lusgs_tile=16, wake_cut=sp["wake_cut"], expand=expand,
+                         reconstruction=recon)
     c = oracle.Case(2, sp["n"], [np.ones(n0), np.ones(n1)], sp["bc"], gamma=GAMMA, mu=sp["mu"], T_wall=sp["T_wall"],
                     turb_model=oracle.TURB_KOMEGA, multid=int(expand == "multid"), C_a=0.5,
-                    limiter=oracle.LIM_VANLEER, bc_prim=sp["bc_prim"], wake_cut=sp["wake_cut"])
+                    limiter=oracle.LIM_VANLEER, bc_prim=sp["bc_prim"], wake_cut=sp["wake_cut"],
+                    recon={"muscl2": 0, "muscl3": 1, "weno5": 2}[recon])
     W = c.prim_to_cons(np.asarray(sp["prim"], dtype=np.float64).ravel())
     s.set_state(W)
     s.set_turbulence(sp["k"], sp["om"])
@@ -57,11 +59,12 @@ def rel_per_var(a, b, nv=4):
     return np.array([np.abs(a[v] - b[v]).max() / np.abs(b[v]).max() for v in range(nv)])
 
 
-@pytest.mark.parametrize("name,expand", [("corner", "directional"), ("cgrid", "directional"), ("cgrid", "multid")])
-def test_fp64_cycles_with_transport_match_oracle(name, expand):
+@pytest.mark.parametrize("name,expand,recon", [("corner", "directional", "muscl2"), ("cgrid", "directional", "muscl2"),
+                                               ("cgrid", "multid", "muscl2"), ("cgrid", "multid", "weno5")])
+def test_fp64_cycles_with_transport_match_oracle(name, expand, recon):
     sp = corner(64, 32) if name == "corner" else cgrid()
     levels = 3
-    s, c, W = both(sp, levels, expand=expand)
+    s, c, W = both(sp, levels, expand=expand, recon=recon)
     cfls = [1.0, 1.0, 3.0]
     res_g = np.concatenate([s.cycles(2, cfl=1.0), s.cycles(1, cfl=3.0)])
     Wo, ko, wo, res_o = oracle_cycles(c, sp, W, levels, cfls)
