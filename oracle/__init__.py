@@ -15,6 +15,17 @@ Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
   k-omega transport (Wilcox 2006 reading)                   -- pinned (homogeneous decay against the
       closed-form ODE solution, uniform-shear production and its limiter, exact discrete diffusion of
       a Fourier mode, advection by a uniform stream, conservation on periodic grids)
+  higher-order reconstructions (MUSCL-3, WENO-5)            -- pinned (convergence orders, exact
+      quadratics, Sod stability, smooth-wave accuracy)
+  body-fitted step, both expansions, C-grid wake cut        -- pinned (equal to the rectilinear step
+      on uniform and wall-clustered grids, free stream, rotation, conservation, second-order
+      convergence, the cut against a rectilinear strip, symmetry)
+  body-fitted MUSCL-3 / WENO-5, rarefaction, transport      -- pinned (rectilinear equivalence, free
+      stream, rotation; exact divergence of a linear field; conservation and exact decay)
+  steady residual, LU-SGS, multigrid cycle                  -- pinned (time-accurate equivalence of
+      the residual, dense solve of the LU-SGS factors, convergence to one steady state)
+  steady k-omega update                                     -- pinned (point-implicit closed form at
+      rest, free stream, first-order consistency with the time-accurate transport, bounded iteration)
 """
 import ctypes
 import os

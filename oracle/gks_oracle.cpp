@@ -39,8 +39,17 @@
  *     mean of the two cells) and a ghost cell the value of its source cell.  The multi-dimensional
  *     expansion takes tangential slopes in the face frame: limited differences along the transverse
  *     grid line, each over the centroid step projected on the face tangent.
+ *     MUSCL-3 and WENO-5 on such grids reconstruct the rotated states along the grid line in index
+ *     space; their normal slopes are the one-sided differences to the face values over the
+ *     centroid-to-face distances.  C-grids: the first and last wake_cut cells of the j-lo side see
+ *     the cells across the wake cut as their ghosts.
+ *   - k-omega transport (Wilcox 2006; the paper cites the model without its equations): after each
+ *     flow step with the same dt, convection by the face mass fluxes with half-time upwind values,
+ *     normal diffusion with the mean coefficient of the two cells, sources from central (Green-Gauss
+ *     on body-fitted grids) gradients, point-implicit destruction.
  *   - Steady-state solver (Section 4 names local time stepping, LU-SGS after Yoon and Jameson and
- *     4-level multigrid without formulas): see the block before curv_lts.
+ *     4-level multigrid without formulas): see the block before curv_lts; with k-omega transport one
+ *     diagonal-implicit steady k-omega step per cycle (orc_steady_komega).
  */
 #include "gks_oracle.h"
 
