@@ -455,12 +455,13 @@ void residual(gks_steady* s, int l, const void* Win, const void* forcing, double
     launch_curv_residual(s->prec, A, lev.G, SA, s->stream);
 }
 
-// Four-cell means of the turbulence fields down the levels.
+// Four-cell means of the turbulence fields down the levels (f1 only for a mu_t field).
 void restrict_fields(gks_steady* s) {
+  const int nq = s->L[0].g.turb_model == GKS_TURB_MUT ? 1 : 2;
   for (int l = 1; l < s->levels; ++l) {
     SteadyLevel& c = s->L[l];
     SteadyLevel& p = s->L[l - 1];
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < nq; ++q) {
       const void* src = q == 0 ? p.f1 : p.f2;
       void* dst = q == 0 ? c.f1 : c.f2;
       if (s->prec == PREC_F64)
