@@ -247,6 +247,10 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
 #pragma unroll
     for (int q = 0; q < 8; ++q) cp_async<sizeof(R)>(&Gs[q * NF + l], &src[(long)q * nf + gf]);
   }
+  // everything below may read what the previous kernel in the stream wrote: with a programmatic
+  // (early) launch of this kernel, wait here for that kernel's completion; the face records
+  // above are the grid's static geometry
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (MODE == 1) {
     if (tid == 0) s_dt = 1.0;
   } else if (tid == 0) {
@@ -544,6 +548,8 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
     return;
   }
 
+  // the next step may start its launch (it waits for this kernel's completion before its reads)
+  if (MODE == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // ---- update, next CFL rate, physical check, residual norms ---------------------------------
   R rmax = R(0);
   unsigned bad = 0u;
@@ -665,8 +671,33 @@ template <int PREC, int V, int MODE = 0, bool MD = false, int RC = 0, bool TR = 
 void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const SteadyArgs& SA = SteadyArgs{}) {
   using TG = CurvTileGeom<V, halo_for(RC)>;
   const int nt = ((A.g.n[0] + TG::X - 1) / TG::X) * ((A.g.n[1] + TG::Y - 1) / TG::Y);
-  curv_step_kernel<PREC, V, MODE, MD, RC, TR>
-      <<<nt, TG::T, TG::template smem_bytes<typename PrecT<PREC>::R, TR>(), s>>>(A, G, SA);
+  const size_t smem = TG::template smem_bytes<typename PrecT<PREC>::R, TR>();
+  // time steps follow one another: on a grid of one wave of tiles or less a programmatic launch
+  // lets a step's prologue (the static face records) overlap the end of the previous step; larger
+  // grids (and the steady residual) launch plainly
+  static int resident = 0;  // CTAs of this instantiation that fit on the GPU at once
+  if (MODE == 0 && resident == 0) {
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, curv_step_kernel<PREC, V, MODE, MD, RC, TR>, TG::T, smem);
+    resident = per_sm * nsm > 0 ? per_sm * nsm : -1;
+  }
+  if (MODE == 1 || nt > resident) {
+    curv_step_kernel<PREC, V, MODE, MD, RC, TR><<<nt, TG::T, smem, s>>>(A, G, SA);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nt);
+  cfg.blockDim = dim3((unsigned)TG::T);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, curv_step_kernel<PREC, V, MODE, MD, RC, TR>, A, G, SA);
 }
 
 template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false>
