@@ -19,7 +19,8 @@ struct FaceView {
 
 // Turbulent relaxation time of interior cell (gi, gj) from Green-Gauss gradients; st(q, v) gives
 // the state of the cell (q = 4) and of its neighbours i-1, i+1, j-1, j+1 (q = 0..3).
-template <class R, class StateOf>
+// CONS = false: a caller whose fields are never rho k, rho omega (g.turb_cons unset) skips that test.
+template <class R, bool CONS = true, class StateOf>
 __device__ __forceinline__ R tau_gg(const DevGrid& g, const Consts<R>& kc, const CurvGeom& G, const void* f1p,
                                     const void* f2p, int gi, int gj, StateOf st) {
   const int n0 = g.n[0];
@@ -29,10 +30,10 @@ __device__ __forceinline__ R tau_gg(const DevGrid& g, const Consts<R>& kc, const
   for (int v = 0; v < 4; ++v) w[v] = st(4, v);
   const R p = pressure_of<R>(2, kc.gamma, w);
   R f1 = ((const R*)f1p)[c];
-  if (g.turb_cons) f1 = g_div(f1, w[0]);  // rho k -> k (k-omega transport)
+  if (CONS && g.turb_cons) f1 = g_div(f1, w[0]);  // rho k -> k (k-omega transport)
   if (g.turb_model == TURB_MUT) return g_div(f1, p);
   R f2 = ((const R*)f2p)[c];
-  if (g.turb_cons) f2 = g_div(f2, w[0]);
+  if (CONS && g.turb_cons) f2 = g_div(f2, w[0]);
   const FaceView<R> fi{(const R*)G.face[0], G.nf[0]}, fj{(const R*)G.face[1], G.nf[1]};
   const long fa = (long)gj * (n0 + 1) + gi, fc = (long)gj * n0 + gi;
   const long fid[4] = {fa, fa + 1, fc, fc + n0};
@@ -200,6 +201,10 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   using S = typename PrecT<PREC>::S;
   using TG = CurvTileGeom<V, halo_for(RC)>;
   constexpr int X = TG::X, Y = TG::Y, T = TG::T, H = TG::H, HX = TG::HX, NH = TG::NH;
+  // k-omega transport runs through this instantiation's fields and mass fluxes unless it is fused
+  // (TR): the MUSCL-2 time step in FP64 or the FP32 float pair carries it fused, or has none
+  constexpr bool SEPARATE_KW = MODE == 1 || RC != 0 || PREC == PREC_F32D;
+  constexpr bool CONS = TR || SEPARATE_KW;
   constexpr int NFX = TG::NFX, NF = TG::NF, TX = TG::TX, NT = TG::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* Ws = (R*)smem_raw;    // [4][NH] state of the tile and its halo
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
       if (gi >= 0 && gi < n0 && gj >= 0 && gj < n1) {
         const int h0 = (tj + H) * HX + (ti + H);
         const int off[5] = {-1, 1, -HX, HX, 0};
-        t = tau_gg<R>(g, kc, G, A.f1, A.f2, gi, gj, [&](int q, int v) { return Ws[v * NH + h0 + off[q]]; });
+        t = tau_gg<R, CONS>(g, kc, G, A.f1, A.f2, gi, gj, [&](int q, int v) { return Ws[v * NH + h0 + off[q]]; });
       } else {  // a ghost cell takes its source cell's value
         const long sc = field_cell(g, 2, gi, gj, 0);
         const int si = (int)(sc % n0), sj = (int)(sc / n0);
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         const int di[5] = {-1, 1, 0, 0, 0}, dj[5] = {0, 0, -1, 1, 0};
 #pragma unroll
         for (int q = 0; q < 5; ++q) load_cell<2, PREC>(g, A.Win, kc, si + di[q], sj + dj[q], 0, nb[q]);
-        t = tau_gg<R>(g, kc, G, A.f1, A.f2, si, sj, [&](int q, int v) { return nb[q][v]; });
+        t = tau_gg<R, CONS>(g, kc, G, A.f1, A.f2, si, sj, [&](int q, int v) { return nb[q][v]; });
       }
       Ts[l] = t;
       if (MODE == 1 && ti >= 0 && ti < X && tj >= 0 && tj < Y && gi < n0 && gj < n1)
@@ -513,8 +518,8 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         Gk[l] = out[0];
         Gw[l] = out[1];
       }
-      if (A.mflux[0]) {  // the face's mass flux times L (k-omega transport): time-integrated, or the
-                         // rate over the window in the residual mode
+      if (SEPARATE_KW && A.mflux[0]) {  // the face's mass flux times L for a separate transport step:
+                                        // time-integrated, or the rate over the residual's window
         const long gfm = a == 0 ? (long)(oy + lj) * (n0 + 1) + ox + li : (long)(oy + lj) * n0 + ox + li;
         ((R*)A.mflux[a])[gfm] = Fs[l];
       }
