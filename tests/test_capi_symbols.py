@@ -46,3 +46,26 @@ def test_face_record_length():
     build.build()
     gks.load()
     assert [gks.face_record_len(d) for d in (1, 2, 3)] == [21, 35, 53]
+
+
+def test_null_handles_are_rejected_without_touching_the_device():
+    """Entry points of the steady solver, the k-omega transport and the body-fitted grids return
+    GKS_EINVAL for null handles or arguments before any CUDA call (so this runs without a GPU)."""
+    from paper_1302_2132_gb300 import build
+    L = ctypes.CDLL(build.build())
+    EINVAL = 1
+    V = ctypes.c_void_p
+    L.gks_steady_set_komega.argtypes = [V, V]
+    L.gks_steady_get_turbulence.argtypes = [V, V, V, ctypes.c_int, ctypes.c_int]
+    L.gks_steady_cycles.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, V]
+    L.gks_steady_residual.argtypes = [V, ctypes.c_double, ctypes.c_int, V, V]
+    L.gks_set_nodes.argtypes = [V, V, ctypes.c_int]
+    L.gks_get_turbulence.argtypes = [V, V, V, ctypes.c_int, ctypes.c_int]
+    L.gks_komega_defaults.argtypes = [V]
+    assert L.gks_steady_set_komega(None, None) == EINVAL
+    assert L.gks_steady_get_turbulence(None, None, None, 0, 0) == EINVAL
+    assert L.gks_steady_cycles(None, 1, 1.0, 0.5, None) == EINVAL
+    assert L.gks_steady_residual(None, 0.5, 0, None, None) == EINVAL
+    assert L.gks_set_nodes(None, None, 0) == EINVAL
+    assert L.gks_get_turbulence(None, None, None, 0, 0) == EINVAL
+    assert L.gks_komega_defaults(None) == EINVAL
