@@ -116,3 +116,64 @@ def test_multigrid_cycles_run_on_a_c_grid():
         assert st == 0
         hist.append(res)
     assert hist[-1] < 0.2 * max(hist)
+
+
+def kw_profile(y):
+    """k and omega rising through the cut (y = 0), so that their limited slopes there are not zero."""
+    return 0.01 * (1.0 + 0.4 * np.tanh(y / 0.4)), 20.0 * (1.0 + 0.3 * np.tanh((y - 0.05) / 0.5))
+
+
+def test_transport_across_the_wake_cut_matches_a_rectilinear_strip():
+    """The k-omega transport sees the cells across the cut as a rectilinear grid would: the same
+    C-grid / periodic-strip construction as above, y-only state and fields, and every wake cell at
+    least three cells from the trailing edge takes the increments of rho, rho k and rho omega of the
+    matching strip cell (convection, diffusion and the Green-Gauss source gradients across the cut)."""
+    nw, ns, n1, R = 12, 16, 8, 3.0
+    sp = inputs.naca0012_case(nw, ns, n1, R=R, x_out=4.0, mach=0.7, alpha_deg=0.0)
+    nodes = sp["nodes"].copy()
+    n0 = sp["n"][0]
+    eta = -nodes[:, 0, 1] / R
+    eta_up = eta ** 0.8
+    for i in range(n0 // 2 + 1, n0 + 1):
+        nodes[:, i] = nodes[0, i] + eta_up[:, None] * (nodes[-1, i] - nodes[0, i])
+    pts = inputs.cell_points(nodes)
+    prim, _, _ = profile(pts[..., 1])
+    k, om = kw_profile(pts[..., 1])
+    c = oracle.Case(2, sp["n"], sp["dx"], sp["bc"], gamma=GAMMA, mu=1e-3, T_wall=sp["T_wall"], multid=0, C_a=0.3,
+                    turb_model=oracle.TURB_KOMEGA, bc_prim=sp["bc_prim"], wake_cut=nw)
+    W = c.prim_to_cons(prim.ravel())
+    nc = n0 * n1
+    RK, RW = k.ravel() * W[:nc], om.ravel() * W[:nc]
+    dt = 2e-3
+    Wc, RKc, RWc, st = c.step_komega_curv(nodes, W, RK, RW, dt, nthreads=4)
+    assert st == 0
+    ys = np.concatenate([-eta[::-1] * R, eta_up[1:] * R])
+    nx = 8
+    xs = np.arange(nx + 1) * (3.0 / nw)
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    rnodes = np.stack([X, Y], axis=-1)
+    rpts = inputs.cell_points(rnodes)
+    rprim, _, _ = profile(rpts[..., 1])
+    rk, rom = kw_profile(rpts[..., 1])
+    free = sp["bc_prim"][1][1][0]
+    dirich = np.tile(free, (nx, 1))
+    r = oracle.Case(2, (nx, 2 * n1), [np.full(nx, 1.0), np.full(2 * n1, 1.0)], [[0, 0], [3, 3]], gamma=GAMMA, mu=1e-3,
+                    multid=0, C_a=0.3, turb_model=oracle.TURB_KOMEGA, bc_prim=[[None, None], [dirich, dirich]])
+    Wr0 = r.prim_to_cons(rprim.ravel())
+    nr = nx * 2 * n1
+    RKr0, RWr0 = rk.ravel() * Wr0[:nr], rom.ravel() * Wr0[:nr]
+    Wr, RKr, RWr, st = r.step_komega_curv(rnodes, Wr0, RKr0, RWr0, dt, nthreads=4)
+    assert st == 0
+    fields_c = [(Wc[:nc] - W[:nc]), (RKc - RK), (RWc - RW)]
+    fields_r = [(Wr[:nr] - Wr0[:nr]), (RKr - RKr0), (RWr - RWr0)]
+    checked = 0
+    for fc_, fr_ in zip(fields_c, fields_r):
+        fc_, fr_ = fc_.reshape(n1, n0), fr_.reshape(2 * n1, nx)
+        scale = np.abs(fr_).max()
+        assert scale > 0
+        for i in range(0, nw - 2):
+            for j in range(n1):
+                for (ci, rj) in ((i, n1 - 1 - j), (n0 - 1 - i, n1 + j)):
+                    assert abs(fc_[j, ci] - fr_[rj, 3]) <= 1e-10 * scale + 1e-15, (i, j, ci)
+                    checked += 1
+    assert checked == 3 * 2 * (nw - 2) * n1
