@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--no-serving", action="store_true", help="leave the serving summary out")
     p.add_argument("--requests", type=int, default=4000)
     p.add_argument("--accuracy", action="store_true", help="report FP32-form errors against the oracle")
+    p.add_argument("--profile", type=int, default=0, metavar="NSTEPS",
+                   help="capture mode for ncu: set the workload's state and take NSTEPS time steps, untimed, "
+                        "then exit (no warm-up, no bench line)")
     return p.parse_args()
 
 
@@ -447,6 +450,15 @@ def run_ours(args):
         f2 = torch.tensor(spec["f2"].ravel(), device=dev)
         if not transport:  # transported fields are set after each set_state
             solver.set_turbulence(f1, f2)
+    if args.profile > 0:
+        # a short run for kernel captures: state in, NSTEPS steps, nothing timed
+        solver.set_state(prim_dev, layout="soa_prim")
+        if transport:
+            solver.set_turbulence(f1, f2)
+        solver.step(nsteps=args.profile, cfl=CFL, t_end=wl["t_end"])
+        torch.cuda.synchronize()
+        solver.close()
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = solver.stream
     nsteps = wl["nsteps"]

@@ -324,14 +324,17 @@ int gks_recon_op_count(int dim, int recon, long long* counts);
  * CFL reduction.
  *   dim, n[dim], h[dim]  grid dimension, cells and (uniform) cell width per axis
  *   W        device, SoA conservative state [nv][cells] in double (caller-owned, read only)
- *   dt_out   host: cfl / max_cells sum_d (|U_d| + c) / h_d
+ *   dt_out   host: cfl / max_cells sum_d (|U_d| + c) / h_d; not written unless GKS_OK
+ * Errors: GKS_EINVAL for bad sizes or arguments, more than GKS_NOALLOC_MAX_CELLS cells, or a stream
+ * that is being captured into a CUDA graph (the call copies to the host and synchronises, which a
+ * capture cannot hold: never make it on a capturing stream); GKS_ENONPHYS if a cell has rho <= 0,
+ * p <= 0 or NaN (as gks_compute_dt reports such a state); GKS_ECUDA.
  * No device memory is allocated: the scratch is a static device array inside the library (about
- * 8 KB, held on every device that loads the library until the process exits), which limits W to
- * GKS_NOALLOC_MAX_CELLS cells (larger states return GKS_EINVAL).  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the array and the last call's contents stay in it, so calls that
- * overlap on the GPU (concurrent streams or threads) race and must be serialised by the caller.
- * Synchronises cuda_stream (NULL: the legacy default stream). */
+ * 8 KB, 1024 partial maxima, held on every device that loads the library until the process exits).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and the SM
+ * count with that device current.  Every call shares the array and the last call's contents stay in
+ * it, so calls that overlap on the GPU (concurrent streams or threads) race and must be serialised by
+ * the caller.  Synchronises cuda_stream (NULL: the legacy default stream). */
 #define GKS_NOALLOC_MAX_CELLS (16384L * 1024L)
 gks_status gks_cfl_dt_noalloc(int dim, const int* n, const double* h, double gamma, const double* W,
                               double cfl, double* dt_out, void* cuda_stream);
@@ -383,6 +386,11 @@ gks_status gks_probe_alu(double* fp32_tflops, double* fp64_tflops);
  * instruction, sm_100 and later), in TFLOP/s: whether pairing raises the FP32 rate or only halves the
  * issue slots it takes.  Same conditions and errors as gks_probe_alu. */
 gks_status gks_probe_alu_packed(double* fp32x2_tflops);
+/* Conversion throughput of the current device, double -> float and float -> double, in units of 1e9
+ * conversions per second (independent chains on every SM, CUDA events): context for the
+ * double-state form (GKS_FP32_ACC64), which converts the staged state and the increments.  Same
+ * conditions and errors as gks_probe_alu. */
+gks_status gks_probe_cvt(double* d2f_gops, double* f2d_gops);
 
 #ifdef __cplusplus
 }

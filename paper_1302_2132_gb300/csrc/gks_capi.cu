@@ -211,6 +211,8 @@ void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
     launch_step_d1_variant(variant, h->prec, A, tiles_for(h, variant), h->stream);
   else if (h->D == 1)
     launch_step_d1(h->prec, false, A, tiles_for(h, 0), h->stream);
+  else if (h->D >= 2 && variant > 0 && h->prec == PREC_F32D)
+    launch_step_acc64_variant(h->D, variant, h->multid, A, tiles_for(h, variant), h->stream);
   else if (h->D == 2 && variant > 0)
     launch_step_d2_variant(variant, h->multid, A, tiles_for(h, variant), h->stream);
   else if (h->D == 3 && variant > 0)
@@ -437,9 +439,9 @@ std::vector<int> tile_candidates(const gks_handle* h) {
     if (h->D == 2 && h->prec == PREC_F32 && h->multid) c.push_back(3);  // 32 x 27 (four full waves at 1024^2)
     return c;
   }
+  const bool f32 = h->prec == PREC_F32 || h->prec == PREC_F32D;
   const int n = h->D == 1 ? kTileVariants1D
-                          : (h->D == 2 && h->prec == PREC_F32 ? kTileVariants2D
-                                                               : (h->D == 3 && h->prec == PREC_F32 ? kTileVariants3D : 1));
+                          : (h->D == 2 && f32 ? kTileVariants2D : (h->D == 3 && f32 ? kTileVariants3D : 1));
   for (int v = 0; v < n; ++v) c.push_back(v);
   return c;
 }
@@ -448,8 +450,8 @@ int n_variants(const gks_handle* h) {
   if (h->curv) return (h->recon != GKS_RECON_MUSCL2 || fused_transport(h)) ? 2 : kCurvVariants;
   if (h->recon != GKS_RECON_MUSCL2) return (int)tile_candidates(h).size();
   if (h->D == 1) return kTileVariants1D;
-  if (h->D == 2 && h->prec == PREC_F32) return kTileVariants2D;
-  if (h->D == 3 && h->prec == PREC_F32) return kTileVariants3D;
+  if (h->D == 2 && (h->prec == PREC_F32 || h->prec == PREC_F32D)) return kTileVariants2D;
+  if (h->D == 3 && (h->prec == PREC_F32 || h->prec == PREC_F32D)) return kTileVariants3D;
   return 1;
 }
 
@@ -597,6 +599,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     if (e == cudaSuccess && D == 2) e = prepare_curv_transport();
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
+    if (e == cudaSuccess && D >= 2) e = prepare_step_acc64();
     if (e == cudaSuccess) e = prepare_komega();
     if (e == cudaSuccess) e = prepare_step_muscl3();
     if (e == cudaSuccess) e = prepare_step_weno5();

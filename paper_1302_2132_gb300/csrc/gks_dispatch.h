@@ -27,6 +27,9 @@ void launch_step_d2_variant2(int variant, bool multid, const StepArgs& A, int nb
 cudaError_t prepare_step_d3_variants();
 void launch_step_d3_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 constexpr int kTileVariants3D = 3;
+// double-state form (FP32 flux, IEEE double state): 2D variants 1 to 5, 3D variants 1 and 2
+cudaError_t prepare_step_acc64();
+void launch_step_acc64_variant(int D, int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 // 1D tile variants 1 and 2 (narrow tiles for small grids)
 cudaError_t prepare_step_d1_variants();
 void launch_step_d1_variant(int variant, int prec, const StepArgs& A, int nblocks, cudaStream_t s);

@@ -68,13 +68,22 @@ template <int D, int V = 0, int H = 2> struct TileGeom {
   static constexpr int NFZ = D >= 3 ? X * Y * (Z + 1) : 0;
   static constexpr int NF = NFX + NFY + NFZ;
   static constexpr int nv = D + 2;
-  // pre: limited slopes of the first halo ring stored per cell and axis (D * nv * NR more values);
+  // Shared memory, in elements of the arithmetic type R: the staged state [nv][NH], tau_t of the
+  // ring [NR], the width tables 3 (HX + HY + HZ), then (from an 8-byte boundary) the face fluxes
+  // [nv][NF] and, with pre, the limited slopes of the first halo ring per cell and axis [D][nv][NR];
   // then the two turbulence fields of the ring and, for the float-pair state, the low words of the
-  // tile's own cells (staged with the state so that the tile waits on global memory once)
-  template <class R> static constexpr size_t smem_bytes(bool pre, bool lo) {
-    return sizeof(R) * ((size_t)nv * NH + NR + (size_t)nv * NF + 3 * (HX + HY + HZ) + (pre ? (size_t)D * nv * NR : 0) +
-                        2 * (size_t)NR) +
+  // tile's own cells (staged with the state so that the tile waits on global memory once).
+  template <class R> __host__ __device__ static constexpr size_t fs_offset() {
+    return ((size_t)nv * NH + NR + 3 * (HX + HY + HZ) + (8 / sizeof(R) - 1)) / (8 / sizeof(R)) * (8 / sizeof(R));
+  }
+  template <class R> __host__ __device__ static constexpr size_t smem_bytes(bool pre, bool lo) {
+    return sizeof(R) * (fs_offset<R>() + (size_t)nv * NF + (pre ? (size_t)D * nv * NR : 0) + 2 * (size_t)NR) +
            (lo ? sizeof(float) * (size_t)nv * NC : 0);
+  }
+  // The double-state form stages the tile's doubles in the space of the face fluxes and slopes (free
+  // until the ring phase) and converts them to float there; true if they fit.
+  __host__ __device__ static constexpr bool dstage_fits(bool pre) {
+    return sizeof(double) * (size_t)nv * NH <= sizeof(float) * ((size_t)nv * NF + (pre ? (size_t)D * nv * NR : 0));
   }
 };
 
@@ -189,6 +198,31 @@ template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
 
 __device__ __forceinline__ long cell_index(const DevGrid& g, int i, int j, int k) {
   return ((long)k * g.n[1] + j) * g.n[0] + i;
+}
+
+// Conversions between the double state and the float arithmetic of the double-state form, on the
+// integer pipe: this part converts at the FP64 rate (gks_probe_cvt: about 2 conversions per clock per
+// SM, 1/64 of the FP32 rate), while these take about ten full-rate integer instructions.
+// d2f rounds toward zero (the FP32 flux inputs carry 2^-23 relative error either way); magnitudes
+// below 2^-126 give a signed zero, 2^128 and above, infinities and NaN give NaN (so that a non-physical
+// state stays visible).
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned int H = (unsigned int)__double2hiint(x), L = (unsigned int)__double2loint(x);
+  const unsigned int e = (H >> 20) & 0x7ffu;  // biased double exponent
+  // bits 29..60 of the double: 23 mantissa bits and the low 9 exponent bits; rebias 1023 -> 127
+  unsigned int f = ((__funnelshift_r(L, H, 29) + 0x40000000u) & 0x7fffffffu) | (H & 0x80000000u);
+  f = e <= 896u ? (H & 0x80000000u) : f;
+  f = e >= 1151u ? 0x7fffffffu : f;
+  return __uint_as_float(f);
+}
+// Exact float -> double (a subnormal float gives a signed zero; infinities and NaN give NaN).
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned int f = __float_as_uint(x), a = f & 0x7fffffffu, sg = f & 0x80000000u;
+  unsigned int H = ((a >> 3) + (896u << 20)) | sg, L = f << 29;
+  H = a < 0x00800000u ? sg : H;
+  L = a < 0x00800000u ? 0u : L;
+  H = a >= 0x7f800000u ? 0x7ff80000u : H;
+  return __hiloint2double((int)H, (int)L);
 }
 
 // Asynchronous global -> shared copy of one 4- or 8-byte element (cp.async, completed by
@@ -318,6 +352,40 @@ __device__ void load_cell(const DevGrid& g, const void* Win, const Consts<typena
       for (int v = 0; v < D + 2; ++v) out[v] = (R)d[v];
     }
   }
+}
+
+// A (possibly ghost) cell whose state is a plain copy of one cell of the grid -- in the grid, or a
+// ghost cell of periodic, transmissive or outflow sides or across a C-grid wake cut, the same rules as
+// load_cell -- gets that cell's index in *src (the copy can then be asynchronous); false for ghost
+// cells that a wall image or Dirichlet data transform.
+__device__ __forceinline__ bool plain_source(const DevGrid& g, int D, int i, int j, int k, long* src) {
+  int c[3] = {i, j, k}, xf[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) c[a] = min(max(c[a], -3), g.n[a] + 2);
+  int s[3] = {c[0], c[1], c[2]};
+  for (int a = 0; a < D; ++a) {
+    const int n = g.n[a];
+    if (c[a] < 0 || c[a] >= n) {
+      const int sd = c[a] < 0 ? 0 : 1;
+      const int bc = g.bc[a][sd];
+      if (bc == BC_PERIODIC) {
+        s[a] = sd == 0 ? c[a] + n : c[a] - n;
+      } else if (bc == BC_WALL) {
+        s[a] = sd == 0 ? -c[a] - 1 : 2 * n - 1 - c[a];
+        xf[a] = 1;
+      } else {
+        s[a] = sd == 0 ? 0 : n - 1;
+        if (bc == BC_DIRICHLET) xf[a] = 1;
+      }
+    }
+  }
+  if (D == 2 && g.wake_cut > 0 && c[1] < 0 && (s[0] < g.wake_cut || s[0] >= g.n[0] - g.wake_cut)) {
+    s[0] = g.n[0] - 1 - s[0];
+    s[1] = -c[1] - 1;
+    xf[1] = 0;
+  }
+  if (xf[0] || xf[1] || xf[2]) return false;
+  *src = cell_index(g, s[0], s[1], s[2]);
+  return true;
 }
 
 // Cell whose turbulence field value a (possibly ghost) cell takes: periodic axes wrap, other axes
@@ -629,8 +697,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   R* Ws = (R*)smem_raw;                    // [nv][HZ][HY][HX]
   constexpr bool PRE = pre_slopes<D, PREC, V>();
   R* taus = Ws + (size_t)nv * G::NH;       // [RZ][RY][RX]
-  R* Fs = taus + G::NR;                    // [nv][NF]
-  R* wsx = Fs + (size_t)nv * G::NF;        // widths with halo
+  R* wsx = taus + G::NR;                   // widths with halo
   R* wsy = wsx + HX;
   R* wsz = wsy + HY;
   R* icx = wsz + HZ;  // 1 / centre distance between halo cells p - 1 and p, per axis
@@ -639,11 +706,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   R* igx = icz + HZ;  // 1 / (distance between the centres of p - 1 and p + 1), per axis
   R* igy = igx + HX;
   R* igz = igy + HY;
-  R* Ss = igz + HZ;  // PRE: [D][nv][NR] limited slopes of the ring cells along each axis
+  R* Fs = Ws + G::template fs_offset<R>();  // [nv][NF], 8-byte aligned
+  R* Ss = Fs + (size_t)nv * G::NF;          // PRE: [D][nv][NR] limited slopes of the ring cells along each axis
   R* Fl = Ss + (PRE ? (size_t)D * nv * G::NR : 0);  // [2][NR] turbulence fields of the ring cells
   float* Lo = (float*)(Fl + 2 * G::NR);             // PREC_F32: [nv][NC] low words of the tile's cells
-  // the stored type is the arithmetic type (FP64, FP32 pair): in-grid cells are copied as they are
+  // the stored type is the arithmetic type (FP64, FP32 pair): cells that are plain copies of grid
+  // cells are copied as they are
   constexpr bool ASYNC = sizeof(S) == sizeof(R);
+  // double state, float arithmetic: the doubles are copied to the flux/slope space [nv][NH] and
+  // converted to float once the copies have landed
+  constexpr bool DSTAGE = PREC == PREC_F32D && G::dstage_fits(PRE);
+  double* Wd = (double*)Fs;
   __shared__ double red[kMaxWarps];
 
   const DevGrid& g = A.g;
@@ -661,10 +734,23 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   for (int l = tid; l < G::NH; l += kThreads) {
     const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
     const int gi = ox + hi - H, gj = D >= 2 ? oy + hj - H : 0, gk = D >= 3 ? oz + hk - H : 0;
-    if (ASYNC && in_grid(g, D, gi, gj, gk)) {
-      const S* src = (const S*)A.Win + cell_index(g, gi, gj, gk);
+    long sc;
+    const bool plain = (ASYNC || DSTAGE) && plain_source(g, D, gi, gj, gk, &sc);
+    if (plain) {
+      const S* src = (const S*)A.Win + sc;
+      if constexpr (DSTAGE) {
 #pragma unroll
-      for (int v = 0; v < nv; ++v) cp_async<sizeof(S)>(&Ws[v * G::NH + l], src + (long)v * g.ncell);
+        for (int v = 0; v < nv; ++v) cp_async<8>(&Wd[v * G::NH + l], src + (long)v * g.ncell);
+      } else {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) cp_async<sizeof(S)>(&Ws[v * G::NH + l], src + (long)v * g.ncell);
+      }
+    } else if constexpr (DSTAGE) {
+      // wall image or Dirichlet ghost: the boundary rule in double precision, converted with the rest
+      double w[nv];
+      load_cell<D, PREC_F64>(g, A.Win, g.kd, gi, gj, gk, w);
+#pragma unroll
+      for (int v = 0; v < nv; ++v) Wd[v * G::NH + l] = w[v];
     } else {
       R w[nv];
       load_cell<D, PREC>(g, A.Win, kc, gi, gj, gk, w);
@@ -743,6 +829,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   }
   cp_async_wait_all();
   __syncthreads();
+  if constexpr (DSTAGE) {
+    for (int q = tid; q < nv * G::NH; q += kThreads) Ws[q] = d2f(Wd[q]);
+    __syncthreads();
+  }
   const double dt_d = s_dt;
   if (dt_d == 0.0) {  // t_end reached: carry the state over
     for (int l = tid; l < G::NC; l += kThreads) {
@@ -925,6 +1015,21 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         __syncwarp();
     }
   }
+  // double state: the old doubles of this thread's cells are loaded while the CTA meets at the barrier
+  constexpr int NCI = (G::NC + kThreads - 1) / kThreads;
+  double wold[PREC == PREC_F32D ? NCI : 1][nv];
+  if constexpr (PREC == PREC_F32D) {
+#pragma unroll
+    for (int q = 0; q < NCI; ++q) {
+      const int l = tid + q * kThreads;
+      const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
+      const int gi = ox + li, gj = oy + lj, gk = oz + lk;
+      if (l >= G::NC || gi >= g.n[0] || (D >= 2 && gj >= g.n[1]) || (D >= 3 && gk >= g.n[2])) continue;
+      const long c = cell_index(g, gi, gj, gk);
+#pragma unroll
+      for (int v = 0; v < nv; ++v) wold[q][v] = __ldg((const double*)A.Win + (long)v * g.ncell + c);
+    }
+  }
   __syncthreads();
 
   // ---- conservative update, CFL rate of the new state, residual norms --------------------------
@@ -933,10 +1038,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
 #pragma unroll
   for (int q = 0; q < 15; ++q) racc[q] = 0.0;
   unsigned int bad = 0;
-  for (int l = tid; l < G::NC; l += kThreads) {
+#pragma unroll
+  for (int qc = 0; qc < NCI; ++qc) {
+    const int l = tid + qc * kThreads;
     const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
     const int gi = ox + li, gj = oy + lj, gk = oz + lk;
-    if (gi >= g.n[0] || (D >= 2 && gj >= g.n[1]) || (D >= 3 && gk >= g.n[2])) continue;
+    if (l >= G::NC || gi >= g.n[0] || (D >= 2 && gj >= g.n[1]) || (D >= 3 && gk >= g.n[2])) continue;
     const long c = cell_index(g, gi, gj, gk);
     // faces below/above the cell along each axis
     int fm[3], fp[3];
@@ -963,12 +1070,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       const int gc[3] = {gi, gj, gk};
       for (int d = 0; d < D; ++d) vol *= g.w[d][gc[d] + kWG];
     }
-    // the cell's old state: staged in shared memory (FP64, float pair), else read from the grid
+    // the cell's old state: staged in shared memory (FP64, float pair), else loaded into wold above
     const int hidx = ((lk + (D >= 3 ? H : 0)) * HY + (lj + (D >= 2 ? H : 0))) * HX + (li + H);
 #pragma unroll
     for (int v = 0; v < nv; ++v) {
       const long gidx = (long)v * g.ncell + c;
-      if (PREC == PREC_F64) {
+      if constexpr (PREC == PREC_F64) {
         double w = (double)Ws[v * G::NH + hidx];
         const double w_old = w;
 #pragma unroll
@@ -986,7 +1093,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
 #pragma unroll
         for (int d = 0; d < D; ++d) inc -= (Fs[v * G::NF + fp[d]] - Fs[v * G::NF + fm[d]]) * ih[d];
         double wd = 0.0;
-        if (PREC == PREC_F32) {
+        if constexpr (PREC == PREC_F32) {
           // (hi, lo) += inc with an error-free sum, then renormalise
           const float hi = (float)Ws[v * G::NH + hidx], lo = Lo[v * G::NC + l];
           const float s = hi + inc;
@@ -1000,9 +1107,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           wn[v] = nhi;
           if (A.resid) wd = (double)nhi + (double)nlo;
         } else {
-          const double w = ((const double*)A.Win)[gidx] + (double)inc;
+          const double w = wold[qc][v] + f2d(inc);
           ((double*)A.Wout)[gidx] = w;
-          wn[v] = (R)w;
+          wn[v] = (float)Ws[v * G::NH + hidx] + inc;  // the new state in float, for the rate and status
           wd = w;
         }
         if (A.resid) {

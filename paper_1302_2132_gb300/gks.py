@@ -111,6 +111,8 @@ def load():
     L.gks_probe_alu.restype = _I
     L.gks_probe_alu_packed.argtypes = [_PD]
     L.gks_probe_alu_packed.restype = _I
+    L.gks_probe_cvt.argtypes = [_PD, _PD]
+    L.gks_probe_cvt.restype = _I
     L.gks_face_op_count.argtypes = [_I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_face_op_count.restype = _I
     L.gks_cell_op_count.argtypes = [_I, ctypes.POINTER(ctypes.c_longlong)]
@@ -383,6 +385,14 @@ def probe_alu_packed():
     if st != OK:
         raise GksError(st, "gks_probe_alu_packed failed")
     return a.value
+
+def probe_cvt():
+    """(double -> float, float -> double) conversions per second of the current device, in 1e9/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().gks_probe_cvt(ctypes.byref(a), ctypes.byref(b))
+    if st != OK:
+        raise GksError(st, "gks_probe_cvt failed")
+    return a.value, b.value
 
 
 def face_op_count(dim, expand=True, with_recon=True):
