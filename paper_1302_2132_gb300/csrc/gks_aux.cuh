@@ -87,7 +87,8 @@ __global__ void copy_kernel(const T* src, T* dst, long n) {
   if (c < n) dst[c] = src[c];
 }
 
-// CFL rate of the stored state into ctrl->rate[slot] (a step computes it for its successor).
+// CFL rate of the stored state into ctrl->rate[slot] (a step computes it for its successor); a cell
+// with rho <= 0 or p <= 0 sets the non-physical status bit, as the step's update does.
 template <int D, int PREC>
 __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ StepArgs A) {
   using R = typename PrecT<PREC>::R;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ 
   const DevGrid& g = A.g;
   const Consts<R> kc = make_consts<R>(g);
   R rmax = R(0);
+  int bad = 0;
   for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += (long)gridDim.x * blockDim.x) {
     R w[D + 2];
     load_stored<D, PREC>(A.g, A.Win, c, w);
@@ -104,10 +106,12 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(const __grid_constant__ 
     pos[2] = (int)(c / ((long)g.n[0] * g.n[1]));
     R h[D];
     for (int d = 0; d < D; ++d) h[d] = (R)g.w[d][pos[d] + kWG];
+    if (!(w[0] > R(0)) || !(pressure_of<R>(D, kc.gamma, w) > R(0))) bad = 1;
     rmax = fmax(rmax, cell_rate<D, R>(w, kc.gamma, h));
   }
   const double m = block_max<double>((double)rmax, red);
   if (threadIdx.x == 0) atomic_max_nonneg(&A.ctrl->rate[A.slot], m);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&A.ctrl->status, 1u);
 }
 
 template <int unused = 0>
