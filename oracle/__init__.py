@@ -83,6 +83,7 @@ class Problem(ctypes.Structure):
         ("abar_mode", ctypes.c_int),
         ("recon", ctypes.c_int),
         ("wake_cut", ctypes.c_int),
+        ("no_fallback", ctypes.c_int),
     ]
 
 
@@ -143,6 +144,7 @@ def lib():
             L.orc_tau_turb.argtypes = [P, _PD, _PD, _PD, _PD]
             L.orc_rarefaction.argtypes = [P, _PD, _PD, _PD, _PD]
             L.orc_step.argtypes = [P, _PD, _PD, _PD, _D, _PD, _I]
+            L.orc_fallback_count.argtypes = [P, _PD, _PD, _PD, ctypes.POINTER(ctypes.c_long)]
             L.orc_run.argtypes = [P, _PD, _PD, _PD, _D, _D, _I, _D, _PD, ctypes.POINTER(_I), _I]
             L.orc_step_curv.argtypes = [P, _PD, _PD, _PD, _PD, _D, _I]
             L.orc_compute_dt_curv.argtypes = [P, _PD, _PD, _D, _PD]
@@ -307,6 +309,14 @@ class Case:
         prim = np.zeros_like(W)
         lib().orc_cons_to_prim(ctypes.byref(self.P), _ptr(W), _ptr(prim), self.ncell)
         return prim
+
+    def fallback_count(self, W, f1=None, f2=None):
+        """Face sides evaluated at first order (reconstructed rho or p not positive) in a step from W."""
+        W = self._state(W)
+        n = ctypes.c_long()
+        lib().orc_fallback_count(ctypes.byref(self.P), _ptr(W), _ptr(self._field(f1)), _ptr(self._field(f2)),
+                                 ctypes.byref(n))
+        return n.value
 
     def compute_dt(self, W, cfl):
         W = self._state(W)

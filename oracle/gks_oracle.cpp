@@ -744,8 +744,9 @@ void prepare(const orc_problem* P, const double* W, const double* f1, const doub
         C.taut[G.idx(i, j, k)] = tau_turb_cell(P, G, C.Wp, C.f1p, C.f2p, i, j, k);
 }
 
-// Face record for the face between cell c (index j along axis d) and its + neighbour.
-void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
+// Face record for the face between cell c (index j along axis d) and its + neighbour; *nfb (if
+// given) receives the number of sides that fell back to first order.
+void build_face(const StepCtx& C, int d, const int* c, orc_face& f, int* nfb = nullptr) {
   const Grid& G = C.G;
   const orc_problem* P = C.P;
   const int D = G.D, nv = G.nv;
@@ -782,12 +783,15 @@ void build_face(const StepCtx& C, int d, const int* c, orc_face& f) {
     f.cr[v] = S[3][v];
   }
   // first order on a side whose reconstructed density or pressure is not positive
-  if (!(f.wl[0] > 0.0) || !(pressure(D, P->gamma, f.wl) > 0.0))
+  const bool bad_l = !(f.wl[0] > 0.0) || !(pressure(D, P->gamma, f.wl) > 0.0);
+  const bool bad_r = !(f.wr[0] > 0.0) || !(pressure(D, P->gamma, f.wr) > 0.0);
+  if (nfb) *nfb = (int)bad_l + (int)bad_r;
+  if (bad_l && !P->no_fallback)
     for (int v = 0; v < nv; ++v) {
       f.wl[v] = S[2][v];
       f.sl[v] = 0.0;
     }
-  if (!(f.wr[0] > 0.0) || !(pressure(D, P->gamma, f.wr) > 0.0))
+  if (bad_r && !P->no_fallback)
     for (int v = 0; v < nv; ++v) {
       f.wr[v] = S[3][v];
       f.sr[v] = 0.0;
@@ -905,6 +909,29 @@ int orc_euler_flux(int D, double gamma, const double* w, double* F) {
   F[0] = w[1];
   for (int i = 0; i < D; ++i) F[1 + i] = w[1 + i] * un + (i == 0 ? p : 0.0);
   F[D + 1] = un * (w[D + 1] + p);
+  return 0;
+}
+
+int orc_fallback_count(const orc_problem* P, const double* W, const double* f1, const double* f2, long* count) {
+  StepCtx C;
+  prepare(P, W, f1, f2, C);
+  const Grid& G = C.G;
+  long total = 0;
+  for (int d = 0; d < G.D; ++d) {
+    int nf[3] = {G.n[0], G.n[1], G.n[2]};
+    nf[d] += 1;
+    for (int k = 0; k < nf[2]; ++k)
+      for (int j = 0; j < nf[1]; ++j)
+        for (int i = 0; i < nf[0]; ++i) {
+          int c[3] = {i, j, k};
+          c[d] -= 1;  // left cell of the face
+          orc_face f;
+          int nfb = 0;
+          build_face(C, d, c, f, &nfb);
+          total += nfb;
+        }
+  }
+  *count = total;
   return 0;
 }
 

@@ -39,6 +39,8 @@ typedef struct {
   int recon;                    /* ORC_RECON_*; MUSCL2 uses `limiter` */
   int wake_cut;                 /* 2D C-grids: the first and last wake_cut cells of the j-lo side are a
                                    wake cut, ghost (i, -k) = cell (n0 - 1 - i, k - 1); 0: none */
+  int no_fallback;              /* tests only: the rectilinear step skips the first-order fallback of a face side whose
+                                   reconstructed rho or p is not positive (a planted mistake) */
 } orc_problem;
 
 /* Per-face record, normal frame (velocity index 0 is the face normal):
@@ -76,6 +78,9 @@ int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int mul
 int orc_face_flux_compact(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
                           int printed_beta, const orc_face* f, double* F);
 int orc_euler_flux(int D, double gamma, const double* w, double* F);
+/* Number of face sides (over every face of every axis) whose reconstructed density or pressure is
+ * not positive, i.e. that the step evaluates at first order. */
+int orc_fallback_count(const orc_problem* P, const double* W, const double* f1, const double* f2, long* count);
 /* Face values of a 1D row of cell averages v[0..n) with widths h (the ends take the nearest
  * cell): wl[i] = value at the right face of cell i (its own reconstruction), wr[i] = value at the
  * left face of cell i, for the faces with a full stencil; other entries are left untouched. */

@@ -12,6 +12,7 @@ inputs of this library):
                     solenoidal velocity with E(k) ~ k^4 exp(-2 (k/k0)^2) scaled to a turbulent Mach
                     number, rho = 1, p = 1/gamma; log-normal k and epsilon fields from 8 Fourier modes
   riemann_quadrant  2D four-state Riemann problem with seeded states
+  near_vacuum       strongly expanding low-pressure states (the first-order fallback of MUSCL)
   shock_boundary_layer  Mach 2.85 flat-plate boundary layer under an oblique shock on a
                     wall-clustered grid, with log-law k-omega profiles
   compression_corner  Mach 2.85 boundary layer over a ramp of alpha degrees on a body-fitted,
@@ -116,6 +117,24 @@ def riemann_quadrant(n, seed):
         for v in range(4):
             prim[v][q == k] = st[k][v]
     return dict(dim=2, n=(n, n), dx=[np.full(n, 1.0 / n)] * 2, bc=[[1, 1], [1, 1]], prim=prim)
+
+
+def near_vacuum(n, dim, seed, p_ref=0.02, du=1.2):
+    """A strongly expanding, low-pressure state on [0,1]^dim with transmissive boundaries (the kind
+    of data where a MUSCL reconstruction of the conservative variables can give a face state with
+    negative pressure): each velocity component increases along its own axis by seeded random steps
+    in [0, du] per cell (centred on zero), rho in [0.5, 1.5] and p in [p_ref, 1.5 p_ref] drawn per
+    cell."""
+    rng = np.random.default_rng(seed)
+    shape = (n,) * dim
+    prim = np.zeros((dim + 2,) + shape)
+    prim[0] = rng.uniform(0.5, 1.5, shape)
+    for a in range(dim):
+        steps = rng.uniform(0.0, du, shape)
+        u = np.cumsum(steps, axis=dim - 1 - a)  # axis a of the grid is array axis dim - 1 - a
+        prim[1 + a] = u - u.mean()
+    prim[dim + 1] = p_ref * rng.uniform(1.0, 1.5, shape)
+    return dict(dim=dim, n=shape, dx=[np.full(n, 1.0 / n)] * dim, bc=[[1, 1]] * dim, prim=prim)
 
 
 def sod_2d(n, seed=0):
