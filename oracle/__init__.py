@@ -83,6 +83,7 @@ class Problem(ctypes.Structure):
         ("abar_mode", ctypes.c_int),
         ("recon", ctypes.c_int),
         ("wake_cut", ctypes.c_int),
+        ("rarefaction", ctypes.c_int),
         ("no_fallback", ctypes.c_int),
     ]
 
@@ -104,7 +105,7 @@ class FaceDiag(ctypes.Structure):
         ("Al", ctypes.c_double * 5), ("Ar", ctypes.c_double * 5),
         ("abl", ctypes.c_double * 5), ("abr", ctypes.c_double * 5),
         ("bb", (ctypes.c_double * 5) * 2), ("Ab", ctypes.c_double * 5),
-        ("tau", ctypes.c_double), ("T", ctypes.c_double * 6),
+        ("tau", ctypes.c_double), ("T", ctypes.c_double * 6), ("tauhat", ctypes.c_double),
     ]
 
 
@@ -132,9 +133,10 @@ def lib():
             L.orc_ximoments.argtypes = [_D, _D, _I, _PD]
             L.orc_time_coeffs.argtypes = [_D, _D, _PD]
             L.orc_slope.argtypes = [_I, _D, _PD, _PD, _PD]
-            L.orc_face_flux.argtypes = [_I, _D, _D, _D, _D, _I, _I, ctypes.POINTER(Face), _PD,
+            L.orc_time_coeffs_hat.argtypes = [_D, _D, _D, _PD]
+            L.orc_face_flux.argtypes = [_I, _D, _D, _D, _D, _I, _I, _I, ctypes.POINTER(Face), _PD,
                                         ctypes.POINTER(FaceDiag)]
-            L.orc_face_flux_compact.argtypes = [_I, _D, _D, _D, _D, _I, _I, _I, ctypes.POINTER(Face), _PD]
+            L.orc_face_flux_compact.argtypes = [_I, _D, _D, _D, _D, _I, _I, _I, _I, ctypes.POINTER(Face), _PD]
             L.orc_euler_flux.argtypes = [_I, _D, _PD, _PD]
             L.orc_reconstruct.argtypes = [_I, _I, _PD, _PD, _I, _PD, _PD]
             P = ctypes.POINTER(Problem)
@@ -217,19 +219,27 @@ def make_face(D, wl, wr, cl=None, cr=None, sl=None, sr=None, tl=None, tr=None, d
     return f
 
 
-def face_flux(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIMEINT, diag=False):
+def time_coeffs_hat(dt, tau, eps):
+    """T0..T5 and dt^2/2 - T2 with the degree of rarefaction eps in place of tau/dt."""
+    out = np.zeros(7)
+    lib().orc_time_coeffs_hat(dt, tau, eps, _ptr(out))
+    return out
+
+
+def face_flux(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIMEINT, diag=False, rarefaction=0):
     F = np.zeros(D + 2)
     dg = FaceDiag()
-    lib().orc_face_flux(D, gamma, mu, C_a, dt, multid, abar_mode, ctypes.byref(face), _ptr(F),
+    lib().orc_face_flux(D, gamma, mu, C_a, dt, multid, abar_mode, int(rarefaction), ctypes.byref(face), _ptr(F),
                         ctypes.byref(dg))
     if diag:
         return F, dg
     return F
 
 
-def face_flux_compact(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIMEINT, printed_beta=False):
+def face_flux_compact(D, gamma, mu, C_a, dt, face, multid=1, abar_mode=ABAR_TIMEINT, printed_beta=False,
+                      rarefaction=0):
     F = np.zeros(D + 2)
-    lib().orc_face_flux_compact(D, gamma, mu, C_a, dt, multid, abar_mode, int(printed_beta),
+    lib().orc_face_flux_compact(D, gamma, mu, C_a, dt, multid, abar_mode, int(rarefaction), int(printed_beta),
                                 ctypes.byref(face), _ptr(F))
     return F
 
@@ -260,7 +270,7 @@ class Case:
 
     def __init__(self, dim, n, dx, bc, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model=TURB_NONE,
                  C_mu=0.09, beta_star=0.09, C_a=0.0, limiter=LIM_VANLEER, multid=1,
-                 abar_mode=ABAR_TIMEINT, bc_prim=None, recon=RECON_MUSCL2, wake_cut=0):
+                 abar_mode=ABAR_TIMEINT, bc_prim=None, recon=RECON_MUSCL2, wake_cut=0, rarefaction=0):
         self.dim = dim
         self.n = tuple(n)
         self.P = Problem()
@@ -283,6 +293,7 @@ class Case:
         self.P.limiter, self.P.multid, self.P.abar_mode = limiter, multid, abar_mode
         self.P.recon = recon
         self.P.wake_cut = int(wake_cut)
+        self.P.rarefaction = int(rarefaction)
         self.ncell = int(np.prod(n[:dim]))
         self.nv = dim + 2
 

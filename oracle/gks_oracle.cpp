@@ -288,6 +288,50 @@ void time_coeffs(double dt, double tau, double* T) {
   }
 }
 
+// The time coefficients with the degree of rarefaction eps in place of tau/dt (Eqs. tautautilde,
+// rarefactionkepsilon, epsilonkomega; reading G9): Eq. fkepsilon with alpha = eps (1 - e^{-1/eps}) and
+// beta = e^{-1/eps} (Eq. alphabetakepsilon with the corrected beta of reading G7), written as the
+// T0..T5 of Eq. fluxesf (the compact form equals the time integral with these alpha, beta):
+//   T0 = dt (1 - alpha)            T3 = dt alpha
+//   T1 = dt tau (2 alpha - 1 - beta)  T4 = dt tau (beta - 2 alpha)
+//   T2 = dt (dt/2 - tau (1 - alpha))  T5 = -dt tau alpha,   T[6] = dt^2/2 - T2 = dt tau (1 - alpha).
+// With eps = tau/dt these are the coefficients of time_coeffs.  For eps > 1, 1 - alpha and
+// 2 alpha - 1 - beta cancel to O(1/eps) and O(1/eps^2): they are summed from the exponential series
+// in x = 1/eps term by term.
+void time_coeffs_hat(double dt, double tau, double eps, double* T) {
+  double a, one_a, c1, c4;
+  if (eps > 1.0) {
+    const double x = 1.0 / eps;
+    a = 0.0;
+    one_a = 0.0;
+    c1 = 0.0;
+    double xp = 1.0, fact = 1.0;  // xp = x^m, fact = (m+1)!
+    for (int m = 0; m < 40; ++m) {
+      const double term = xp / fact;  // x^m/(m+1)!
+      const double sg = (m % 2 == 0) ? 1.0 : -1.0;
+      a += sg * term;                          // alpha = sum (-x)^m/(m+1)!
+      if (m >= 1) one_a -= sg * term;          // 1 - alpha
+      if (m >= 2) c1 += sg * (1.0 - m) * term;  // 2 alpha - 1 - beta
+      xp *= x;
+      fact *= (m + 2);
+    }
+    c4 = std::exp(-x) - 2.0 * a;
+  } else {
+    const double beta = eps > 0.0 ? std::exp(-1.0 / eps) : 0.0;
+    a = eps * (1.0 - beta);
+    one_a = 1.0 - a;
+    c1 = 2.0 * a - 1.0 - beta;
+    c4 = beta - 2.0 * a;
+  }
+  T[0] = dt * one_a;
+  T[1] = dt * tau * c1;
+  T[2] = dt * (0.5 * dt - tau * one_a);
+  T[3] = dt * a;
+  T[4] = dt * tau * c4;
+  T[5] = -dt * tau * a;
+  T[6] = dt * tau * one_a;
+}
+
 double pressure(int D, double gamma, const double* w) {
   double q = 0.0;
   for (int i = 0; i < D; ++i) q += w[1 + i] * w[1 + i];
@@ -300,11 +344,12 @@ struct FaceWork {
   Maxw gl, gr, g0;
   double w0[5], al[5], ar[5], bl[2][5], br[2][5], Al[5], Ar[5], abl[5], abr[5], bb[2][5], Ab[5];
   double tau, T[7];
+  double tauhat;  // rarefaction option: the resolved time scale rho / |D rho| at the face
   Poly Ql, Qr, Q0l, Q0r, Qt0, PAl, PAr, PAb;
 };
 
 bool face_setup(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
-                const orc_face& f, FaceWork& W) {
+                const orc_face& f, FaceWork& W, int rarefaction = 0) {
   const int nv = D + 2;
   const double K = 2.0 / (gamma - 1.0) - D;
   W.D = D;
@@ -368,7 +413,28 @@ bool face_setup(int D, double gamma, double mu, double C_a, double dt, int multi
   double p0 = r0 / (2.0 * W.g0.lam);
   double pl = rl / (2.0 * W.gl.lam), pr = rr / (2.0 * W.gr.lam);
   W.tau = mu / p0 + f.tau_t + C_a * std::fabs(pr - pl) / std::fabs(pr + pl) * dt;
-  time_coeffs(dt, W.tau, W.T);
+  W.tauhat = 0.0;
+  if (rarefaction) {
+    // Eqs. tautautilde, tautilde, epsilonkomega: the degree of rarefaction eps = tau / tauhat with
+    // tauhat = rho / |D rho| at the face, D rho = d_t rho + U_n d_n rho (reading G9).  d_t rho is the
+    // density row of the equilibrium time slope of the t = 0 compatibility condition
+    // <(abar u + bbar v + A0) psi>_0 = 0; d_n rho that of the mean of the two normal slopes abar.
+    double rhs0[5], A0[5], ab[5];
+    for (int m = 0; m < nv; ++m) {
+      Poly p = psi(D, m);
+      rhs0[m] = -(moment(W.g0, ORC_POS, W.Q0l * p) + moment(W.g0, ORC_NEG, W.Q0r * p) +
+                  moment(W.g0, ORC_FULL, W.Qt0 * p));
+      ab[m] = 0.5 * (W.abl[m] + W.abr[m]);
+    }
+    slope(W.g0, rhs0, A0);
+    const double dt_rho = r0 * moment(W.g0, ORC_FULL, expansion(D, A0) * psi(D, 0));
+    const double dn_rho = r0 * moment(W.g0, ORC_FULL, expansion(D, ab) * psi(D, 0));
+    const double Drho = std::fabs(dt_rho + W.g0.U[0] * dn_rho);
+    W.tauhat = Drho > 1e-30 * r0 ? r0 / Drho : 1e30;  // uniform flow: tauhat -> infinity, eps -> 0
+    time_coeffs_hat(dt, W.tau, W.tau / W.tauhat, W.T);
+  } else {
+    time_coeffs(dt, W.tau, W.T);
+  }
 
   // Abar from the compatibility condition integrated over [0, dt] at the face:
   //   Dn <Abar psi>_0 = T1 <(abar u + bbar v) psi>_0 + T4 (rho_l <(a_l u + b_l v) psi>_{l,u>0}
@@ -411,6 +477,7 @@ void fill_diag(const FaceWork& W, orc_face_diag* dg) {
   }
   dg->tau = W.tau;
   for (int i = 0; i < 6; ++i) dg->T[i] = W.T[i];
+  dg->tauhat = W.tauhat;
 }
 
 // Eq. fluxesf: F = int_0^dt int u psi f dXi dt, with f from Eq. resultingf.
@@ -857,6 +924,11 @@ int orc_time_coeffs(double dt, double tau, double* T) {
   return 0;
 }
 
+int orc_time_coeffs_hat(double dt, double tau, double eps, double* T) {
+  time_coeffs_hat(dt, tau, eps, T);
+  return 0;
+}
+
 int orc_slope(int D, double K, const double* w, const double* rhs, double* a_out) {
   Maxw g = make_maxw(D, K, w);
   slope(g, rhs, a_out);
@@ -864,9 +936,9 @@ int orc_slope(int D, double K, const double* w, const double* rhs, double* a_out
 }
 
 int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
-                  const orc_face* f, double* F, orc_face_diag* diag) {
+                  int rarefaction, const orc_face* f, double* F, orc_face_diag* diag) {
   FaceWork W;
-  face_setup(D, gamma, mu, C_a, dt, multid, abar_mode, *f, W);
+  face_setup(D, gamma, mu, C_a, dt, multid, abar_mode, *f, W, rarefaction);
   face_flux(W, F);
   fill_diag(W, diag);
   return 0;
@@ -879,12 +951,14 @@ int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int mul
 // spatial-expansion terms, and the time factor of Eq. resultingf2 is (t/tau) e^{-t/tau}; with the
 // leading Maxwellians kept in f~ the form no longer equals the time integral of Eq. resultingf.
 int orc_face_flux_compact(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
-                          int printed_beta, const orc_face* f, double* F) {
+                          int rarefaction, int printed_beta, const orc_face* f, double* F) {
   FaceWork W;
-  face_setup(D, gamma, mu, C_a, dt, multid, abar_mode, *f, W);
+  face_setup(D, gamma, mu, C_a, dt, multid, abar_mode, *f, W, rarefaction);
   const Poly u = pvar(0);
   const double r0 = W.g0.rho, rl = W.gl.rho, rr = W.gr.rho, tau = W.tau;
-  double eps = tau / dt;
+  // the degree of rarefaction: tau/dt (Eq. epsilonkepsilon) or tau/tauhat (Eqs. rarefactionkepsilon,
+  // epsilonkomega)
+  double eps = rarefaction ? tau / W.tauhat : tau / dt;
   double ex = std::exp(-1.0 / eps);
   double alpha = eps * (1.0 - ex);
   double beta = printed_beta ? eps * ex : ex;
@@ -1045,7 +1119,7 @@ int flow_step(const orc_problem* P, double* W, const double* f1, const double* f
       build_face(C, d, c, f);
       double Fr[5];
       FaceWork Wk;
-      face_setup(D, P->gamma, P->mu, P->C_a, dt, P->multid, P->abar_mode, f, Wk);
+      face_setup(D, P->gamma, P->mu, P->C_a, dt, P->multid, P->abar_mode, f, Wk, P->rarefaction);
       face_flux(Wk, Fr);
       double* Fo = &Fd[fi * nv];
       Fo[0] = Fr[0];
@@ -1625,7 +1699,7 @@ void curv_fluxes(const CurvCtx& C, double dt, const std::vector<double>* win, bo
       }
       FaceWork Wk;
       face_setup(2, P->gamma, P->mu, P->C_a, win ? win[d][f] : dt, P->multid && !first_order ? 1 : 0, P->abar_mode,
-                 fc, Wk);
+                 fc, Wk, P->rarefaction);
       double Fr[4];
       face_flux(Wk, Fr);
       double* Fo = d == 0 ? &Fi[f * nv] : &Fj[f * nv];

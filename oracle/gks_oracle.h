@@ -39,6 +39,8 @@ typedef struct {
   int recon;                    /* ORC_RECON_*; MUSCL2 uses `limiter` */
   int wake_cut;                 /* 2D C-grids: the first and last wake_cut cells of the j-lo side are a
                                    wake cut, ghost (i, -k) = cell (n0 - 1 - i, k - 1); 0: none */
+  int rarefaction;              /* 0: x = dt/tau in the time coefficients; 1: the degree of rarefaction
+                                   eps = tau/tauhat of Eqs. tautautilde, epsilonkomega in their place */
   int no_fallback;              /* tests only: the rectilinear step skips the first-order fallback of a face side whose
                                    reconstructed rho or p is not positive (a planted mistake) */
 } orc_problem;
@@ -67,16 +69,18 @@ typedef struct {
   double Ab[5];                 /* equilibrium time coefficient */
   double tau;                   /* total relaxation time */
   double T[6];                  /* T0..T5 */
+  double tauhat;                /* rarefaction option: rho / |D rho| at the face (0 otherwise) */
 } orc_face_diag;
 
 int orc_umoments(double U, double lam, int region, int nmax, double* out);
 int orc_ximoments(double K, double lam, int lmax, double* out);
 int orc_time_coeffs(double dt, double tau, double* T /* T0..T5, then dt^2/2 - T2 */);
 int orc_slope(int D, double K, const double* w, const double* rhs, double* a_out);
+int orc_time_coeffs_hat(double dt, double tau, double eps, double* T /* as orc_time_coeffs */);
 int orc_face_flux(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
-                  const orc_face* f, double* F, orc_face_diag* diag);
+                  int rarefaction, const orc_face* f, double* F, orc_face_diag* diag);
 int orc_face_flux_compact(int D, double gamma, double mu, double C_a, double dt, int multid, int abar_mode,
-                          int printed_beta, const orc_face* f, double* F);
+                          int rarefaction, int printed_beta, const orc_face* f, double* F);
 int orc_euler_flux(int D, double gamma, const double* w, double* F);
 /* Number of face sides (over every face of every axis) whose reconstructed density or pressure is
  * not positive, i.e. that the step evaluates at first order. */
