@@ -92,11 +92,29 @@ typedef struct {
   double T_wall;   /* wall temperature in units of p/rho, GKS_BC_WALL */
 } gks_gas;
 
+/* degree of rarefaction in the time coefficients (Section 3): x = dt/tau, the exact time integral of
+ * Eq. resultingf (the default; Eq. epsilonkepsilon), or eps = tau/tauhat with tauhat = rho/|D rho| the
+ * resolved time scale of the mean flow (Eqs. tautautilde, tautilde, rarefactionkepsilon; Section 4,
+ * Eq. epsilonkomega) in place of tau/dt inside alpha and beta of Eq. fkepsilon.  The library's reading:
+ * D rho = d_t rho + U_n d_n rho at the face, d_t rho from the t = 0 compatibility condition of the
+ * equilibrium part (-rho0 <(abar u + bbar v) psi_rho>_0), d_n rho the mean of (w0 - W_l)/dxl and
+ * (W_r - w0)/dxr; tauhat at most 1e30 (uniform flow: eps -> 0); alpha = eps (1 - e^{-1/eps}),
+ * beta = e^{-1/eps}; T0 = dt (1 - alpha), T1 = dt tau (2 alpha - 1 - beta), T2 = dt (dt/2 - tau
+ * (1 - alpha)), T3 = dt alpha, T4 = dt tau (beta - 2 alpha), T5 = -dt tau alpha, and Abar from the
+ * compatibility condition integrated with these. */
+enum { GKS_RAR_DT = 0, GKS_RAR_TAUHAT = 1 };
+
+/* Turbulence inputs (Section 3: tau_t from an eddy viscosity, Eq. tauttrivial, or from k and epsilon,
+ * Eq. tautchen; Section 4: k and omega, Eq. tautchenadjusted; tau_a of Eq. taua). */
 typedef struct {
   int model;        /* GKS_TURB_* */
   double C_mu;      /* k-epsilon constant (Eq. tautchen), usually 0.09 */
   double beta_star; /* k-omega: eta = S / (beta* omega) */
   double C_a;       /* artificial dissipation coefficient in [0, 1] (Eq. taua) */
+  int rarefaction;  /* GKS_RAR_DT (default, zero) or GKS_RAR_TAUHAT.  GKS_RAR_TAUHAT is built for
+                       MUSCL2 in every precision on rectilinear grids (the default tile shape), and
+                       for GKS_FP64 and GKS_FP32 on body-fitted grids and in the steady solver;
+                       GKS_EUNSUPPORTED otherwise */
 } gks_turb;
 
 typedef struct {
@@ -107,14 +125,20 @@ typedef struct {
   int reconstruction;  /* GKS_RECON_*; zero (the default) is MUSCL2 */
 } gks_numerics;
 
-/* Create a solver on the current CUDA device.  cuda_stream is a cudaStream_t or NULL (the library
- * then creates its own non-blocking stream).  All device buffers are allocated here and owned by
- * the handle.  Errors: GKS_EINVAL for bad sizes, codes or Dirichlet data, GKS_ENOMEM, GKS_ECUDA. */
+/* Create a solver on the current CUDA device for the problem the paper states: a state on a grid
+ * (Section 2, Eq. moment1), a gas with gamma and mu = tau p (Section 2, Eqs. maxwellian,
+ * chapman-enskog-ns; Pr = 1), the turbulence inputs of Sections 3 and 4 (Eqs. tauttrivial, tautchen,
+ * tautchenadjusted, taua) and the numerics of Section 4.  cuda_stream is a cudaStream_t or NULL (the
+ * library then creates its own non-blocking stream).  All device buffers are allocated here and owned
+ * by the handle.  Errors: GKS_EINVAL for bad sizes, codes or Dirichlet data, GKS_EUNSUPPORTED for an
+ * option that is not built (prandtl != 1, see also gks_turb.rarefaction), GKS_ENOMEM, GKS_ECUDA. */
 gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb,
                       const gks_numerics* num, void* cuda_stream, gks_handle** out);
 
-/* Copy a state in (any layout, float or double, host or device) and reset time to 0, the step
- * counter and the sticky status.  The CFL rate of the new state is computed on the device. */
+/* Copy a state in: the conservative variables W = (rho, rho U, rho E), the moments of the distribution
+ * (Section 2, Eq. moment1), in any layout, float or double, host or device; reset time to 0, the step
+ * counter and the sticky status.  The CFL rate of the new state is computed on the device; a cell with
+ * rho <= 0 or p <= 0 sets the sticky GKS_ENONPHYS status. */
 gks_status gks_set_state(gks_handle* h, const void* W, int layout, int memspace, int dtype);
 
 /* Body-fitted 2D grid (the C-type and channel grids of the paper's cases, Section 5, Table 2):
@@ -174,6 +198,9 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace);
  *     rho k -= R / D, D = A / (cfl s) + sum_faces (max(m_out, 0) + conductance) / rho + A beta omega
  *     (beta* for k, beta0 for omega), then the floors; the flow cycle keeps the fields of the
  *     cycle's start.
+ *   - gks_turb.rarefaction = GKS_RAR_TAUHAT (the paper's steady solver): the faces of every level's
+ *     residual take the degree of rarefaction eps = tau/tauhat in place of tau over the face window
+ *     inside the time coefficients (MUSCL2 only); the window itself is unchanged.
  * Built for GKS_FP64 and GKS_FP32 (state stored in the arithmetic type), both expansions and the
  * three reconstructions (MUSCL2, MUSCL3, WENO5 as for gks_set_nodes) on the finest level (coarse
  * levels are first order), turbulence models NONE, MUT, KEPS, KOMEGA (prescribed fields) and
@@ -184,27 +211,31 @@ typedef struct gks_steady gks_steady;
 gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb,
                              const gks_numerics* num, const double* nodes, int levels, int lusgs_tile,
                              void* cuda_stream, gks_steady** out);
-/* Copy the fine-grid state in (as gks_set_state); the prescribed turbulence fields (as
+/* Copy the fine-grid state in (as gks_set_state; Section 2, Eq. moment1); the prescribed turbulence fields (as
  * gks_set_turbulence; coarse levels take four-cell means).  With GKS_TURB_KOMEGA_TRANSPORT the fields
  * are the initial k and omega, stored as rho k and rho omega with the density of the current state:
  * set the state first (gks_steady_set_state clears them); GKS_EINVAL otherwise. */
 gks_status gks_steady_set_state(gks_steady* s, const void* W, int layout, int memspace, int dtype);
 gks_status gks_steady_set_turbulence(gks_steady* s, const void* f1, const void* f2, int memspace, int dtype);
-/* Run ncycles multigrid cycles (one CUDA graph per cycle, captured once per (cfl, cfl_flux)); res_out
+/* Run ncycles multigrid cycles of the steady solver of Section 4 (one CUDA graph per cycle, captured
+ * once per (cfl, cfl_flux)); res_out
  * (host, ncycles entries, or NULL) receives the RMS over fine cells of R_rho / A before each cycle.
  * Synchronises the stream; GKS_ENONPHYS if the fine state is non-physical afterwards. */
 gks_status gks_steady_cycles(gks_steady* s, int ncycles, double cfl, double cfl_flux, double* res_out);
-/* The fine-level local steps (host, ncell) and residual (host, [4][ncell]) of the current state,
- * second order unless first_order; either output may be NULL.  Synchronises. */
+/* The fine-level local steps (host, ncell) and steady residual (Section 4; host, [4][ncell]) of the
+ * current state, second order unless first_order; either output may be NULL.  Synchronises. */
 gks_status gks_steady_residual(gks_steady* s, double cfl_flux, int first_order, double* dt_out, double* R_out);
+/* Copy out the fine-grid state (Section 2, Eq. moment1). */
 gks_status gks_steady_get_state(gks_steady* s, void* W_out, int layout, int memspace, int dtype);
+/* Free the steady solver; the message of its last failing call (no paper counterpart). */
 gks_status gks_steady_destroy(gks_steady* s);
 const char* gks_steady_last_error(const gks_steady* s);
 
-/* Copy out the current state in the requested layout and type. */
+/* Copy out the current state W (Section 2, Eq. moment1) in the requested layout and type. */
 gks_status gks_get_state(gks_handle* h, void* W_out, int layout, int memspace, int dtype);
 
-/* Copy in the turbulence fields, one value per cell in [z][y][x] order: f1 = k (or mu_t),
+/* Copy in the turbulence fields (Section 3, Eqs. tauttrivial and tautchen; Section 4,
+ * Eq. tautchenadjusted), one value per cell in [z][y][x] order: f1 = k (or mu_t),
  * f2 = epsilon or omega (NULL for GKS_TURB_MUT).  With GKS_TURB_KOMEGA_TRANSPORT these are the
  * initial k and omega, stored as rho k and rho omega with the density of the current state: call
  * it after gks_set_state (which clears transported fields); GKS_EINVAL otherwise. */
@@ -230,42 +261,53 @@ typedef struct {
   int diffusion;       /* 0: no diffusion (tests) */
 } gks_komega;
 
-/* Wilcox's 2006 values: alpha 13/25, beta0 0.0708, sigma 1/2, sigma* 3/5, sigma_do 1/8, C_lim 7/8;
+/* The closure coefficients of the k-omega model the paper uses (Section 4: Wilcox 2006), Wilcox's
+ * values: alpha 13/25, beta0 0.0708, sigma 1/2, sigma* 3/5, sigma_do 1/8, C_lim 7/8;
  * omega_floor 1e-12, sources and diffusion on.  Errors: GKS_EINVAL for a null pointer. */
 gks_status gks_komega_defaults(gks_komega* c);
 
-/* Replace the closure coefficients of a GKS_TURB_KOMEGA_TRANSPORT handle (the defaults are set at
+/* Replace the closure coefficients (Section 4, the k-omega model) of a GKS_TURB_KOMEGA_TRANSPORT handle (the defaults are set at
  * gks_create).  Takes effect from the next gks_step.  Errors: GKS_EINVAL (null, other model). */
 gks_status gks_set_komega(gks_handle* h, const gks_komega* c);
 
-/* Copy out the transported k and omega (GKS_TURB_KOMEGA_TRANSPORT), one value per cell. */
+/* Copy out the transported k and omega (Section 4; GKS_TURB_KOMEGA_TRANSPORT), one value per cell. */
 gks_status gks_get_turbulence(gks_handle* h, void* k_out, void* omega_out, int memspace, int dtype);
 
-/* Steady solver handles with GKS_TURB_KOMEGA_TRANSPORT: replace the closure coefficients (defaults gks_komega_defaults;
+/* Steady solver handles with GKS_TURB_KOMEGA_TRANSPORT (Section 4): replace the closure coefficients (defaults gks_komega_defaults;
  * effective from the next cycle), and copy out k = rho k / rho, omega = rho omega / rho of the
  * current state (either output may be NULL; synchronises).  GKS_EINVAL for other handles. */
 gks_status gks_steady_set_komega(gks_steady* s, const gks_komega* c);
 gks_status gks_steady_get_turbulence(gks_steady* s, void* k_out, void* omega_out, int memspace, int dtype);
 
-/* CFL time step of the current state: dt = cfl / max_cells sum_d (|U_d| + c) / dx_d. Synchronises. */
+/* CFL time step of the current state: dt = cfl / max_cells sum_d (|U_d| + c) / dx_d (no paper
+ * counterpart: the paper's solver is steady and gives no time-step rule; this is the library's
+ * reading).  Synchronises;
+ * GKS_ENONPHYS if the sticky status is set. */
 gks_status gks_compute_dt(gks_handle* h, double cfl, double* dt_out);
 
-/* Advance nsteps steps.  dt > 0: fixed step; dt <= 0: the CFL step of the current state each step.
+/* Advance nsteps steps of the finite-volume scheme with the time-integrated interface fluxes of
+ * Eq. fluxesf (Section 2: Eqs. intermediatestate, initialf0, eqlgform, resultingf; relaxation time of
+ * Eqs. relaxation time, taua and the turbulent part of Sections 3 and 4), W <- W - sum_d dF_d/dx_d.
+ * dt > 0: fixed step; dt <= 0: the CFL step of the current state each step.
  * t_end > 0: the step that would pass t_end is clamped to reach it and later steps do nothing.
  * Asynchronous; the last step also accumulates the residual norms read by gks_residual. */
 gks_status gks_step(gks_handle* h, double dt, double cfl, int nsteps, double t_end);
 
-/* Time and number of steps taken since the last gks_set_state (or gks_set_time).  Synchronises. */
+/* Time and number of steps taken since the last gks_set_state (or gks_set_time); no paper
+ * counterpart.  Synchronises. */
 gks_status gks_get_time(gks_handle* h, double* t, long long* steps);
 
-/* Set the solution time (restart from a checkpoint: gks_set_state then gks_set_time). */
+/* Set the solution time (restart from a checkpoint: gks_set_state then gks_set_time); no paper
+ * counterpart. */
 gks_status gks_set_time(gks_handle* h, double t);
 
-/* Norms of (W^{n+1} - W^n)/dt of the last step of the last gks_step call, per variable (nv each):
+/* Residual of the last step (the rate of change that the steady solver of Section 4 drives to zero):
+ * norms of (W^{n+1} - W^n)/dt of the last step of the last gks_step call, per variable (nv each):
  * L2 = sqrt(mean of squares), L-infinity, and total = sum of W times cell volume.  Synchronises. */
 gks_status gks_residual(gks_handle* h, double* l2, double* linf, double* total);
 
-/* Sticky status bits (bit 0: non-physical state) and the last time step used.  Synchronises. */
+/* Sticky status bits (bit 0: non-physical state) and the last time step used (no paper
+ * counterpart).  Synchronises. */
 gks_status gks_status_word(gks_handle* h, unsigned int* bits, double* last_dt);
 
 /* Rarefaction diagnostic per cell (Eqs. tautautilde, tautilde): eps = (mu/p + tau_t) |div U|,
@@ -276,23 +318,27 @@ gks_status gks_get_rarefaction(gks_handle* h, void* eps_out, int memspace, int d
 gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtype);
 
 /* Device time of the step kernels launched by gks_step while timing is enabled (CUDA events on
- * the handle's stream around each launch; graphs are not used while timing). */
+ * the handle's stream around each launch; graphs are not used while timing); no paper counterpart. */
 gks_status gks_enable_timing(gks_handle* h, int enable);
 gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
 
-/* Tile shape of the handle's step kernel.  2D FP32 handles choose among six shapes (variants
- * 0..5: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 cells; 512 threads per CTA for 32x31 and 64x27, 256
- * otherwise), 1D handles among 256, 31 and 63 cells per CTA, on their first gks_step: each is timed
+/* Tile shape of the handle's step kernel (no paper counterpart).  2D GKS_FP32 and GKS_FP32_ACC64 handles choose among six
+ * shapes (variants 0..5: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 cells; 512 threads per CTA for 32x31
+ * and 64x27, 256 otherwise), 3D ones among three (16x8x4, 16x8x2, 8x8x4), 1D handles among 256, 31 and
+ * 63 cells per CTA (the rarefaction option runs the first shape of each), on their first gks_step: each is timed
  * on the step about to be taken and the fastest kept (and reused by later handles of the same grid);
  * the environment variable GKS_TILE_VARIANT forces one (0..5 in 2D, 0..2 in 1D).  The result does
  * not depend on it beyond rounding. */
 gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz);
 
+/* Free the handle and everything it owns (no paper counterpart: resource management). */
 gks_status gks_destroy(gks_handle* h);
+/* Message of the last failing call on a handle (no paper counterpart). */
 const char* gks_last_error(const gks_handle* h);
 
-/* Stateless evaluation of nfaces interface fluxes (Eq. fluxesf) on the device, for testing and
- * for callers with their own reconstruction.  faces: device array of nfaces records of
+/* Stateless evaluation of nfaces interface fluxes (Eq. fluxesf; Eqs. intermediatestate, initialf0,
+ * eqlgform, resultingf, relaxation time, taua) on the device, for testing and for callers with their
+ * own reconstruction.  rarefaction: GKS_RAR_DT or GKS_RAR_TAUHAT (see gks_turb).  faces: device array of nfaces records of
  * gks_face_record_len(dim) doubles, in the frame of the face (velocity 0 = normal):
  *   wl[nv] wr[nv] cl[nv] cr[nv] sl[nv] sr[nv] tl[dim-1][nv] tr[dim-1][nv] dxl dxr tau_t
  * (reconstructed states, adjacent cell averages, normal slopes, tangential slopes, centre-to-face
@@ -300,19 +346,19 @@ const char* gks_last_error(const gks_handle* h);
  * tau_out: device, nfaces total relaxation times, or NULL.  precision GKS_FP64 or GKS_FP32.
  * Asynchronous on cuda_stream. */
 int gks_face_record_len(int dim);
-gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, double gamma, double mu,
-                         double C_a, double dt, const double* faces, long nfaces, double* F_out,
+gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, int rarefaction, double gamma,
+                         double mu, double C_a, double dt, const double* faces, long nfaces, double* F_out,
                          double* tau_out, void* cuda_stream);
 
-/* Operation count of one interface flux as the device code is written (no GPU needed): counts[0..5]
+/* Operation count of one interface flux (Eq. fluxesf) as the device code is written (no GPU needed): counts[0..5]
  * = additions/subtractions, multiplications, divisions, square roots, exponentials, erfc.
  * with_recon adds the face values of the MUSCL reconstruction from the cell slopes.  Operations on
  * literal 0 or 1 are not counted.  Used to state the algorithmic FLOPs behind the roofline figures. */
 int gks_face_op_count(int dim, int expand, int with_recon, long long* counts);
-/* The same count for the per-cell part of the reconstruction: the limited (van Leer) slope of every
+/* The same count for the per-cell part of the reconstruction (Section 4): the limited (van Leer) slope of every
  * variable along every axis, computed once per cell and step. */
 int gks_cell_op_count(int dim, long long* counts);
-/* The same count for the face values of a higher-order reconstruction (recon = GKS_RECON_MUSCL3 or
+/* The same count for the face values of a higher-order reconstruction (Section 4; recon = GKS_RECON_MUSCL3 or
  * GKS_RECON_WENO5): both sides, every variable, and the two one-sided normal slopes of a face.
  * Returns nonzero for other values. */
 int gks_recon_op_count(int dim, int recon, long long* counts);
@@ -339,7 +385,8 @@ int gks_recon_op_count(int dim, int recon, long long* counts);
 gks_status gks_cfl_dt_noalloc(int dim, const int* n, const double* h, double gamma, const double* W,
                               double cfl, double* dt_out, void* cuda_stream);
 
-/* ---- Serving: continuous batching of independent solves on one GPU ----------------------------
+/* ---- Serving: continuous batching of independent solves on one GPU (no paper counterpart: each
+ * solve is the time-accurate scheme of gks_step, Eq. fluxesf) ----------------------------------
  * A server owns a device arena.  Submitted requests wait in arrival order until the arena has room
  * for their state (footprint admission); admitted solves stay resident and advance together, one
  * persistent batch launch per step per group (1D, 2D directional, 2D multi-dimensional), in chunks
@@ -361,32 +408,34 @@ typedef struct {
   int nsteps;            /* steps to run */
 } gks_request;
 
-/* precision GKS_FP32 (float-pair state) or GKS_FP64; arena_bytes of device memory for resident
+/* Serving (no paper counterpart).  precision GKS_FP32 (float-pair state) or GKS_FP64; arena_bytes of device memory for resident
  * solves; max_cells per request; chunk_steps a multiple of 6.  Starts the worker thread. */
 gks_status gks_server_create(int precision, size_t arena_bytes, long max_cells, int chunk_steps, void* cuda_stream,
                              gks_server** out);
-/* Queue a request with its initial primitive state (host, SoA (rho, u.., p), copied).  GKS_ENOMEM if
+/* Serving (no paper counterpart): queue a request with its initial primitive state (host, SoA (rho, u.., p), copied).  GKS_ENOMEM if
  * the request can never fit in the arena. */
 gks_status gks_server_submit(gks_server* s, const gks_request* q, const double* prim, long long* id_out);
-/* done = 1 once finished; then W_out (host, SoA conservative, or NULL) receives the final state and
+/* Serving (no paper counterpart): done = 1 once finished; then W_out (host, SoA conservative, or NULL) receives the final state and
  * latency_s the time from submission to completion. */
 gks_status gks_server_poll(gks_server* s, long long id, int* done, double* W_out, double* latency_s);
-/* Block until every submitted request has finished (GKS_ETIMEOUT after timeout_s seconds). */
+/* Serving (no paper counterpart): block until every submitted request has finished (GKS_ETIMEOUT
+ * after timeout_s seconds). */
 gks_status gks_server_wait_all(gks_server* s, double timeout_s);
-/* Completed requests, latency percentiles (seconds), completions per second since the first
- * submission, and seconds the GPU spent in batch steps. */
+/* Serving (no paper counterpart): completed requests, latency percentiles (seconds), completions per
+ * second since the first submission, and seconds the GPU spent in batch steps; destroy a server. */
 gks_status gks_server_stats(gks_server* s, long long* completed, double* p50_s, double* p99_s, double* solves_per_s,
                             double* busy_s);
 gks_status gks_server_destroy(gks_server* s);
 
 /* Measured FMA throughput of the current device for FP32 and FP64 (independent FMA chains on every
- * SM, CUDA events), in TFLOP/s: context for the arithmetic roofline.  Synchronises the device. */
+ * SM, CUDA events), in TFLOP/s: context for the arithmetic roofline (no paper counterpart).
+ * Synchronises the device. */
 gks_status gks_probe_alu(double* fp32_tflops, double* fp64_tflops);
-/* The FP32 chains of gks_probe_alu with the paired single-precision FMA (two FMAs per thread
+/* No paper counterpart: the FP32 chains of gks_probe_alu with the paired single-precision FMA (two FMAs per thread
  * instruction, sm_100 and later), in TFLOP/s: whether pairing raises the FP32 rate or only halves the
  * issue slots it takes.  Same conditions and errors as gks_probe_alu. */
 gks_status gks_probe_alu_packed(double* fp32x2_tflops);
-/* Conversion throughput of the current device, double -> float and float -> double, in units of 1e9
+/* No paper counterpart: conversion throughput of the current device, double -> float and float -> double, in units of 1e9
  * conversions per second (independent chains on every SM, CUDA events): context for the
  * double-state form (GKS_FP32_ACC64), which converts the staged state and the increments.  Same
  * conditions and errors as gks_probe_alu. */

@@ -69,3 +69,53 @@ def test_null_handles_are_rejected_without_touching_the_device():
     assert L.gks_set_nodes(None, None, 0) == EINVAL
     assert L.gks_get_turbulence(None, None, None, 0, 0) == EINVAL
     assert L.gks_komega_defaults(None) == EINVAL
+
+
+def comment_before(text, pos):
+    """The last /* ... */ block that ends before pos."""
+    end = text.rfind("*/", 0, pos)
+    start = text.rfind("/*", 0, end)
+    return text[start:end + 2] if start >= 0 and end >= 0 else ""
+
+
+def test_every_call_cites_its_passage_or_has_no_counterpart():
+    """Each declaration's comment names the section or equation of the paper that defines the
+    operation, or says that the paper has no counterpart (resource management, diagnostics)."""
+    text = open(os.path.join(ROOT, "include", "gks.h")).read()
+    bad = []
+    for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(gks_[a-z0-9_]+)\s*\(", text, re.M):
+        c = re.sub(r"\s*\n\s*\*?\s*", " ", comment_before(text, m.start()))
+        if not re.search(r"Section \d|Eqs?\. [a-z]|Table \d|no paper counterpart|paper has no counterpart", c, re.I):
+            bad.append(m.group(1))
+    assert not bad, bad
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Offsets and sizes of the boundary's structs, compiled from include/gks.h with the host compiler,
+    equal those of the ctypes binding (gks_turb carries the rarefaction option)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    from paper_1302_2132_gb300 import gks
+    fields = {"gks_turb": (gks._Turb, ["model", "C_mu", "beta_star", "C_a", "rarefaction"]),
+              "gks_gas": (gks._Gas, ["gamma", "mu", "prandtl", "T_wall"]),
+              "gks_numerics": (gks._Num, ["limiter", "expand", "precision", "abar_mode", "reconstruction"]),
+              "gks_grid": (gks._Grid, ["dim", "n", "lo", "hi", "dx", "bc", "bc_data", "wake_cut"])}
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "gks.h"', "int main(void) {"]
+    for st, (_, names) in fields.items():
+        src.append('printf("%s %%zu\\n", sizeof(%s));' % (st, st))
+        for n in names:
+            src.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st, n, st, n))
+    src.append('printf("GKS_RAR_TAUHAT %d\\n", GKS_RAR_TAUHAT); return 0; }')
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    out = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, (cls, names) in fields.items():
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for n in names:
+            assert int(out["%s.%s" % (st, n)]) == getattr(cls, n).offset, (st, n)
+    assert int(out["GKS_RAR_TAUHAT"]) == gks.RAREFACTION["tauhat"]
