@@ -3,11 +3,15 @@
 Workload (one bench step): 1024 x 1024 cells on [0, 2 pi)^2, periodic; random-phase solenoidal
 velocity with E(k) ~ k^4 exp(-2 (k/8)^2) at turbulent Mach 0.3, rho = 1, p = 1/gamma; k-epsilon
 turbulent relaxation time from seeded log-normal k, epsilon fields; multi-dimensional expansion,
-van Leer MUSCL; FP32 flux arithmetic with the state accumulated in a float pair (48-bit) form;
-200 CFL time steps (CFL 0.5) from the initial state.  Inputs are synthetic (seed 1302).
+van Leer MUSCL; FP32 flux arithmetic with the state accumulated in IEEE double (FP32 bulk, FP64
+accumulation); 200 CFL time steps (CFL 0.5) from the initial state.  Inputs are synthetic (seed
+1302).  The same workload with the state kept as a float pair (about 48 bits) is timed the same way
+and reported beside it (`float_pair_form`).
 
-Metric: interface-flux evaluations per second (2 faces per cell per time step in 2D); cell updates
-per second are reported beside it.  `value` is timed with CUDA events on the library's stream with
+Metric: interface-flux evaluations per second (distinct faces: 2 per cell per time step on the
+periodic 2D grid); cell updates per second are reported beside it.  The step kernel's time per
+launch (roofline) is taken inside the timed region, from the end of the state copy-in to the end of
+the last time step (the step kernels run in their captured graphs), divided by the steps.  `value` is timed with CUDA events on the library's stream with
 the inputs resident in HBM; `e2e` through the same C ABI from pinned host buffers, host<->device
 copies included.  The L2 cache is flushed (a 256 MiB write) between bench steps; within one bench
 step the 200 time steps work on a state that fits in L2, as the algorithm allows.
@@ -29,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "turb2d_1024_keps_multid_fp32"
+WORKLOAD = "turb2d_1024_keps_multid_fp32_acc64"
 N = 1024
 NSTEPS = 200
 CFL = 0.5
@@ -145,8 +149,10 @@ def make_workload(name, precision):
     if name == "turb2d_1024":
         spec = workload_inputs()
         return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
-                                       expand="multid"), nsteps=NSTEPS, t_end=0.0, precision=precision or "fp32",
-                    desc="2D decaying turbulence 1024^2, k-epsilon tau_t, multi-D, 200 CFL steps")
+                                       expand="multid"), nsteps=NSTEPS, t_end=0.0,
+                    precision=precision or "fp32_acc64",
+                    desc="2D decaying turbulence 1024^2, k-epsilon tau_t, multi-D, 200 CFL steps, FP32 flux with "
+                         "the state accumulated in IEEE double")
     if name == "turb2d_1024_transport":
         spec = dict(workload_inputs())
         # k-omega transport from the same initial fields: omega = eps / (C_mu k), so that nu_t = k/omega
@@ -235,11 +241,13 @@ TRAFFIC_PER_LAUNCH = {("turb2d_1024_keps_multid_fp32", 3): 44.319232e6,
                       ("turb2d_1024_keps_multid_fp32", 5): 43.990528e6}
 
 
-def faces_of(n):
+def faces_of(n, bc=None):
+    """Distinct faces of a grid: n_d + 1 per grid line along axis d, n_d on a periodic axis (the wrap
+    face is one face)."""
     D = len(n)
     tot = 0
     for d in range(D):
-        f = n[d] + 1
+        f = n[d] + (0 if bc is not None and bc[d][0] == 0 else 1)
         for e in range(D):
             if e != d:
                 f *= n[e]
@@ -435,7 +443,7 @@ def run_ours(args):
     spec = wl["spec"]
     D = spec["dim"]
     n = tuple(spec["n"])
-    faces_per_step = faces_of(n)
+    faces_per_step = faces_of(n, spec["bc"] if wl.get("nodes") is None else None)
     cells = int(np.prod(n))
     solver = gks.Solver(D, n, spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"), precision=wl["precision"],
                         reconstruction=args.reconstruction, **wl["kw"])
@@ -471,16 +479,20 @@ def run_ours(args):
             solver.step(nsteps=1, cfl=CFL, t_end=wl["t_end"])
             nsteps += 1
 
-    def one_step():
+    def one_step(mid=None):
         solver.set_state(prim_dev, layout="soa_prim")
         if transport:
             solver.set_turbulence(f1, f2)
+        if mid is not None:
+            mid.record(stream)
         solver.step(nsteps=nsteps, cfl=CFL, t_end=wl["t_end"])
 
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     # ---- timed region: K bench steps, each bracketed by events on the library stream ----------
+    # A third event after the state copy-in marks the start of the time steps: the step kernels are
+    # timed as the bench runs them, inside the captured graphs.
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -492,25 +504,20 @@ def run_ours(args):
     for _ in range(args.steps):
         flush.fill_(1)
         stream.wait_stream(torch.cuda.current_stream())
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        one_step()
+        one_step(em)
         e1.record(stream)
-        evs.append((e0, e1))
+        evs.append((e0, em, e1))
         torch.cuda.current_stream().wait_stream(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    # ---- dominant kernel: the fused step kernel, timed launch by launch (events on its stream) ----
-    solver.enable_timing(True)
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        one_step()
-    kms, klaunch = solver.kernel_time()
-    solver.enable_timing(False)
+    ms = sum(a.elapsed_time(c) for a, _, c in evs)
+    # the time steps of each bench step (step kernels in their graphs; with a separate transport
+    # kernel, both), per time step
+    kms = sum(b.elapsed_time(c) for _, b, c in evs)
+    klaunch = nsteps * args.steps
     clock_info = clocks.stop() if clocks else None
     # sanity of the result: finite state, conservation monitor
     _, _, total = solver.residual()
@@ -556,7 +563,7 @@ def run_ours(args):
     prec_name = {"fp64": "PREC_F64", "fp32": "PREC_F32", "fp32_acc64": "PREC_F32D"}[wl["precision"]]
     lanes = 2 if fp64 else 128  # FP64 runs at 1/64 of the FP32 rate on this part
     peak = 152 * lanes * 2 * 2.070e9 / 1e12
-    workload_name = (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32"
+    workload_name = (WORKLOAD if args.workload == "turb2d_1024" and wl["precision"] == "fp32_acc64"
                      else "%s_%s" % (args.workload, wl["precision"]))
     if args.reconstruction != "muscl2":
         workload_name += "_" + args.reconstruction
@@ -612,6 +619,10 @@ def run_ours(args):
         "total_mass": float(total[0]),
     }
     line["config"]["tile"] = tile_info
+    if args.workload == "turb2d_1024" and args.precision is None and args.reconstruction == "muscl2":
+        # the float-pair form of the same workload, timed the same way: a second, labelled figure
+        line["float_pair_form"] = time_other_form(args, wl, "fp32", faces_per_step, nsteps, ops_per_launch, peak,
+                                                  dev, flush)
     if not args.no_cpu_baseline and args.workload == "turb2d_1024":
         line["cpu_baseline"] = cpu_baseline(budget_s=15.0)
     if not args.no_serving and args.workload == "turb2d_1024":
@@ -623,6 +634,46 @@ def run_ours(args):
     sys.stdout.flush()
     if world > 1:
         dist.destroy_process_group()
+
+
+def time_other_form(args, wl, precision, faces_per_step, nsteps, ops_per_launch, peak, dev, flush):
+    """The same workload in another arithmetic form, timed as the headline is (K bench steps after W
+    warm-up steps, events on the library stream, L2 flushed between bench steps)."""
+    import torch
+    from paper_1302_2132_gb300 import gks
+    spec = wl["spec"]
+    s = gks.Solver(spec["dim"], tuple(spec["n"]), spec["bc"], dx=spec["dx"], precision=precision, **wl["kw"])
+    prim = torch.tensor(spec["prim"].ravel(), device=dev)
+    f1 = torch.tensor(spec["f1"].ravel(), device=dev)
+    f2 = torch.tensor(spec["f2"].ravel(), device=dev)
+    s.set_turbulence(f1, f2)
+    st = s.stream
+    for _ in range(args.warmup):
+        s.set_state(prim, layout="soa_prim")
+        s.step(nsteps=nsteps, cfl=CFL)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        st.wait_stream(torch.cuda.current_stream())
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        s.set_state(prim, layout="soa_prim")
+        em.record(st)
+        s.step(nsteps=nsteps, cfl=CFL)
+        e1.record(st)
+        evs.append((e0, em, e1))
+        torch.cuda.current_stream().wait_stream(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, _, c in evs)
+    kus = sum(b.elapsed_time(c) for _, b, c in evs) * 1e3 / (nsteps * args.steps)
+    tile = s.tile_shape()
+    s.close()
+    return {"precision": precision, "state_accumulation": "float pair (hi+lo), about 48 significant bits",
+            "value": faces_per_step * nsteps * args.steps / (ms / 1e3), "unit": "face_flux_evals/s",
+            "ms_per_step": ms / args.steps, "avg_launch_us": kus,
+            "roofline_frac": ops_per_launch / (kus * 1e-6) / 1e12 / peak,
+            "kernel": "step_kernel<2, PREC_F32, multid>", "tile": {"variant": tile[0], "cells": list(tile[1:3])}}
 
 
 # per-cell operations of the k-omega transport step (hand count of the kernel: per axis about 190 --
@@ -758,18 +809,18 @@ def fp64_loop(reqs):
 
 def serving_summary(count):
     """Serving form on the seeded stream: capacity (burst of 400), a Poisson stream at 0.8x capacity,
-    a 2x overload of 1000 requests, and the plain FP64 per-solve loop on the first 40 requests."""
+    a 2x overload of 1000 requests, and the plain FP64 per-solve loop on the first 400 requests."""
     reqs = serving_requests(count)
     burst = serve_stream(reqs[:400], 0.0, 1)
     capacity = burst["completed"] / burst["wall_s"]
     steady = serve_stream(reqs, 0.8 * capacity, 2)
     over = serve_stream(reqs[:1000], 2.0 * capacity, 3)
-    base = fp64_loop(reqs[:40])
+    base = fp64_loop(reqs[:400])
     return {"metric": "serving solves/sec, p50/p99", "unit": "solves/s", "requests": len(reqs),
             "solves_per_s": steady["solves_per_s"], "p50_s": steady["p50_s"], "p99_s": steady["p99_s"],
             "offered_rate": steady["offered_rate"], "capacity_solves_per_s": capacity,
             "overload_2x": {k: over[k] for k in ("solves_per_s", "p50_s", "p99_s", "completed")},
-            "fp64_per_solve_loop_solves_per_s": base["solves_per_s"],
+            "fp64_per_solve_loop_solves_per_s": base["solves_per_s"], "fp64_per_solve_loop_requests": base["requests"],
             "batched_fp32_over_fp64_loop": capacity / base["solves_per_s"],
             "mix": "50% 1D (256-4096 cells), 50% 2D (64^2-512^2); Sod, Riemann quadrant, periodic turbulence; "
                    "50-500 steps; seed 4000; Poisson arrivals"}
@@ -837,7 +888,7 @@ def run_serving(args):
     capacity = burst["completed"] / burst["wall_s"]
     steady = serve_stream(reqs, 0.8 * capacity, 2)
     over = serve_stream(reqs[:1000], 2.0 * capacity, 3)
-    sample = reqs[:40]
+    sample = reqs[:400]
     base = fp64_loop(sample)
     line = {"metric": "serving solves/sec, p50/p99", "value": steady["solves_per_s"], "unit": "solves/s",
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
