@@ -184,10 +184,17 @@ int tiles_for(const gks_handle* h, int variant) {
 // k-omega transport fused into the body-fitted step (MUSCL-2, FP64 or the FP32 float-pair form);
 // other combinations run the step and the transport kernel one after the other.
 bool fused_transport(const gks_handle* h) {
-  return h->curv && h->transport && h->recon == GKS_RECON_MUSCL2 && h->prec != PREC_F32D;
+  return h->curv && h->transport && h->recon == GKS_RECON_MUSCL2 && h->prec != PREC_F32D && !h->base.g.rar;
 }
 
 void launch_step_variant(gks_handle* h, const StepArgs& A, int variant) {
+  if (h->base.g.rar) {  // the rarefaction option: one tile shape per grid kind
+    if (h->curv)
+      launch_curv_step_rar(h->prec, A, h->cg, h->multid, h->stream);
+    else
+      launch_step_rar(h->D, h->prec, h->multid, A, tiles_for(h, 0), h->stream);
+    return;
+  }
   if (fused_transport(h)) {
     launch_curv_step_transport(h->prec, A, h->cg, variant, h->multid, h->stream);
     return;
@@ -428,6 +435,7 @@ std::mutex g_tuned_mutex;
 // Tile variants the autotuner tries for a handle (variant indices of tile_shape).
 std::vector<int> tile_candidates(const gks_handle* h) {
   std::vector<int> c;
+  if (h->base.g.rar) return {h->curv ? 2 : 0};  // the tile the rarefaction kernels are built for
   if (h->curv) {
     // the tiles the reconstruction and fused-transport kernels are built for
     if (h->recon != GKS_RECON_MUSCL2 || fused_transport(h)) return {0, 2};
@@ -447,6 +455,7 @@ std::vector<int> tile_candidates(const gks_handle* h) {
 }
 
 int n_variants(const gks_handle* h) {
+  if (h->base.g.rar) return 1;
   if (h->curv) return (h->recon != GKS_RECON_MUSCL2 || fused_transport(h)) ? 2 : kCurvVariants;
   if (h->recon != GKS_RECON_MUSCL2) return (int)tile_candidates(h).size();
   if (h->D == 1) return kTileVariants1D;
@@ -458,7 +467,10 @@ int n_variants(const gks_handle* h) {
 gks_status autotune(gks_handle* h) {
   h->tuned = true;
   const int nvar = n_variants(h);
-  if (nvar == 1) return GKS_OK;
+  if (nvar == 1) {
+    h->tile_variant = tile_candidates(h)[0];
+    return GKS_OK;
+  }
   const char* force = std::getenv("GKS_TILE_VARIANT");
   if (force) {
     const int v = std::atoi(force);
@@ -552,6 +564,10 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   if (num->abar_mode != GKS_ABAR_TIMEINT && num->abar_mode != GKS_ABAR_T0) return bad(GKS_EINVAL, "abar_mode");
   const int model = turb ? turb->model : GKS_TURB_NONE;
   if (model < GKS_TURB_NONE || model > GKS_TURB_KOMEGA_TRANSPORT) return bad(GKS_EINVAL, "turbulence model");
+  const int rar = turb ? turb->rarefaction : GKS_RAR_DT;
+  if (rar != GKS_RAR_DT && rar != GKS_RAR_TAUHAT) return bad(GKS_EINVAL, "rarefaction");
+  if (rar == GKS_RAR_TAUHAT && num->reconstruction != GKS_RECON_MUSCL2)
+    return bad(GKS_EUNSUPPORTED, "the rarefaction option is built for MUSCL2");
   h->transport = model == GKS_TURB_KOMEGA_TRANSPORT;
   for (int d = 0; d < D; ++d) {
     for (int s = 0; s < 2; ++s) {
@@ -600,6 +616,8 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess && D >= 2) e = prepare_step_acc64();
+    if (e == cudaSuccess) e = prepare_step_rar();
+    if (e == cudaSuccess && D == 2) e = prepare_curv_rar();
     if (e == cudaSuccess) e = prepare_komega();
     if (e == cudaSuccess) e = prepare_step_muscl3();
     if (e == cudaSuccess) e = prepare_step_weno5();
@@ -709,6 +727,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   g.limiter = num->limiter;
   g.abar_t0 = num->abar_mode == GKS_ABAR_T0;
   g.wake_cut = grid->wake_cut;
+  g.rar = rar == GKS_RAR_TAUHAT;
   set_consts(g);
   h->base.f1 = h->f1;
   h->base.f2 = h->f2;
@@ -1112,6 +1131,8 @@ gks_status gks_set_nodes(gks_handle* h, const double* nodes, int memspace) {
   if (!h || !nodes) return fail(h, GKS_EINVAL, "null argument");
   if (memspace != GKS_MEM_HOST && memspace != GKS_MEM_DEVICE) return fail(h, GKS_EINVAL, "memspace");
   if (h->D != 2) return fail(h, GKS_EUNSUPPORTED, "curvilinear grids are built in 2D");
+  if (h->base.g.rar && h->prec == PREC_F32D)
+    return fail(h, GKS_EUNSUPPORTED, "the rarefaction option on body-fitted grids is built for GKS_FP64 and GKS_FP32");
   DeviceGuard dg(h->dev);
   GKS_CK(h, cudaStreamSynchronize(h->stream));
   free_curv(h);
@@ -1225,16 +1246,17 @@ int gks_face_record_len(int dim) {
   return 6 * nv + 2 * (dim - 1) * nv + 3;
 }
 
-gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, double gamma, double mu, double C_a,
-                         double dt, const double* faces, long nfaces, double* F_out, double* tau_out,
+gks_status gks_face_flux(int dim, int precision, int expand, int abar_mode, int rarefaction, double gamma, double mu,
+                         double C_a, double dt, const double* faces, long nfaces, double* F_out, double* tau_out,
                          void* cuda_stream) {
   if (dim < 1 || dim > 3 || !faces || !F_out || nfaces < 0) return GKS_EINVAL;
   if (precision != GKS_FP64 && precision != GKS_FP32) return GKS_EINVAL;
+  if (rarefaction != GKS_RAR_DT && rarefaction != GKS_RAR_TAUHAT) return GKS_EINVAL;
   if (!(gamma > 1.0) || 2.0 / (gamma - 1.0) - dim < 0.0 || !(dt > 0.0)) return GKS_EINVAL;
   if (nfaces == 0) return GKS_OK;
   launch_face_flux(dim, precision == GKS_FP64 ? 0 : 1, dim > 1 && expand == GKS_EXPAND_MULTID,
-                   abar_mode == GKS_ABAR_T0, gamma, mu, C_a, dt, faces, nfaces, F_out, tau_out,
-                   (cudaStream_t)cuda_stream);
+                   abar_mode == GKS_ABAR_T0, rarefaction == GKS_RAR_TAUHAT, gamma, mu, C_a, dt, faces, nfaces, F_out,
+                   tau_out, (cudaStream_t)cuda_stream);
   if (cudaGetLastError() != cudaSuccess) return GKS_ECUDA;
   return GKS_OK;
 }

@@ -56,6 +56,11 @@ void launch_curv_step_transport(int prec, const StepArgs& A, const CurvGeom& G, 
 void launch_curv_residual_recon(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
 void launch_curv_step_recon(int prec, int recon, const StepArgs& A, const CurvGeom& G, int variant, bool multid,
                             cudaStream_t s);
+// The rarefaction option (gks_turb.rarefaction = GKS_RAR_TAUHAT), MUSCL-2, FP64 or FP32: the time step on
+// the 16 x 11 tile and the steady residual.
+cudaError_t prepare_curv_rar();
+void launch_curv_step_rar(int prec, const StepArgs& A, const CurvGeom& G, bool multid, cudaStream_t s);
+void launch_curv_residual_rar(int prec, const StepArgs& A, const CurvGeom& G, const SteadyArgs& SA, cudaStream_t s);
 void curv_tile_shape(int variant, int* x, int* y);
 constexpr int kCurvVariants = 3;
 void launch_curv_rate(int prec, const StepArgs& A, const CurvGeom& G, cudaStream_t s);

@@ -193,7 +193,8 @@ __host__ __device__ constexpr int halo_for(int rc) { return rc == 2 ? 3 : 2; }
 // the tile and its halo are staged, each face also evaluates the transport fluxes of rho k and
 // rho omega with its mass flux, and each cell's update advances them (the transport kernel's
 // arithmetic) into A.RKout, A.RWout.
-template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false>
+// RAR: the rarefaction option (eps = tau/tauhat in the faces' time coefficients).
+template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false, bool RAR = false>
 __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / CurvTile<V>::T)
     curv_step_kernel(const __grid_constant__ StepArgs A, const __grid_constant__ CurvGeom G,
                      const __grid_constant__ SteadyArgs SA) {
@@ -495,9 +496,9 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         Ls = L / win;
       }
       if (MD && !fo)
-        face_flux<2, R, true>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+        face_flux<2, R, true, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
       else
-        face_flux<2, R, false>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+        face_flux<2, R, false, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
       const R L_ = Ls;
       Fs[l] = F[0] * L_;
       Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   }
 }
 
-template <int PREC, int V, int MODE = 0, bool MD = false, int RC = 0, bool TR = false>
+template <int PREC, int V, int MODE = 0, bool MD = false, int RC = 0, bool TR = false, bool RAR = false>
 void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const SteadyArgs& SA = SteadyArgs{}) {
   using TG = CurvTileGeom<V, halo_for(RC)>;
   const int nt = ((A.g.n[0] + TG::X - 1) / TG::X) * ((A.g.n[1] + TG::Y - 1) / TG::Y);
@@ -685,11 +686,12 @@ void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const St
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, curv_step_kernel<PREC, V, MODE, MD, RC, TR>, TG::T, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, curv_step_kernel<PREC, V, MODE, MD, RC, TR, RAR>, TG::T,
+                                                  smem);
     resident = per_sm * nsm > 0 ? per_sm * nsm : -1;
   }
   if (MODE == 1 || nt > resident) {
-    curv_step_kernel<PREC, V, MODE, MD, RC, TR><<<nt, TG::T, smem, s>>>(A, G, SA);
+    curv_step_kernel<PREC, V, MODE, MD, RC, TR, RAR><<<nt, TG::T, smem, s>>>(A, G, SA);
     return;
   }
   cudaLaunchConfig_t cfg = {};
@@ -702,13 +704,13 @@ void launch_fused(const StepArgs& A, const CurvGeom& G, cudaStream_t s, const St
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, curv_step_kernel<PREC, V, MODE, MD, RC, TR>, A, G, SA);
+  cudaLaunchKernelEx(&cfg, curv_step_kernel<PREC, V, MODE, MD, RC, TR, RAR>, A, G, SA);
 }
 
-template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false>
+template <int PREC, int V, int MODE, bool MD, int RC = 0, bool TR = false, bool RAR = false>
 cudaError_t prepare_one() {
   using TG = CurvTileGeom<V, halo_for(RC)>;
-  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE, MD, RC, TR>,
+  return cudaFuncSetAttribute(curv_step_kernel<PREC, V, MODE, MD, RC, TR, RAR>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)TG::template smem_bytes<typename PrecT<PREC>::R, TR>());
 }

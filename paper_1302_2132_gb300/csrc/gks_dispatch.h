@@ -30,6 +30,9 @@ constexpr int kTileVariants3D = 3;
 // double-state form (FP32 flux, IEEE double state): 2D variants 1 to 5, 3D variants 1 and 2
 cudaError_t prepare_step_acc64();
 void launch_step_acc64_variant(int D, int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
+// the rarefaction option (MUSCL-2, default tile of each dimension, every precision)
+cudaError_t prepare_step_rar();
+void launch_step_rar(int D, int prec, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 // 1D tile variants 1 and 2 (narrow tiles for small grids)
 cudaError_t prepare_step_d1_variants();
 void launch_step_d1_variant(int variant, int prec, const StepArgs& A, int nblocks, cudaStream_t s);
@@ -52,7 +55,7 @@ bool launch_step_weno5(int D, int prec, bool multid, int variant, const StepArgs
 cudaError_t prepare_komega();
 void launch_komega(int D, int prec, const KOmegaArgs& K, cudaStream_t s);
 
-void launch_face_flux(int D, int prec, bool multid, int abar_t0, double gamma, double mu, double C_a,
+void launch_face_flux(int D, int prec, bool multid, int abar_t0, int rar, double gamma, double mu, double C_a,
                       double dt, const double* faces, long nfaces, double* F, double* tau, cudaStream_t s);
 
 }  // namespace gks

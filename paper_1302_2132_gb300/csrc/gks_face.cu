@@ -4,7 +4,7 @@
 
 namespace gks {
 
-template <int D, class R, bool MULTID>
+template <int D, class R, bool MULTID, bool RAR>
 __global__ void __launch_bounds__(128) face_kernel(int abar_t0, double gamma, double mu, double C_a, double dt,
                                                    const double* faces, long nfaces, double* Fout, double* tout) {
   constexpr int nv = D + 2;
@@ -36,41 +36,44 @@ __global__ void __launch_bounds__(128) face_kernel(int abar_t0, double gamma, do
   gas.mu = (R)mu;
   gas.C_a = (R)C_a;
   R F[nv], tau;
-  face_flux<D, R, MULTID>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, tau_t, (R)dt, gas, abar_t0, F, &tau);
+  face_flux<D, R, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, tau_t, (R)dt, gas, abar_t0, F, &tau);
 #pragma unroll
   for (int v = 0; v < nv; ++v) Fout[f * nv + v] = (double)F[v];
   if (tout) tout[f] = (double)tau;
 }
 
 template <int D, class R, bool M>
-static void go(int abar_t0, double gamma, double mu, double C_a, double dt, const double* faces, long n,
+static void go(bool rar, int abar_t0, double gamma, double mu, double C_a, double dt, const double* faces, long n,
                double* F, double* tau, cudaStream_t s) {
   const int threads = 128;
   const long blocks = (n + threads - 1) / threads;
-  face_kernel<D, R, M><<<(unsigned)blocks, threads, 0, s>>>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau);
+  if (rar)
+    face_kernel<D, R, M, true><<<(unsigned)blocks, threads, 0, s>>>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau);
+  else
+    face_kernel<D, R, M, false><<<(unsigned)blocks, threads, 0, s>>>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau);
 }
 
-void launch_face_flux(int D, int prec, bool multid, int abar_t0, double gamma, double mu, double C_a,
+void launch_face_flux(int D, int prec, bool multid, int abar_t0, int rar, double gamma, double mu, double C_a,
                       double dt, const double* faces, long n, double* F, double* tau, cudaStream_t s) {
-  const bool f64 = prec == 0;
+  const bool f64 = prec == 0, r = rar != 0;
   if (D == 1) {
-    if (f64) go<1, double, false>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
-    else go<1, float, false>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+    if (f64) go<1, double, false>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+    else go<1, float, false>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
   } else if (D == 2) {
     if (f64) {
-      if (multid) go<2, double, true>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
-      else go<2, double, false>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      if (multid) go<2, double, true>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      else go<2, double, false>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
     } else {
-      if (multid) go<2, float, true>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
-      else go<2, float, false>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      if (multid) go<2, float, true>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      else go<2, float, false>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
     }
   } else {
     if (f64) {
-      if (multid) go<3, double, true>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
-      else go<3, double, false>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      if (multid) go<3, double, true>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      else go<3, double, false>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
     } else {
-      if (multid) go<3, float, true>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
-      else go<3, float, false>(abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      if (multid) go<3, float, true>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
+      else go<3, float, false>(r, abar_t0, gamma, mu, C_a, dt, faces, n, F, tau, s);
     }
   }
 }

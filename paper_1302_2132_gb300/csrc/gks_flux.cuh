@@ -496,6 +496,94 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
   }
 }
 
+// The time coefficients with the degree of rarefaction eps in place of tau/dt (Eqs. tautautilde,
+// rarefactionkepsilon, epsilonkomega): Eq. fkepsilon with alpha = eps (1 - e^{-1/eps}) and
+// beta = e^{-1/eps} (Eq. alphabetakepsilon with the corrected beta), in the T0..T5 form:
+//   T0 = dt (1 - alpha), T1 = dt tau (2 alpha - 1 - beta), T2 = dt (dt/2 - tau (1 - alpha)),
+//   T3 = dt alpha, T4 = dt tau (beta - 2 alpha), T5 = -dt tau alpha, Dn = dt tau (1 - alpha),
+// so r1 = (2 alpha - 1 - beta)/(1 - alpha), r4 = (beta - 2 alpha)/(1 - alpha), r5 = -alpha/(1 - alpha).
+// eps = tau/dt gives time_coeffs.  For eps > 1 (x = 1/eps < 1) alpha = phi1(x), 1 - alpha = x phi2,
+// 2 alpha - 1 - beta = -x^2 (phi2 - 2 phi3), from the cancellation-free series.
+template <class T>
+GKS_FN void time_coeffs_hat(T dt, T tau, T eps, T* Tc, T& r1, T& r4, T& r5) {
+  T a, one_a, c1, c4;
+  if (eps > T(1)) {
+    const T x = g_rcp(eps);
+    T p1, p2, p3, e;
+    phi_series(x, p1, p2, p3, e);
+    a = p1;
+    one_a = x * p2;
+    c1 = -x * x * (p2 - T(2) * p3);
+    c4 = e - T(2) * p1;
+  } else {
+    const T beta = eps > T(0) ? g_exp(-g_rcp(eps)) : T(0);
+    a = eps * (T(1) - beta);
+    one_a = T(1) - a;
+    c1 = T(2) * a - T(1) - beta;
+    c4 = beta - T(2) * a;
+  }
+  const T dtau = dt * tau;
+  Tc[0] = dt * one_a;
+  Tc[1] = dtau * c1;
+  Tc[2] = dt * (T(0.5) * dt - tau * one_a);
+  Tc[3] = dt * a;
+  Tc[4] = dtau * c4;
+  Tc[5] = -dtau * a;
+  const T i1 = g_rcp(one_a);
+  r1 = c1 * i1;
+  r4 = c4 * i1;
+  r5 = -a * i1;
+}
+
+// The density row <u^k gamma (a . psi)> of amom alone.
+template <int D, class T>
+GKS_FN T amom_rho(const T* u, const Trans<D, T>& t, int k, int tg, const T* a) {
+  constexpr int NB = D + 1;
+  const T hE = T(0.5) * a[D + 1];
+  const T SA0 = a[0] * u[k] + a[1] * u[k + 1] + hE * u[k + 2];
+  T g0 = tg < 0 ? t.m1[0] : t.m2[1 + tg][0], c1 = T(0);
+#pragma unroll
+  for (int b = 1; b < NB; ++b) c1 += a[b == D ? D + 1 : 1 + b] * (tg < 0 ? t.m1[b] : t.m2[1 + tg][b]);
+  return SA0 * g0 + u[k] * c1;
+}
+
+// |D rho| = |d_t rho + U_n d_n rho| at the face for the rarefaction option (Eqs. tautautilde,
+// tautilde): d_t rho = -rho0 (<abar_l . psi u>_{u>0} + <abar_r . psi u>_{u<0} + <bbar . psi v>) from
+// the t = 0 compatibility condition of the equilibrium part, d_n rho the mean of the density slopes
+// (w0 - W_j)/dxl and (W_{j+1} - w0)/dxr.  Slopes and moments of g0 as in face_flux.
+template <int D, class T, bool MULTID>
+GKS_FN T face_drho(const Maxw<D, T>& g0, const T* w0, const T* cl, const T* cr, const T (*tl)[D + 2],
+                   const T (*tr)[D + 2], T dxl, T dxr, T i0, T bK, T K) {
+  constexpr int nv = D + 2;
+  const T dn = T(0.5) * (g_div(w0[0] - cl[0], dxl) + g_div(cr[0] - w0[0], dxr));
+  Trans<D, T> t0;
+  transverse<D, T>(g0, K, t0);
+  T oF[7], oP[7], half[7], r[nv], ab[nv];
+  u_full<D, T>(g0, oF);
+  u_half<D, T>(g0, T(1), oP);
+  const T fl = g_div(i0, dxl), fr = g_div(i0, dxr);
+#pragma unroll
+  for (int m = 0; m < nv; ++m) r[m] = (w0[m] - cl[m]) * fl;
+  slope<D, T>(g0, bK, r, ab);
+  T x1 = amom_rho<D, T>(oP, t0, 1, -1, ab);
+#pragma unroll
+  for (int m = 0; m < nv; ++m) r[m] = (cr[m] - w0[m]) * fr;
+  slope<D, T>(g0, bK, r, ab);
+#pragma unroll
+  for (int n = 0; n < 7; ++n) half[n] = oF[n] - oP[n];
+  x1 += amom_rho<D, T>(half, t0, 1, -1, ab);
+  if (MULTID) {
+#pragma unroll
+    for (int q = 0; q < D - 1; ++q) {
+#pragma unroll
+      for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (tl[q][m] + tr[q][m]) * i0;
+      slope<D, T>(g0, bK, r, ab);
+      x1 += amom_rho<D, T>(oF, t0, 0, q, ab);
+    }
+  }
+  return g_abs(-g0.rho * x1 + g0.U[0] * dn);
+}
+
 // One face.  Inputs in the face frame:
 //   wl, wr   reconstructed states; cl, cr cell averages of the two cells; sl, sr normal slopes;
 //   tl, tr   tangential slopes (multi-dimensional expansion only); dxl, dxr centre-to-face distances;
@@ -506,7 +594,9 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
 // right one, and the two halves and the full line of the equilibrium g0) is visited once, adding
 // both its part of the right-hand side of the Abar equation and its part of the flux; only the
 // Abar term of the flux waits for Abar.
-template <int D, class T, bool MULTID>
+// RAR: the rarefaction option -- the degree of rarefaction eps = tau/tauhat, tauhat = rho0/|D rho|
+// (capped at 1e30), replaces tau/dt inside the time coefficients (Eq. epsilonkomega).
+template <int D, class T, bool MULTID, bool RAR = false>
 GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const T* sl, const T* sr,
                       const T (*tl)[D + 2], const T (*tr)[D + 2], T dxl, T dxr, T tau_t, T dt, const Gas<T>& gas,
                       int abar_t0, T* F, T* tau_out) {
@@ -536,7 +626,13 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
   const T tau = g_div(gas.mu, p0) + tau_t + g_div(gas.C_a * g_abs(pr - pl), pr + pl) * dt;
   *tau_out = tau;
   T Tc[6], r1, r4, r5;
-  time_coeffs<T>(dt, tau, Tc, r1, r4, r5);
+  if constexpr (RAR) {
+    const T drho = face_drho<D, T, MULTID>(g0, w0, cl, cr, tl, tr, dxl, dxr, g_rcp(g0.rho), bK, K);
+    const T eps = drho > T(1e-30) * g0.rho ? g_div(tau * drho, g0.rho) : tau * T(1e-30);
+    time_coeffs_hat<T>(dt, tau, eps, Tc, r1, r4, r5);
+  } else {
+    time_coeffs<T>(dt, tau, Tc, r1, r4, r5);
+  }
   if (abar_t0) {
     r1 = T(-1);
     r4 = r5 = T(0);

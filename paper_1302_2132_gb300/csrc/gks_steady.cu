@@ -451,6 +451,8 @@ void residual(gks_steady* s, int l, const void* Win, const void* forcing, double
   SA.recon = l == 0 ? s->recon : GKS_RECON_MUSCL2;
   if (SA.recon != GKS_RECON_MUSCL2)
     launch_curv_residual_recon(s->prec, A, lev.G, SA, s->stream);
+  else if (A.g.rar)
+    launch_curv_residual_rar(s->prec, A, lev.G, SA, s->stream);
   else
     launch_curv_residual(s->prec, A, lev.G, SA, s->stream);
 }
@@ -612,6 +614,9 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
   if (num->precision != GKS_FP64 && num->precision != GKS_FP32) return GKS_EUNSUPPORTED;
   const int model_in = turb ? turb->model : GKS_TURB_NONE;
   if (model_in < GKS_TURB_NONE || model_in > GKS_TURB_KOMEGA_TRANSPORT) return GKS_EUNSUPPORTED;
+  const int rar = turb ? turb->rarefaction : GKS_RAR_DT;
+  if (rar != GKS_RAR_DT && rar != GKS_RAR_TAUHAT) return GKS_EINVAL;
+  if (rar == GKS_RAR_TAUHAT && num->reconstruction != GKS_RECON_MUSCL2) return GKS_EUNSUPPORTED;
   // with transport the levels take tau_t from the fields k, omega of each cycle's start
   const int model = model_in == GKS_TURB_KOMEGA_TRANSPORT ? (int)GKS_TURB_KOMEGA : model_in;
   if (levels < 1 || levels > 6) return GKS_EINVAL;
@@ -653,7 +658,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     }
     s->own_stream = true;
   }
-  if (prepare_curv() != cudaSuccess || prepare_curv_recon() != cudaSuccess ||
+  if (prepare_curv() != cudaSuccess || prepare_curv_recon() != cudaSuccess || prepare_curv_rar() != cudaSuccess ||
       cudaFuncSetAttribute(lusgs_kernel<PREC_F64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)lusgs_smem<double, 32>()) != cudaSuccess ||
       cudaFuncSetAttribute(lusgs_kernel<PREC_F32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -747,6 +752,7 @@ gks_status gks_steady_create(const gks_grid* grid, const gks_gas* gas, const gks
     g.mu = gas->mu;
     g.T_wall = gas->T_wall;
     g.C_a = turb ? turb->C_a : 0.0;
+    g.rar = rar == GKS_RAR_TAUHAT;
     g.C_mu = turb ? turb->C_mu : 0.09;
     g.beta_star = turb ? turb->beta_star : 0.09;
     g.turb_model = model;
@@ -989,6 +995,8 @@ gks_status gks_steady_residual(gks_steady* s, double cfl_flux, int first_order, 
   SA.tau = f.G.tau;
   if (SA.recon != GKS_RECON_MUSCL2)
     launch_curv_residual_recon(s->prec, A, f.G, SA, s->stream);
+  else if (A.g.rar)
+    launch_curv_residual_rar(s->prec, A, f.G, SA, s->stream);
   else
     launch_curv_residual(s->prec, A, f.G, SA, s->stream);
   GKS_SCK(s, cudaGetLastError());

@@ -113,6 +113,7 @@ struct DevGrid {
   int turb_model, limiter, abar_t0;
   int turb_cons;  // the turbulence fields hold rho k and rho omega (k-omega transport), not k and omega
   int wake_cut;   // 2D C-grids: the first and last wake_cut cells of the j-lo side form a wake cut
+  int rar;        // the rarefaction option (eps = tau/tauhat in the time coefficients): kernels built with RAR
   // the constants above in each arithmetic type, filled by set_consts on the host (kernels read
   // them from the parameter bank instead of converting)
   Consts<float> kf;
@@ -683,8 +684,9 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
   }
 }
 
-// One tile of one step: every thread of the CTA calls it with the same arguments.
-template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
+// One tile of one step: every thread of the CTA calls it with the same arguments.  RAR: the time
+// coefficients of the faces take the degree of rarefaction tau/tauhat (gks_turb.rarefaction).
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2, bool RAR = false>
 __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   using R = typename PrecT<PREC>::R;
   using S = typename PrecT<PREC>::S;
@@ -994,8 +996,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         }
         const R tau_t = R(0.5) * (taus[rl] + taus[rc]);
         R F[nv], tau;
-        face_flux<D, R, MULTID>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
-                                g.abar_t0, F, &tau);
+        face_flux<D, R, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
+                                     g.abar_t0, F, &tau);
         Fs[0 * G::NF + f] = F[0];
 #pragma unroll
         for (int k = 0; k < D; ++k) Fs[(1 + perm[k]) * G::NF + f] = F[1 + k];
@@ -1143,10 +1145,10 @@ template <int D, int V = 0> constexpr int min_blocks(int prec) {
   return prec != PREC_F64 ? 512 / Tile<D, V>::T : 1;
 }
 
-template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2, bool RAR = false>
 __global__ void __launch_bounds__(Tile<D, V>::T, min_blocks<D, V>(PREC))
     step_kernel(const __grid_constant__ StepArgs A) {
-  step_tile<D, PREC, MULTID, V, RECON>(A, blockIdx.x);
+  step_tile<D, PREC, MULTID, V, RECON, RAR>(A, blockIdx.x);
 }
 
 // ---- batches of independent solves --------------------------------------------------------------
@@ -1199,21 +1201,21 @@ cudaError_t prepare_batch() {
                               (int)sm);
 }
 
-template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2, bool RAR = false>
 void launch_step(const StepArgs& A, int nblocks, cudaStream_t s) {
   using R = typename PrecT<PREC>::R;
   const size_t sm =
       TileGeom<D, V, halo_of(RECON)>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
-  step_kernel<D, PREC, MULTID, V, RECON><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
+  step_kernel<D, PREC, MULTID, V, RECON, RAR><<<nblocks, Tile<D, V>::T, sm, s>>>(A);
 }
 
-template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2>
+template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2, bool RAR = false>
 cudaError_t prepare_step() {
   using R = typename PrecT<PREC>::R;
   const size_t sm =
       TileGeom<D, V, halo_of(RECON)>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
-  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V, RECON>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sm);
+  return cudaFuncSetAttribute(step_kernel<D, PREC, MULTID, V, RECON, RAR>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 }  // namespace gks

@@ -20,6 +20,7 @@ LIMITER = {"minmod": 0, "vanleer": 1}
 EXPAND = {"directional": 0, "multid": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
 ABAR = {"timeint": 0, "t0": 1}
+RAREFACTION = {"dt": 0, "tauhat": 1}
 RECON = {"muscl2": 0, "muscl3": 1, "weno5": 2}
 LAYOUT = {"soa_cons": 0, "aos_cons": 1, "soa_prim": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -47,7 +48,7 @@ class _Gas(ctypes.Structure):
 
 
 class _Turb(ctypes.Structure):
-    _fields_ = [("model", _I), ("C_mu", _D), ("beta_star", _D), ("C_a", _D)]
+    _fields_ = [("model", _I), ("C_mu", _D), ("beta_star", _D), ("C_a", _D), ("rarefaction", _I)]
 
 
 class _Num(ctypes.Structure):
@@ -119,7 +120,7 @@ def load():
     L.gks_cell_op_count.restype = _I
     L.gks_recon_op_count.argtypes = [_I, _I, ctypes.POINTER(ctypes.c_longlong)]
     L.gks_recon_op_count.restype = _I
-    L.gks_face_flux.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _V, ctypes.c_long, _V, _V, _V]
+    L.gks_face_flux.argtypes = [_I, _I, _I, _I, _I, _D, _D, _D, _D, _V, ctypes.c_long, _V, _V, _V]
     for name in ("gks_create", "gks_set_state", "gks_get_state", "gks_set_turbulence", "gks_compute_dt",
                  "gks_step", "gks_get_time", "gks_set_time", "gks_residual", "gks_status_word",
                  "gks_get_rarefaction", "gks_get_tau_turb", "gks_enable_timing", "gks_kernel_time",
@@ -153,7 +154,7 @@ def komega_defaults(**over):
 
 
 def _structs(dim, n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model, C_mu, beta_star, C_a, limiter, expand,
-             precision, abar_mode, reconstruction, wake_cut=0):
+             precision, abar_mode, reconstruction, wake_cut=0, rarefaction="dt"):
     """gks_grid, gks_gas, gks_turb, gks_numerics and the arrays they point to."""
     keep = []
     g = _Grid()
@@ -177,7 +178,8 @@ def _structs(dim, n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model, C_m
                 g.bc_data[d][s] = a.ctypes.data_as(_PD)
     gas = _Gas(gamma, mu, 1.0, T_wall)
     tm = TURB[turb_model] if isinstance(turb_model, str) else int(turb_model)
-    turb = _Turb(tm, C_mu, beta_star, C_a)
+    turb = _Turb(tm, C_mu, beta_star, C_a,
+                 RAREFACTION[rarefaction] if isinstance(rarefaction, str) else int(rarefaction))
     num = _Num(LIMITER[limiter] if isinstance(limiter, str) else int(limiter),
                EXPAND[expand] if isinstance(expand, str) else int(expand),
                PRECISION[precision] if isinstance(precision, str) else int(precision),
@@ -193,7 +195,8 @@ class Solver:
 
     def __init__(self, dim, n, bc, dx=None, lo=None, hi=None, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0,
                  turb_model="none", C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", expand="multid",
-                 precision="fp64", abar_mode="timeint", reconstruction="muscl2", wake_cut=0, stream=None):
+                 precision="fp64", abar_mode="timeint", reconstruction="muscl2", wake_cut=0, stream=None,
+                 rarefaction="dt"):
         import torch
         L = load()
         self.dim, self.nv = dim, dim + 2
@@ -201,7 +204,7 @@ class Solver:
         self.ncell = int(np.prod(self.n))
         g, gas, turb, num, self._keep = _structs(dim, self.n, bc, dx, lo, hi, bc_data, gamma, mu, T_wall, turb_model,
                                                  C_mu, beta_star, C_a, limiter, expand, precision, abar_mode,
-                                                 reconstruction, wake_cut)
+                                                 reconstruction, wake_cut, rarefaction)
         self.precision = num.precision
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = _V()
@@ -424,7 +427,7 @@ def face_record_len(dim):
 
 
 def face_flux(dim, faces, dt, gamma=1.4, mu=1e-5, C_a=0.0, precision="fp64", expand="multid",
-              abar_mode="timeint", stream=None):
+              abar_mode="timeint", stream=None, rarefaction="dt"):
     """Evaluate interface fluxes for face records held in a CUDA float64 tensor
     [nfaces, face_record_len(dim)]; returns (F [nfaces, dim+2], tau [nfaces]) as CUDA tensors."""
     import torch
@@ -433,7 +436,8 @@ def face_flux(dim, faces, dt, gamma=1.4, mu=1e-5, C_a=0.0, precision="fp64", exp
     F = torch.empty((nf, dim + 2), dtype=torch.float64, device=faces.device)
     tau = torch.empty((nf,), dtype=torch.float64, device=faces.device)
     s = stream if stream is not None else torch.cuda.current_stream(faces.device)
-    st = load().gks_face_flux(dim, PRECISION[precision], EXPAND[expand], ABAR[abar_mode], gamma, mu, C_a, dt,
+    st = load().gks_face_flux(dim, PRECISION[precision], EXPAND[expand], ABAR[abar_mode], RAREFACTION[rarefaction],
+                              gamma, mu, C_a, dt,
                               _V(faces.data_ptr()), nf, _V(F.data_ptr()), _V(tau.data_ptr()),
                               _V(s.cuda_stream))
     if st != OK:
@@ -447,7 +451,7 @@ class SteadySolver:
 
     def __init__(self, n, bc, nodes, levels=4, bc_data=None, gamma=1.4, mu=1e-5, T_wall=1.0, turb_model="none",
                  C_mu=0.09, beta_star=0.09, C_a=0.0, limiter="vanleer", precision="fp64", lusgs_tile=16, wake_cut=0,
-                 expand="directional", stream=None, reconstruction="muscl2"):
+                 expand="directional", stream=None, reconstruction="muscl2", rarefaction="dt"):
         import torch
         L = load()
         self.n = (int(n[0]), int(n[1]))
@@ -456,7 +460,7 @@ class SteadySolver:
         dx = [np.ones(self.n[0]), np.ones(self.n[1])]
         g, gas, turb, num, self._keep = _structs(2, self.n, bc, dx, None, None, bc_data, gamma, mu, T_wall, turb_model,
                                                  C_mu, beta_star, C_a, limiter, expand, precision, "timeint",
-                                                 reconstruction, wake_cut)
+                                                 reconstruction, wake_cut, rarefaction)
         nodes = _f64(nodes)
         assert nodes.size == 2 * (self.n[0] + 1) * (self.n[1] + 1)
         self.stream = stream if stream is not None else torch.cuda.Stream()

@@ -12,9 +12,10 @@ inputs of this library):
                     solenoidal velocity with E(k) ~ k^4 exp(-2 (k/k0)^2) scaled to a turbulent Mach
                     number, rho = 1, p = 1/gamma; log-normal k and epsilon fields from 8 Fourier modes
   riemann_quadrant  2D four-state Riemann problem with seeded states
-  near_vacuum       strongly expanding low-pressure states (the first-order fallback of MUSCL)
+  near_vacuum       expansion kinks in a smooth background (the first-order fallback of MUSCL)
   shock_boundary_layer  Mach 2.85 flat-plate boundary layer under an oblique shock on a
-                    wall-clustered grid, with log-law k-omega profiles
+                    wall-clustered grid, with log-law k-omega profiles (and the wall corner of the
+                    full-size grid, shock_boundary_layer_crop)
   compression_corner  Mach 2.85 boundary layer over a ramp of alpha degrees on a body-fitted,
                     wall-clustered channel grid (nodes given), log-law k-omega profiles
   naca0012_case     C-grid round a NACA 0012 section with a wake cut (transonic free stream)
@@ -119,21 +120,41 @@ def riemann_quadrant(n, seed):
     return dict(dim=2, n=(n, n), dx=[np.full(n, 1.0 / n)] * 2, bc=[[1, 1], [1, 1]], prim=prim)
 
 
-def near_vacuum(n, dim, seed, p_ref=0.02, du=1.2):
-    """A strongly expanding, low-pressure state on [0,1]^dim with transmissive boundaries (the kind
-    of data where a MUSCL reconstruction of the conservative variables can give a face state with
-    negative pressure): each velocity component increases along its own axis by seeded random steps
-    in [0, du] per cell (centred on zero), rho in [0.5, 1.5] and p in [p_ref, 1.5 p_ref] drawn per
-    cell."""
+def near_vacuum(n, dim, seed, kinks=4, a=1.0, p_lo=0.02, p_hi=0.5):
+    """Expansion kinks in a smooth background on [0,1]^dim with transmissive boundaries: the data where a
+    MUSCL reconstruction of the conservative variables gives a face state with negative pressure,
+    while every other face keeps a moderate Mach number.  Background: rho = 1 + 0.1 r, each velocity
+    component 0.1 r, p = p_hi (r seeded uniform in [-1, 1] per cell).  Each kink, at a seeded cell
+    away from the boundaries, along a seeded axis a: the velocity component along that axis is -a, 0,
+    +a on the three cells through it, the pressure p_hi, p_lo, p_hi.  With a = 1, p_lo = 0.02 and
+    p_hi = 0.5 the reconstructed states on both faces of the middle cell have p = 0.4 (p_lo/0.4 - a^2/8)
+    < 0 (the energy is an extremum there, so its limited slope is zero, while the momentum slope is
+    a)."""
     rng = np.random.default_rng(seed)
     shape = (n,) * dim
     prim = np.zeros((dim + 2,) + shape)
-    prim[0] = rng.uniform(0.5, 1.5, shape)
-    for a in range(dim):
-        steps = rng.uniform(0.0, du, shape)
-        u = np.cumsum(steps, axis=dim - 1 - a)  # axis a of the grid is array axis dim - 1 - a
-        prim[1 + a] = u - u.mean()
-    prim[dim + 1] = p_ref * rng.uniform(1.0, 1.5, shape)
+    prim[0] = 1.0 + 0.1 * rng.uniform(-1.0, 1.0, shape)
+    for d in range(dim):
+        prim[1 + d] = 0.1 * rng.uniform(-1.0, 1.0, shape)
+    prim[dim + 1] = p_hi
+    used = set()
+    k = 0
+    while k < kinks:
+        c = tuple(int(v) for v in rng.integers(3, n - 3, dim))  # array index (z, y, x order reversed below)
+        ax = int(rng.integers(0, dim))  # grid axis
+        arr_ax = dim - 1 - ax
+        cells = []
+        for off in (-1, 0, 1):
+            q = list(c)
+            q[arr_ax] += off
+            cells.append(tuple(q))
+        if any(max(abs(q[e] - u[e]) for e in range(dim)) <= 3 for q in cells for u in used):
+            continue  # keep kinks four cells apart
+        for q, u, p in zip(cells, (-a, 0.0, a), (p_hi, p_lo, p_hi)):
+            prim[(1 + ax,) + q] = u
+            prim[(dim + 1,) + q] = p
+            used.add(q)
+        k += 1
     return dict(dim=dim, n=shape, dx=[np.full(n, 1.0 / n)] * dim, bc=[[1, 1]] * dim, prim=prim)
 
 
@@ -258,6 +279,20 @@ def shock_boundary_layer(nx, ny, M=2.85, delta=0.1, theta_deg=24.0, Re_delta=1.6
 # ------------------------------------------------------------------------------------------------
 # Curvilinear (body-fitted) 2D grids: node arrays nodes[n1 + 1, n0 + 1, 2] = (x, y), right-handed
 # ------------------------------------------------------------------------------------------------
+def shock_boundary_layer_crop(nx, ny, full=(1024, 384)):
+    """The wall corner of the full-size shock / boundary-layer workload: its first nx columns and ny
+    rows (the same cell sizes, so the same wall-clustered first rows, time step and physical time
+    per step), inflow rows and wall as in the full grid, outflow on the right, and the full grid's
+    initial state just above the crop as Dirichlet data on top."""
+    f = shock_boundary_layer(*full)
+    prim = np.ascontiguousarray(f["prim"][:, :ny, :nx])
+    inflow = np.ascontiguousarray(f["bc_prim"][0][0][:ny])
+    top = np.ascontiguousarray(f["prim"][:, ny, :nx].T)
+    return dict(dim=2, n=(nx, ny), dx=[f["dx"][0][:nx].copy(), f["dx"][1][:ny].copy()], bc=[[3, 4], [2, 3]],
+                bc_prim=[[inflow, None], [None, top]], prim=prim, T_wall=f["T_wall"], mu=f["mu"],
+                f1=np.ascontiguousarray(f["f1"][:ny, :nx]), f2=np.ascontiguousarray(f["f2"][:ny, :nx]))
+
+
 def uniform_nodes(n0, n1, lx=1.0, ly=1.0):
     """The nodes of a uniform rectilinear grid on [0, lx] x [0, ly]."""
     X, Y = np.meshgrid(np.linspace(0.0, lx, n0 + 1), np.linspace(0.0, ly, n1 + 1), indexing="xy")

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1302_2132_gb300 import inputs
-from tests.cases import gpu_solver, oracle_case, rel_err_per_var
+from tests.cases import gpu_solver, max_rel_elementwise, oracle_case
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +65,7 @@ def cases():
 def test_fp64_curvilinear_step_matches_oracle(name, multid):
     spec, kw, steps = cases()[name]
     s, Wg, Wo = curv_both(spec, steps, multid=multid, **kw)
-    assert np.all(rel_err_per_var(Wg, Wo, 4) < 1e-12)
+    assert np.all(max_rel_elementwise(Wg, Wo, 4, 1e-2) < 1e-12)
     s.close()
 
 
@@ -92,7 +92,7 @@ def test_full_size_corner_grid_matches_oracle():
     degrees with k-omega: FP64 two steps element by element, FP32 ten steps in L1."""
     spec = corner_spec(528, 136)
     s, Wg, Wo = curv_both(spec, 2, turb_model=3, C_a=0.5)
-    assert np.all(rel_err_per_var(Wg, Wo, 4) < 1e-12)
+    assert np.all(max_rel_elementwise(Wg, Wo, 4, 1e-2) < 1e-12)
     s.close()
     s, Wg, Wo = curv_both(spec, 10, turb_model=3, C_a=0.5, precision="fp32", check_dt=False)
     n = Wo.size // 4
@@ -208,5 +208,5 @@ def test_every_tile_shape_matches_oracle(monkeypatch, variant):
     spec = corner_spec(70, 37)
     s, Wg, Wo = curv_both(spec, 3, turb_model=3, C_a=0.5)
     assert s.tile_shape()[0] == int(variant)
-    assert np.all(rel_err_per_var(Wg, Wo, 4) < 1e-12)
+    assert np.all(max_rel_elementwise(Wg, Wo, 4, 1e-2) < 1e-12)
     s.close()

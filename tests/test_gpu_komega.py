@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1302_2132_gb300 import inputs
-from tests.cases import gpu_solver, oracle_case, rel_err_per_var
+from tests.cases import gpu_solver, max_rel_elementwise, oracle_case
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +70,7 @@ def test_fp64_transport_matches_oracle(name):
     mu = spec.get("mu", 1e-5)
     s, Wg, Wo, kg, wg, ko, wo = run_both(spec, steps, k, om, C_a=C_a, mu=mu)
     nv = spec["dim"] + 2
-    assert np.all(rel_err_per_var(Wg, Wo, nv) < 1e-12)
+    assert np.all(max_rel_elementwise(Wg, Wo, nv, 1e-2) < 1e-12)
     assert rel(kg, ko) < 1e-12 and rel(wg, wo) < 1e-12
     # the fields did evolve
     assert rel(ko, k) > 1e-6 and rel(wo, om) > 1e-6

@@ -1,8 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the oracle.
 
-Tolerances: the FP64 path matches the oracle to 1e-12 relative per step (normwise per variable, the
-accuracy required of the double-precision path); interface fluxes to 1e-12 per face.  The FP32
-forms are held to L1(rho) <= 1e-5 relative after a run.
+Tolerances: the FP64 path matches the oracle to 1e-12 relative per step, element by element
+(|a - b| <= 1e-12 max(|b|, 1e-2 max|b_v|) for every cell and variable v; the floor at 1% of the
+variable's largest value keeps components that pass through zero, such as a momentum, at the scale
+of their variable); interface fluxes to 1e-12 per face.  The FP32 forms are held to L1(rho) <= 1e-5
+relative after a run, and their face fluxes to the single-precision accuracy stated in each test.
 """
 import math
 
@@ -10,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import gpu_solver, oracle_case, rel_err_per_var
+from cases import gpu_solver, max_rel_elementwise, oracle_case, rel_err_per_var
 from paper_1302_2132_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -88,6 +90,29 @@ def test_face_flux_fp32_close_to_oracle(D):
     assert np.median(errs) < 2e-6 and max(errs) < 1e-4, (np.median(errs), max(errs))
 
 
+@pytest.mark.parametrize("D", [1, 2, 3])
+@pytest.mark.parametrize("x", [1e-6, 1e-4, 1e-2, 80.0, 300.0])
+def test_face_flux_fp32_at_extreme_dt_over_tau(D, x):
+    """x = dt/tau at the ends of its range: near-free transport (tau >> dt, the series branch of the
+    time coefficients in single precision) and near-equilibrium (tau << dt).  mu = C_a = 0, so tau is
+    the face's turbulent relaxation time and x = dt/tau_t exactly."""
+    rng = np.random.default_rng(3000 + D + int(1e3 * math.log10(x) + 7000))
+    dt = 1e-3
+    recs, faces = random_faces(rng, D, 200, dt)
+    recs[:, -1] = dt / x
+    F, tau = gks.face_flux(D, torch.tensor(recs, device="cuda"), dt, mu=0.0, C_a=0.0, precision="fp32")
+    F, tau = F.cpu().numpy(), tau.cpu().numpy()
+    errs = []
+    for i, f in enumerate(faces):
+        f.tau_t = dt / x
+        Fo, dg = oracle.face_flux(D, GAMMA, 0.0, 0.0, dt, f, diag=True)
+        assert abs(dg.tau - dt / x) <= 1e-15 * dg.tau
+        errs.append(np.linalg.norm(F[i] - Fo) / np.linalg.norm(Fo))
+    errs = np.array(errs)
+    print("D=%d x=%g: median %.2e max %.2e" % (D, x, np.median(errs), errs.max()))
+    assert np.median(errs) < 5e-6 and errs.max() < 1e-4, (np.median(errs), errs.max())
+
+
 def step_both(spec, nsteps=1, cfl=0.5, **kw):
     prec = kw.pop("precision", "fp64")
     s = gpu_solver(spec, precision=prec, **kw)
@@ -132,11 +157,11 @@ def test_one_step_fp64_matches_oracle(name):
     spec, kw = config_cases()[name]
     s, c, Wg, Wo, res = step_both(spec, nsteps=1, **kw)
     nv = spec["dim"] + 2
-    err = rel_err_per_var(Wg, Wo, nv)
+    err = max_rel_elementwise(Wg, Wo, nv, 1e-2)
     assert np.all(err < 1e-12), err
     # the increment itself agrees to a few digits fewer than the state (cancellation in W^1 - W^0)
     W0 = c.prim_to_cons(spec["prim"].ravel())
-    inc = rel_err_per_var(Wg - W0, Wo - W0, nv)
+    inc = max_rel_elementwise(Wg - W0, Wo - W0, nv, 1e-2)
     assert np.all(inc < 1e-9), inc
     l2, linf, tot = s.residual()
     assert np.allclose(l2, res[0], rtol=1e-9, atol=1e-300)
@@ -155,7 +180,7 @@ def test_sod_full_run_fp64_matches_oracle():
     t, steps = s.time()
     W, to, so, st = c.run(c.prim_to_cons(spec["prim"].ravel()), 100000, cfl=0.5, t_end=0.2, nthreads=8)
     assert abs(t - 0.2) < 1e-14 and abs(to - 0.2) < 1e-14
-    err = rel_err_per_var(s.get_state(), W, 3)
+    err = max_rel_elementwise(s.get_state(), W, 3, 1e-2)
     assert np.all(err < 1e-10), err
     s.close()
 
@@ -366,7 +391,7 @@ def test_1d_tile_variants_match_oracle(monkeypatch, variant):
     spec = inputs.sod_1d(400)
     s, c, Wg, Wo, res = step_both(spec, nsteps=3, C_a=1.0, limiter=1, mu=1e-5)
     assert s.tile_shape()[:2] == (int(variant), {"0": 256, "1": 31, "2": 63}[variant])
-    assert np.all(rel_err_per_var(Wg, Wo, 3) < 1e-12)
+    assert np.all(max_rel_elementwise(Wg, Wo, 3, 1e-2) < 1e-12)
     s.close()
 
 
@@ -406,5 +431,5 @@ def test_steps_continue_after_t_end():
     s.step(nsteps=1, cfl=0.5)
     Wo, st, _ = c.step(W, dt_o, f1=spec["f1"].ravel(), f2=spec["f2"].ravel(), nthreads=8)
     assert st == 0
-    assert np.all(rel_err_per_var(s.get_state(), Wo, 4) < 1e-12)
+    assert np.all(max_rel_elementwise(s.get_state(), Wo, 4, 1e-2) < 1e-12)
     s.close()

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_1302_2132_gb300 import inputs
-from tests.cases import gpu_solver, oracle_case, rel_err_per_var
+from tests.cases import gpu_solver, max_rel_elementwise, oracle_case, rel_err_per_var
 from tests.test_gpu_parity import step_both
 
 pytestmark = pytest.mark.gpu
@@ -31,7 +31,7 @@ def cases():
 def test_fp64_higher_order_step_matches_oracle(name, recon):
     spec, kw, steps = cases()[name]
     s, c, Wg, Wo, res = step_both(spec, nsteps=steps, recon=recon, **kw)
-    assert np.all(rel_err_per_var(Wg, Wo, spec["dim"] + 2) < 1e-12)
+    assert np.all(max_rel_elementwise(Wg, Wo, spec["dim"] + 2, 1e-2) < 1e-12)
     s.close()
 
 

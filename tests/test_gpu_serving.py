@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import oracle_case, rel_err_per_var
+from cases import max_rel_elementwise, oracle_case, rel_err_per_var
 from paper_1302_2132_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -76,7 +76,7 @@ def test_fp64_server_matches_the_oracle():
         c = oracle_case(s, C_a=KW["C_a"], mu=KW["mu"], multid=1, limiter=1)
         Wo, t, n, stt = c.run(c.prim_to_cons(s["prim"].ravel()), s["nsteps"], cfl=KW["cfl"], nthreads=8)
         assert n == s["nsteps"] and stt == 0
-        assert np.all(rel_err_per_var(W, Wo, s["dim"] + 2) < 1e-10)
+        assert np.all(max_rel_elementwise(W, Wo, s["dim"] + 2, 1e-2) < 1e-10)
 
 
 def test_admission_waits_for_memory():
