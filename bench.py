@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None, choices=["fp32", "fp32_acc64", "fp64"])
     p.add_argument("--workload", default="turb2d_1024",
-                   choices=["turb2d_1024", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
+                   choices=["turb2d_1024", "turb2d_512", "turb2d_1024_transport", "sod1d_400", "shock_bl_1024x384", "turb3d_256",
+                            "turb3d_160", "shock_bl_512x192",
                             "corner2d_528x136", "corner2d_2112x544", "steady_corner_528x136",
                             "steady_corner_2112x544", "naca2d_608x160", "naca2d_608x160_transport",
                             "steady_naca_608x160", "steady_naca_608x160_transport"])
@@ -57,6 +58,8 @@ def parse():
                    help="expansion of the body-fitted and steady workloads (default: directional)")
     p.add_argument("--reconstruction", default="muscl2", choices=["muscl2", "muscl3", "weno5"],
                    help="face reconstruction (the default is the second-order MUSCL the metric is quoted on)")
+    p.add_argument("--rarefaction", default="dt", choices=["dt", "tauhat"],
+                   help="degree of rarefaction in the time coefficients: tau/dt (default) or tau/tauhat")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--lusgs-tile", type=int, default=16, choices=[16, 32],
                    help="LU-SGS tile edge of the steady workloads")
@@ -153,6 +156,12 @@ def make_workload(name, precision):
                     precision=precision or "fp32_acc64",
                     desc="2D decaying turbulence 1024^2, k-epsilon tau_t, multi-D, 200 CFL steps, FP32 flux with "
                          "the state accumulated in IEEE double")
+    if name == "turb2d_512":  # a smaller case of the same kernel for multi-pass captures
+        spec = inputs.turbulence(512, 2, seed=SEED)
+        return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
+                                       expand="multid"), nsteps=NSTEPS, t_end=0.0,
+                    precision=precision or "fp32_acc64",
+                    desc="2D decaying turbulence 512^2, k-epsilon tau_t, multi-D, 200 CFL steps")
     if name == "turb2d_1024_transport":
         spec = dict(workload_inputs())
         # k-omega transport from the same initial fields: omega = eps / (C_mu k), so that nu_t = k/omega
@@ -168,13 +177,14 @@ def make_workload(name, precision):
         return dict(spec=spec, kw=dict(gamma=1.4, mu=1e-5, C_a=1.0, limiter="vanleer", expand="directional"),
                     nsteps=0, t_end=0.2, precision=precision or "fp64",
                     desc="Sod shock tube, 400 cells, van Leer, C_a = 1, CFL 0.5, to t = 0.2")
-    if name == "shock_bl_1024x384":
-        spec = inputs.shock_boundary_layer(1024, 384)
+    if name.startswith("shock_bl_"):  # 1024x384: the workload; 512x192: a smaller case for kernel captures
+        nx, ny = (int(v) for v in name.split("_")[2].split("x"))
+        spec = inputs.shock_boundary_layer(nx, ny)
         return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega",
                                        beta_star=0.09, C_a=0.5, limiter="vanleer", expand="multid"),
                     nsteps=5000, t_end=0.0, precision=precision or "fp32",
-                    desc="Mach 2.85 boundary layer under a 24-degree shock, 1024x384 wall-clustered, k-omega tau_t, "
-                         "5000 CFL steps")
+                    desc="Mach 2.85 boundary layer under a 24-degree shock, %dx%d wall-clustered, k-omega tau_t, "
+                         "5000 CFL steps" % (nx, ny))
     if name.startswith("steady_corner_"):
         nx, ny = (int(v) for v in name.split("_")[2].split("x"))
         spec = inputs.compression_corner(nx, ny, alpha_deg=24.0)
@@ -226,11 +236,12 @@ def make_workload(name, precision):
                     desc="Mach 2.85 boundary layer over a 24-degree compression corner on a body-fitted "
                          "%dx%d wall-clustered channel grid, k-omega tau_t, directional expansion in each "
                          "face's frame, 2000 CFL steps" % (nx, ny))
-    if name == "turb3d_256":
-        spec = inputs.turbulence(256, 3, seed=2132)
+    if name.startswith("turb3d_"):  # 256: the workload; 160: a smaller case (still larger than L2) for captures
+        n3 = int(name.split("_")[1])
+        spec = inputs.turbulence(n3, 3, seed=2132)
         return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
                                        expand="multid"), nsteps=100, t_end=0.0, precision=precision or "fp32",
-                    desc="3D decaying turbulence 256^3, k-epsilon tau_t, multi-D, 100 CFL steps")
+                    desc="3D decaying turbulence %d^3, k-epsilon tau_t, multi-D, 100 CFL steps" % n3)
     raise ValueError(name)
 
 
@@ -289,7 +300,8 @@ def run_steady(args, wl):
                          mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega_transport" if transport
                          else "komega", beta_star=0.09, C_a=0.5,
                          limiter="vanleer", precision=wl["precision"], lusgs_tile=args.lusgs_tile,
-                         wake_cut=spec.get("wake_cut", 0), expand=args.expand or "directional")
+                         wake_cut=spec.get("wake_cut", 0), expand=args.expand or "directional",
+                         rarefaction=args.rarefaction)
     prim_dev = torch.tensor(spec["prim"].ravel(), device=dev)
     f1_dev = torch.tensor(np.ravel(spec["f1"]), dtype=torch.float64, device=dev)
     f2_dev = torch.tensor(np.ravel(spec["f2"]), dtype=torch.float64, device=dev)
@@ -386,7 +398,8 @@ def run_steady(args, wl):
         "dtype": "f64" if fp64 else "f32",
         "data": "synthetic",
         "config": {"workload": "%s_%s" % (args.workload, wl["precision"]) + ("_multid" if args.expand == "multid"
-                                                                             else ""),
+                                                                             else "") +
+                               ("_rarefaction_tauhat" if args.rarefaction != "dt" else ""),
                    "description": wl["desc"], "grid": list(n), "expand": args.expand or "directional",
                    "levels": levels, "lusgs_tile": args.lusgs_tile, "cycles_per_bench_step": ncyc,
                    "precision": wl["precision"],
@@ -446,7 +459,7 @@ def run_ours(args):
     faces_per_step = faces_of(n, spec["bc"] if wl.get("nodes") is None else None)
     cells = int(np.prod(n))
     solver = gks.Solver(D, n, spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"), precision=wl["precision"],
-                        reconstruction=args.reconstruction, **wl["kw"])
+                        reconstruction=args.reconstruction, rarefaction=args.rarefaction, **wl["kw"])
     curv = wl.get("nodes") is not None
     if curv:
         solver.set_nodes(wl["nodes"])
@@ -569,6 +582,8 @@ def run_ours(args):
         workload_name += "_" + args.reconstruction
     if args.expand == "multid" and curv:
         workload_name += "_multid"
+    if args.rarefaction != "dt":
+        workload_name += "_rarefaction_tauhat"
     tile = solver.tile_shape()
     # on body-fitted grids the MUSCL-2 step in FP64 or the FP32 float-pair form carries the transport
     fused_tr = transport and curv and args.reconstruction == "muscl2" and wl["precision"] in ("fp32", "fp64")
@@ -770,6 +785,7 @@ def serve_stream(reqs, rate, seed, arena=16 << 30):
     """Submit reqs at Poisson arrival times (rate per second; 0 = all at once) and wait for all."""
     from paper_1302_2132_gb300 import inputs, serve
     srv = serve.Server(precision="fp32", arena_bytes=arena, max_cells=512 * 512, chunk_steps=24)
+    tiles = srv.tile_variants()
     arrivals = inputs.poisson_arrivals(len(reqs), rate, seed) if rate > 0 else np.zeros(len(reqs))
     t0 = time.perf_counter()
     for r, ta in zip(reqs, arrivals):
@@ -783,6 +799,7 @@ def serve_stream(reqs, rate, seed, arena=16 << 30):
     srv.close()
     st["wall_s"] = wall
     st["offered_rate"] = rate
+    st["tile_variants"] = tiles
     return st
 
 
@@ -811,6 +828,10 @@ def serving_summary(count):
     """Serving form on the seeded stream: capacity (burst of 400), a Poisson stream at 0.8x capacity,
     a 2x overload of 1000 requests, and the plain FP64 per-solve loop on the first 400 requests."""
     reqs = serving_requests(count)
+    # capacity with the first tile shape of every group, then with the shapes the server tunes
+    os.environ["GKS_BATCH_TILES"] = "0,0,0"
+    burst0 = serve_stream(reqs[:400], 0.0, 1)
+    del os.environ["GKS_BATCH_TILES"]
     burst = serve_stream(reqs[:400], 0.0, 1)
     capacity = burst["completed"] / burst["wall_s"]
     steady = serve_stream(reqs, 0.8 * capacity, 2)
@@ -819,6 +840,8 @@ def serving_summary(count):
     return {"metric": "serving solves/sec, p50/p99", "unit": "solves/s", "requests": len(reqs),
             "solves_per_s": steady["solves_per_s"], "p50_s": steady["p50_s"], "p99_s": steady["p99_s"],
             "offered_rate": steady["offered_rate"], "capacity_solves_per_s": capacity,
+            "batch_tiles": {"tuned": burst["tile_variants"],
+                            "capacity_with_first_shapes": burst0["completed"] / burst0["wall_s"]},
             "overload_2x": {k: over[k] for k in ("solves_per_s", "p50_s", "p99_s", "completed")},
             "fp64_per_solve_loop_solves_per_s": base["solves_per_s"], "fp64_per_solve_loop_requests": base["requests"],
             "batched_fp32_over_fp64_loop": capacity / base["solves_per_s"],
@@ -884,6 +907,9 @@ def run_serving(args):
     build.build()
     gks.load()
     cells = [int(np.prod(r["n"])) * r["nsteps"] for r in reqs]
+    os.environ["GKS_BATCH_TILES"] = "0,0,0"
+    burst0 = serve_stream(reqs[:400], 0.0, 1)
+    del os.environ["GKS_BATCH_TILES"]
     burst = serve_stream(reqs[:400], 0.0, 1)
     capacity = burst["completed"] / burst["wall_s"]
     steady = serve_stream(reqs, 0.8 * capacity, 2)
@@ -897,6 +923,7 @@ def run_serving(args):
                               "turbulence; 50-500 steps; FP32 flux, float-pair state",
                        "cell_steps_total": int(sum(cells))},
             "capacity_solves_per_s": capacity, "burst": burst, "steady_0p8": steady, "overload_2x": over,
+            "capacity_with_first_tile_shapes": burst0["completed"] / burst0["wall_s"],
             "fp64_per_solve_loop": base,
             "batched_vs_fp64_loop": capacity / base["solves_per_s"]}
     print(json.dumps(line))

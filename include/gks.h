@@ -322,12 +322,14 @@ gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtyp
 gks_status gks_enable_timing(gks_handle* h, int enable);
 gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
 
-/* Tile shape of the handle's step kernel (no paper counterpart).  2D GKS_FP32 and GKS_FP32_ACC64 handles choose among six
- * shapes (variants 0..5: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 cells; 512 threads per CTA for 32x31
- * and 64x27, 256 otherwise), 3D ones among three (16x8x4, 16x8x2, 8x8x4), 1D handles among 256, 31 and
+/* Tile shape of the handle's step kernel (no paper counterpart).  2D GKS_FP32 and GKS_FP32_ACC64 handles choose among eight
+ * shapes (variants 0..5: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 cells, one face per thread per round,
+ * 512 threads per CTA for 32x31 and 64x27, 256 otherwise; variants 6 and 7: 32x27 on 128 and 64x27 on
+ * 256 threads, each thread evaluating two faces at once with the paired FP32 instructions), 3D ones
+ * among four (16x8x4, 16x8x2, 8x8x4, and 16x8x2 with two faces per thread on 128 threads), 1D handles among 256, 31 and
  * 63 cells per CTA (the rarefaction option runs the first shape of each), on their first gks_step: each is timed
  * on the step about to be taken and the fastest kept (and reused by later handles of the same grid);
- * the environment variable GKS_TILE_VARIANT forces one (0..5 in 2D, 0..2 in 1D).  The result does
+ * the environment variable GKS_TILE_VARIANT forces one (0..7 in 2D, 0..3 in 3D, 0..2 in 1D).  The result does
  * not depend on it beyond rounding. */
 gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz);
 
@@ -425,6 +427,13 @@ gks_status gks_server_wait_all(gks_server* s, double timeout_s);
  * second since the first submission, and seconds the GPU spent in batch steps; destroy a server. */
 gks_status gks_server_stats(gks_server* s, long long* completed, double* p50_s, double* p99_s, double* solves_per_s,
                             double* busy_s);
+/* Serving (no paper counterpart): the tile shape of each group's batch kernel (variants of
+ * gks_tile_shape: [0] 1D, [1] 2D directional, [2] 2D multi-dimensional).  A GKS_FP32 server times the
+ * candidate shapes (1D: 0, 1, 2; 2D: 0, 1, 3, 4) on a synthetic batch of periodic solves once per
+ * process and device, at the first gks_server_create, and keeps the fastest per group for every server
+ * of the process (so a solve's result does not depend on the server or mix it runs in); the
+ * environment variable GKS_BATCH_TILES="v1d,v2d,v2dm" forces them.  GKS_FP64 servers use shape 0. */
+gks_status gks_server_tile_variants(gks_server* s, int* variants);
 gks_status gks_server_destroy(gks_server* s);
 
 /* Measured FMA throughput of the current device for FP32 and FP64 (independent FMA chains on every

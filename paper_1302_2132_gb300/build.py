@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgks.so")
-UNITS = ["gks_serve.cu", "gks_step_2d.cu", "gks_step_2d_tiles.cu", "gks_step_2d_tiles2.cu", "gks_step_acc64.cu", "gks_step_rar.cu", "gks_step_3d.cu", "gks_step_3d_tiles.cu", "gks_step_1d.cu", "gks_face.cu", "gks_capi.cu", "gks_count.cpp", "gks_probe.cu", "gks_noalloc.cu", "gks_komega.cu", "gks_step_muscl3.cu", "gks_step_weno5.cu", "gks_curv.cu", "gks_curv_recon.cu", "gks_curv_kw.cu", "gks_curv_rar.cu", "gks_steady.cu"]
+UNITS = ["gks_serve.cu", "gks_step_2d.cu", "gks_step_2d_tiles.cu", "gks_step_2d_tiles2.cu", "gks_step_acc64.cu", "gks_step_pair.cu", "gks_step_rar.cu", "gks_step_3d.cu", "gks_step_3d_tiles.cu", "gks_step_1d.cu", "gks_face.cu", "gks_capi.cu", "gks_count.cpp", "gks_probe.cu", "gks_noalloc.cu", "gks_komega.cu", "gks_step_muscl3.cu", "gks_step_weno5.cu", "gks_curv.cu", "gks_curv_recon.cu", "gks_curv_kw.cu", "gks_curv_rar.cu", "gks_steady.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

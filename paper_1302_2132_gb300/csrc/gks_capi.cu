@@ -616,6 +616,7 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
     if (e == cudaSuccess && D == 1) e = prepare_step_d1_variants();
     if (e == cudaSuccess && D == 3) e = prepare_step_d3_variants();
     if (e == cudaSuccess && D >= 2) e = prepare_step_acc64();
+    if (e == cudaSuccess && D >= 2) e = prepare_step_pair();
     if (e == cudaSuccess) e = prepare_step_rar();
     if (e == cudaSuccess && D == 2) e = prepare_curv_rar();
     if (e == cudaSuccess) e = prepare_komega();

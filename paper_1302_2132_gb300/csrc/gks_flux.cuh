@@ -14,6 +14,11 @@
 #endif
 #include <math.h>
 
+#include <type_traits>
+#ifndef GKS_HOST_COUNT
+#include "gks_f2.cuh"
+#endif
+
 #ifndef GKS_FN
 #define GKS_FN __device__ __forceinline__
 #endif
@@ -71,6 +76,34 @@ GKS_FN float erfc_cheb(float x) {
   return x >= 0.0f ? r : 2.0f - r;
 }
 template <> GKS_FN float g_erfc<float>(float x) { return erfc_cheb(x); }
+
+// The same functions on two lanes (two faces per thread): quotients by the hardware reciprocal,
+// exponentials and square roots per lane, erfc from the same Chebyshev fit with paired arithmetic.
+GKS_FN F2 g_rcp(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+GKS_FN F2 g_div(F2 a, F2 b) { return F2(a * g_rcp(b)); }
+GKS_FN F2 g_exp(F2 x) { return F2(__expf(x.v.x), __expf(x.v.y)); }
+GKS_FN F2 g_sqrt(F2 x) { return F2(g_sqrt<float>(x.v.x), g_sqrt<float>(x.v.y)); }
+GKS_FN F2 g_abs(F2 x) { return F2(fabsf(x.v.x), fabsf(x.v.y)); }
+GKS_FN F2 g_erfc(F2 x) {
+  const F2 z = g_abs(x);
+  const F2 t = g_rcp(F2(1.0f) + F2(0.5f) * z);
+  const float c[10] = {-1.26551223f, 1.00002368f, 0.37409196f, 0.09678418f, -0.18628806f,
+                       0.27886807f, -1.13520398f, 1.48851587f, -0.82215223f, 0.17087277f};
+  F2 p = F2(c[9]);
+#pragma unroll
+  for (int i = 8; i >= 0; --i) p = p * t + F2(c[i]);
+  const F2 r = F2(t * g_exp(p - z * z));
+  return F2(x.v.x >= 0.0f ? r.v.x : 2.0f - r.v.x, x.v.y >= 0.0f ? r.v.y : 2.0f - r.v.y);
+}
+GKS_FN F2 f2_select(bool cx, bool cy, F2 a, F2 b) { return F2(cx ? a.v.x : b.v.x, cy ? a.v.y : b.v.y); }
+// a pending product as the argument: rounded first (exact overloads, so the templates above are not
+// deduced with the product type)
+GKS_FN F2 g_rcp(F2Mul x) { return g_rcp(F2(x)); }
+GKS_FN F2 g_div(F2Mul a, F2Mul b) { return g_div(F2(a), F2(b)); }
+GKS_FN F2 g_exp(F2Mul x) { return g_exp(F2(x)); }
+GKS_FN F2 g_sqrt(F2Mul x) { return g_sqrt(F2(x)); }
+GKS_FN F2 g_abs(F2Mul x) { return g_abs(F2(x)); }
+GKS_FN F2 g_erfc(F2Mul x) { return g_erfc(F2(x)); }
 #endif
 
 constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
@@ -440,7 +473,7 @@ struct TimeCoef {
 // reach double precision, 12 leave a truncation below 1e-9 (enough in single precision).
 template <class T>
 GKS_FN void phi_series(T x, T& p1, T& p2, T& p3, T& e) {
-  constexpr int N = sizeof(T) == sizeof(float) ? 12 : 18;
+  constexpr int N = std::is_same<T, double>::value ? 18 : 12;
   const double c[18] = {1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
                         1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
                         1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0,
@@ -495,6 +528,53 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
     r5 = -yq * inv;
   }
 }
+
+#ifndef GKS_HOST_COUNT
+// Two lanes: both branches of time_coeffs, each lane keeping its own (x < 1: the series).
+template <>
+GKS_FN void time_coeffs<F2>(F2 dt, F2 tau, F2* Tc, F2& r1, F2& r4, F2& r5) {
+  const F2 x = g_div(dt, tau);
+  const bool sx = x.v.x < 1.0f, sy = x.v.y < 1.0f;
+  F2 p1, p2, p3, e;
+  phi_series(x, p1, p2, p3, e);
+  const F2 dt2 = F2(dt * dt);
+  const F2 Dn = F2(dt2 * p2);
+  F2 Ts[6];
+  const F2 T1s = F2(-dt2 * x) * (p2 - F2(2.0f) * p3);
+  const F2 T4s = F2(tau * dt) * (e - F2(2.0f) * p1);
+  const F2 T5s = -(F2(tau * dt) * p1);
+  Ts[0] = F2(dt * x) * p2;
+  Ts[1] = T1s;
+  Ts[2] = F2(dt2 * x) * p3;
+  Ts[3] = dt * p1;
+  Ts[4] = T4s;
+  Ts[5] = T5s;
+  const F2 iDn = g_rcp(Dn);
+  const F2 r1s = T1s * iDn, r4s = T4s * iDn, r5s = T5s * iDn;
+  // closed forms in e = exp(-x)
+  const F2 ec = g_exp(-x);
+  const F2 q = F2(1.0f) - ec;
+  const F2 tq = tau * q;
+  F2 Tcl[6];
+  Tcl[0] = dt - tq;
+  Tcl[1] = F2(-(tau * dt)) * (F2(1.0f) + ec) + F2(2.0f) * F2(tau * tq);
+  Tcl[2] = F2(0.5f) * F2(dt * dt) - tau * dt + tau * tq;
+  Tcl[3] = tq;
+  Tcl[4] = F2(tau * dt) * ec - F2(2.0f) * F2(tau * tq);
+  Tcl[5] = -(tau * tq);
+  const F2 y = g_div(tau, dt);
+  const F2 yq = y * q;
+  const F2 inv = g_rcp(F2(1.0f) - yq);
+  const F2 r1c = (F2(2.0f) * yq - (F2(1.0f) + ec)) * inv;
+  const F2 r4c = (ec - F2(2.0f) * yq) * inv;
+  const F2 r5c = -(yq * inv);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Tc[i] = f2_select(sx, sy, Ts[i], Tcl[i]);
+  r1 = f2_select(sx, sy, r1s, r1c);
+  r4 = f2_select(sx, sy, r4s, r4c);
+  r5 = f2_select(sx, sy, r5s, r5c);
+}
+#endif
 
 // The time coefficients with the degree of rarefaction eps in place of tau/dt (Eqs. tautautilde,
 // rarefactionkepsilon, epsilonkomega): Eq. fkepsilon with alpha = eps (1 - e^{-1/eps}) and

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -131,7 +133,8 @@ struct gks_server {
   bool stop = false;
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
-  int persistent_blocks = 0;
+  int var[NGROUPS] = {0, 0, 0};     // tile variant of each group (chosen at creation)
+  int blocks[NGROUPS] = {0, 0, 0};  // persistent CTAs of each group's launch
   // statistics
   long long completed = 0;
   double t_first_submit = 0, t_last_done = 0, busy_s = 0;
@@ -152,9 +155,15 @@ size_t footprint(int prec, const Req& r) {
   return b + round_up(sizeof(Ctrl));
 }
 
-int tiles_of(const gks_request& q) {
-  if (q.dim == 1) return (q.n[0] + Tile<1>::X - 1) / Tile<1>::X;
-  return ((q.n[0] + Tile<2>::X - 1) / Tile<2>::X) * ((q.n[1] + Tile<2>::Y - 1) / Tile<2>::Y);
+int tiles_of(const gks_request& q, int variant) {
+  int t[3];
+  tile_shape(q.dim, variant, &t[0], &t[1], &t[2]);
+  if (q.dim == 1) return (q.n[0] + t[0] - 1) / t[0];
+  return ((q.n[0] + t[0] - 1) / t[0]) * ((q.n[1] + t[1] - 1) / t[1]);
+}
+
+int group_of(const gks_request& q) {
+  return q.dim == 1 ? GROUP_1D : (q.expand == GKS_EXPAND_MULTID ? GROUP_2D_MULTID : GROUP_2D);
 }
 
 void fail_req(gks_server* s, Req* r, const char* msg) {
@@ -299,21 +308,22 @@ void rebuild_items(gks_server* s) {
   s->dirty = false;
 }
 
+void launch_group(gks_server* s, int g, int phase) {
+  BatchArgs B;
+  B.solves = s->d_solves;
+  B.counter = s->d_counter;
+  B.phase = phase;
+  B.items = s->d_items[g];
+  B.nitems = s->d_nitems + g;
+  if (g == GROUP_1D)
+    launch_batch_d1(s->prec, s->var[g], B, s->blocks[g], s->stream);
+  else
+    launch_batch_d2(s->prec, s->var[g], g == GROUP_2D_MULTID, B, s->blocks[g], s->stream);
+}
+
 void launch_chunk_steps(gks_server* s, int nsteps, long long start) {
-  for (int k = 0; k < nsteps; ++k) {
-    BatchArgs B;
-    B.solves = s->d_solves;
-    B.counter = s->d_counter;
-    B.phase = (int)((start + k) % 6);
-    for (int g = 0; g < NGROUPS; ++g) {
-      B.items = s->d_items[g];
-      B.nitems = s->d_nitems + g;
-      if (g == GROUP_1D)
-        launch_batch_d1(s->prec, false, B, s->persistent_blocks, s->stream);
-      else
-        launch_batch_d2(s->prec, g == GROUP_2D_MULTID, B, s->persistent_blocks, s->stream);
-    }
-  }
+  for (int k = 0; k < nsteps; ++k)
+    for (int g = 0; g < NGROUPS; ++g) launch_group(s, g, (int)((start + k) % 6));
 }
 
 bool run_chunk(gks_server* s) {
@@ -405,6 +415,157 @@ void worker_main(gks_server* s) {
   }
 }
 
+// Tile shape of each group, timed once per process and device on a synthetic batch (every server of
+// the process then uses the same shapes, so a solve's result does not depend on which server or mix
+// it runs in): for each group, a batch of periodic solves of typical sizes is admitted and each
+// candidate shape runs three rounds of six batch steps (CUDA events); the fastest round decides.
+// GKS_BATCH_TILES="v1d,v2d,v2d_multid" forces the shapes.
+std::mutex g_tune_mu;
+std::map<int, std::vector<int>> g_tuned_batch;
+
+bool tune_batch(gks_server* s, const int* res1, const int* res2, int sms) {
+  static const std::vector<int> cand[NGROUPS] = {{0, 1, 2}, {0, 1, 3, 4}, {0, 1, 3, 4}};
+  auto set_blocks = [&](int g) {
+    const int v = s->var[g];
+    const int per = g == GROUP_1D ? res1[v] : res2[2 * v + (g == GROUP_2D_MULTID)];
+    s->blocks[g] = sms * std::max(per, 1);
+  };
+  if (const char* f = std::getenv("GKS_BATCH_TILES")) {
+    int v[3] = {0, 0, 0};
+    if (std::sscanf(f, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3)
+      for (int g = 0; g < NGROUPS; ++g)
+        for (int c : cand[g])
+          if (c == v[g]) s->var[g] = c;
+    for (int g = 0; g < NGROUPS; ++g) set_blocks(g);
+    return true;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_batch.find(s->dev);
+    if (it != g_tuned_batch.end()) {
+      for (int g = 0; g < NGROUPS; ++g) {
+        s->var[g] = it->second[g];
+        set_blocks(g);
+      }
+      return true;
+    }
+  }
+  // synthetic batch: 48 1D solves of 2048 cells; per 2D group 8 solves of 192^2 and 8 of 96^2
+  std::vector<Req*> reqs;
+  auto add = [&](int dim, int n, int expand) -> bool {
+    Req* r = new (std::nothrow) Req();
+    if (!r) return false;
+    gks_request& q = r->q;
+    std::memset(&q, 0, sizeof(q));
+    q.dim = dim;
+    r->ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+      q.n[d] = d < dim ? n : 1;
+      q.lo[d] = 0.0;
+      q.hi[d] = 1.0;
+      if (d < dim) r->ncell *= n;
+    }
+    q.gamma = 1.4;
+    q.mu = 1e-4;
+    q.T_wall = 1.0;
+    q.cfl = 0.5;
+    q.limiter = GKS_LIM_VANLEER;
+    q.expand = expand;
+    q.nsteps = 1 << 30;
+    const int nv = dim + 2;
+    r->prim.assign((size_t)nv * r->ncell, 0.0);
+    for (long c = 0; c < r->ncell; ++c) {
+      const double x = (double)(c % n) / n;
+      r->prim[c] = 1.0 + 0.1 * std::sin(6.283185307179586 * x);
+      r->prim[r->ncell + c] = 0.3;
+      if (dim == 2) r->prim[2 * r->ncell + c] = 0.2;
+      r->prim[(size_t)(nv - 1) * r->ncell + c] = 0.7;
+    }
+    r->group = group_of(q);
+    r->bytes = footprint(s->prec, *r);
+    if (s->free_slots.empty() || !s->alloc.alloc(r->bytes, &r->off)) {
+      delete r;
+      return false;
+    }
+    r->slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    reqs.push_back(r);
+    if (admit(s, r)) return true;
+    r->group = -1;  // not in any group's items; released with the others
+    return false;
+  };
+  // (a small arena admits fewer of them; a group with none keeps its first shape)
+  int admitted[NGROUPS] = {0, 0, 0};
+  for (int i = 0; i < 48; ++i)
+    if (add(1, 2048, GKS_EXPAND_DIRECTIONAL)) ++admitted[GROUP_1D];
+  for (int e = 0; e < 2; ++e)
+    for (int i = 0; i < 16; ++i)
+      if (add(2, i < 8 ? 192 : 96, e ? GKS_EXPAND_MULTID : GKS_EXPAND_DIRECTIONAL))
+        ++admitted[e ? GROUP_2D_MULTID : GROUP_2D];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  int phase = 0;
+  for (int g = 0; g < NGROUPS && ok; ++g) {
+    if (!admitted[g]) {
+      s->var[g] = cand[g][0];
+      set_blocks(g);
+      continue;
+    }
+    float best = 1e30f;
+    int best_v = cand[g][0];
+    for (int v : cand[g]) {
+      s->var[g] = v;
+      set_blocks(g);
+      int n = 0;
+      for (Req* r : reqs)
+        if (r->group == g) {
+          r->tiles = tiles_of(r->q, v);
+          for (int t = 0; t < r->tiles; ++t) s->h_items[(size_t)g * s->max_items + n++] = make_int2(r->slot, t);
+        }
+      for (int h = 0; h < NGROUPS; ++h) s->h_nitems[h] = h == g ? n : 0;
+      cudaMemcpyAsync(s->d_items[g], s->h_items + (size_t)g * s->max_items, sizeof(int2) * n, cudaMemcpyHostToDevice,
+                      s->stream);
+      cudaMemcpyAsync(s->d_nitems, s->h_nitems, sizeof(int) * NGROUPS, cudaMemcpyHostToDevice, s->stream);
+      for (int k = 0; k < 3; ++k) launch_group(s, g, phase++ % 6);  // warm-up
+      for (int round = 0; round < 3; ++round) {
+        cudaEventRecord(e0, s->stream);
+        for (int k = 0; k < 6; ++k) launch_group(s, g, phase++ % 6);
+        cudaEventRecord(e1, s->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          ok = false;
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_v = v;
+        }
+      }
+    }
+    s->var[g] = best_v;
+    set_blocks(g);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // drop the synthetic solves and start the server's step count afresh
+  cudaStreamSynchronize(s->stream);
+  for (Req* r : reqs) {
+    s->alloc.release(r->off, r->bytes);
+    s->free_slots.push_back(r->slot);
+    delete r;
+  }
+  s->step = 0;
+  cudaMemsetAsync(s->d_counter, 0, sizeof(long long) * 2, s->stream);
+  cudaMemsetAsync(s->d_nitems, 0, sizeof(int) * NGROUPS, s->stream);
+  ok = ok && cudaStreamSynchronize(s->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+  if (ok) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_batch[s->dev] = std::vector<int>(s->var, s->var + NGROUPS);
+  }
+  return ok;
+}
+
 }  // namespace
 
 extern "C" {
@@ -432,10 +593,15 @@ gks_status gks_server_create(int precision, size_t arena_bytes, long max_cells, 
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GKS_ECUDA);
     s->own_stream = true;
   }
-  if (prepare_batch_d1() != cudaSuccess || prepare_batch_d2() != cudaSuccess) return bail(GKS_ECUDA);
+  int res1[3] = {0, 0, 0}, res2[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (prepare_batch_d1(s->prec, res1) != cudaSuccess || prepare_batch_d2(s->prec, res2) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(GKS_ECUDA);
+  }
   // descriptor slots: enough for arena / smallest footprint, bounded
   s->max_slots = 4096;
-  s->max_items = (int)std::min<long>(1L << 22, (long)(arena_bytes / (Tile<1>::X * 4 * sizeof(float) * 3)) + 4096);
+  // items are tiles: the narrowest (the 31-cell 1D tile) bounds their number for a full arena
+  s->max_items = (int)std::min<long>(1L << 22, (long)(arena_bytes / (Tile<1, 1>::X * 4 * sizeof(float) * 3)) + 4096);
   if (cudaMalloc(&s->arena, arena_bytes) != cudaSuccess ||
       cudaMalloc(&s->d_solves, sizeof(BatchSolve) * s->max_slots) != cudaSuccess ||
       cudaMalloc(&s->d_nitems, sizeof(int) * NGROUPS) != cudaSuccess ||
@@ -459,10 +625,17 @@ gks_status gks_server_create(int precision, size_t arena_bytes, long max_cells, 
   for (int i = s->max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
-  s->persistent_blocks = sms * (s->prec == PREC_F32 ? 2 : 1);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     return bail(GKS_ECUDA);
+  }
+  if (s->prec == PREC_F32) {
+    if (!tune_batch(s, res1, res2, sms)) {
+      cudaGetLastError();
+      return bail(GKS_ECUDA);
+    }
+  } else {
+    for (int g = 0; g < NGROUPS; ++g) s->blocks[g] = sms * std::max(g == GROUP_1D ? res1[0] : res2[g == GROUP_2D_MULTID], 1);
   }
   s->worker = std::thread(worker_main, s);
   *out = s;
@@ -492,8 +665,8 @@ gks_status gks_server_submit(gks_server* s, const gks_request* q, const double* 
   if (!r) return GKS_ENOMEM;
   r->q = *q;
   r->ncell = ncell;
-  r->tiles = tiles_of(*q);
-  r->group = q->dim == 1 ? GROUP_1D : (q->expand == GKS_EXPAND_MULTID ? GROUP_2D_MULTID : GROUP_2D);
+  r->group = group_of(*q);
+  r->tiles = tiles_of(*q, s->var[r->group]);
   r->prim.assign(prim, prim + (size_t)(q->dim + 2) * ncell);
   if (footprint(s->prec, *r) > s->capacity) {
     delete r;
@@ -569,6 +742,12 @@ gks_status gks_server_stats(gks_server* s, long long* completed, double* p50_s, 
   const double span = s->t_last_done - s->t_first_submit;
   if (solves_per_s) *solves_per_s = span > 0 ? s->completed / span : 0.0;
   if (busy_s) *busy_s = s->busy_s;
+  return GKS_OK;
+}
+
+gks_status gks_server_tile_variants(gks_server* s, int* variants) {
+  if (!s || !variants) return GKS_EINVAL;
+  for (int g = 0; g < NGROUPS; ++g) variants[g] = s->var[g];
   return GKS_OK;
 }
 

@@ -50,6 +50,13 @@ template <> struct Tile<2, 4> { static constexpr int X = 32, Y = 18, Z = 1, T = 
 // 64x27 on one 512-thread CTA per SM: 3547 faces in 7 rounds (99%), 608 tiles = 4 full waves; all
 // warps of an SM work in the same phase of one tile
 template <> struct Tile<2, 5> { static constexpr int X = 64, Y = 27, Z = 1, T = 512; };
+// Paired tiles (FP32 forms): each thread evaluates two faces at once with the paired FP32 instructions
+// (two operations per issue slot); the face body then needs up to 255 registers, so 32x27 runs 128
+// threads (two CTAs per SM) and 64x27 256 threads (one CTA per SM), both in 7 rounds of face pairs.
+template <> struct Tile<2, 6> { static constexpr int X = 32, Y = 27, Z = 1, T = 128; };
+template <> struct Tile<2, 7> { static constexpr int X = 64, Y = 27, Z = 1, T = 256; };
+template <> struct Tile<3, 3> { static constexpr int X = 16, Y = 8, Z = 2, T = 128; };
+template <int D, int V> __host__ __device__ constexpr bool paired_tile() { return (D == 2 && V >= 6) || (D == 3 && V >= 3); }
 template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 256; };
 // 256-cell 3D tiles with the per-cell slope table (two CTAs per SM): 944 and 896 faces
 template <> struct Tile<3, 1> { static constexpr int X = 16, Y = 8, Z = 2, T = 256; };
@@ -698,6 +705,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* Ws = (R*)smem_raw;                    // [nv][HZ][HY][HX]
   constexpr bool PRE = pre_slopes<D, PREC, V>();
+  constexpr bool PAIR = paired_tile<D, V>() && std::is_same<R, float>::value && RECON == RECON_MUSCL2 && !RAR;
   R* taus = Ws + (size_t)nv * G::NH;       // [RZ][RY][RX]
   R* wsx = taus + G::NR;                   // widths with halo
   R* wsy = wsx + HX;
@@ -864,157 +872,231 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     gas.mu = kc.mu;
     gas.C_a = kc.C_a;
     const R gamma = kc.gamma;
-    // Rounds of kThreads faces; after each round the warps of every 128-thread group meet at a
-    // named barrier, so that the warps sharing an SM sub-partition run the ~1000-instruction face
-    // body close together and share its instruction fetches.  Every thread runs every round.
-    constexpr int kRounds = (G::NF + kThreads - 1) / kThreads;
-    for (int it = 0; it < kRounds; ++it) {
-      const int f = tid + it * kThreads;
-      if (f < G::NF) {
-        int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
-        if (f < G::NFX) {
-          ax = 0;
-          ci = f % (X + 1);
-          cj = (f / (X + 1)) % Y;
-          ck = f / ((X + 1) * Y);
-        } else if (D >= 2 && f < G::NFX + G::NFY) {
-          const int q = f - G::NFX;
-          ax = 1;
-          ci = q % X;
-          cj = (q / X) % (Y + 1);
-          ck = q / (X * (Y + 1));
-        } else {
-          const int q = f - G::NFX - G::NFY;
-          ax = 2;
-          ci = q % X;
-          cj = (q / X) % Y;
-          ck = q / (X * Y);
-        }
-        const int st[3] = {1, HX, HX * HY};
-        const int sn = st[ax];
-        const int hc = ((ck + (D >= 3 ? H : 0)) * HY + (cj + (D >= 2 ? H : 0))) * HX + (ci + H);
-        // velocity order in the face frame: normal first, then tangential axes
-        int perm[3];
-        perm[0] = ax;
-        if (D == 2) perm[1] = 1 - ax;
-        if (D == 3) {
-          perm[1] = ax == 0 ? 1 : 0;
-          perm[2] = ax == 2 ? 1 : 2;
-        }
-        const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
-        const int pn = ax == 0 ? ci + H : (ax == 1 ? cj + H : ck + H);  // halo coordinate of cell c
-        const R h1 = wn[pn - 1], h2 = wn[pn];
-        R i2h1 = R(0), i2h2 = R(0);  // 2 / width of the two cells (higher-order slopes)
+    // Inputs of one face in its frame (velocity order: normal first, then tangential axes).
+    struct FaceIn {
+      R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv], tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
+      R dxl, dxr, tau_t;
+      int ax, ci, cj, ck, perm[3];
+    };
+    auto prep = [&](int f, FaceIn& in) {
+      int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
+      if (f < G::NFX) {
+        ax = 0;
+        ci = f % (X + 1);
+        cj = (f / (X + 1)) % Y;
+        ck = f / ((X + 1) * Y);
+      } else if (D >= 2 && f < G::NFX + G::NFY) {
+        const int q = f - G::NFX;
+        ax = 1;
+        ci = q % X;
+        cj = (q / X) % (Y + 1);
+        ck = q / (X * (Y + 1));
+      } else {
+        const int q = f - G::NFX - G::NFY;
+        ax = 2;
+        ci = q % X;
+        cj = (q / X) % Y;
+        ck = q / (X * Y);
+      }
+      in.ax = ax;
+      in.ci = ci;
+      in.cj = cj;
+      in.ck = ck;
+      const int st[3] = {1, HX, HX * HY};
+      const int sn = st[ax];
+      const int hc = ((ck + (D >= 3 ? H : 0)) * HY + (cj + (D >= 2 ? H : 0))) * HX + (ci + H);
+      int* perm = in.perm;
+      perm[0] = ax;
+      if (D == 2) perm[1] = 1 - ax;
+      if (D == 3) {
+        perm[1] = ax == 0 ? 1 : 0;
+        perm[2] = ax == 2 ? 1 : 2;
+      }
+      const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
+      const int pn = ax == 0 ? ci + H : (ax == 1 ? cj + H : ck + H);  // halo coordinate of cell c
+      const R h1 = wn[pn - 1], h2 = wn[pn];
+      R i2h1 = R(0), i2h2 = R(0);  // 2 / width of the two cells (higher-order slopes)
+      if constexpr (RECON != RECON_MUSCL2) {
+        i2h1 = g_rcp(R(0.5) * h1);
+        i2h2 = g_rcp(R(0.5) * h2);
+      }
+      const R* icn = ax == 0 ? icx : (ax == 1 ? icy : icz);
+      (void)icn;
+      // ring indices of the two cells
+      const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
+      const int rst[3] = {1, G::RX, G::RX * G::RY};
+      const int rl = rc - rst[ax];
+      R* wl = in.wl;
+      R* wr = in.wr;
+      R* cl = in.cl;
+      R* cr = in.cr;
+      R* sl = in.sl;
+      R* sr = in.sr;
+#pragma unroll
+      for (int v = 0; v < nv; ++v) {
+        const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+        const R* p = Ws + sv * G::NH + hc;
+        const R s1 = p[-sn], s2 = p[0];
         if constexpr (RECON != RECON_MUSCL2) {
-          i2h1 = g_rcp(R(0.5) * h1);
-          i2h2 = g_rcp(R(0.5) * h2);
+          // higher-order face values from the normal stencil (cells pn-3 .. pn+2); the normal
+          // slopes are the one-sided differences to them
+          if constexpr (RECON == RECON_WENO5) {
+            wl[v] = weno5<R>(p[-3 * sn], p[-2 * sn], s1, s2, p[sn]);
+            wr[v] = weno5<R>(p[2 * sn], p[sn], s2, s1, p[-2 * sn]);
+          } else {
+            wl[v] = muscl3_right<R>(p[-2 * sn], s1, s2);
+            wr[v] = muscl3_left<R>(s1, s2, p[sn]);
+          }
+          sl[v] = (wl[v] - s1) * i2h1;
+          sr[v] = (s2 - wr[v]) * i2h2;
+        } else if (PRE) {
+          sl[v] = Ss[(ax * nv + sv) * G::NR + rl];
+          sr[v] = Ss[(ax * nv + sv) * G::NR + rc];
+          wl[v] = s1 + R(0.5) * h1 * sl[v];
+          wr[v] = s2 - R(0.5) * h2 * sr[v];
+        } else {
+          // MUSCL with the tabulated inverse centre distances (cells pn-2 .. pn+1 along the normal)
+          const R dm = (s1 - p[-2 * sn]) * icn[pn - 1], dc = (s2 - s1) * icn[pn], dp = (p[sn] - s2) * icn[pn + 1];
+          sl[v] = limiter<R>(g.limiter, dm, dc);
+          sr[v] = limiter<R>(g.limiter, dc, dp);
+          wl[v] = s1 + R(0.5) * h1 * sl[v];
+          wr[v] = s2 - R(0.5) * h2 * sr[v];
         }
-        const R* icn = ax == 0 ? icx : (ax == 1 ? icy : icz);
-        (void)icn;
-        // ring indices of the two cells
-        const int rc = ((ck + (D >= 3 ? 1 : 0)) * G::RY + (cj + (D >= 2 ? 1 : 0))) * G::RX + (ci + 1);
-        const int rst[3] = {1, G::RX, G::RX * G::RY};
-        const int rl = rc - rst[ax];
-        R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv];
+        cl[v] = s1;
+        cr[v] = s2;
+      }
+      if (!physical<D, R>(gamma, wl)) {
 #pragma unroll
         for (int v = 0; v < nv; ++v) {
-          const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
-          const R* p = Ws + sv * G::NH + hc;
-          const R s1 = p[-sn], s2 = p[0];
-          if constexpr (RECON != RECON_MUSCL2) {
-            // higher-order face values from the normal stencil (cells pn-3 .. pn+2); the normal
-            // slopes are the one-sided differences to them
-            if constexpr (RECON == RECON_WENO5) {
-              wl[v] = weno5<R>(p[-3 * sn], p[-2 * sn], s1, s2, p[sn]);
-              wr[v] = weno5<R>(p[2 * sn], p[sn], s2, s1, p[-2 * sn]);
-            } else {
-              wl[v] = muscl3_right<R>(p[-2 * sn], s1, s2);
-              wr[v] = muscl3_left<R>(s1, s2, p[sn]);
-            }
-            sl[v] = (wl[v] - s1) * i2h1;
-            sr[v] = (s2 - wr[v]) * i2h2;
-          } else if (PRE) {
-            sl[v] = Ss[(ax * nv + sv) * G::NR + rl];
-            sr[v] = Ss[(ax * nv + sv) * G::NR + rc];
-            wl[v] = s1 + R(0.5) * h1 * sl[v];
-            wr[v] = s2 - R(0.5) * h2 * sr[v];
-          } else {
-            // MUSCL with the tabulated inverse centre distances (cells pn-2 .. pn+1 along the normal)
-            const R dm = (s1 - p[-2 * sn]) * icn[pn - 1], dc = (s2 - s1) * icn[pn], dp = (p[sn] - s2) * icn[pn + 1];
-            sl[v] = limiter<R>(g.limiter, dm, dc);
-            sr[v] = limiter<R>(g.limiter, dc, dp);
-            wl[v] = s1 + R(0.5) * h1 * sl[v];
-            wr[v] = s2 - R(0.5) * h2 * sr[v];
-          }
-          cl[v] = s1;
-          cr[v] = s2;
-        }
-        if (!physical<D, R>(gamma, wl)) {
-#pragma unroll
-          for (int v = 0; v < nv; ++v) {
-            wl[v] = cl[v];
-            sl[v] = R(0);
-          }
-        }
-        if (!physical<D, R>(gamma, wr)) {
-#pragma unroll
-          for (int v = 0; v < nv; ++v) {
-            wr[v] = cr[v];
-            sr[v] = R(0);
-          }
-        }
-        R tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
-        if (MULTID && PRE) {
-#pragma unroll
-          for (int s = 0; s < D - 1; ++s) {
-            const int ta = perm[1 + s];
-#pragma unroll
-            for (int v = 0; v < nv; ++v) {
-              const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
-              tl[s][v] = Ss[(ta * nv + sv) * G::NR + rl];
-              tr[s][v] = Ss[(ta * nv + sv) * G::NR + rc];
-            }
-          }
-        } else if (MULTID) {
-#pragma unroll
-          for (int s = 0; s < D - 1; ++s) {
-            const int ta = perm[1 + s];
-            const int stt = st[ta];
-            const R* ict = ta == 0 ? icx : (ta == 1 ? icy : icz);
-            const int hcell[3] = {ci + H, cj + (D >= 2 ? H : 0), ck + (D >= 3 ? H : 0)};
-            const int pt = hcell[ta];
-            const R im = ict[pt], ip = ict[pt + 1];
-#pragma unroll
-            for (int v = 0; v < nv; ++v) {
-              const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
-              const R* pc = Ws + sv * G::NH + hc;
-              const R* pl = pc - sn;
-              tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) * im, (pl[stt] - pl[0]) * ip);
-              tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) * im, (pc[stt] - pc[0]) * ip);
-            }
-          }
-        }
-        const R tau_t = R(0.5) * (taus[rl] + taus[rc]);
-        R F[nv], tau;
-        face_flux<D, R, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, R(0.5) * h1, R(0.5) * h2, tau_t, dt, gas,
-                                     g.abar_t0, F, &tau);
-        Fs[0 * G::NF + f] = F[0];
-#pragma unroll
-        for (int k = 0; k < D; ++k) Fs[(1 + perm[k]) * G::NF + f] = F[1 + k];
-        Fs[(D + 1) * G::NF + f] = F[D + 1];
-        if (A.mflux[0]) {
-          // global face (cell c = tile origin + (ci, cj, ck), face c - 1/2 along ax)
-          const int gc[3] = {ox + ci, oy + cj, oz + ck};
-          int nf[3] = {g.n[0], g.n[1], g.n[2]};
-          nf[ax] += 1;
-          if (gc[0] < nf[0] && gc[1] < nf[1] && gc[2] < nf[2])
-            ((R*)A.mflux[ax])[((long)gc[2] * nf[1] + gc[1]) * nf[0] + gc[0]] = F[0];
+          wl[v] = cl[v];
+          sl[v] = R(0);
         }
       }
-      if constexpr (kThreads % 128 == 0)
-        asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");
-      else
-        __syncwarp();
+      if (!physical<D, R>(gamma, wr)) {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) {
+          wr[v] = cr[v];
+          sr[v] = R(0);
+        }
+      }
+      if (MULTID && PRE) {
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) {
+          const int ta = perm[1 + s];
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+            in.tl[s][v] = Ss[(ta * nv + sv) * G::NR + rl];
+            in.tr[s][v] = Ss[(ta * nv + sv) * G::NR + rc];
+          }
+        }
+      } else if (MULTID) {
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) {
+          const int ta = perm[1 + s];
+          const int stt = st[ta];
+          const R* ict = ta == 0 ? icx : (ta == 1 ? icy : icz);
+          const int hcell[3] = {ci + H, cj + (D >= 2 ? H : 0), ck + (D >= 3 ? H : 0)};
+          const int pt = hcell[ta];
+          const R im = ict[pt], ip = ict[pt + 1];
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            const int sv = (v >= 1 && v <= D) ? 1 + perm[v - 1] : v;
+            const R* pc = Ws + sv * G::NH + hc;
+            const R* pl = pc - sn;
+            in.tl[s][v] = limiter<R>(g.limiter, (pl[0] - pl[-stt]) * im, (pl[stt] - pl[0]) * ip);
+            in.tr[s][v] = limiter<R>(g.limiter, (pc[0] - pc[-stt]) * im, (pc[stt] - pc[0]) * ip);
+          }
+        }
+      }
+      in.dxl = R(0.5) * h1;
+      in.dxr = R(0.5) * h2;
+      in.tau_t = R(0.5) * (taus[rl] + taus[rc]);
+    };
+    // the flux of face f back in the grid frame; with a mass-flux output (k-omega transport) also
+    // the face's time-integrated mass flux
+    auto store = [&](int f, const FaceIn& in, const R* F) {
+      Fs[0 * G::NF + f] = F[0];
+#pragma unroll
+      for (int k = 0; k < D; ++k) Fs[(1 + in.perm[k]) * G::NF + f] = F[1 + k];
+      Fs[(D + 1) * G::NF + f] = F[D + 1];
+      if (A.mflux[0]) {
+        // global face (cell c = tile origin + (ci, cj, ck), face c - 1/2 along ax)
+        const int gc[3] = {ox + in.ci, oy + in.cj, oz + in.ck};
+        int nf[3] = {g.n[0], g.n[1], g.n[2]};
+        nf[in.ax] += 1;
+        if (gc[0] < nf[0] && gc[1] < nf[1] && gc[2] < nf[2])
+          ((R*)A.mflux[in.ax])[((long)gc[2] * nf[1] + gc[1]) * nf[0] + gc[0]] = F[0];
+      }
+    };
+    // Rounds of kThreads faces (of 2 kThreads faces, two per thread, on the paired tiles); after each
+    // round the warps of every 128-thread group meet at a named barrier, so that the warps sharing an
+    // SM sub-partition run the ~1000-instruction face body close together and share its instruction
+    // fetches.  Every thread runs every round.
+    if constexpr (PAIR) {
+      // two faces per thread, fa and fb = fa + kThreads, evaluated together with paired FP32
+      // instructions (lane x: fa, lane y: fb; a missing fb repeats fa and is not stored)
+      Gas<F2> gas2;
+      gas2.bK = F2(kc.bK);
+      gas2.K = F2(kc.K);
+      gas2.mu = F2(kc.mu);
+      gas2.C_a = F2(kc.C_a);
+      constexpr int kRounds2 = (G::NF + 2 * kThreads - 1) / (2 * kThreads);
+      for (int it = 0; it < kRounds2; ++it) {
+        const int fa = tid + 2 * it * kThreads, fb = fa + kThreads;
+        if (fa < G::NF) {
+          FaceIn a, b;
+          prep(fa, a);
+          prep(fb < G::NF ? fb : fa, b);
+          F2 wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv], tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            wl[v] = F2(a.wl[v], b.wl[v]);
+            wr[v] = F2(a.wr[v], b.wr[v]);
+            cl[v] = F2(a.cl[v], b.cl[v]);
+            cr[v] = F2(a.cr[v], b.cr[v]);
+            sl[v] = F2(a.sl[v], b.sl[v]);
+            sr[v] = F2(a.sr[v], b.sr[v]);
+#pragma unroll
+            for (int s = 0; s < Dims<D>::nt; ++s) {
+              tl[s][v] = F2(a.tl[s][v], b.tl[s][v]);
+              tr[s][v] = F2(a.tr[s][v], b.tr[s][v]);
+            }
+          }
+          F2 F[nv], tau;
+          face_flux<D, F2, MULTID, false>(wl, wr, cl, cr, sl, sr, tl, tr, F2(a.dxl, b.dxl), F2(a.dxr, b.dxr),
+                                          F2(a.tau_t, b.tau_t), F2(dt), gas2, g.abar_t0, F, &tau);
+          R Fa[nv], Fb[nv];
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            Fa[v] = F[v].v.x;
+            Fb[v] = F[v].v.y;
+          }
+          store(fa, a, Fa);
+          if (fb < G::NF) store(fb, b, Fb);
+        }
+        if constexpr (kThreads % 128 == 0)
+          asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");
+        else
+          __syncwarp();
+      }
+    } else {
+      constexpr int kRounds = (G::NF + kThreads - 1) / kThreads;
+      for (int it = 0; it < kRounds; ++it) {
+        const int f = tid + it * kThreads;
+        if (f < G::NF) {
+          FaceIn in;
+          prep(f, in);
+          R F[nv], tau;
+          face_flux<D, R, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
+                                       in.tau_t, dt, gas, g.abar_t0, F, &tau);
+          store(f, in, F);
+        }
+        if constexpr (kThreads % 128 == 0)
+          asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");
+        else
+          __syncwarp();
+      }
     }
   }
   // double state: the old doubles of this thread's cells are loaded while the CTA meets at the barrier
@@ -1142,7 +1224,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
 }
 
 template <int D, int V = 0> constexpr int min_blocks(int prec) {
-  return prec != PREC_F64 ? 512 / Tile<D, V>::T : 1;
+  return prec != PREC_F64 ? (paired_tile<D, V>() ? 256 : 512) / Tile<D, V>::T : 1;
 }
 
 template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2, bool RAR = false>
@@ -1171,9 +1253,10 @@ struct BatchArgs {
   int phase;                // k mod 6 of the launch (fixed by the position in a captured chunk)
 };
 
-// Persistent CTAs stride over the work items of one step.
-template <int D, int PREC, bool MULTID>
-__global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) batch_step_kernel(const __grid_constant__ BatchArgs B) {
+// Persistent CTAs stride over the work items of one step.  V: the tile shape (the items are tiles of
+// that shape; the server picks one per group).
+template <int D, int PREC, bool MULTID, int V = 0>
+__global__ void __launch_bounds__(Tile<D, V>::T, min_blocks<D, V>(PREC)) batch_step_kernel(const __grid_constant__ BatchArgs B) {
   const int tslot = B.phase & 1;
   const long long k = B.counter[tslot];
   if (blockIdx.x == 0 && threadIdx.x == 0) B.counter[tslot ^ 1] = k + 1;
@@ -1181,24 +1264,32 @@ __global__ void __launch_bounds__(kThreads, min_blocks<D>(PREC)) batch_step_kern
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = B.items[it];
     const BatchSolve& S = B.solves[w.x];
-    if (k < S.stop_at) step_tile<D, PREC, MULTID>(S.args[B.phase], w.y);
+    if (k < S.stop_at) step_tile<D, PREC, MULTID, V>(S.args[B.phase], w.y);
     __syncthreads();
   }
 }
 
-template <int D, int PREC, bool MULTID>
-void launch_batch(const BatchArgs& B, int nblocks, cudaStream_t s) {
+template <int D, int PREC, bool MULTID, int V = 0>
+size_t batch_smem() {
   using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
-  batch_step_kernel<D, PREC, MULTID><<<nblocks, kThreads, sm, s>>>(B);
+  return TileGeom<D, V>::template smem_bytes<R>(pre_slopes<D, PREC, V>(), PREC == PREC_F32);
 }
 
-template <int D, int PREC, bool MULTID>
-cudaError_t prepare_batch() {
-  using R = typename PrecT<PREC>::R;
-  const size_t sm = TileGeom<D>::template smem_bytes<R>(pre_slopes<D, PREC>(), PREC == PREC_F32);
-  return cudaFuncSetAttribute(batch_step_kernel<D, PREC, MULTID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sm);
+template <int D, int PREC, bool MULTID, int V = 0>
+void launch_batch(const BatchArgs& B, int nblocks, cudaStream_t s) {
+  batch_step_kernel<D, PREC, MULTID, V><<<nblocks, Tile<D, V>::T, batch_smem<D, PREC, MULTID, V>(), s>>>(B);
+}
+
+// Sets the kernel's shared-memory limit; *resident (if given) receives the CTAs per SM that fit.
+template <int D, int PREC, bool MULTID, int V = 0>
+cudaError_t prepare_batch(int* resident = nullptr) {
+  const size_t sm = batch_smem<D, PREC, MULTID, V>();
+  cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<D, PREC, MULTID, V>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess && resident)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, batch_step_kernel<D, PREC, MULTID, V>, Tile<D, V>::T,
+                                                      sm);
+  return e;
 }
 
 template <int D, int PREC, bool MULTID, int V = 0, int RECON = RECON_MUSCL2, bool RAR = false>

@@ -24,16 +24,22 @@ void launch_step_d1(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
 }
 
 
-cudaError_t prepare_batch_d1() {
+// Batch kernels of 1D solves: tile variants 0 (256 cells), 1 (31), 2 (63) in FP32, variant 0 in FP64.
+// resident[v]: CTAs per SM of variant v (FP32), or of variant 0 (FP64, resident[0]).
+cudaError_t prepare_batch_d1(int prec, int* resident) {
   cudaError_t e = cudaSuccess, r;
-  if ((r = prepare_batch<1, PREC_F64, false>()) != cudaSuccess) e = r;
-  if ((r = prepare_batch<1, PREC_F32, false>()) != cudaSuccess) e = r;
+  if (prec == PREC_F64) return prepare_batch<1, PREC_F64, false, 0>(&resident[0]);
+  if ((r = prepare_batch<1, PREC_F32, false, 0>(&resident[0])) != cudaSuccess) e = r;
+  if ((r = prepare_batch<1, PREC_F32, false, 1>(&resident[1])) != cudaSuccess) e = r;
+  if ((r = prepare_batch<1, PREC_F32, false, 2>(&resident[2])) != cudaSuccess) e = r;
   return e;
 }
 
-void launch_batch_d1(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s) {
-  if (prec == PREC_F64) launch_batch<1, PREC_F64, false>(B, nblocks, s);
-  else launch_batch<1, PREC_F32, false>(B, nblocks, s);
+void launch_batch_d1(int prec, int variant, const BatchArgs& B, int nblocks, cudaStream_t s) {
+  if (prec == PREC_F64) launch_batch<1, PREC_F64, false, 0>(B, nblocks, s);
+  else if (variant == 1) launch_batch<1, PREC_F32, false, 1>(B, nblocks, s);
+  else if (variant == 2) launch_batch<1, PREC_F32, false, 2>(B, nblocks, s);
+  else launch_batch<1, PREC_F32, false, 0>(B, nblocks, s);
 }
 
 

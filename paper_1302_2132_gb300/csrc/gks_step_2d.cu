@@ -31,23 +31,47 @@ void launch_step_d2(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
 }
 
 
-cudaError_t prepare_batch_d2() {
+// Batch kernels of 2D solves: in FP32 the tile variants 0 (32x15), 1 (64x7), 3 (32x27), 4 (32x18) of
+// both expansions, in FP64 variant 0.  resident[2 v + multid]: CTAs per SM.
+template <int V>
+cudaError_t prep_b2(int* resident) {
+  cudaError_t e = prepare_batch<2, PREC_F32, false, V>(&resident[2 * V]);
+  const cudaError_t f = prepare_batch<2, PREC_F32, true, V>(&resident[2 * V + 1]);
+  return e != cudaSuccess ? e : f;
+}
+
+cudaError_t prepare_batch_d2(int prec, int* resident) {
+  if (prec == PREC_F64) {
+    const cudaError_t e = prepare_batch<2, PREC_F64, false, 0>(&resident[0]);
+    const cudaError_t f = prepare_batch<2, PREC_F64, true, 0>(&resident[1]);
+    return e != cudaSuccess ? e : f;
+  }
   cudaError_t e = cudaSuccess, r;
-  if ((r = prepare_batch<2, PREC_F64, false>()) != cudaSuccess) e = r;
-  if ((r = prepare_batch<2, PREC_F32, false>()) != cudaSuccess) e = r;
-  if ((r = prepare_batch<2, PREC_F64, true>()) != cudaSuccess) e = r;
-  if ((r = prepare_batch<2, PREC_F32, true>()) != cudaSuccess) e = r;
+  if ((r = prep_b2<0>(resident)) != cudaSuccess) e = r;
+  if ((r = prep_b2<1>(resident)) != cudaSuccess) e = r;
+  if ((r = prep_b2<3>(resident)) != cudaSuccess) e = r;
+  if ((r = prep_b2<4>(resident)) != cudaSuccess) e = r;
   return e;
 }
 
-void launch_batch_d2(int prec, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s) {
-  if (multid) {
-    if (prec == PREC_F64) launch_batch<2, PREC_F64, true>(B, nblocks, s);
-    else launch_batch<2, PREC_F32, true>(B, nblocks, s);
+template <int V>
+void launch_b2(bool multid, const BatchArgs& B, int nblocks, cudaStream_t s) {
+  if (multid) launch_batch<2, PREC_F32, true, V>(B, nblocks, s);
+  else launch_batch<2, PREC_F32, false, V>(B, nblocks, s);
+}
+
+void launch_batch_d2(int prec, int variant, bool multid, const BatchArgs& B, int nblocks, cudaStream_t s) {
+  if (prec == PREC_F64) {
+    if (multid) launch_batch<2, PREC_F64, true, 0>(B, nblocks, s);
+    else launch_batch<2, PREC_F64, false, 0>(B, nblocks, s);
     return;
   }
-  if (prec == PREC_F64) launch_batch<2, PREC_F64, false>(B, nblocks, s);
-  else launch_batch<2, PREC_F32, false>(B, nblocks, s);
+  switch (variant) {
+    case 1: launch_b2<1>(multid, B, nblocks, s); break;
+    case 3: launch_b2<3>(multid, B, nblocks, s); break;
+    case 4: launch_b2<4>(multid, B, nblocks, s); break;
+    default: launch_b2<0>(multid, B, nblocks, s); break;
+  }
 }
 
 }  // namespace gks

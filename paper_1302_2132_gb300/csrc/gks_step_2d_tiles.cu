@@ -14,7 +14,9 @@ cudaError_t prepare_step_d2_variants() {
 }
 
 void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
-  if (variant >= 3) {
+  if (variant >= 6) {
+    launch_step_pair(2, PREC_F32, variant, multid, A, nblocks, s);
+  } else if (variant >= 3) {
     launch_step_d2_variant2(variant, multid, A, nblocks, s);
   } else if (variant == 1) {
     if (multid) launch_step<2, PREC_F32, true, 1>(A, nblocks, s);
@@ -33,7 +35,8 @@ void tile_shape(int D, int variant, int* x, int* y, int* z) {
     return;
   }
   if (D == 3) {
-    if (variant == 1) { *x = Tile<3, 1>::X; *y = Tile<3, 1>::Y; *z = Tile<3, 1>::Z; }
+    if (variant == 3) { *x = Tile<3, 3>::X; *y = Tile<3, 3>::Y; *z = Tile<3, 3>::Z; }
+    else if (variant == 1) { *x = Tile<3, 1>::X; *y = Tile<3, 1>::Y; *z = Tile<3, 1>::Z; }
     else if (variant == 2) { *x = Tile<3, 2>::X; *y = Tile<3, 2>::Y; *z = Tile<3, 2>::Z; }
     else { *x = Tile<3, 0>::X; *y = Tile<3, 0>::Y; *z = Tile<3, 0>::Z; }
     return;
@@ -43,6 +46,8 @@ void tile_shape(int D, int variant, int* x, int* y, int* z) {
   else if (variant == 3) { *x = Tile<2, 3>::X; *y = Tile<2, 3>::Y; }
   else if (variant == 4) { *x = Tile<2, 4>::X; *y = Tile<2, 4>::Y; }
   else if (variant == 5) { *x = Tile<2, 5>::X; *y = Tile<2, 5>::Y; }
+  else if (variant == 6) { *x = Tile<2, 6>::X; *y = Tile<2, 6>::Y; }
+  else if (variant == 7) { *x = Tile<2, 7>::X; *y = Tile<2, 7>::Y; }
   else { *x = Tile<2, 0>::X; *y = Tile<2, 0>::Y; }
   *z = 1;
 }

@@ -15,7 +15,9 @@ cudaError_t prepare_step_d3_variants() {
 }
 
 void launch_step_d3_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
-  if (variant == 1) {
+  if (variant == 3) {
+    launch_step_pair(3, PREC_F32, 3, multid, A, nblocks, s);
+  } else if (variant == 1) {
     if (multid) launch_step<3, PREC_F32, true, 1>(A, nblocks, s);
     else launch_step<3, PREC_F32, false, 1>(A, nblocks, s);
   } else {

@@ -28,8 +28,13 @@ void launch_acc64(bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
 
 void launch_step_acc64_variant(int D, int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s) {
   if (D == 3) {
-    if (variant == 1) launch_acc64<3, 1>(multid, A, nblocks, s);
+    if (variant == 3) launch_step_pair(3, PREC_F32D, 3, multid, A, nblocks, s);
+    else if (variant == 1) launch_acc64<3, 1>(multid, A, nblocks, s);
     else launch_acc64<3, 2>(multid, A, nblocks, s);
+    return;
+  }
+  if (variant >= 6) {
+    launch_step_pair(2, PREC_F32D, variant, multid, A, nblocks, s);
     return;
   }
   switch (variant) {

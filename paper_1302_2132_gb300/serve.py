@@ -33,8 +33,9 @@ def _lib():
         L.gks_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                                        ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)]
         L.gks_server_destroy.argtypes = [P]
+        L.gks_server_tile_variants.argtypes = [P, ctypes.POINTER(_I)]
         for f in ("gks_server_create", "gks_server_submit", "gks_server_poll", "gks_server_wait_all",
-                  "gks_server_stats", "gks_server_destroy"):
+                  "gks_server_stats", "gks_server_destroy", "gks_server_tile_variants"):
             getattr(L, f).restype = _I
         L._serve_ready = True
     return L
@@ -96,6 +97,12 @@ class Server:
                                 ctypes.byref(busy))
         return {"completed": c.value, "p50_s": p50.value, "p99_s": p99.value, "solves_per_s": sps.value,
                 "gpu_busy_s": busy.value}
+
+    def tile_variants(self):
+        """Tile shape (gks_tile_shape variant) of each group's batch kernel: 1D, 2D, 2D multi-D."""
+        v = (_I * 3)()
+        _lib().gks_server_tile_variants(self._h, v)
+        return list(v)
 
     def close(self):
         if self._h is not None:

@@ -357,12 +357,13 @@ def test_full_size_2d_turbulence_sampled_cells(prec):
 
 
 def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
-    """The six 2D FP32 tile shapes evaluate the same faces: their results agree to FP32 rounding
-    (different compiled kernels), and the autotuner keeps one of them."""
+    """The eight 2D FP32 tile shapes (two of them evaluating two faces per thread with paired
+    instructions) evaluate the same faces: their results agree to FP32 rounding (different compiled
+    kernels), and the autotuner keeps one of them."""
     spec = inputs.turbulence(100, 2, seed=8)
     kw = dict(turb_model=2, multid=1, mu=1e-5, precision="fp32")
     out = []
-    for v in ("0", "1", "2", "3", "4", "5"):
+    for v in ("0", "1", "2", "3", "4", "5", "6", "7"):
         monkeypatch.setenv("GKS_TILE_VARIANT", v)
         s = gpu_solver(spec, **kw)
         s.set_state(spec["prim"].ravel(), layout="soa_prim")
@@ -379,7 +380,7 @@ def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
     s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
     s.step(nsteps=30, cfl=0.5)
     v = s.tile_shape()
-    assert v[0] in (0, 1, 2, 3, 4, 5) and v[1] * v[2] in (480, 448, 992, 864, 576, 1728)
+    assert v[0] in range(8) and v[1] * v[2] in (480, 448, 992, 864, 576, 1728)
     assert np.all(rel_err_per_var(s.get_state(), out[0], 4) < 1e-6)
     s.close()
 
@@ -396,12 +397,12 @@ def test_1d_tile_variants_match_oracle(monkeypatch, variant):
 
 
 def test_3d_tile_variants_agree(monkeypatch):
-    """The three 3D FP32 tile shapes (16x8x4 without the slope table, 16x8x2 and 8x8x4 with it)
-    evaluate the same faces: their results agree to FP32 rounding."""
+    """The four 3D FP32 tile shapes (16x8x4 without the slope table, 16x8x2 and 8x8x4 with it, and
+    16x8x2 with two faces per thread) evaluate the same faces: their results agree to FP32 rounding."""
     spec = inputs.turbulence(20, 3, seed=17)
     kw = dict(turb_model=2, multid=1, mu=1e-5, precision="fp32")
     out = []
-    for v in ("0", "1", "2"):
+    for v in ("0", "1", "2", "3"):
         monkeypatch.setenv("GKS_TILE_VARIANT", v)
         s = gpu_solver(spec, **kw)
         s.set_state(spec["prim"].ravel(), layout="soa_prim")
