@@ -248,8 +248,7 @@ def make_workload(name, precision):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the step kernel, taken from
 # one ncu capture of the same kernel build, keyed by workload and tile variant; a combination that
 # was not captured (or whose kernel changed since) reports null.
-TRAFFIC_PER_LAUNCH = {("turb2d_1024_keps_multid_fp32", 3): 44.319232e6,
-                      ("turb2d_1024_keps_multid_fp32", 5): 43.990528e6}
+TRAFFIC_PER_LAUNCH = {("turb2d_1024_keps_multid_fp32_acc64", 3): 43.523e6}
 
 
 def faces_of(n, bc=None):

@@ -495,10 +495,18 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
         win = (R)SA.cfl_flux * fmin(sloc[field_cell(g, 2, ai, aj, 0)], sloc[field_cell(g, 2, ox + li, oy + lj, 0)]);
         Ls = L / win;
       }
-      if (MD && !fo)
-        face_flux<2, R, true, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
-      else
-        face_flux<2, R, false, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+      if constexpr (std::is_same<R, float>::value) {
+        // single precision: the two sides of the face on the paired FP32 instructions
+        if (MD && !fo)
+          face_flux_ps<2, true, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+        else
+          face_flux_ps<2, false, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+      } else {
+        if (MD && !fo)
+          face_flux<2, R, true, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+        else
+          face_flux<2, R, false, RAR>(wl, wr, cl, cr, sl, sr, tl, trr, dl, dr, tau_t, win, gas, g.abar_t0, F, &tau);
+      }
       const R L_ = Ls;
       Fs[l] = F[0] * L_;
       Fs[NF + l] = (F[1] * nx - F[2] * ny) * L_;

@@ -36,7 +36,12 @@ __global__ void __launch_bounds__(128) face_kernel(int abar_t0, double gamma, do
   gas.mu = (R)mu;
   gas.C_a = (R)C_a;
   R F[nv], tau;
-  face_flux<D, R, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, tau_t, (R)dt, gas, abar_t0, F, &tau);
+  // the same flux code as the step kernels: in single precision below three dimensions the two sides
+  // of the face on the paired FP32 instructions
+  if constexpr (std::is_same<R, float>::value && D <= 2)
+    face_flux_ps<D, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, tau_t, (R)dt, gas, abar_t0, F, &tau);
+  else
+    face_flux<D, R, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, tau_t, (R)dt, gas, abar_t0, F, &tau);
 #pragma unroll
   for (int v = 0; v < nv; ++v) Fout[f * nv + v] = (double)F[v];
   if (tout) tout[f] = (double)tau;

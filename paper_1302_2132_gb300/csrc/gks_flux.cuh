@@ -631,11 +631,10 @@ GKS_FN T amom_rho(const T* u, const Trans<D, T>& t, int k, int tg, const T* a) {
 // tautilde): d_t rho = -rho0 (<abar_l . psi u>_{u>0} + <abar_r . psi u>_{u<0} + <bbar . psi v>) from
 // the t = 0 compatibility condition of the equilibrium part, d_n rho the mean of the density slopes
 // (w0 - W_j)/dxl and (W_{j+1} - w0)/dxr.  Slopes and moments of g0 as in face_flux.
-template <int D, class T, bool MULTID>
-GKS_FN T face_drho(const Maxw<D, T>& g0, const T* w0, const T* cl, const T* cr, const T (*tl)[D + 2],
-                   const T (*tr)[D + 2], T dxl, T dxr, T i0, T bK, T K) {
+template <int D, class T, bool MULTID, class In>
+GKS_FN T face_drho(const Maxw<D, T>& g0, const T* w0, const In& in, T dxl, T dxr, T i0, T bK, T K) {
   constexpr int nv = D + 2;
-  const T dn = T(0.5) * (g_div(w0[0] - cl[0], dxl) + g_div(cr[0] - w0[0], dxr));
+  const T dn = T(0.5) * (g_div(w0[0] - in.c(0, 0), dxl) + g_div(in.c(1, 0) - w0[0], dxr));
   Trans<D, T> t0;
   transverse<D, T>(g0, K, t0);
   T oF[7], oP[7], half[7], r[nv], ab[nv];
@@ -643,11 +642,11 @@ GKS_FN T face_drho(const Maxw<D, T>& g0, const T* w0, const T* cl, const T* cr, 
   u_half<D, T>(g0, T(1), oP);
   const T fl = g_div(i0, dxl), fr = g_div(i0, dxr);
 #pragma unroll
-  for (int m = 0; m < nv; ++m) r[m] = (w0[m] - cl[m]) * fl;
+  for (int m = 0; m < nv; ++m) r[m] = (w0[m] - in.c(0, m)) * fl;
   slope<D, T>(g0, bK, r, ab);
   T x1 = amom_rho<D, T>(oP, t0, 1, -1, ab);
 #pragma unroll
-  for (int m = 0; m < nv; ++m) r[m] = (cr[m] - w0[m]) * fr;
+  for (int m = 0; m < nv; ++m) r[m] = (in.c(1, m) - w0[m]) * fr;
   slope<D, T>(g0, bK, r, ab);
 #pragma unroll
   for (int n = 0; n < 7; ++n) half[n] = oF[n] - oP[n];
@@ -656,7 +655,7 @@ GKS_FN T face_drho(const Maxw<D, T>& g0, const T* w0, const T* cl, const T* cr, 
 #pragma unroll
     for (int q = 0; q < D - 1; ++q) {
 #pragma unroll
-      for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (tl[q][m] + tr[q][m]) * i0;
+      for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (in.t(0, q, m) + in.t(1, q, m)) * i0;
       slope<D, T>(g0, bK, r, ab);
       x1 += amom_rho<D, T>(oF, t0, 0, q, ab);
     }
@@ -676,10 +675,13 @@ GKS_FN T face_drho(const Maxw<D, T>& g0, const T* w0, const T* cl, const T* cr, 
 // Abar term of the flux waits for Abar.
 // RAR: the rarefaction option -- the degree of rarefaction eps = tau/tauhat, tauhat = rho0/|D rho|
 // (capped at 1e30), replaces tau/dt inside the time coefficients (Eq. epsilonkomega).
-template <int D, class T, bool MULTID, bool RAR = false>
-GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const T* sl, const T* sr,
-                      const T (*tl)[D + 2], const T (*tr)[D + 2], T dxl, T dxr, T tau_t, T dt, const Gas<T>& gas,
-                      int abar_t0, T* F, T* tau_out) {
+//
+// The inputs other than wl, wr come through an accessor `in` (FaceArrays below, or a view of a
+// shared-memory tile): in.s(sd, m) the normal slope, in.c(sd, m) the cell average and in.t(sd, q, m)
+// the q-th tangential slope of component m on side sd (0 left, 1 right), each read where it is used.
+template <int D, class T, bool MULTID, bool RAR = false, class In>
+GKS_FN void face_flux_in(const T* wl, const T* wr, const In& in, T dxl, T dxr, T tau_t, T dt, const Gas<T>& gas,
+                         int abar_t0, T* F, T* tau_out) {
   constexpr int nv = D + 2;
   const T bK = gas.bK, K = gas.K;
   const Maxw<D, T> gl = maxwellian<D, T>(wl, bK);
@@ -707,7 +709,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
   *tau_out = tau;
   T Tc[6], r1, r4, r5;
   if constexpr (RAR) {
-    const T drho = face_drho<D, T, MULTID>(g0, w0, cl, cr, tl, tr, dxl, dxr, g_rcp(g0.rho), bK, K);
+    const T drho = face_drho<D, T, MULTID>(g0, w0, in, dxl, dxr, g_rcp(g0.rho), bK, K);
     const T eps = drho > T(1e-30) * g0.rho ? g_div(tau * drho, g0.rho) : tau * T(1e-30);
     time_coeffs_hat<T>(dt, tau, eps, Tc, r1, r4, r5);
   } else {
@@ -740,13 +742,13 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
     for (int n = 0; n < 7; ++n) half[n] = sd ? rN[n] : lP[n];
     const T ir = g_rcp(g.rho);
 #pragma unroll
-    for (int m = 0; m < nv; ++m) r[m] = (sd ? sr[m] : sl[m]) * ir;
+    for (int m = 0; m < nv; ++m) r[m] = in.s(sd, m) * ir;
     slope<D, T>(g, bK, r, a);
     if (MULTID) {
 #pragma unroll
       for (int q = 0; q < D - 1; ++q) {
 #pragma unroll
-        for (int m = 0; m < nv; ++m) r[m] = (sd ? tr[q][m] : tl[q][m]) * ir;
+        for (int m = 0; m < nv; ++m) r[m] = in.t(sd, q, m) * ir;
         slope<D, T>(g, bK, r, b[q]);
       }
     }
@@ -796,7 +798,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
       // sd = 0: abar_l on u > 0; sd = 1: abar_r on u < 0 (table = full line minus u > 0)
       T r[nv], ab[nv], half[7];
 #pragma unroll
-      for (int m = 0; m < nv; ++m) r[m] = sd ? (cr[m] - w0[m]) * fr : (w0[m] - cl[m]) * fl;
+      for (int m = 0; m < nv; ++m) r[m] = sd ? (in.c(1, m) - w0[m]) * fr : (w0[m] - in.c(0, m)) * fl;
 #pragma unroll
       for (int n = 0; n < 7; ++n) half[n] = sd ? oF[n] - oP[n] : oP[n];
       slope<D, T>(g0, bK, r, ab);
@@ -807,7 +809,7 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
 #pragma unroll
       for (int q = 0; q < D - 1; ++q) {
 #pragma unroll
-        for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (tl[q][m] + tr[q][m]) * i0;
+        for (int m = 0; m < nv; ++m) r[m] = T(0.5) * (in.t(0, q, m) + in.t(1, q, m)) * i0;
         slope<D, T>(g0, bK, r, ab);
         amom2<D, T>(oF, tr0, 0, q, ab, r1, rhs, s1f, F);
       }
@@ -823,5 +825,207 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
     amom<D, T>(oF, tr0, 1, -1, Ab, g0.rho, F);
   }
 }
+
+// Face inputs held in the caller's arrays (registers): sl, sr normal slopes, cl, cr cell averages,
+// tl, tr tangential slopes (read only with the multi-dimensional expansion).
+template <int D, class T> struct FaceArrays {
+  const T *sl, *sr, *cl, *cr;
+  const T (*tl)[D + 2];
+  const T (*tr)[D + 2];
+  GKS_FN T s(int sd, int m) const { return sd ? sr[m] : sl[m]; }
+  GKS_FN T c(int sd, int m) const { return sd ? cr[m] : cl[m]; }
+  GKS_FN T t(int sd, int q, int m) const { return sd ? tr[q][m] : tl[q][m]; }
+};
+
+// face_flux_in with the inputs in arrays.
+template <int D, class T, bool MULTID, bool RAR = false>
+GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const T* sl, const T* sr,
+                      const T (*tl)[D + 2], const T (*tr)[D + 2], T dxl, T dxr, T tau_t, T dt, const Gas<T>& gas,
+                      int abar_t0, T* F, T* tau_out) {
+  const FaceArrays<D, T> in{sl, sr, cl, cr, tl, tr};
+  face_flux_in<D, T, MULTID, RAR>(wl, wr, in, dxl, dxr, tau_t, dt, gas, abar_t0, F, tau_out);
+}
+
+#ifndef GKS_HOST_COUNT
+// face_flux_in in single precision with the two sides of the face evaluated together on the paired
+// FP32 instructions: lane x carries the left Maxwellian on u > 0, lane y the right one on u < 0, for
+// the intermediate state, the slopes a, b, A and their parts of the Abar right-hand side and of the
+// flux; the two one-sided equilibrium slopes abar_l (u > 0) and abar_r (u < 0) are paired the same
+// way.  The paired sums are added lane x + lane y at the end of each part.  Same terms as
+// face_flux_in; only the order of the final additions differs.
+template <int D, bool MULTID, bool RAR = false, class In>
+GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float dxl, float dxr, float tau_t,
+                         float dt, const Gas<float>& gas, int abar_t0, float* F, float* tau_out) {
+  using T = float;
+  constexpr int nv = D + 2;
+  const T bK = gas.bK, K = gas.K;
+  F2 w2[nv];
+#pragma unroll
+  for (int m = 0; m < nv; ++m) w2[m] = F2(wl[m], wr[m]);
+  const Maxw<D, F2> gs = maxwellian<D, F2>(w2, F2(bK));
+  F2 hs[7];  // <u^n> over u > 0 (left) and u < 0 (right)
+  u_half<D, F2>(gs, F2(1.0f, -1.0f), hs);
+
+  // Eq. intermediatestate: w0 = rho_l <psi>_{l,u>0} + rho_r <psi>_{r,u<0}
+  T w0[nv];
+  {
+    F2 ab[nv], m1[D + 1];
+    trans_mean<D, F2>(gs, F2(K), m1);
+    psi_mean<D, F2>(hs, m1, ab);
+#pragma unroll
+    for (int m = 0; m < nv; ++m) {
+      const F2 q = F2(gs.rho * ab[m]);
+      w0[m] = q.v.x + q.v.y;
+    }
+  }
+  const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK);
+
+  // Eqs. relaxation time and taua
+  const F2 plr = F2(gs.rho * gs.il);
+  const T p0 = g0.rho * g0.il, pl = plr.v.x, pr = plr.v.y;
+  const T tau = g_div(gas.mu, p0) + tau_t + g_div(gas.C_a * g_abs(pr - pl), pr + pl) * dt;
+  *tau_out = tau;
+  T Tc[6], r1, r4, r5;
+  if constexpr (RAR) {
+    const T drho = face_drho<D, T, MULTID>(g0, w0, in, dxl, dxr, g_rcp(g0.rho), bK, K);
+    const T eps = drho > T(1e-30) * g0.rho ? g_div(tau * drho, g0.rho) : tau * T(1e-30);
+    time_coeffs_hat<T>(dt, tau, eps, Tc, r1, r4, r5);
+  } else {
+    time_coeffs<T>(dt, tau, Tc, r1, r4, r5);
+  }
+  if (abar_t0) {
+    r1 = T(-1);
+    r4 = r5 = T(0);
+  }
+  const T i0 = g_rcp(g0.rho);
+
+  T rhs[nv];
+  // the two sides of the initial state: slopes a (normal), b (tangential), A (Eq. initialf0)
+  {
+    Trans<D, F2> ts;
+    transverse<D, F2>(gs, F2(K), ts);
+    F2 a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
+    const F2 ir = g_rcp(gs.rho);
+#pragma unroll
+    for (int m = 0; m < nv; ++m) r[m] = F2(F2(in.s(0, m), in.s(1, m)) * ir);
+    slope<D, F2>(gs, F2(bK), r, a);
+    if (MULTID) {
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+#pragma unroll
+        for (int m = 0; m < nv; ++m) r[m] = F2(F2(in.t(0, q, m), in.t(1, q, m)) * ir);
+        slope<D, F2>(gs, F2(bK), r, b[q]);
+      }
+    }
+    // A from the compatibility condition at t = 0: <(a u + b v + A) psi> = 0 (full line)
+    {
+      F2 uf[7];
+      u_full<D, F2>(gs, uf);
+#pragma unroll
+      for (int m = 0; m < nv; ++m) r[m] = F2(0.0f);
+      amom<D, F2>(uf, ts, 1, -1, a, F2(-1.0f), r);
+      if (MULTID) {
+#pragma unroll
+        for (int q = 0; q < D - 1; ++q) amom<D, F2>(uf, ts, 0, q, b[q], F2(-1.0f), r);
+      }
+      slope<D, F2>(gs, F2(bK), r, A);
+    }
+    // Abar rhs r4 rho/rho0 <(a u + b v) psi> + r5 rho/rho0 <A psi> and the flux
+    // rho [T3 <u psi> + T5 <u A psi> + T4 (<u^2 a psi> + <u v b psi>)], over each side's half line
+    const F2 s4 = F2(F2(r4 * i0) * gs.rho), s5 = F2(F2(r5 * i0) * gs.rho), s4f = F2(F2(Tc[4]) * gs.rho);
+    F2 rh2[nv], F2s[nv];
+#pragma unroll
+    for (int m = 0; m < nv; ++m) rh2[m] = F2s[m] = F2(0.0f);
+    amom2<D, F2>(hs, ts, 1, -1, a, s4, rh2, s4f, F2s);
+    amom2<D, F2>(hs, ts, 0, -1, A, s5, rh2, F2(F2(Tc[5]) * gs.rho), F2s);
+    {
+      F2 m[nv];
+      psi_mean<D, F2>(hs + 1, ts.m1, m);  // <u psi> over the half line
+      const F2 s3 = F2(F2(Tc[3]) * gs.rho);
+#pragma unroll
+      for (int q = 0; q < nv; ++q) F2s[q] += s3 * m[q];
+    }
+    if (MULTID) {
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) amom2<D, F2>(hs, ts, 0, q, b[q], s4, rh2, s4f, F2s);
+    }
+#pragma unroll
+    for (int m = 0; m < nv; ++m) {
+      rhs[m] = rh2[m].v.x + rh2[m].v.y;
+      F[m] = F2s[m].v.x + F2s[m].v.y;
+    }
+  }
+
+  // equilibrium g0: Eq. eqlgform slopes from W_j -> w0 -> W_{j+1} (and the mean tangential slope)
+  Trans<D, T> tr0;
+  transverse<D, T>(g0, K, tr0);
+  T oF[7], oP[7];
+  u_full<D, T>(g0, oF);
+  u_half<D, T>(g0, T(1), oP);
+  {
+    // lane x: abar_l on u > 0; lane y: abar_r on u < 0 (table = full line minus u > 0)
+    const T fl = g_div(i0, dxl), fr = g_div(i0, dxr);
+    Maxw<D, F2> g02;
+    g02.rho = F2(g0.rho);
+#pragma unroll
+    for (int i = 0; i < D; ++i) g02.U[i] = F2(g0.U[i]);
+    g02.lam = F2(g0.lam);
+    g02.il = F2(g0.il);
+    g02.c = F2(g0.c);
+    g02.f4 = F2(g0.f4);
+    Trans<D, F2> t02;
+#pragma unroll
+    for (int b = 0; b <= D; ++b) {
+      t02.m1[b] = F2(tr0.m1[b]);
+#pragma unroll
+      for (int c = 0; c <= D; ++c) t02.m2[b][c] = F2(tr0.m2[b][c]);
+    }
+    F2 r[nv], ab[nv], half[7];
+#pragma unroll
+    for (int m = 0; m < nv; ++m) r[m] = F2(F2(w0[m] - in.c(0, m), in.c(1, m) - w0[m]) * F2(fl, fr));
+#pragma unroll
+    for (int n = 0; n < 7; ++n) half[n] = F2(oP[n], oF[n] - oP[n]);
+    slope<D, F2>(g02, F2(bK), r, ab);
+    F2 rh2[nv], F2s[nv];
+#pragma unroll
+    for (int m = 0; m < nv; ++m) rh2[m] = F2s[m] = F2(0.0f);
+    amom2<D, F2>(half, t02, 1, -1, ab, F2(r1), rh2, F2(Tc[1] * g0.rho), F2s);
+#pragma unroll
+    for (int m = 0; m < nv; ++m) {
+      rhs[m] += rh2[m].v.x + rh2[m].v.y;
+      F[m] += F2s[m].v.x + F2s[m].v.y;
+    }
+    if (MULTID) {
+      const T s1f = Tc[1] * g0.rho;
+      T rr[nv], abt[nv];
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+#pragma unroll
+        for (int m = 0; m < nv; ++m) rr[m] = T(0.5) * (in.t(0, q, m) + in.t(1, q, m)) * i0;
+        slope<D, T>(g0, bK, rr, abt);
+        amom2<D, T>(oF, tr0, 0, q, abt, r1, rhs, s1f, F);
+      }
+    }
+  }
+  // Abar from the compatibility condition integrated over [0, dt]; flux rho0 <u (T0 + T2 Abar) psi>
+  {
+    T Ab[nv];
+    slope<D, T>(g0, bK, rhs, Ab);
+#pragma unroll
+    for (int m = 0; m < nv; ++m) Ab[m] *= Tc[2];
+    Ab[0] += Tc[0];
+    amom<D, T>(oF, tr0, 1, -1, Ab, g0.rho, F);
+  }
+}
+
+// face_flux_ps with the inputs in arrays.
+template <int D, bool MULTID, bool RAR = false>
+GKS_FN void face_flux_ps(const float* wl, const float* wr, const float* cl, const float* cr, const float* sl,
+                         const float* sr, const float (*tl)[D + 2], const float (*tr)[D + 2], float dxl, float dxr,
+                         float tau_t, float dt, const Gas<float>& gas, int abar_t0, float* F, float* tau_out) {
+  const FaceArrays<D, float> in{sl, sr, cl, cr, tl, tr};
+  face_flux_ps<D, MULTID, RAR>(wl, wr, in, dxl, dxr, tau_t, dt, gas, abar_t0, F, tau_out);
+}
+#endif  // GKS_HOST_COUNT
 
 }  // namespace gks

@@ -1088,8 +1088,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           FaceIn in;
           prep(f, in);
           R F[nv], tau;
-          face_flux<D, R, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
-                                       in.tau_t, dt, gas, g.abar_t0, F, &tau);
+          if constexpr (std::is_same<R, float>::value && D <= 2) {
+            // single precision: the two sides of the face on the paired FP32 instructions (in 3D the
+            // paired body does not fit the register budget of two CTAs per SM)
+            face_flux_ps<D, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
+                                         in.tau_t, dt, gas, g.abar_t0, F, &tau);
+          } else {
+            face_flux<D, R, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
+                                         in.tau_t, dt, gas, g.abar_t0, F, &tau);
+          }
           store(f, in, F);
         }
         if constexpr (kThreads % 128 == 0)
