@@ -182,9 +182,9 @@ def make_workload(name, precision):
         spec = inputs.shock_boundary_layer(nx, ny)
         return dict(spec=spec, kw=dict(gamma=1.4, mu=spec["mu"], T_wall=spec["T_wall"], turb_model="komega",
                                        beta_star=0.09, C_a=0.5, limiter="vanleer", expand="multid"),
-                    nsteps=5000, t_end=0.0, precision=precision or "fp32",
+                    nsteps=5000, t_end=0.0, precision=precision or "fp32_acc64",
                     desc="Mach 2.85 boundary layer under a 24-degree shock, %dx%d wall-clustered, k-omega tau_t, "
-                         "5000 CFL steps" % (nx, ny))
+                         "5000 CFL steps, FP32 flux with the state accumulated in IEEE double" % (nx, ny))
     if name.startswith("steady_corner_"):
         nx, ny = (int(v) for v in name.split("_")[2].split("x"))
         spec = inputs.compression_corner(nx, ny, alpha_deg=24.0)
@@ -240,8 +240,9 @@ def make_workload(name, precision):
         n3 = int(name.split("_")[1])
         spec = inputs.turbulence(n3, 3, seed=2132)
         return dict(spec=spec, kw=dict(gamma=1.4, mu=MU, turb_model="keps", C_mu=0.09, C_a=0.0, limiter="vanleer",
-                                       expand="multid"), nsteps=100, t_end=0.0, precision=precision or "fp32",
-                    desc="3D decaying turbulence %d^3, k-epsilon tau_t, multi-D, 100 CFL steps" % n3)
+                                       expand="multid"), nsteps=100, t_end=0.0, precision=precision or "fp32_acc64",
+                    desc="3D decaying turbulence %d^3, k-epsilon tau_t, multi-D, 100 CFL steps, FP32 flux with the "
+                         "state accumulated in IEEE double" % n3)
     raise ValueError(name)
 
 
@@ -586,7 +587,7 @@ def run_ours(args):
     tile = solver.tile_shape()
     # on body-fitted grids the MUSCL-2 step in FP64 or the FP32 float-pair form carries the transport
     fused_tr = transport and curv and args.reconstruction == "muscl2" and wl["precision"] in ("fp32", "fp64")
-    tile_info = {"variant": tile[0], "cells": list(tile[1:3]), "chosen_by": "autotuner"}
+    tile_info = {"variant": tile[0], "cells": list(tile[1:1 + D]), "chosen_by": "autotuner"}
     line = {
         "metric": "interface flux evals/sec and cell-updates/sec (% roofline); serving solves/sec, p50/p99",
         "value": value,
@@ -633,7 +634,8 @@ def run_ours(args):
         "total_mass": float(total[0]),
     }
     line["config"]["tile"] = tile_info
-    if args.workload == "turb2d_1024" and args.precision is None and args.reconstruction == "muscl2":
+    if (args.workload in ("turb2d_1024", "shock_bl_1024x384", "turb3d_256") and args.precision is None
+            and args.reconstruction == "muscl2" and args.rarefaction == "dt"):
         # the float-pair form of the same workload, timed the same way: a second, labelled figure
         line["float_pair_form"] = time_other_form(args, wl, "fp32", faces_per_step, nsteps, ops_per_launch, peak,
                                                   dev, flush)
@@ -656,7 +658,8 @@ def time_other_form(args, wl, precision, faces_per_step, nsteps, ops_per_launch,
     import torch
     from paper_1302_2132_gb300 import gks
     spec = wl["spec"]
-    s = gks.Solver(spec["dim"], tuple(spec["n"]), spec["bc"], dx=spec["dx"], precision=precision, **wl["kw"])
+    s = gks.Solver(spec["dim"], tuple(spec["n"]), spec["bc"], dx=spec["dx"], bc_data=spec.get("bc_prim"),
+                   precision=precision, **wl["kw"])
     prim = torch.tensor(spec["prim"].ravel(), device=dev)
     f1 = torch.tensor(spec["f1"].ravel(), device=dev)
     f2 = torch.tensor(spec["f2"].ravel(), device=dev)
@@ -687,7 +690,8 @@ def time_other_form(args, wl, precision, faces_per_step, nsteps, ops_per_launch,
             "value": faces_per_step * nsteps * args.steps / (ms / 1e3), "unit": "face_flux_evals/s",
             "ms_per_step": ms / args.steps, "avg_launch_us": kus,
             "roofline_frac": ops_per_launch / (kus * 1e-6) / 1e12 / peak,
-            "kernel": "step_kernel<2, PREC_F32, multid>", "tile": {"variant": tile[0], "cells": list(tile[1:3])}}
+            "kernel": "step_kernel<%d, PREC_F32, multid>" % spec["dim"],
+            "tile": {"variant": tile[0], "cells": list(tile[1:1 + spec["dim"]])}}
 
 
 # per-cell operations of the k-omega transport step (hand count of the kernel: per axis about 190 --

@@ -473,15 +473,26 @@ struct TimeCoef {
 // reach double precision, 12 leave a truncation below 1e-9 (enough in single precision).
 template <class T>
 GKS_FN void phi_series(T x, T& p1, T& p2, T& p3, T& e) {
-  constexpr int N = std::is_same<T, double>::value ? 18 : 12;
-  const double c[18] = {1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
-                        1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
-                        1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0,
-                        1.0 / 355687428096000.0, 1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0,
-                        1.0 / 2432902008176640000.0};
-  T s = T(c[N - 1]);
+  T s;
+  if constexpr (std::is_same<T, double>::value) {
+    const double c[18] = {1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
+                          1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
+                          1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0,
+                          1.0 / 355687428096000.0, 1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0,
+                          1.0 / 2432902008176640000.0};
+    s = c[17];
 #pragma unroll
-  for (int m = N - 2; m >= 0; --m) s = T(c[m]) - x * s;
+    for (int m = 16; m >= 0; --m) s = c[m] - x * s;
+  } else {
+    // single-precision coefficients written as such, so that no double-to-float conversion (an FP64
+    // pipe instruction) is left in the series
+    const float c[12] = {1.0f / 6, 1.0f / 24, 1.0f / 120, 1.0f / 720, 1.0f / 5040, 1.0f / 40320, 1.0f / 362880,
+                         1.0f / 3628800, 1.0f / 39916800, 1.0f / 479001600, 1.0f / 6227020800.0f,
+                         1.0f / 87178291200.0f};
+    s = T(c[11]);
+#pragma unroll
+    for (int m = 10; m >= 0; --m) s = T(c[m]) - x * s;
+  }
   p3 = s;
   p2 = T(0.5) - x * p3;
   p1 = T(1) - x * p2;

@@ -737,6 +737,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   const int oz = D >= 3 ? (b / (tiles_x * tiles_y)) * Z : 0;
   const int tid = threadIdx.x;
   const Consts<R> kc = make_consts<R>(g);
+  __shared__ R s_dtr;   // the time step in the arithmetic type, converted once per CTA
+  __shared__ int s_end;  // the time step is zero (t_end reached)
   __shared__ double s_dt;
 
   // ---- stage the tile with two halo layers, the ring's turbulence fields and the low words ------
@@ -829,6 +831,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   // the time step of this step (thread 0), read while the tile's copies are in flight
   if (tid == 0) {
     const double dtv = step_dt(A);
+    s_dtr = (R)dtv;
+    s_end = dtv == 0.0;
     s_dt = dtv;
     if (b == 0) {
       Ctrl* c = A.ctrl;
@@ -844,7 +848,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     __syncthreads();
   }
   const double dt_d = s_dt;
-  if (dt_d == 0.0) {  // t_end reached: carry the state over
+  if (s_end) {  // t_end reached: carry the state over
     for (int l = tid; l < G::NC; l += kThreads) {
       const int li = l % X, lj = (l / X) % Y, lk = l / (X * Y);
       const int gi = ox + li, gj = oy + lj, gk = oz + lk;
@@ -857,7 +861,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     }
     return;
   }
-  const R dt = (R)dt_d;
+  const R dt = s_dtr;
 
   // ---- turbulent relaxation time and limited slopes on the tile and its first halo ring -------
   ring_phase<D, PREC, V, H>(kc, g.turb_model, g.turb_cons != 0, g.limiter, Ws, Fl, taus, Ss, icx, icy, icz, igx, igy,
@@ -1029,10 +1033,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           ((R*)A.mflux[in.ax])[((long)gc[2] * nf[1] + gc[1]) * nf[0] + gc[0]] = F[0];
       }
     };
-    // Rounds of kThreads faces (of 2 kThreads faces, two per thread, on the paired tiles); after each
-    // round the warps of every 128-thread group meet at a named barrier, so that the warps sharing an
-    // SM sub-partition run the ~1000-instruction face body close together and share its instruction
-    // fetches.  Every thread runs every round.
+    // Rounds of kThreads faces (of 2 kThreads faces, two per thread, on the paired tiles).  On the
+    // paired tiles, whose face body is about twice as long, the warps of every 128-thread group meet
+    // at a named barrier after each round, so that the warps sharing an SM sub-partition run the body
+    // close together and share its instruction fetches (every thread runs every round).  With one
+    // face per thread and the two sides paired, the body is short enough that such a barrier costs
+    // more than it saves (2% on the 1024^2 workload), so those rounds run free.
     if constexpr (PAIR) {
       // two faces per thread, fa and fb = fa + kThreads, evaluated together with paired FP32
       // instructions (lane x: fa, lane y: fb; a missing fb repeats fa and is not stored)
@@ -1099,10 +1105,6 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
           }
           store(f, in, F);
         }
-        if constexpr (kThreads % 128 == 0)
-          asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");
-        else
-          __syncwarp();
       }
     }
   }
