@@ -112,6 +112,7 @@ static void count_face(int with_recon, Ops* out) {
   }
   Gas<Cnt> gas;
   gas.bK = Cnt::run(5.0);
+  gas.ibK = Cnt::run(0.2);
   gas.K = Cnt::run(5.0 - D);
   gas.mu = Cnt::run(1e-5);
   gas.C_a = Cnt::run(0.0);

@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   {
     Gas<R> gas;
     gas.bK = kc.bK;
+    gas.ibK = kc.ibK;
     gas.K = kc.K;
     gas.mu = kc.mu;
     gas.C_a = kc.C_a;

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(128) face_kernel(int abar_t0, double gamma, do
   const R dxl = (R)r[len - 3], dxr = (R)r[len - 2], tau_t = (R)r[len - 1];
   Gas<R> gas;
   gas.bK = (R)(2.0 / (gamma - 1.0));
+  gas.ibK = (R)((gamma - 1.0) / 2.0);
   gas.K = (R)(2.0 / (gamma - 1.0) - D);
   gas.mu = (R)mu;
   gas.C_a = (R)C_a;

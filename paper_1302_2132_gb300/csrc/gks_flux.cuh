@@ -115,34 +115,37 @@ template <int D> struct Dims {
 
 // Macroscopic description of one Maxwellian.
 template <int D, class T> struct Maxw {
-  T rho, U[D], lam, il;  // il = 1/(2 lambda)
+  T rho, ir, U[D], lam, il;  // ir = 1/rho, il = 1/(2 lambda)
   T c, f4;               // |U|^2 + bK il and 4 lambda^2 / bK (used by every slope solve)
 };
 
 // Gas constants used by every face.
 template <class T> struct Gas {
   T bK;   // K + D = 2/(gamma - 1)
+  T ibK;  // 1 / bK
   T K;    // internal degrees of freedom
   T mu;   // molecular viscosity (tau_mol = mu / p)
   T C_a;  // artificial-dissipation coefficient (Eq. taua)
 };
 
 // (rho, U, lambda) of the Maxwellian carrying the conservative state w (Section 2: E = (u^2 + xi^2)/2,
-// so rho E = rho |U|^2 / 2 + bK rho / (4 lambda)).
+// so rho E = rho |U|^2 / 2 + bK rho / (4 lambda)).  Two reciprocals: 1/rho, and 1/(2 lambda) =
+// (2 rho E - rho |U|^2) / (bK rho) is a product, lambda its reciprocal; ibK = 1/bK.
 template <int D, class T>
-GKS_FN Maxw<D, T> maxwellian(const T* w, T bK) {
+GKS_FN Maxw<D, T> maxwellian(const T* w, T bK, T ibK) {
   Maxw<D, T> g;
   g.rho = w[0];
+  g.ir = g_rcp(w[0]);
   T q = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    g.U[i] = g_div(w[1 + i], w[0]);
+    g.U[i] = w[1 + i] * g.ir;
     q += g.U[i] * g.U[i];
   }
-  g.lam = g_div(bK * w[0], T(4) * (w[D + 1] - T(0.5) * w[0] * q));
-  g.il = g_div(T(0.5), g.lam);
+  g.il = (T(2) * w[D + 1] - w[0] * q) * g.ir * ibK;
+  g.lam = T(0.5) * g_rcp(g.il);
   g.c = q + bK * g.il;
-  g.f4 = g_div(T(4) * g.lam * g.lam, bK);
+  g.f4 = T(4) * g.lam * g.lam * ibK;
   return g;
 }
 
@@ -694,9 +697,9 @@ template <int D, class T, bool MULTID, bool RAR = false, class In>
 GKS_FN void face_flux_in(const T* wl, const T* wr, const In& in, T dxl, T dxr, T tau_t, T dt, const Gas<T>& gas,
                          int abar_t0, T* F, T* tau_out) {
   constexpr int nv = D + 2;
-  const T bK = gas.bK, K = gas.K;
-  const Maxw<D, T> gl = maxwellian<D, T>(wl, bK);
-  const Maxw<D, T> gr = maxwellian<D, T>(wr, bK);
+  const T bK = gas.bK, K = gas.K, ibK = gas.ibK;
+  const Maxw<D, T> gl = maxwellian<D, T>(wl, bK, ibK);
+  const Maxw<D, T> gr = maxwellian<D, T>(wr, bK, ibK);
 
   // Eq. intermediatestate: w0 = rho_l <psi>_{l,u>0} + rho_r <psi>_{r,u<0}
   T w0[nv];
@@ -712,7 +715,7 @@ GKS_FN void face_flux_in(const T* wl, const T* wr, const In& in, T dxl, T dxr, T
 #pragma unroll
     for (int m = 0; m < nv; ++m) w0[m] = gl.rho * a[m] + gr.rho * b[m];
   }
-  const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK);
+  const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK, ibK);
 
   // Eqs. relaxation time and taua: tau = mu/p0 + tau_t + C_a |p_r - p_l| / (p_r + p_l) dt
   const T p0 = g0.rho * g0.il, pl = gl.rho * gl.il, pr = gr.rho * gr.il;
@@ -720,7 +723,7 @@ GKS_FN void face_flux_in(const T* wl, const T* wr, const In& in, T dxl, T dxr, T
   *tau_out = tau;
   T Tc[6], r1, r4, r5;
   if constexpr (RAR) {
-    const T drho = face_drho<D, T, MULTID>(g0, w0, in, dxl, dxr, g_rcp(g0.rho), bK, K);
+    const T drho = face_drho<D, T, MULTID>(g0, w0, in, dxl, dxr, g0.ir, bK, K);
     const T eps = drho > T(1e-30) * g0.rho ? g_div(tau * drho, g0.rho) : tau * T(1e-30);
     time_coeffs_hat<T>(dt, tau, eps, Tc, r1, r4, r5);
   } else {
@@ -730,7 +733,7 @@ GKS_FN void face_flux_in(const T* wl, const T* wr, const In& in, T dxl, T dxr, T
     r1 = T(-1);
     r4 = r5 = T(0);
   }
-  const T i0 = g_rcp(g0.rho);
+  const T i0 = g0.ir;
 
   // Abar right-hand side (per unit rho0) and flux, accumulated region by region
   T rhs[nv];
@@ -751,7 +754,7 @@ GKS_FN void face_flux_in(const T* wl, const T* wr, const In& in, T dxl, T dxr, T
     T half[7], a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
 #pragma unroll
     for (int n = 0; n < 7; ++n) half[n] = sd ? rN[n] : lP[n];
-    const T ir = g_rcp(g.rho);
+    const T ir = g.ir;
 #pragma unroll
     for (int m = 0; m < nv; ++m) r[m] = in.s(sd, m) * ir;
     slope<D, T>(g, bK, r, a);
@@ -869,11 +872,11 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
                          float dt, const Gas<float>& gas, int abar_t0, float* F, float* tau_out) {
   using T = float;
   constexpr int nv = D + 2;
-  const T bK = gas.bK, K = gas.K;
+  const T bK = gas.bK, K = gas.K, ibK = gas.ibK;
   F2 w2[nv];
 #pragma unroll
   for (int m = 0; m < nv; ++m) w2[m] = F2(wl[m], wr[m]);
-  const Maxw<D, F2> gs = maxwellian<D, F2>(w2, F2(bK));
+  const Maxw<D, F2> gs = maxwellian<D, F2>(w2, F2(bK), F2(ibK));
   F2 hs[7];  // <u^n> over u > 0 (left) and u < 0 (right)
   u_half<D, F2>(gs, F2(1.0f, -1.0f), hs);
 
@@ -889,7 +892,7 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
       w0[m] = q.v.x + q.v.y;
     }
   }
-  const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK);
+  const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK, ibK);
 
   // Eqs. relaxation time and taua
   const F2 plr = F2(gs.rho * gs.il);
@@ -898,7 +901,7 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
   *tau_out = tau;
   T Tc[6], r1, r4, r5;
   if constexpr (RAR) {
-    const T drho = face_drho<D, T, MULTID>(g0, w0, in, dxl, dxr, g_rcp(g0.rho), bK, K);
+    const T drho = face_drho<D, T, MULTID>(g0, w0, in, dxl, dxr, g0.ir, bK, K);
     const T eps = drho > T(1e-30) * g0.rho ? g_div(tau * drho, g0.rho) : tau * T(1e-30);
     time_coeffs_hat<T>(dt, tau, eps, Tc, r1, r4, r5);
   } else {
@@ -908,7 +911,7 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
     r1 = T(-1);
     r4 = r5 = T(0);
   }
-  const T i0 = g_rcp(g0.rho);
+  const T i0 = g0.ir;
 
   T rhs[nv];
   // the two sides of the initial state: slopes a (normal), b (tangential), A (Eq. initialf0)
@@ -916,7 +919,7 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
     Trans<D, F2> ts;
     transverse<D, F2>(gs, F2(K), ts);
     F2 a[nv], b[Dims<D>::nt][nv], A[nv], r[nv];
-    const F2 ir = g_rcp(gs.rho);
+    const F2 ir = gs.ir;
 #pragma unroll
     for (int m = 0; m < nv; ++m) r[m] = F2(F2(in.s(0, m), in.s(1, m)) * ir);
     slope<D, F2>(gs, F2(bK), r, a);
@@ -978,6 +981,7 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
     const T fl = g_div(i0, dxl), fr = g_div(i0, dxr);
     Maxw<D, F2> g02;
     g02.rho = F2(g0.rho);
+    g02.ir = F2(g0.ir);
 #pragma unroll
     for (int i = 0; i < D; ++i) g02.U[i] = F2(g0.U[i]);
     g02.lam = F2(g0.lam);

@@ -76,12 +76,12 @@ template <int D, int V = 0, int H = 2> struct TileGeom {
   static constexpr int NF = NFX + NFY + NFZ;
   static constexpr int nv = D + 2;
   // Shared memory, in elements of the arithmetic type R: the staged state [nv][NH], tau_t of the
-  // ring [NR], the width tables 3 (HX + HY + HZ), then (from an 8-byte boundary) the face fluxes
+  // ring [NR], the width tables 4 (HX + HY + HZ), then (from a 16-byte boundary) the face fluxes
   // [nv][NF] and, with pre, the limited slopes of the first halo ring per cell and axis [D][nv][NR];
   // then the two turbulence fields of the ring and, for the float-pair state, the low words of the
   // tile's own cells (staged with the state so that the tile waits on global memory once).
   template <class R> __host__ __device__ static constexpr size_t fs_offset() {
-    return ((size_t)nv * NH + NR + 3 * (HX + HY + HZ) + (8 / sizeof(R) - 1)) / (8 / sizeof(R)) * (8 / sizeof(R));
+    return ((size_t)nv * NH + NR + 4 * (HX + HY + HZ) + (16 / sizeof(R) - 1)) / (16 / sizeof(R)) * (16 / sizeof(R));
   }
   template <class R> __host__ __device__ static constexpr size_t smem_bytes(bool pre, bool lo) {
     return sizeof(R) * (fs_offset<R>() + (size_t)nv * NF + (pre ? (size_t)D * nv * NR : 0) + 2 * (size_t)NR) +
@@ -107,7 +107,7 @@ struct Ctrl {
 
 // Gas and model constants in the arithmetic type.
 template <class R> struct Consts {
-  R gamma, mu, C_mu, beta_star, T_wall, bK, K, C_a;
+  R gamma, mu, C_mu, beta_star, T_wall, bK, K, C_a, ibK;
 };
 
 struct DevGrid {
@@ -135,6 +135,7 @@ inline void fill_consts(const DevGrid& g, Consts<R>& c) {
   c.beta_star = (R)g.beta_star;
   c.T_wall = (R)g.T_wall;
   c.bK = (R)g.bK;
+  c.ibK = (R)(1.0 / g.bK);
   c.K = (R)g.K;
   c.C_a = (R)g.C_a;
 }
@@ -238,12 +239,14 @@ __device__ __forceinline__ double f2d(float x) {
 // flight together.
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  static_assert(BYTES == 4 || BYTES == 8, "element copies of 4 or 8 bytes");
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "element copies of 4, 8 or 16 bytes");
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   if (BYTES == 4)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else
+  else if (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -608,6 +611,17 @@ __device__ __forceinline__ R cell_rate(const R* w, R gamma, const R* h) {
   return r;
 }
 
+// The same rate from the inverse cell widths, with one reciprocal of the density and one square root.
+template <int D, class R>
+__device__ __forceinline__ R cell_rate_inv(const R* w, R gamma, const R* ih) {
+  const R ir = g_rcp(w[0]);
+  const R cs = g_sqrt(gamma * pressure_of<R>(D, gamma, w) * ir);
+  R r = R(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) r += (g_abs(w[1 + d] * ir) + cs) * ih[d];
+  return r;
+}
+
 // Turbulent relaxation time (Eqs. tautchen, tautchenadjusted, tauttrivial) and, with PRE, the
 // limited MUSCL slope along each axis of every cell of the tile's first halo ring.  A function of its
 // own (not inlined) so that its register allocation is separate from the face loop's: each thread
@@ -632,10 +646,13 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
   constexpr int NIT = (G::NR + kThreads - 1) / kThreads;
   constexpr int GRP = D == 3 ? 2 : (NIT < 4 ? NIT : 4);
   constexpr int NS = PRE ? D * nv : 1;
-  const bool keps = turb_model == TURB_KEPS;
-  auto ring = [&](auto two_eq_tag, auto lim_tag) {
+  auto ring = [&](auto two_eq_tag, auto lim_tag, auto keps_tag) {
     constexpr bool TWO_EQ = decltype(two_eq_tag)::value;
     constexpr int LIM = decltype(lim_tag)::value;
+    constexpr bool KEPS = decltype(keps_tag)::value;
+    // single precision, van Leer: the slopes along x and y of each variable limited together on the
+    // paired FP32 instructions (reciprocals per lane)
+    constexpr bool PAIRXY = std::is_same<R, float>::value && D >= 2 && LIM == LIM_VANLEER;
     (void)LIM;
     for (int i0 = 0; i0 < NIT; i0 += GRP) {
       R tv[GRP], sv[GRP][NS];
@@ -648,12 +665,33 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
         const int idx = (hk * HY + hj) * HX + hi;
         const int pos[3] = {hi, hj, hk};
         if constexpr (TWO_EQ)
-          tv[q] = tau_turb_two_eq<D, R>(keps, cons, kc, Ws, G::NH, idx, strides, igrad, pos, Fl[l],
+          tv[q] = tau_turb_two_eq<D, R>(KEPS, cons, kc, Ws, G::NH, idx, strides, igrad, pos, Fl[l],
                                         Fl[G::NR + l]);
         else
           tv[q] = tau_turb_cell<D, R>(turb_model, cons, kc, Ws, G::NH, idx, strides, igrad, pos,
                                       turb_model == TURB_NONE ? R(0) : Fl[l], R(0));
-        if constexpr (PRE) {
+        if constexpr (PRE && PAIRXY) {
+          const F2 im2(icent[0][pos[0]], icent[1][pos[1]]), ip2(icent[0][pos[0] + 1], icent[1][pos[1] + 1]);
+#pragma unroll
+          for (int v = 0; v < nv; ++v) {
+            const R* pc = Ws + v * G::NH + idx;
+            const F2 c(pc[0]);
+            const F2 dm = F2((c - F2(pc[-strides[0]], pc[-strides[1]])) * im2);
+            const F2 dp = F2((F2(pc[strides[0]], pc[strides[1]]) - c) * ip2);
+            const F2 ab = F2(dm * dp), den = dm + dp;
+            const F2 lim = F2((ab + ab) * g_rcp(den));
+            sv[q][v] = ab.v.x > 0.0f ? lim.v.x : 0.0f;
+            sv[q][nv + v] = ab.v.y > 0.0f ? lim.v.y : 0.0f;
+          }
+          if constexpr (D == 3) {
+            const R im = icent[2][pos[2]], ip = icent[2][pos[2] + 1];
+#pragma unroll
+            for (int v = 0; v < nv; ++v) {
+              const R* pc = Ws + v * G::NH + idx;
+              sv[q][2 * nv + v] = limiter<R>(LIM, (pc[0] - pc[-strides[2]]) * im, (pc[strides[2]] - pc[0]) * ip);
+            }
+          }
+        } else if constexpr (PRE) {
           // slope along each axis: normal slope of the faces along that axis, tangential slope of
           // the faces along the others
 #pragma unroll
@@ -684,10 +722,11 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
   using LV = std::integral_constant<int, LIM_VANLEER>;
   using LM = std::integral_constant<int, LIM_MINMOD>;
   const bool two_eq = turb_model == TURB_KEPS || turb_model == TURB_KOMEGA;
+  const bool keps = turb_model == TURB_KEPS;
   if (lim == LIM_VANLEER) {
-    if (two_eq) ring(T1{}, LV{}); else ring(T0{}, LV{});
+    if (two_eq && keps) ring(T1{}, LV{}, T1{}); else if (two_eq) ring(T1{}, LV{}, T0{}); else ring(T0{}, LV{}, T0{});
   } else {
-    if (two_eq) ring(T1{}, LM{}); else ring(T0{}, LM{});
+    if (two_eq && keps) ring(T1{}, LM{}, T1{}); else if (two_eq) ring(T1{}, LM{}, T0{}); else ring(T0{}, LM{}, T0{});
   }
 }
 
@@ -716,6 +755,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   R* igx = icz + HZ;  // 1 / (distance between the centres of p - 1 and p + 1), per axis
   R* igy = igx + HX;
   R* igz = igy + HY;
+  R* iwx = igz + HZ;  // 1 / width, per axis
+  R* iwy = iwx + HX;
+  R* iwz = iwy + HY;
   R* Fs = Ws + G::template fs_offset<R>();  // [nv][NF], 8-byte aligned
   R* Ss = Fs + (size_t)nv * G::NF;          // PRE: [D][nv][NR] limited slopes of the ring cells along each axis
   R* Fl = Ss + (PRE ? (size_t)D * nv * G::NR : 0);  // [2][NR] turbulence fields of the ring cells
@@ -742,8 +784,30 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   __shared__ double s_dt;
 
   // ---- stage the tile with two halo layers, the ring's turbulence fields and the low words ------
-  // In-grid cells are copied asynchronously; ghost cells are resolved by the boundary rules.
-  for (int l = tid; l < G::NH; l += kThreads) {
+  // In-grid cells are copied asynchronously; ghost cells are resolved by the boundary rules.  A tile
+  // whose halo lies inside the grid copies two cells along x per instruction (both elements of a
+  // pair are in-grid and adjacent in memory; the pair starts on an even cell, hence on a boundary of
+  // twice the element size, when the halo origin, the row length and the state pointer allow it).
+  constexpr bool PAIRCOPY = (ASYNC || DSTAGE) && HX % 2 == 0;
+  const bool inner = ox >= H && ox + X + H <= g.n[0] && (D < 2 || (oy >= H && oy + Y + H <= g.n[1])) &&
+                     (D < 3 || (oz >= H && oz + Z + H <= g.n[2]));
+  const bool pairs = PAIRCOPY && inner && (ox - H) % 2 == 0 && g.n[0] % 2 == 0 &&
+                     ((size_t)A.Win % (2 * sizeof(S))) == 0;
+  if (pairs) {
+    for (int l2 = tid; l2 < G::NH / 2; l2 += kThreads) {
+      const int l = 2 * l2;
+      const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
+      const S* src = (const S*)A.Win + cell_index(g, ox + hi - H, D >= 2 ? oy + hj - H : 0, D >= 3 ? oz + hk - H : 0);
+#pragma unroll
+      for (int v = 0; v < nv; ++v) {
+        if constexpr (DSTAGE)
+          cp_async<16>(&Wd[v * G::NH + l], src + (long)v * g.ncell);
+        else
+          cp_async<2 * sizeof(S)>(&Ws[v * G::NH + l], src + (long)v * g.ncell);
+      }
+    }
+  }
+  for (int l = pairs ? G::NH : tid; l < G::NH; l += kThreads) {
     const int hi = l % HX, hj = (l / HX) % HY, hk = l / (HX * HY);
     const int gi = ox + hi - H, gj = D >= 2 ? oy + hj - H : 0, gk = D >= 3 ? oz + hk - H : 0;
     long sc;
@@ -813,6 +877,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     R* wd = a == 0 ? wsx : (a == 1 ? wsy : wsz);
     R* ic = a == 0 ? icx : (a == 1 ? icy : icz);
     R* ig = a == 0 ? igx : (a == 1 ? igy : igz);
+    R* iwd = a == 0 ? iwx : (a == 1 ? iwy : iwz);
     if (a < D) {
       const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 2 * kWG - 1;
       const int iw = o + p - H + kWG;
@@ -822,10 +887,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       wd[p] = w0;
       ic[p] = g_rcp(R(0.5) * (wm + w0));
       ig[p] = g_rcp(R(0.5) * wm + w0 + R(0.5) * wp);
+      iwd[p] = g_rcp(w0);
     } else {
       wd[p] = R(1);
       ic[p] = R(1);
       ig[p] = R(1);
+      iwd[p] = R(1);
     }
   }
   // the time step of this step (thread 0), read while the tile's copies are in flight
@@ -844,6 +911,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   cp_async_wait_all();
   __syncthreads();
   if constexpr (DSTAGE) {
+#pragma unroll 4
     for (int q = tid; q < nv * G::NH; q += kThreads) Ws[q] = d2f(Wd[q]);
     __syncthreads();
   }
@@ -872,6 +940,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   {
     Gas<R> gas;
     gas.bK = kc.bK;
+    gas.ibK = kc.ibK;
     gas.K = kc.K;
     gas.mu = kc.mu;
     gas.C_a = kc.C_a;
@@ -882,14 +951,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       R dxl, dxr, tau_t;
       int ax, ci, cj, ck, perm[3];
     };
-    auto prep = [&](int f, FaceIn& in) {
+    // AX: the face's axis when the caller knows it at compile time (the frame permutation, strides
+    // and shared-memory offsets below then fold to constants), -1 when it is found from f here
+    auto prep = [&](int f, FaceIn& in, auto ax_tag) {
+      constexpr int AX = decltype(ax_tag)::value;
       int ax, ci, cj, ck;  // face between cell (c - e_ax) and c, tile coordinates
-      if (f < G::NFX) {
+      if (AX == 0 || (AX < 0 && f < G::NFX)) {
         ax = 0;
         ci = f % (X + 1);
         cj = (f / (X + 1)) % Y;
         ck = f / ((X + 1) * Y);
-      } else if (D >= 2 && f < G::NFX + G::NFY) {
+      } else if (AX == 1 || (AX < 0 && D >= 2 && f < G::NFX + G::NFY)) {
         const int q = f - G::NFX;
         ax = 1;
         ci = q % X;
@@ -1044,6 +1116,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       // instructions (lane x: fa, lane y: fb; a missing fb repeats fa and is not stored)
       Gas<F2> gas2;
       gas2.bK = F2(kc.bK);
+      gas2.ibK = F2(kc.ibK);
       gas2.K = F2(kc.K);
       gas2.mu = F2(kc.mu);
       gas2.C_a = F2(kc.C_a);
@@ -1052,8 +1125,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         const int fa = tid + 2 * it * kThreads, fb = fa + kThreads;
         if (fa < G::NF) {
           FaceIn a, b;
-          prep(fa, a);
-          prep(fb < G::NF ? fb : fa, b);
+          prep(fa, a, std::integral_constant<int, -1>{});
+          prep(fb < G::NF ? fb : fa, b, std::integral_constant<int, -1>{});
           F2 wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv], tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
 #pragma unroll
           for (int v = 0; v < nv; ++v) {
@@ -1092,7 +1165,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
         const int f = tid + it * kThreads;
         if (f < G::NF) {
           FaceIn in;
-          prep(f, in);
+          if (f < G::NFX)
+            prep(f, in, std::integral_constant<int, 0>{});
+          else if (D < 3 || f < G::NFX + G::NFY)
+            prep(f, in, std::integral_constant<int, D >= 2 ? 1 : 0>{});
+          else
+            prep(f, in, std::integral_constant<int, D >= 3 ? 2 : 0>{});
           R F[nv], tau;
           if constexpr (std::is_same<R, float>::value && D <= 2) {
             // single precision: the two sides of the face on the paired FP32 instructions (in 3D the
@@ -1156,7 +1234,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     }
     R ih[3];
 #pragma unroll
-    for (int d = 0; d < D; ++d) ih[d] = g_rcp(h[d]);
+    for (int d = 0; d < D; ++d) ih[d] = (d == 0 ? iwx[li + H] : (d == 1 ? iwy[lj + H] : iwz[lk + H]));
     R wn[nv];
     double vol = 1.0;
     if (A.resid) {  // cell volume from the double-precision widths
@@ -1215,7 +1293,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     }
     const R p = pressure_of<R>(D, kc.gamma, wn);
     if (!(wn[0] > R(0)) || !(p > R(0))) bad = 1u;
-    rmax = fmax(rmax, cell_rate<D, R>(wn, kc.gamma, h));
+    rmax = fmax(rmax, cell_rate_inv<D, R>(wn, kc.gamma, ih));
   }
   const unsigned long long bmax = block_max_rate<R>(rmax, red);
   if (tid == 0) atomicMax(&A.ctrl->rate[(A.slot + 1) % 3], bmax);

@@ -11,6 +11,7 @@ static void run(int abar_t0, double gamma, double mu, double C_a, double dt, con
   constexpr int len = 6 * nv + 2 * (D - 1) * nv + 3;
   gks::Gas<double> gas;
   gas.bK = 2.0 / (gamma - 1.0);
+  gas.ibK = (gamma - 1.0) / 2.0;
   gas.K = gas.bK - D;
   gas.mu = mu;
   gas.C_a = C_a;
