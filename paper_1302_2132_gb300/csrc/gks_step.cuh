@@ -201,6 +201,12 @@ template <int PREC> struct PrecT;
 // 256 cells); the 15 slopes per ring cell of the 512-cell 3D tile would hold it to one CTA per SM,
 // so its faces recompute them (two CTAs per SM in FP32).
 template <int D, int PREC, int V = 0> __host__ __device__ constexpr bool pre_slopes() { return D < 3 || V > 0; }
+
+// Axis order of the face frame of a face normal to axis ax: the normal first, then the tangential
+// axes in increasing order (entries past D are 0).
+template <int D> __host__ __device__ constexpr int face_perm_c(int ax, int k) {
+  return k == 0 ? ax : (D == 2 ? (k == 1 ? 1 - ax : 0) : (D == 3 ? (k == 1 ? (ax == 0 ? 1 : 0) : (ax == 2 ? 1 : 2)) : 0));
+}
 template <> struct PrecT<PREC_F64> { using R = double; using S = double; };
 template <> struct PrecT<PREC_F32> { using R = float; using S = float; };
 template <> struct PrecT<PREC_F32D> { using R = float; using S = double; };
@@ -909,12 +915,25 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     }
   }
   cp_async_wait_all();
-  __syncthreads();
   if constexpr (DSTAGE) {
-#pragma unroll 4
-    for (int q = tid; q < nv * G::NH; q += kThreads) Ws[q] = d2f(Wd[q]);
-    __syncthreads();
+    // each thread converts the cells it staged: its own copies have landed, so no barrier is needed
+    // before the conversion (the same cell-to-thread assignment as the staging loops above)
+    if (pairs) {
+      for (int l2 = tid; l2 < G::NH / 2; l2 += kThreads) {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) {
+          Ws[v * G::NH + 2 * l2] = d2f(Wd[v * G::NH + 2 * l2]);
+          Ws[v * G::NH + 2 * l2 + 1] = d2f(Wd[v * G::NH + 2 * l2 + 1]);
+        }
+      }
+    } else {
+      for (int l = tid; l < G::NH; l += kThreads) {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) Ws[v * G::NH + l] = d2f(Wd[v * G::NH + l]);
+      }
+    }
   }
+  __syncthreads();
   const double dt_d = s_dt;
   if (s_end) {  // t_end reached: carry the state over
     for (int l = tid; l < G::NC; l += kThreads) {
@@ -1091,10 +1110,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     };
     // the flux of face f back in the grid frame; with a mass-flux output (k-omega transport) also
     // the face's time-integrated mass flux
-    auto store = [&](int f, const FaceIn& in, const R* F) {
+    auto store = [&](int f, const FaceIn& in, const R* F, auto ax_tag) {
+      constexpr int AX = decltype(ax_tag)::value;  // the face's axis if known at compile time, else -1
       Fs[0 * G::NF + f] = F[0];
 #pragma unroll
-      for (int k = 0; k < D; ++k) Fs[(1 + in.perm[k]) * G::NF + f] = F[1 + k];
+      for (int k = 0; k < D; ++k) Fs[(1 + (AX >= 0 ? face_perm_c<D>(AX, k) : in.perm[k])) * G::NF + f] = F[1 + k];
       Fs[(D + 1) * G::NF + f] = F[D + 1];
       if (A.mflux[0]) {
         // global face (cell c = tile origin + (ci, cj, ck), face c - 1/2 along ax)
@@ -1151,8 +1171,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
             Fa[v] = F[v].v.x;
             Fb[v] = F[v].v.y;
           }
-          store(fa, a, Fa);
-          if (fb < G::NF) store(fb, b, Fb);
+          store(fa, a, Fa, std::integral_constant<int, -1>{});
+          if (fb < G::NF) store(fb, b, Fb, std::integral_constant<int, -1>{});
         }
         if constexpr (kThreads % 128 == 0)
           asm volatile("bar.sync %0, 128;" ::"r"(1 + (tid >> 7)) : "memory");
@@ -1181,7 +1201,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
             face_flux<D, R, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
                                          in.tau_t, dt, gas, g.abar_t0, F, &tau);
           }
-          store(f, in, F);
+          if (f < G::NFX)
+            store(f, in, F, std::integral_constant<int, 0>{});
+          else if (D < 3 || f < G::NFX + G::NFY)
+            store(f, in, F, std::integral_constant<int, D >= 2 ? 1 : 0>{});
+          else
+            store(f, in, F, std::integral_constant<int, D >= 3 ? 2 : 0>{});
         }
       }
     }
