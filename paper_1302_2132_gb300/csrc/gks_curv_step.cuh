@@ -257,17 +257,17 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
   // (early) launch of this kernel, wait here for that kernel's completion; the face records
   // above are the grid's static geometry
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (MODE == 1) {
-    if (tid == 0) s_dt = 1.0;
-  } else if (tid == 0) {
-    const double dtv = step_dt(A);
-    s_dt = dtv;
-    if (blockIdx.x == 0) {
-      Ctrl* c = A.ctrl;
-      c->t[A.tslot ^ 1] = c->t[A.tslot] + dtv;
-      c->rate[(A.slot + 2) % 3] = 0ull;
-      c->last_dt = dtv;
-    }
+  // the control words of the time step (thread 0), loaded before the state copies are issued so that
+  // their latency overlaps them; the time step itself is formed once the copies are in flight
+  double c_dtf = 0.0, c_cfl = 0.0, c_tend = 0.0, c_t = 0.0;
+  unsigned long long c_rate = 0ull;
+  if (MODE != 1 && tid == 0) {
+    const Ctrl* c = A.ctrl;
+    c_dtf = c->dt_fixed;
+    c_cfl = c->cfl;
+    c_tend = c->t_end;
+    c_t = c->t[A.tslot];
+    c_rate = c->rate[A.slot];
   }
   // ---- state of the tile and two halo layers, boundary rules applied -------------------------
   // (cells inside the grid by asynchronous copies where the stored type is the arithmetic one;
@@ -299,6 +299,19 @@ __global__ void __launch_bounds__(CurvTile<V>::T, PREC == PREC_F64 ? 1 : 512 / C
 #pragma unroll
       for (int v = 0; v < 4; ++v) cp_async<4>(&Lo[v * X * Y + l], &A.Win_lo[(long)v * g.ncell + (long)gj * n0 + gi]);
     }
+  if (MODE == 1) {
+    if (tid == 0) s_dt = 1.0;
+  } else if (tid == 0) {
+    double dtv = c_dtf > 0.0 ? c_dtf : c_cfl / __longlong_as_double((long long)c_rate);
+    if (c_tend > 0.0) dtv = (c_t >= c_tend) ? 0.0 : fmin(dtv, c_tend - c_t);
+    s_dt = dtv;
+    if (blockIdx.x == 0) {
+      Ctrl* c = A.ctrl;
+      c->t[A.tslot ^ 1] = c_t + dtv;
+      c->rate[(A.slot + 2) % 3] = 0ull;
+      c->last_dt = dtv;
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
   const double dt_d = s_dt;

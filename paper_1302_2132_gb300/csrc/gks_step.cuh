@@ -517,16 +517,6 @@ __device__ __forceinline__ R tau_turb_two_eq(bool keps, bool cons, const Consts<
   return (f1 > R(0) && f2 > R(0)) ? t : R(0);
 }
 
-__device__ __forceinline__ double step_dt(const StepArgs& A) {
-  // every control word is read up front: one round trip to memory
-  const Ctrl* c = A.ctrl;
-  const double dt_fixed = c->dt_fixed, cfl = c->cfl, t_end = c->t_end, t = c->t[A.tslot];
-  const unsigned long long rate = c->rate[A.slot];
-  double dt = dt_fixed > 0.0 ? dt_fixed : cfl / __longlong_as_double((long long)rate);
-  if (t_end > 0.0) dt = (t >= t_end) ? 0.0 : fmin(dt, t_end - t);
-  return dt;
-}
-
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
@@ -794,6 +784,35 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
   // whose halo lies inside the grid copies two cells along x per instruction (both elements of a
   // pair are in-grid and adjacent in memory; the pair starts on an even cell, hence on a boundary of
   // twice the element size, when the halo origin, the row length and the state pointer allow it).
+  // The widths of this thread's width-table entry (threads 0 .. HX + HY + HZ - 1) and the control
+  // words of the time step (one thread without a table entry) are loaded before the copies are
+  // issued, so that their memory latency overlaps the copies instead of following them.
+  constexpr bool WT1 = HX + HY + HZ < kThreads;  // at most one table entry per thread
+  constexpr int kDtThread = WT1 ? kThreads - 1 : 0;
+  double wtab[3] = {1.0, 1.0, 1.0};
+  if constexpr (WT1) {
+    if (tid < HX + HY + HZ) {
+      const int a = tid < HX ? 0 : (tid < HX + HY ? 1 : 2);
+      const int p = a == 0 ? tid : (a == 1 ? tid - HX : tid - HX - HY);
+      if (a < D) {
+        const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 2 * kWG - 1;
+        const int iw = o + p - H + kWG;
+        wtab[0] = g.w[a][min(max(iw - 1, 0), top)];
+        wtab[1] = g.w[a][min(max(iw, 0), top)];
+        wtab[2] = g.w[a][min(max(iw + 1, 0), top)];
+      }
+    }
+  }
+  double c_dtf = 0.0, c_cfl = 0.0, c_tend = 0.0, c_t = 0.0;
+  unsigned long long c_rate = 0ull;
+  if (tid == kDtThread) {
+    const Ctrl* c = A.ctrl;
+    c_dtf = c->dt_fixed;
+    c_cfl = c->cfl;
+    c_tend = c->t_end;
+    c_t = c->t[A.tslot];
+    c_rate = c->rate[A.slot];
+  }
   constexpr bool PAIRCOPY = (ASYNC || DSTAGE) && HX % 2 == 0;
   const bool inner = ox >= H && ox + X + H <= g.n[0] && (D < 2 || (oy >= H && oy + Y + H <= g.n[1])) &&
                      (D < 3 || (oz >= H && oz + Z + H <= g.n[2]));
@@ -875,41 +894,59 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       for (int v = 0; v < nv; ++v) cp_async<4>(&Lo[v * G::NC + l], src + (long)v * g.ncell);
     }
   }
-  for (int l = tid; l < HX + HY + HZ; l += kThreads) {
-    // halo position p is the cell origin + p - H, width index cell + kWG (clamped to the ghosts);
-    // the inverse distances make the slope and gradient quotients products
-    const int a = l < HX ? 0 : (l < HX + HY ? 1 : 2);
-    const int p = a == 0 ? l : (a == 1 ? l - HX : l - HX - HY);
-    R* wd = a == 0 ? wsx : (a == 1 ? wsy : wsz);
-    R* ic = a == 0 ? icx : (a == 1 ? icy : icz);
-    R* ig = a == 0 ? igx : (a == 1 ? igy : igz);
-    R* iwd = a == 0 ? iwx : (a == 1 ? iwy : iwz);
-    if (a < D) {
-      const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 2 * kWG - 1;
-      const int iw = o + p - H + kWG;
-      const R wm = (R)g.w[a][min(max(iw - 1, 0), top)];
-      const R w0 = (R)g.w[a][min(max(iw, 0), top)];
-      const R wp = (R)g.w[a][min(max(iw + 1, 0), top)];
+  if constexpr (WT1) {
+    // this thread's width-table entry, from the widths loaded before the copies
+    if (tid < HX + HY + HZ) {
+      const int a = tid < HX ? 0 : (tid < HX + HY ? 1 : 2);
+      const int p = a == 0 ? tid : (a == 1 ? tid - HX : tid - HX - HY);
+      R* wd = a == 0 ? wsx : (a == 1 ? wsy : wsz);
+      R* ic = a == 0 ? icx : (a == 1 ? icy : icz);
+      R* ig = a == 0 ? igx : (a == 1 ? igy : igz);
+      R* iwd = a == 0 ? iwx : (a == 1 ? iwy : iwz);
+      const R wm = (R)wtab[0], w0 = (R)wtab[1], wp = (R)wtab[2];
       wd[p] = w0;
-      ic[p] = g_rcp(R(0.5) * (wm + w0));
-      ig[p] = g_rcp(R(0.5) * wm + w0 + R(0.5) * wp);
-      iwd[p] = g_rcp(w0);
-    } else {
-      wd[p] = R(1);
-      ic[p] = R(1);
-      ig[p] = R(1);
-      iwd[p] = R(1);
+      ic[p] = a < D ? g_rcp(R(0.5) * (wm + w0)) : R(1);
+      ig[p] = a < D ? g_rcp(R(0.5) * wm + w0 + R(0.5) * wp) : R(1);
+      iwd[p] = a < D ? g_rcp(w0) : R(1);
+    }
+  } else {
+    for (int l = tid; l < HX + HY + HZ; l += kThreads) {
+      // halo position p is the cell origin + p - H, width index cell + kWG (clamped to the ghosts);
+      // the inverse distances make the slope and gradient quotients products
+      const int a = l < HX ? 0 : (l < HX + HY ? 1 : 2);
+      const int p = a == 0 ? l : (a == 1 ? l - HX : l - HX - HY);
+      R* wd = a == 0 ? wsx : (a == 1 ? wsy : wsz);
+      R* ic = a == 0 ? icx : (a == 1 ? icy : icz);
+      R* ig = a == 0 ? igx : (a == 1 ? igy : igz);
+      R* iwd = a == 0 ? iwx : (a == 1 ? iwy : iwz);
+      if (a < D) {
+        const int o = a == 0 ? ox : (a == 1 ? oy : oz), top = g.n[a] + 2 * kWG - 1;
+        const int iw = o + p - H + kWG;
+        const R wm = (R)g.w[a][min(max(iw - 1, 0), top)];
+        const R w0 = (R)g.w[a][min(max(iw, 0), top)];
+        const R wp = (R)g.w[a][min(max(iw + 1, 0), top)];
+        wd[p] = w0;
+        ic[p] = g_rcp(R(0.5) * (wm + w0));
+        ig[p] = g_rcp(R(0.5) * wm + w0 + R(0.5) * wp);
+        iwd[p] = g_rcp(w0);
+      } else {
+        wd[p] = R(1);
+        ic[p] = R(1);
+        ig[p] = R(1);
+        iwd[p] = R(1);
+      }
     }
   }
-  // the time step of this step (thread 0), read while the tile's copies are in flight
-  if (tid == 0) {
-    const double dtv = step_dt(A);
+  // the time step of this step, from the control words read before the copies
+  if (tid == kDtThread) {
+    double dtv = c_dtf > 0.0 ? c_dtf : c_cfl / __longlong_as_double((long long)c_rate);
+    if (c_tend > 0.0) dtv = (c_t >= c_tend) ? 0.0 : fmin(dtv, c_tend - c_t);
     s_dtr = (R)dtv;
     s_end = dtv == 0.0;
     s_dt = dtv;
     if (b == 0) {
       Ctrl* c = A.ctrl;
-      c->t[A.tslot ^ 1] = c->t[A.tslot] + dtv;
+      c->t[A.tslot ^ 1] = c_t + dtv;
       c->rate[(A.slot + 2) % 3] = 0ull;
       c->last_dt = dtv;
     }
