@@ -322,14 +322,14 @@ gks_status gks_get_tau_turb(gks_handle* h, void* tau_out, int memspace, int dtyp
 gks_status gks_enable_timing(gks_handle* h, int enable);
 gks_status gks_kernel_time(gks_handle* h, double* ms_total, long long* launches);
 
-/* Tile shape of the handle's step kernel (no paper counterpart).  2D GKS_FP32 and GKS_FP32_ACC64 handles choose among eight
- * shapes (variants 0..5: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 cells, one face per thread per round,
- * 512 threads per CTA for 32x31 and 64x27, 256 otherwise; variants 6 and 7: 32x27 on 128 and 64x27 on
- * 256 threads, each thread evaluating two faces at once with the paired FP32 instructions), 3D ones
+/* Tile shape of the handle's step kernel (no paper counterpart).  2D GKS_FP32 and GKS_FP32_ACC64 handles choose among nine
+ * shapes (variants 0..5 and 8: 32x15, 64x7, 32x31, 32x27, 32x18, 64x27 and 32x21 cells, one face per thread
+ * per round, 512 threads per CTA for 32x31 and 64x27, 256 otherwise; variants 6 and 7: 32x27 on 128 and
+ * 64x27 on 256 threads, each thread evaluating two faces at once with the paired FP32 instructions), 3D ones
  * among four (16x8x4, 16x8x2, 8x8x4, and 16x8x2 with two faces per thread on 128 threads), 1D handles among 256, 31 and
  * 63 cells per CTA (the rarefaction option runs the first shape of each), on their first gks_step: each is timed
  * on the step about to be taken and the fastest kept (and reused by later handles of the same grid);
- * the environment variable GKS_TILE_VARIANT forces one (0..7 in 2D, 0..3 in 3D, 0..2 in 1D).  The result does
+ * the environment variable GKS_TILE_VARIANT forces one (0..8 in 2D, 0..3 in 3D, 0..2 in 1D).  The result does
  * not depend on it beyond rounding. */
 gks_status gks_tile_shape(gks_handle* h, int* variant, int* tx, int* ty, int* tz);
 

@@ -19,7 +19,7 @@ void launch_step_d3(int prec, bool multid, const StepArgs& A, int nblocks, cudaS
 cudaError_t prepare_step_d2_variants();
 void launch_step_d2_variant(int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);
 void tile_shape(int D, int variant, int* x, int* y, int* z);
-constexpr int kTileVariants2D = 8;
+constexpr int kTileVariants2D = 9;
 // the paired tiles (two faces per thread) of the FP32 forms: 2D variants 6 and 7, 3D variant 3
 cudaError_t prepare_step_pair();
 void launch_step_pair(int D, int prec, int variant, bool multid, const StepArgs& A, int nblocks, cudaStream_t s);

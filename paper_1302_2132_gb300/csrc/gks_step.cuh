@@ -56,7 +56,12 @@ template <> struct Tile<2, 5> { static constexpr int X = 64, Y = 27, Z = 1, T = 
 template <> struct Tile<2, 6> { static constexpr int X = 32, Y = 27, Z = 1, T = 128; };
 template <> struct Tile<2, 7> { static constexpr int X = 64, Y = 27, Z = 1, T = 256; };
 template <> struct Tile<3, 3> { static constexpr int X = 16, Y = 8, Z = 2, T = 128; };
-template <int D, int V> __host__ __device__ constexpr bool paired_tile() { return (D == 2 && V >= 6) || (D == 3 && V >= 3); }
+// 32 x 21 on two 256-thread CTAs per SM: 1397 faces in 6 rounds; 1024 x 384 gives 608 tiles, two
+// full waves on 152 SMs
+template <> struct Tile<2, 8> { static constexpr int X = 32, Y = 21, Z = 1, T = 256; };
+template <int D, int V> __host__ __device__ constexpr bool paired_tile() {
+  return (D == 2 && (V == 6 || V == 7)) || (D == 3 && V == 3);
+}
 template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 8, Z = 4, T = 256; };
 // 256-cell 3D tiles with the per-cell slope table (two CTAs per SM): 944 and 896 faces
 template <> struct Tile<3, 1> { static constexpr int X = 16, Y = 8, Z = 2, T = 256; };

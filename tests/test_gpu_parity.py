@@ -356,14 +356,15 @@ def test_full_size_2d_turbulence_sampled_cells(prec):
     assert np.all(np.abs(tot - W0) <= (1e-11 if prec == "fp64" else 1e-9) * (np.abs(W0) + 1.0))
 
 
-def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
-    """The eight 2D FP32 tile shapes (two of them evaluating two faces per thread with paired
-    instructions) evaluate the same faces: their results agree to FP32 rounding (different compiled
-    kernels), and the autotuner keeps one of them."""
+@pytest.mark.parametrize("precision", ["fp32", "fp32_acc64"])
+def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch, precision):
+    """The nine 2D single-precision tile shapes (two of them evaluating two faces per thread with
+    paired instructions) evaluate the same faces: their results agree to FP32 rounding (different
+    compiled kernels), and the autotuner keeps one of them; for the float-pair and the double state."""
     spec = inputs.turbulence(100, 2, seed=8)
-    kw = dict(turb_model=2, multid=1, mu=1e-5, precision="fp32")
+    kw = dict(turb_model=2, multid=1, mu=1e-5, precision=precision)
     out = []
-    for v in ("0", "1", "2", "3", "4", "5", "6", "7"):
+    for v in ("0", "1", "2", "3", "4", "5", "6", "7", "8"):
         monkeypatch.setenv("GKS_TILE_VARIANT", v)
         s = gpu_solver(spec, **kw)
         s.set_state(spec["prim"].ravel(), layout="soa_prim")
@@ -380,7 +381,7 @@ def test_tile_variants_agree_and_autotuner_picks_one(monkeypatch):
     s.set_turbulence(spec["f1"].ravel(), spec["f2"].ravel())
     s.step(nsteps=30, cfl=0.5)
     v = s.tile_shape()
-    assert v[0] in range(8) and v[1] * v[2] in (480, 448, 992, 864, 576, 1728)
+    assert v[0] in range(9) and v[1] * v[2] in (480, 448, 992, 864, 576, 1728, 672)
     assert np.all(rel_err_per_var(s.get_state(), out[0], 4) < 1e-6)
     s.close()
 
