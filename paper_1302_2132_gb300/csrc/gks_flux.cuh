@@ -868,8 +868,9 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
 // way.  The paired sums are added lane x + lane y at the end of each part.  Same terms as
 // face_flux_in; only the order of the final additions differs.
 template <int D, bool MULTID, bool RAR = false, class In>
-GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float dxl, float dxr, float tau_t,
-                         float dt, const Gas<float>& gas, int abar_t0, float* F, float* tau_out) {
+GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float dxl, float dxr, float idxl,
+                         float idxr, float tau_t, float dt, const Gas<float>& gas, int abar_t0, float* F,
+                         float* tau_out) {
   using T = float;
   constexpr int nv = D + 2;
   const T bK = gas.bK, K = gas.K, ibK = gas.ibK;
@@ -894,10 +895,13 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
   }
   const Maxw<D, T> g0 = maxwellian<D, T>(w0, bK, ibK);
 
-  // Eqs. relaxation time and taua
-  const F2 plr = F2(gs.rho * gs.il);
-  const T p0 = g0.rho * g0.il, pl = plr.v.x, pr = plr.v.y;
-  const T tau = g_div(gas.mu, p0) + tau_t + g_div(gas.C_a * g_abs(pr - pl), pr + pl) * dt;
+  // Eqs. relaxation time and taua: mu/p0 = 2 mu lambda0 / rho0; the artificial part only with C_a > 0
+  T tau = T(2) * gas.mu * g0.lam * g0.ir + tau_t;
+  if (gas.C_a != T(0)) {
+    const F2 plr = F2(gs.rho * gs.il);
+    const T pl = plr.v.x, pr = plr.v.y;
+    tau += g_div(gas.C_a * g_abs(pr - pl), pr + pl) * dt;
+  }
   *tau_out = tau;
   T Tc[6], r1, r4, r5;
   if constexpr (RAR) {
@@ -978,7 +982,7 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
   u_half<D, T>(g0, T(1), oP);
   {
     // lane x: abar_l on u > 0; lane y: abar_r on u < 0 (table = full line minus u > 0)
-    const T fl = g_div(i0, dxl), fr = g_div(i0, dxr);
+    const T fl = i0 * idxl, fr = i0 * idxr;
     Maxw<D, F2> g02;
     g02.rho = F2(g0.rho);
     g02.ir = F2(g0.ir);
@@ -1033,13 +1037,23 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float d
   }
 }
 
+// face_flux_ps with the inputs in arrays, the inverse centre-to-face distances given.
+template <int D, bool MULTID, bool RAR = false>
+GKS_FN void face_flux_ps(const float* wl, const float* wr, const float* cl, const float* cr, const float* sl,
+                         const float* sr, const float (*tl)[D + 2], const float (*tr)[D + 2], float dxl, float dxr,
+                         float idxl, float idxr, float tau_t, float dt, const Gas<float>& gas, int abar_t0, float* F,
+                         float* tau_out) {
+  const FaceArrays<D, float> in{sl, sr, cl, cr, tl, tr};
+  face_flux_ps<D, MULTID, RAR>(wl, wr, in, dxl, dxr, idxl, idxr, tau_t, dt, gas, abar_t0, F, tau_out);
+}
+
 // face_flux_ps with the inputs in arrays.
 template <int D, bool MULTID, bool RAR = false>
 GKS_FN void face_flux_ps(const float* wl, const float* wr, const float* cl, const float* cr, const float* sl,
                          const float* sr, const float (*tl)[D + 2], const float (*tr)[D + 2], float dxl, float dxr,
                          float tau_t, float dt, const Gas<float>& gas, int abar_t0, float* F, float* tau_out) {
-  const FaceArrays<D, float> in{sl, sr, cl, cr, tl, tr};
-  face_flux_ps<D, MULTID, RAR>(wl, wr, in, dxl, dxr, tau_t, dt, gas, abar_t0, F, tau_out);
+  face_flux_ps<D, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, g_rcp(dxl), g_rcp(dxr), tau_t, dt, gas,
+                               abar_t0, F, tau_out);
 }
 #endif  // GKS_HOST_COUNT
 

@@ -1009,7 +1009,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
     // Inputs of one face in its frame (velocity order: normal first, then tangential axes).
     struct FaceIn {
       R wl[nv], wr[nv], cl[nv], cr[nv], sl[nv], sr[nv], tl[Dims<D>::nt][nv], tr[Dims<D>::nt][nv];
-      R dxl, dxr, tau_t;
+      R dxl, dxr, idxl, idxr, tau_t;
       int ax, ci, cj, ck, perm[3];
     };
     // AX: the face's axis when the caller knows it at compile time (the frame permutation, strides
@@ -1148,6 +1148,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       }
       in.dxl = R(0.5) * h1;
       in.dxr = R(0.5) * h2;
+      {
+        const R* iwn = ax == 0 ? iwx : (ax == 1 ? iwy : iwz);
+        in.idxl = R(2) * iwn[pn - 1];
+        in.idxr = R(2) * iwn[pn];
+      }
       in.tau_t = R(0.5) * (taus[rl] + taus[rc]);
     };
     // the flux of face f back in the grid frame; with a mass-flux output (k-omega transport) also
@@ -1238,7 +1243,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
             // single precision: the two sides of the face on the paired FP32 instructions (in 3D the
             // paired body does not fit the register budget of two CTAs per SM)
             face_flux_ps<D, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
-                                         in.tau_t, dt, gas, g.abar_t0, F, &tau);
+                                         in.idxl, in.idxr, in.tau_t, dt, gas, g.abar_t0, F, &tau);
           } else {
             face_flux<D, R, MULTID, RAR>(in.wl, in.wr, in.cl, in.cr, in.sl, in.sr, in.tl, in.tr, in.dxl, in.dxr,
                                          in.tau_t, dt, gas, g.abar_t0, F, &tau);
