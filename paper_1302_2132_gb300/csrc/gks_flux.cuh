@@ -38,6 +38,15 @@ template <> GKS_FN float g_sqrt<float>(float x) {
 }
 #endif
 template <> GKS_FN double g_sqrt<double>(double x) { return sqrt(x); }
+// 1/sqrt(x): the hardware approximate reciprocal square root in single precision, IEEE otherwise
+template <class T> GKS_FN T g_rsqrt(T x) { return T(1) / g_sqrt(x); }
+#ifndef GKS_HOST_COUNT
+template <> GKS_FN float g_rsqrt<float>(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+#endif
 template <class T> GKS_FN T g_exp(T x);
 #ifdef GKS_HOST_COUNT
 template <> GKS_FN float g_exp<float>(float x) { return expf(x); }
@@ -49,6 +58,10 @@ template <> GKS_FN float g_erfc<float>(float x) { return erfcf(x); }
 #endif
 template <> GKS_FN double g_erfc<double>(double x) { return erfc(x); }
 template <class T> GKS_FN T g_abs(T x) { return x < T(0) ? -x : x; }
+#ifndef GKS_HOST_COUNT
+template <> GKS_FN float g_abs<float>(float x) { return fabsf(x); }
+template <> GKS_FN double g_abs<double>(double x) { return fabs(x); }
+#endif
 
 // Quotient and reciprocal: IEEE in double precision (the FP64 path matches the oracle to 1e-12);
 // in single precision the hardware reciprocal (about 1 ulp), which avoids the multi-instruction
@@ -83,6 +96,7 @@ GKS_FN F2 g_rcp(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.
 GKS_FN F2 g_div(F2 a, F2 b) { return F2(a * g_rcp(b)); }
 GKS_FN F2 g_exp(F2 x) { return F2(__expf(x.v.x), __expf(x.v.y)); }
 GKS_FN F2 g_sqrt(F2 x) { return F2(g_sqrt<float>(x.v.x), g_sqrt<float>(x.v.y)); }
+GKS_FN F2 g_rsqrt(F2 x) { return F2(g_rsqrt<float>(x.v.x), g_rsqrt<float>(x.v.y)); }
 GKS_FN F2 g_abs(F2 x) { return F2(fabsf(x.v.x), fabsf(x.v.y)); }
 GKS_FN F2 g_erfc(F2 x) {
   const F2 z = g_abs(x);
@@ -287,10 +301,10 @@ GKS_FN void u_full(const Maxw<D, T>& g, T* u) {
 //   <1>_{u>0} = erfc(-sqrt(lam) U)/2,  <u>_{u>0} = U <1>_{u>0} + exp(-lam U^2)/(2 sqrt(pi lam)).
 template <int D, class T>
 GKS_FN void u_half(const Maxw<D, T>& g, T sgn, T* u) {
-  const T sl = g_sqrt(g.lam);
-  const T z = sl * g.U[0];
+  const T rs = g_rsqrt(g.lam);  // 1/sqrt(lambda); sqrt(lambda) = lambda / sqrt(lambda)
+  const T z = g.lam * rs * g.U[0];
   u[0] = T(0.5) * g_erfc(-sgn * z);
-  u[1] = g.U[0] * u[0] + g_div(sgn * T(0.5) * g_exp(-z * z) * T(kInvSqrtPi), sl);
+  u[1] = g.U[0] * u[0] + sgn * T(0.5) * g_exp(-z * z) * T(kInvSqrtPi) * rs;
   recur<7>(g.U[0], g.il, u);
 }
 
