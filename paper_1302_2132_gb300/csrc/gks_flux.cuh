@@ -880,7 +880,8 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
 // the intermediate state, the slopes a, b, A and their parts of the Abar right-hand side and of the
 // flux; the two one-sided equilibrium slopes abar_l (u > 0) and abar_r (u < 0) are paired the same
 // way.  The paired sums are added lane x + lane y at the end of each part.  Same terms as
-// face_flux_in; only the order of the final additions differs.
+// face_flux_in; the order of the final additions differs, mu/p0 is taken as 2 mu lambda0 / rho0, the
+// artificial part of tau is skipped when C_a = 0, and idxl, idxr are the reciprocals of dxl, dxr.
 template <int D, bool MULTID, bool RAR = false, class In>
 GKS_FN void face_flux_ps(const float* wl, const float* wr, const In& in, float dxl, float dxr, float idxl,
                          float idxr, float tau_t, float dt, const Gas<float>& gas, int abar_t0, float* F,
