@@ -645,7 +645,8 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
   const R* igrad[3] = {igx, igy, igz};
   const R* icent[3] = {icx, icy, icz};
   constexpr int NIT = (G::NR + kThreads - 1) / kThreads;
-  constexpr int GRP = D == 3 ? 2 : (NIT < 4 ? NIT : 4);
+  // groups of at most four ring cells per thread, as even as the count allows (5 -> 3 + 3, not 4 + 4)
+  constexpr int GRP = D == 3 ? 2 : (NIT + (NIT + 3) / 4 - 1) / ((NIT + 3) / 4);
   constexpr int NS = PRE ? D * nv : 1;
   auto ring = [&](auto two_eq_tag, auto lim_tag, auto keps_tag) {
     constexpr bool TWO_EQ = decltype(two_eq_tag)::value;
