@@ -623,6 +623,43 @@ __device__ __forceinline__ R cell_rate_inv(const R* w, R gamma, const R* ih) {
   return r;
 }
 
+// Ring cells that the faces of a tile read: in 3D the tile and its six face layers (the edge and
+// corner cells of the ring box border no face of the tile), otherwise the whole ring box.  ring_used
+// is their number, ring_slot(s) the ring index of the s-th (tile cells first, then the x, y and z
+// layers, low side before high side).
+template <int D, class G> __host__ __device__ constexpr int ring_used() {
+  return D == 3 ? G::X * G::Y * G::Z + 2 * (G::Y * G::Z + G::X * G::Z + G::X * G::Y) : G::NR;
+}
+template <int D, class G> __device__ __forceinline__ int ring_slot(int s) {
+  if constexpr (D < 3) {
+    return s;
+  } else {
+    constexpr int X = G::X, Y = G::Y, Z = G::Z;
+    int ri, rj, rk;
+    if (s < X * Y * Z) {
+      ri = s % X + 1;
+      rj = (s / X) % Y + 1;
+      rk = s / (X * Y) + 1;
+    } else if (s < X * Y * Z + 2 * Y * Z) {
+      const int t = s - X * Y * Z;
+      ri = t < Y * Z ? 0 : X + 1;
+      rj = (t % (Y * Z)) % Y + 1;
+      rk = (t % (Y * Z)) / Y + 1;
+    } else if (s < X * Y * Z + 2 * Y * Z + 2 * X * Z) {
+      const int t = s - X * Y * Z - 2 * Y * Z;
+      rj = t < X * Z ? 0 : Y + 1;
+      ri = (t % (X * Z)) % X + 1;
+      rk = (t % (X * Z)) / X + 1;
+    } else {
+      const int t = s - X * Y * Z - 2 * Y * Z - 2 * X * Z;
+      rk = t < X * Y ? 0 : Z + 1;
+      ri = (t % (X * Y)) % X + 1;
+      rj = (t % (X * Y)) / X + 1;
+    }
+    return (rk * G::RY + rj) * G::RX + ri;
+  }
+}
+
 // Turbulent relaxation time (Eqs. tautchen, tautchenadjusted, tauttrivial) and, with PRE, the
 // limited MUSCL slope along each axis of every cell of the tile's first halo ring.  A function of its
 // own (not inlined) so that its register allocation is separate from the face loop's: each thread
@@ -644,7 +681,8 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
   const int strides[3] = {1, HX, HX * HY};
   const R* igrad[3] = {igx, igy, igz};
   const R* icent[3] = {icx, icy, icz};
-  constexpr int NIT = (G::NR + kThreads - 1) / kThreads;
+  constexpr int NU = ring_used<D, G>();
+  constexpr int NIT = (NU + kThreads - 1) / kThreads;
   // groups of at most four ring cells per thread, as even as the count allows (5 -> 3 + 3, not 4 + 4)
   constexpr int GRP = D == 3 ? 2 : (NIT + (NIT + 3) / 4 - 1) / ((NIT + 3) / 4);
   constexpr int NS = PRE ? D * nv : 1;
@@ -661,7 +699,7 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
       (void)sv;
 #pragma unroll
       for (int q = 0; q < GRP; ++q) {
-        const int l = min(tid + (i0 + q) * kThreads, G::NR - 1);
+        const int l = ring_slot<D, G>(min(tid + (i0 + q) * kThreads, NU - 1));
         const int ri = l % G::RX, rj = (l / G::RX) % G::RY, rk = l / (G::RX * G::RY);
         const int hi = ri + H - 1, hj = D >= 2 ? rj + H - 1 : 0, hk = D >= 3 ? rk + H - 1 : 0;
         const int idx = (hk * HY + hj) * HX + hi;
@@ -709,8 +747,9 @@ __device__ __noinline__ void ring_phase(const Consts<typename PrecT<PREC>::R> kc
       }
 #pragma unroll
       for (int q = 0; q < GRP; ++q) {
-        const int l = tid + (i0 + q) * kThreads;
-        if (i0 + q >= NIT || l >= G::NR) continue;
+        const int su = tid + (i0 + q) * kThreads;
+        if (i0 + q >= NIT || su >= NU) continue;
+        const int l = ring_slot<D, G>(su);
         taus[l] = tv[q];
         if constexpr (PRE) {
 #pragma unroll
