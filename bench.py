@@ -253,7 +253,7 @@ TRAFFIC_PER_LAUNCH = {("turb2d_1024_keps_multid_fp32_acc64", 3): 43.06e6,
                       ("shock_bl_1024x384_fp32_acc64", 4): 15.883e6,
                       ("shock_bl_1024x384_fp32_acc64", 8): 15.89e6,
                       # 160^3 capture of the same kernel scaled by cells (x 4.096): the state streams at both sizes
-                      ("turb3d_256_fp32_acc64", 2): 1.3816e9}
+                      ("turb3d_256_fp32_acc64", 2): 1.3804e9}
 
 
 def faces_of(n, bc=None):
