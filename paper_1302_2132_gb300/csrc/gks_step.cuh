@@ -630,7 +630,7 @@ __device__ __forceinline__ R cell_rate_inv(const R* w, R gamma, const R* ih) {
 template <int D, class G> __host__ __device__ constexpr int ring_used() {
   return D == 3 ? G::X * G::Y * G::Z + 2 * (G::Y * G::Z + G::X * G::Z + G::X * G::Y) : G::NR;
 }
-template <int D, class G> __device__ __forceinline__ int ring_slot(int s) {
+template <int D, class G> __host__ __device__ __forceinline__ int ring_slot(int s) {
   if constexpr (D < 3) {
     return s;
   } else {
@@ -1092,7 +1092,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, const int b) {
       const R* wn = ax == 0 ? wsx : (ax == 1 ? wsy : wsz);
       const int pn = ax == 0 ? ci + H : (ax == 1 ? cj + H : ck + H);  // halo coordinate of cell c
       const R h1 = wn[pn - 1], h2 = wn[pn];
-      R i2h1 = R(0), i2h2 = R(0);  // 2 / width of the two cells (higher-order slopes)
+      [[maybe_unused]] R i2h1 = R(0), i2h2 = R(0);  // 2 / width of the two cells (higher-order slopes)
       if constexpr (RECON != RECON_MUSCL2) {
         i2h1 = g_rcp(R(0.5) * h1);
         i2h2 = g_rcp(R(0.5) * h2);
