@@ -15,9 +15,7 @@
 #include <math.h>
 
 #include <type_traits>
-#ifndef GKS_HOST_COUNT
 #include "gks_f2.cuh"
-#endif
 
 #ifndef GKS_FN
 #define GKS_FN __device__ __forceinline__
@@ -89,12 +87,13 @@ GKS_FN float erfc_cheb(float x) {
   return x >= 0.0f ? r : 2.0f - r;
 }
 template <> GKS_FN float g_erfc<float>(float x) { return erfc_cheb(x); }
+#endif
 
-// The same functions on two lanes (two faces per thread): quotients by the hardware reciprocal,
-// exponentials and square roots per lane, erfc from the same Chebyshev fit with paired arithmetic.
-GKS_FN F2 g_rcp(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+// The same functions on two lanes (two faces per thread): reciprocals, exponentials and square roots
+// per lane as in single precision, erfc from the same Chebyshev fit with paired arithmetic.
+GKS_FN F2 g_rcp(F2 x) { return F2(g_rcp<float>(x.v.x), g_rcp<float>(x.v.y)); }
 GKS_FN F2 g_div(F2 a, F2 b) { return F2(a * g_rcp(b)); }
-GKS_FN F2 g_exp(F2 x) { return F2(__expf(x.v.x), __expf(x.v.y)); }
+GKS_FN F2 g_exp(F2 x) { return F2(g_exp<float>(x.v.x), g_exp<float>(x.v.y)); }
 GKS_FN F2 g_sqrt(F2 x) { return F2(g_sqrt<float>(x.v.x), g_sqrt<float>(x.v.y)); }
 GKS_FN F2 g_rsqrt(F2 x) { return F2(g_rsqrt<float>(x.v.x), g_rsqrt<float>(x.v.y)); }
 GKS_FN F2 g_abs(F2 x) { return F2(fabsf(x.v.x), fabsf(x.v.y)); }
@@ -118,7 +117,6 @@ GKS_FN F2 g_exp(F2Mul x) { return g_exp(F2(x)); }
 GKS_FN F2 g_sqrt(F2Mul x) { return g_sqrt(F2(x)); }
 GKS_FN F2 g_abs(F2Mul x) { return g_abs(F2(x)); }
 GKS_FN F2 g_erfc(F2Mul x) { return g_erfc(F2(x)); }
-#endif
 
 constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
 
@@ -557,7 +555,6 @@ GKS_FN void time_coeffs(T dt, T tau, T* Tc, T& r1, T& r4, T& r5) {
   }
 }
 
-#ifndef GKS_HOST_COUNT
 // Two lanes: both branches of time_coeffs, each lane keeping its own (x < 1: the series).
 template <>
 GKS_FN void time_coeffs<F2>(F2 dt, F2 tau, F2* Tc, F2& r1, F2& r4, F2& r5) {
@@ -602,7 +599,6 @@ GKS_FN void time_coeffs<F2>(F2 dt, F2 tau, F2* Tc, F2& r1, F2& r4, F2& r5) {
   r4 = f2_select(sx, sy, r4s, r4c);
   r5 = f2_select(sx, sy, r5s, r5c);
 }
-#endif
 
 // The time coefficients with the degree of rarefaction eps in place of tau/dt (Eqs. tautautilde,
 // rarefactionkepsilon, epsilonkomega): Eq. fkepsilon with alpha = eps (1 - e^{-1/eps}) and
@@ -874,7 +870,6 @@ GKS_FN void face_flux(const T* wl, const T* wr, const T* cl, const T* cr, const 
   face_flux_in<D, T, MULTID, RAR>(wl, wr, in, dxl, dxr, tau_t, dt, gas, abar_t0, F, tau_out);
 }
 
-#ifndef GKS_HOST_COUNT
 // face_flux_in in single precision with the two sides of the face evaluated together on the paired
 // FP32 instructions: lane x carries the left Maxwellian on u > 0, lane y the right one on u < 0, for
 // the intermediate state, the slopes a, b, A and their parts of the Abar right-hand side and of the
@@ -1070,6 +1065,5 @@ GKS_FN void face_flux_ps(const float* wl, const float* wr, const float* cl, cons
   face_flux_ps<D, MULTID, RAR>(wl, wr, cl, cr, sl, sr, tl, tr, dxl, dxr, g_rcp(dxl), g_rcp(dxr), tau_t, dt, gas,
                                abar_t0, F, tau_out);
 }
-#endif  // GKS_HOST_COUNT
 
 }  // namespace gks
