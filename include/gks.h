@@ -125,13 +125,20 @@ typedef struct {
   int reconstruction;  /* GKS_RECON_*; zero (the default) is MUSCL2 */
 } gks_numerics;
 
+/* Largest grid gks_create accepts, in cells: over a terabyte of state, beyond any device's memory. */
+#define GKS_MAX_CELLS (1LL << 34)
+
 /* Create a solver on the current CUDA device for the problem the paper states: a state on a grid
  * (Section 2, Eq. moment1), a gas with gamma and mu = tau p (Section 2, Eqs. maxwellian,
  * chapman-enskog-ns; Pr = 1), the turbulence inputs of Sections 3 and 4 (Eqs. tauttrivial, tautchen,
  * tautchenadjusted, taua) and the numerics of Section 4.  cuda_stream is a cudaStream_t or NULL (the
  * library then creates its own non-blocking stream).  All device buffers are allocated here and owned
- * by the handle.  Errors: GKS_EINVAL for bad sizes, codes or Dirichlet data, GKS_EUNSUPPORTED for an
- * option that is not built (prandtl != 1, see also gks_turb.rarefaction), GKS_ENOMEM, GKS_ECUDA. */
+ * by the handle.  Errors: GKS_EINVAL for bad sizes (fewer than two cells on an active axis, more than
+ * GKS_MAX_CELLS cells in all), codes or Dirichlet data, GKS_EUNSUPPORTED for an option that is not
+ * built (prandtl != 1, see also gks_turb.rarefaction), GKS_ENOMEM, GKS_ECUDA.  Arguments are checked
+ * before any CUDA call.  On an error after the handle itself is allocated (every error but a null
+ * argument or a failed host allocation), *out receives a handle that holds the message
+ * (gks_last_error) and must be passed to gks_destroy. */
 gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* turb,
                       const gks_numerics* num, void* cuda_stream, gks_handle** out);
 

@@ -549,6 +549,9 @@ gks_status gks_create(const gks_grid* grid, const gks_gas* gas, const gks_turb* 
   for (int d = 0; d < 3; ++d) {
     h->n[d] = d < D ? grid->n[d] : 1;
     if (d < D && h->n[d] < 2) return bad(GKS_EINVAL, "at least two cells per active axis");
+    // the cell count is bounded before it is formed, so that it and every byte count taken from it
+    // stay exact (GKS_MAX_CELLS cells hold more state than any device's memory)
+    if (h->n[d] > GKS_MAX_CELLS / h->ncell) return bad(GKS_EINVAL, "more than GKS_MAX_CELLS cells");
     h->ncell *= h->n[d];
   }
   if (!(gas->gamma > 1.0)) return bad(GKS_EINVAL, "gamma must exceed 1");

@@ -71,6 +71,37 @@ def test_null_handles_are_rejected_without_touching_the_device():
     assert L.gks_komega_defaults(None) == EINVAL
 
 
+def test_create_rejects_bad_sizes_before_touching_the_device():
+    """gks_create refuses a grid of more than GKS_MAX_CELLS cells (among them one whose cell count
+    would wrap a 64-bit product) and an axis of fewer than two cells, with a message, before any
+    CUDA call (so this runs without a GPU); the returned handle is released by gks_destroy."""
+    from paper_1302_2132_gb300 import build, gks
+    build.build()
+    L = gks.load()
+    EINVAL = 1
+    cases = [((1 << 22, 1 << 22, 1 << 21), "GKS_MAX_CELLS"),   # 2^65 cells: wraps to 0 in 64 bits
+             ((1 << 30, 1 << 30, 16), "GKS_MAX_CELLS"),
+             ((1 << 17, 1 << 17, 2), "GKS_MAX_CELLS"),        # 2^35
+             ((1 << 17, 1 << 16, 1), "two cells")]            # third axis active with one cell
+    for n, msg in cases:
+        g = gks._Grid()
+        g.dim = 3
+        for d in range(3):
+            g.n[d] = n[d]
+            g.lo[d], g.hi[d] = 0.0, 1.0
+        gas = gks._Gas(1.4, 1e-5, 1.0, 1.0)
+        turb = gks._Turb(0, 0.09, 0.09, 0.0, 0)
+        num = gks._Num(1, 1, 0, 0, 0)
+        h = ctypes.c_void_p()
+        st = L.gks_create(ctypes.byref(g), ctypes.byref(gas), ctypes.byref(turb), ctypes.byref(num), None,
+                          ctypes.byref(h))
+        assert st == EINVAL and h.value
+        assert msg in L.gks_last_error(h).decode()
+        assert L.gks_destroy(h) == 0
+    header = open(os.path.join(ROOT, "include", "gks.h")).read()
+    assert "#define GKS_MAX_CELLS (1LL << 34)" in header
+
+
 def comment_before(text, pos):
     """The last /* ... */ block that ends before pos."""
     end = text.rfind("*/", 0, pos)
